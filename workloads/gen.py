@@ -1,0 +1,232 @@
+"""Seeded input generators for the CROM latent-space step workloads.
+
+Everything here is input preparation: random draws (numpy PCG64 via
+``np.random.default_rng``, identical on x86-64 and aarch64), uniform grids,
+sample-set selection and array packing.  Nothing here evaluates the decoder,
+a PDE update or the Gauss-Newton projection; both the FP64 oracle and the CUDA
+library consume the exact same arrays produced here.
+
+Workload recipes (paper: §5 and App. G/H for the PDEs, App. D for the network):
+
+* ``heat1d_small``   1D heat u_t = u_xx on [0,1], Dirichlet 0, P=256 nodes,
+  u0 = sum_{k=1..4} a_k sin(k pi x), a_k ~ U(-1,1); decoder R^{1+3} -> R,
+  4 ELU layers of width 64, Xavier-normal (seed 0); |M| = 16 distinct interior
+  nodes; dt = 1e-5; 100 steps; 1 Gauss-Newton iteration.
+* ``heat2d_single``  2D heat u_t = alpha Lap u on a 128x128 grid, zero Neumann,
+  alpha = 1; u0 = 8 Gaussian bumps; decoder R^{2+8} -> R, 5 ELU layers of
+  width 128; |M| = 200 interior nodes; dt = 1e-5; 1000 steps; 2 GN iterations.
+* ``recon_dense``    the same 2D decoder with bf16-representable weights; dense
+  reconstruction at 1024^2 points x 64 codes q ~ N(0,1); plus a 2048-sample step.
+* ``heat2d_batched`` 1024 instances of the 2D heat problem, alpha ~ U(0.5, 2),
+  |M_i| ~ U{32..512}, per-instance seeds 1000+i, bf16-representable weights.
+
+Initial latent codes: an untrained, randomly initialised decoder cannot represent
+the Gaussian-bump initial fields, so q0 ~ N(0,1) is drawn per instance (the bumps
+are still generated for the full-order solver).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "DecoderSpec", "bf16_round", "xavier_decoder", "pack_params", "param_count",
+    "interior_nodes_1d", "interior_nodes_2d", "gaussian_bumps_2d", "sine_modes_1d",
+    "StepWorkload", "heat1d_small", "heat2d_single", "heat2d_batched", "recon_dense",
+    "grid_points_2d", "ragged_offsets",
+]
+
+
+@dataclass(frozen=True)
+class DecoderSpec:
+    """Shape of the implicit-neural-representation decoder g: R^{m+r} -> R.
+
+    m: spatial dimension, r: latent dimension, width: hidden width (beta*d in
+    App. D), hidden: number of ELU hidden layers (the output layer is linear).
+    """
+    m: int
+    r: int
+    width: int
+    hidden: int
+
+    @property
+    def dims(self):
+        return [self.m + self.r] + [self.width] * self.hidden + [1]
+
+
+def bf16_round(a: np.ndarray) -> np.ndarray:
+    """Round to the nearest bfloat16 value (ties to even); returns float64.
+
+    Used so that weights drawn here are exactly representable in bf16: the BF16
+    tensor-core path then carries the very same model as the FP64 oracle.
+    """
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    u = (u + 0x7FFF + lsb) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def xavier_decoder(spec: DecoderSpec, seed: int, bias_std: float = 0.0,
+                   bf16_exact: bool = False):
+    """Xavier-normal weights (std = sqrt(2/(fan_in+fan_out))), zero biases (App. D.1).
+
+    Returns a list of (W [out][in], b [out]) float64 pairs, layer 1 first.  Layer 1
+    takes the input vector ordered (x_1..x_m, q_1..q_r).  ``bias_std`` > 0 draws
+    N(0, bias_std^2) biases instead of zeros (used by tests to exercise bias paths).
+    """
+    rng = np.random.default_rng(seed)
+    dims = spec.dims
+    params = []
+    for l in range(len(dims) - 1):
+        fan_in, fan_out = dims[l], dims[l + 1]
+        std = np.sqrt(2.0 / (fan_in + fan_out))
+        W = rng.standard_normal((fan_out, fan_in)) * std
+        b = rng.standard_normal(fan_out) * bias_std if bias_std > 0 else np.zeros(fan_out)
+        if bf16_exact:
+            W, b = bf16_round(W), bf16_round(b)
+        else:
+            W, b = W.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)
+        params.append((W, b))
+    return params
+
+
+def param_count(spec: DecoderSpec) -> int:
+    d = spec.dims
+    return sum(d[l + 1] * d[l] + d[l + 1] for l in range(len(d) - 1))
+
+
+def pack_params(params) -> np.ndarray:
+    """Packed float32 image: for each layer, W row-major [out][in], then b [out]."""
+    parts = []
+    for W, b in params:
+        parts.append(np.asarray(W, dtype=np.float32).ravel())
+        parts.append(np.asarray(b, dtype=np.float32).ravel())
+    return np.ascontiguousarray(np.concatenate(parts))
+
+
+def interior_nodes_1d(P: int, count: int, rng) -> np.ndarray:
+    """Distinct interior nodes i/(P-1), i in 1..P-2, drawn without replacement."""
+    idx = rng.choice(np.arange(1, P - 1), size=count, replace=False)
+    return (idx / (P - 1)).astype(np.float32).reshape(-1, 1)
+
+
+def interior_nodes_2d(n: int, count: int, rng) -> np.ndarray:
+    """Distinct interior nodes (i/(n-1), j/(n-1)), 1 <= i, j <= n-2, without replacement."""
+    inner = n - 2
+    flat = rng.choice(inner * inner, size=count, replace=False)
+    i = flat // inner + 1
+    j = flat % inner + 1
+    return np.stack([i / (n - 1), j / (n - 1)], axis=1).astype(np.float32)
+
+
+def grid_points_2d(n: int) -> np.ndarray:
+    """All n*n nodes of the uniform grid on [0,1]^2, row-major (x1 slow, x2 fast)."""
+    t = np.arange(n) / (n - 1)
+    X1, X2 = np.meshgrid(t, t, indexing="ij")
+    return np.stack([X1.ravel(), X2.ravel()], axis=1).astype(np.float32)
+
+
+def sine_modes_1d(P: int, rng, modes: int = 4):
+    """u0(x) = sum_k a_k sin(k pi x) on x_i = i/(P-1), a_k ~ U(-1,1)."""
+    a = rng.uniform(-1.0, 1.0, size=modes)
+    x = np.arange(P) / (P - 1)
+    u0 = sum(a[k] * np.sin((k + 1) * np.pi * x) for k in range(modes))
+    return a, u0
+
+
+def gaussian_bumps_2d(n: int, rng, count: int = 8):
+    """Sum of Gaussian bumps on the n x n grid: centres U[0,1]^2, sigma ~ U(0.03, 0.1),
+    amplitude ~ U(0.5, 1)."""
+    c = rng.uniform(0.0, 1.0, size=(count, 2))
+    s = rng.uniform(0.03, 0.1, size=count)
+    a = rng.uniform(0.5, 1.0, size=count)
+    t = np.arange(n) / (n - 1)
+    X1, X2 = np.meshgrid(t, t, indexing="ij")
+    u = np.zeros((n, n))
+    for k in range(count):
+        u += a[k] * np.exp(-((X1 - c[k, 0]) ** 2 + (X2 - c[k, 1]) ** 2) / (2 * s[k] ** 2))
+    return u
+
+
+def ragged_offsets(sizes) -> np.ndarray:
+    off = np.zeros(len(sizes) + 1, dtype=np.int32)
+    off[1:] = np.cumsum(sizes)
+    return off
+
+
+@dataclass
+class StepWorkload:
+    """Inputs of one batched latent step (all instances share one decoder)."""
+    name: str
+    spec: DecoderSpec
+    params: list
+    q0: np.ndarray          # [n_inst][r] float64
+    alpha: np.ndarray       # [n_inst] float32 (diffusivity per instance)
+    s_off: np.ndarray       # [n_inst+1] int32
+    samples: np.ndarray     # [S_total][m] float32
+    dt: float
+    gn_iters: int
+    steps: int
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_inst(self) -> int:
+        return int(self.q0.shape[0])
+
+    @property
+    def sizes(self) -> np.ndarray:
+        return np.diff(self.s_off)
+
+
+def heat1d_small(bias_std: float = 0.0) -> StepWorkload:
+    spec = DecoderSpec(m=1, r=3, width=64, hidden=4)
+    params = xavier_decoder(spec, seed=0, bias_std=bias_std)
+    a, u0 = sine_modes_1d(256, np.random.default_rng(1))
+    samples = interior_nodes_1d(256, 16, np.random.default_rng(2))
+    q0 = np.random.default_rng(5).standard_normal((1, spec.r))
+    return StepWorkload("heat1d_P256_M16_r3_w64", spec, params, q0,
+                        np.ones(1, np.float32), ragged_offsets([16]), samples,
+                        dt=1e-5, gn_iters=1, steps=100, extra={"a": a, "u0": u0, "P": 256})
+
+
+def heat2d_single(bias_std: float = 0.0, bf16_exact: bool = False) -> StepWorkload:
+    spec = DecoderSpec(m=2, r=8, width=128, hidden=5)
+    params = xavier_decoder(spec, seed=0, bias_std=bias_std, bf16_exact=bf16_exact)
+    u0 = gaussian_bumps_2d(128, np.random.default_rng(3))
+    samples = interior_nodes_2d(128, 200, np.random.default_rng(6))
+    q0 = np.random.default_rng(5).standard_normal((1, spec.r))
+    return StepWorkload("heat2d_128sq_M200_r8_w128", spec, params, q0,
+                        np.ones(1, np.float32), ragged_offsets([200]), samples,
+                        dt=1e-5, gn_iters=2, steps=1000, extra={"u0": u0, "n": 128})
+
+
+def heat2d_batched(n_inst: int = 1024, m_lo: int = 32, m_hi: int = 512,
+                   bias_std: float = 0.0, bf16_exact: bool = True,
+                   with_bumps: bool = False) -> StepWorkload:
+    spec = DecoderSpec(m=2, r=8, width=128, hidden=5)
+    params = xavier_decoder(spec, seed=0, bias_std=bias_std, bf16_exact=bf16_exact)
+    sizes, alphas, qs, samp, bumps = [], [], [], [], []
+    for i in range(n_inst):
+        rng = np.random.default_rng(1000 + i)
+        alphas.append(rng.uniform(0.5, 2.0))
+        M = int(rng.integers(m_lo, m_hi + 1))
+        sizes.append(M)
+        samp.append(interior_nodes_2d(128, M, rng))
+        qs.append(rng.standard_normal(spec.r))
+        if with_bumps:
+            bumps.append(gaussian_bumps_2d(128, rng))
+    return StepWorkload(f"heat2d_batched_{n_inst}x_M{m_lo}-{m_hi}_r8_w128", spec, params,
+                        np.array(qs), np.array(alphas, dtype=np.float32),
+                        ragged_offsets(sizes), np.concatenate(samp, axis=0),
+                        dt=1e-5, gn_iters=2, steps=1000,
+                        extra={"u0": bumps} if with_bumps else {})
+
+
+def recon_dense(n_side: int = 1024, n_codes: int = 64):
+    """Dense reconstruction workload: grid points, latent codes and the 2D decoder."""
+    spec = DecoderSpec(m=2, r=8, width=128, hidden=5)
+    params = xavier_decoder(spec, seed=0, bf16_exact=True)
+    codes = np.random.default_rng(4).standard_normal((n_codes, spec.r))
+    return spec, params, codes, grid_points_2d(n_side)
