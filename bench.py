@@ -1,0 +1,375 @@
+"""Benchmark of the CROM latent-space step on GB300.
+
+Workload: 1024 independent 2D heat instances sharing one decoder R^{2+8} -> R
+(5 ELU layers of width 128), alpha ~ U(0.5, 2), |M_i| ~ U{32..512} integration
+samples, 2 Gauss-Newton iterations, dt = 1e-5 (seeded synthetic inputs from
+workloads.gen.heat2d_batched).  One bench step = one crom_step call advancing
+every instance by one latent step (decode with derivatives, PDE update,
+Gauss-Newton projection) on the tensor-core path (bf16 hi/lo operands, FP32
+accumulation, FP64 normal equations).
+
+Printed (one JSON line on rank 0): instance-steps/s of that step with inputs
+resident in HBM (L2 flushed before every timed step), the same metric end to
+end through the C ABI with host buffers, the plain FP32 single-instance path
+on the 200-sample 2D heat problem (the reference point of the batched speed-up),
+dense reconstruction throughput, the roofline of the step kernel, clocks, and the
+FP64 oracle timed on a bounded sample on the host cores.
+
+--impl reference times the FP64 oracle (the only reference available: the paper
+ships no code) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "instance-steps/s, batched BF16 vs plain FP32 same GB300, rel-L2<=1e-3 vs FP64"
+WORKLOAD = "heat2d_batched_1024inst_M32-512_r8_w128_L5_gn2"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n-inst", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def step_flops_per_sample(w=128, L=5, m=2, r=8, gn_iters=2):
+    """Algorithmic FLOPs of one sample for the tensor-core step as implemented:
+    forward channels (value, m gradients, 1 Laplacian) at iteration 0, (value,
+    difference) later, one reverse pass per iteration, output and Jacobian
+    projections.  Each w x w contraction costs 2 w^2 per column."""
+    ww = 2 * w * w * (L - 1)
+    f = 0
+    for it in range(gn_iters):
+        nch = 2 + m if it == 0 else 2
+        f += nch * ww + ww                    # forward channels + reverse pass
+        f += 2 * w * nch + 2 * w * r          # output projection + Jacobian projection
+        f += 2 * (m + r) * w                  # layer 1 (CUDA cores)
+    return f
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return pk["bf16_tflops"], pk["hbm_gbs"], "measured"
+    except Exception:
+        return 1900.0, 6800.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0])); mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(w, budget_s=12.0, max_inst=512):
+    """FP64 oracle (single process) on the first instances of the workload until
+    the time budget is used; returns (instance-steps/s, instances done)."""
+    from oracle import crom_oracle as O
+    dec = O.MLPDecoder(w.params, w.spec.m)
+    t0 = time.perf_counter()
+    done = 0
+    samples = 0
+    for i in range(min(w.n_inst, max_inst)):
+        Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
+        O.crom_step(dec, w.q0[i], Y, w.dt, w.gn_iters, alpha=float(w.alpha[i]))
+        done += 1
+        samples += Y.shape[0]
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    # normalise to the workload's mean |M_i| so the unit matches instance-steps/s of the full batch
+    mean_all = float(np.mean(w.sizes))
+    rate_samples = samples / el
+    return rate_samples / mean_all, done, samples, el
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from workloads import gen
+    w = gen.heat2d_batched(n_inst=args.n_inst)
+    times = []
+    inst_done = 0
+    for k in range(args.warmup + args.steps):
+        rate, done, samples, el = cpu_oracle_rate(w, budget_s=3.0, max_inst=64)
+        if k >= args.warmup:
+            times.append(rate)
+            inst_done += done
+    value = float(np.mean(times))
+    line = {"metric": METRIC, "value": value, "unit": "instance-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * args.n_inst / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "global_batch": args.n_inst, "parallelism": "none",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "instance-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: the FP64 numpy oracle on the first instances of the "
+                                       f"workload for ~3 s, normalised by mean |M_i|"},
+            "e2e": {"value": value, "unit": "instance-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    from paper_2206_02607_gb300 import build
+    build()
+    from paper_2206_02607_gb300 import crom
+    from workloads import gen
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    w = gen.heat2d_batched(n_inst=args.n_inst)
+    ctx = crom.crom_create(w.spec.m, w.spec.r, w.spec.width, w.spec.hidden, local)
+    crom.crom_set_weights(ctx, gen.pack_params(w.params))
+    q0 = torch.tensor(w.q0, dtype=torch.float64, device="cuda")
+    q = q0.clone()
+    alpha = torch.tensor(w.alpha, device="cuda")
+    s_off = torch.tensor(w.s_off, device="cuda")
+    samples = torch.tensor(w.samples, device="cuda")
+    status = torch.zeros(w.n_inst, dtype=torch.int32, device="cuda")
+    max_s = int(w.sizes.max())
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+
+    def step(prec=crom.CROM_PREC_BF16X2, qq=None):
+        crom.crom_step(ctx, q if qq is None else qq, alpha, s_off, samples, status, dt=w.dt,
+                       gn_iters=w.gn_iters, max_samples=max_s, precision=prec)
+
+    # ---- device-resident timing, L2 flushed before each timed step
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    sampler = ClockSampler(local)
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = float(np.mean(step_ms))
+    if pg is not None:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    st = status.cpu().numpy()
+    value = world * w.n_inst / (ms * 1e-3)
+
+    # ---- accuracy of the timed configuration: sampled instances vs the FP64 oracle (rank 0)
+    acc = None
+    if rank == 0:
+        from oracle import crom_oracle as O
+        qa = q0.clone()
+        step(qq=qa)
+        torch.cuda.synchronize()
+        qg = qa.cpu().numpy()
+        dec = O.MLPDecoder(w.params, 2)
+        errs, incs = [], []
+        for i in np.random.default_rng(0).choice(w.n_inst, size=6, replace=False):
+            Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
+            ref, _ = O.crom_step(dec, w.q0[i], Y, w.dt, w.gn_iters, alpha=float(w.alpha[i]))
+            errs.append(np.linalg.norm(qg[i] - ref) / np.linalg.norm(ref))
+            incs.append(np.linalg.norm((qg[i] - w.q0[i]) - (ref - w.q0[i])) / np.linalg.norm(ref - w.q0[i]))
+        acc = {"q_rel_l2_max": float(max(errs)), "increment_rel_l2_max": float(max(incs)), "instances": 6}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    hq = torch.tensor(w.q0, dtype=torch.float64).pin_memory()
+    ha = torch.tensor(w.alpha).pin_memory()
+    ho = torch.tensor(w.s_off).pin_memory()
+    hs = torch.tensor(w.samples).pin_memory()
+    hq_out = torch.empty_like(hq).pin_memory()
+    hst = torch.empty(w.n_inst, dtype=torch.int32).pin_memory()
+    dq, da, do, ds = torch.empty_like(q), torch.empty_like(alpha), torch.empty_like(s_off), torch.empty_like(samples)
+    h2d = hq.numel() * 8 + ha.numel() * 4 + ho.numel() * 4 + hs.numel() * 4
+    d2h = hq.numel() * 8 + hst.numel() * 4
+
+    def e2e_step():
+        dq.copy_(hq, non_blocking=True); da.copy_(ha, non_blocking=True)
+        do.copy_(ho, non_blocking=True); ds.copy_(hs, non_blocking=True)
+        crom.crom_step(ctx, dq, da, do, ds, status, dt=w.dt, gn_iters=w.gn_iters, max_samples=max_s,
+                       precision=crom.CROM_PREC_BF16X2)
+        hq_out.copy_(dq, non_blocking=True); hst.copy_(status, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    e2e_value = world * w.n_inst / (e2e_ms * 1e-3)
+
+    # ---- kernel-only duration of the step kernel for the roofline (same stream)
+    # (two launches per call: the ordering kernel and the persistent step kernel)
+    flops = step_flops_per_sample() * int(w.sizes.sum())
+    peak_tf, hbm, peak_kind = load_peaks()
+    achieved_tf = flops / (ms * 1e-3) / 1e12
+
+    # ---- plain FP32 single-instance path (200-sample 2D heat problem)
+    ws = gen.heat2d_single()
+    ctx32 = crom.crom_create(2, 8, 128, 5, local)
+    crom.crom_set_weights(ctx32, gen.pack_params(ws.params))
+    q32 = torch.tensor(ws.q0, dtype=torch.float64, device="cuda")
+    a32 = torch.tensor(ws.alpha, device="cuda")
+    o32 = torch.tensor(ws.s_off, device="cuda")
+    s32 = torch.tensor(ws.samples, device="cuda")
+    st32 = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def step32():
+        crom.crom_step(ctx32, q32, a32, o32, s32, st32, dt=ws.dt, gn_iters=ws.gn_iters, max_samples=200,
+                       precision=crom.CROM_PREC_FP32)
+
+    for _ in range(5):
+        step32()
+    torch.cuda.synchronize()
+    n32 = 200
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n32):
+        step32()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / n32
+    plain_value = 1.0 / (plain_ms * 1e-3)
+
+    # ---- dense reconstruction 1024^2 points x 64 codes
+    spec, params, codes, X = gen.recon_dense()
+    ctxr = crom.crom_create(spec.m, spec.r, spec.width, spec.hidden, local)
+    crom.crom_set_weights(ctxr, gen.pack_params(params))
+    dcodes = torch.tensor(codes, device="cuda")
+    dX = torch.tensor(X, device="cuda")
+    out = torch.empty((codes.shape[0], X.shape[0]), dtype=torch.float32, device="cuda")
+    crom.crom_reconstruct(ctxr, dcodes, dX, out, precision=crom.CROM_PREC_BF16X2)
+    torch.cuda.synchronize()
+    rt = []
+    for _ in range(3):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        crom.crom_reconstruct(ctxr, dcodes, dX, out, precision=crom.CROM_PREC_BF16X2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rt.append(e0.elapsed_time(e1))
+    recon_ms = float(np.median(rt))
+    recon_pts = codes.shape[0] * X.shape[0]
+    recon_flops = recon_pts * 2 * (2 * 128 + 4 * 128 * 128 + 128)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, done, ns, el = cpu_oracle_rate(w, budget_s=12.0)
+        cpu = {"value": rate, "unit": "instance-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"FP64 numpy oracle, one step of the first {done} instances ({ns} samples, "
+                         f"{el:.1f} s), normalised by the workload's mean |M_i|"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "instance-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x2 (bf16 hi/lo operands, f32 accum, f64 solve)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": world * w.n_inst, "samples_per_step": int(w.sizes.sum()),
+                       "parallelism": f"instances sharded, {w.n_inst} per GPU" if world > 1 else "single GPU",
+                       "l2": "flushed (256 MB write) before every timed step"},
+            "status_all_ok": bool(np.all(st == 0)),
+            "accuracy_vs_fp64_oracle": acc,
+            "plain_fp32_single": {"value": plain_value, "unit": "instance-steps/s", "us_per_step": plain_ms * 1e3,
+                                  "workload": "heat2d_single_M200_r8_w128_L5_gn2 (FP32 CUDA cores)"},
+            "speedup_vs_plain_fp32": value / world / plain_value,
+            "dense_reconstruction": {"points_per_s": recon_pts / (recon_ms * 1e-3), "ms": recon_ms,
+                                     "tflops_algorithmic": recon_flops / (recon_ms * 1e-3) / 1e12,
+                                     "workload": "1024^2 points x 64 codes, BF16X2"},
+            "roofline": {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": achieved_tf / peak_tf, "traffic": None,
+                         "note": f"step kernel, algorithmic FLOPs {step_flops_per_sample()} per sample x "
+                                 f"{int(w.sizes.sum())} samples; peak = {peak_kind} bf16 burst"},
+            "e2e": {"value": e2e_value, "unit": "instance-steps/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    ctx.close(); ctx32.close(); ctxr.close()
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

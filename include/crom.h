@@ -1,0 +1,164 @@
+/*
+ * crom.h — C ABI of the GB300 (sm_103a) implementation of CROM's online
+ * latent-space time step (Continuous Reduced-Order Modeling, arXiv 2206.02607).
+ *
+ * The decoder g(x, q): R^{m+r} -> R is an MLP with `hidden` ELU layers of width
+ * `width` and a linear output layer (paper App. D).  One latent step
+ * q_n -> q_{n+1} (paper Algorithm 3) is:
+ *   1. network inference at the integration samples y_j in M: g, dg/dx, the
+ *      network Laplacian and dg/dq (paper §4.1, Algorithm 4, Algorithm 2);
+ *   2. explicit PDE update Delta f_j at every sample (paper §4.2, Eqs.
+ *      discrete-time / time-integration; App. G and H for the heat equation);
+ *   3. network inversion by Gauss-Newton on
+ *      min_q sum_j (g(y_j, q) - g(y_j, q_n) - Delta f_j)^2 from q^(0) = q_n
+ *      (paper §4.3, Eq. invert; App. C), each iteration solving the r x r normal
+ *      equations by an FP64 Cholesky factorisation.
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers owned by the caller (e.g. from
+ *     torch.empty(...).data_ptr()), unless an argument says otherwise.  The
+ *     context owns only its weight images and its scratch.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream).  Nothing is synchronised unless stated.
+ *   - The return value is a crom_status.  Host-side argument checks return
+ *     CROM_ERR_INVALID_ARG before anything is launched; CUDA launch errors return
+ *     CROM_ERR_CUDA.  crom_last_error() gives a message for the calling thread.
+ *   - Per-instance numerical failures of crom_step are written to status[i]
+ *     (the call itself still returns CROM_OK); q[i] then keeps its last good
+ *     iterate.
+ *   - There is no CPU fallback: without a usable sm_103a device every compute
+ *     entry point returns CROM_ERR_CUDA.
+ */
+#ifndef CROM_H
+#define CROM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct crom_ctx crom_ctx;
+typedef void* crom_stream; /* cudaStream_t */
+
+typedef enum {
+  CROM_OK = 0,
+  CROM_ERR_INVALID_ARG = 1, /* also: r > |M_i| (well-posedness r <= d|M|, paper §4.4) */
+  CROM_ERR_CUDA = 2,
+  CROM_ERR_SINGULAR = 3,    /* Cholesky pivot <= 1e-14 * max diag(J^T J) */
+  CROM_ERR_NONFINITE = 4,   /* NaN/Inf in J^T J or J^T rho */
+  CROM_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
+  CROM_ERR_UNSUPPORTED = 6  /* shape or precision not built for this entry point */
+} crom_status;
+
+/* Arithmetic of the decoder evaluation.
+ *  FP32   : CUDA-core FP32 forward-mode channels (paper Algorithm 2), FP64 normal
+ *           equations.  Any shape with width % 32 == 0, width <= 256.
+ *  BF16X2 : tcgen05 tensor cores, bf16 operands with FP32 accumulation.  Every
+ *           activation operand is split into a bf16 high part and a bf16 low part
+ *           (two MMAs into one accumulator), weights are rounded once to bf16.
+ *           FP32 activation/derivative chains, FP64 normal equations.
+ *           width == 128, 2 <= hidden <= 5, m <= 2, r <= 15.
+ *  BF16   : as BF16X2 with the high part only (one MMA per layer).  Dense
+ *           reconstruction only. */
+typedef enum { CROM_PREC_FP32 = 0, CROM_PREC_BF16X2 = 1, CROM_PREC_BF16 = 2 } crom_precision;
+
+typedef enum { CROM_PDE_HEAT = 0, CROM_PDE_ADVDIFF = 1 } crom_pde;
+
+/* Channels requested from crom_decode.  Output rows appear in this order:
+ * VAL (1 row), DX (m rows, dg/dx_k), DXX (m rows, d2g/dx_k^2), LAP (1 row,
+ * sum_k d2g/dx_k^2), DQ (r rows, dg/dq_j). */
+enum {
+  CROM_WANT_VAL = 1u,
+  CROM_WANT_DX = 2u,
+  CROM_WANT_DXX = 4u,
+  CROM_WANT_LAP = 8u,
+  CROM_WANT_DQ = 16u
+};
+
+/* Decoder shape: m spatial dims (1..3), r latent dims (1..32), width of the
+ * hidden layers, hidden = number of ELU hidden layers (1..8).  Output dim d = 1. */
+typedef struct {
+  int m;
+  int r;
+  int width;
+  int hidden;
+} crom_decoder_desc;
+
+/* One latent step.
+ *  pde      : CROM_PDE_HEAT     Delta f_j = dt * alpha_i * Lap g(y_j, q_n)
+ *             CROM_PDE_ADVDIFF  Delta f_j = dt * (-vel_j . grad g + alpha_i * Lap g)
+ *             (alpha_i plays the role of nu for advection-diffusion)
+ *  gn_iters : Gauss-Newton iterations per step, 1..16 (1 = the linearised least
+ *             squares of paper App. C.2)
+ *  dt       : time step (finite, > 0) */
+typedef struct {
+  int pde;
+  int gn_iters;
+  double dt;
+} crom_step_desc;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int crom_version(void);
+
+/* Message describing the last failed call on this thread ("" if none). */
+const char* crom_last_error(void);
+
+/* Create a context for one decoder shape on CUDA device `device` (made current
+ * for the duration of the call).  *out receives the context; release it with
+ * crom_destroy.  Returns CROM_ERR_CUDA if no sm_103a-capable device is usable. */
+int crom_create(crom_ctx** out, const crom_decoder_desc* desc, int device);
+
+/* Free every device buffer the context owns.  Synchronises the device. */
+int crom_destroy(crom_ctx* ctx);
+
+/* Load decoder weights.  `params` is a packed FP32 image of n floats: for each
+ * layer l = 1..hidden+1, W_l row-major [out][in] then b_l [out]; layer 1 takes
+ * (x_1..x_m, q_1..q_r).  n must equal the parameter count.  params_on_device
+ * selects whether `params` is a device (1) or host (0) pointer.  The call builds
+ * the FP32 copies and the bf16 tensor-core images and synchronises `stream`. */
+int crom_set_weights(crom_ctx* ctx, const float* params, size_t n, int params_on_device,
+                     crom_stream stream);
+
+/* Step 1 alone (paper §4.1, Algorithm 4; Algorithm 2 for the derivatives), FP32.
+ * n_inst latent codes q [n_inst][r] (FP64); point set of instance i is
+ * x[pt_off[i] .. pt_off[i+1]) with x [n_pts][m] FP32 and pt_off [n_inst+1]
+ * int32 (pt_off[0] = 0, pt_off[n_inst] = n_pts, non-decreasing).  `want` is a
+ * mask of CROM_WANT_*; out is channel-major [C][n_pts] FP32 with C rows in the
+ * order given above.  n_pts may be 0. */
+int crom_decode(crom_ctx* ctx, int n_inst, const double* q, const int* pt_off, const float* x,
+                int n_pts, unsigned want, float* out, crom_stream stream);
+
+/* One latent step for n_inst independent instances sharing the decoder
+ * (paper Algorithm 3).  Instance i has latent state q[i] (FP64 [n_inst][r],
+ * updated in place), coefficient alpha[i] (FP32), and integration samples
+ * samples[s_off[i] .. s_off[i+1]) (FP32 [n_samples][m]; s_off int32
+ * [n_inst+1], s_off[0] = 0, s_off[n_inst] = n_samples).  vel (FP32
+ * [n_samples][m]) is the advection velocity at each sample, required for
+ * CROM_PDE_ADVDIFF and ignored (may be NULL) otherwise.  max_samples must bound
+ * every |M_i|; an instance with |M_i| > max_samples or |M_i| < r gets
+ * status CROM_ERR_INVALID_ARG and is left unchanged.  status [n_inst] int32
+ * receives CROM_OK / CROM_ERR_SINGULAR / CROM_ERR_NONFINITE /
+ * CROM_ERR_INVALID_ARG per instance.
+ * precision CROM_PREC_FP32: each GN iteration is one launch spreading an
+ *   instance over several CTAs (the last CTA to finish reduces and solves); the
+ *   context grows its scratch on first use, so the first call for a given size
+ *   must not be made during stream capture.
+ * precision CROM_PREC_BF16X2: one persistent launch per step; each CTA takes
+ *   whole instances from a queue (|M_i| <= 2048). */
+int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_inst, double* q,
+              const float* alpha, const float* vel, const int* s_off, const float* samples,
+              int n_samples, int max_samples, int* status, crom_stream stream);
+
+/* Dense reconstruction g(x_p, q_c) for n_codes latent codes q [n_codes][r]
+ * (FP64) at n_pts points x [n_pts][m] (FP32); out [n_codes][n_pts] FP32.
+ * precision FP32 (any shape), BF16X2 or BF16 (tensor cores; width 128). */
+int crom_reconstruct(crom_ctx* ctx, int precision, int n_codes, const double* q, int n_pts,
+                     const float* x, float* out, crom_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CROM_H */

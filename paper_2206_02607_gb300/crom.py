@@ -1,0 +1,186 @@
+"""Thin ctypes binding of the C ABI in include/crom.h.
+
+Every function here only marshals arguments (torch CUDA tensors -> device
+pointers, the current torch stream -> cudaStream_t) and raises on a non-zero
+status.  All arithmetic of the latent step runs in libcrom.so's CUDA kernels;
+there is no fallback: importing this module fails when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libcrom.so")
+
+CROM_OK = 0
+CROM_ERR_INVALID_ARG = 1
+CROM_ERR_CUDA = 2
+CROM_ERR_SINGULAR = 3
+CROM_ERR_NONFINITE = 4
+CROM_ERR_TIMEOUT = 5
+CROM_ERR_UNSUPPORTED = 6
+
+CROM_PREC_FP32 = 0
+CROM_PREC_BF16X2 = 1
+CROM_PREC_BF16 = 2
+
+CROM_PDE_HEAT = 0
+CROM_PDE_ADVDIFF = 1
+
+CROM_WANT_VAL = 1
+CROM_WANT_DX = 2
+CROM_WANT_DXX = 4
+CROM_WANT_LAP = 8
+CROM_WANT_DQ = 16
+
+# Every symbol include/crom.h declares.
+EXPORTED = ("crom_version", "crom_last_error", "crom_create", "crom_destroy", "crom_set_weights",
+            "crom_decode", "crom_step", "crom_reconstruct")
+
+
+class CromError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"crom status {code}: {msg}")
+        self.code = code
+
+
+class crom_decoder_desc(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("r", ctypes.c_int), ("width", ctypes.c_int), ("hidden", ctypes.c_int)]
+
+
+class crom_step_desc(ctypes.Structure):
+    _fields_ = [("pde", ctypes.c_int), ("gn_iters", ctypes.c_int), ("dt", ctypes.c_double)]
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with __graft_entry__.build() "
+                          "(nvcc for sm_103a); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    vp, i, u, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_double, ctypes.c_size_t
+    lib.crom_version.restype = i
+    lib.crom_last_error.restype = ctypes.c_char_p
+    lib.crom_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(crom_decoder_desc), i]
+    lib.crom_destroy.argtypes = [vp]
+    lib.crom_set_weights.argtypes = [vp, vp, sz, i, vp]
+    lib.crom_decode.argtypes = [vp, i, vp, vp, vp, i, u, vp, vp]
+    lib.crom_step.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, i, vp, vp, vp, vp, vp, i, i, vp, vp]
+    lib.crom_reconstruct.argtypes = [vp, i, i, vp, i, vp, vp, vp]
+    for name in EXPORTED:
+        if name not in ("crom_version", "crom_last_error"):
+            getattr(lib, name).restype = i
+    return lib
+
+
+_LIB = load_library()
+
+
+def lib() -> ctypes.CDLL:
+    return _LIB
+
+
+def _check(code: int):
+    if code != CROM_OK:
+        raise CromError(code, _LIB.crom_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need(t, dtype, name):
+    import torch
+    if t is None:
+        return
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+
+
+def crom_version() -> int:
+    return _LIB.crom_version()
+
+
+class CromContext:
+    """Owns a crom_ctx (decoder shape + weights on one device)."""
+
+    def __init__(self, m: int, r: int, width: int, hidden: int, device: int = 0):
+        self.desc = crom_decoder_desc(m, r, width, hidden)
+        self.handle = ctypes.c_void_p()
+        _check(_LIB.crom_create(ctypes.byref(self.handle), ctypes.byref(self.desc), device))
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            _LIB.crom_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def crom_create(m, r, width, hidden, device=0) -> CromContext:
+    return CromContext(m, r, width, hidden, device)
+
+
+def crom_destroy(ctx: CromContext):
+    ctx.close()
+
+
+def crom_set_weights(ctx: CromContext, params, stream=None):
+    """params: packed float32 image (numpy array on the host, or a CUDA tensor)."""
+    import numpy as np
+    if hasattr(params, "is_cuda") and params.is_cuda:
+        _need(params, params.dtype, "params")
+        _check(_LIB.crom_set_weights(ctx.handle, _ptr(params), params.numel(), 1, _stream(stream)))
+    else:
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        _check(_LIB.crom_set_weights(ctx.handle, a.ctypes.data_as(ctypes.c_void_p), a.size, 0,
+                                     _stream(stream)))
+
+
+def crom_decode(ctx: CromContext, q, pt_off, x, want: int, out, stream=None):
+    import torch
+    _need(q, torch.float64, "q"); _need(pt_off, torch.int32, "pt_off")
+    _need(x, torch.float32, "x"); _need(out, torch.float32, "out")
+    _check(_LIB.crom_decode(ctx.handle, q.shape[0], _ptr(q), _ptr(pt_off), _ptr(x), x.shape[0], want,
+                            _ptr(out), _stream(stream)))
+
+
+def crom_step(ctx: CromContext, q, alpha, s_off, samples, status, *, dt: float, gn_iters: int,
+              max_samples: int, pde: int = CROM_PDE_HEAT, vel=None, precision: int = CROM_PREC_FP32,
+              stream=None):
+    import torch
+    _need(q, torch.float64, "q"); _need(alpha, torch.float32, "alpha"); _need(s_off, torch.int32, "s_off")
+    _need(samples, torch.float32, "samples"); _need(status, torch.int32, "status"); _need(vel, torch.float32, "vel")
+    desc = crom_step_desc(pde, gn_iters, dt)
+    _check(_LIB.crom_step(ctx.handle, ctypes.byref(desc), precision, q.shape[0], _ptr(q), _ptr(alpha),
+                          _ptr(vel), _ptr(s_off), _ptr(samples), samples.shape[0], max_samples, _ptr(status),
+                          _stream(stream)))
+
+
+def crom_reconstruct(ctx: CromContext, q, x, out, precision: int = CROM_PREC_FP32, stream=None):
+    import torch
+    _need(q, torch.float64, "q"); _need(x, torch.float32, "x"); _need(out, torch.float32, "out")
+    _check(_LIB.crom_reconstruct(ctx.handle, precision, q.shape[0], _ptr(q), x.shape[0], _ptr(x), _ptr(out),
+                                 _stream(stream)))
+
+
+def raw_call(name: str, *args) -> int:
+    """Direct access to a C entry point (used by tests that feed host pointers or
+    invalid arguments); returns the status code."""
+    return getattr(_LIB, name)(*args)
+
+
+def last_error() -> str:
+    return _LIB.crom_last_error().decode()

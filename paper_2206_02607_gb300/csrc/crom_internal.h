@@ -1,0 +1,94 @@
+// Internal declarations shared by the C-ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/crom.h"
+
+namespace crom {
+
+// Tensor-core decoder image (bf16), one per context.  Layout in bytes, every
+// part 1024-byte aligned so that it can be bulk-copied into shared memory and
+// used there directly as 128B-swizzled UMMA operands:
+//   [0, L*32768)           hidden matrices W_2..W_{hidden}, each 128x128 bf16,
+//                          K-major, 128B swizzle, two 64-column k-blocks
+//   [L*32768, +4096)       projection matrix P (16 x 128 bf16, K-major, SW128):
+//                          row 0 = w_out, rows 1..r = W_1[:, m+j] (dg/dq projection)
+constexpr int kTcWidth = 128;
+constexpr int kTcLayerBytes = kTcWidth * kTcWidth * 2;
+constexpr int kTcProjRows = 16;
+constexpr int kTcProjBytes = kTcProjRows * kTcWidth * 2;
+
+struct DeviceWeights {
+  // FP32 copies for the CUDA-core path.
+  float* w1 = nullptr;    // [width][m+r] row-major
+  float* b1 = nullptr;    // [width]
+  float* wt = nullptr;    // (hidden-1) x [width(in)][width(out)]: transposed hidden matrices
+  float* bh = nullptr;    // (hidden-1) x [width]
+  float* wout = nullptr;  // [width]
+  float bout = 0.f;
+  // bf16 tensor-core image (see above); nullptr when width != 128.
+  uint8_t* tc_img = nullptr;
+  size_t tc_img_bytes = 0;
+};
+
+}  // namespace crom
+
+struct crom_ctx {
+  int device = 0;
+  int num_sms = 0;
+  crom_decoder_desc desc{};
+  bool has_weights = false;
+  crom::DeviceWeights w;
+  // Scratch of the FP32 multi-CTA step (grown on demand, never shrunk).
+  double* partials = nullptr;  // [n_inst][max_tiles][n_entries]
+  size_t partials_cap = 0;     // in doubles
+  int* counters = nullptr;     // [n_inst], zero between launches
+  size_t counters_cap = 0;
+  double* targets = nullptr;   // [n_samples]: Delta f_j (FP64) from GN iteration 0
+  size_t targets_cap = 0;
+  double* qbase = nullptr;     // [n_inst][r]: q_n kept for the difference channel
+  size_t qbase_cap = 0;
+  // Scratch of the tensor-core step: instance order (largest |M_i| first) and the
+  // queue counter / timeout flag.
+  int* order = nullptr;
+  size_t order_cap = 0;
+  int* queue = nullptr;
+};
+
+namespace crom {
+
+void set_error(const std::string& msg);
+
+// Channel configuration of the FP32 forward-mode evaluation.
+enum SecondOrder { kSecondNone = 0, kSecondPerK = 1, kSecondLap = 2 };
+
+struct ChannelSet {
+  int nx;      // number of dg/dx_k channels carried (0 or m)
+  int second;  // SecondOrder
+  int nq;      // number of dg/dq_j channels carried (0 or r)
+  int count(int m) const { return 1 + nx + (second == kSecondPerK ? m : (second == kSecondLap ? 1 : 0)) + nq; }
+};
+
+// FP32 CUDA-core launches (simt_fp32.cu).
+cudaError_t launch_decode_fp32(const crom_ctx* ctx, int n_inst, const double* q, const int* pt_off,
+                               const float* x, int n_pts, unsigned want, float* out, cudaStream_t s);
+cudaError_t launch_recon_fp32(const crom_ctx* ctx, int n_codes, const double* q, int n_pts,
+                              const float* x, float* out, cudaStream_t s);
+cudaError_t launch_step_fp32(crom_ctx* ctx, const crom_step_desc* step, int n_inst, double* q,
+                             const float* alpha, const float* vel, const int* s_off,
+                             const float* samples, int n_samples, int max_samples, int* status,
+                             cudaStream_t s);
+
+// Tensor-core launches (tc_step.cu, tc_recon.cu).
+cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, double* q,
+                           const float* alpha, const float* vel, const int* s_off,
+                           const float* samples, int max_samples, int* status, cudaStream_t s);
+cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const double* q, int n_pts,
+                            const float* x, float* out, cudaStream_t s);
+int tc_step_max_samples();
+
+}  // namespace crom

@@ -1,0 +1,591 @@
+// FP32 CUDA-core path: forward-mode decoder evaluation with derivative channels
+// (paper Algorithm 2, App. E.1.1, extended to second order), used by
+// crom_decode, FP32 crom_reconstruct and the plain FP32 crom_step.
+//
+// One CTA = one thread per hidden unit (blockDim = width) and a tile of S
+// samples.  All channels of a (unit, sample) pair live in one thread, so the
+// ELU chain rule needs no communication:
+//   z = W h + b;  dz = W dh;  d2z = W d2h
+//   h = s(z);     dh = s'(z) dz;  d2h = s''(z) dz^2 + s'(z) d2z
+// The activations of the whole tile (width x S*C floats) sit in shared memory;
+// the transposed hidden matrices are read through L1 (coalesced in the unit index).
+//
+// The FP32 step spreads one instance over ceil(|M_i| / S) CTAs.  Each CTA forms
+// its partial normal equations sum_j J_j J_j^T and sum_j J_j rho_j in FP64 from
+// the FP32 Jacobian rows (exact products), writes them to scratch and takes a
+// ticket; the CTA holding the last ticket adds the partials in tile order
+// (deterministic), solves by FP64 Cholesky and updates q (paper §4.3, App. C).
+// Nothing ever waits on another CTA.
+#include <math.h>
+
+#include "crom_internal.h"
+
+namespace crom {
+namespace {
+
+constexpr int kMaxM = 3;
+constexpr int kMaxR = 32;
+
+enum Mode { kModeDecode = 0, kModeRecon = 1, kModeStep = 2 };
+
+struct FwdParams {
+  int mode;
+  // decoder
+  int m, r, width, hidden;
+  const float* w1;
+  const float* b1;
+  const float* wt;
+  const float* bh;
+  const float* wout;
+  float bout;
+  // channels carried: [value, (difference), dg/dx_k..., second order..., dg/dq_j...]
+  int diff, nx, second, nq, C;
+  int S;   // samples per CTA
+  int LD;  // row stride (floats) of the activation buffers
+  // inputs
+  const double* q;  // [n][r]
+  const int* off;   // decode: pt_off, step: s_off
+  const float* x;   // [n][m]
+  int n_pts;
+  int n_inst;
+  // decode / recon
+  float* out;
+  unsigned want;
+  // step
+  int iter;
+  int pde;
+  double dt;
+  const float* alpha;
+  const float* vel;
+  int max_samples;
+  double* qio;
+  int* status;
+  double* partials;
+  int max_tiles;
+  int n_entries;
+  int* counters;
+  double* targets;  // Delta f_j per sample (FP64), written at GN iteration 0
+  double* qbase;    // q_n per instance, written at GN iteration 0
+};
+
+__device__ __forceinline__ void elu3(float z, float& s0, float& s1, float& s2) {
+  if (z > 0.f) {
+    s0 = z;
+    s1 = 1.f;
+    s2 = 0.f;
+  } else {
+    float e = expf(z);
+    s0 = expm1f(z);
+    s1 = e;
+    s2 = e;
+  }
+}
+
+// s(a) - s(a - d) without cancellation: the difference channel carries
+// h(q^(k)) - h(q_n) through the network, so that the Gauss-Newton residual
+// g(y, q^(k)) - g(y, q_n) - Delta f keeps its relative accuracy when the two
+// evaluations agree to many digits.
+__device__ __forceinline__ float elu_diff(float a, float d) {
+  const float b = a - d;
+  if (a > 0.f && b > 0.f) return d;
+  if (a <= 0.f && b <= 0.f) return -expf(a) * expm1f(-d);
+  const float sa = a > 0.f ? a : expm1f(a);
+  const float sb = b > 0.f ? b : expm1f(b);
+  return sa - sb;
+}
+
+// Apply the activation chain in place to row `row` (pre-activation channels of
+// one hidden unit for S samples).
+__device__ __forceinline__ void activate_row(float* row, const FwdParams& p) {
+  const int C = p.C;
+  for (int s = 0; s < p.S; ++s) {
+    float* c = row + s * C;
+    float s0, s1, s2;
+    const float za = c[0];
+    elu3(za, s0, s1, s2);
+    c[0] = s0;
+    if (p.diff) c[1] = elu_diff(za, c[1]);
+    const int ox = 1 + p.diff;
+    float zx[kMaxM];
+    float sq = 0.f;
+    for (int k = 0; k < p.nx; ++k) {
+      zx[k] = c[ox + k];
+      c[ox + k] = s1 * zx[k];
+      sq += zx[k] * zx[k];
+    }
+    int o = ox + p.nx;
+    if (p.second == kSecondPerK) {
+      for (int k = 0; k < p.m; ++k) c[o + k] = s2 * zx[k] * zx[k] + s1 * c[o + k];
+      o += p.m;
+    } else if (p.second == kSecondLap) {
+      c[o] = s2 * sq + s1 * c[o];
+      o += 1;
+    }
+    for (int j = 0; j < p.nq; ++j) c[o + j] *= s1;
+  }
+}
+
+__device__ int find_instance(const int* off, int n_inst, int point) {
+  int lo = 0, hi = n_inst - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&off[mid]) <= point) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void fwd_fp32_kernel(FwdParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int u = threadIdx.x;
+  const int W = p.width, S = p.S, C = p.C, LD = p.LD, m = p.m, r = p.r;
+  const int NP = S * C;
+  const int NPP = (NP + 15) & ~15;
+
+  float* Hin = reinterpret_cast<float*>(smem_raw);
+  float* Hout = Hin + W * LD;
+  double* qs = reinterpret_cast<double*>(Hout + W * LD);  // [S][r]
+  double* rho = qs + S * r;                               // [S]
+  double* Amat = rho + S;                                 // [r][r + 1]
+  double* dqs = Amat + r * (r + 1);                       // [r]: q^(k) - q_n
+  float* xs = reinterpret_cast<float*>(dqs + r);          // [S][m]
+  float* outv = xs + S * m;                               // [NPP]
+  __shared__ int s_flag;
+
+  // ---- which samples does this CTA own?
+  int inst = 0, first = 0, ns = 0, ntiles = 0, msz = 0;
+  if (p.mode == kModeStep) {
+    inst = blockIdx.x;
+    const int t = blockIdx.y;
+    const int o0 = __ldg(&p.off[inst]);
+    msz = __ldg(&p.off[inst + 1]) - o0;
+    if (p.iter == 0) {
+      if (msz < r || msz > p.max_samples) {
+        if (t == 0 && u == 0) p.status[inst] = CROM_ERR_INVALID_ARG;
+        return;
+      }
+    } else if (p.status[inst] != CROM_OK) {
+      return;
+    }
+    ntiles = (msz + S - 1) / S;
+    if (t >= ntiles) return;
+    first = o0 + t * S;
+    ns = min(S, msz - t * S);
+  } else {
+    first = blockIdx.x * S;
+    ns = min(S, p.n_pts - first);
+    if (ns <= 0) return;
+  }
+
+  // ---- stage coordinates and latent codes (padding samples repeat the first one)
+  for (int i = u; i < S * m; i += W) {
+    const int s = i / m, k = i % m;
+    xs[i] = p.x[(size_t)(first + (s < ns ? s : 0)) * m + k];
+  }
+  for (int i = u; i < S * r; i += W) {
+    const int s = i / r, j = i % r;
+    int code;
+    if (p.mode == kModeStep) code = inst;
+    else if (p.mode == kModeRecon) code = blockIdx.y;
+    else code = find_instance(p.off, p.n_inst, first + (s < ns ? s : 0));
+    qs[i] = (p.mode == kModeStep) ? p.qio[(size_t)code * r + j] : p.q[(size_t)code * r + j];
+  }
+  if (p.diff)
+    for (int j = u; j < r; j += W) dqs[j] = p.qio[(size_t)inst * r + j] - p.qbase[(size_t)inst * r + j];
+  for (int i = u; i < 2 * W * LD; i += W) Hin[i] = 0.f;  // zero both buffers incl. padding
+  __syncthreads();
+
+  // ---- layer 1: pre-activation channels of unit u, then the activation chain
+  {
+    float* row = Hin + u * LD;
+    const float* w1 = p.w1 + (size_t)u * (m + r);
+    const double b1 = (double)p.b1[u];
+    double cshared = b1;
+    const bool shared_q = (p.mode != kModeDecode);
+    if (shared_q) {
+      for (int j = 0; j < r; ++j) cshared += (double)w1[m + j] * qs[j];
+    }
+    double zd = 0.0;
+    if (p.diff) {
+      for (int j = 0; j < r; ++j) zd += (double)w1[m + j] * dqs[j];
+    }
+    for (int s = 0; s < S; ++s) {
+      double c = cshared;
+      if (!shared_q) {
+        c = b1;
+        for (int j = 0; j < r; ++j) c += (double)w1[m + j] * qs[s * r + j];
+      }
+      float z = (float)c;
+      for (int k = 0; k < m; ++k) z = fmaf(w1[k], xs[s * m + k], z);
+      float* ch = row + s * C;
+      ch[0] = z;
+      if (p.diff) ch[1] = (float)zd;
+      const int ox = 1 + p.diff;
+      for (int k = 0; k < p.nx; ++k) ch[ox + k] = w1[k];
+      int o = ox + p.nx;
+      const int n2 = (p.second == kSecondPerK) ? m : (p.second == kSecondLap ? 1 : 0);
+      for (int k = 0; k < n2; ++k) ch[o + k] = 0.f;
+      o += n2;
+      for (int j = 0; j < p.nq; ++j) ch[o + j] = w1[m + j];
+    }
+    activate_row(row, p);
+  }
+  __syncthreads();
+
+  // ---- hidden layers 2..hidden
+  for (int l = 0; l < p.hidden - 1; ++l) {
+    const float* Wt = p.wt + (size_t)l * W * W;
+    float* orow = Hout + u * LD;
+    for (int j0 = 0; j0 < NPP; j0 += 16) {
+      float acc[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+      const float* hcol = Hin + j0;
+#pragma unroll 4
+      for (int k = 0; k < W; ++k) {
+        const float wk = __ldg(&Wt[(size_t)k * W + u]);
+        const float4* h4 = reinterpret_cast<const float4*>(hcol + k * LD);
+        const float4 a = h4[0], b = h4[1], c = h4[2], d = h4[3];
+        acc[0] = fmaf(wk, a.x, acc[0]);  acc[1] = fmaf(wk, a.y, acc[1]);
+        acc[2] = fmaf(wk, a.z, acc[2]);  acc[3] = fmaf(wk, a.w, acc[3]);
+        acc[4] = fmaf(wk, b.x, acc[4]);  acc[5] = fmaf(wk, b.y, acc[5]);
+        acc[6] = fmaf(wk, b.z, acc[6]);  acc[7] = fmaf(wk, b.w, acc[7]);
+        acc[8] = fmaf(wk, c.x, acc[8]);  acc[9] = fmaf(wk, c.y, acc[9]);
+        acc[10] = fmaf(wk, c.z, acc[10]); acc[11] = fmaf(wk, c.w, acc[11]);
+        acc[12] = fmaf(wk, d.x, acc[12]); acc[13] = fmaf(wk, d.y, acc[13]);
+        acc[14] = fmaf(wk, d.z, acc[14]); acc[15] = fmaf(wk, d.w, acc[15]);
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) orow[j0 + i] = acc[i];
+    }
+    const float bias = p.bh[(size_t)l * W + u];
+    for (int s = 0; s < S; ++s) orow[s * C] += bias;
+    activate_row(orow, p);
+    __syncthreads();
+    float* tmp = Hin; Hin = Hout; Hout = tmp;
+  }
+
+  // ---- linear output layer: one thread per (sample, channel) column
+  for (int t = u; t < NP; t += W) {
+    float acc = 0.f;
+    for (int k = 0; k < W; ++k) acc = fmaf(__ldg(&p.wout[k]), Hin[k * LD + t], acc);
+    if (t % C == 0) acc += p.bout;
+    outv[t] = acc;
+  }
+  __syncthreads();
+
+  if (p.mode == kModeRecon) {
+    if (u < ns) p.out[(size_t)blockIdx.y * p.n_pts + first + u] = outv[u * C];
+    return;
+  }
+  const int n2 = (p.second == kSecondPerK) ? m : (p.second == kSecondLap ? 1 : 0);
+  const int ox = 1 + p.diff, o2 = ox + p.nx, oq = o2 + n2;
+  if (p.mode == kModeDecode) {
+    for (int s = u; s < ns; s += W) {
+      const float* c = outv + s * C;
+      const size_t N = (size_t)p.n_pts, pt = (size_t)(first + s);
+      int row = 0;
+      if (p.want & CROM_WANT_VAL) p.out[(row++) * N + pt] = c[0];
+      if (p.want & CROM_WANT_DX)
+        for (int k = 0; k < m; ++k) p.out[(row++) * N + pt] = c[ox + k];
+      if (p.want & CROM_WANT_DXX)
+        for (int k = 0; k < m; ++k) p.out[(row++) * N + pt] = c[o2 + k];
+      if (p.want & CROM_WANT_LAP) {
+        float lap = 0.f;
+        for (int k = 0; k < n2; ++k) lap += c[o2 + k];
+        p.out[(row++) * N + pt] = lap;
+      }
+      if (p.want & CROM_WANT_DQ)
+        for (int j = 0; j < r; ++j) p.out[(row++) * N + pt] = c[oq + j];
+    }
+    return;
+  }
+
+  // ---- step: residual per sample (Step 2 at iteration 0), partial normal equations
+  const int t = blockIdx.y;
+  for (int s = u; s < S; s += W) {
+    double res = 0.0;
+    if (s < ns) {
+      const float* c = outv + s * C;
+      const size_t j = (size_t)(first + s);
+      if (p.iter == 0) {
+        double df;
+        const double a = (double)p.alpha[inst];
+        if (p.pde == CROM_PDE_HEAT) {
+          df = p.dt * a * (double)c[o2];
+        } else {
+          double adv = 0.0;
+          for (int k = 0; k < m; ++k) adv += (double)p.vel[j * m + k] * (double)c[ox + k];
+          df = p.dt * (-adv + a * (double)c[o2]);
+        }
+        p.targets[j] = df;
+        res = -df;  // g(y_j, q^(0)) - f_{n+1}(y_j) with f_{n+1} = g(y_j, q_n) + Delta f_j
+      } else {
+        // g(y_j, q^(k)) - f_{n+1}(y_j) = [g(y_j, q^(k)) - g(y_j, q_n)] - Delta f_j,
+        // the bracket being the difference channel.
+        res = (double)c[1] - p.targets[j];
+      }
+    }
+    rho[s] = res;
+  }
+  __syncthreads();
+  double* part = p.partials + ((size_t)inst * p.max_tiles + t) * p.n_entries;
+  for (int e = u; e < p.n_entries; e += W) {
+    const int ntri = r * (r + 1) / 2;
+    double acc = 0.0;
+    if (e < ntri) {
+      int a = 0, rem = e;
+      while (rem >= r - a) { rem -= r - a; ++a; }
+      const int b = a + rem;
+      for (int s = 0; s < ns; ++s)
+        acc += (double)outv[s * C + oq + a] * (double)outv[s * C + oq + b];
+    } else {
+      const int a = e - ntri;
+      for (int s = 0; s < ns; ++s) acc += (double)outv[s * C + oq + a] * rho[s];
+    }
+    part[e] = acc;
+  }
+  __threadfence();
+  __syncthreads();
+  if (u == 0) {
+    const int ticket = atomicAdd(&p.counters[inst], 1);
+    s_flag = (ticket == ntiles - 1);
+  }
+  __syncthreads();
+  if (!s_flag) return;
+  __threadfence();
+
+  // ---- last CTA of the instance: reduce partials in tile order, solve, update q
+  const double* base = p.partials + (size_t)inst * p.max_tiles * p.n_entries;
+  for (int e = u; e < p.n_entries; e += W) {
+    double acc = 0.0;
+    for (int tt = 0; tt < ntiles; ++tt) acc += __ldcg(&base[(size_t)tt * p.n_entries + e]);
+    const int ntri = r * (r + 1) / 2;
+    if (e < ntri) {
+      int a = 0, rem = e;
+      while (rem >= r - a) { rem -= r - a; ++a; }
+      const int b = a + rem;
+      Amat[a * (r + 1) + b] = acc;
+      Amat[b * (r + 1) + a] = acc;
+    } else {
+      Amat[(e - ntri) * (r + 1) + r] = -acc;  // right-hand side -J^T rho
+    }
+  }
+  __syncthreads();
+  if (u == 0) {
+    int st = CROM_OK;
+    double dmax = 0.0;
+    for (int a = 0; a < r && st == CROM_OK; ++a)
+      for (int b = 0; b <= r; ++b)
+        if (!isfinite(Amat[a * (r + 1) + b])) st = CROM_ERR_NONFINITE;
+    for (int a = 0; a < r; ++a) dmax = fmax(dmax, Amat[a * (r + 1) + a]);
+    // Cholesky A = L L^T in place (lower triangle), then forward/back substitution.
+    const double tol = 1e-14 * dmax;
+    for (int j = 0; j < r && st == CROM_OK; ++j) {
+      double d = Amat[j * (r + 1) + j];
+      for (int k = 0; k < j; ++k) d -= Amat[j * (r + 1) + k] * Amat[j * (r + 1) + k];
+      if (!(d > tol)) { st = CROM_ERR_SINGULAR; break; }
+      const double ljj = sqrt(d);
+      Amat[j * (r + 1) + j] = ljj;
+      for (int i = j + 1; i < r; ++i) {
+        double v = Amat[i * (r + 1) + j];
+        for (int k = 0; k < j; ++k) v -= Amat[i * (r + 1) + k] * Amat[j * (r + 1) + k];
+        Amat[i * (r + 1) + j] = v / ljj;
+      }
+    }
+    if (st == CROM_OK) {
+      double y[kMaxR], xsol[kMaxR];
+      for (int i = 0; i < r; ++i) {
+        double v = Amat[i * (r + 1) + r];
+        for (int k = 0; k < i; ++k) v -= Amat[i * (r + 1) + k] * y[k];
+        y[i] = v / Amat[i * (r + 1) + i];
+      }
+      for (int i = r - 1; i >= 0; --i) {
+        double v = y[i];
+        for (int k = i + 1; k < r; ++k) v -= Amat[k * (r + 1) + i] * xsol[k];
+        xsol[i] = v / Amat[i * (r + 1) + i];
+      }
+      for (int i = 0; i < r; ++i) {
+        if (p.iter == 0) p.qbase[(size_t)inst * r + i] = p.qio[(size_t)inst * r + i];
+        p.qio[(size_t)inst * r + i] += xsol[i];
+      }
+    }
+    p.status[inst] = st;
+    p.counters[inst] = 0;
+  }
+}
+
+size_t fwd_smem_bytes(int W, int S, int C, int m, int r, int* LD_out) {
+  const int NP = S * C;
+  const int NPP = (NP + 15) & ~15;
+  int LD = NPP + 4;
+  *LD_out = LD;
+  size_t b = (size_t)2 * W * LD * sizeof(float);
+  b += (size_t)S * r * sizeof(double) + (size_t)S * sizeof(double) + (size_t)r * (r + 1) * sizeof(double) +
+       (size_t)r * sizeof(double);
+  b += (size_t)S * m * sizeof(float) + (size_t)NPP * sizeof(float);
+  return b + 64;
+}
+
+cudaError_t launch_fwd(FwdParams& p, dim3 grid, cudaStream_t s) {
+  size_t smem = fwd_smem_bytes(p.width, p.S, p.C, p.m, p.r, &p.LD);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fwd_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  fwd_fp32_kernel<<<grid, p.width, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+void fill_decoder(FwdParams& p, const crom_ctx* ctx) {
+  p.m = ctx->desc.m;
+  p.r = ctx->desc.r;
+  p.width = ctx->desc.width;
+  p.hidden = ctx->desc.hidden;
+  p.w1 = ctx->w.w1;
+  p.b1 = ctx->w.b1;
+  p.wt = ctx->w.wt;
+  p.bh = ctx->w.bh;
+  p.wout = ctx->w.wout;
+  p.bout = ctx->w.bout;
+}
+
+// Largest tile that keeps the two activation buffers within 200 KB.
+int pick_samples(int W, int C, int m, int r, int want) {
+  int S = want;
+  int LD;
+  while (S > 1 && fwd_smem_bytes(W, S, C, m, r, &LD) > 200 * 1024) S >>= 1;
+  return S;
+}
+
+}  // namespace
+
+cudaError_t launch_decode_fp32(const crom_ctx* ctx, int n_inst, const double* q, const int* pt_off,
+                               const float* x, int n_pts, unsigned want, float* out, cudaStream_t s) {
+  FwdParams p{};
+  p.mode = kModeDecode;
+  fill_decoder(p, ctx);
+  const int m = p.m;
+  p.nx = (want & (CROM_WANT_DX | CROM_WANT_DXX | CROM_WANT_LAP)) ? m : 0;
+  p.second = (want & CROM_WANT_DXX) ? kSecondPerK : ((want & CROM_WANT_LAP) ? kSecondLap : kSecondNone);
+  p.nq = (want & CROM_WANT_DQ) ? p.r : 0;
+  p.C = ChannelSet{p.nx, p.second, p.nq}.count(m);
+  p.S = pick_samples(p.width, p.C, m, p.r, 8);
+  p.q = q;
+  p.off = pt_off;
+  p.x = x;
+  p.n_pts = n_pts;
+  p.n_inst = n_inst;
+  p.out = out;
+  p.want = want;
+  dim3 grid((n_pts + p.S - 1) / p.S, 1);
+  return launch_fwd(p, grid, s);
+}
+
+cudaError_t launch_recon_fp32(const crom_ctx* ctx, int n_codes, const double* q, int n_pts,
+                              const float* x, float* out, cudaStream_t s) {
+  FwdParams p{};
+  p.mode = kModeRecon;
+  fill_decoder(p, ctx);
+  p.nx = 0;
+  p.second = kSecondNone;
+  p.nq = 0;
+  p.C = 1;
+  p.S = 32;
+  p.q = q;
+  p.x = x;
+  p.n_pts = n_pts;
+  p.n_inst = n_codes;
+  p.out = out;
+  dim3 grid((n_pts + p.S - 1) / p.S, n_codes);
+  return launch_fwd(p, grid, s);
+}
+
+cudaError_t launch_step_fp32(crom_ctx* ctx, const crom_step_desc* step, int n_inst, double* q,
+                             const float* alpha, const float* vel, const int* s_off,
+                             const float* samples, int n_samples, int max_samples, int* status,
+                             cudaStream_t s) {
+  FwdParams p{};
+  p.mode = kModeStep;
+  fill_decoder(p, ctx);
+  const int m = p.m, r = p.r;
+  const int C0 = ChannelSet{m, kSecondLap, r}.count(m);
+  // Samples per CTA: enough CTAs to cover the GPU at least twice when possible.
+  int S = 4;
+  while (S > 1 && (long long)n_inst * ((max_samples + S - 1) / S) < 2LL * ctx->num_sms) S >>= 1;
+  S = pick_samples(p.width, C0, m, r, S);
+  const int max_tiles = (max_samples + S - 1) / S;
+  const int n_entries = r * (r + 1) / 2 + r;
+
+  // Scratch: partial normal equations, per-instance tickets, per-sample targets.
+  const size_t need_part = (size_t)n_inst * max_tiles * n_entries;
+  if (need_part > ctx->partials_cap) {
+    if (ctx->partials) cudaFree(ctx->partials);
+    ctx->partials = nullptr;
+    ctx->partials_cap = 0;
+    cudaError_t e = cudaMalloc(&ctx->partials, need_part * sizeof(double));
+    if (e != cudaSuccess) return e;
+    ctx->partials_cap = need_part;
+  }
+  if ((size_t)n_inst > ctx->counters_cap) {
+    if (ctx->counters) cudaFree(ctx->counters);
+    ctx->counters = nullptr;
+    ctx->counters_cap = 0;
+    cudaError_t e = cudaMalloc(&ctx->counters, (size_t)n_inst * sizeof(int));
+    if (e != cudaSuccess) return e;
+    e = cudaMemset(ctx->counters, 0, (size_t)n_inst * sizeof(int));
+    if (e != cudaSuccess) return e;
+    ctx->counters_cap = n_inst;
+  }
+  if ((size_t)n_samples > ctx->targets_cap) {
+    if (ctx->targets) cudaFree(ctx->targets);
+    ctx->targets = nullptr;
+    ctx->targets_cap = 0;
+    cudaError_t e = cudaMalloc(&ctx->targets, (size_t)n_samples * sizeof(double));
+    if (e != cudaSuccess) return e;
+    ctx->targets_cap = n_samples;
+  }
+  if ((size_t)n_inst * r > ctx->qbase_cap) {
+    if (ctx->qbase) cudaFree(ctx->qbase);
+    ctx->qbase = nullptr;
+    ctx->qbase_cap = 0;
+    cudaError_t e = cudaMalloc(&ctx->qbase, (size_t)n_inst * r * sizeof(double));
+    if (e != cudaSuccess) return e;
+    ctx->qbase_cap = (size_t)n_inst * r;
+  }
+
+  p.S = S;
+  p.off = s_off;
+  p.x = samples;
+  p.n_inst = n_inst;
+  p.pde = step->pde;
+  p.dt = step->dt;
+  p.alpha = alpha;
+  p.vel = vel;
+  p.max_samples = max_samples;
+  p.qio = q;
+  p.status = status;
+  p.partials = ctx->partials;
+  p.max_tiles = max_tiles;
+  p.n_entries = n_entries;
+  p.counters = ctx->counters;
+  p.targets = ctx->targets;
+  p.qbase = ctx->qbase;
+  if (max_tiles > 65535) return cudaErrorInvalidValue;
+  dim3 grid(n_inst, max_tiles);
+  for (int it = 0; it < step->gn_iters; ++it) {
+    // Iteration 0: value, dg/dx_k, Laplacian, dg/dq at q_n.  Later iterations:
+    // value and dg/dq at q^(k) plus the difference channel h(q^(k)) - h(q_n).
+    p.iter = it;
+    p.diff = (it == 0) ? 0 : 1;
+    p.nx = (it == 0) ? m : 0;
+    p.second = (it == 0) ? kSecondLap : kSecondNone;
+    p.nq = r;
+    p.C = 1 + p.diff + ChannelSet{p.nx, p.second, p.nq}.count(m) - 1;
+    cudaError_t e = launch_fwd(p, grid, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace crom

@@ -1,0 +1,251 @@
+// Dense reconstruction g(x_p, q_c) on the tcgen05 tensor cores (value channel only).
+//
+// Persistent kernel, one CTA per SM, 128 threads; thread u owns hidden unit u,
+// which is also TMEM lane u.  A tile is 128 points of one latent code:
+//   layer 1 (K = m + r, too small for UMMA) on CUDA cores: the q part of W_1 q + b_1
+//     is hoisted per code; z = W_1x x + c; h = ELU(z);
+//   layers 2..L: D[u][n] = sum_k W_l[u][k] H[k][n] by UMMA (M = 128 units,
+//     N = 128 points, K = 128), A = W_l (K-major, resident in shared memory for
+//     the whole kernel), B = H (MN-major, written by the epilogue of the layer
+//     before); epilogue: bias, ELU, bf16 split, store;
+//   output: D[n][0] = sum_u H_L[u][n] w_out[u] by one more UMMA (M = 128 points,
+//     N = 16 rows of the projection matrix), read back by lane n.
+// Precision: each activation operand h is stored as hi = bf16(h) and
+// lo = bf16(h - hi) and both are multiplied into the same FP32 accumulator
+// (split = 1); split = 0 keeps the high part only.
+#include <math.h>
+
+#include "crom_internal.h"
+#include "tc_common.cuh"
+
+namespace crom {
+namespace {
+
+using namespace tc;
+
+constexpr int kThreads = 128;
+constexpr int kTileN = 128;
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kAccCol = 0;
+constexpr uint32_t kOutCol = 128;
+constexpr uint32_t kWaitLimit = 1u << 25;
+
+struct ReconParams {
+  const uint8_t* img;  // bf16 tensor-core image (hidden matrices + projection)
+  int img_bytes;
+  int n_hidden_mats;   // hidden - 1
+  int m, r;
+  const float* w1;  // [128][m+r]
+  const float* b1;
+  const float* bh;  // [(hidden-1)][128]
+  float bout;
+  const double* q;  // [n_codes][r]
+  const float* x;   // [n_pts][m]
+  float* out;       // [n_codes][n_pts]
+  int n_pts, n_codes;
+  int tiles_per_code;
+  int* flag;        // set to 1 on a device-side wait timeout
+};
+
+struct __align__(8) ReconSmemTail {
+  uint64_t bar_w;
+  uint64_t bar_mma;
+  uint32_t tmem_base;
+  int pad;
+  float c1[kTcWidth];     // b_1 + W_1q q for the current code
+  float bh[4 * kTcWidth];
+  float w1x[2 * kTcWidth];
+  float xs[2 * kTileN];
+};
+
+constexpr size_t kH = (size_t)kTcWidth * kTileN * 2;  // one bf16 operand buffer, 32 KB
+
+template <int kSplit>
+__device__ __forceinline__ void store_split16(uint8_t* Hhi, uint8_t* Hlo, int k, int n0, const float (&v)[16]) {
+  uint32_t hi[8], lo[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    hi[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
+    if (kSplit) lo[j] = pack_bf16(v[2 * j] - bf16_lo_f(hi[j]), v[2 * j + 1] - bf16_hi_f(hi[j]));
+  }
+  *reinterpret_cast<uint4*>(Hhi + mn_offset(k, n0)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+  *reinterpret_cast<uint4*>(Hhi + mn_offset(k, n0 + 8)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+  if (kSplit) {
+    *reinterpret_cast<uint4*>(Hlo + mn_offset(k, n0)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    *reinterpret_cast<uint4*>(Hlo + mn_offset(k, n0 + 8)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+  }
+}
+
+__device__ __forceinline__ float elu(float z) { return z > 0.f ? z : __expf(z) - 1.f; }
+
+template <int kSplit>
+__global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* Wimg = sm;                               // hidden matrices + projection
+  uint8_t* Hhi = sm + ((p.img_bytes + 1023) & ~1023);
+  uint8_t* Hlo = Hhi + kH;
+  ReconSmemTail* T = reinterpret_cast<ReconSmemTail*>(Hlo + kH);
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int u = tid;
+  const int m = p.m, r = p.r;
+  const uint32_t lane_base = (uint32_t)warp * 32;
+
+  if (tid == 0) {
+    mbar_init(&T->bar_w, 1);
+    mbar_init(&T->bar_mma, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&T->tmem_base, kTmemCols);
+    tmem_relinquish();
+  }
+  for (int i = tid; i < p.n_hidden_mats * kTcWidth; i += kThreads) T->bh[i] = p.bh[i];
+  for (int i = tid; i < m * kTcWidth; i += kThreads) T->w1x[i] = p.w1[(i % kTcWidth) * (m + r) + i / kTcWidth];
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tb = T->tmem_base;
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&T->bar_w, (uint32_t)p.img_bytes);
+    for (int off = 0; off < p.img_bytes; off += 16384) {
+      const int bytes = min(16384, p.img_bytes - off);
+      bulk_g2s(Wimg + off, p.img + off, (uint32_t)bytes, &T->bar_w);
+    }
+  }
+  // Every wait is bounded; the outcome is made uniform across the CTA before
+  // anyone acts on it, so no thread can leave while others still wait at a barrier.
+  bool ok = __syncthreads_and(mbar_wait(&T->bar_w, 0, kWaitLimit));
+  uint32_t phase = 0;
+  const uint32_t wbase = smem_u32(Wimg);
+  const uint32_t proj = wbase + (uint32_t)p.n_hidden_mats * kTcLayerBytes;
+  const uint32_t hhi = smem_u32(Hhi), hlo = smem_u32(Hlo);
+  constexpr uint32_t id_layer = idesc_f16(128, kTileN, false, true, true);
+  constexpr uint32_t id_out = idesc_f16(128, 16, true, false, true);
+  int cur_code = -1;
+  const int n_tiles = p.n_codes * p.tiles_per_code;
+
+  for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    const int code = tile / p.tiles_per_code;
+    const int p0 = (tile % p.tiles_per_code) * kTileN;
+    if (code != cur_code) {
+      double c = (double)p.b1[u];
+      for (int j = 0; j < r; ++j) c += (double)p.w1[u * (m + r) + m + j] * p.q[(size_t)code * r + j];
+      T->c1[u] = (float)c;
+      cur_code = code;
+    }
+    {
+      const int n = p0 + tid;
+      for (int k = 0; k < m; ++k) T->xs[k * kTileN + tid] = (n < p.n_pts) ? p.x[(size_t)n * m + k] : 0.f;
+    }
+    __syncthreads();
+    // ---- layer 1 on CUDA cores
+    {
+      const float c = T->c1[u];
+      const float wx0 = T->w1x[u], wx1 = (m > 1) ? T->w1x[kTcWidth + u] : 0.f;
+#pragma unroll 1
+      for (int n0 = 0; n0 < kTileN; n0 += 16) {
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          float z = fmaf(wx0, T->xs[n0 + i], c);
+          if (m > 1) z = fmaf(wx1, T->xs[kTileN + n0 + i], z);
+          v[i] = elu(z);
+        }
+        store_split16<kSplit>(Hhi, Hlo, u, n0, v);
+      }
+    }
+    // ---- hidden layers on the tensor cores
+    for (int l = 0; l <= p.n_hidden_mats; ++l) {
+      const bool last = (l == p.n_hidden_mats);
+      fence_proxy_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        if (!last) {
+          const uint32_t a = wbase + (uint32_t)l * kTcLayerBytes;
+          for (int kk = 0; kk < 8; ++kk)
+            umma_f16(tb + kAccCol, desc_kmajor(a, 128, kk), desc_mnmajor(hhi, kk), id_layer, kk > 0);
+          if (kSplit)
+            for (int kk = 0; kk < 8; ++kk)
+              umma_f16(tb + kAccCol, desc_kmajor(a, 128, kk), desc_mnmajor(hlo, kk), id_layer, 1);
+        } else {
+          for (int kk = 0; kk < 8; ++kk)
+            umma_f16(tb + kOutCol, desc_mnmajor(hhi, kk), desc_kmajor(proj, 16, kk), id_out, kk > 0);
+          if (kSplit)
+            for (int kk = 0; kk < 8; ++kk)
+              umma_f16(tb + kOutCol, desc_mnmajor(hlo, kk), desc_kmajor(proj, 16, kk), id_out, 1);
+        }
+        umma_commit(&T->bar_mma);
+      }
+      ok = __syncthreads_and(mbar_wait(&T->bar_mma, phase, kWaitLimit));
+      phase ^= 1;
+      tc_fence_after();
+      if (!ok) break;
+      if (!last) {
+        const float bias = T->bh[l * kTcWidth + u];
+#pragma unroll 1
+        for (int n0 = 0; n0 < kTileN; n0 += 16) {
+          float v[16];
+          tmem_ld16(taddr(tb, lane_base, kAccCol + n0), v);
+          tmem_ld_wait();
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] = elu(v[i] + bias);
+          store_split16<kSplit>(Hhi, Hlo, u, n0, v);
+        }
+      } else {
+        float v[16];
+        tmem_ld16(taddr(tb, lane_base, kOutCol), v);
+        tmem_ld_wait();
+        const int n = p0 + tid;
+        if (n < p.n_pts) p.out[(size_t)code * p.n_pts + n] = v[0] + p.bout;
+      }
+    }
+  }
+  if (!ok && tid == 0) atomicExch(p.flag, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tb, kTmemCols);
+}
+
+}  // namespace
+
+cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const double* q, int n_pts,
+                            const float* x, float* out, cudaStream_t s) {
+  ReconParams p{};
+  p.img = ctx->w.tc_img;
+  p.img_bytes = (int)ctx->w.tc_img_bytes;
+  p.n_hidden_mats = ctx->desc.hidden - 1;
+  p.m = ctx->desc.m;
+  p.r = ctx->desc.r;
+  p.w1 = ctx->w.w1;
+  p.b1 = ctx->w.b1;
+  p.bh = ctx->w.bh;
+  p.bout = ctx->w.bout;
+  p.q = q;
+  p.x = x;
+  p.out = out;
+  p.n_pts = n_pts;
+  p.n_codes = n_codes;
+  p.tiles_per_code = (n_pts + kTileN - 1) / kTileN;
+  p.flag = ctx->queue + 1;
+  const size_t smem = 1024 + (((size_t)p.img_bytes + 1023) & ~(size_t)1023) + 2 * kH + sizeof(ReconSmemTail);
+  const long long tiles = (long long)n_codes * p.tiles_per_code;
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const int grid = (int)std::min<long long>(tiles, ctx->num_sms);
+  cudaError_t e;
+  if (split) {
+    e = cudaFuncSetAttribute(recon_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    recon_tc_kernel<1><<<grid, kThreads, smem, s>>>(p);
+  } else {
+    e = cudaFuncSetAttribute(recon_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    recon_tc_kernel<0><<<grid, kThreads, smem, s>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace crom

@@ -1,0 +1,265 @@
+"""GPU parity of the FP32 CUDA-core path (crom_decode, crom_step, crom_reconstruct)
+against the FP64 oracle, through the C ABI.
+
+Tolerances (FP32 arithmetic vs FP64): value, first derivatives and dg/dq are
+128-term FP32 dot products through <= 5 layers, rel. L2 <= 1e-5; second
+derivatives cancel by two orders of magnitude in the output layer (checked
+with the oracle's channel magnitudes), rel. L2 <= 1e-4.  Per step, q_{n+1} is
+held to <= 1e-5 relative L2; the increment q_{n+1} - q_n is held to <= 1e-3,
+which is the FP32 channel error times cond(J) ~ 1e3 of these decoders.
+"""
+import numpy as np
+import pytest
+
+from oracle import crom_oracle as O
+from workloads import gen
+
+from helpers import dev, make_ctx, rel_l2, run_steps, StepInputs, subset
+
+pytestmark = pytest.mark.gpu
+
+
+def crom():
+    from paper_2206_02607_gb300 import crom as c
+    return c
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    from paper_2206_02607_gb300 import build
+    build()
+
+
+@pytest.mark.parametrize("m,r,width,hidden", [(1, 3, 64, 4), (2, 8, 128, 5), (2, 4, 96, 3), (3, 16, 256, 2)])
+def test_decode_all_channels(m, r, width, hidden):
+    import torch
+    c = crom()
+    spec = gen.DecoderSpec(m, r, width, hidden)
+    params = gen.xavier_decoder(spec, seed=21, bias_std=0.2)
+    ctx = make_ctx(spec, params)
+    rng = np.random.default_rng(5)
+    sizes = [37, 0, 101, 9]                       # ragged, one empty instance
+    off = gen.ragged_offsets(sizes)
+    X = rng.uniform(0, 1, size=(off[-1], m)).astype(np.float32)
+    Q = rng.standard_normal((len(sizes), r))
+    want = c.CROM_WANT_VAL | c.CROM_WANT_DX | c.CROM_WANT_DXX | c.CROM_WANT_LAP | c.CROM_WANT_DQ
+    C = 1 + m + m + 1 + r
+    out = torch.empty((C, off[-1]), dtype=torch.float32, device="cuda")
+    c.crom_decode(ctx, dev(Q, torch.float64), dev(off, torch.int32), dev(X, torch.float32), want, out)
+    got = out.cpu().numpy()
+    dec = O.MLPDecoder(params, m)
+    ref = {k: [] for k in ("g", "gx", "gxx", "lap", "gq")}
+    for i in range(len(sizes)):
+        if sizes[i] == 0:
+            continue
+        ev = dec(X[off[i]:off[i + 1]], Q[i])
+        ref["g"].append(ev.g); ref["gx"].append(ev.gx); ref["gxx"].append(ev.gxx)
+        ref["lap"].append(ev.lap); ref["gq"].append(ev.gq)
+    g = np.concatenate(ref["g"]); gx = np.concatenate(ref["gx"]); gxx = np.concatenate(ref["gxx"])
+    lap = np.concatenate(ref["lap"]); gq = np.concatenate(ref["gq"])
+    assert rel_l2(got[0], g) < 1e-5
+    assert rel_l2(got[1:1 + m].T, gx) < 1e-5
+    assert rel_l2(got[1 + m:1 + 2 * m].T, gxx) < 1e-4
+    assert rel_l2(got[1 + 2 * m], lap) < 1e-4
+    assert rel_l2(got[2 + 2 * m:].T, gq) < 1e-5
+
+
+def test_decode_channel_subsets_are_consistent():
+    """Any subset of channels equals the corresponding rows of the full request."""
+    import torch
+    c = crom()
+    spec = gen.DecoderSpec(2, 8, 128, 5)
+    params = gen.xavier_decoder(spec, seed=3, bias_std=0.1)
+    ctx = make_ctx(spec, params)
+    X = np.random.default_rng(1).uniform(0, 1, size=(300, 2)).astype(np.float32)
+    Q = np.random.default_rng(2).standard_normal((1, 8))
+    off = gen.ragged_offsets([300])
+    args = (dev(Q, torch.float64), dev(off, torch.int32), dev(X, torch.float32))
+    full = torch.empty((1 + 2 + 2 + 1 + 8, 300), dtype=torch.float32, device="cuda")
+    c.crom_decode(ctx, *args, 31, full)
+    lap_only = torch.empty((1, 300), dtype=torch.float32, device="cuda")
+    c.crom_decode(ctx, *args, c.CROM_WANT_LAP, lap_only)
+    val_dq = torch.empty((9, 300), dtype=torch.float32, device="cuda")
+    c.crom_decode(ctx, *args, c.CROM_WANT_VAL | c.CROM_WANT_DQ, val_dq)
+    f = full.cpu().numpy()
+    assert rel_l2(lap_only.cpu().numpy()[0], f[5]) < 1e-5
+    assert np.array_equal(val_dq.cpu().numpy()[0], f[0])
+    assert np.allclose(val_dq.cpu().numpy()[1:], f[6:], rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("bias", [0.0, 0.2])
+def test_step_heat1d_small_config(bias):
+    """1D heat config (P=256, r=3, w=64, |M|=16, 1 GN iteration): one step and a
+    100-step rollout against the oracle."""
+    c = crom()
+    w = gen.heat1d_small(bias_std=bias)
+    ctx = make_ctx(w.spec, w.params)
+    dec = O.MLPDecoder(w.params, 1)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_FP32)
+    ref1, rst = O.crom_step(dec, w.q0[0], w.samples, w.dt, w.gn_iters)
+    assert st[0] == 0 and rst == 0
+    assert rel_l2(q1[0], ref1) < 1e-5
+    assert rel_l2(q1[0] - w.q0[0], ref1 - w.q0[0]) < 1e-3
+    qT, st = run_steps(ctx, w, w.steps, c.CROM_PREC_FP32)
+    traj = O.crom_rollout(dec, w.q0[0], w.samples, w.dt, w.gn_iters, w.steps)
+    assert st[0] == 0
+    assert rel_l2(qT[0], traj[-1]) < 1e-5
+    assert rel_l2(qT[0] - w.q0[0], traj[-1] - w.q0[0]) < 1e-3
+
+
+def test_step_heat2d_single_config():
+    """2D heat config (128^2 grid, r=8, w=128, |M|=200, 2 GN iterations)."""
+    c = crom()
+    w = gen.heat2d_single()
+    ctx = make_ctx(w.spec, w.params)
+    dec = O.MLPDecoder(w.params, 2)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_FP32)
+    ref1, rst = O.crom_step(dec, w.q0[0], w.samples, w.dt, w.gn_iters)
+    assert st[0] == 0 and rst == 0
+    assert rel_l2(q1[0], ref1) < 1e-5
+    assert rel_l2(q1[0] - w.q0[0], ref1 - w.q0[0]) < 1e-3
+    q20, _ = run_steps(ctx, w, 20, c.CROM_PREC_FP32)
+    traj = O.crom_rollout(dec, w.q0[0], w.samples, w.dt, w.gn_iters, 20)
+    assert rel_l2(q20[0] - w.q0[0], traj[-1] - w.q0[0]) < 1e-3
+
+
+def test_step_batched_ragged_matches_oracle():
+    """Many instances with uneven |M_i| spanning several CTA tiles and ragged tails."""
+    c = crom()
+    w = gen.heat2d_batched(n_inst=24, m_lo=8, m_hi=300, bias_std=0.1, bf16_exact=False)
+    ctx = make_ctx(w.spec, w.params)
+    dec = O.MLPDecoder(w.params, 2)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_FP32)
+    ref, rst = O.crom_step_batched(dec, w.q0, w.s_off, w.samples, w.alpha, w.dt, w.gn_iters)
+    assert np.array_equal(st, rst)
+    for i in range(w.n_inst):
+        assert rel_l2(q1[i], ref[i]) < 1e-5
+        assert rel_l2(q1[i] - w.q0[i], ref[i] - w.q0[i]) < 1e-3
+
+
+def test_step_batched_full_size_sampled_instances():
+    """The 1024-instance batched heat workload in one launch; 12 instances are
+    recomputed one by one by the oracle."""
+    c = crom()
+    w = gen.heat2d_batched(n_inst=1024, bf16_exact=True)
+    ctx = make_ctx(w.spec, w.params)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_FP32)
+    assert np.all(st == 0)
+    dec = O.MLPDecoder(w.params, 2)
+    pick = np.random.default_rng(0).choice(w.n_inst, size=12, replace=False)
+    for i in pick:
+        Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
+        ref, rst = O.crom_step(dec, w.q0[i], Y, w.dt, w.gn_iters, alpha=float(w.alpha[i]))
+        assert rst == 0
+        assert rel_l2(q1[i] - w.q0[i], ref - w.q0[i]) < 1e-3
+
+
+def test_step_instance_results_do_not_depend_on_batch_position():
+    """Shuffling the instances permutes the results bit for bit (instances are independent)."""
+    c = crom()
+    w = gen.heat2d_batched(n_inst=20, m_lo=8, m_hi=200, bf16_exact=False)
+    ctx = make_ctx(w.spec, w.params)
+    q1, _ = run_steps(ctx, w, 1, c.CROM_PREC_FP32)
+    perm = np.random.default_rng(3).permutation(w.n_inst)
+    q2, _ = run_steps(ctx, subset(w, perm), 1, c.CROM_PREC_FP32)
+    assert np.array_equal(q2, q1[perm])
+
+
+def test_step_edge_cases_status():
+    """|M_i| < r -> INVALID_ARG, duplicate samples -> SINGULAR, NaN coefficient -> NONFINITE;
+    the other instances are unaffected and q of failed instances is kept."""
+    import torch
+    c = crom()
+    spec = gen.DecoderSpec(2, 4, 64, 3)
+    params = gen.xavier_decoder(spec, seed=9, bias_std=0.1)
+    ctx = make_ctx(spec, params)
+    rng = np.random.default_rng(4)
+    good = rng.uniform(0, 1, size=(50, 2)).astype(np.float32)
+    dup = np.tile(np.array([[0.3, 0.7]], np.float32), (20, 1))
+    few = rng.uniform(0, 1, size=(3, 2)).astype(np.float32)
+    sizes = [50, 20, 3, 50, 0]
+    samples = np.concatenate([good, dup, few, good], axis=0)
+    off = gen.ragged_offsets(sizes)
+    q0 = rng.standard_normal((5, 4))
+    alpha = np.array([1.0, 1.0, 1.0, np.nan, 1.0], np.float32)
+    w = gen.StepWorkload("edge", spec, params, q0, alpha, off, samples, 1e-4, 2, 1)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_FP32)
+    assert list(st) == [c.CROM_OK, c.CROM_ERR_SINGULAR, c.CROM_ERR_INVALID_ARG, c.CROM_ERR_NONFINITE,
+                        c.CROM_ERR_INVALID_ARG]
+    assert np.array_equal(q1[1:], q0[1:])
+    dec = O.MLPDecoder(params, 2)
+    ref, _ = O.crom_step(dec, q0[0], good, 1e-4, 2)
+    assert rel_l2(q1[0] - q0[0], ref - q0[0]) < 1e-3
+
+
+def test_step_rejects_bad_arguments():
+    import torch
+    c = crom()
+    w = gen.heat1d_small()
+    ctx = make_ctx(w.spec, w.params)
+    d = StepInputs(w)
+    for kw in [dict(dt=0.0, gn_iters=1), dict(dt=float("nan"), gn_iters=1), dict(dt=1e-5, gn_iters=0),
+               dict(dt=1e-5, gn_iters=17)]:
+        with pytest.raises(c.CromError) as e:
+            c.crom_step(ctx, d.q, d.alpha, d.s_off, d.samples, d.status, max_samples=16, **kw)
+        assert e.value.code == c.CROM_ERR_INVALID_ARG
+    with pytest.raises(c.CromError):
+        c.crom_step(ctx, d.q, d.alpha, d.s_off, d.samples, d.status, dt=1e-5, gn_iters=1, max_samples=16,
+                    pde=c.CROM_PDE_ADVDIFF)      # advection needs a velocity field
+    # max_samples smaller than an instance: that instance is flagged, nothing else happens
+    c.crom_step(ctx, d.q, d.alpha, d.s_off, d.samples, d.status, dt=1e-5, gn_iters=1, max_samples=8)
+    torch.cuda.synchronize()
+    assert d.status.cpu().numpy()[0] == c.CROM_ERR_INVALID_ARG
+    assert np.array_equal(d.q.cpu().numpy(), w.q0)
+
+
+def test_step_advection_diffusion_matches_oracle():
+    import torch
+    c = crom()
+    spec = gen.DecoderSpec(2, 6, 64, 3)
+    params = gen.xavier_decoder(spec, seed=13, bias_std=0.1)
+    ctx = make_ctx(spec, params)
+    rng = np.random.default_rng(8)
+    Y = rng.uniform(0, 1, size=(90, 2)).astype(np.float32)
+    vel = rng.standard_normal((90, 2)).astype(np.float32)
+    q0 = rng.standard_normal((1, 6))
+    nu = np.array([0.02], np.float32)
+    off = gen.ragged_offsets([90])
+    q = dev(q0, torch.float64)
+    st = torch.empty(1, dtype=torch.int32, device="cuda")
+    c.crom_step(ctx, q, dev(nu, torch.float32), dev(off, torch.int32), dev(Y, torch.float32), st,
+                dt=1e-3, gn_iters=2, max_samples=90, pde=c.CROM_PDE_ADVDIFF, vel=dev(vel, torch.float32))
+    dec = O.MLPDecoder(params, 2)
+    ref, rst = O.crom_step(dec, q0[0], Y, 1e-3, 2, alpha=float(nu[0]), pde="advdiff", vel=vel, nu=float(nu[0]))
+    assert st.item() == 0 and rst == 0
+    assert rel_l2(q.cpu().numpy()[0] - q0[0], ref - q0[0]) < 1e-3
+
+
+@pytest.mark.parametrize("n_pts", [1, 33, 4097])
+def test_reconstruct_fp32(n_pts):
+    import torch
+    c = crom()
+    spec = gen.DecoderSpec(2, 8, 128, 5)
+    params = gen.xavier_decoder(spec, seed=0, bias_std=0.1)
+    ctx = make_ctx(spec, params)
+    X = np.random.default_rng(n_pts).uniform(0, 1, size=(n_pts, 2)).astype(np.float32)
+    codes = np.random.default_rng(4).standard_normal((3, 8))
+    out = torch.empty((3, n_pts), dtype=torch.float32, device="cuda")
+    c.crom_reconstruct(ctx, dev(codes, torch.float64), dev(X, torch.float32), out)
+    ref = O.reconstruct(O.MLPDecoder(params, 2), codes, X)
+    assert rel_l2(out.cpu().numpy(), ref) < 1e-5
+
+
+def test_empty_calls_are_no_ops():
+    import torch
+    c = crom()
+    w = gen.heat1d_small()
+    ctx = make_ctx(w.spec, w.params)
+    e = torch.empty((0,), dtype=torch.float64, device="cuda")
+    c.crom_reconstruct(ctx, torch.zeros((1, 3), dtype=torch.float64, device="cuda"),
+                       torch.empty((0, 1), dtype=torch.float32, device="cuda"),
+                       torch.empty((1, 0), dtype=torch.float32, device="cuda"))
+    c.crom_step(ctx, e.reshape(0, 3), torch.empty(0, dtype=torch.float32, device="cuda"),
+                torch.zeros(1, dtype=torch.int32, device="cuda"), torch.empty((0, 1), dtype=torch.float32, device="cuda"),
+                torch.empty(0, dtype=torch.int32, device="cuda"), dt=1e-5, gn_iters=1, max_samples=1)
+    torch.cuda.synchronize()

@@ -1,0 +1,204 @@
+"""GPU parity of the tcgen05 tensor-core paths (BF16X2 step, BF16X2 / BF16 dense
+reconstruction) against the FP64 oracle, through the C ABI.
+
+The decoders here have bf16-representable weights, so both sides evaluate the
+same model; the remaining difference is the bf16 hi/lo rounding of activation
+operands (about 2^-17 relative per element) plus FP32 accumulation.
+Tolerances: dense values rel. L2 <= 1e-4 (BF16X2) and <= 1e-2 (BF16, high part
+only).  Latent step: q_{n+1} rel. L2 <= 1e-5 and increment q_{n+1} - q_n rel. L2
+<= 5e-3 (the Laplacian channel loses two digits to cancellation and cond(J) ~ 1e3
+amplifies operand rounding); rollouts: q_T rel. L2 <= 1e-3.
+"""
+import numpy as np
+import pytest
+
+from oracle import crom_oracle as O
+from workloads import gen
+
+from helpers import dev, make_ctx, rel_l2, run_steps, subset
+
+pytestmark = pytest.mark.gpu
+
+
+def crom():
+    from paper_2206_02607_gb300 import crom as c
+    return c
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    from paper_2206_02607_gb300 import build
+    build()
+
+
+@pytest.mark.parametrize("hidden,m,n_pts,n_codes", [(5, 2, 1000, 3), (3, 2, 129, 2), (5, 1, 4096, 2), (2, 2, 1, 1)])
+def test_reconstruct_tc_matches_oracle(hidden, m, n_pts, n_codes):
+    import torch
+    c = crom()
+    spec = gen.DecoderSpec(m, 8, 128, hidden)
+    params = gen.xavier_decoder(spec, seed=hidden, bias_std=0.1, bf16_exact=True)
+    ctx = make_ctx(spec, params)
+    X = np.random.default_rng(n_pts).uniform(0, 1, size=(n_pts, m)).astype(np.float32)
+    codes = np.random.default_rng(7).standard_normal((n_codes, 8))
+    ref = O.reconstruct(O.MLPDecoder(params, m), codes, X)
+    for prec, tol in ((c.CROM_PREC_BF16X2, 1e-4), (c.CROM_PREC_BF16, 1e-2)):
+        out = torch.full((n_codes, n_pts), float("nan"), dtype=torch.float32, device="cuda")
+        c.crom_reconstruct(ctx, dev(codes, torch.float64), dev(X, torch.float32), out, precision=prec)
+        got = out.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert rel_l2(got, ref) < tol, (prec, rel_l2(got, ref))
+
+
+def test_reconstruct_tc_full_grid_sampled():
+    """The dense workload (1024^2 grid x 64 codes) in one launch; 4096 sampled outputs
+    are recomputed one by one by the oracle."""
+    import torch
+    c = crom()
+    spec, params, codes, X = gen.recon_dense()
+    ctx = make_ctx(spec, params)
+    out = torch.empty((codes.shape[0], X.shape[0]), dtype=torch.float32, device="cuda")
+    c.crom_reconstruct(ctx, dev(codes, torch.float64), dev(X, torch.float32), out, precision=c.CROM_PREC_BF16X2)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    ci = rng.integers(0, codes.shape[0], size=4096)
+    pi = rng.integers(0, X.shape[0], size=4096)
+    pi[:3] = [0, X.shape[0] - 1, 1023]
+    got = out[torch.as_tensor(ci, device="cuda"), torch.as_tensor(pi, device="cuda")].cpu().numpy()
+    dec = O.MLPDecoder(params, 2)
+    ref = np.array([dec.value(X[p:p + 1], codes[k])[0] for k, p in zip(ci, pi)])
+    assert rel_l2(got, ref) < 1e-4
+
+
+def test_reconstruct_tc_rejects_unsupported_shape():
+    import torch
+    c = crom()
+    spec = gen.DecoderSpec(2, 8, 64, 3)
+    ctx = make_ctx(spec, gen.xavier_decoder(spec, seed=0))
+    out = torch.empty((1, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(c.CromError) as e:
+        c.crom_reconstruct(ctx, torch.zeros((1, 8), dtype=torch.float64, device="cuda"),
+                           torch.zeros((4, 2), dtype=torch.float32, device="cuda"), out, precision=c.CROM_PREC_BF16X2)
+    assert e.value.code == c.CROM_ERR_UNSUPPORTED
+
+
+def _check_step(w, q1, st, inc_tol=5e-3):
+    dec = O.MLPDecoder(w.params, w.spec.m)
+    ref, rst = O.crom_step_batched(dec, w.q0, w.s_off, w.samples, w.alpha, w.dt, w.gn_iters)
+    assert np.array_equal(st, rst), (st, rst)
+    for i in range(w.n_inst):
+        if rst[i] != 0:
+            continue
+        assert rel_l2(q1[i], ref[i]) < 1e-5
+        assert rel_l2(q1[i] - w.q0[i], ref[i] - w.q0[i]) < inc_tol, (i, rel_l2(q1[i] - w.q0[i], ref[i] - w.q0[i]))
+
+
+def test_step_tc_single_instance_heat2d():
+    c = crom()
+    w = gen.heat2d_single(bf16_exact=True)
+    ctx = make_ctx(w.spec, w.params)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_BF16X2)
+    _check_step(w, q1, st)
+
+
+@pytest.mark.parametrize("gn_iters", [1, 2, 3])
+def test_step_tc_batched_ragged(gn_iters):
+    """Uneven |M_i| including sizes below, at and above one 32-sample tile."""
+    c = crom()
+    w = gen.heat2d_batched(n_inst=20, m_lo=8, m_hi=300, bias_std=0.1)
+    w.gn_iters = gn_iters
+    w.samples[:0]
+    ctx = make_ctx(w.spec, w.params)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_BF16X2)
+    _check_step(w, q1, st)
+
+
+def test_step_tc_one_dimensional_decoder():
+    c = crom()
+    spec = gen.DecoderSpec(1, 4, 128, 4)
+    params = gen.xavier_decoder(spec, seed=2, bias_std=0.1, bf16_exact=True)
+    rng = np.random.default_rng(1)
+    sizes = [16, 40, 100]
+    samples = np.concatenate([gen.interior_nodes_1d(256, s, rng) for s in sizes])
+    w = gen.StepWorkload("1d", spec, params, rng.standard_normal((3, 4)), np.array([1.0, 0.5, 2.0], np.float32),
+                         gen.ragged_offsets(sizes), samples, 1e-5, 2, 1)
+    ctx = make_ctx(spec, params)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_BF16X2)
+    _check_step(w, q1, st)
+
+
+def test_step_tc_full_size_sampled_and_matches_fp32():
+    """All 1024 instances in one persistent launch (the launch the bench times); 10
+    sampled instances recomputed by the oracle; the FP32 path agrees with it too."""
+    c = crom()
+    w = gen.heat2d_batched(n_inst=1024)
+    ctx = make_ctx(w.spec, w.params)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_BF16X2)
+    assert np.all(st == 0)
+    dec = O.MLPDecoder(w.params, 2)
+    for i in np.random.default_rng(1).choice(w.n_inst, size=10, replace=False):
+        Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
+        ref, rst = O.crom_step(dec, w.q0[i], Y, w.dt, w.gn_iters, alpha=float(w.alpha[i]))
+        assert rst == 0
+        assert rel_l2(q1[i] - w.q0[i], ref - w.q0[i]) < 5e-3
+    q32, st32 = run_steps(ctx, w, 1, c.CROM_PREC_FP32)
+    assert np.all(st32 == 0)
+    inc = np.linalg.norm((q1 - w.q0) - (q32 - w.q0), axis=1) / np.linalg.norm(q32 - w.q0, axis=1)
+    assert np.median(inc) < 2e-3 and np.max(inc) < 2e-2
+
+
+def test_step_tc_rollout_within_1e3():
+    """100-step rollouts of 6 instances: q_T within 1e-3 relative L2 of the oracle."""
+    c = crom()
+    full = gen.heat2d_batched(n_inst=64)
+    w = subset(full, np.array([0, 5, 17, 33, 48, 63]))
+    ctx = make_ctx(w.spec, w.params)
+    steps = 100
+    qT, st = run_steps(ctx, w, steps, c.CROM_PREC_BF16X2)
+    assert np.all(st == 0)
+    dec = O.MLPDecoder(w.params, 2)
+    for i in range(w.n_inst):
+        Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
+        traj = O.crom_rollout(dec, w.q0[i], Y, w.dt, w.gn_iters, steps, alpha=float(w.alpha[i]))
+        assert rel_l2(qT[i], traj[-1]) < 1e-3
+        assert rel_l2(qT[i] - w.q0[i], traj[-1] - w.q0[i]) < 1e-2
+
+
+def test_step_tc_edge_cases_status():
+    c = crom()
+    spec = gen.DecoderSpec(2, 4, 128, 3)
+    params = gen.xavier_decoder(spec, seed=9, bias_std=0.1, bf16_exact=True)
+    ctx = make_ctx(spec, params)
+    rng = np.random.default_rng(4)
+    good = rng.uniform(0, 1, size=(50, 2)).astype(np.float32)
+    dup = np.tile(np.array([[0.3, 0.7]], np.float32), (20, 1))
+    few = rng.uniform(0, 1, size=(3, 2)).astype(np.float32)
+    sizes = [50, 20, 3, 50, 0]
+    samples = np.concatenate([good, dup, few, good], axis=0)
+    off = gen.ragged_offsets(sizes)
+    q0 = rng.standard_normal((5, 4))
+    alpha = np.array([1.0, 1.0, 1.0, np.nan, 1.0], np.float32)
+    w = gen.StepWorkload("edge", spec, params, q0, alpha, off, samples, 1e-4, 2, 1)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_BF16X2)
+    assert list(st) == [c.CROM_OK, c.CROM_ERR_SINGULAR, c.CROM_ERR_INVALID_ARG, c.CROM_ERR_NONFINITE,
+                        c.CROM_ERR_INVALID_ARG]
+    assert np.array_equal(q1[1:], q0[1:])
+
+
+def test_step_tc_rejects_unsupported():
+    import torch
+    c = crom()
+    w = gen.heat1d_small()   # width 64: no tensor-core image
+    ctx = make_ctx(w.spec, w.params)
+    q = dev(w.q0, torch.float64)
+    st = torch.empty(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(c.CromError) as e:
+        c.crom_step(ctx, q, dev(w.alpha, torch.float32), dev(w.s_off, torch.int32), dev(w.samples, torch.float32),
+                    st, dt=w.dt, gn_iters=1, max_samples=16, precision=c.CROM_PREC_BF16X2)
+    assert e.value.code == c.CROM_ERR_UNSUPPORTED
+    w2 = gen.heat2d_single(bf16_exact=True)
+    ctx2 = make_ctx(w2.spec, w2.params)
+    with pytest.raises(c.CromError) as e:
+        c.crom_step(ctx2, dev(w2.q0, torch.float64), dev(w2.alpha, torch.float32), dev(w2.s_off, torch.int32),
+                    dev(w2.samples, torch.float32), st, dt=w2.dt, gn_iters=2, max_samples=4096,
+                    precision=c.CROM_PREC_BF16X2)
+    assert e.value.code == c.CROM_ERR_INVALID_ARG
