@@ -44,8 +44,47 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--n-inst", type=int, default=1024)
+    ap.add_argument("--n-codes", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default=None, choices=["step", "recon", "plain"],
+                    help="run only one part (warmup + steps launches) for profiling; prints a short JSON line")
     return ap.parse_args()
+
+
+def run_only(args):
+    """Profiling driver: the named part alone, on the bench's workloads."""
+    import torch
+    from paper_2206_02607_gb300 import build
+    build()
+    from paper_2206_02607_gb300 import crom
+    from workloads import gen
+    torch.cuda.set_device(0)
+    n = args.warmup + args.steps
+    if args.only in ("step", "plain"):
+        w = gen.heat2d_batched(n_inst=args.n_inst) if args.only == "step" else gen.heat2d_single()
+        prec = crom.CROM_PREC_BF16X2 if args.only == "step" else crom.CROM_PREC_FP32
+        ctx = crom.crom_create(w.spec.m, w.spec.r, w.spec.width, w.spec.hidden, 0)
+        crom.crom_set_weights(ctx, gen.pack_params(w.params))
+        q = torch.tensor(w.q0, device="cuda")
+        a, o = torch.tensor(w.alpha, device="cuda"), torch.tensor(w.s_off, device="cuda")
+        s, st = torch.tensor(w.samples, device="cuda"), torch.zeros(w.n_inst, dtype=torch.int32, device="cuda")
+        for _ in range(n):
+            crom.crom_step(ctx, q, a, o, s, st, dt=w.dt, gn_iters=w.gn_iters, max_samples=int(w.sizes.max()),
+                           precision=prec)
+        torch.cuda.synchronize()
+        print(json.dumps({"only": args.only, "instances": w.n_inst, "calls": n,
+                          "status_all_ok": bool((st.cpu().numpy() == 0).all())}))
+    else:
+        spec, params, codes, X = gen.recon_dense(n_codes=args.n_codes)
+        ctx = crom.crom_create(spec.m, spec.r, spec.width, spec.hidden, 0)
+        crom.crom_set_weights(ctx, gen.pack_params(params))
+        c, x = torch.tensor(codes, device="cuda"), torch.tensor(X, device="cuda")
+        out = torch.empty((codes.shape[0], X.shape[0]), device="cuda")
+        for _ in range(n):
+            crom.crom_reconstruct(ctx, c, x, out, precision=crom.CROM_PREC_BF16X2)
+        torch.cuda.synchronize()
+        print(json.dumps({"only": "recon", "codes": codes.shape[0], "points": X.shape[0], "calls": n}))
+    ctx.close()
 
 
 def dist_env():
@@ -169,6 +208,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.only:
+        run_only(args)
         return
     import torch
     from paper_2206_02607_gb300 import build

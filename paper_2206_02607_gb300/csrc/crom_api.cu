@@ -273,9 +273,7 @@ int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_in
   } else if (precision == CROM_PREC_BF16X2) {
     if (!tc_shape_ok(ctx->desc) || !ctx->w.tc_img)
       return fail(CROM_ERR_UNSUPPORTED, "crom_step: BF16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15");
-    if (max_samples > tc_step_max_samples())
-      return fail(CROM_ERR_INVALID_ARG, "crom_step: BF16X2 supports |M_i| <= " + std::to_string(tc_step_max_samples()));
-    e = launch_step_tc(ctx, step, n_inst, q, alpha, vel, s_off, samples, max_samples, status, s);
+    e = launch_step_tc(ctx, step, n_inst, q, alpha, vel, s_off, samples, n_samples, max_samples, status, s);
   } else {
     return fail(CROM_ERR_UNSUPPORTED, "crom_step: precision not available for the step");
   }

@@ -86,9 +86,9 @@ cudaError_t launch_step_fp32(crom_ctx* ctx, const crom_step_desc* step, int n_in
 // Tensor-core launches (tc_step.cu, tc_recon.cu).
 cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, double* q,
                            const float* alpha, const float* vel, const int* s_off,
-                           const float* samples, int max_samples, int* status, cudaStream_t s);
+                           const float* samples, int n_samples, int max_samples, int* status,
+                           cudaStream_t s);
 cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const double* q, int n_pts,
                             const float* x, float* out, cudaStream_t s);
-int tc_step_max_samples();
 
 }  // namespace crom

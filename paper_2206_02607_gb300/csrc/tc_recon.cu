@@ -1,19 +1,23 @@
 // Dense reconstruction g(x_p, q_c) on the tcgen05 tensor cores (value channel only).
 //
-// Persistent kernel, one CTA per SM, 128 threads; thread u owns hidden unit u,
-// which is also TMEM lane u.  A tile is 128 points of one latent code:
-//   layer 1 (K = m + r, too small for UMMA) on CUDA cores: the q part of W_1 q + b_1
-//     is hoisted per code; z = W_1x x + c; h = ELU(z);
+// Persistent kernel, one CTA per SM with the decoder's bf16 hidden matrices in
+// shared memory, two independent groups of 128 threads (one tile of 64 points
+// each, own operand buffers / TMEM columns / mbarrier / named barrier) so that
+// one group's UMMAs overlap the other's epilogue.  Thread u of a group owns
+// hidden unit u, which is also TMEM lane u.  A tile is 64 points of one code:
+//   layer 1 (K = m + r, too small for UMMA) on CUDA cores: the q part of
+//     W_1 [x; q] + b_1 is hoisted per code; h = ELU(W_1x x + c);
 //   layers 2..L: D[u][n] = sum_k W_l[u][k] H[k][n] by UMMA (M = 128 units,
-//     N = 128 points, K = 128), A = W_l (K-major, resident in shared memory for
-//     the whole kernel), B = H (MN-major, written by the epilogue of the layer
-//     before); epilogue: bias, ELU, bf16 split, store;
-//   output: D[n][0] = sum_u H_L[u][n] w_out[u] by one more UMMA (M = 128 points,
-//     N = 16 rows of the projection matrix), read back by lane n.
+//     N = 64 points, K = 128), A = W_l (K-major, resident), B = H (MN-major,
+//     written by the previous epilogue); epilogue: bias, ELU, bf16 split, store;
+//   output: D[n][0] = sum_u H_L[u][n] w_out[u] by one more UMMA (M = 128 rows
+//     of which the 64 points are used, N = 16 rows of the projection matrix).
 // Precision: each activation operand h is stored as hi = bf16(h) and
 // lo = bf16(h - hi) and both are multiplied into the same FP32 accumulator
-// (split = 1); split = 0 keeps the high part only.
+// (kSplit = 1); kSplit = 0 keeps the high part only.
 #include <math.h>
+
+#include <algorithm>
 
 #include "crom_internal.h"
 #include "tc_common.cuh"
@@ -23,17 +27,21 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 128;
-constexpr int kTileN = 128;
+constexpr int kGroups = 2;
+constexpr int kGT = 128;
+constexpr int kThreads = kGroups * kGT;
+constexpr int kTileN = 64;
 constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kGroupCols = 128;
 constexpr uint32_t kAccCol = 0;
-constexpr uint32_t kOutCol = 128;
+constexpr uint32_t kOutCol = 64;
 constexpr uint32_t kWaitLimit = 1u << 25;
+constexpr size_t kHBuf = (size_t)kTcWidth * kTileN * 2;  // one bf16 operand buffer, 16 KB
 
 struct ReconParams {
-  const uint8_t* img;  // bf16 tensor-core image (hidden matrices + projection)
+  const uint8_t* img;
   int img_bytes;
-  int n_hidden_mats;   // hidden - 1
+  int n_hidden_mats;  // hidden - 1
   int m, r;
   const float* w1;  // [128][m+r]
   const float* b1;
@@ -44,21 +52,44 @@ struct ReconParams {
   float* out;       // [n_codes][n_pts]
   int n_pts, n_codes;
   int tiles_per_code;
-  int* flag;        // set to 1 on a device-side wait timeout
+  int* flag;  // set to 1 on a device-side wait timeout
 };
 
-struct __align__(8) ReconSmemTail {
+struct __align__(16) Shared {
   uint64_t bar_w;
-  uint64_t bar_mma;
   uint32_t tmem_base;
   int pad;
-  float c1[kTcWidth];     // b_1 + W_1q q for the current code
-  float bh[4 * kTcWidth];
-  float w1x[2 * kTcWidth];
-  float xs[2 * kTileN];
+  float bh[4][kTcWidth];
+  float w1x[2][kTcWidth];
 };
 
-constexpr size_t kH = (size_t)kTcWidth * kTileN * 2;  // one bf16 operand buffer, 32 KB
+struct __align__(16) Group {
+  uint64_t bar_mma;
+  int pad[2];
+  float c1[kTcWidth];
+  float xs[2][kTileN];
+};
+
+// The output UMMA reads 128 rows of a 64-row operand; the rows beyond are unused
+// but the reads must stay inside shared memory.
+constexpr size_t kTailBytes = sizeof(Shared) + kGroups * sizeof(Group);
+constexpr size_t kTailPad = kTailBytes >= kHBuf ? 0 : kHBuf - kTailBytes;
+
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGT) : "memory");
+}
+__device__ __forceinline__ bool group_sync_and(int g, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(1 + g), "r"(kGT)
+      : "memory");
+  return r != 0;
+}
 
 template <int kSplit>
 __device__ __forceinline__ void store_split16(uint8_t* Hhi, uint8_t* Hlo, int k, int n0, const float (&v)[16]) {
@@ -82,41 +113,45 @@ template <int kSplit>
 __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* Wimg = sm;                               // hidden matrices + projection
-  uint8_t* Hhi = sm + ((p.img_bytes + 1023) & ~1023);
-  uint8_t* Hlo = Hhi + kH;
-  ReconSmemTail* T = reinterpret_cast<ReconSmemTail*>(Hlo + kH);
   const int tid = threadIdx.x;
-  const int warp = tid >> 5;
-  const int u = tid;
+  const int g = tid / kGT, u = tid % kGT;
+  const uint32_t lane_base = (uint32_t)(u >> 5) * 32;
   const int m = p.m, r = p.r;
-  const uint32_t lane_base = (uint32_t)warp * 32;
+  uint8_t* Wimg = sm;
+  uint8_t* Hbase = sm + ((p.img_bytes + 1023) & ~1023);
+  uint8_t* Hhi = Hbase + (size_t)g * 2 * kHBuf;
+  uint8_t* Hlo = Hhi + kHBuf;
+  Shared* S = reinterpret_cast<Shared*>(Hbase + (size_t)kGroups * 2 * kHBuf);
+  Group* G = reinterpret_cast<Group*>(S + 1) + g;
 
   if (tid == 0) {
-    mbar_init(&T->bar_w, 1);
-    mbar_init(&T->bar_mma, 1);
+    mbar_init(&S->bar_w, 1);
     fence_mbar_init();
   }
-  if (warp == 0) {
-    tmem_alloc(&T->tmem_base, kTmemCols);
+  if (u == 0) {
+    mbar_init(&G->bar_mma, 1);
+    fence_mbar_init();
+  }
+  if (tid < 32) {
+    tmem_alloc(&S->tmem_base, kTmemCols);
     tmem_relinquish();
   }
-  for (int i = tid; i < p.n_hidden_mats * kTcWidth; i += kThreads) T->bh[i] = p.bh[i];
-  for (int i = tid; i < m * kTcWidth; i += kThreads) T->w1x[i] = p.w1[(i % kTcWidth) * (m + r) + i / kTcWidth];
+  if (g == 0) {
+    for (int i = u; i < p.n_hidden_mats * kTcWidth; i += kGT) S->bh[i / kTcWidth][i % kTcWidth] = p.bh[i];
+    for (int k = 0; k < m; ++k) S->w1x[k][u] = p.w1[u * (m + r) + k];
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tb = T->tmem_base;
+  const uint32_t tb = S->tmem_base + (uint32_t)g * kGroupCols;
   if (tid == 0) {
-    mbar_arrive_expect_tx(&T->bar_w, (uint32_t)p.img_bytes);
-    for (int off = 0; off < p.img_bytes; off += 16384) {
-      const int bytes = min(16384, p.img_bytes - off);
-      bulk_g2s(Wimg + off, p.img + off, (uint32_t)bytes, &T->bar_w);
-    }
+    mbar_arrive_expect_tx(&S->bar_w, (uint32_t)p.img_bytes);
+    for (int off = 0; off < p.img_bytes; off += 16384)
+      bulk_g2s(Wimg + off, p.img + off, (uint32_t)min(16384, p.img_bytes - off), &S->bar_w);
   }
-  // Every wait is bounded; the outcome is made uniform across the CTA before
-  // anyone acts on it, so no thread can leave while others still wait at a barrier.
-  bool ok = __syncthreads_and(mbar_wait(&T->bar_w, 0, kWaitLimit));
+  // Every wait is bounded; the outcome is made uniform across the CTA (or group)
+  // before anyone acts on it, so no thread leaves while others wait at a barrier.
+  bool ok = __syncthreads_and(mbar_wait(&S->bar_w, 0, kWaitLimit));
   uint32_t phase = 0;
   const uint32_t wbase = smem_u32(Wimg);
   const uint32_t proj = wbase + (uint32_t)p.n_hidden_mats * kTcLayerBytes;
@@ -124,68 +159,64 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
   constexpr uint32_t id_layer = idesc_f16(128, kTileN, false, true, true);
   constexpr uint32_t id_out = idesc_f16(128, 16, true, false, true);
   int cur_code = -1;
+  float c = 0.f;
+  const float wx0 = S->w1x[0][u], wx1 = (m > 1) ? S->w1x[1][u] : 0.f;
   const int n_tiles = p.n_codes * p.tiles_per_code;
 
-  for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+  for (int tile = blockIdx.x * kGroups + g; tile < n_tiles && ok; tile += gridDim.x * kGroups) {
     const int code = tile / p.tiles_per_code;
     const int p0 = (tile % p.tiles_per_code) * kTileN;
     if (code != cur_code) {
-      double c = (double)p.b1[u];
-      for (int j = 0; j < r; ++j) c += (double)p.w1[u * (m + r) + m + j] * p.q[(size_t)code * r + j];
-      T->c1[u] = (float)c;
+      double cc = (double)p.b1[u];
+      for (int j = 0; j < r; ++j) cc += (double)p.w1[u * (m + r) + m + j] * p.q[(size_t)code * r + j];
+      c = (float)cc;
       cur_code = code;
     }
-    {
-      const int n = p0 + tid;
-      for (int k = 0; k < m; ++k) T->xs[k * kTileN + tid] = (n < p.n_pts) ? p.x[(size_t)n * m + k] : 0.f;
+    if (u < kTileN) {
+      const int n = p0 + u;
+      for (int k = 0; k < m; ++k) G->xs[k][u] = (n < p.n_pts) ? p.x[(size_t)n * m + k] : 0.f;
     }
-    __syncthreads();
+    group_sync(g);
     // ---- layer 1 on CUDA cores
-    {
-      const float c = T->c1[u];
-      const float wx0 = T->w1x[u], wx1 = (m > 1) ? T->w1x[kTcWidth + u] : 0.f;
 #pragma unroll 1
-      for (int n0 = 0; n0 < kTileN; n0 += 16) {
-        float v[16];
+    for (int n0 = 0; n0 < kTileN; n0 += 16) {
+      float v[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          float z = fmaf(wx0, T->xs[n0 + i], c);
-          if (m > 1) z = fmaf(wx1, T->xs[kTileN + n0 + i], z);
-          v[i] = elu(z);
-        }
-        store_split16<kSplit>(Hhi, Hlo, u, n0, v);
+      for (int i = 0; i < 16; ++i) {
+        float z = fmaf(wx0, G->xs[0][n0 + i], c);
+        if (m > 1) z = fmaf(wx1, G->xs[1][n0 + i], z);
+        v[i] = elu(z);
       }
+      store_split16<kSplit>(Hhi, Hlo, u, n0, v);
     }
-    // ---- hidden layers on the tensor cores
+    // ---- hidden layers and the output layer on the tensor cores
     for (int l = 0; l <= p.n_hidden_mats; ++l) {
       const bool last = (l == p.n_hidden_mats);
       fence_proxy_async_smem();
       tc_fence_before();
-      __syncthreads();
-      if (tid == 0) {
+      group_sync(g);
+      if (u == 0) {
         tc_fence_after();
         if (!last) {
           const uint32_t a = wbase + (uint32_t)l * kTcLayerBytes;
-          for (int kk = 0; kk < 8; ++kk)
-            umma_f16(tb + kAccCol, desc_kmajor(a, 128, kk), desc_mnmajor(hhi, kk), id_layer, kk > 0);
-          if (kSplit)
+          for (int part = 0; part <= kSplit; ++part)
             for (int kk = 0; kk < 8; ++kk)
-              umma_f16(tb + kAccCol, desc_kmajor(a, 128, kk), desc_mnmajor(hlo, kk), id_layer, 1);
+              umma_f16(tb + kAccCol, desc_kmajor(a, 128, kk), desc_mnmajor(part ? hlo : hhi, kk), id_layer,
+                       (part | kk) != 0);
         } else {
-          for (int kk = 0; kk < 8; ++kk)
-            umma_f16(tb + kOutCol, desc_mnmajor(hhi, kk), desc_kmajor(proj, 16, kk), id_out, kk > 0);
-          if (kSplit)
+          for (int part = 0; part <= kSplit; ++part)
             for (int kk = 0; kk < 8; ++kk)
-              umma_f16(tb + kOutCol, desc_mnmajor(hlo, kk), desc_kmajor(proj, 16, kk), id_out, 1);
+              umma_f16(tb + kOutCol, desc_mnmajor(part ? hlo : hhi, kk), desc_kmajor(proj, 16, kk), id_out,
+                       (part | kk) != 0);
         }
-        umma_commit(&T->bar_mma);
+        umma_commit(&G->bar_mma);
       }
-      ok = __syncthreads_and(mbar_wait(&T->bar_mma, phase, kWaitLimit));
+      ok = group_sync_and(g, mbar_wait(&G->bar_mma, phase, kWaitLimit));
       phase ^= 1;
       tc_fence_after();
       if (!ok) break;
       if (!last) {
-        const float bias = T->bh[l * kTcWidth + u];
+        const float bias = S->bh[l][u];
 #pragma unroll 1
         for (int n0 = 0; n0 < kTileN; n0 += 16) {
           float v[16];
@@ -199,15 +230,15 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
         float v[16];
         tmem_ld16(taddr(tb, lane_base, kOutCol), v);
         tmem_ld_wait();
-        const int n = p0 + tid;
-        if (n < p.n_pts) p.out[(size_t)code * p.n_pts + n] = v[0] + p.bout;
+        const int n = p0 + u;
+        if (u < kTileN && n < p.n_pts) p.out[(size_t)code * p.n_pts + n] = v[0] + p.bout;
       }
     }
   }
-  if (!ok && tid == 0) atomicExch(p.flag, 1);
+  if (!ok && u == 0) atomicExch(p.flag, 1);
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tb, kTmemCols);
+  if (tid < 32) tmem_dealloc(S->tmem_base, kTmemCols);
 }
 
 }  // namespace
@@ -230,11 +261,12 @@ cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const d
   p.n_pts = n_pts;
   p.n_codes = n_codes;
   p.tiles_per_code = (n_pts + kTileN - 1) / kTileN;
-  p.flag = ctx->queue + 1;
-  const size_t smem = 1024 + (((size_t)p.img_bytes + 1023) & ~(size_t)1023) + 2 * kH + sizeof(ReconSmemTail);
+  p.flag = ctx->queue + 2;
+  const size_t smem = 1024 + (((size_t)p.img_bytes + 1023) & ~(size_t)1023) + (size_t)kGroups * 2 * kHBuf +
+                      kTailBytes + kTailPad;
   const long long tiles = (long long)n_codes * p.tiles_per_code;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-  const int grid = (int)std::min<long long>(tiles, ctx->num_sms);
+  const int grid = (int)std::min<long long>((tiles + kGroups - 1) / kGroups, ctx->num_sms);
   cudaError_t e;
   if (split) {
     e = cudaFuncSetAttribute(recon_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -45,6 +45,47 @@ def run_steps(ctx, w, steps, precision, gn_iters=None, dt=None):
     return d.q.cpu().numpy(), d.status.cpu().numpy()
 
 
+def kink_margin(params, Y, q):
+    """Smallest |pre-activation| over all hidden units at any of the samples
+    (plain test-side forward pass).  ELU is C^1 but not C^2: its s'' jumps from
+    e^0 = 1 to 0 at z = 0, so the network Laplacian is discontinuous there and two
+    correct evaluations in different precisions may take opposite branches at a
+    sample that lies within rounding distance of a kink."""
+    Y = np.asarray(Y, np.float64)
+    h = np.concatenate([Y, np.broadcast_to(np.asarray(q, np.float64), (Y.shape[0], len(q)))], axis=1)
+    margin = np.inf
+    for W, b in params[:-1]:
+        z = h @ np.asarray(W).T + np.asarray(b)
+        margin = min(margin, float(np.abs(z).min()))
+        h = np.where(z > 0, z, np.expm1(np.minimum(z, 0)))
+    return margin
+
+
+def increment_errors(params, m, q0, Y, q_gpu, q_ref, dt, alpha):
+    """Errors of a GPU step against the oracle's, for one instance.
+
+    Returns (inc, res, kappa, margin):
+      inc    = ||d_gpu - d_ref|| / ||d_ref||, d = q_{n+1} - q_n (the latent increment);
+      res    = ||J (d_gpu - d_ref)|| / ||Delta f|| with the FP64 Jacobian J = dg/dq(Y, q_n)
+               and the oracle's PDE update Delta f at the samples: the error of the
+               fitted field change, relative to the update being fitted (a backward-
+               error measure of the least-squares projection);
+      kappa  = condition number of J;
+      margin = kink_margin at q_n.
+    Least-squares perturbation theory bounds inc by about kappa times the relative
+    errors of J and Delta f, so ill-conditioned instances legitimately show a larger
+    `inc` while `res` stays at the level of the arithmetic."""
+    from oracle import crom_oracle as O
+    dec = O.MLPDecoder(params, m)
+    ev = dec(Y, q0)
+    J = ev.gq
+    df = dt * float(alpha) * ev.lap
+    d_gpu, d_ref = q_gpu - q0, q_ref - q0
+    inc = float(np.linalg.norm(d_gpu - d_ref) / np.linalg.norm(d_ref))
+    res = float(np.linalg.norm(J @ (d_gpu - d_ref)) / np.linalg.norm(df))
+    return inc, res, float(np.linalg.cond(J)), kink_margin(params, Y, q0)
+
+
 def subset(w, idx):
     """A StepWorkload restricted to the instances in idx (oracle-sized sample)."""
     from workloads import gen
