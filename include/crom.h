@@ -151,6 +151,27 @@ int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_in
               const float* alpha, const float* vel, const int* s_off, const float* samples,
               int n_samples, int max_samples, int* status, crom_stream stream);
 
+/* crom_step with precision CROM_PREC_FP32, for callers that cannot allocate
+ * device memory when they step: code recording the step into a CUDA graph during
+ * stream capture (where cudaMalloc is not allowed), hosts whose memory policy
+ * forbids direct cudaMalloc/cudaFree, and latency-critical loops that must not
+ * risk an allocation that synchronises the device.  The paper has no
+ * counterpart; this is an operational variant of the same step.
+ * Arguments, results and status codes are those of crom_step.  The scratch lives
+ * in one fixed 8 MiB device array per GPU, held from library load until process
+ * exit; a batch that needs more (about n_inst * ceil(max_samples / S) *
+ * (r(r+1)/2 + r) * 8 bytes of partial sums, S <= 4 samples per CTA, plus
+ * 8 * (n_samples + n_inst * r) bytes) is rejected with CROM_ERR_INVALID_ARG and
+ * nothing is launched.  The call allocates and frees nothing.  Its first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  Every call shares the array and finds
+ * the previous call's contents in it: the call clears the parts that must start
+ * at zero, but two calls whose work may overlap on the GPU (different streams
+ * without ordering) race on the array and must not be issued. */
+int crom_step_noalloc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, double* q,
+                      const float* alpha, const float* vel, const int* s_off, const float* samples,
+                      int n_samples, int max_samples, int* status, crom_stream stream);
+
 /* Dense reconstruction g(x_p, q_c) for n_codes latent codes q [n_codes][r]
  * (FP64) at n_pts points x [n_pts][m] (FP32); out [n_codes][n_pts] FP32.
  * precision FP32 (any shape), BF16X2 or BF16 (tensor cores; width 128). */

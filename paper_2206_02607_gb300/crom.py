@@ -36,7 +36,7 @@ CROM_WANT_DQ = 16
 
 # Every symbol include/crom.h declares.
 EXPORTED = ("crom_version", "crom_last_error", "crom_create", "crom_destroy", "crom_set_weights",
-            "crom_decode", "crom_step", "crom_reconstruct")
+            "crom_decode", "crom_step", "crom_step_noalloc", "crom_reconstruct")
 
 
 class CromError(RuntimeError):
@@ -66,6 +66,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.crom_set_weights.argtypes = [vp, vp, sz, i, vp]
     lib.crom_decode.argtypes = [vp, i, vp, vp, vp, i, u, vp, vp]
     lib.crom_step.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, i, vp, vp, vp, vp, vp, i, i, vp, vp]
+    lib.crom_step_noalloc.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, vp, vp, vp, vp, vp, i, i, vp, vp]
     lib.crom_reconstruct.argtypes = [vp, i, i, vp, i, vp, vp, vp]
     for name in EXPORTED:
         if name not in ("crom_version", "crom_last_error"):
@@ -167,6 +168,19 @@ def crom_step(ctx: CromContext, q, alpha, s_off, samples, status, *, dt: float, 
     _check(_LIB.crom_step(ctx.handle, ctypes.byref(desc), precision, q.shape[0], _ptr(q), _ptr(alpha),
                           _ptr(vel), _ptr(s_off), _ptr(samples), samples.shape[0], max_samples, _ptr(status),
                           _stream(stream)))
+
+
+def crom_step_noalloc(ctx: CromContext, q, alpha, s_off, samples, status, *, dt: float, gn_iters: int,
+                      max_samples: int, pde: int = CROM_PDE_HEAT, vel=None, stream=None):
+    """The FP32 step with its scratch in the library's fixed device array: for
+    callers that must not allocate device memory while stepping (see crom.h)."""
+    import torch
+    _need(q, torch.float64, "q"); _need(alpha, torch.float32, "alpha"); _need(s_off, torch.int32, "s_off")
+    _need(samples, torch.float32, "samples"); _need(status, torch.int32, "status"); _need(vel, torch.float32, "vel")
+    desc = crom_step_desc(pde, gn_iters, dt)
+    _check(_LIB.crom_step_noalloc(ctx.handle, ctypes.byref(desc), q.shape[0], _ptr(q), _ptr(alpha), _ptr(vel),
+                                  _ptr(s_off), _ptr(samples), samples.shape[0], max_samples, _ptr(status),
+                                  _stream(stream)))
 
 
 def crom_reconstruct(ctx: CromContext, q, x, out, precision: int = CROM_PREC_FP32, stream=None):

@@ -281,6 +281,37 @@ int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_in
   return CROM_OK;
 }
 
+int crom_step_noalloc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, double* q, const float* alpha,
+                      const float* vel, const int* s_off, const float* samples, int n_samples, int max_samples,
+                      int* status, crom_stream stream) {
+  if (!ctx || !step) return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: null argument");
+  if (!ctx->has_weights) return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: weights not set");
+  if (n_inst < 0 || n_samples < 0) return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: negative size");
+  if (!(step->dt > 0.0) || !isfinite(step->dt))
+    return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: dt must be finite and > 0");
+  if (step->gn_iters < 1 || step->gn_iters > 16)
+    return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: gn_iters must be in 1..16");
+  if (step->pde != CROM_PDE_HEAT && step->pde != CROM_PDE_ADVDIFF)
+    return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: unknown pde");
+  if (n_inst == 0) return CROM_OK;
+  if (!q || !alpha || !s_off || !status || (n_samples > 0 && !samples))
+    return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: null array");
+  if (step->pde == CROM_PDE_ADVDIFF && !vel)
+    return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: advection needs vel");
+  if (max_samples < 1) return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: max_samples must be >= 1");
+  DeviceGuard g(ctx->device);
+  size_t need = 0;
+  cudaError_t e = launch_step_fp32_noalloc(ctx, step, n_inst, q, alpha, vel, s_off, samples, n_samples,
+                                           max_samples, status, (cudaStream_t)stream, &need);
+  if (need > noalloc_scratch_capacity())
+    return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: this batch needs " + std::to_string(need) +
+                                          " bytes of scratch, more than the fixed " +
+                                          std::to_string(noalloc_scratch_capacity()) +
+                                          " bytes; use crom_step or a smaller batch");
+  if (e != cudaSuccess) return cuda_fail(e, "crom_step_noalloc");
+  return CROM_OK;
+}
+
 int crom_reconstruct(crom_ctx* ctx, int precision, int n_codes, const double* q, int n_pts,
                      const float* x, float* out, crom_stream stream) {
   if (!ctx) return fail(CROM_ERR_INVALID_ARG, "crom_reconstruct: null context");

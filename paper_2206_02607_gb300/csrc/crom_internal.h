@@ -83,6 +83,13 @@ cudaError_t launch_step_fp32(crom_ctx* ctx, const crom_step_desc* step, int n_in
                              const float* samples, int n_samples, int max_samples, int* status,
                              cudaStream_t s);
 
+// FP32 step with its scratch in a fixed-size device array (no allocation).
+size_t noalloc_scratch_capacity();
+cudaError_t launch_step_fp32_noalloc(const crom_ctx* ctx, const crom_step_desc* step, int n_inst, double* q,
+                                     const float* alpha, const float* vel, const int* s_off,
+                                     const float* samples, int n_samples, int max_samples, int* status,
+                                     cudaStream_t s, size_t* need_bytes);
+
 // Tensor-core launches (tc_step.cu, tc_recon.cu).
 cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, double* q,
                            const float* alpha, const float* vel, const int* s_off,

@@ -18,6 +18,8 @@
 // Nothing ever waits on another CTA.
 #include <math.h>
 
+#include <mutex>
+
 #include "crom_internal.h"
 
 namespace crom {
@@ -583,6 +585,117 @@ cudaError_t launch_step_fp32(crom_ctx* ctx, const crom_step_desc* step, int n_in
     p.nq = r;
     p.C = 1 + p.diff + ChannelSet{p.nx, p.second, p.nq}.count(m) - 1;
     cudaError_t e = launch_fwd(p, grid, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace crom
+
+// ---------------------------------------------------------------------------
+// FP32 step without any device allocation (crom_step_noalloc).
+//
+// Some callers cannot allocate device memory at the time they step: code that
+// records the step into a CUDA graph while the stream is being captured (a
+// cudaMalloc there is an error in global capture mode), hosts whose allocator
+// policy forbids direct cudaMalloc/cudaFree, and latency-critical loops where an
+// allocation may synchronise the device.  For them this variant of the FP32 step
+// takes its scratch (per-CTA partial normal equations, per-instance tickets,
+// per-sample Delta f and per-instance q_n) from one file-scope device array of
+// fixed size instead of the context's growable buffers.
+//
+// The array exists once per device for the life of the process (every GPU that
+// loads the library holds its 8 MiB).  All calls on a device share it and it
+// keeps the last call's contents: the tickets are cleared with a memset at every
+// call; two calls whose kernels overlap on the GPU (different streams, no
+// ordering between them) race on it and must not be issued.
+namespace crom {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {};
+int g_noalloc_ready[kMaxDevices] = {};
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+size_t noalloc_scratch_capacity() { return kNoAllocScratchBytes; }
+
+// Set-up, once per device and with that device current: the host-side name of
+// the array is only a stand-in, the kernel needs its device address.
+cudaError_t noalloc_scratch_address(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!g_noalloc_ready[device]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[device] = ptr;
+    g_noalloc_ready[device] = 1;
+  }
+  *out = g_noalloc_ptr[device];
+  return cudaSuccess;
+}
+
+cudaError_t launch_step_fp32_noalloc(const crom_ctx* ctx, const crom_step_desc* step, int n_inst, double* q,
+                                     const float* alpha, const float* vel, const int* s_off,
+                                     const float* samples, int n_samples, int max_samples, int* status,
+                                     cudaStream_t s, size_t* need_bytes) {
+  FwdParams p{};
+  p.mode = kModeStep;
+  fill_decoder(p, ctx);
+  const int m = p.m, r = p.r;
+  const int C0 = ChannelSet{m, kSecondLap, r}.count(m);
+  int S = 4;
+  while (S > 1 && (long long)n_inst * ((max_samples + S - 1) / S) < 2LL * ctx->num_sms) S >>= 1;
+  S = pick_samples(p.width, C0, m, r, S);
+  const int max_tiles = (max_samples + S - 1) / S;
+  const int n_entries = r * (r + 1) / 2 + r;
+  // layout inside the static array
+  const size_t off_cnt = 0;
+  const size_t off_part = off_cnt + align256((size_t)n_inst * sizeof(int));
+  const size_t off_tgt = off_part + align256((size_t)n_inst * max_tiles * n_entries * sizeof(double));
+  const size_t off_qb = off_tgt + align256((size_t)n_samples * sizeof(double));
+  const size_t total = off_qb + align256((size_t)n_inst * r * sizeof(double));
+  *need_bytes = total;
+  if (total > kNoAllocScratchBytes || max_tiles > 65535) return cudaErrorInvalidValue;
+  void* base = nullptr;
+  cudaError_t e = noalloc_scratch_address(ctx->device, &base);
+  if (e != cudaSuccess) return e;
+  unsigned char* b = static_cast<unsigned char*>(base);
+  e = cudaMemsetAsync(b + off_cnt, 0, (size_t)n_inst * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  p.S = S;
+  p.off = s_off;
+  p.x = samples;
+  p.n_inst = n_inst;
+  p.pde = step->pde;
+  p.dt = step->dt;
+  p.alpha = alpha;
+  p.vel = vel;
+  p.max_samples = max_samples;
+  p.qio = q;
+  p.status = status;
+  p.partials = reinterpret_cast<double*>(b + off_part);
+  p.max_tiles = max_tiles;
+  p.n_entries = n_entries;
+  p.counters = reinterpret_cast<int*>(b + off_cnt);
+  p.targets = reinterpret_cast<double*>(b + off_tgt);
+  p.qbase = reinterpret_cast<double*>(b + off_qb);
+  dim3 grid(n_inst, max_tiles);
+  for (int it = 0; it < step->gn_iters; ++it) {
+    p.iter = it;
+    p.diff = (it == 0) ? 0 : 1;
+    p.nx = (it == 0) ? m : 0;
+    p.second = (it == 0) ? kSecondLap : kSecondNone;
+    p.nq = r;
+    p.C = 1 + p.diff + ChannelSet{p.nx, p.second, p.nq}.count(m) - 1;
+    e = launch_fwd(p, grid, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
