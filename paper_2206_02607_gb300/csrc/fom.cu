@@ -1,0 +1,116 @@
+// Full-order models on the GPU: explicit finite differences + forward Euler
+// (paper App. G.2 for the 1D heat equation, App. H.2 for the 2D form), batched
+// over independent fields.  These are the data generators and the judges of
+// rollout error; every update is a 5-point (3-point in 1D) stencil, so the
+// kernels are bound by memory traffic: one read and one write of u per node and
+// step (plus the two face velocities for advection).  Neighbour values are
+// served by L1/L2.
+//
+//  * heat 1D, Dirichlet 0: nodes x_i = i/(P-1); interior
+//      u_i += dt * nu * (u_{i-1} + u_{i+1} - 2 u_i) / dx^2, boundary nodes = 0.
+//  * heat 2D, zero Neumann: nodes (i, j)/(n-1); mirror ghost nodes
+//      u_{-1} = u_1, u_n = u_{n-2}; u += dt * alpha * Lap_h u.
+//  * advection-diffusion 2D, periodic cells of width 1/n: conservative
+//      first-order upwind fluxes with face velocities ax[i][j] (between cells
+//      (i, j) and (i+1, j)) and ay[i][j] (between (i, j) and (i, j+1)), central
+//      diffusion: u += dt * (-div(a u) + nu * Lap_h u).
+// Layout: fields [n_batch][nx][ny] FP32 row-major (j fastest); face velocities
+// [n_batch][nx][ny]; coefficients nu/alpha per field.
+#include "crom_internal.h"
+
+namespace crom {
+namespace {
+
+__global__ void heat1d_kernel(const float* __restrict__ u, float* __restrict__ out, const float* __restrict__ coef,
+                              int P, float r_over) {
+  // r_over = dt / dx^2
+  const int b = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const float* ub = u + (size_t)b * P;
+  float v = 0.f;
+  if (i > 0 && i < P - 1) {
+    const float c = ub[i];
+    v = fmaf(r_over * coef[b], ub[i - 1] + ub[i + 1] - 2.f * c, c);
+  }
+  out[(size_t)b * P + i] = v;
+}
+
+__global__ void heat2d_neumann_kernel(const float* __restrict__ u, float* __restrict__ out,
+                                      const float* __restrict__ coef, int n, float r_over) {
+  // r_over = dt / h^2; block = 32 x 8 nodes, j fastest
+  const int b = blockIdx.z;
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  const int i = blockIdx.y * 8 + threadIdx.y;
+  if (i >= n || j >= n) return;
+  const float* ub = u + (size_t)b * n * n;
+  const int im = i > 0 ? i - 1 : 1, ip = i < n - 1 ? i + 1 : n - 2;
+  const int jm = j > 0 ? j - 1 : 1, jp = j < n - 1 ? j + 1 : n - 2;
+  const float c = ub[(size_t)i * n + j];
+  const float lap = (ub[(size_t)im * n + j] + ub[(size_t)ip * n + j] - 2.f * c) +
+                    (ub[(size_t)i * n + jm] + ub[(size_t)i * n + jp] - 2.f * c);
+  out[(size_t)b * n * n + (size_t)i * n + j] = fmaf(r_over * coef[b], lap, c);
+}
+
+__global__ void advdiff2d_kernel(const float* __restrict__ u, float* __restrict__ out,
+                                 const float* __restrict__ ax, const float* __restrict__ ay,
+                                 const float* __restrict__ coef, int n, float dt, float inv_h, float inv_h2) {
+  const int b = blockIdx.z;
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  const int i = blockIdx.y * 8 + threadIdx.y;
+  if (i >= n || j >= n) return;
+  const size_t base = (size_t)b * n * n;
+  const float* ub = u + base;
+  const float* axb = ax + base;
+  const float* ayb = ay + base;
+  const int im = i > 0 ? i - 1 : n - 1, ip = i < n - 1 ? i + 1 : 0;
+  const int jm = j > 0 ? j - 1 : n - 1, jp = j < n - 1 ? j + 1 : 0;
+  const float c = ub[(size_t)i * n + j];
+  const float uim = ub[(size_t)im * n + j], uip = ub[(size_t)ip * n + j];
+  const float ujm = ub[(size_t)i * n + jm], ujp = ub[(size_t)i * n + jp];
+  const float a_r = axb[(size_t)i * n + j], a_l = axb[(size_t)im * n + j];
+  const float b_r = ayb[(size_t)i * n + j], b_l = ayb[(size_t)i * n + jm];
+  const float fr = a_r * (a_r > 0.f ? c : uip);    // flux through the face (i+1/2, j)
+  const float fl = a_l * (a_l > 0.f ? uim : c);    // flux through the face (i-1/2, j)
+  const float gr = b_r * (b_r > 0.f ? c : ujp);
+  const float gl = b_l * (b_l > 0.f ? ujm : c);
+  const float div = (fr - fl + gr - gl) * inv_h;
+  const float lap = (uim + uip + ujm + ujp - 4.f * c) * inv_h2;
+  out[base + (size_t)i * n + j] = fmaf(dt, fmaf(coef[b], lap, -div), c);
+}
+
+}  // namespace
+
+cudaError_t launch_fom(int kind, int n_batch, int nx, int ny, const float* coef, const float* ax, const float* ay,
+                       double dt, int n_steps, float* u, float* tmp, cudaStream_t s) {
+  float* src = u;
+  float* dst = tmp;
+  for (int k = 0; k < n_steps; ++k) {
+    if (kind == CROM_FOM_HEAT1D_DIRICHLET) {
+      const double dx = 1.0 / (nx - 1);
+      dim3 grid((nx + 255) / 256, n_batch);
+      heat1d_kernel<<<grid, 256, 0, s>>>(src, dst, coef, nx, (float)(dt / (dx * dx)));
+    } else if (kind == CROM_FOM_HEAT2D_NEUMANN) {
+      const double h = 1.0 / (nx - 1);
+      dim3 grid((nx + 31) / 32, (nx + 7) / 8, n_batch);
+      heat2d_neumann_kernel<<<grid, dim3(32, 8), 0, s>>>(src, dst, coef, nx, (float)(dt / (h * h)));
+    } else {
+      const double h = 1.0 / nx;
+      dim3 grid((nx + 31) / 32, (nx + 7) / 8, n_batch);
+      advdiff2d_kernel<<<grid, dim3(32, 8), 0, s>>>(src, dst, ax, ay, coef, nx, (float)dt, (float)(1.0 / h),
+                                                    (float)(1.0 / (h * h)));
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    float* t = src;
+    src = dst;
+    dst = t;
+  }
+  if (src != u) {
+    const size_t bytes = (size_t)n_batch * nx * ny * sizeof(float);
+    return cudaMemcpyAsync(u, src, bytes, cudaMemcpyDeviceToDevice, s);
+  }
+  return cudaSuccess;
+}
+
+}  // namespace crom
