@@ -151,6 +151,18 @@ int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_in
               const float* alpha, const float* vel, const int* s_off, const float* samples,
               int n_samples, int max_samples, int* status, crom_stream stream);
 
+/* A rollout: n_steps consecutive crom_step calls (same arguments, q advanced in
+ * place) recorded once into a CUDA graph and replayed with one launch.  The graph
+ * is built on the first call for a given argument set (pointers, sizes, step
+ * description, precision, n_steps) and cached in the context; a call with the
+ * same arguments relaunches the cached graph, a call with different arguments
+ * rebuilds it.  status receives the per-instance status of the last step.  The
+ * first call for an argument set allocates and records: do not make it during
+ * stream capture. */
+int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_steps, int n_inst, double* q,
+                 const float* alpha, const float* vel, const int* s_off, const float* samples, int n_samples,
+                 int max_samples, int* status, crom_stream stream);
+
 /* crom_step with precision CROM_PREC_FP32, for callers that cannot allocate
  * device memory when they step: code recording the step into a CUDA graph during
  * stream capture (where cudaMalloc is not allowed), hosts whose memory policy
@@ -171,6 +183,61 @@ int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_in
 int crom_step_noalloc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, double* q,
                       const float* alpha, const float* vel, const int* s_off, const float* samples,
                       int n_samples, int max_samples, int* status, crom_stream stream);
+
+/* Full-order model: n_steps explicit finite-difference steps with forward Euler
+ * (paper App. G.2 and H.2) for n_batch independent FP32 fields, in place on the
+ * current CUDA device.  Fields u [n_batch][nx][ny] row-major (ny fastest);
+ * tmp is caller-owned scratch of the same size (distinct from u); coef
+ * [n_batch] is nu (heat 1D), alpha (heat 2D) or nu (advection-diffusion).
+ *  CROM_FOM_HEAT1D_DIRICHLET   ny == 1, nodes x_i = i/(nx-1), boundary nodes 0.
+ *  CROM_FOM_HEAT2D_NEUMANN     ny == nx, nodes (i, j)/(nx-1), zero-flux boundary
+ *                              by mirror ghost nodes (u_{-1} = u_1).
+ *  CROM_FOM_ADVDIFF2D_PERIODIC ny == nx, periodic cells of width 1/nx,
+ *                              conservative first-order upwind advection with face
+ *                              velocities ax (between cells (i,j),(i+1,j)) and ay
+ *                              (between (i,j),(i,j+1)), [n_batch][nx][ny] each,
+ *                              plus central diffusion.
+ * nx >= 3, n_batch <= 65535.  The result is in u when the call's work completes. */
+typedef enum {
+  CROM_FOM_HEAT1D_DIRICHLET = 0,
+  CROM_FOM_HEAT2D_NEUMANN = 1,
+  CROM_FOM_ADVDIFF2D_PERIODIC = 2
+} crom_fom_kind;
+
+int crom_fom_step(int kind, int n_batch, int nx, int ny, const float* coef, const float* ax, const float* ay,
+                  double dt, int n_steps, float* u, float* tmp, crom_stream stream);
+
+/* ---- Manifold construction: one training step (paper §3, Eq. loss; App. D) ----
+ * Encoder e(f): 1D convolutions (kernel 6, stride 4, one channel, no padding,
+ * ELU after each) on the flattened snapshot of P nodes, repeated while the output
+ * stays >= 32 long; a dense layer to 32 (ELU); a linear layer to r.  Decoder:
+ * g(x, q) of the given crom_decoder_desc.  Loss: mean over B snapshots x S
+ * sampled nodes of (g(x_j, e(f_b)) - f_b(x_j))^2.  Adam (beta1 0.9, beta2 0.999,
+ * eps 1e-8) on FP32 master parameters; FP32 arithmetic on CUDA cores.
+ * Parameter vector (FP32): the decoder exactly as crom_set_weights packs it, then
+ * per convolution w[6], b, then the dense layers W[32][L_last], b[32], W[r][32],
+ * b[r].  The trainer owns all its device memory. */
+typedef struct crom_trainer crom_trainer;
+
+/* P snapshot nodes, B snapshots and S sampled nodes per step (fixed per trainer).
+ * Parameters start at zero: load them with crom_trainer_set_params. */
+int crom_trainer_create(crom_trainer** out, const crom_decoder_desc* dec, int P, int B, int S, int device);
+int crom_trainer_destroy(crom_trainer* tr);
+/* Number of floats in the parameter vector. */
+int crom_trainer_param_count(const crom_trainer* tr, size_t* n);
+/* Copy the parameter vector in (set) or out (get); on_device selects device (1)
+ * or host (0) memory for `params`.  set also resets the Adam moments and step. */
+int crom_trainer_set_params(crom_trainer* tr, const float* params, size_t n, int on_device, crom_stream stream);
+int crom_trainer_get_params(crom_trainer* tr, float* params, size_t n, int on_device, crom_stream stream);
+/* Gradient of the last crom_train_step (same layout as the parameters). */
+int crom_trainer_get_grads(crom_trainer* tr, float* grads, size_t n, int on_device, crom_stream stream);
+/* One step: snaps [B][P] FP32, pt_idx [B][S] int32 node indices in [0, P),
+ * coords [P][m] FP32 node coordinates, learning rate lr; loss_out (device, one
+ * double, may be NULL) receives the loss before the update. */
+int crom_train_step(crom_trainer* tr, const float* snaps, const int* pt_idx, const float* coords, float lr,
+                    double* loss_out, crom_stream stream);
+/* Encoder only: q [n][r] FP32 for n <= B snapshots [n][P] (initial latent codes). */
+int crom_encode(crom_trainer* tr, int n, const float* snaps, float* q, crom_stream stream);
 
 /* Dense reconstruction g(x_p, q_c) for n_codes latent codes q [n_codes][r]
  * (FP64) at n_pts points x [n_pts][m] (FP32); out [n_codes][n_pts] FP32.

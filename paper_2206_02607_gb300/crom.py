@@ -35,8 +35,15 @@ CROM_WANT_LAP = 8
 CROM_WANT_DQ = 16
 
 # Every symbol include/crom.h declares.
+CROM_FOM_HEAT1D_DIRICHLET = 0
+CROM_FOM_HEAT2D_NEUMANN = 1
+CROM_FOM_ADVDIFF2D_PERIODIC = 2
+
 EXPORTED = ("crom_version", "crom_last_error", "crom_create", "crom_destroy", "crom_set_weights",
-            "crom_decode", "crom_step", "crom_step_noalloc", "crom_reconstruct")
+            "crom_decode", "crom_step", "crom_rollout", "crom_step_noalloc", "crom_fom_step", "crom_trainer_create",
+            "crom_trainer_destroy", "crom_trainer_param_count", "crom_trainer_set_params",
+            "crom_trainer_get_params", "crom_trainer_get_grads", "crom_train_step", "crom_encode",
+            "crom_reconstruct")
 
 
 class CromError(RuntimeError):
@@ -67,6 +74,15 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.crom_decode.argtypes = [vp, i, vp, vp, vp, i, u, vp, vp]
     lib.crom_step.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, i, vp, vp, vp, vp, vp, i, i, vp, vp]
     lib.crom_step_noalloc.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, vp, vp, vp, vp, vp, i, i, vp, vp]
+    lib.crom_rollout.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, i, i, vp, vp, vp, vp, vp, i, i, vp, vp]
+    lib.crom_fom_step.argtypes = [i, i, i, i, vp, vp, vp, d, i, vp, vp, vp]
+    lib.crom_trainer_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(crom_decoder_desc), i, i, i, i]
+    lib.crom_trainer_destroy.argtypes = [vp]
+    lib.crom_trainer_param_count.argtypes = [vp, ctypes.POINTER(sz)]
+    for name in ("crom_trainer_set_params", "crom_trainer_get_params", "crom_trainer_get_grads"):
+        getattr(lib, name).argtypes = [vp, vp, sz, i, vp]
+    lib.crom_train_step.argtypes = [vp, vp, vp, vp, ctypes.c_float, vp, vp]
+    lib.crom_encode.argtypes = [vp, i, vp, vp, vp]
     lib.crom_reconstruct.argtypes = [vp, i, i, vp, i, vp, vp, vp]
     for name in EXPORTED:
         if name not in ("crom_version", "crom_last_error"):
@@ -170,6 +186,19 @@ def crom_step(ctx: CromContext, q, alpha, s_off, samples, status, *, dt: float, 
                           _stream(stream)))
 
 
+def crom_rollout(ctx: CromContext, q, alpha, s_off, samples, status, *, n_steps: int, dt: float, gn_iters: int,
+                 max_samples: int, pde: int = CROM_PDE_HEAT, vel=None, precision: int = CROM_PREC_FP32,
+                 stream=None):
+    """n_steps latent steps replayed from a CUDA graph cached in the context."""
+    import torch
+    _need(q, torch.float64, "q"); _need(alpha, torch.float32, "alpha"); _need(s_off, torch.int32, "s_off")
+    _need(samples, torch.float32, "samples"); _need(status, torch.int32, "status"); _need(vel, torch.float32, "vel")
+    desc = crom_step_desc(pde, gn_iters, dt)
+    _check(_LIB.crom_rollout(ctx.handle, ctypes.byref(desc), precision, n_steps, q.shape[0], _ptr(q), _ptr(alpha),
+                             _ptr(vel), _ptr(s_off), _ptr(samples), samples.shape[0], max_samples, _ptr(status),
+                             _stream(stream)))
+
+
 def crom_step_noalloc(ctx: CromContext, q, alpha, s_off, samples, status, *, dt: float, gn_iters: int,
                       max_samples: int, pde: int = CROM_PDE_HEAT, vel=None, stream=None):
     """The FP32 step with its scratch in the library's fixed device array: for
@@ -181,6 +210,80 @@ def crom_step_noalloc(ctx: CromContext, q, alpha, s_off, samples, status, *, dt:
     _check(_LIB.crom_step_noalloc(ctx.handle, ctypes.byref(desc), q.shape[0], _ptr(q), _ptr(alpha), _ptr(vel),
                                   _ptr(s_off), _ptr(samples), samples.shape[0], max_samples, _ptr(status),
                                   _stream(stream)))
+
+
+def crom_fom_step(kind: int, u, tmp, coef, *, dt: float, n_steps: int, ax=None, ay=None, stream=None):
+    """u: [n_batch, nx] (1D) or [n_batch, nx, nx] (2D) float32 CUDA tensor, advanced in place."""
+    import torch
+    for t, name in ((u, "u"), (tmp, "tmp"), (coef, "coef"), (ax, "ax"), (ay, "ay")):
+        _need(t, torch.float32, name)
+    nb, nx = u.shape[0], u.shape[1]
+    ny = 1 if u.dim() == 2 else u.shape[2]
+    _check(_LIB.crom_fom_step(kind, nb, nx, ny, _ptr(coef), _ptr(ax), _ptr(ay), dt, n_steps, _ptr(u), _ptr(tmp),
+                              _stream(stream)))
+
+
+class CromTrainer:
+    """Owns a crom_trainer (encoder + decoder parameters, Adam state, activations)."""
+
+    def __init__(self, m, r, width, hidden, P, B, S, device=0):
+        self.desc = crom_decoder_desc(m, r, width, hidden)
+        self.handle = ctypes.c_void_p()
+        _check(_LIB.crom_trainer_create(ctypes.byref(self.handle), ctypes.byref(self.desc), P, B, S, device))
+        n = ctypes.c_size_t()
+        _check(_LIB.crom_trainer_param_count(self.handle, ctypes.byref(n)))
+        self.n_params = n.value
+        self.B, self.S, self.P = B, S, P
+
+    def _io(self, fn, arr, stream):
+        import numpy as np
+        if hasattr(arr, "is_cuda") and arr.is_cuda:
+            _check(fn(self.handle, _ptr(arr), arr.numel(), 1, _stream(stream)))
+        else:
+            _check(fn(self.handle, arr.ctypes.data_as(ctypes.c_void_p), arr.size, 0, _stream(stream)))
+
+    def set_params(self, params, stream=None):
+        import numpy as np
+        if not (hasattr(params, "is_cuda") and params.is_cuda):
+            params = np.ascontiguousarray(params, dtype=np.float32)
+        self._io(_LIB.crom_trainer_set_params, params, stream)
+
+    def get_params(self, stream=None):
+        import numpy as np
+        out = np.empty(self.n_params, np.float32)
+        self._io(_LIB.crom_trainer_get_params, out, stream)
+        return out
+
+    def get_grads(self, stream=None):
+        import numpy as np
+        out = np.empty(self.n_params, np.float32)
+        self._io(_LIB.crom_trainer_get_grads, out, stream)
+        return out
+
+    def close(self):
+        if self.handle:
+            _LIB.crom_trainer_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def crom_train_step(tr: CromTrainer, snaps, pt_idx, coords, lr: float, loss_out=None, stream=None):
+    import torch
+    _need(snaps, torch.float32, "snaps"); _need(pt_idx, torch.int32, "pt_idx"); _need(coords, torch.float32, "coords")
+    _need(loss_out, torch.float64, "loss_out")
+    _check(_LIB.crom_train_step(tr.handle, _ptr(snaps), _ptr(pt_idx), _ptr(coords), lr, _ptr(loss_out),
+                                _stream(stream)))
+
+
+def crom_encode(tr: CromTrainer, snaps, q_out, stream=None):
+    import torch
+    _need(snaps, torch.float32, "snaps"); _need(q_out, torch.float32, "q_out")
+    _check(_LIB.crom_encode(tr.handle, snaps.shape[0], _ptr(snaps), _ptr(q_out), _stream(stream)))
 
 
 def crom_reconstruct(ctx: CromContext, q, x, out, precision: int = CROM_PREC_FP32, stream=None):

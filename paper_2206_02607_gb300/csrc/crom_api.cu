@@ -138,6 +138,8 @@ int crom_destroy(crom_ctx* ctx) {
     cudaFree(ctx->qbase);
     cudaFree(ctx->order);
     cudaFree(ctx->queue);
+    if (ctx->rollout_exec) cudaGraphExecDestroy(ctx->rollout_exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   }
   delete ctx;
   return CROM_OK;
@@ -281,6 +283,77 @@ int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_in
   return CROM_OK;
 }
 
+int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_steps, int n_inst, double* q,
+                 const float* alpha, const float* vel, const int* s_off, const float* samples, int n_samples,
+                 int max_samples, int* status, crom_stream stream) {
+  if (!ctx || !step) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: null argument");
+  if (n_steps < 0) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: n_steps must be >= 0");
+  if (n_steps == 0 || n_inst == 0) return CROM_OK;
+  // Validate exactly as crom_step does (nothing is launched on failure).
+  if (!ctx->has_weights) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: weights not set");
+  if (n_inst < 0 || n_samples < 0) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: negative size");
+  if (!(step->dt > 0.0) || !isfinite(step->dt)) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: dt must be finite and > 0");
+  if (step->gn_iters < 1 || step->gn_iters > 16) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: gn_iters must be in 1..16");
+  if (step->pde != CROM_PDE_HEAT && step->pde != CROM_PDE_ADVDIFF) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: unknown pde");
+  if (!q || !alpha || !s_off || !status || (n_samples > 0 && !samples))
+    return fail(CROM_ERR_INVALID_ARG, "crom_rollout: null array");
+  if (step->pde == CROM_PDE_ADVDIFF && !vel) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: advection needs vel");
+  if (max_samples < 1) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: max_samples must be >= 1");
+  if (precision == CROM_PREC_BF16X2) {
+    if (!tc_shape_ok(ctx->desc) || !ctx->w.tc_img)
+      return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: BF16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15");
+  } else if (precision != CROM_PREC_FP32) {
+    return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: precision not available for the step");
+  }
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  // The key: every argument that the recorded launches depend on.
+  struct Key {
+    int precision, n_steps, n_inst, n_samples, max_samples, pde, gn_iters;
+    double dt;
+    const void *q, *alpha, *vel, *s_off, *samples, *status, *weights;
+  } key{precision, n_steps, n_inst, n_samples, max_samples, step->pde, step->gn_iters, step->dt,
+        q, alpha, vel, s_off, samples, status, ctx->w.w1};
+  std::vector<unsigned char> kb(sizeof(Key));
+  memcpy(kb.data(), &key, sizeof(Key));
+  cudaError_t e;
+  if (!ctx->rollout_exec || kb != ctx->rollout_key) {
+    if (!ctx->cap_stream) {
+      e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(e, "crom_rollout (stream)");
+    }
+    // Make the captured stream wait for the caller's stream is not needed: the
+    // recording does not execute anything; relaxed mode lets the first-use
+    // scratch growth inside the launch helpers allocate while recording.
+    e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return cuda_fail(e, "crom_rollout (begin capture)");
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < n_steps && le == cudaSuccess; ++k) {
+      le = (precision == CROM_PREC_FP32)
+               ? launch_step_fp32(ctx, step, n_inst, q, alpha, vel, s_off, samples, n_samples, max_samples, status,
+                                  ctx->cap_stream)
+               : launch_step_tc(ctx, step, n_inst, q, alpha, vel, s_off, samples, n_samples, max_samples, status,
+                                ctx->cap_stream);
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (le != cudaSuccess || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(le != cudaSuccess ? le : e, "crom_rollout (record)");
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "crom_rollout (instantiate)");
+    if (ctx->rollout_exec) cudaGraphExecDestroy(ctx->rollout_exec);
+    ctx->rollout_exec = exec;
+    ctx->rollout_key = kb;
+  }
+  e = cudaGraphLaunch(ctx->rollout_exec, s);
+  if (e != cudaSuccess) return cuda_fail(e, "crom_rollout (launch)");
+  return CROM_OK;
+}
+
 int crom_step_noalloc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, double* q, const float* alpha,
                       const float* vel, const int* s_off, const float* samples, int n_samples, int max_samples,
                       int* status, crom_stream stream) {
@@ -309,6 +382,130 @@ int crom_step_noalloc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, dou
                                           std::to_string(noalloc_scratch_capacity()) +
                                           " bytes; use crom_step or a smaller batch");
   if (e != cudaSuccess) return cuda_fail(e, "crom_step_noalloc");
+  return CROM_OK;
+}
+
+int crom_fom_step(int kind, int n_batch, int nx, int ny, const float* coef, const float* ax, const float* ay,
+                  double dt, int n_steps, float* u, float* tmp, crom_stream stream) {
+  if (kind < CROM_FOM_HEAT1D_DIRICHLET || kind > CROM_FOM_ADVDIFF2D_PERIODIC)
+    return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: unknown kind");
+  if (n_batch < 0 || n_batch > 65535 || n_steps < 0) return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: bad batch or step count");
+  if (nx < 3) return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: nx must be >= 3");
+  if (kind == CROM_FOM_HEAT1D_DIRICHLET ? ny != 1 : ny != nx)
+    return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: ny must be 1 (1D) or nx (2D)");
+  if (!(dt > 0.0) || !isfinite(dt)) return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: dt must be finite and > 0");
+  if (n_batch == 0 || n_steps == 0) return CROM_OK;
+  if (!coef || !u || !tmp || u == tmp) return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: null or aliased array");
+  if (kind == CROM_FOM_ADVDIFF2D_PERIODIC && (!ax || !ay))
+    return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: advection needs ax and ay");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(CROM_ERR_CUDA, "crom_fom_step: no CUDA device");
+  cudaError_t e = launch_fom(kind, n_batch, nx, ny, coef, ax, ay, dt, n_steps, u, tmp, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "crom_fom_step");
+  return CROM_OK;
+}
+
+int crom_trainer_create(crom_trainer** out, const crom_decoder_desc* dec, int P, int B, int S, int device) {
+  if (!out || !dec) return fail(CROM_ERR_INVALID_ARG, "crom_trainer_create: null argument");
+  *out = nullptr;
+  const crom_decoder_desc d = *dec;
+  if (d.m < 1 || d.m > 3 || d.r < 1 || d.r > 32 || d.width < 1 || d.width > 1024 || d.hidden < 1 || d.hidden > 8)
+    return fail(CROM_ERR_INVALID_ARG, "crom_trainer_create: bad decoder shape");
+  if (P < 38 || B < 1 || S < 1 || (long long)B * S > (1LL << 26))
+    return fail(CROM_ERR_INVALID_ARG, "crom_trainer_create: need P >= 38 (one convolution of length >= 32), "
+                                      "B, S >= 1, B*S <= 2^26");
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return fail(CROM_ERR_CUDA, "crom_trainer_create: no CUDA device");
+  if (device < 0 || device >= n) return fail(CROM_ERR_INVALID_ARG, "crom_trainer_create: bad device index");
+  crom_trainer* t = new crom_trainer();
+  t->device = device;
+  t->dec = d;
+  t->P = P;
+  t->B = B;
+  t->S = S;
+  t->lens.push_back(P);
+  while ((t->lens.back() - 6) / 4 + 1 >= 32) t->lens.push_back((t->lens.back() - 6) / 4 + 1);
+  DeviceGuard g(device);
+  cudaError_t e = trainer_alloc(t);
+  if (e != cudaSuccess) {
+    trainer_free(t);
+    delete t;
+    return cuda_fail(e, "crom_trainer_create");
+  }
+  *out = t;
+  return CROM_OK;
+}
+
+int crom_trainer_destroy(crom_trainer* tr) {
+  if (!tr) return CROM_OK;
+  {
+    DeviceGuard g(tr->device);
+    cudaDeviceSynchronize();
+    trainer_free(tr);
+  }
+  delete tr;
+  return CROM_OK;
+}
+
+int crom_trainer_param_count(const crom_trainer* tr, size_t* n) {
+  if (!tr || !n) return fail(CROM_ERR_INVALID_ARG, "crom_trainer_param_count: null argument");
+  *n = trainer_param_count(tr);
+  return CROM_OK;
+}
+
+static int trainer_copy(crom_trainer* tr, float* dev_buf, float* other, size_t n, int on_device, bool to_dev,
+                        crom_stream stream, const char* who) {
+  if (!tr || !other) return fail(CROM_ERR_INVALID_ARG, std::string(who) + ": null argument");
+  if (n != trainer_param_count(tr))
+    return fail(CROM_ERR_INVALID_ARG, std::string(who) + ": expected " + std::to_string(trainer_param_count(tr)) +
+                                          " floats");
+  DeviceGuard g(tr->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice
+                                        : (to_dev ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+  cudaError_t e = to_dev ? cudaMemcpyAsync(dev_buf, other, n * 4, kind, s) : cudaMemcpyAsync(other, dev_buf, n * 4, kind, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, who);
+  return CROM_OK;
+}
+
+int crom_trainer_set_params(crom_trainer* tr, const float* params, size_t n, int on_device, crom_stream stream) {
+  int st = trainer_copy(tr, tr ? tr->params : nullptr, const_cast<float*>(params), n, on_device, true, stream,
+                        "crom_trainer_set_params");
+  if (st != CROM_OK) return st;
+  DeviceGuard g(tr->device);
+  cudaError_t e = cudaMemset(tr->am, 0, n * 4);
+  if (e == cudaSuccess) e = cudaMemset(tr->av, 0, n * 4);
+  if (e != cudaSuccess) return cuda_fail(e, "crom_trainer_set_params");
+  tr->step = 0;
+  return CROM_OK;
+}
+
+int crom_trainer_get_params(crom_trainer* tr, float* params, size_t n, int on_device, crom_stream stream) {
+  return trainer_copy(tr, tr ? tr->params : nullptr, params, n, on_device, false, stream, "crom_trainer_get_params");
+}
+
+int crom_trainer_get_grads(crom_trainer* tr, float* grads, size_t n, int on_device, crom_stream stream) {
+  return trainer_copy(tr, tr ? tr->grads : nullptr, grads, n, on_device, false, stream, "crom_trainer_get_grads");
+}
+
+int crom_train_step(crom_trainer* tr, const float* snaps, const int* pt_idx, const float* coords, float lr,
+                    double* loss_out, crom_stream stream) {
+  if (!tr || !snaps || !pt_idx || !coords) return fail(CROM_ERR_INVALID_ARG, "crom_train_step: null argument");
+  if (!(lr >= 0.f) || !isfinite(lr)) return fail(CROM_ERR_INVALID_ARG, "crom_train_step: lr must be finite and >= 0");
+  DeviceGuard g(tr->device);
+  cudaError_t e = trainer_step(tr, snaps, pt_idx, coords, lr, loss_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "crom_train_step");
+  return CROM_OK;
+}
+
+int crom_encode(crom_trainer* tr, int n, const float* snaps, float* q, crom_stream stream) {
+  if (!tr || !snaps || !q) return fail(CROM_ERR_INVALID_ARG, "crom_encode: null argument");
+  if (n < 0 || n > tr->B) return fail(CROM_ERR_INVALID_ARG, "crom_encode: n must be in 0..B");
+  if (n == 0) return CROM_OK;
+  DeviceGuard g(tr->device);
+  cudaError_t e = trainer_encode(tr, n, snaps, q, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "crom_encode");
   return CROM_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/crom.h"
 
@@ -57,11 +58,53 @@ struct crom_ctx {
   int* order = nullptr;
   size_t order_cap = 0;
   int* queue = nullptr;
+  // Cached rollout graph and the arguments it was recorded with.
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t rollout_exec = nullptr;
+  std::vector<unsigned char> rollout_key;
+};
+
+namespace crom {
+struct TrainerLayout {
+  std::vector<long> dec_w, dec_b;  // offsets of W_l, b_l (l = 0..hidden) in the parameter vector
+  std::vector<long> conv;          // offsets of convolution l (w[6], b)
+  long d1w = 0, d1b = 0, d2w = 0, d2b = 0;
+  long total = 0;
+};
+}  // namespace crom
+
+// Training state: FP32 master parameters, gradients, Adam moments, activations.
+struct crom_trainer {
+  int device = 0;
+  crom_decoder_desc dec{};
+  int P = 0, B = 0, S = 0;
+  std::vector<int> lens;  // convolution lengths: P, ..., L_last
+  crom::TrainerLayout lay;
+  float *params = nullptr, *grads = nullptr, *am = nullptr, *av = nullptr;
+  long step = 0;
+  std::vector<float*> conv_z, conv_h;  // per convolution: [B][L_l]
+  float *d1z = nullptr, *d1h = nullptr, *q = nullptr;
+  float *in0 = nullptr, *target = nullptr, *g = nullptr, *dg = nullptr;
+  std::vector<float*> Z, H;  // per hidden layer: [B*S][width]
+  float *delta = nullptr, *delta2 = nullptr, *din = nullptr, *dq = nullptr;
+  float* split = nullptr;  // split-K partial sums of weight gradients
+  float *edh = nullptr, *edx = nullptr, *ed1 = nullptr;
+  double* partial = nullptr;
+  double* loss_dev = nullptr;
+  std::vector<void*> owned;
 };
 
 namespace crom {
 
 void set_error(const std::string& msg);
+
+// Training (train.cu).
+size_t trainer_param_count(const crom_trainer* t);
+cudaError_t trainer_alloc(crom_trainer* t);
+void trainer_free(crom_trainer* t);
+cudaError_t trainer_encode(crom_trainer* t, int nb, const float* snaps, float* q_out, cudaStream_t s);
+cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx, const float* coords, float lr,
+                         double* loss_out, cudaStream_t s);
 
 // Channel configuration of the FP32 forward-mode evaluation.
 enum SecondOrder { kSecondNone = 0, kSecondPerK = 1, kSecondLap = 2 };
@@ -89,6 +132,10 @@ cudaError_t launch_step_fp32_noalloc(const crom_ctx* ctx, const crom_step_desc* 
                                      const float* alpha, const float* vel, const int* s_off,
                                      const float* samples, int n_samples, int max_samples, int* status,
                                      cudaStream_t s, size_t* need_bytes);
+
+// Full-order model stencils (fom.cu).
+cudaError_t launch_fom(int kind, int n_batch, int nx, int ny, const float* coef, const float* ax, const float* ay,
+                       double dt, int n_steps, float* u, float* tmp, cudaStream_t s);
 
 // Tensor-core launches (tc_step.cu, tc_recon.cu).
 cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, double* q,

@@ -119,6 +119,22 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) 
       "r"(__float_as_uint(v[15]))
       : "memory");
 }
+// 32 lanes x 32 bit, 8 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+               "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+               : "memory");
+}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
@@ -163,6 +179,17 @@ __device__ __forceinline__ uint64_t desc_kmajor(uint32_t base, int rows, int kk)
 __device__ __forceinline__ uint64_t desc_mnmajor(uint32_t base, int kk) {
   return smem_desc_sw128(base + (uint32_t)(kk * 2048), 16384, 1024);
 }
+
+// Descriptor of the same layout moved by `bytes` (a multiple of 16): the start
+// address field holds addr >> 4 in 14 bits and shared addresses stay below
+// 256 KB, so the addition never carries out of the field.
+__device__ __forceinline__ uint64_t desc_add(uint64_t d, uint32_t bytes) { return d + (uint64_t)(bytes >> 4); }
+// Byte offset of the 16-wide K slice kk in a K-major SW128 operand with `rows` rows.
+__host__ __device__ constexpr uint32_t kmajor_kslice(int rows, int kk) {
+  return (uint32_t)((kk >> 2) * rows * 128 + (kk & 3) * 32);
+}
+// Byte offset of the 16-wide K slice kk in an MN-major SW128 operand.
+__host__ __device__ constexpr uint32_t mnmajor_kslice(int kk) { return (uint32_t)(kk * 2048); }
 
 // Byte offset of element (k, n) inside an MN-major SW128 operand with 128 k-rows.
 __device__ __forceinline__ uint32_t mn_offset(int k, int n) {

@@ -1,10 +1,11 @@
 // Dense reconstruction g(x_p, q_c) on the tcgen05 tensor cores (value channel only).
 //
 // Persistent kernel, one CTA per SM with the decoder's bf16 hidden matrices in
-// shared memory, two independent groups of 128 threads (one tile of 64 points
+// shared memory, two independent groups of 256 threads (one tile of 64 points
 // each, own operand buffers / TMEM columns / mbarrier / named barrier) so that
-// one group's UMMAs overlap the other's epilogue.  Thread u of a group owns
-// hidden unit u, which is also TMEM lane u.  A tile is 64 points of one code:
+// one group's UMMAs overlap the other's epilogue.  Hidden unit u is TMEM lane u
+// and is served by two threads of the group, each taking 32 of the tile's
+// points.  A tile is 64 points of one code:
 //   layer 1 (K = m + r, too small for UMMA) on CUDA cores: the q part of
 //     W_1 [x; q] + b_1 is hoisted per code; h = ELU(W_1x x + c);
 //   layers 2..L: D[u][n] = sum_k W_l[u][k] H[k][n] by UMMA (M = 128 units,
@@ -28,7 +29,7 @@ namespace {
 using namespace tc;
 
 constexpr int kGroups = 2;
-constexpr int kGT = 128;
+constexpr int kGT = 256;  // two threads per TMEM lane, each half of the tile's points
 constexpr int kThreads = kGroups * kGT;
 constexpr int kTileN = 64;
 constexpr uint32_t kTmemCols = 256;
@@ -114,8 +115,11 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x;
-  const int g = tid / kGT, u = tid % kGT;
-  const uint32_t lane_base = (uint32_t)(u >> 5) * 32;
+  const int g = tid / kGT, gt = tid % kGT;
+  const int lq = (gt >> 5) & 3, half = gt >> 7;
+  const int u = lq * 32 + (gt & 31);           // hidden unit = TMEM lane
+  const int nbeg = half * (kTileN / 2);        // this thread's 32 points of the tile
+  const uint32_t lane_base = (uint32_t)lq * 32;
   const int m = p.m, r = p.r;
   uint8_t* Wimg = sm;
   uint8_t* Hbase = sm + ((p.img_bytes + 1023) & ~1023);
@@ -128,7 +132,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
     mbar_init(&S->bar_w, 1);
     fence_mbar_init();
   }
-  if (u == 0) {
+  if (gt == 0) {
     mbar_init(&G->bar_mma, 1);
     fence_mbar_init();
   }
@@ -136,9 +140,9 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
     tmem_alloc(&S->tmem_base, kTmemCols);
     tmem_relinquish();
   }
-  if (g == 0) {
-    for (int i = u; i < p.n_hidden_mats * kTcWidth; i += kGT) S->bh[i / kTcWidth][i % kTcWidth] = p.bh[i];
-    for (int k = 0; k < m; ++k) S->w1x[k][u] = p.w1[u * (m + r) + k];
+  if (tid < kTcWidth) {
+    for (int l = 0; l < p.n_hidden_mats; ++l) S->bh[l][tid] = p.bh[l * kTcWidth + tid];
+    for (int k = 0; k < m; ++k) S->w1x[k][tid] = p.w1[tid * (m + r) + k];
   }
   tc_fence_before();
   __syncthreads();
@@ -154,8 +158,11 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
   bool ok = __syncthreads_and(mbar_wait(&S->bar_w, 0, kWaitLimit));
   uint32_t phase = 0;
   const uint32_t wbase = smem_u32(Wimg);
-  const uint32_t proj = wbase + (uint32_t)p.n_hidden_mats * kTcLayerBytes;
-  const uint32_t hhi = smem_u32(Hhi), hlo = smem_u32(Hlo);
+  // Base UMMA descriptors; every operand slice is base + a compile-time offset.
+  const uint64_t dW = smem_desc_sw128(wbase, 16, 1024);
+  const uint64_t dP = smem_desc_sw128(wbase + (uint32_t)p.n_hidden_mats * kTcLayerBytes, 16, 1024);
+  const uint64_t dHhi = smem_desc_sw128(smem_u32(Hhi), 16384, 1024);
+  const uint64_t dHlo = smem_desc_sw128(smem_u32(Hlo), 16384, 1024);
   constexpr uint32_t id_layer = idesc_f16(128, kTileN, false, true, true);
   constexpr uint32_t id_out = idesc_f16(128, 16, true, false, true);
   int cur_code = -1;
@@ -172,14 +179,14 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
       c = (float)cc;
       cur_code = code;
     }
-    if (u < kTileN) {
-      const int n = p0 + u;
-      for (int k = 0; k < m; ++k) G->xs[k][u] = (n < p.n_pts) ? p.x[(size_t)n * m + k] : 0.f;
+    if (gt < kTileN) {
+      const int n = p0 + gt;
+      for (int k = 0; k < m; ++k) G->xs[k][gt] = (n < p.n_pts) ? p.x[(size_t)n * m + k] : 0.f;
     }
     group_sync(g);
     // ---- layer 1 on CUDA cores
 #pragma unroll 1
-    for (int n0 = 0; n0 < kTileN; n0 += 16) {
+    for (int n0 = nbeg; n0 < nbeg + kTileN / 2; n0 += 16) {
       float v[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
@@ -195,30 +202,39 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
       fence_proxy_async_smem();
       tc_fence_before();
       group_sync(g);
-      if (u == 0) {
-        tc_fence_after();
-        if (!last) {
-          const uint32_t a = wbase + (uint32_t)l * kTcLayerBytes;
-          for (int part = 0; part <= kSplit; ++part)
-            for (int kk = 0; kk < 8; ++kk)
-              umma_f16(tb + kAccCol, desc_kmajor(a, 128, kk), desc_mnmajor(part ? hlo : hhi, kk), id_layer,
-                       (part | kk) != 0);
-        } else {
-          for (int part = 0; part <= kSplit; ++part)
-            for (int kk = 0; kk < 8; ++kk)
-              umma_f16(tb + kOutCol, desc_mnmajor(part ? hlo : hhi, kk), desc_kmajor(proj, 16, kk), id_out,
-                       (part | kk) != 0);
+      bool done = true;
+      if ((gt >> 5) == 0) {  // one thread issues, the first warp waits, the rest wait at the barrier
+        if (gt == 0) {
+          tc_fence_after();
+          if (!last) {
+            const uint64_t a0 = desc_add(dW, (uint32_t)l * kTcLayerBytes);
+#pragma unroll
+            for (int part = 0; part <= kSplit; ++part)
+#pragma unroll
+              for (int kk = 0; kk < 8; ++kk)
+                umma_f16(tb + kAccCol, desc_add(a0, kmajor_kslice(128, kk)),
+                         desc_add(part ? dHlo : dHhi, mnmajor_kslice(kk)), id_layer, (part | kk) != 0);
+          } else {
+#pragma unroll
+            for (int part = 0; part <= kSplit; ++part)
+#pragma unroll
+              for (int kk = 0; kk < 8; ++kk)
+                umma_f16(tb + kOutCol, desc_add(part ? dHlo : dHhi, mnmajor_kslice(kk)),
+                         desc_add(dP, kmajor_kslice(16, kk)), id_out, (part | kk) != 0);
+          }
+          umma_commit(&G->bar_mma);
         }
-        umma_commit(&G->bar_mma);
+        __syncwarp();
+        done = mbar_wait(&G->bar_mma, phase, kWaitLimit);
       }
-      ok = group_sync_and(g, mbar_wait(&G->bar_mma, phase, kWaitLimit));
+      ok = group_sync_and(g, done);
       phase ^= 1;
       tc_fence_after();
       if (!ok) break;
       if (!last) {
         const float bias = S->bh[l][u];
 #pragma unroll 1
-        for (int n0 = 0; n0 < kTileN; n0 += 16) {
+        for (int n0 = nbeg; n0 < nbeg + kTileN / 2; n0 += 16) {
           float v[16];
           tmem_ld16(taddr(tb, lane_base, kAccCol + n0), v);
           tmem_ld_wait();
@@ -226,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
           for (int i = 0; i < 16; ++i) v[i] = elu(v[i] + bias);
           store_split16<kSplit>(Hhi, Hlo, u, n0, v);
         }
-      } else {
+      } else if (half == 0) {
         float v[16];
         tmem_ld16(taddr(tb, lane_base, kOutCol), v);
         tmem_ld_wait();
@@ -235,7 +251,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
       }
     }
   }
-  if (!ok && u == 0) atomicExch(p.flag, 1);
+  if (!ok && gt == 0) atomicExch(p.flag, 1);
   tc_fence_before();
   __syncthreads();
   if (tid < 32) tmem_dealloc(S->tmem_base, kTmemCols);

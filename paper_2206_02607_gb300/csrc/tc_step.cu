@@ -1,11 +1,13 @@
 // Batched latent step on the tcgen05 tensor cores (crom_step, CROM_PREC_BF16X2).
 //
 // One persistent launch per step, one CTA per SM holding the decoder's bf16
-// hidden matrices in shared memory.  The CTA runs two independent groups of 128
+// hidden matrices in shared memory.  The CTA runs two independent groups of 256
 // threads; each group takes whole instances from a queue ordered by |M_i|
 // (largest first) and has its own operand buffers, TMEM columns, mbarrier and
 // named barrier, so the UMMAs of one group overlap the CUDA-core epilogue of the
-// other.  Inside a group thread u owns hidden unit u = TMEM lane u.
+// other.  Inside a group, hidden unit u is TMEM lane u and is served by two
+// threads (warps w and w + 4 of the group share a lane quadrant), each taking
+// half of the 16 samples of a tile.
 //
 // Per instance, per Gauss-Newton iteration k, per tile of 16 samples
 // (paper §4, Algorithm 3):
@@ -44,9 +46,10 @@ namespace {
 using namespace tc;
 
 constexpr int kGroups = 2;
-constexpr int kGT = 128;                 // threads per group
+constexpr int kGT = 256;                 // threads per group
 constexpr int kThreads = kGroups * kGT;
 constexpr int kS = 16;                   // samples per tile
+constexpr int kHalf = kS / 2;            // samples per thread
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kGroupCols = 256;     // TMEM columns per group
 constexpr uint32_t kAcc = 0;             // accumulator, up to 64 columns
@@ -127,61 +130,76 @@ __device__ __forceinline__ bool group_sync_and(int g, bool pred) {
   return r != 0;
 }
 
-__device__ __forceinline__ void split_store16(uint8_t* Hhi, uint8_t* Hlo, int k, int n0, const float* v) {
-  uint32_t hi[8], lo[8];
+// Eight consecutive columns n0..n0+7 of row k as a bf16 hi/lo pair (one 16-byte
+// chunk in each buffer).
+__device__ __forceinline__ void split_store8(uint8_t* Hhi, uint8_t* Hlo, int k, int n0, const float (&v)[8]) {
+  uint32_t hi[4], lo[4];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
+  for (int j = 0; j < 4; ++j) {
     hi[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
     lo[j] = pack_bf16(v[2 * j] - bf16_lo_f(hi[j]), v[2 * j + 1] - bf16_hi_f(hi[j]));
   }
-  *reinterpret_cast<uint4*>(Hhi + mn_offset(k, n0)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-  *reinterpret_cast<uint4*>(Hhi + mn_offset(k, n0 + 8)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
-  *reinterpret_cast<uint4*>(Hlo + mn_offset(k, n0)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-  *reinterpret_cast<uint4*>(Hlo + mn_offset(k, n0 + 8)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+  const uint32_t off = mn_offset(k, n0);
+  *reinterpret_cast<uint4*>(Hhi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+  *reinterpret_cast<uint4*>(Hlo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
 }
 
-// s(a) - s(a - d) without cancellation: the difference channel carries
-// h(q^(k)) - h(q_n), so the residual g(y, q^(k)) - g(y, q_n) - Delta f keeps its
-// relative accuracy although the two evaluations agree to many digits.
-__device__ __forceinline__ float elu_diff(float a, float d) {
+// e^x - 1: degree-5 Taylor polynomial for |x| < 1/16 (truncation < 1.3e-9
+// relative), the library function otherwise.
+__device__ __forceinline__ float expm1_small(float x) {
+  if (fabsf(x) < 0.0625f)
+    return x * fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f), 0.5f), 1.f);
+  return expm1f(x);
+}
+
+// s(a) - s(a - d) without cancellation, given e = exp(min(a, 0)): the difference
+// channel carries h(q^(k)) - h(q_n), so the residual g(y, q^(k)) - g(y, q_n) - Delta f
+// keeps its relative accuracy although the two evaluations agree to many digits.
+__device__ __forceinline__ float elu_diff(float a, float d, float e) {
   const float b = a - d;
   if (a > 0.f && b > 0.f) return d;
-  if (a <= 0.f && b <= 0.f) return -__expf(a) * expm1f(-d);
+  if (a <= 0.f && b <= 0.f) return -e * expm1_small(-d);
   const float sa = a > 0.f ? a : expm1f(a);
   const float sb = b > 0.f ? b : expm1f(b);
   return sa - sb;
 }
 
-// D(+)= A * B^T over K = 128 with the B operand as hi + lo parts.
-__device__ __forceinline__ void issue_layer(uint32_t d, uint32_t a_base, bool a_mn, uint32_t hhi, uint32_t hlo,
-                                           uint32_t idesc) {
-#pragma unroll 1
-  for (int part = 0; part < 2; ++part) {
-    const uint32_t b_base = part ? hlo : hhi;
-    for (int kk = 0; kk < 8; ++kk) {
-      const uint64_t a = a_mn ? desc_mnmajor(a_base, kk) : desc_kmajor(a_base, 128, kk);
-      umma_f16(d, a, desc_mnmajor(b_base, kk), idesc, (part | kk) != 0);
-    }
-  }
+// D(+)= A * B^T over K = 128 with the B operand as hi + lo parts.  a0: descriptor
+// of A's first K slice; A is K-major (forward, W_l) or MN-major (reverse pass,
+// W_l^T read from the same image); B descriptors are MN-major.
+template <bool kAMN>
+__device__ __forceinline__ void issue_layer(uint32_t d, uint64_t a0, uint64_t bhi, uint64_t blo, uint32_t idesc) {
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk)
+    umma_f16(d, desc_add(a0, kAMN ? mnmajor_kslice(kk) : kmajor_kslice(128, kk)), desc_add(bhi, mnmajor_kslice(kk)),
+             idesc, kk > 0);
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk)
+    umma_f16(d, desc_add(a0, kAMN ? mnmajor_kslice(kk) : kmajor_kslice(128, kk)), desc_add(blo, mnmajor_kslice(kk)),
+             idesc, 1);
 }
-// PRJ[n][j] = sum_u H[u][n] P[j][u] with H as the hi + lo parts.
-__device__ __forceinline__ void issue_proj(uint32_t d, uint32_t hhi, uint32_t hlo, uint32_t proj) {
+// PRJ[n][j] = sum_u H[u][n] P[j][u] with H (MN-major A) as the hi + lo parts.
+__device__ __forceinline__ void issue_proj(uint32_t d, uint64_t ahi, uint64_t alo, uint64_t p0) {
   constexpr uint32_t id = idesc_f16(128, 16, true, false, true);
-#pragma unroll 1
-  for (int part = 0; part < 2; ++part) {
-    const uint32_t a_base = part ? hlo : hhi;
-    for (int kk = 0; kk < 8; ++kk)
-      umma_f16(d, desc_mnmajor(a_base, kk), desc_kmajor(proj, 16, kk), id, (part | kk) != 0);
-  }
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk)
+    umma_f16(d, desc_add(ahi, mnmajor_kslice(kk)), desc_add(p0, kmajor_kslice(16, kk)), id, kk > 0);
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk)
+    umma_f16(d, desc_add(alo, mnmajor_kslice(kk)), desc_add(p0, kmajor_kslice(16, kk)), id, 1);
 }
 
 __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x;
-  const int g = tid / kGT, u = tid % kGT;
-  const int lwarp = u >> 5;              // lane quadrant of this warp
-  const uint32_t lane_base = (uint32_t)lwarp * 32;
+  const int g = tid / kGT, gt = tid % kGT;
+  const int gw = gt >> 5;                 // warp within the group
+  const int lq = gw & 3;                  // TMEM lane quadrant of this warp
+  const int half = gw >> 2;               // which 8 samples of a tile
+  const int u = lq * 32 + (gt & 31);      // hidden unit = TMEM lane
+  const int s0 = half * kHalf;
+  const uint32_t lane_base = (uint32_t)lq * 32;
   const int m = p.m, r = p.r, L = p.L;
 
   uint8_t* Wimg = sm;
@@ -195,7 +213,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
     mbar_init(&S->bar_w, 1);
     fence_mbar_init();
   }
-  if (u == 0) {
+  if (gt == 0) {
     mbar_init(&G->bar_mma, 1);
     fence_mbar_init();
   }
@@ -203,11 +221,11 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
     tmem_alloc(&S->tmem_base, kTmemCols);
     tmem_relinquish();
   }
-  if (g == 0) {
-    for (int l = 0; l < L - 1; ++l) S->bh[l][u] = p.bh[l * kTcWidth + u];
-    for (int k = 0; k < m; ++k) S->w1x[k][u] = p.w1[u * (m + r) + k];
-    for (int j = 0; j < r; ++j) S->w1q[j][u] = p.w1[u * (m + r) + m + j];
-    S->wout[u] = p.wout[u];
+  if (tid < kTcWidth) {
+    for (int l = 0; l < L - 1; ++l) S->bh[l][tid] = p.bh[l * kTcWidth + tid];
+    for (int k = 0; k < m; ++k) S->w1x[k][tid] = p.w1[tid * (m + r) + k];
+    for (int j = 0; j < r; ++j) S->w1q[j][tid] = p.w1[tid * (m + r) + m + j];
+    S->wout[tid] = p.wout[tid];
   }
   tc_fence_before();
   __syncthreads();
@@ -221,34 +239,45 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
   bool ok = __syncthreads_and(mbar_wait(&S->bar_w, 0, kWaitLimit));
   uint32_t phase = 0;
   const uint32_t wbase = smem_u32(Wimg);
-  const uint32_t proj = wbase + (uint32_t)(L - 1) * kTcLayerBytes;
-  const uint32_t hhi = smem_u32(Hhi), hlo = smem_u32(Hlo);
+  // Base UMMA descriptors; every operand slice is base + a compile-time offset.
+  const uint64_t dW_k = smem_desc_sw128(wbase, 16, 1024);       // W_l as K-major A
+  const uint64_t dW_mn = smem_desc_sw128(wbase, 16384, 1024);   // W_l^T as MN-major A
+  const uint64_t dP = smem_desc_sw128(wbase + (uint32_t)(L - 1) * kTcLayerBytes, 16, 1024);
+  const uint64_t dHhi = smem_desc_sw128(smem_u32(Hhi), 16384, 1024);
+  const uint64_t dHlo = smem_desc_sw128(smem_u32(Hlo), 16384, 1024);
   const int ntri = r * (r + 1) / 2;
-  const int n_entries = ntri + r;
-  // FP64 normal-equation entry owned by this thread (n_entries <= 135 for r <= 15)
+  const int n_entries = ntri + r;  // <= 135 < kGT
+  // FP64 normal-equation entry owned by this thread
   int ea = -1, eb = -1;
-  if (u < ntri) {
-    int a = 0, rem = u;
+  if (gt < ntri) {
+    int a = 0, rem = gt;
     while (rem >= r - a) { rem -= r - a; ++a; }
     ea = a; eb = a + rem;
-  } else if (u < n_entries) {
-    ea = u - ntri; eb = -2;
+  } else if (gt < n_entries) {
+    ea = gt - ntri; eb = -2;
   }
-  const bool extra = (u + kGT < n_entries);  // second entry (r >= 15 only)
-  int ea2 = -1;
-  if (extra) ea2 = u + kGT - ntri;
+  const float wx0 = S->w1x[0][u], wx1 = (m > 1) ? S->w1x[1][u] : 0.f;
+  const float wsq = wx0 * wx0 + wx1 * wx1;
+  const float wo = S->wout[u];
 
-  // Issue + wait helper for one UMMA stage of this group.
+  // Issue + wait of one UMMA stage of this group: one thread issues, the first
+  // warp waits on the mbarrier, the rest wait at the group barrier; every thread
+  // returns the same value.
   auto stage = [&](auto issue) -> bool {
     fence_proxy_async_smem();
     tc_fence_before();
     group_sync(g);
-    if (u == 0) {
-      tc_fence_after();
-      issue();
-      umma_commit(&G->bar_mma);
+    bool done = true;
+    if (gw == 0) {
+      if (gt == 0) {
+        tc_fence_after();
+        issue();
+        umma_commit(&G->bar_mma);
+      }
+      __syncwarp();
+      done = mbar_wait(&G->bar_mma, phase, kWaitLimit);
     }
-    const bool done = group_sync_and(g, mbar_wait(&G->bar_mma, phase, kWaitLimit));
+    done = group_sync_and(g, done);
     phase ^= 1;
     tc_fence_after();
     return done;
@@ -256,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
 
   while (ok) {
     group_sync(g);  // everyone is done with the previous instance's group state
-    if (u == 0) G->s_idx = atomicAdd(&p.queue[0], 1);
+    if (gt == 0) G->s_idx = atomicAdd(&p.queue[0], 1);
     group_sync(g);
     const int idx = G->s_idx;
     if (idx >= p.n_inst) break;
@@ -264,15 +293,15 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
     const int o0 = p.off[inst];
     const int M = p.off[inst + 1] - o0;
     if (M < r || M > p.max_samples) {
-      if (u == 0) p.status[inst] = CROM_ERR_INVALID_ARG;
+      if (gt == 0) p.status[inst] = CROM_ERR_INVALID_ARG;
       continue;
     }
-    if (u < r) {
-      const double v = p.q[(size_t)inst * r + u];
-      G->qn[u] = v;
-      G->qcur[u] = v;
+    if (gt < r) {
+      const double v = p.q[(size_t)inst * r + gt];
+      G->qn[gt] = v;
+      G->qcur[gt] = v;
     }
-    if (u == 0) G->s_status = CROM_OK;
+    if (gt == 0) G->s_status = CROM_OK;
     const float alpha = p.alpha[inst];
     group_sync(g);
     const int ntiles = (M + kS - 1) / kS;
@@ -281,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
       const bool first = (it == 0);
       const int nch = first ? 2 + m : 2;  // iteration 0: v, dx_1..dx_m, Lap; later: v(q^(k)), diff
       const int N = nch * kS;
-      {
+      if (half == 0) {
         double c = (double)p.b1[u], dz = 0.0;
         for (int j = 0; j < r; ++j) {
           c += (double)S->w1q[j][u] * G->qcur[j];
@@ -290,24 +319,22 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
         G->c1[u] = (float)c;
         G->dz1[u] = (float)dz;
       }
-      double acc = 0.0, acc2 = 0.0;
+      double acc = 0.0;
       for (int t = 0; t < ntiles && ok; ++t) {
         const int ns = min(kS, M - t * kS);
-        if (u < kS) {
-          const int s = u < ns ? u : 0;
-          for (int k = 0; k < m; ++k) G->xs[k][u] = p.x[(size_t)(o0 + t * kS + s) * m + k];
+        if (gt < kS) {
+          const int s = gt < ns ? gt : 0;
+          for (int k = 0; k < m; ++k) G->xs[k][gt] = p.x[(size_t)(o0 + t * kS + s) * m + k];
         }
         group_sync(g);
         // ---------------- layer 1 (CUDA cores)
         {
           const float c = G->c1[u], dz = G->dz1[u];
-          const float wx0 = S->w1x[0][u], wx1 = (m > 1) ? S->w1x[1][u] : 0.f;
-          const float wsq = wx0 * wx0 + wx1 * wx1;
-          float v[4][kS], sg[kS];
+          float v[4][kHalf], sg[kHalf];
 #pragma unroll
-          for (int i = 0; i < kS; ++i) {
-            float z = fmaf(wx0, G->xs[0][i], c);
-            if (m > 1) z = fmaf(wx1, G->xs[1][i], z);
+          for (int i = 0; i < kHalf; ++i) {
+            float z = fmaf(wx0, G->xs[0][s0 + i], c);
+            if (m > 1) z = fmaf(wx1, G->xs[1][s0 + i], z);
             const float e = __expf(fminf(z, 0.f));
             const bool pos = z > 0.f;
             const float s1 = pos ? 1.f : e, s2 = pos ? 0.f : e;
@@ -322,28 +349,30 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
                 v[2][i] = s2 * wsq;
               }
             } else {
-              v[1][i] = elu_diff(z, dz);
+              v[1][i] = elu_diff(z, dz, e);
             }
           }
-          tmem_st16(taddr(tb, lane_base, kSig), sg);
+          tmem_st8(taddr(tb, lane_base, kSig + s0), sg);
 #pragma unroll
           for (int ch = 0; ch < 4; ++ch)
-            if (ch < nch) split_store16(Hhi, Hlo, u, ch * kS, v[ch]);
+            if (ch < nch) split_store8(Hhi, Hlo, u, ch * kS + s0, v[ch]);
           tmem_st_wait();
         }
         // ---------------- hidden layers 2..L (tensor cores)
         const uint32_t id_fwd = idesc_f16(128, N, false, true, true);
         for (int l = 0; l < L - 1 && ok; ++l) {
-          ok = stage([&] { issue_layer(tb + kAcc, wbase + (uint32_t)l * kTcLayerBytes, false, hhi, hlo, id_fwd); });
+          ok = stage([&] {
+            issue_layer<false>(tb + kAcc, desc_add(dW_k, (uint32_t)l * kTcLayerBytes), dHhi, dHlo, id_fwd);
+          });
           if (!ok) break;
           const float bias = S->bh[l][u];
-          float v[4][kS], sg[kS];
+          float v[4][kHalf], sg[kHalf];
 #pragma unroll
           for (int ch = 0; ch < 4; ++ch)
-            if (ch < nch) tmem_ld16(taddr(tb, lane_base, kAcc + ch * kS), v[ch]);
+            if (ch < nch) tmem_ld8(taddr(tb, lane_base, kAcc + ch * kS + s0), v[ch]);
           tmem_ld_wait();
 #pragma unroll
-          for (int i = 0; i < kS; ++i) {
+          for (int i = 0; i < kHalf; ++i) {
             const float z = v[0][i] + bias;
             const float e = __expf(fminf(z, 0.f));
             const bool pos = z > 0.f;
@@ -355,90 +384,91 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
                 const float a = v[1][i], b = v[2][i];
                 v[1][i] = s1 * a;
                 v[2][i] = s1 * b;
-                v[3][i] = fmaf(s2, a * a + b * b, s1 * v[3][i]);
+                v[3][i] = fmaf(s2, fmaf(a, a, b * b), s1 * v[3][i]);
               } else {
                 const float a = v[1][i];
                 v[1][i] = s1 * a;
                 v[2][i] = fmaf(s2, a * a, s1 * v[2][i]);
               }
             } else {
-              v[1][i] = elu_diff(z, v[1][i]);
+              v[1][i] = elu_diff(z, v[1][i], e);
             }
           }
-          tmem_st16(taddr(tb, lane_base, kSig + (l + 1) * kS), sg);
+          tmem_st8(taddr(tb, lane_base, kSig + (l + 1) * kS + s0), sg);
 #pragma unroll
           for (int ch = 0; ch < 4; ++ch)
-            if (ch < nch) split_store16(Hhi, Hlo, u, ch * kS, v[ch]);
+            if (ch < nch) split_store8(Hhi, Hlo, u, ch * kS + s0, v[ch]);
           tmem_st_wait();
         }
         if (!ok) break;
         // ---------------- output layer: PRJ[n][0] = w_out . h_L[:, n]
-        ok = stage([&] { issue_proj(tb + kPrj, hhi, hlo, proj); });
+        ok = stage([&] { issue_proj(tb + kPrj, dHhi, dHlo, dP); });
         if (!ok) break;
-        {
-          float v[16];
-          tmem_ld16(taddr(tb, lane_base, kPrj), v);
+        if (half == 0) {
+          float v[8];
+          tmem_ld8(taddr(tb, lane_base, kPrj), v);
           tmem_ld_wait();
           if (u < N) G->gout[u / kS][u % kS] = v[0];
         }
         group_sync(g);
         // ---------------- Step 2 and the residual rho_j
-        if (u < kS) {
+        if (gt < kS) {
           float rho = 0.f;
-          if (u < ns) {
-            const int j = o0 + t * kS + u;
+          if (gt < ns) {
+            const int j = o0 + t * kS + gt;
             if (first) {
-              const float lap = G->gout[m + 1][u];
+              const float lap = G->gout[m + 1][gt];
               double df;
               if (p.pde == CROM_PDE_HEAT) {
                 df = p.dt * (double)alpha * (double)lap;
               } else {
                 double adv = 0.0;
-                for (int k = 0; k < m; ++k) adv += (double)p.vel[(size_t)j * m + k] * (double)G->gout[1 + k][u];
+                for (int k = 0; k < m; ++k) adv += (double)p.vel[(size_t)j * m + k] * (double)G->gout[1 + k][gt];
                 df = p.dt * (-adv + (double)alpha * (double)lap);
               }
               p.df[j] = df;
               rho = (float)(-df);
             } else {
-              rho = (float)((double)G->gout[1][u] - p.df[j]);
+              rho = (float)((double)G->gout[1][gt] - p.df[j]);
             }
           }
-          G->rho[u] = rho;
+          G->rho[gt] = rho;
         }
         // ---------------- reverse pass for dg/dq at q^(k)
         {
-          float sg[kS];
-          tmem_ld16(taddr(tb, lane_base, kSig + (L - 1) * kS), sg);
+          float sg[kHalf];
+          tmem_ld8(taddr(tb, lane_base, kSig + (L - 1) * kS + s0), sg);
           tmem_ld_wait();
-          const float w = S->wout[u];
 #pragma unroll
-          for (int i = 0; i < kS; ++i) sg[i] *= w;
-          split_store16(Hhi, Hlo, u, 0, sg);  // delta_L
+          for (int i = 0; i < kHalf; ++i) sg[i] *= wo;
+          split_store8(Hhi, Hlo, u, s0, sg);  // delta_L
         }
         constexpr uint32_t id_bwd = idesc_f16(128, kS, true, true, true);
         for (int l = L - 2; l >= 0 && ok; --l) {
           // accumulator = W_{l+2}^T delta_{l+2}; times s'(z_{l+1}) gives delta_{l+1}
-          ok = stage([&] { issue_layer(tb + kAcc, wbase + (uint32_t)l * kTcLayerBytes, true, hhi, hlo, id_bwd); });
+          ok = stage([&] {
+            issue_layer<true>(tb + kAcc, desc_add(dW_mn, (uint32_t)l * kTcLayerBytes), dHhi, dHlo, id_bwd);
+          });
           if (!ok) break;
-          float v[kS], sg[kS];
-          tmem_ld16(taddr(tb, lane_base, kAcc), v);
-          tmem_ld16(taddr(tb, lane_base, kSig + l * kS), sg);
+          float v[kHalf], sg[kHalf];
+          tmem_ld8(taddr(tb, lane_base, kAcc + s0), v);
+          tmem_ld8(taddr(tb, lane_base, kSig + l * kS + s0), sg);
           tmem_ld_wait();
 #pragma unroll
-          for (int i = 0; i < kS; ++i) v[i] *= sg[i];
-          split_store16(Hhi, Hlo, u, 0, v);
+          for (int i = 0; i < kHalf; ++i) v[i] *= sg[i];
+          split_store8(Hhi, Hlo, u, s0, v);
         }
         if (!ok) break;
         // J[s][j] = sum_u W_1q[u][j] delta_1[u][s]
-        ok = stage([&] { issue_proj(tb + kPrj, hhi, hlo, proj); });
+        ok = stage([&] { issue_proj(tb + kPrj, dHhi, dHlo, dP); });
         if (!ok) break;
-        if (lwarp == 0) {
+        if (gw == 0) {
           float v[16];
           tmem_ld16(taddr(tb, 0, kPrj), v);
           tmem_ld_wait();
-          if (u < kS) {
+          if (gt < kS) {
 #pragma unroll
-            for (int j = 0; j < 15; ++j) G->jt[u][j] = v[j + 1];
+            for (int j = 0; j < 15; ++j) G->jt[gt][j] = v[j + 1];
           }
         }
         group_sync(g);
@@ -452,11 +482,6 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
           }
           acc += s;
         }
-        if (extra) {
-          double s = 0.0;
-          for (int i = 0; i < ns; ++i) s = fma((double)G->jt[i][ea2], (double)G->rho[i], s);
-          acc2 += s;
-        }
       }  // tiles
       if (!ok) break;
       const int R = r + 1;
@@ -468,9 +493,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
           G->amat[ea * R + r] = -acc;
         }
       }
-      if (extra) G->amat[ea2 * R + r] = -acc2;
       group_sync(g);
-      if (u == 0) {
+      if (gt == 0) {
         double* A = G->amat;
         int st = CROM_OK;
         double dmax = 0.0;
@@ -511,10 +535,10 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
       if (G->s_status != CROM_OK) break;
     }  // GN iterations
     if (!ok) break;
-    if (u < r) p.q[(size_t)inst * r + u] = G->qcur[u];
-    if (u == 0) p.status[inst] = G->s_status;
+    if (gt < r) p.q[(size_t)inst * r + gt] = G->qcur[gt];
+    if (gt == 0) p.status[inst] = G->s_status;
   }
-  if (!ok && u == 0) atomicExch(&p.queue[1], 1);
+  if (!ok && gt == 0) atomicExch(&p.queue[1], 1);
   tc_fence_before();
   __syncthreads();
   if (tid < 32) tmem_dealloc(S->tmem_base, kTmemCols);

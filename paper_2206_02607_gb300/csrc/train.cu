@@ -1,0 +1,455 @@
+// One training step of the CROM manifold (paper §3, Eq. loss; App. D): strided
+// 1D-convolution encoder + MLP decoder, MSE over sampled points, hand-written
+// reverse pass and Adam, all in FP32 on CUDA cores with FP32 master weights.
+//
+// Encoder (App. D): convolutions of kernel 6, stride 4, one channel, no padding,
+// ELU after each, repeated while the output length stays >= 32; then a dense
+// layer to 32 (ELU) and a linear layer to r.  Decoder: g(x, q) with the layer
+// sizes of the crom_decoder_desc.  Loss: mean over the B x S sampled points of
+// (g(x_j, e(f_b)) - f_b(x_j))^2.  Adam with beta1 = 0.9, beta2 = 0.999, eps = 1e-8.
+//
+// Parameter vector (FP32, also the layout of crom_trainer_get/set_params):
+// decoder layers as in crom_set_weights (W row-major, then b), then for each
+// convolution w[6], b, then the dense layers (W [32][L_last], b[32]),
+// (W [r][32], b[r]).
+//
+// The dense contractions go through one tiled FP32 GEMM with strided operands
+// and fused epilogues (bias + ELU, multiply by s'(z)); weight gradients reduce
+// over the B*S points with a fixed split along K and a second pass that adds
+// the splits in order, so a step is deterministic.
+#include <math.h>
+
+#include <vector>
+
+#include "crom_internal.h"
+
+namespace crom {
+namespace {
+
+constexpr int kTile = 64;
+constexpr int kTK = 16;
+constexpr int kSplitK = 32;
+
+__device__ __forceinline__ float elu_f(float z) { return z > 0.f ? z : expm1f(z); }
+__device__ __forceinline__ float elu_d(float z) { return z > 0.f ? 1.f : expf(z); }
+
+enum Epi { kEpiStore = 0, kEpiBiasElu = 1, kEpiTimesEluD = 2 };
+
+// C[i][j] = sum_k A(i, k) B(k, j), A(i, k) = A[i*sai + k*sak], B(k, j) = B[k*sbk + j*sbj].
+// Epilogues: kEpiStore (C row-major, ldc); kEpiBiasElu (Z = C + bias[j] stored in C,
+// ELU(Z) stored in H); kEpiTimesEluD (C *= s'(Zp[i][j])).  blockIdx.z splits K into
+// gridDim.z contiguous ranges writing to C + z * split_stride (kEpiStore only).
+__global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const float* __restrict__ A, long sai,
+                                                   long sak, const float* __restrict__ B, long sbk, long sbj,
+                                                   float* __restrict__ C, long ldc, long split_stride, int epi,
+                                                   const float* __restrict__ bias, float* __restrict__ H,
+                                                   const float* __restrict__ Zp) {
+  __shared__ float As[kTK][kTile + 4];
+  __shared__ float Bs[kTK][kTile + 4];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int i0 = blockIdx.y * kTile, j0 = blockIdx.x * kTile;
+  const int splits = gridDim.z;
+  const int kchunk = ((K + splits - 1) / splits + kTK - 1) / kTK * kTK;
+  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+  float acc[4][4] = {};
+  for (int k0 = kbeg; k0 < kend; k0 += kTK) {
+    for (int e = threadIdx.x; e < kTK * kTile; e += 256) {
+      const int kk = e / kTile, ii = e % kTile;
+      const int k = k0 + kk;
+      As[kk][ii] = (i0 + ii < M && k < kend) ? A[(long)(i0 + ii) * sai + (long)k * sak] : 0.f;
+      Bs[kk][ii] = (j0 + ii < N && k < kend) ? B[(long)k * sbk + (long)(j0 + ii) * sbj] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kTK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        a[t] = As[kk][ty + 16 * t];
+        b[t] = Bs[kk][tx + 16 * t];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+  float* Cz = C + (long)blockIdx.z * split_stride;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int i = i0 + ty + 16 * p;
+    if (i >= M) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + tx + 16 * q;
+      if (j >= N) continue;
+      float v = acc[p][q];
+      const long o = (long)i * ldc + j;
+      if (epi == kEpiBiasElu) {
+        v += bias[j];
+        Cz[o] = v;
+        H[o] = elu_f(v);
+      } else if (epi == kEpiTimesEluD) {
+        Cz[o] = v * elu_d(Zp[o]);
+      } else {
+        Cz[o] = v;
+      }
+    }
+  }
+}
+
+// out[e] = sum_s parts[s * stride + e] (in split order), then optionally out[e] = val.
+__global__ void sum_splits_kernel(const float* parts, int splits, long stride, long n, float* out) {
+  const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  float s = 0.f;
+  for (int k = 0; k < splits; ++k) s += parts[k * stride + e];
+  out[e] = s;
+}
+
+// Column sums of X [rows][cols] in fixed order: out[c] = sum_r X[r][c] (one block per column).
+__global__ void colsum_kernel(const float* X, long rows, int cols, float* out) {
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (long r = threadIdx.x; r < rows; r += blockDim.x) s += (double)X[r * cols + c];
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = (float)red[0];
+}
+
+// Strided convolution y[b][i] = bias + sum_k w[k] x[b][4i + k]; z stored, ELU(z) stored.
+__global__ void conv_fwd_kernel(const float* x, int Lin, int Lout, int B, const float* w, float* z, float* h) {
+  const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e >= (long)B * Lout) return;
+  const int b = (int)(e / Lout), i = (int)(e % Lout);
+  const float* xb = x + (long)b * Lin + 4 * i;
+  float s = w[6];
+  for (int k = 0; k < 6; ++k) s = fmaf(w[k], xb[k], s);
+  z[e] = s;
+  h[e] = elu_f(s);
+}
+
+// Backward of one convolution: dz = dh * s'(z) (in place into dz), input gradient
+// dx[b][j] = sum over i with 0 <= j - 4i < 6 of w[j - 4i] dz[b][i].
+__global__ void conv_dz_kernel(const float* dh, const float* z, long n, float* dz) {
+  const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e < n) dz[e] = dh[e] * elu_d(z[e]);
+}
+__global__ void conv_dx_kernel(const float* dz, int Lin, int Lout, int B, const float* w, float* dx) {
+  const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e >= (long)B * Lin) return;
+  const int b = (int)(e / Lin), j = (int)(e % Lin);
+  float s = 0.f;
+  int ihi = j / 4;
+  if (ihi > Lout - 1) ihi = Lout - 1;
+  for (int i = ihi; i >= 0 && j - 4 * i < 6; --i) s = fmaf(w[j - 4 * i], dz[(long)b * Lout + i], s);
+  dx[e] = s;
+}
+// Parameter gradients of one convolution: gw[k] = sum_{b,i} dz[b][i] x[b][4i+k], gb = sum dz.
+__global__ void conv_grad_kernel(const float* dz, const float* x, int Lin, int Lout, int B, float* gw) {
+  const int k = blockIdx.x;  // 0..6 (6 = bias)
+  double s = 0.0;
+  for (long e = threadIdx.x; e < (long)B * Lout; e += blockDim.x) {
+    const int b = (int)(e / Lout), i = (int)(e % Lout);
+    s += (double)dz[e] * (k < 6 ? (double)x[(long)b * Lin + 4 * i + k] : 1.0);
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) gw[k] = (float)red[0];
+}
+
+// Decoder input rows [x_j ; q_b] for the B*S sampled points, and the targets.
+__global__ void gather_kernel(const float* snaps, const int* pt_idx, const float* coords, const float* q, int B,
+                              int S, int P, int m, int r, float* in, float* target) {
+  const long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (n >= (long)B * S) return;
+  const int b = (int)(n / S);
+  const int node = pt_idx[n];
+  const int ld = m + r;
+  for (int k = 0; k < m; ++k) in[n * ld + k] = coords[(long)node * m + k];
+  for (int j = 0; j < r; ++j) in[n * ld + m + j] = q[(long)b * r + j];
+  target[n] = snaps[(long)b * P + node];
+}
+
+// Output layer g = w_out . h + b_out, residual and dL/dg = 2 (g - t) / N; per-block
+// partial sums of the squared residual (FP64).
+__global__ void output_loss_kernel(const float* H, int w, long N, const float* wout, const float* bout,
+                                   const float* target, float* dg, double* partial) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const long n = blockIdx.x * 8L + warp;
+  double sq = 0.0;
+  if (n < N) {
+    float s = 0.f;
+    for (int u = lane; u < w; u += 32) s = fmaf(wout[u], H[n * w + u], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float res = s + bout[0] - target[n];
+    if (lane == 0) {
+      dg[n] = 2.f * res / (float)N;
+      sq = (double)res * (double)res;
+    }
+  }
+  __shared__ double red[8];
+  if (lane == 0) red[warp] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < 8; ++i) s += red[i];
+    partial[blockIdx.x] = s;
+  }
+}
+__global__ void loss_final_kernel(const double* partial, int n, long N, double* loss) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += partial[i];
+    *loss = s / (double)N;
+  }
+}
+
+// delta_L[n][u] = dg[n] w_out[u] s'(z_L[n][u]); output-layer gradients.
+__global__ void out_delta_kernel(const float* dg, const float* wout, const float* Z, int w, long N, float* delta) {
+  const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e >= N * w) return;
+  const long n = e / w;
+  const int u = (int)(e % w);
+  delta[e] = dg[n] * wout[u] * elu_d(Z[e]);
+}
+
+// dq[b][j] = sum over the S points of snapshot b of din[n][m + j]  (fixed order).
+__global__ void dq_kernel(const float* din, int B, int S, int m, int r, float* dq) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B * r) return;
+  const int b = e / r, j = e % r;
+  float s = 0.f;
+  for (int i = 0; i < S; ++i) s += din[((long)b * S + i) * (m + r) + m + j];
+  dq[e] = s;
+}
+
+__global__ void adam_kernel(float* p, const float* g, float* m, float* v, long n, float lr, float c1, float c2) {
+  const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const float gi = g[e];
+  const float mi = 0.9f * m[e] + 0.1f * gi;
+  const float vi = 0.999f * v[e] + 0.001f * gi * gi;
+  m[e] = mi;
+  v[e] = vi;
+  p[e] -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+}
+
+inline unsigned blocks(long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+size_t trainer_param_count(const crom_trainer* t) { return (size_t)t->lay.total; }
+
+cudaError_t trainer_alloc(crom_trainer* t) {
+  auto A = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes > 0 ? bytes : 16) != cudaSuccess) return nullptr;
+    t->owned.push_back(p);
+    return p;
+  };
+  const int m = t->dec.m, r = t->dec.r, w = t->dec.width, L = t->dec.hidden;
+  const long N = (long)t->B * t->S;
+  // parameter layout
+  TrainerLayout& lay = t->lay;
+  long o = 0;
+  std::vector<int> dims = {m + r};
+  for (int l = 0; l < L; ++l) dims.push_back(w);
+  dims.push_back(1);
+  for (int l = 0; l + 1 < (int)dims.size(); ++l) {
+    lay.dec_w.push_back(o);
+    o += (long)dims[l + 1] * dims[l];
+    lay.dec_b.push_back(o);
+    o += dims[l + 1];
+  }
+  for (size_t c = 1; c < t->lens.size(); ++c) {
+    lay.conv.push_back(o);
+    o += 7;
+  }
+  const int Llast = t->lens.back();
+  lay.d1w = o; o += 32L * Llast;
+  lay.d1b = o; o += 32;
+  lay.d2w = o; o += (long)r * 32;
+  lay.d2b = o; o += r;
+  lay.total = o;
+  t->params = (float*)A(o * 4);
+  t->grads = (float*)A(o * 4);
+  t->am = (float*)A(o * 4);
+  t->av = (float*)A(o * 4);
+  for (size_t c = 1; c < t->lens.size(); ++c) {
+    t->conv_z.push_back((float*)A((size_t)t->B * t->lens[c] * 4));
+    t->conv_h.push_back((float*)A((size_t)t->B * t->lens[c] * 4));
+  }
+  t->d1z = (float*)A((size_t)t->B * 32 * 4);
+  t->d1h = (float*)A((size_t)t->B * 32 * 4);
+  t->q = (float*)A((size_t)t->B * r * 4);
+  t->in0 = (float*)A((size_t)N * (m + r) * 4);
+  t->target = (float*)A((size_t)N * 4);
+  t->g = (float*)A((size_t)N * 4);
+  t->dg = (float*)A((size_t)N * 4);
+  for (int l = 0; l < L; ++l) {
+    t->Z.push_back((float*)A((size_t)N * w * 4));
+    t->H.push_back((float*)A((size_t)N * w * 4));
+  }
+  t->delta = (float*)A((size_t)N * w * 4);
+  t->delta2 = (float*)A((size_t)N * w * 4);
+  t->din = (float*)A((size_t)N * (m + r) * 4);
+  t->dq = (float*)A((size_t)t->B * r * 4);
+  t->split = (float*)A((size_t)kSplitK * w * std::max(w, m + r) * 4);
+  t->edh = (float*)A((size_t)t->B * t->lens[0] * 4);
+  t->edx = (float*)A((size_t)t->B * t->lens[0] * 4);
+  t->ed1 = (float*)A((size_t)t->B * 32 * 4);
+  t->partial = (double*)A((size_t)blocks(N, 8) * 8);
+  t->loss_dev = (double*)A(8);
+  for (void* p : t->owned)
+    if (!p) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMemset(t->am, 0, o * 4);
+  if (e == cudaSuccess) e = cudaMemset(t->av, 0, o * 4);
+  return e;
+}
+
+void trainer_free(crom_trainer* t) {
+  for (void* p : t->owned) cudaFree(p);
+  t->owned.clear();
+}
+
+// C = A * B (strided operands) with an epilogue; K split over kSplitK partials when requested.
+static cudaError_t gemm(cudaStream_t s, int M, int N, int K, const float* A, long sai, long sak, const float* B,
+                        long sbk, long sbj, float* C, long ldc, int epi, const float* bias, float* H,
+                        const float* Zp, float* split = nullptr) {
+  dim3 grid(blocks(N, kTile), blocks(M, kTile), split ? kSplitK : 1);
+  if (split) {
+    gemm_kernel<<<grid, 256, 0, s>>>(M, N, K, A, sai, sak, B, sbk, sbj, split, ldc, (long)M * ldc, kEpiStore,
+                                     nullptr, nullptr, nullptr);
+    sum_splits_kernel<<<blocks((long)M * ldc, 256), 256, 0, s>>>(split, kSplitK, (long)M * ldc, (long)M * ldc, C);
+  } else {
+    gemm_kernel<<<grid, 256, 0, s>>>(M, N, K, A, sai, sak, B, sbk, sbj, C, ldc, 0, epi, bias, H, Zp);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t trainer_encode(crom_trainer* t, int nb, const float* snaps, float* q_out, cudaStream_t s) {
+  // nb <= B; forward through the encoder only
+  const int r = t->dec.r;
+  const float* x = snaps;
+  for (size_t c = 1; c < t->lens.size(); ++c) {
+    const int Lin = t->lens[c - 1], Lout = t->lens[c];
+    conv_fwd_kernel<<<blocks((long)nb * Lout, 256), 256, 0, s>>>(x, Lin, Lout, nb, t->params + t->lay.conv[c - 1],
+                                                                t->conv_z[c - 1], t->conv_h[c - 1]);
+    x = t->conv_h[c - 1];
+  }
+  const int Ll = t->lens.back();
+  cudaError_t e = gemm(s, nb, 32, Ll, x, Ll, 1, t->params + t->lay.d1w, 1, Ll, t->d1z, 32, kEpiBiasElu,
+                       t->params + t->lay.d1b, t->d1h, nullptr);
+  if (e != cudaSuccess) return e;
+  // q = W2 h1 + b2: reuse the bias epilogue by writing Z = q and discarding ELU into edh scratch
+  return gemm(s, nb, r, 32, t->d1h, 32, 1, t->params + t->lay.d2w, 1, 32, q_out, r, kEpiBiasElu,
+              t->params + t->lay.d2b, t->ed1, nullptr);
+}
+
+cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx, const float* coords, float lr,
+                         double* loss_out, cudaStream_t s) {
+  const int m = t->dec.m, r = t->dec.r, w = t->dec.width, L = t->dec.hidden;
+  const int B = t->B, S = t->S, P = t->P;
+  const long N = (long)B * S;
+  const TrainerLayout& lay = t->lay;
+  float* p = t->params;
+  float* gr = t->grads;
+  cudaError_t e;
+  // ---- encoder forward: q_b
+  if ((e = trainer_encode(t, B, snaps, t->q, s)) != cudaSuccess) return e;
+  // ---- decoder forward on the sampled points
+  gather_kernel<<<blocks(N, 256), 256, 0, s>>>(snaps, pt_idx, coords, t->q, B, S, P, m, r, t->in0, t->target);
+  const float* hin = t->in0;
+  int kin = m + r;
+  for (int l = 0; l < L; ++l) {
+    e = gemm(s, (int)N, w, kin, hin, kin, 1, p + lay.dec_w[l], 1, kin, t->Z[l], w, kEpiBiasElu, p + lay.dec_b[l],
+             t->H[l], nullptr);
+    if (e != cudaSuccess) return e;
+    hin = t->H[l];
+    kin = w;
+  }
+  output_loss_kernel<<<blocks(N, 8), 256, 0, s>>>(t->H[L - 1], w, N, p + lay.dec_w[L], p + lay.dec_b[L], t->target,
+                                                   t->dg, t->partial);
+  loss_final_kernel<<<1, 32, 0, s>>>(t->partial, (int)blocks(N, 8), N, loss_out ? loss_out : t->loss_dev);
+  // ---- decoder reverse pass
+  // output layer: gW_out[u] = sum_n dg[n] H_L[n][u], gb_out = sum dg
+  e = gemm(s, 1, w, (int)N, t->dg, 0, 1, t->H[L - 1], w, 1, gr + lay.dec_w[L], w, kEpiStore, nullptr, nullptr,
+           nullptr, t->split);
+  if (e != cudaSuccess) return e;
+  colsum_kernel<<<1, 256, 0, s>>>(t->dg, N, 1, gr + lay.dec_b[L]);
+  out_delta_kernel<<<blocks(N * w, 256), 256, 0, s>>>(t->dg, p + lay.dec_w[L], t->Z[L - 1], w, N, t->delta);
+  float* dcur = t->delta;
+  float* dnext = t->delta2;
+  for (int l = L - 1; l >= 0; --l) {
+    const float* hprev = (l == 0) ? t->in0 : t->H[l - 1];
+    const int kprev = (l == 0) ? m + r : w;
+    // gW_l [w][kprev] = delta^T hprev (K = N, split), gb_l = column sums of delta
+    e = gemm(s, w, kprev, (int)N, dcur, 1, w, hprev, kprev, 1, gr + lay.dec_w[l], kprev, kEpiStore, nullptr,
+             nullptr, nullptr, t->split);
+    if (e != cudaSuccess) return e;
+    colsum_kernel<<<w, 256, 0, s>>>(dcur, N, w, gr + lay.dec_b[l]);
+    if (l > 0) {
+      // delta_{l-1} = (delta_l W_l) * s'(Z_{l-1})
+      e = gemm(s, (int)N, w, w, dcur, w, 1, p + lay.dec_w[l], w, 1, dnext, w, kEpiTimesEluD, nullptr, nullptr,
+               t->Z[l - 1]);
+    } else {
+      // input gradient din = delta_1 W_1  [N][m + r]
+      e = gemm(s, (int)N, m + r, w, dcur, w, 1, p + lay.dec_w[0], m + r, 1, t->din, m + r, kEpiStore, nullptr,
+               nullptr, nullptr);
+    }
+    if (e != cudaSuccess) return e;
+    float* tmp = dcur;
+    dcur = dnext;
+    dnext = tmp;
+  }
+  dq_kernel<<<blocks((long)B * r, 128), 128, 0, s>>>(t->din, B, S, m, r, t->dq);
+  // ---- encoder reverse pass
+  // dense 2: gW2 = dq^T h1, gb2 = sum dq, dz1 = (dq W2) * s'(z1)
+  const int Ll = t->lens.back();
+  if ((e = gemm(s, r, 32, B, t->dq, 1, r, t->d1h, 32, 1, gr + lay.d2w, 32, kEpiStore, nullptr, nullptr, nullptr)) !=
+      cudaSuccess)
+    return e;
+  colsum_kernel<<<r, 256, 0, s>>>(t->dq, B, r, gr + lay.d2b);
+  if ((e = gemm(s, B, 32, r, t->dq, r, 1, p + lay.d2w, 32, 1, t->ed1, 32, kEpiTimesEluD, nullptr, nullptr,
+                t->d1z)) != cudaSuccess)
+    return e;
+  // dense 1: gW1 = dz1^T h_conv, gb1 = sum dz1, dh_conv = dz1 W1
+  const float* hconv = t->conv_h.back();
+  if ((e = gemm(s, 32, Ll, B, t->ed1, 1, 32, hconv, Ll, 1, gr + lay.d1w, Ll, kEpiStore, nullptr, nullptr,
+                nullptr)) != cudaSuccess)
+    return e;
+  colsum_kernel<<<32, 256, 0, s>>>(t->ed1, B, 32, gr + lay.d1b);
+  if ((e = gemm(s, B, Ll, 32, t->ed1, 32, 1, p + lay.d1w, Ll, 1, t->edh, Ll, kEpiStore, nullptr, nullptr,
+                nullptr)) != cudaSuccess)
+    return e;
+  // convolutions, last to first
+  for (int c = (int)t->lens.size() - 1; c >= 1; --c) {
+    const int Lin = t->lens[c - 1], Lout = t->lens[c];
+    const long n = (long)B * Lout;
+    conv_dz_kernel<<<blocks(n, 256), 256, 0, s>>>(t->edh, t->conv_z[c - 1], n, t->edx);  // dz in edx
+    const float* xin = (c == 1) ? snaps : t->conv_h[c - 2];
+    conv_grad_kernel<<<7, 256, 0, s>>>(t->edx, xin, Lin, Lout, B, gr + lay.conv[c - 1]);
+    if (c > 1) conv_dx_kernel<<<blocks((long)B * Lin, 256), 256, 0, s>>>(t->edx, Lin, Lout, B,
+                                                                         p + lay.conv[c - 1], t->edh);
+  }
+  // ---- Adam
+  t->step += 1;
+  const float c1 = (float)(1.0 - pow(0.9, (double)t->step));
+  const float c2 = (float)(1.0 - pow(0.999, (double)t->step));
+  adam_kernel<<<blocks(lay.total, 256), 256, 0, s>>>(p, gr, t->am, t->av, lay.total, lr, c1, c2);
+  return cudaGetLastError();
+}
+
+}  // namespace crom

@@ -175,6 +175,27 @@ def test_step_tc_rollout_within_1e3():
         assert rel_l2(qT[i] - w.q0[i], traj[-1] - w.q0[i]) < 1e-2
 
 
+@pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_BF16X2"])
+def test_rollout_graph_equals_repeated_steps(prec_name):
+    """crom_rollout (a cached CUDA graph of n steps) gives bit-identical results to n
+    crom_step calls; a second call replays the cached graph and continues."""
+    import torch
+    c = crom()
+    prec = getattr(c, prec_name)
+    w = gen.heat2d_batched(n_inst=40, m_lo=20, m_hi=200)
+    ctx = make_ctx(w.spec, w.params)
+    q_ref, st_ref = run_steps(ctx, w, 24, prec)
+    q = dev(w.q0, torch.float64)
+    a, o, s = dev(w.alpha, torch.float32), dev(w.s_off, torch.int32), dev(w.samples, torch.float32)
+    st = torch.full((w.n_inst,), -1, dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        c.crom_rollout(ctx, q, a, o, s, st, n_steps=12, dt=w.dt, gn_iters=w.gn_iters,
+                       max_samples=int(w.sizes.max()), precision=prec)
+    torch.cuda.synchronize()
+    assert np.array_equal(q.cpu().numpy(), q_ref)
+    assert np.array_equal(st.cpu().numpy(), st_ref)
+
+
 def test_step_tc_edge_cases_status():
     c = crom()
     spec = gen.DecoderSpec(2, 4, 128, 3)

@@ -1,0 +1,117 @@
+"""GPU training step (crom_train_step, crom_encode) against the FP64 training
+oracle: loss, every gradient and the Adam update, through the C ABI.
+
+FP32 arithmetic: the loss and gradients are sums over B*S points, so they are
+held to relative L2 <= 1e-4 per parameter group against FP64; the Adam update is
+compared where the gradient is not negligible (a gradient within FP32 noise of 0
+may legitimately flip the sign of a first Adam step)."""
+import numpy as np
+import pytest
+
+from oracle import train_oracle as T
+from workloads import gen
+
+from helpers import dev, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c():
+    from paper_2206_02607_gb300 import build
+    build()
+    from paper_2206_02607_gb300 import crom
+    return crom
+
+
+def make_problem(seed, n, r, width, hidden, B, S):
+    rng = np.random.default_rng(seed)
+    P = n * n
+    lens = T.conv_lengths(P)
+    enc = {"conv": [(rng.standard_normal(6) * 0.4, rng.standard_normal() * 0.1) for _ in lens[1:]],
+           "dense": [(rng.standard_normal((32, lens[-1])) * 0.2, rng.standard_normal(32) * 0.1),
+                     (rng.standard_normal((r, 32)) * 0.3, rng.standard_normal(r) * 0.1)]}
+    dec = gen.xavier_decoder(gen.DecoderSpec(2, r, width, hidden), seed=seed + 1, bias_std=0.2)
+    enc = {"conv": [(np.float32(w).astype(np.float64), float(np.float32(b))) for w, b in enc["conv"]],
+           "dense": [(np.float32(W).astype(np.float64), np.float32(b).astype(np.float64)) for W, b in enc["dense"]]}
+    snaps = rng.standard_normal((B, P)).astype(np.float32)
+    pt_idx = np.stack([rng.choice(P, size=S, replace=False) for _ in range(B)]).astype(np.int32)
+    coords = gen.grid_points_2d(n)
+    return enc, dec, snaps, pt_idx, coords
+
+
+def groups(enc, dec):
+    """Slices of the flat parameter vector: one per weight/bias array."""
+    sizes = []
+    for W, b in dec:
+        sizes += [np.size(W), np.size(b)]
+    for w, b in enc["conv"]:
+        sizes += [6, 1]
+    for W, b in enc["dense"]:
+        sizes += [np.size(W), np.size(b)]
+    o, out = 0, []
+    for s in sizes:
+        out.append(slice(o, o + s))
+        o += s
+    return out
+
+
+@pytest.mark.parametrize("cfg", [dict(seed=0, n=16, r=3, width=32, hidden=3, B=3, S=37),
+                                 dict(seed=1, n=64, r=8, width=64, hidden=4, B=5, S=300)])
+def test_train_step_loss_gradients_and_adam(c, cfg):
+    import torch
+    enc, dec, snaps, pt_idx, coords = make_problem(**cfg)
+    n, B, S = cfg["n"], cfg["B"], cfg["S"]
+    tr = c.CromTrainer(2, cfg["r"], cfg["width"], cfg["hidden"], n * n, B, S)
+    p0 = T.flatten(enc, dec)
+    assert tr.n_params == p0.size
+    tr.set_params(p0.astype(np.float32))
+    loss_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lr = 1e-3
+    c.crom_train_step(tr, dev(snaps, torch.float32), dev(pt_idx, torch.int32), dev(coords, torch.float32), lr,
+                      loss_dev)
+    torch.cuda.synchronize()
+    loss, eg, dg = T.loss_and_grads(enc, dec, snaps.astype(np.float64), pt_idx, coords.astype(np.float64), 2)
+    assert abs(loss_dev.item() - loss) < 1e-5 * loss
+    g_ref = T.flatten(eg, dg)
+    g_gpu = tr.get_grads().astype(np.float64)
+    for sl in groups(enc, dec):
+        assert rel_l2(g_gpu[sl], g_ref[sl]) < 1e-4, sl
+    p1_ref, _, _ = T.adam_step(p0, g_ref, np.zeros_like(p0), np.zeros_like(p0), 1, lr)
+    p1 = tr.get_params().astype(np.float64)
+    big = np.abs(g_ref) > 1e-3 * np.abs(g_ref).max()
+    np.testing.assert_allclose(p1[big] - p0[big], p1_ref[big] - p0[big], rtol=1e-3, atol=1e-7)
+    tr.close()
+
+
+def test_encode_matches_oracle(c):
+    import torch
+    enc, dec, snaps, pt_idx, coords = make_problem(3, 64, 8, 32, 2, 4, 10)
+    tr = c.CromTrainer(2, 8, 32, 2, 64 * 64, 4, 10)
+    tr.set_params(T.flatten(enc, dec).astype(np.float32))
+    q = torch.empty((3, 8), dtype=torch.float32, device="cuda")
+    c.crom_encode(tr, dev(snaps[:3], torch.float32), q)
+    torch.cuda.synchronize()
+    q_ref, _ = T.encoder_forward(enc, snaps[:3].astype(np.float64))
+    assert rel_l2(q.cpu().numpy(), q_ref) < 1e-5
+    tr.close()
+
+
+def test_training_reduces_the_loss(c):
+    """20 Adam steps on snapshots of smooth fields lower the loss."""
+    import torch
+    n, r, B, S = 32, 4, 4, 256
+    enc, dec, _, _, coords = make_problem(5, n, r, 32, 3, B, S)
+    rng = np.random.default_rng(6)
+    snaps = np.stack([gen.gaussian_bumps_2d(n, rng, count=3).ravel() for _ in range(B)]).astype(np.float32)
+    tr = c.CromTrainer(2, r, 32, 3, n * n, B, S)
+    tr.set_params(T.flatten(enc, dec).astype(np.float32))
+    s_d, c_d = dev(snaps, torch.float32), dev(coords, torch.float32)
+    losses = []
+    for k in range(20):
+        pt = dev(np.stack([rng.choice(n * n, size=S, replace=False) for _ in range(B)]).astype(np.int32), torch.int32)
+        l = torch.zeros(1, dtype=torch.float64, device="cuda")
+        c.crom_train_step(tr, s_d, pt, c_d, 3e-3, l)
+        losses.append(l.item())
+    assert np.mean(losses[-5:]) < 0.7 * np.mean(losses[:5]), losses
+    tr.close()
