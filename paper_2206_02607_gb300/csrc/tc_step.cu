@@ -7,16 +7,16 @@
 // named barrier, so the UMMAs of one group overlap the CUDA-core epilogue of the
 // other.  Inside a group, hidden unit u is TMEM lane u and is served by two
 // threads (warps w and w + 4 of the group share a lane quadrant), each taking
-// half of the 16 samples of a tile.
+// half of the samples of a tile.
 //
-// Per instance, per Gauss-Newton iteration k, per tile of 16 samples
-// (paper §4, Algorithm 3):
+// Per instance, per Gauss-Newton iteration k, per tile of samples (16 at
+// iteration 0, 32 later; paper §4, Algorithm 3):
 //
 //  Step 1 (network inference): a forward pass whose UMMA columns are
 //  (channel, sample) pairs, D[u][n] = sum_k W_l[u][k] H[k][n] (M = 128 units,
-//  K = 128).  Iteration 0 carries the value, dg/dx_k and a single Laplacian
-//  channel (d2z = W d2h with d2h = s''(z) sum_k (dz/dx_k)^2 + s'(z) d2z, the
-//  m diagonal second-derivative channels of Algorithm 2 summed); iteration
+//  K = 128, N <= 64).  Iteration 0 carries the value, dg/dx_k and a single
+//  Laplacian channel (d2z = W d2h with d2h = s''(z) sum_k (dz/dx_k)^2 + s'(z) d2z,
+//  the m diagonal second-derivative channels of Algorithm 2 summed); iteration
 //  k >= 1 carries the value at q^(k) and the difference channel
 //  h(q^(k)) - h(q_n).  The epilogue (bias, ELU chain; s'(z) kept in TMEM for the
 //  reverse pass) runs in FP32 registers and writes bf16 hi/lo operand pairs.
@@ -27,9 +27,10 @@
 //  Step 3 (network inversion): Jacobian rows dg/dq(y_j) from one reverse-mode
 //  pass, delta_L = w_out * s'(z_L), delta_{l-1} = (W_l^T delta_l) * s'(z_{l-1}) on
 //  the tensor cores (A = W_l read MN-major from the same shared image), then
-//  J = W_1q^T delta_1 by a projection UMMA.  J^T J and J^T rho are accumulated
-//  in FP64 from the FP32 rows (exact products); the r x r system is solved by
-//  FP64 Cholesky and q is updated in FP64.
+//  J = W_1q^T delta_1 by a projection UMMA.  J^T J and J^T rho are formed from
+//  exact FP32 products (two-product) with compensated sums per tile and added in
+//  FP64; the r x r system is solved by an FP64 Cholesky factorisation spread
+//  over a warp; q is updated in FP64.
 //
 // The output layer w_out . h_L and the projection W_1q^T delta_1 share one
 // 16-row bf16 matrix P (row 0 = w_out, rows 1..r = W_1q columns).
@@ -48,13 +49,14 @@ using namespace tc;
 constexpr int kGroups = 2;
 constexpr int kGT = 256;                 // threads per group
 constexpr int kThreads = kGroups * kGT;
-constexpr int kS = 16;                   // samples per tile
-constexpr int kHalf = kS / 2;            // samples per thread
+constexpr int kS0 = 16;                  // samples per tile at GN iteration 0 (4 channels)
+constexpr int kS1 = 32;                  // samples per tile at later iterations (2 channels)
+constexpr int kSMax = 32;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kGroupCols = 256;     // TMEM columns per group
 constexpr uint32_t kAcc = 0;             // accumulator, up to 64 columns
-constexpr uint32_t kSig = 64;            // s'(z_l), l = 1..L (<= 5): 16 columns each
-constexpr uint32_t kPrj = 144;           // projection output, 16 columns
+constexpr uint32_t kSig = 64;            // s'(z_l), l = 1..L (<= 5): kS columns each (<= 160)
+constexpr uint32_t kPrj = 224;           // projection output, 16 columns
 constexpr uint32_t kWaitLimit = 1u << 25;
 constexpr size_t kHBuf = (size_t)kTcWidth * 64 * 2;  // one bf16 operand buffer (<= 64 columns), 16 KB
 
@@ -62,7 +64,7 @@ struct StepParams {
   const uint8_t* img;
   int img_bytes;
   int L;  // hidden layers
-  int m, r;
+  int r;
   const float* w1;
   const float* b1;
   const float* bh;
@@ -101,12 +103,13 @@ struct __align__(16) Group {
   double qn[16];
   double qcur[16];
   double amat[15 * 16];
+  double invd[16];
   float c1[kTcWidth];
   float dz1[kTcWidth];
-  float xs[2][kS];
-  float gout[4][kS];
-  float rho[kS];
-  float jt[kS][16];
+  float xs[2][kSMax];
+  float gout[4][kSMax];
+  float rho[kSMax];
+  float jt[kSMax][16];
 };
 
 // The projection UMMA reads 128 rows (two 64-column blocks) of a 64-column
@@ -132,7 +135,7 @@ __device__ __forceinline__ bool group_sync_and(int g, bool pred) {
 
 // Eight consecutive columns n0..n0+7 of row k as a bf16 hi/lo pair (one 16-byte
 // chunk in each buffer).
-__device__ __forceinline__ void split_store8(uint8_t* Hhi, uint8_t* Hlo, int k, int n0, const float (&v)[8]) {
+__device__ __forceinline__ void split_store8(uint8_t* Hhi, uint8_t* Hlo, int k, int n0, const float* v) {
   uint32_t hi[4], lo[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -189,31 +192,297 @@ __device__ __forceinline__ void issue_proj(uint32_t d, uint64_t ahi, uint64_t al
     umma_f16(d, desc_add(alo, mnmajor_kslice(kk)), desc_add(p0, kmajor_kslice(16, kk)), id, 1);
 }
 
+// Per-thread view of the group it belongs to.
+struct Lane {
+  int g, gt, gw, u, half;
+  uint32_t lane_base, tb;
+  uint8_t* Hhi;
+  uint8_t* Hlo;
+  Shared* S;
+  Group* G;
+  uint64_t dW_k, dW_mn, dP, dHhi, dHlo;
+  float wx0, wx1, wsq, wo;
+  uint32_t phase;
+};
+
+// One UMMA stage of the group: fence the epilogue's shared-memory writes, meet,
+// one thread issues and commits, the first warp waits on the mbarrier, the rest at
+// the group barrier.  Returns the group-uniform completion flag.
+enum StageKind { kStageFwd = 0, kStageBwd = 1, kStageProj = 2 };
+template <StageKind kKind>
+__device__ __forceinline__ bool stage(Lane& c, int layer, uint32_t idesc) {
+  fence_proxy_async_smem();
+  tc_fence_before();
+  group_sync(c.g);
+  bool done = true;
+  if (c.gw == 0) {
+    if (c.gt == 0) {
+      tc_fence_after();
+      if (kKind == kStageFwd)
+        issue_layer<false>(c.tb + kAcc, desc_add(c.dW_k, (uint32_t)layer * kTcLayerBytes), c.dHhi, c.dHlo, idesc);
+      else if (kKind == kStageBwd)
+        issue_layer<true>(c.tb + kAcc, desc_add(c.dW_mn, (uint32_t)layer * kTcLayerBytes), c.dHhi, c.dHlo, idesc);
+      else
+        issue_proj(c.tb + kPrj, c.dHhi, c.dHlo, c.dP);
+      umma_commit(&c.G->bar_mma);
+    }
+    __syncwarp();
+    done = mbar_wait(&c.G->bar_mma, c.phase, kWaitLimit);
+  }
+  done = group_sync_and(c.g, done);
+  c.phase ^= 1;
+  tc_fence_after();
+  return done;
+}
+
+// Exact product-sum of up to kSMax FP32 pairs: two-product (a*b = p + e exactly by
+// one FMA) and a compensated (two-sum) accumulation of the p, in FP32; returned in
+// FP64.  Relative error ~2^-46, well below the FP32 inputs' own rounding.
+__device__ __forceinline__ double dot_exact(const float* a, int sa, const float* b, int sb, int n) {
+  float s = 0.f, comp = 0.f;
+  for (int i = 0; i < n; ++i) {
+    const float x = a[i * sa], y = b[i * sb];
+    const float p = __fmul_rn(x, y);  // rounded product (kept out of FMA contraction)
+    const float e = fmaf(x, y, -p);   // its exact rounding error
+    const float t = __fadd_rn(s, p);
+    const float bp = __fsub_rn(t, s);
+    comp += __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp)) + e;
+    s = t;
+  }
+  return (double)s + (double)comp;
+}
+
+// One tile of kSm samples of one GN iteration: forward pass, PDE update / residual,
+// reverse pass, Jacobian projection and this tile's share of J^T J and J^T rho.
+template <int kM, int kSm, bool kFirst>
+__device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, int t, int ns, float alpha, int ea,
+                                         int eb, double& acc) {
+  constexpr int kCh = kFirst ? 2 + kM : 2;  // iteration 0: v, dx_1..dx_m, Lap; later: v(q^(k)), diff
+  constexpr int kN = kCh * kSm;
+  constexpr int kHalf = kSm / 2;            // samples of this thread
+  static_assert(kN <= 64 && kHalf % 8 == 0, "tile shape");
+  Group* G = c.G;
+  const Shared* S = c.S;
+  const int u = c.u, s0 = c.half * kHalf;
+  const uint32_t lb = c.lane_base, tb = c.tb;
+  if (c.gt < kSm) {
+    const int s = c.gt < ns ? c.gt : 0;
+    for (int k = 0; k < kM; ++k) G->xs[k][c.gt] = p.x[(size_t)(o0 + t * kSm + s) * kM + k];
+  }
+  group_sync(c.g);
+  // ---------------- layer 1 (CUDA cores)
+  {
+    const float cc = G->c1[u], dz = G->dz1[u];
+#pragma unroll
+    for (int h8 = 0; h8 < kHalf; h8 += 8) {
+      float v[kCh][8], sg[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float z = fmaf(c.wx0, G->xs[0][s0 + h8 + i], cc);
+        if (kM > 1) z = fmaf(c.wx1, G->xs[1][s0 + h8 + i], z);
+        const float e = __expf(fminf(z, 0.f));
+        const bool pos = z > 0.f;
+        const float s1 = pos ? 1.f : e, s2 = pos ? 0.f : e;
+        sg[i] = s1;
+        v[0][i] = pos ? z : e - 1.f;
+        if (kFirst) {
+          v[1][i] = s1 * c.wx0;
+          if (kM > 1) v[2][i] = s1 * c.wx1;
+          v[kCh - 1][i] = s2 * c.wsq;
+        } else {
+          v[1][i] = elu_diff(z, dz, e);
+        }
+      }
+      tmem_st8(taddr(tb, lb, kSig + s0 + h8), sg);
+#pragma unroll
+      for (int ch = 0; ch < kCh; ++ch) split_store8(c.Hhi, c.Hlo, u, ch * kSm + s0 + h8, v[ch]);
+    }
+    tmem_st_wait();
+  }
+  // ---------------- hidden layers 2..L (tensor cores)
+  constexpr uint32_t id_fwd = idesc_f16(128, kN, false, true, true);
+  for (int l = 0; l < p.L - 1; ++l) {
+    if (!stage<kStageFwd>(c, l, id_fwd)) return false;
+    const float bias = S->bh[l][u];
+#pragma unroll
+    for (int h8 = 0; h8 < kHalf; h8 += 8) {
+      float v[kCh][8], sg[8];
+#pragma unroll
+      for (int ch = 0; ch < kCh; ++ch) tmem_ld8(taddr(tb, lb, kAcc + ch * kSm + s0 + h8), v[ch]);
+      tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float z = v[0][i] + bias;
+        const float e = __expf(fminf(z, 0.f));
+        const bool pos = z > 0.f;
+        const float s1 = pos ? 1.f : e, s2 = pos ? 0.f : e;
+        sg[i] = s1;
+        v[0][i] = pos ? z : e - 1.f;
+        if (kFirst) {
+          const float a = v[1][i];
+          const float b = (kM > 1) ? v[2][i] : 0.f;
+          v[1][i] = s1 * a;
+          if (kM > 1) v[2][i] = s1 * b;
+          v[kCh - 1][i] = fmaf(s2, fmaf(a, a, b * b), s1 * v[kCh - 1][i]);
+        } else {
+          v[1][i] = elu_diff(z, v[1][i], e);
+        }
+      }
+      tmem_st8(taddr(tb, lb, kSig + (l + 1) * kSm + s0 + h8), sg);
+#pragma unroll
+      for (int ch = 0; ch < kCh; ++ch) split_store8(c.Hhi, c.Hlo, u, ch * kSm + s0 + h8, v[ch]);
+    }
+    tmem_st_wait();
+  }
+  // ---------------- output layer: PRJ[n][0] = w_out . h_L[:, n]
+  if (!stage<kStageProj>(c, 0, 0)) return false;
+  if (c.half == 0) {
+    float v[8];
+    tmem_ld8(taddr(tb, lb, kPrj), v);
+    tmem_ld_wait();
+    if (u < kN) G->gout[u / kSm][u % kSm] = v[0];
+  }
+  group_sync(c.g);
+  // ---------------- Step 2 and the residual rho_j
+  if (c.gt < kSm) {
+    float rho = 0.f;
+    if (c.gt < ns) {
+      const int j = o0 + t * kSm + c.gt;
+      if (kFirst) {
+        const float lap = G->gout[kM + 1][c.gt];
+        double df;
+        if (p.pde == CROM_PDE_HEAT) {
+          df = p.dt * (double)alpha * (double)lap;
+        } else {
+          double adv = 0.0;
+          for (int k = 0; k < kM; ++k) adv += (double)p.vel[(size_t)j * kM + k] * (double)G->gout[1 + k][c.gt];
+          df = p.dt * (-adv + (double)alpha * (double)lap);
+        }
+        p.df[j] = df;
+        rho = (float)(-df);
+      } else {
+        rho = (float)((double)G->gout[1][c.gt] - p.df[j]);
+      }
+    }
+    G->rho[c.gt] = rho;
+  }
+  // ---------------- reverse pass for dg/dq at q^(k)
+#pragma unroll
+  for (int h8 = 0; h8 < kHalf; h8 += 8) {
+    float sg[8];
+    tmem_ld8(taddr(tb, lb, kSig + (p.L - 1) * kSm + s0 + h8), sg);
+    tmem_ld_wait();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sg[i] *= c.wo;
+    split_store8(c.Hhi, c.Hlo, u, s0 + h8, sg);  // delta_L
+  }
+  constexpr uint32_t id_bwd = idesc_f16(128, kSm, true, true, true);
+  for (int l = p.L - 2; l >= 0; --l) {
+    // accumulator = W_{l+2}^T delta_{l+2}; times s'(z_{l+1}) gives delta_{l+1}
+    if (!stage<kStageBwd>(c, l, id_bwd)) return false;
+#pragma unroll
+    for (int h8 = 0; h8 < kHalf; h8 += 8) {
+      float v[8], sg[8];
+      tmem_ld8(taddr(tb, lb, kAcc + s0 + h8), v);
+      tmem_ld8(taddr(tb, lb, kSig + l * kSm + s0 + h8), sg);
+      tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] *= sg[i];
+      split_store8(c.Hhi, c.Hlo, u, s0 + h8, v);
+    }
+  }
+  // J[s][j] = sum_u W_1q[u][j] delta_1[u][s]
+  if (!stage<kStageProj>(c, 0, 0)) return false;
+  if (c.gw == 0) {
+    float v[16];
+    tmem_ld16(taddr(tb, 0, kPrj), v);
+    tmem_ld_wait();
+    if (c.gt < kSm) {
+#pragma unroll
+      for (int j = 0; j < 15; ++j) G->jt[c.gt][j] = v[j + 1];
+    }
+  }
+  group_sync(c.g);
+  // ---------------- this tile's normal-equation terms
+  if (ea >= 0) acc += dot_exact(&G->jt[0][ea], 16, eb >= 0 ? &G->jt[0][eb] : G->rho, eb >= 0 ? 16 : 1, ns);
+  return true;
+}
+
+// Warp-parallel FP64 Cholesky solve of A x = b with A = amat[a*(r+1)+b] and b in
+// column r (right-looking: lane i owns row i).  Returns the status; on success
+// x_k is left in amat[k*(r+1)+r].
+__device__ int chol_solve_warp(double* A, double* invd, int r, int lane) {
+  const int R = r + 1;
+  bool bad = false;
+  for (int e = lane; e < r * R; e += 32) bad |= !isfinite(A[e]);
+  if (__any_sync(0xffffffffu, bad)) return CROM_ERR_NONFINITE;
+  double dmax = 0.0;
+  for (int a = 0; a < r; ++a) dmax = fmax(dmax, A[a * R + a]);
+  const double tol = 1e-14 * dmax;
+  for (int j = 0; j < r; ++j) {
+    const double d = A[j * R + j];
+    if (!(d > tol)) return CROM_ERR_SINGULAR;
+    const double ljj = sqrt(d);
+    const double inv = 1.0 / ljj;
+    __syncwarp();
+    if (lane == 0) {
+      A[j * R + j] = ljj;
+      invd[j] = inv;
+    }
+    if (lane > j && lane < r) A[lane * R + j] *= inv;
+    __syncwarp();
+    if (lane > j && lane < r) {
+      const double lij = A[lane * R + j];
+      for (int k = j + 1; k <= lane; ++k) A[lane * R + k] -= lij * A[k * R + j];
+    }
+    __syncwarp();
+  }
+  for (int k = 0; k < r; ++k) {  // L y = b
+    const double yk = A[k * R + r] * invd[k];
+    __syncwarp();
+    if (lane == 0) A[k * R + r] = yk;
+    if (lane > k && lane < r) A[lane * R + r] -= A[lane * R + k] * yk;
+    __syncwarp();
+  }
+  for (int k = r - 1; k >= 0; --k) {  // L^T x = y
+    const double xk = A[k * R + r] * invd[k];
+    __syncwarp();
+    if (lane == 0) A[k * R + r] = xk;
+    if (lane < k) A[lane * R + r] -= A[k * R + lane] * xk;
+    __syncwarp();
+  }
+  return CROM_OK;
+}
+
+template <int kM>
 __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x;
-  const int g = tid / kGT, gt = tid % kGT;
-  const int gw = gt >> 5;                 // warp within the group
-  const int lq = gw & 3;                  // TMEM lane quadrant of this warp
-  const int half = gw >> 2;               // which 8 samples of a tile
-  const int u = lq * 32 + (gt & 31);      // hidden unit = TMEM lane
-  const int s0 = half * kHalf;
-  const uint32_t lane_base = (uint32_t)lq * 32;
-  const int m = p.m, r = p.r, L = p.L;
+  const int r = p.r, L = p.L;
+  Lane c;
+  c.g = tid / kGT;
+  c.gt = tid % kGT;
+  c.gw = c.gt >> 5;
+  const int lq = c.gw & 3;        // TMEM lane quadrant of this warp
+  c.half = c.gw >> 2;              // which half of a tile's samples
+  c.u = lq * 32 + (c.gt & 31);     // hidden unit = TMEM lane
+  c.lane_base = (uint32_t)lq * 32;
 
   uint8_t* Wimg = sm;
   uint8_t* Hbase = sm + ((p.img_bytes + 1023) & ~1023);
-  uint8_t* Hhi = Hbase + (size_t)g * 2 * kHBuf;
-  uint8_t* Hlo = Hhi + kHBuf;
-  Shared* S = reinterpret_cast<Shared*>(Hbase + (size_t)kGroups * 2 * kHBuf);
-  Group* G = reinterpret_cast<Group*>(S + 1) + g;
+  c.Hhi = Hbase + (size_t)c.g * 2 * kHBuf;
+  c.Hlo = c.Hhi + kHBuf;
+  c.S = reinterpret_cast<Shared*>(Hbase + (size_t)kGroups * 2 * kHBuf);
+  c.G = reinterpret_cast<Group*>(c.S + 1) + c.g;
+  Shared* S = c.S;
+  Group* G = c.G;
 
   if (tid == 0) {
     mbar_init(&S->bar_w, 1);
     fence_mbar_init();
   }
-  if (gt == 0) {
+  if (c.gt == 0) {
     mbar_init(&G->bar_mma, 1);
     fence_mbar_init();
   }
@@ -223,266 +492,86 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
   }
   if (tid < kTcWidth) {
     for (int l = 0; l < L - 1; ++l) S->bh[l][tid] = p.bh[l * kTcWidth + tid];
-    for (int k = 0; k < m; ++k) S->w1x[k][tid] = p.w1[tid * (m + r) + k];
-    for (int j = 0; j < r; ++j) S->w1q[j][tid] = p.w1[tid * (m + r) + m + j];
+    for (int k = 0; k < kM; ++k) S->w1x[k][tid] = p.w1[tid * (kM + r) + k];
+    for (int j = 0; j < r; ++j) S->w1q[j][tid] = p.w1[tid * (kM + r) + kM + j];
     S->wout[tid] = p.wout[tid];
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tb = S->tmem_base + (uint32_t)g * kGroupCols;
+  c.tb = S->tmem_base + (uint32_t)c.g * kGroupCols;
   if (tid == 0) {
     mbar_arrive_expect_tx(&S->bar_w, (uint32_t)p.img_bytes);
     for (int o = 0; o < p.img_bytes; o += 16384)
       bulk_g2s(Wimg + o, p.img + o, (uint32_t)min(16384, p.img_bytes - o), &S->bar_w);
   }
   bool ok = __syncthreads_and(mbar_wait(&S->bar_w, 0, kWaitLimit));
-  uint32_t phase = 0;
+  c.phase = 0;
   const uint32_t wbase = smem_u32(Wimg);
   // Base UMMA descriptors; every operand slice is base + a compile-time offset.
-  const uint64_t dW_k = smem_desc_sw128(wbase, 16, 1024);       // W_l as K-major A
-  const uint64_t dW_mn = smem_desc_sw128(wbase, 16384, 1024);   // W_l^T as MN-major A
-  const uint64_t dP = smem_desc_sw128(wbase + (uint32_t)(L - 1) * kTcLayerBytes, 16, 1024);
-  const uint64_t dHhi = smem_desc_sw128(smem_u32(Hhi), 16384, 1024);
-  const uint64_t dHlo = smem_desc_sw128(smem_u32(Hlo), 16384, 1024);
+  c.dW_k = smem_desc_sw128(wbase, 16, 1024);       // W_l as K-major A
+  c.dW_mn = smem_desc_sw128(wbase, 16384, 1024);   // W_l^T as MN-major A
+  c.dP = smem_desc_sw128(wbase + (uint32_t)(L - 1) * kTcLayerBytes, 16, 1024);
+  c.dHhi = smem_desc_sw128(smem_u32(c.Hhi), 16384, 1024);
+  c.dHlo = smem_desc_sw128(smem_u32(c.Hlo), 16384, 1024);
+  c.wx0 = S->w1x[0][c.u];
+  c.wx1 = (kM > 1) ? S->w1x[1][c.u] : 0.f;
+  c.wsq = c.wx0 * c.wx0 + c.wx1 * c.wx1;
+  c.wo = S->wout[c.u];
   const int ntri = r * (r + 1) / 2;
   const int n_entries = ntri + r;  // <= 135 < kGT
-  // FP64 normal-equation entry owned by this thread
+  // normal-equation entry owned by this thread: (ea, eb) of J^T J, or (ea, -2) of J^T rho
   int ea = -1, eb = -1;
-  if (gt < ntri) {
-    int a = 0, rem = gt;
+  if (c.gt < ntri) {
+    int a = 0, rem = c.gt;
     while (rem >= r - a) { rem -= r - a; ++a; }
     ea = a; eb = a + rem;
-  } else if (gt < n_entries) {
-    ea = gt - ntri; eb = -2;
+  } else if (c.gt < n_entries) {
+    ea = c.gt - ntri; eb = -2;
   }
-  const float wx0 = S->w1x[0][u], wx1 = (m > 1) ? S->w1x[1][u] : 0.f;
-  const float wsq = wx0 * wx0 + wx1 * wx1;
-  const float wo = S->wout[u];
-
-  // Issue + wait of one UMMA stage of this group: one thread issues, the first
-  // warp waits on the mbarrier, the rest wait at the group barrier; every thread
-  // returns the same value.
-  auto stage = [&](auto issue) -> bool {
-    fence_proxy_async_smem();
-    tc_fence_before();
-    group_sync(g);
-    bool done = true;
-    if (gw == 0) {
-      if (gt == 0) {
-        tc_fence_after();
-        issue();
-        umma_commit(&G->bar_mma);
-      }
-      __syncwarp();
-      done = mbar_wait(&G->bar_mma, phase, kWaitLimit);
-    }
-    done = group_sync_and(g, done);
-    phase ^= 1;
-    tc_fence_after();
-    return done;
-  };
 
   while (ok) {
-    group_sync(g);  // everyone is done with the previous instance's group state
-    if (gt == 0) G->s_idx = atomicAdd(&p.queue[0], 1);
-    group_sync(g);
+    group_sync(c.g);  // everyone is done with the previous instance's group state
+    if (c.gt == 0) G->s_idx = atomicAdd(&p.queue[0], 1);
+    group_sync(c.g);
     const int idx = G->s_idx;
     if (idx >= p.n_inst) break;
     const int inst = p.order[idx];
     const int o0 = p.off[inst];
     const int M = p.off[inst + 1] - o0;
     if (M < r || M > p.max_samples) {
-      if (gt == 0) p.status[inst] = CROM_ERR_INVALID_ARG;
+      if (c.gt == 0) p.status[inst] = CROM_ERR_INVALID_ARG;
       continue;
     }
-    if (gt < r) {
-      const double v = p.q[(size_t)inst * r + gt];
-      G->qn[gt] = v;
-      G->qcur[gt] = v;
+    if (c.gt < r) {
+      const double v = p.q[(size_t)inst * r + c.gt];
+      G->qn[c.gt] = v;
+      G->qcur[c.gt] = v;
     }
-    if (gt == 0) G->s_status = CROM_OK;
+    if (c.gt == 0) G->s_status = CROM_OK;
     const float alpha = p.alpha[inst];
-    group_sync(g);
-    const int ntiles = (M + kS - 1) / kS;
+    group_sync(c.g);
 
     for (int it = 0; it < p.gn_iters && ok; ++it) {
-      const bool first = (it == 0);
-      const int nch = first ? 2 + m : 2;  // iteration 0: v, dx_1..dx_m, Lap; later: v(q^(k)), diff
-      const int N = nch * kS;
-      if (half == 0) {
-        double c = (double)p.b1[u], dz = 0.0;
+      if (c.half == 0) {
+        double cc = (double)p.b1[c.u], dz = 0.0;
         for (int j = 0; j < r; ++j) {
-          c += (double)S->w1q[j][u] * G->qcur[j];
-          dz += (double)S->w1q[j][u] * (G->qcur[j] - G->qn[j]);
+          cc += (double)S->w1q[j][c.u] * G->qcur[j];
+          dz += (double)S->w1q[j][c.u] * (G->qcur[j] - G->qn[j]);
         }
-        G->c1[u] = (float)c;
-        G->dz1[u] = (float)dz;
+        G->c1[c.u] = (float)cc;
+        G->dz1[c.u] = (float)dz;
       }
       double acc = 0.0;
-      for (int t = 0; t < ntiles && ok; ++t) {
-        const int ns = min(kS, M - t * kS);
-        if (gt < kS) {
-          const int s = gt < ns ? gt : 0;
-          for (int k = 0; k < m; ++k) G->xs[k][gt] = p.x[(size_t)(o0 + t * kS + s) * m + k];
-        }
-        group_sync(g);
-        // ---------------- layer 1 (CUDA cores)
-        {
-          const float c = G->c1[u], dz = G->dz1[u];
-          float v[4][kHalf], sg[kHalf];
-#pragma unroll
-          for (int i = 0; i < kHalf; ++i) {
-            float z = fmaf(wx0, G->xs[0][s0 + i], c);
-            if (m > 1) z = fmaf(wx1, G->xs[1][s0 + i], z);
-            const float e = __expf(fminf(z, 0.f));
-            const bool pos = z > 0.f;
-            const float s1 = pos ? 1.f : e, s2 = pos ? 0.f : e;
-            sg[i] = s1;
-            v[0][i] = pos ? z : e - 1.f;
-            if (first) {
-              v[1][i] = s1 * wx0;
-              if (m > 1) {
-                v[2][i] = s1 * wx1;
-                v[3][i] = s2 * wsq;
-              } else {
-                v[2][i] = s2 * wsq;
-              }
-            } else {
-              v[1][i] = elu_diff(z, dz, e);
-            }
-          }
-          tmem_st8(taddr(tb, lane_base, kSig + s0), sg);
-#pragma unroll
-          for (int ch = 0; ch < 4; ++ch)
-            if (ch < nch) split_store8(Hhi, Hlo, u, ch * kS + s0, v[ch]);
-          tmem_st_wait();
-        }
-        // ---------------- hidden layers 2..L (tensor cores)
-        const uint32_t id_fwd = idesc_f16(128, N, false, true, true);
-        for (int l = 0; l < L - 1 && ok; ++l) {
-          ok = stage([&] {
-            issue_layer<false>(tb + kAcc, desc_add(dW_k, (uint32_t)l * kTcLayerBytes), dHhi, dHlo, id_fwd);
-          });
-          if (!ok) break;
-          const float bias = S->bh[l][u];
-          float v[4][kHalf], sg[kHalf];
-#pragma unroll
-          for (int ch = 0; ch < 4; ++ch)
-            if (ch < nch) tmem_ld8(taddr(tb, lane_base, kAcc + ch * kS + s0), v[ch]);
-          tmem_ld_wait();
-#pragma unroll
-          for (int i = 0; i < kHalf; ++i) {
-            const float z = v[0][i] + bias;
-            const float e = __expf(fminf(z, 0.f));
-            const bool pos = z > 0.f;
-            const float s1 = pos ? 1.f : e, s2 = pos ? 0.f : e;
-            sg[i] = s1;
-            v[0][i] = pos ? z : e - 1.f;
-            if (first) {
-              if (m > 1) {
-                const float a = v[1][i], b = v[2][i];
-                v[1][i] = s1 * a;
-                v[2][i] = s1 * b;
-                v[3][i] = fmaf(s2, fmaf(a, a, b * b), s1 * v[3][i]);
-              } else {
-                const float a = v[1][i];
-                v[1][i] = s1 * a;
-                v[2][i] = fmaf(s2, a * a, s1 * v[2][i]);
-              }
-            } else {
-              v[1][i] = elu_diff(z, v[1][i], e);
-            }
-          }
-          tmem_st8(taddr(tb, lane_base, kSig + (l + 1) * kS + s0), sg);
-#pragma unroll
-          for (int ch = 0; ch < 4; ++ch)
-            if (ch < nch) split_store8(Hhi, Hlo, u, ch * kS + s0, v[ch]);
-          tmem_st_wait();
-        }
-        if (!ok) break;
-        // ---------------- output layer: PRJ[n][0] = w_out . h_L[:, n]
-        ok = stage([&] { issue_proj(tb + kPrj, dHhi, dHlo, dP); });
-        if (!ok) break;
-        if (half == 0) {
-          float v[8];
-          tmem_ld8(taddr(tb, lane_base, kPrj), v);
-          tmem_ld_wait();
-          if (u < N) G->gout[u / kS][u % kS] = v[0];
-        }
-        group_sync(g);
-        // ---------------- Step 2 and the residual rho_j
-        if (gt < kS) {
-          float rho = 0.f;
-          if (gt < ns) {
-            const int j = o0 + t * kS + gt;
-            if (first) {
-              const float lap = G->gout[m + 1][gt];
-              double df;
-              if (p.pde == CROM_PDE_HEAT) {
-                df = p.dt * (double)alpha * (double)lap;
-              } else {
-                double adv = 0.0;
-                for (int k = 0; k < m; ++k) adv += (double)p.vel[(size_t)j * m + k] * (double)G->gout[1 + k][gt];
-                df = p.dt * (-adv + (double)alpha * (double)lap);
-              }
-              p.df[j] = df;
-              rho = (float)(-df);
-            } else {
-              rho = (float)((double)G->gout[1][gt] - p.df[j]);
-            }
-          }
-          G->rho[gt] = rho;
-        }
-        // ---------------- reverse pass for dg/dq at q^(k)
-        {
-          float sg[kHalf];
-          tmem_ld8(taddr(tb, lane_base, kSig + (L - 1) * kS + s0), sg);
-          tmem_ld_wait();
-#pragma unroll
-          for (int i = 0; i < kHalf; ++i) sg[i] *= wo;
-          split_store8(Hhi, Hlo, u, s0, sg);  // delta_L
-        }
-        constexpr uint32_t id_bwd = idesc_f16(128, kS, true, true, true);
-        for (int l = L - 2; l >= 0 && ok; --l) {
-          // accumulator = W_{l+2}^T delta_{l+2}; times s'(z_{l+1}) gives delta_{l+1}
-          ok = stage([&] {
-            issue_layer<true>(tb + kAcc, desc_add(dW_mn, (uint32_t)l * kTcLayerBytes), dHhi, dHlo, id_bwd);
-          });
-          if (!ok) break;
-          float v[kHalf], sg[kHalf];
-          tmem_ld8(taddr(tb, lane_base, kAcc + s0), v);
-          tmem_ld8(taddr(tb, lane_base, kSig + l * kS + s0), sg);
-          tmem_ld_wait();
-#pragma unroll
-          for (int i = 0; i < kHalf; ++i) v[i] *= sg[i];
-          split_store8(Hhi, Hlo, u, s0, v);
-        }
-        if (!ok) break;
-        // J[s][j] = sum_u W_1q[u][j] delta_1[u][s]
-        ok = stage([&] { issue_proj(tb + kPrj, dHhi, dHlo, dP); });
-        if (!ok) break;
-        if (gw == 0) {
-          float v[16];
-          tmem_ld16(taddr(tb, 0, kPrj), v);
-          tmem_ld_wait();
-          if (gt < kS) {
-#pragma unroll
-            for (int j = 0; j < 15; ++j) G->jt[gt][j] = v[j + 1];
-          }
-        }
-        group_sync(g);
-        // ---------------- normal equations in FP64 (exact products of FP32 rows)
-        if (ea >= 0) {
-          double s = 0.0;
-          if (eb >= 0) {
-            for (int i = 0; i < ns; ++i) s = fma((double)G->jt[i][ea], (double)G->jt[i][eb], s);
-          } else {
-            for (int i = 0; i < ns; ++i) s = fma((double)G->jt[i][ea], (double)G->rho[i], s);
-          }
-          acc += s;
-        }
-      }  // tiles
+      if (it == 0) {
+        const int nt = (M + kS0 - 1) / kS0;
+        for (int t = 0; t < nt && ok; ++t)
+          ok = run_tile<kM, kS0, true>(c, p, o0, t, min(kS0, M - t * kS0), alpha, ea, eb, acc);
+      } else {
+        const int nt = (M + kS1 - 1) / kS1;
+        for (int t = 0; t < nt && ok; ++t)
+          ok = run_tile<kM, kS1, false>(c, p, o0, t, min(kS1, M - t * kS1), alpha, ea, eb, acc);
+      }
       if (!ok) break;
       const int R = r + 1;
       if (ea >= 0) {
@@ -493,52 +582,20 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
           G->amat[ea * R + r] = -acc;
         }
       }
-      group_sync(g);
-      if (gt == 0) {
-        double* A = G->amat;
-        int st = CROM_OK;
-        double dmax = 0.0;
-        for (int a = 0; a < r; ++a)
-          for (int b = 0; b <= r; ++b)
-            if (!isfinite(A[a * R + b])) st = CROM_ERR_NONFINITE;
-        for (int a = 0; a < r; ++a) dmax = fmax(dmax, A[a * R + a]);
-        const double tol = 1e-14 * dmax;
-        for (int j = 0; j < r && st == CROM_OK; ++j) {
-          double d = A[j * R + j];
-          for (int k = 0; k < j; ++k) d -= A[j * R + k] * A[j * R + k];
-          if (!(d > tol)) { st = CROM_ERR_SINGULAR; break; }
-          const double ljj = sqrt(d);
-          A[j * R + j] = ljj;
-          for (int i = j + 1; i < r; ++i) {
-            double v = A[i * R + j];
-            for (int k = 0; k < j; ++k) v -= A[i * R + k] * A[j * R + k];
-            A[i * R + j] = v / ljj;
-          }
-        }
-        if (st == CROM_OK) {
-          double y[16], xs[16];
-          for (int i = 0; i < r; ++i) {
-            double v = A[i * R + r];
-            for (int k = 0; k < i; ++k) v -= A[i * R + k] * y[k];
-            y[i] = v / A[i * R + i];
-          }
-          for (int i = r - 1; i >= 0; --i) {
-            double v = y[i];
-            for (int k = i + 1; k < r; ++k) v -= A[k * R + i] * xs[k];
-            xs[i] = v / A[i * R + i];
-          }
-          for (int i = 0; i < r; ++i) G->qcur[i] += xs[i];
-        }
-        G->s_status = st;
+      group_sync(c.g);
+      if (c.gw == 0) {
+        const int st = chol_solve_warp(G->amat, G->invd, r, c.gt);
+        if (st == CROM_OK && c.gt < r) G->qcur[c.gt] += G->amat[c.gt * R + r];
+        if (c.gt == 0) G->s_status = st;
       }
-      group_sync(g);
+      group_sync(c.g);
       if (G->s_status != CROM_OK) break;
     }  // GN iterations
     if (!ok) break;
-    if (gt < r) p.q[(size_t)inst * r + gt] = G->qcur[gt];
-    if (gt == 0) p.status[inst] = G->s_status;
+    if (c.gt < r) p.q[(size_t)inst * r + c.gt] = G->qcur[c.gt];
+    if (c.gt == 0) p.status[inst] = G->s_status;
   }
-  if (!ok && gt == 0) atomicExch(&p.queue[1], 1);
+  if (!ok && c.gt == 0) atomicExch(&p.queue[1], 1);
   tc_fence_before();
   __syncthreads();
   if (tid < 32) tmem_dealloc(S->tmem_base, kTmemCols);
@@ -622,7 +679,6 @@ cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst
   p.img = ctx->w.tc_img;
   p.img_bytes = (int)ctx->w.tc_img_bytes;
   p.L = ctx->desc.hidden;
-  p.m = ctx->desc.m;
   p.r = ctx->desc.r;
   p.w1 = ctx->w.w1;
   p.b1 = ctx->w.b1;
@@ -644,10 +700,16 @@ cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst
   p.queue = ctx->queue;
   p.df = ctx->targets;
   const size_t smem = tc_step_smem_bytes(p.img_bytes);
-  e = cudaFuncSetAttribute(step_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   const int grid = std::min((n_inst + kGroups - 1) / kGroups, ctx->num_sms);
-  step_tc_kernel<<<grid, kThreads, smem, s>>>(p);
+  if (ctx->desc.m == 2) {
+    e = cudaFuncSetAttribute(step_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    step_tc_kernel<2><<<grid, kThreads, smem, s>>>(p);
+  } else {
+    e = cudaFuncSetAttribute(step_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    step_tc_kernel<1><<<grid, kThreads, smem, s>>>(p);
+  }
   return cudaGetLastError();
 }
 
