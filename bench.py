@@ -40,7 +40,7 @@ WORKLOAD = "heat2d_batched_1024inst_M32-512_r8_w128_L5_gn2"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--n-inst", type=int, default=1024)

@@ -2,13 +2,16 @@
 // (paper Algorithm 2, App. E.1.1, extended to second order), used by
 // crom_decode, FP32 crom_reconstruct and the plain FP32 crom_step.
 //
-// One CTA = one thread per hidden unit (blockDim = width) and a tile of S
+// One CTA = KS threads per hidden unit (blockDim = KS * width) and a tile of S
 // samples.  All channels of a (unit, sample) pair live in one thread, so the
 // ELU chain rule needs no communication:
 //   z = W h + b;  dz = W dh;  d2z = W d2h
 //   h = s(z);     dh = s'(z) dz;  d2h = s''(z) dz^2 + s'(z) d2z
 // The activations of the whole tile (width x S*C floats) sit in shared memory;
 // the transposed hidden matrices are read through L1 (coalesced in the unit index).
+// Each contraction over the width is split in KS slices (one per thread of a unit)
+// whose partial sums are added through shared memory, which shortens the serial
+// dependency chain of the small single-instance problems this path serves.
 //
 // The FP32 step spreads one instance over ceil(|M_i| / S) CTAs.  Each CTA forms
 // its partial normal equations sum_j J_j J_j^T and sum_j J_j rho_j in FP64 from
@@ -27,6 +30,7 @@ namespace {
 
 constexpr int kMaxM = 3;
 constexpr int kMaxR = 32;
+constexpr int kKSplit = 4;  // threads per hidden unit (width <= 256 -> <= 1024 threads)
 
 enum Mode { kModeDecode = 0, kModeRecon = 1, kModeStep = 2 };
 
@@ -97,10 +101,10 @@ __device__ __forceinline__ float elu_diff(float a, float d) {
 }
 
 // Apply the activation chain in place to row `row` (pre-activation channels of
-// one hidden unit for S samples).
-__device__ __forceinline__ void activate_row(float* row, const FwdParams& p) {
+// one hidden unit) for the samples s0, s0 + ds, ... < S.
+__device__ __forceinline__ void activate_row(float* row, const FwdParams& p, int sbeg, int ds) {
   const int C = p.C;
-  for (int s = 0; s < p.S; ++s) {
+  for (int s = sbeg; s < p.S; s += ds) {
     float* c = row + s * C;
     float s0, s1, s2;
     const float za = c[0];
@@ -138,8 +142,11 @@ __device__ int find_instance(const int* off, int n_inst, int point) {
 
 __global__ void fwd_fp32_kernel(FwdParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int u = threadIdx.x;
   const int W = p.width, S = p.S, C = p.C, LD = p.LD, m = p.m, r = p.r;
+  // KS threads per hidden unit: thread (u, ks) owns unit u and the ks-th slice of
+  // the K range of every contraction (and the samples s = ks mod KS elsewhere).
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int u = tid % W, ks = tid / W, KS = NT / W;
   const int NP = S * C;
   const int NPP = (NP + 15) & ~15;
 
@@ -151,6 +158,7 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
   double* dqs = Amat + r * (r + 1);                       // [r]: q^(k) - q_n
   float* xs = reinterpret_cast<float*>(dqs + r);          // [S][m]
   float* outv = xs + S * m;                               // [NPP]
+  float* red = outv + NPP;                                // [KS][W][16] split-K partial sums
   __shared__ int s_flag;
 
   // ---- which samples does this CTA own?
@@ -162,7 +170,7 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
     msz = __ldg(&p.off[inst + 1]) - o0;
     if (p.iter == 0) {
       if (msz < r || msz > p.max_samples) {
-        if (t == 0 && u == 0) p.status[inst] = CROM_ERR_INVALID_ARG;
+        if (t == 0 && tid == 0) p.status[inst] = CROM_ERR_INVALID_ARG;
         return;
       }
     } else if (p.status[inst] != CROM_OK) {
@@ -179,11 +187,11 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
   }
 
   // ---- stage coordinates and latent codes (padding samples repeat the first one)
-  for (int i = u; i < S * m; i += W) {
+  for (int i = tid; i < S * m; i += NT) {
     const int s = i / m, k = i % m;
     xs[i] = p.x[(size_t)(first + (s < ns ? s : 0)) * m + k];
   }
-  for (int i = u; i < S * r; i += W) {
+  for (int i = tid; i < S * r; i += NT) {
     const int s = i / r, j = i % r;
     int code;
     if (p.mode == kModeStep) code = inst;
@@ -192,8 +200,8 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
     qs[i] = (p.mode == kModeStep) ? p.qio[(size_t)code * r + j] : p.q[(size_t)code * r + j];
   }
   if (p.diff)
-    for (int j = u; j < r; j += W) dqs[j] = p.qio[(size_t)inst * r + j] - p.qbase[(size_t)inst * r + j];
-  for (int i = u; i < 2 * W * LD; i += W) Hin[i] = 0.f;  // zero both buffers incl. padding
+    for (int j = tid; j < r; j += NT) dqs[j] = p.qio[(size_t)inst * r + j] - p.qbase[(size_t)inst * r + j];
+  for (int i = tid; i < 2 * W * LD; i += NT) Hin[i] = 0.f;  // zero both buffers incl. padding
   __syncthreads();
 
   // ---- layer 1: pre-activation channels of unit u, then the activation chain
@@ -210,7 +218,7 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
     if (p.diff) {
       for (int j = 0; j < r; ++j) zd += (double)w1[m + j] * dqs[j];
     }
-    for (int s = 0; s < S; ++s) {
+    for (int s = ks; s < S; s += KS) {
       double c = cshared;
       if (!shared_q) {
         c = b1;
@@ -229,7 +237,7 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
       o += n2;
       for (int j = 0; j < p.nq; ++j) ch[o + j] = w1[m + j];
     }
-    activate_row(row, p);
+    activate_row(row, p, ks, KS);
   }
   __syncthreads();
 
@@ -237,13 +245,14 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
   for (int l = 0; l < p.hidden - 1; ++l) {
     const float* Wt = p.wt + (size_t)l * W * W;
     float* orow = Hout + u * LD;
+    const int kper = W / KS;
     for (int j0 = 0; j0 < NPP; j0 += 16) {
       float acc[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) acc[i] = 0.f;
       const float* hcol = Hin + j0;
 #pragma unroll 4
-      for (int k = 0; k < W; ++k) {
+      for (int k = ks * kper; k < (ks + 1) * kper; ++k) {
         const float wk = __ldg(&Wt[(size_t)k * W + u]);
         const float4* h4 = reinterpret_cast<const float4*>(hcol + k * LD);
         const float4 a = h4[0], b = h4[1], c = h4[2], d = h4[3];
@@ -256,18 +265,27 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
         acc[12] = fmaf(wk, d.x, acc[12]); acc[13] = fmaf(wk, d.y, acc[13]);
         acc[14] = fmaf(wk, d.z, acc[14]); acc[15] = fmaf(wk, d.w, acc[15]);
       }
+      // add the KS partial sums of unit u: thread (u, ks) finishes 16 / KS of the columns
+      float* mine = red + ((size_t)ks * W + u) * 16;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) orow[j0 + i] = acc[i];
+      for (int i = 0; i < 16; ++i) mine[i] = acc[i];
+      __syncthreads();
+      for (int i = ks * (16 / KS); i < (ks + 1) * (16 / KS); ++i) {
+        float v = 0.f;
+        for (int kk = 0; kk < KS; ++kk) v += red[((size_t)kk * W + u) * 16 + i];
+        orow[j0 + i] = v;
+      }
+      __syncthreads();
     }
     const float bias = p.bh[(size_t)l * W + u];
-    for (int s = 0; s < S; ++s) orow[s * C] += bias;
-    activate_row(orow, p);
+    for (int s = ks; s < S; s += KS) orow[s * C] += bias;
+    activate_row(orow, p, ks, KS);
     __syncthreads();
     float* tmp = Hin; Hin = Hout; Hout = tmp;
   }
 
   // ---- linear output layer: one thread per (sample, channel) column
-  for (int t = u; t < NP; t += W) {
+  for (int t = tid; t < NP; t += NT) {
     float acc = 0.f;
     for (int k = 0; k < W; ++k) acc = fmaf(__ldg(&p.wout[k]), Hin[k * LD + t], acc);
     if (t % C == 0) acc += p.bout;
@@ -276,13 +294,13 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
   __syncthreads();
 
   if (p.mode == kModeRecon) {
-    if (u < ns) p.out[(size_t)blockIdx.y * p.n_pts + first + u] = outv[u * C];
+    if (tid < ns) p.out[(size_t)blockIdx.y * p.n_pts + first + tid] = outv[tid * C];
     return;
   }
   const int n2 = (p.second == kSecondPerK) ? m : (p.second == kSecondLap ? 1 : 0);
   const int ox = 1 + p.diff, o2 = ox + p.nx, oq = o2 + n2;
   if (p.mode == kModeDecode) {
-    for (int s = u; s < ns; s += W) {
+    for (int s = tid; s < ns; s += NT) {
       const float* c = outv + s * C;
       const size_t N = (size_t)p.n_pts, pt = (size_t)(first + s);
       int row = 0;
@@ -304,7 +322,7 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
 
   // ---- step: residual per sample (Step 2 at iteration 0), partial normal equations
   const int t = blockIdx.y;
-  for (int s = u; s < S; s += W) {
+  for (int s = tid; s < S; s += NT) {
     double res = 0.0;
     if (s < ns) {
       const float* c = outv + s * C;
@@ -331,7 +349,7 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
   }
   __syncthreads();
   double* part = p.partials + ((size_t)inst * p.max_tiles + t) * p.n_entries;
-  for (int e = u; e < p.n_entries; e += W) {
+  for (int e = tid; e < p.n_entries; e += NT) {
     const int ntri = r * (r + 1) / 2;
     double acc = 0.0;
     if (e < ntri) {
@@ -348,7 +366,7 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
   }
   __threadfence();
   __syncthreads();
-  if (u == 0) {
+  if (tid == 0) {
     const int ticket = atomicAdd(&p.counters[inst], 1);
     s_flag = (ticket == ntiles - 1);
   }
@@ -358,7 +376,7 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
 
   // ---- last CTA of the instance: reduce partials in tile order, solve, update q
   const double* base = p.partials + (size_t)inst * p.max_tiles * p.n_entries;
-  for (int e = u; e < p.n_entries; e += W) {
+  for (int e = tid; e < p.n_entries; e += NT) {
     double acc = 0.0;
     for (int tt = 0; tt < ntiles; ++tt) acc += __ldcg(&base[(size_t)tt * p.n_entries + e]);
     const int ntri = r * (r + 1) / 2;
@@ -373,7 +391,7 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
     }
   }
   __syncthreads();
-  if (u == 0) {
+  if (tid == 0) {
     int st = CROM_OK;
     double dmax = 0.0;
     for (int a = 0; a < r && st == CROM_OK; ++a)
@@ -425,6 +443,7 @@ size_t fwd_smem_bytes(int W, int S, int C, int m, int r, int* LD_out) {
   b += (size_t)S * r * sizeof(double) + (size_t)S * sizeof(double) + (size_t)r * (r + 1) * sizeof(double) +
        (size_t)r * sizeof(double);
   b += (size_t)S * m * sizeof(float) + (size_t)NPP * sizeof(float);
+  b += (size_t)kKSplit * W * 16 * sizeof(float);  // split-K partial sums
   return b + 64;
 }
 
@@ -435,7 +454,7 @@ cudaError_t launch_fwd(FwdParams& p, dim3 grid, cudaStream_t s) {
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  fwd_fp32_kernel<<<grid, p.width, smem, s>>>(p);
+  fwd_fp32_kernel<<<grid, p.width * kKSplit, smem, s>>>(p);
   return cudaGetLastError();
 }
 

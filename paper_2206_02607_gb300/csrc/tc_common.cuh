@@ -196,6 +196,58 @@ __device__ __forceinline__ uint32_t mn_offset(int k, int n) {
   return (uint32_t)((n >> 6) * 16384 + k * 128 + ((((n & 63) >> 3) ^ (k & 7)) << 4) + (n & 7) * 2);
 }
 
+// ------------------------------------------------------------------ packed FP32 pairs
+// Two floats in one 64-bit register pair, processed by the f32x2 instructions of
+// sm_100-family cores (one instruction for both lanes of the pair).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpk2(f32x2 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+// 2^x by the hardware approximation (relative error ~2^-22, flushes subnormals).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// ELU of a pair, h = max(z, 0) + (e^{min(z, 0)} - 1), and e = e^{min(z, 0)}
+// (= s'(z) for z <= 0, 1 otherwise), using e^x = 2^(x log2 e).
+__device__ __forceinline__ f32x2 elu2(f32x2 z, float& e0, float& e1) {
+  float z0, z1;
+  unpk2(z, z0, z1);
+  const f32x2 t = mul2(pk2(fminf(z0, 0.f), fminf(z1, 0.f)), pk2(1.4426950408889634f, 1.4426950408889634f));
+  float t0, t1;
+  unpk2(t, t0, t1);
+  e0 = ex2_approx(t0);
+  e1 = ex2_approx(t1);
+  return add2(pk2(fmaxf(z0, 0.f), fmaxf(z1, 0.f)), add2(pk2(e0, e1), pk2(-1.f, -1.f)));
+}
+
 // Pack two floats into bf16x2 (round to nearest even); low half = a.
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);

@@ -92,13 +92,20 @@ __device__ __forceinline__ bool group_sync_and(int g, bool pred) {
   return r != 0;
 }
 
+// Sixteen consecutive columns n0..n0+15 of row k, given as 8 packed pairs, stored as
+// bf16 hi (and lo = bf16(h - hi) when kSplit) operand parts.
 template <int kSplit>
-__device__ __forceinline__ void store_split16(uint8_t* Hhi, uint8_t* Hlo, int k, int n0, const float (&v)[16]) {
+__device__ __forceinline__ void store_split16(uint8_t* Hhi, uint8_t* Hlo, int k, int n0, const f32x2 (&h)[8]) {
   uint32_t hi[8], lo[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    hi[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
-    if (kSplit) lo[j] = pack_bf16(v[2 * j] - bf16_lo_f(hi[j]), v[2 * j + 1] - bf16_hi_f(hi[j]));
+    float a, b;
+    unpk2(h[j], a, b);
+    hi[j] = pack_bf16(a, b);
+    if (kSplit) {
+      unpk2(sub2(h[j], pk2(bf16_lo_f(hi[j]), bf16_hi_f(hi[j]))), a, b);
+      lo[j] = pack_bf16(a, b);
+    }
   }
   *reinterpret_cast<uint4*>(Hhi + mn_offset(k, n0)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
   *reinterpret_cast<uint4*>(Hhi + mn_offset(k, n0 + 8)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
@@ -107,8 +114,6 @@ __device__ __forceinline__ void store_split16(uint8_t* Hhi, uint8_t* Hlo, int k,
     *reinterpret_cast<uint4*>(Hlo + mn_offset(k, n0 + 8)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
   }
 }
-
-__device__ __forceinline__ float elu(float z) { return z > 0.f ? z : __expf(z) - 1.f; }
 
 template <int kSplit>
 __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
@@ -187,14 +192,15 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
     // ---- layer 1 on CUDA cores
 #pragma unroll 1
     for (int n0 = nbeg; n0 < nbeg + kTileN / 2; n0 += 16) {
-      float v[16];
+      f32x2 h[8];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        float z = fmaf(wx0, G->xs[0][n0 + i], c);
-        if (m > 1) z = fmaf(wx1, G->xs[1][n0 + i], z);
-        v[i] = elu(z);
+      for (int j = 0; j < 8; ++j) {
+        f32x2 z = fma2(pk2(wx0, wx0), pk2(G->xs[0][n0 + 2 * j], G->xs[0][n0 + 2 * j + 1]), pk2(c, c));
+        if (m > 1) z = fma2(pk2(wx1, wx1), pk2(G->xs[1][n0 + 2 * j], G->xs[1][n0 + 2 * j + 1]), z);
+        float e0, e1;
+        h[j] = elu2(z, e0, e1);
       }
-      store_split16<kSplit>(Hhi, Hlo, u, n0, v);
+      store_split16<kSplit>(Hhi, Hlo, u, n0, h);
     }
     // ---- hidden layers and the output layer on the tensor cores
     for (int l = 0; l <= p.n_hidden_mats; ++l) {
@@ -238,9 +244,14 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
           float v[16];
           tmem_ld16(taddr(tb, lane_base, kAccCol + n0), v);
           tmem_ld_wait();
+          f32x2 h[8];
+          const f32x2 b2 = pk2(bias, bias);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] = elu(v[i] + bias);
-          store_split16<kSplit>(Hhi, Hlo, u, n0, v);
+          for (int j = 0; j < 8; ++j) {
+            float e0, e1;
+            h[j] = elu2(add2(pk2(v[2 * j], v[2 * j + 1]), b2), e0, e1);
+          }
+          store_split16<kSplit>(Hhi, Hlo, u, n0, h);
         }
       } else if (half == 0) {
         float v[16];

@@ -140,7 +140,9 @@ __device__ __forceinline__ void split_store8(uint8_t* Hhi, uint8_t* Hlo, int k, 
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     hi[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
-    lo[j] = pack_bf16(v[2 * j] - bf16_lo_f(hi[j]), v[2 * j + 1] - bf16_hi_f(hi[j]));
+    float a, b;
+    unpk2(sub2(pk2(v[2 * j], v[2 * j + 1]), pk2(bf16_lo_f(hi[j]), bf16_hi_f(hi[j]))), a, b);
+    lo[j] = pack_bf16(a, b);
   }
   const uint32_t off = mn_offset(k, n0);
   *reinterpret_cast<uint4*>(Hhi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
@@ -165,6 +167,43 @@ __device__ __forceinline__ float elu_diff(float a, float d, float e) {
   const float sa = a > 0.f ? a : expm1f(a);
   const float sb = b > 0.f ? b : expm1f(b);
   return sa - sb;
+}
+
+// Forward activation chain of 8 samples of one hidden unit, in place, on packed
+// pairs.  v[0] holds the value channel's pre-activation z (bias included); at
+// iteration 0 v[1..m] the gradient channels dz/dx_k and v[kCh-1] the Laplacian
+// channel; later v[1] the difference channel.  sg receives s'(z).
+//   h = s(z); dh/dx_k = s'(z) dz/dx_k; Lap h = s''(z) sum_k (dz/dx_k)^2 + s'(z) Lap z.
+template <int kM, bool kFirst, int kCh>
+__device__ __forceinline__ void act8(float (&v)[kCh][8], float (&sg)[8]) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int i0 = 2 * j, i1 = 2 * j + 1;
+    const float z0 = v[0][i0], z1 = v[0][i1];
+    float e0, e1;
+    const f32x2 h = elu2(pk2(z0, z1), e0, e1);
+    const float s10 = z0 > 0.f ? 1.f : e0, s11 = z1 > 0.f ? 1.f : e1;
+    sg[i0] = s10;
+    sg[i1] = s11;
+    unpk2(h, v[0][i0], v[0][i1]);
+    if (kFirst) {
+      const f32x2 s1 = pk2(s10, s11);
+      const f32x2 s2 = pk2(z0 > 0.f ? 0.f : e0, z1 > 0.f ? 0.f : e1);
+      const f32x2 a = pk2(v[1][i0], v[1][i1]);
+      f32x2 sq = mul2(a, a);
+      unpk2(mul2(s1, a), v[1][i0], v[1][i1]);
+      if (kM > 1) {
+        const f32x2 b = pk2(v[2][i0], v[2][i1]);
+        sq = fma2(b, b, sq);
+        unpk2(mul2(s1, b), v[2][i0], v[2][i1]);
+      }
+      const f32x2 lz = pk2(v[kCh - 1][i0], v[kCh - 1][i1]);
+      unpk2(fma2(s2, sq, mul2(s1, lz)), v[kCh - 1][i0], v[kCh - 1][i1]);
+    } else {
+      v[1][i0] = elu_diff(z0, v[1][i0], e0);
+      v[1][i1] = elu_diff(z1, v[1][i1], e1);
+    }
+  }
 }
 
 // D(+)= A * B^T over K = 128 with the B operand as hi + lo parts.  a0: descriptor
@@ -275,24 +314,23 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
     const float cc = G->c1[u], dz = G->dz1[u];
 #pragma unroll
     for (int h8 = 0; h8 < kHalf; h8 += 8) {
+      // layer-1 pre-activation channels: z = W_1x x + W_1q q + b_1, dz/dx_k = W_1[:, k],
+      // Laplacian 0; later iterations: the difference channel's W_1q (q^(k) - q_n)
       float v[kCh][8], sg[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         float z = fmaf(c.wx0, G->xs[0][s0 + h8 + i], cc);
         if (kM > 1) z = fmaf(c.wx1, G->xs[1][s0 + h8 + i], z);
-        const float e = __expf(fminf(z, 0.f));
-        const bool pos = z > 0.f;
-        const float s1 = pos ? 1.f : e, s2 = pos ? 0.f : e;
-        sg[i] = s1;
-        v[0][i] = pos ? z : e - 1.f;
+        v[0][i] = z;
         if (kFirst) {
-          v[1][i] = s1 * c.wx0;
-          if (kM > 1) v[2][i] = s1 * c.wx1;
-          v[kCh - 1][i] = s2 * c.wsq;
+          v[1][i] = c.wx0;
+          if (kM > 1) v[2][i] = c.wx1;
+          v[kCh - 1][i] = 0.f;
         } else {
-          v[1][i] = elu_diff(z, dz, e);
+          v[1][i] = dz;
         }
       }
+      act8<kM, kFirst, kCh>(v, sg);
       tmem_st8(taddr(tb, lb, kSig + s0 + h8), sg);
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) split_store8(c.Hhi, c.Hlo, u, ch * kSm + s0 + h8, v[ch]);
@@ -311,23 +349,8 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
       for (int ch = 0; ch < kCh; ++ch) tmem_ld8(taddr(tb, lb, kAcc + ch * kSm + s0 + h8), v[ch]);
       tmem_ld_wait();
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float z = v[0][i] + bias;
-        const float e = __expf(fminf(z, 0.f));
-        const bool pos = z > 0.f;
-        const float s1 = pos ? 1.f : e, s2 = pos ? 0.f : e;
-        sg[i] = s1;
-        v[0][i] = pos ? z : e - 1.f;
-        if (kFirst) {
-          const float a = v[1][i];
-          const float b = (kM > 1) ? v[2][i] : 0.f;
-          v[1][i] = s1 * a;
-          if (kM > 1) v[2][i] = s1 * b;
-          v[kCh - 1][i] = fmaf(s2, fmaf(a, a, b * b), s1 * v[kCh - 1][i]);
-        } else {
-          v[1][i] = elu_diff(z, v[1][i], e);
-        }
-      }
+      for (int i = 0; i < 8; i += 2) unpk2(add2(pk2(v[0][i], v[0][i + 1]), pk2(bias, bias)), v[0][i], v[0][i + 1]);
+      act8<kM, kFirst, kCh>(v, sg);
       tmem_st8(taddr(tb, lb, kSig + (l + 1) * kSm + s0 + h8), sg);
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) split_store8(c.Hhi, c.Hlo, u, ch * kSm + s0 + h8, v[ch]);
