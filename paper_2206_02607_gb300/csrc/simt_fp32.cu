@@ -24,6 +24,7 @@
 #include <mutex>
 
 #include "crom_internal.h"
+#include "linalg.cuh"
 
 namespace crom {
 namespace {
@@ -158,7 +159,8 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
   double* dqs = Amat + r * (r + 1);                       // [r]: q^(k) - q_n
   float* xs = reinterpret_cast<float*>(dqs + r);          // [S][m]
   float* outv = xs + S * m;                               // [NPP]
-  float* red = outv + NPP;                                // [KS][W][16] split-K partial sums
+  // [KS][W][16] split-K partial sums (16-byte aligned: also reused as doubles)
+  float* red = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(outv + NPP) + 15) & ~uintptr_t(15));
   __shared__ int s_flag;
 
   // ---- which samples does this CTA own?
@@ -374,11 +376,23 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
   if (!s_flag) return;
   __threadfence();
 
-  // ---- last CTA of the instance: reduce partials in tile order, solve, update q
+  // ---- last CTA of the instance: reduce partials in a fixed order, solve, update q
+  // (thread (j, e) adds the tiles j, j + per, ... of entry e; then the per partial
+  // sums of each entry are added in order).
   const double* base = p.partials + (size_t)inst * p.max_tiles * p.n_entries;
-  for (int e = tid; e < p.n_entries; e += NT) {
+  const int ne = p.n_entries;
+  const int per = NT >= ne ? NT / ne : 1;
+  double* red2 = reinterpret_cast<double*>(red);  // [per][ne]
+  for (int idx = tid; idx < per * ne; idx += NT) {
+    const int e = idx % ne, j = idx / ne;
     double acc = 0.0;
-    for (int tt = 0; tt < ntiles; ++tt) acc += __ldcg(&base[(size_t)tt * p.n_entries + e]);
+    for (int tt = j; tt < ntiles; tt += per) acc += __ldcg(&base[(size_t)tt * ne + e]);
+    red2[(size_t)j * ne + e] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < ne; e += NT) {
+    double acc = 0.0;
+    for (int j = 0; j < per; ++j) acc += red2[(size_t)j * ne + e];
     const int ntri = r * (r + 1) / 2;
     if (e < ntri) {
       int a = 0, rem = e;
@@ -391,46 +405,18 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
     }
   }
   __syncthreads();
-  if (tid == 0) {
-    int st = CROM_OK;
-    double dmax = 0.0;
-    for (int a = 0; a < r && st == CROM_OK; ++a)
-      for (int b = 0; b <= r; ++b)
-        if (!isfinite(Amat[a * (r + 1) + b])) st = CROM_ERR_NONFINITE;
-    for (int a = 0; a < r; ++a) dmax = fmax(dmax, Amat[a * (r + 1) + a]);
-    // Cholesky A = L L^T in place (lower triangle), then forward/back substitution.
-    const double tol = 1e-14 * dmax;
-    for (int j = 0; j < r && st == CROM_OK; ++j) {
-      double d = Amat[j * (r + 1) + j];
-      for (int k = 0; k < j; ++k) d -= Amat[j * (r + 1) + k] * Amat[j * (r + 1) + k];
-      if (!(d > tol)) { st = CROM_ERR_SINGULAR; break; }
-      const double ljj = sqrt(d);
-      Amat[j * (r + 1) + j] = ljj;
-      for (int i = j + 1; i < r; ++i) {
-        double v = Amat[i * (r + 1) + j];
-        for (int k = 0; k < j; ++k) v -= Amat[i * (r + 1) + k] * Amat[j * (r + 1) + k];
-        Amat[i * (r + 1) + j] = v / ljj;
-      }
+  if (tid < 32) {
+    // Cholesky A = L L^T and the two triangular solves, spread over one warp
+    __shared__ double s_invd[kMaxR];
+    const int st = chol_solve_warp(Amat, s_invd, r, tid);
+    if (st == CROM_OK && tid < r) {
+      if (p.iter == 0) p.qbase[(size_t)inst * r + tid] = p.qio[(size_t)inst * r + tid];
+      p.qio[(size_t)inst * r + tid] += Amat[tid * (r + 1) + r];
     }
-    if (st == CROM_OK) {
-      double y[kMaxR], xsol[kMaxR];
-      for (int i = 0; i < r; ++i) {
-        double v = Amat[i * (r + 1) + r];
-        for (int k = 0; k < i; ++k) v -= Amat[i * (r + 1) + k] * y[k];
-        y[i] = v / Amat[i * (r + 1) + i];
-      }
-      for (int i = r - 1; i >= 0; --i) {
-        double v = y[i];
-        for (int k = i + 1; k < r; ++k) v -= Amat[k * (r + 1) + i] * xsol[k];
-        xsol[i] = v / Amat[i * (r + 1) + i];
-      }
-      for (int i = 0; i < r; ++i) {
-        if (p.iter == 0) p.qbase[(size_t)inst * r + i] = p.qio[(size_t)inst * r + i];
-        p.qio[(size_t)inst * r + i] += xsol[i];
-      }
+    if (tid == 0) {
+      p.status[inst] = st;
+      p.counters[inst] = 0;
     }
-    p.status[inst] = st;
-    p.counters[inst] = 0;
   }
 }
 

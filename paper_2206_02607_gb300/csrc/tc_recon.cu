@@ -10,7 +10,8 @@
 //     W_1 [x; q] + b_1 is hoisted per code; h = ELU(W_1x x + c);
 //   layers 2..L: D[u][n] = sum_k W_l[u][k] H[k][n] by UMMA (M = 128 units,
 //     N = 64 points, K = 128), A = W_l (K-major, resident), B = H (MN-major,
-//     written by the previous epilogue); epilogue: bias, ELU, bf16 split, store;
+//     written by the previous epilogue; the hi and lo parts side by side as one
+//     N = 128 operand, added in the epilogue); epilogue: bias, ELU, bf16 split, store;
 //   output: D[n][0] = sum_u H_L[u][n] w_out[u] by one more UMMA (M = 128 rows
 //     of which the 64 points are used, N = 16 rows of the projection matrix).
 // Precision: each activation operand h is stored as hi = bf16(h) and
@@ -32,10 +33,10 @@ constexpr int kGroups = 2;
 constexpr int kGT = 256;  // two threads per TMEM lane, each half of the tile's points
 constexpr int kThreads = kGroups * kGT;
 constexpr int kTileN = 64;
-constexpr uint32_t kTmemCols = 256;
-constexpr uint32_t kGroupCols = 128;
-constexpr uint32_t kAccCol = 0;
-constexpr uint32_t kOutCol = 64;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kGroupCols = 256;
+constexpr uint32_t kAccCol = 0;    // W h_hi in columns 0..63, W h_lo in 64..127
+constexpr uint32_t kOutCol = 128;
 constexpr uint32_t kWaitLimit = 1u << 25;
 constexpr size_t kHBuf = (size_t)kTcWidth * kTileN * 2;  // one bf16 operand buffer, 16 KB
 
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
   const uint64_t dP = smem_desc_sw128(wbase + (uint32_t)p.n_hidden_mats * kTcLayerBytes, 16, 1024);
   const uint64_t dHhi = smem_desc_sw128(smem_u32(Hhi), 16384, 1024);
   const uint64_t dHlo = smem_desc_sw128(smem_u32(Hlo), 16384, 1024);
-  constexpr uint32_t id_layer = idesc_f16(128, kTileN, false, true, true);
+  constexpr uint32_t id_layer = idesc_f16(128, kSplit ? 2 * kTileN : kTileN, false, true, true);
   constexpr uint32_t id_out = idesc_f16(128, 16, true, false, true);
   int cur_code = -1;
   float c = 0.f;
@@ -213,13 +214,14 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
         if (gt == 0) {
           tc_fence_after();
           if (!last) {
+            // The lo buffer follows the hi buffer at the operand's 64-column block
+            // stride, so one UMMA with N = 128 multiplies both parts at once: columns
+            // 0..63 of the accumulator get W h_hi, columns 64..127 get W h_lo.
             const uint64_t a0 = desc_add(dW, (uint32_t)l * kTcLayerBytes);
 #pragma unroll
-            for (int part = 0; part <= kSplit; ++part)
-#pragma unroll
-              for (int kk = 0; kk < 8; ++kk)
-                umma_f16(tb + kAccCol, desc_add(a0, kmajor_kslice(128, kk)),
-                         desc_add(part ? dHlo : dHhi, mnmajor_kslice(kk)), id_layer, (part | kk) != 0);
+            for (int kk = 0; kk < 8; ++kk)
+              umma_f16(tb + kAccCol, desc_add(a0, kmajor_kslice(128, kk)), desc_add(dHhi, mnmajor_kslice(kk)),
+                       id_layer, kk != 0);
           } else {
 #pragma unroll
             for (int part = 0; part <= kSplit; ++part)
@@ -241,15 +243,18 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
         const float bias = S->bh[l][u];
 #pragma unroll 1
         for (int n0 = nbeg; n0 < nbeg + kTileN / 2; n0 += 16) {
-          float v[16];
+          float v[16], w[16];
           tmem_ld16(taddr(tb, lane_base, kAccCol + n0), v);
+          if (kSplit) tmem_ld16(taddr(tb, lane_base, kAccCol + kTileN + n0), w);
           tmem_ld_wait();
           f32x2 h[8];
           const f32x2 b2 = pk2(bias, bias);
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             float e0, e1;
-            h[j] = elu2(add2(pk2(v[2 * j], v[2 * j + 1]), b2), e0, e1);
+            f32x2 z = add2(pk2(v[2 * j], v[2 * j + 1]), b2);
+            if (kSplit) z = add2(z, pk2(w[2 * j], w[2 * j + 1]));
+            h[j] = elu2(z, e0, e1);
           }
           store_split16<kSplit>(Hhi, Hlo, u, n0, h);
         }

@@ -39,6 +39,7 @@
 #include <algorithm>
 
 #include "crom_internal.h"
+#include "linalg.cuh"
 #include "tc_common.cuh"
 
 namespace crom {
@@ -54,8 +55,11 @@ constexpr int kS1 = 32;                  // samples per tile at later iterations
 constexpr int kSMax = 32;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kGroupCols = 256;     // TMEM columns per group
-constexpr uint32_t kAcc = 0;             // accumulator, up to 64 columns
-constexpr uint32_t kSig = 64;            // s'(z_l), l = 1..L (<= 5): kS columns each (<= 160)
+constexpr uint32_t kAcc = 0;             // accumulator, up to 128 columns
+// s'(z_l), l = 1..L (<= 5), kS columns each: from column 128 at iteration 0 (the
+// accumulator then holds W h_hi in 0..63 and W h_lo in 64..127), from 64 later.
+constexpr uint32_t kSig0 = 128;
+constexpr uint32_t kSig1 = 64;
 constexpr uint32_t kPrj = 224;           // projection output, 16 columns
 constexpr uint32_t kWaitLimit = 1u << 25;
 constexpr size_t kHBuf = (size_t)kTcWidth * 64 * 2;  // one bf16 operand buffer (<= 64 columns), 16 KB
@@ -220,6 +224,14 @@ __device__ __forceinline__ void issue_layer(uint32_t d, uint64_t a0, uint64_t bh
     umma_f16(d, desc_add(a0, kAMN ? mnmajor_kslice(kk) : kmajor_kslice(128, kk)), desc_add(blo, mnmajor_kslice(kk)),
              idesc, 1);
 }
+// D = A * [B_hi | B_lo]^T over K = 128: the lo buffer follows the hi buffer at the
+// MN-major operand's 64-column block stride, so one N = 128 UMMA per K slice
+// covers both parts (W h_hi lands in accumulator columns 0..63, W h_lo in 64..127).
+__device__ __forceinline__ void issue_cat(uint32_t d, uint64_t a0, uint64_t bhi, uint32_t idesc) {
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk)
+    umma_f16(d, desc_add(a0, kmajor_kslice(128, kk)), desc_add(bhi, mnmajor_kslice(kk)), idesc, kk > 0);
+}
 // PRJ[n][j] = sum_u H[u][n] P[j][u] with H (MN-major A) as the hi + lo parts.
 __device__ __forceinline__ void issue_proj(uint32_t d, uint64_t ahi, uint64_t alo, uint64_t p0) {
   constexpr uint32_t id = idesc_f16(128, 16, true, false, true);
@@ -247,7 +259,7 @@ struct Lane {
 // One UMMA stage of the group: fence the epilogue's shared-memory writes, meet,
 // one thread issues and commits, the first warp waits on the mbarrier, the rest at
 // the group barrier.  Returns the group-uniform completion flag.
-enum StageKind { kStageFwd = 0, kStageBwd = 1, kStageProj = 2 };
+enum StageKind { kStageFwd = 0, kStageBwd = 1, kStageProj = 2, kStageFwdCat = 3 };
 template <StageKind kKind>
 __device__ __forceinline__ bool stage(Lane& c, int layer, uint32_t idesc) {
   fence_proxy_async_smem();
@@ -257,7 +269,9 @@ __device__ __forceinline__ bool stage(Lane& c, int layer, uint32_t idesc) {
   if (c.gw == 0) {
     if (c.gt == 0) {
       tc_fence_after();
-      if (kKind == kStageFwd)
+      if (kKind == kStageFwdCat)  // hi and lo parts side by side as one N = 2 x 64 operand
+        issue_cat(c.tb + kAcc, desc_add(c.dW_k, (uint32_t)layer * kTcLayerBytes), c.dHhi, idesc);
+      else if (kKind == kStageFwd)
         issue_layer<false>(c.tb + kAcc, desc_add(c.dW_k, (uint32_t)layer * kTcLayerBytes), c.dHhi, c.dHlo, idesc);
       else if (kKind == kStageBwd)
         issue_layer<true>(c.tb + kAcc, desc_add(c.dW_mn, (uint32_t)layer * kTcLayerBytes), c.dHhi, c.dHlo, idesc);
@@ -299,6 +313,7 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
   constexpr int kCh = kFirst ? 2 + kM : 2;  // iteration 0: v, dx_1..dx_m, Lap; later: v(q^(k)), diff
   constexpr int kN = kCh * kSm;
   constexpr int kHalf = kSm / 2;            // samples of this thread
+  constexpr uint32_t kSigB = kFirst ? kSig0 : kSig1;
   static_assert(kN <= 64 && kHalf % 8 == 0, "tile shape");
   Group* G = c.G;
   const Shared* S = c.S;
@@ -331,27 +346,38 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
         }
       }
       act8<kM, kFirst, kCh>(v, sg);
-      tmem_st8(taddr(tb, lb, kSig + s0 + h8), sg);
+      tmem_st8(taddr(tb, lb, kSigB + s0 + h8), sg);
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) split_store8(c.Hhi, c.Hlo, u, ch * kSm + s0 + h8, v[ch]);
     }
     tmem_st_wait();
   }
   // ---------------- hidden layers 2..L (tensor cores)
-  constexpr uint32_t id_fwd = idesc_f16(128, kN, false, true, true);
+  constexpr uint32_t id_fwd = idesc_f16(128, kFirst ? 128 : kN, false, true, true);
   for (int l = 0; l < p.L - 1; ++l) {
-    if (!stage<kStageFwd>(c, l, id_fwd)) return false;
+    if (!stage<kFirst ? kStageFwdCat : kStageFwd>(c, l, id_fwd)) return false;
     const float bias = S->bh[l][u];
 #pragma unroll
     for (int h8 = 0; h8 < kHalf; h8 += 8) {
       float v[kCh][8], sg[8];
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) tmem_ld8(taddr(tb, lb, kAcc + ch * kSm + s0 + h8), v[ch]);
+      if (kFirst) {  // add W h_lo
+        float w[kCh][8];
+#pragma unroll
+        for (int ch = 0; ch < kCh; ++ch) tmem_ld8(taddr(tb, lb, kAcc + 64 + ch * kSm + s0 + h8), w[ch]);
+        tmem_ld_wait();
+#pragma unroll
+        for (int ch = 0; ch < kCh; ++ch)
+#pragma unroll
+          for (int i = 0; i < 8; i += 2)
+            unpk2(add2(pk2(v[ch][i], v[ch][i + 1]), pk2(w[ch][i], w[ch][i + 1])), v[ch][i], v[ch][i + 1]);
+      }
       tmem_ld_wait();
 #pragma unroll
       for (int i = 0; i < 8; i += 2) unpk2(add2(pk2(v[0][i], v[0][i + 1]), pk2(bias, bias)), v[0][i], v[0][i + 1]);
       act8<kM, kFirst, kCh>(v, sg);
-      tmem_st8(taddr(tb, lb, kSig + (l + 1) * kSm + s0 + h8), sg);
+      tmem_st8(taddr(tb, lb, kSigB + (l + 1) * kSm + s0 + h8), sg);
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) split_store8(c.Hhi, c.Hlo, u, ch * kSm + s0 + h8, v[ch]);
     }
@@ -393,7 +419,7 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
 #pragma unroll
   for (int h8 = 0; h8 < kHalf; h8 += 8) {
     float sg[8];
-    tmem_ld8(taddr(tb, lb, kSig + (p.L - 1) * kSm + s0 + h8), sg);
+    tmem_ld8(taddr(tb, lb, kSigB + (p.L - 1) * kSm + s0 + h8), sg);
     tmem_ld_wait();
 #pragma unroll
     for (int i = 0; i < 8; ++i) sg[i] *= c.wo;
@@ -407,7 +433,7 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
     for (int h8 = 0; h8 < kHalf; h8 += 8) {
       float v[8], sg[8];
       tmem_ld8(taddr(tb, lb, kAcc + s0 + h8), v);
-      tmem_ld8(taddr(tb, lb, kSig + l * kSm + s0 + h8), sg);
+      tmem_ld8(taddr(tb, lb, kSigB + l * kSm + s0 + h8), sg);
       tmem_ld_wait();
 #pragma unroll
       for (int i = 0; i < 8; ++i) v[i] *= sg[i];
@@ -429,52 +455,6 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
   // ---------------- this tile's normal-equation terms
   if (ea >= 0) acc += dot_exact(&G->jt[0][ea], 16, eb >= 0 ? &G->jt[0][eb] : G->rho, eb >= 0 ? 16 : 1, ns);
   return true;
-}
-
-// Warp-parallel FP64 Cholesky solve of A x = b with A = amat[a*(r+1)+b] and b in
-// column r (right-looking: lane i owns row i).  Returns the status; on success
-// x_k is left in amat[k*(r+1)+r].
-__device__ int chol_solve_warp(double* A, double* invd, int r, int lane) {
-  const int R = r + 1;
-  bool bad = false;
-  for (int e = lane; e < r * R; e += 32) bad |= !isfinite(A[e]);
-  if (__any_sync(0xffffffffu, bad)) return CROM_ERR_NONFINITE;
-  double dmax = 0.0;
-  for (int a = 0; a < r; ++a) dmax = fmax(dmax, A[a * R + a]);
-  const double tol = 1e-14 * dmax;
-  for (int j = 0; j < r; ++j) {
-    const double d = A[j * R + j];
-    if (!(d > tol)) return CROM_ERR_SINGULAR;
-    const double ljj = sqrt(d);
-    const double inv = 1.0 / ljj;
-    __syncwarp();
-    if (lane == 0) {
-      A[j * R + j] = ljj;
-      invd[j] = inv;
-    }
-    if (lane > j && lane < r) A[lane * R + j] *= inv;
-    __syncwarp();
-    if (lane > j && lane < r) {
-      const double lij = A[lane * R + j];
-      for (int k = j + 1; k <= lane; ++k) A[lane * R + k] -= lij * A[k * R + j];
-    }
-    __syncwarp();
-  }
-  for (int k = 0; k < r; ++k) {  // L y = b
-    const double yk = A[k * R + r] * invd[k];
-    __syncwarp();
-    if (lane == 0) A[k * R + r] = yk;
-    if (lane > k && lane < r) A[lane * R + r] -= A[lane * R + k] * yk;
-    __syncwarp();
-  }
-  for (int k = r - 1; k >= 0; --k) {  // L^T x = y
-    const double xk = A[k * R + r] * invd[k];
-    __syncwarp();
-    if (lane == 0) A[k * R + r] = xk;
-    if (lane < k) A[lane * R + r] -= A[k * R + lane] * xk;
-    __syncwarp();
-  }
-  return CROM_OK;
 }
 
 template <int kM>
