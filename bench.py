@@ -231,7 +231,7 @@ def main():
             pg.barrier()
         torch.cuda.synchronize()
 
-    w = gen.heat2d_batched(n_inst=args.n_inst)
+    w = gen.heat2d_batched(n_inst=args.n_inst, first=rank * args.n_inst)   # each rank: its own instances
     ctx = crom.crom_create(w.spec.m, w.spec.r, w.spec.width, w.spec.hidden, local)
     crom.crom_set_weights(ctx, gen.pack_params(w.params))
     q0 = torch.tensor(w.q0, dtype=torch.float64, device="cuda")

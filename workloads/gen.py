@@ -204,11 +204,13 @@ def heat2d_single(bias_std: float = 0.0, bf16_exact: bool = False) -> StepWorklo
 
 def heat2d_batched(n_inst: int = 1024, m_lo: int = 32, m_hi: int = 512,
                    bias_std: float = 0.0, bf16_exact: bool = True,
-                   with_bumps: bool = False) -> StepWorkload:
+                   with_bumps: bool = False, first: int = 0) -> StepWorkload:
+    """Instances first .. first+n_inst-1 of the batched 2D heat workload (instance i
+    draws from seed 1000+i, so disjoint ranges give disjoint instances)."""
     spec = DecoderSpec(m=2, r=8, width=128, hidden=5)
     params = xavier_decoder(spec, seed=0, bias_std=bias_std, bf16_exact=bf16_exact)
     sizes, alphas, qs, samp, bumps = [], [], [], [], []
-    for i in range(n_inst):
+    for i in range(first, first + n_inst):
         rng = np.random.default_rng(1000 + i)
         alphas.append(rng.uniform(0.5, 2.0))
         M = int(rng.integers(m_lo, m_hi + 1))
