@@ -14,26 +14,31 @@
 //
 //  Step 1 (network inference): a forward pass whose UMMA columns are
 //  (channel, sample) pairs, D[u][n] = sum_k W_l[u][k] H[k][n] (M = 128 units,
-//  K = 128, N <= 64).  Iteration 0 carries the value, dg/dx_k and a single
+//  K = 128, 64 columns of bf16 hi parts followed by 64 columns of lo parts, one
+//  N = 128 UMMA per K slice).  Iteration 0 carries the value, dg/dx_k and a single
 //  Laplacian channel (d2z = W d2h with d2h = s''(z) sum_k (dz/dx_k)^2 + s'(z) d2z,
 //  the m diagonal second-derivative channels of Algorithm 2 summed); iteration
 //  k >= 1 carries the value at q^(k) and the difference channel
-//  h(q^(k)) - h(q_n).  The epilogue (bias, ELU chain; s'(z) kept in TMEM for the
-//  reverse pass) runs in FP32 registers and writes bf16 hi/lo operand pairs.
+//  h(q^(k)) - h(q_n).  The epilogue (bias, ELU chain; s'(z) of layers 2..L kept in
+//  TMEM for the reverse pass) runs in FP32 registers and writes bf16 hi/lo pairs.
 //
 //  Step 2 (PDE update): Delta f_j = dt * alpha_i * Lap g(y_j) (or the
 //  advection-diffusion form), kept per sample in global scratch (FP64).
 //
 //  Step 3 (network inversion): Jacobian rows dg/dq(y_j) from one reverse-mode
 //  pass, delta_L = w_out * s'(z_L), delta_{l-1} = (W_l^T delta_l) * s'(z_{l-1}) on
-//  the tensor cores (A = W_l read MN-major from the same shared image), then
+//  the tensor cores (A = W_l read MN-major from the same shared image, B = the hi
+//  and lo parts of delta side by side); s'(z_1) is recomputed from the samples.
 //  J = W_1q^T delta_1 by a projection UMMA.  J^T J and J^T rho are formed from
 //  exact FP32 products (two-product) with compensated sums per tile and added in
 //  FP64; the r x r system is solved by an FP64 Cholesky factorisation spread
 //  over a warp; q is updated in FP64.
 //
 // The output layer w_out . h_L and the projection W_1q^T delta_1 share one
-// 16-row bf16 matrix P (row 0 = w_out, rows 1..r = W_1q columns).
+// 16-row bf16 matrix P (row 0 = w_out, rows 1..r = W_1q columns); their UMMA
+// reads the activation buffer as the M = 128 operand, hi parts in rows 0..63 and
+// lo parts in rows 64..127 (or, after the reverse pass, in rows kS..2kS-1), and
+// the epilogue adds the two rows.
 #include <math.h>
 
 #include <algorithm>
@@ -55,14 +60,13 @@ constexpr int kS1 = 32;                  // samples per tile at later iterations
 constexpr int kSMax = 32;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kGroupCols = 256;     // TMEM columns per group
-constexpr uint32_t kAcc = 0;             // accumulator, up to 128 columns
-// s'(z_l), l = 1..L (<= 5), kS columns each: from column 128 at iteration 0 (the
-// accumulator then holds W h_hi in 0..63 and W h_lo in 64..127), from 64 later.
-constexpr uint32_t kSig0 = 128;
-constexpr uint32_t kSig1 = 64;
-constexpr uint32_t kPrj = 224;           // projection output, 16 columns
+// Accumulator in columns 0..127 (forward: W h_hi in 0..63, W h_lo in 64..127;
+// reverse: hi part in 0..kS-1, lo part in kS..2kS-1; projections: 16 columns);
+// s'(z_l) of hidden layers l = 2..L (<= 5), kS columns each, from column 128.
+constexpr uint32_t kAcc = 0;
+constexpr uint32_t kSig = 128;
 constexpr uint32_t kWaitLimit = 1u << 25;
-constexpr size_t kHBuf = (size_t)kTcWidth * 64 * 2;  // one bf16 operand buffer (<= 64 columns), 16 KB
+constexpr size_t kHBuf = (size_t)kTcWidth * 64 * 2;  // one 64-column bf16 MN-major block, 16 KB
 
 struct StepParams {
   const uint8_t* img;
@@ -111,15 +115,11 @@ struct __align__(16) Group {
   float c1[kTcWidth];
   float dz1[kTcWidth];
   float xs[2][kSMax];
-  float gout[4][kSMax];
+  float gp[128];          // output-layer projection: hi rows 0..63, lo rows 64..127
   float rho[kSMax];
-  float jt[kSMax][16];
+  float zero[kSMax];
+  float jt[2][kSMax][16];  // Jacobian rows from the hi and the lo parts of delta_1
 };
-
-// The projection UMMA reads 128 rows (two 64-column blocks) of a 64-column
-// operand buffer; the rows past the buffer are never used, but the reads must stay
-// inside the CTA's shared memory: at least 16 KB follow the last buffer.
-static_assert(sizeof(Shared) + kGroups * sizeof(Group) >= 16384, "projection over-read must stay in smem");
 
 __device__ __forceinline__ void group_sync(int g) {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGT) : "memory");
@@ -137,9 +137,10 @@ __device__ __forceinline__ bool group_sync_and(int g, bool pred) {
   return r != 0;
 }
 
-// Eight consecutive columns n0..n0+7 of row k as a bf16 hi/lo pair (one 16-byte
-// chunk in each buffer).
-__device__ __forceinline__ void split_store8(uint8_t* Hhi, uint8_t* Hlo, int k, int n0, const float* v) {
+// Eight consecutive columns of row k as a bf16 hi/lo pair: the hi parts go to
+// columns n_hi..n_hi+7, the lo parts to n_lo..n_lo+7 of the MN-major operand H
+// (columns >= 64 lie in the next 64-column block); one 16-byte chunk each.
+__device__ __forceinline__ void split_store8(uint8_t* H, int k, int n_hi, int n_lo, const float* v) {
   uint32_t hi[4], lo[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -148,9 +149,8 @@ __device__ __forceinline__ void split_store8(uint8_t* Hhi, uint8_t* Hlo, int k, 
     unpk2(sub2(pk2(v[2 * j], v[2 * j + 1]), pk2(bf16_lo_f(hi[j]), bf16_hi_f(hi[j]))), a, b);
     lo[j] = pack_bf16(a, b);
   }
-  const uint32_t off = mn_offset(k, n0);
-  *reinterpret_cast<uint4*>(Hhi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-  *reinterpret_cast<uint4*>(Hlo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  *reinterpret_cast<uint4*>(H + mn_offset(k, n_hi)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+  *reinterpret_cast<uint4*>(H + mn_offset(k, n_lo)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
 }
 
 // e^x - 1: degree-5 Taylor polynomial for |x| < 1/16 (truncation < 1.3e-9
@@ -210,48 +210,35 @@ __device__ __forceinline__ void act8(float (&v)[kCh][8], float (&sg)[8]) {
   }
 }
 
-// D(+)= A * B^T over K = 128 with the B operand as hi + lo parts.  a0: descriptor
-// of A's first K slice; A is K-major (forward, W_l) or MN-major (reverse pass,
-// W_l^T read from the same image); B descriptors are MN-major.
+// D = A * B^T over K = 128, one UMMA per K slice.  A is K-major (forward, W_l) or
+// MN-major (reverse pass, W_l^T read from the same image); B is the MN-major
+// activation buffer holding the hi and lo parts side by side along N, so each
+// UMMA yields W h_hi and W h_lo in separate accumulator columns.
 template <bool kAMN>
-__device__ __forceinline__ void issue_layer(uint32_t d, uint64_t a0, uint64_t bhi, uint64_t blo, uint32_t idesc) {
+__device__ __forceinline__ void issue_layer(uint32_t d, uint64_t a0, uint64_t b0, uint32_t idesc) {
 #pragma unroll
   for (int kk = 0; kk < 8; ++kk)
-    umma_f16(d, desc_add(a0, kAMN ? mnmajor_kslice(kk) : kmajor_kslice(128, kk)), desc_add(bhi, mnmajor_kslice(kk)),
+    umma_f16(d, desc_add(a0, kAMN ? mnmajor_kslice(kk) : kmajor_kslice(128, kk)), desc_add(b0, mnmajor_kslice(kk)),
              idesc, kk > 0);
-#pragma unroll
-  for (int kk = 0; kk < 8; ++kk)
-    umma_f16(d, desc_add(a0, kAMN ? mnmajor_kslice(kk) : kmajor_kslice(128, kk)), desc_add(blo, mnmajor_kslice(kk)),
-             idesc, 1);
 }
-// D = A * [B_hi | B_lo]^T over K = 128: the lo buffer follows the hi buffer at the
-// MN-major operand's 64-column block stride, so one N = 128 UMMA per K slice
-// covers both parts (W h_hi lands in accumulator columns 0..63, W h_lo in 64..127).
-__device__ __forceinline__ void issue_cat(uint32_t d, uint64_t a0, uint64_t bhi, uint32_t idesc) {
-#pragma unroll
-  for (int kk = 0; kk < 8; ++kk)
-    umma_f16(d, desc_add(a0, kmajor_kslice(128, kk)), desc_add(bhi, mnmajor_kslice(kk)), idesc, kk > 0);
-}
-// PRJ[n][j] = sum_u H[u][n] P[j][u] with H (MN-major A) as the hi + lo parts.
-__device__ __forceinline__ void issue_proj(uint32_t d, uint64_t ahi, uint64_t alo, uint64_t p0) {
+// PRJ[n][j] = sum_u H[u][n] P[j][u]: the activation buffer (both 64-column blocks)
+// is the MN-major A operand, so row n < 64 projects a hi part and row 64 + n the
+// matching lo part.
+__device__ __forceinline__ void issue_proj(uint32_t d, uint64_t a0, uint64_t p0) {
   constexpr uint32_t id = idesc_f16(128, 16, true, false, true);
 #pragma unroll
   for (int kk = 0; kk < 8; ++kk)
-    umma_f16(d, desc_add(ahi, mnmajor_kslice(kk)), desc_add(p0, kmajor_kslice(16, kk)), id, kk > 0);
-#pragma unroll
-  for (int kk = 0; kk < 8; ++kk)
-    umma_f16(d, desc_add(alo, mnmajor_kslice(kk)), desc_add(p0, kmajor_kslice(16, kk)), id, 1);
+    umma_f16(d, desc_add(a0, mnmajor_kslice(kk)), desc_add(p0, kmajor_kslice(16, kk)), id, kk > 0);
 }
 
 // Per-thread view of the group it belongs to.
 struct Lane {
   int g, gt, gw, u, half;
   uint32_t lane_base, tb;
-  uint8_t* Hhi;
-  uint8_t* Hlo;
+  uint8_t* H;
   Shared* S;
   Group* G;
-  uint64_t dW_k, dW_mn, dP, dHhi, dHlo;
+  uint64_t dW_k, dW_mn, dP, dH;
   float wx0, wx1, wsq, wo;
   uint32_t phase;
 };
@@ -259,7 +246,7 @@ struct Lane {
 // One UMMA stage of the group: fence the epilogue's shared-memory writes, meet,
 // one thread issues and commits, the first warp waits on the mbarrier, the rest at
 // the group barrier.  Returns the group-uniform completion flag.
-enum StageKind { kStageFwd = 0, kStageBwd = 1, kStageProj = 2, kStageFwdCat = 3 };
+enum StageKind { kStageFwd = 0, kStageBwd = 1, kStageProj = 2 };
 template <StageKind kKind>
 __device__ __forceinline__ bool stage(Lane& c, int layer, uint32_t idesc) {
   fence_proxy_async_smem();
@@ -269,14 +256,12 @@ __device__ __forceinline__ bool stage(Lane& c, int layer, uint32_t idesc) {
   if (c.gw == 0) {
     if (c.gt == 0) {
       tc_fence_after();
-      if (kKind == kStageFwdCat)  // hi and lo parts side by side as one N = 2 x 64 operand
-        issue_cat(c.tb + kAcc, desc_add(c.dW_k, (uint32_t)layer * kTcLayerBytes), c.dHhi, idesc);
-      else if (kKind == kStageFwd)
-        issue_layer<false>(c.tb + kAcc, desc_add(c.dW_k, (uint32_t)layer * kTcLayerBytes), c.dHhi, c.dHlo, idesc);
+      if (kKind == kStageFwd)
+        issue_layer<false>(c.tb + kAcc, desc_add(c.dW_k, (uint32_t)layer * kTcLayerBytes), c.dH, idesc);
       else if (kKind == kStageBwd)
-        issue_layer<true>(c.tb + kAcc, desc_add(c.dW_mn, (uint32_t)layer * kTcLayerBytes), c.dHhi, c.dHlo, idesc);
+        issue_layer<true>(c.tb + kAcc, desc_add(c.dW_mn, (uint32_t)layer * kTcLayerBytes), c.dH, idesc);
       else
-        issue_proj(c.tb + kPrj, c.dHhi, c.dHlo, c.dP);
+        issue_proj(c.tb + kAcc, c.dH, c.dP);
       umma_commit(&c.G->bar_mma);
     }
     __syncwarp();
@@ -290,11 +275,13 @@ __device__ __forceinline__ bool stage(Lane& c, int layer, uint32_t idesc) {
 
 // Exact product-sum of up to kSMax FP32 pairs: two-product (a*b = p + e exactly by
 // one FMA) and a compensated (two-sum) accumulation of the p, in FP32; returned in
-// FP64.  Relative error ~2^-46, well below the FP32 inputs' own rounding.
-__device__ __forceinline__ double dot_exact(const float* a, int sa, const float* b, int sb, int n) {
+// FP64.  Relative error ~2^-46, well below the FP32 inputs' own rounding.  Each
+// factor is the FP32 sum of two parts (a0 + a1, b0 + b1).
+__device__ __forceinline__ double dot_exact(const float* a0, const float* a1, int sa, const float* b0,
+                                            const float* b1, int sb, int n) {
   float s = 0.f, comp = 0.f;
   for (int i = 0; i < n; ++i) {
-    const float x = a[i * sa], y = b[i * sb];
+    const float x = __fadd_rn(a0[i * sa], a1[i * sa]), y = __fadd_rn(b0[i * sb], b1[i * sb]);
     const float p = __fmul_rn(x, y);  // rounded product (kept out of FMA contraction)
     const float e = fmaf(x, y, -p);   // its exact rounding error
     const float t = __fadd_rn(s, p);
@@ -305,16 +292,33 @@ __device__ __forceinline__ double dot_exact(const float* a, int sa, const float*
   return (double)s + (double)comp;
 }
 
+// s'(z_1) of eight samples of this thread's unit, recomputed exactly as the
+// forward pass formed it (same FP32 operations), for the last reverse step.
+template <int kM>
+__device__ __forceinline__ void sig1_8(const Lane& c, const Group* G, float cc, int s, float (&sg)[8]) {
+#pragma unroll
+  for (int i = 0; i < 8; i += 2) {
+    float z0 = fmaf(c.wx0, G->xs[0][s + i], cc), z1 = fmaf(c.wx0, G->xs[0][s + i + 1], cc);
+    if (kM > 1) {
+      z0 = fmaf(c.wx1, G->xs[1][s + i], z0);
+      z1 = fmaf(c.wx1, G->xs[1][s + i + 1], z1);
+    }
+    float e0, e1;
+    (void)elu2(pk2(z0, z1), e0, e1);
+    sg[i] = z0 > 0.f ? 1.f : e0;
+    sg[i + 1] = z1 > 0.f ? 1.f : e1;
+  }
+}
+
 // One tile of kSm samples of one GN iteration: forward pass, PDE update / residual,
 // reverse pass, Jacobian projection and this tile's share of J^T J and J^T rho.
 template <int kM, int kSm, bool kFirst>
 __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, int t, int ns, float alpha, int ea,
                                          int eb, double& acc) {
   constexpr int kCh = kFirst ? 2 + kM : 2;  // iteration 0: v, dx_1..dx_m, Lap; later: v(q^(k)), diff
-  constexpr int kN = kCh * kSm;
+  constexpr int kN = kCh * kSm;             // hi columns 0..kN-1, lo columns 64..64+kN-1
   constexpr int kHalf = kSm / 2;            // samples of this thread
-  constexpr uint32_t kSigB = kFirst ? kSig0 : kSig1;
-  static_assert(kN <= 64 && kHalf % 8 == 0, "tile shape");
+  static_assert(kN <= 64 && kHalf % 8 == 0 && kSig + 4 * kSm <= kGroupCols, "tile shape");
   Group* G = c.G;
   const Shared* S = c.S;
   const int u = c.u, s0 = c.half * kHalf;
@@ -346,50 +350,51 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
         }
       }
       act8<kM, kFirst, kCh>(v, sg);
-      tmem_st8(taddr(tb, lb, kSigB + s0 + h8), sg);
 #pragma unroll
-      for (int ch = 0; ch < kCh; ++ch) split_store8(c.Hhi, c.Hlo, u, ch * kSm + s0 + h8, v[ch]);
+      for (int ch = 0; ch < kCh; ++ch) {
+        const int n = ch * kSm + s0 + h8;
+        split_store8(c.H, u, n, 64 + n, v[ch]);
+      }
     }
-    tmem_st_wait();
   }
-  // ---------------- hidden layers 2..L (tensor cores)
-  constexpr uint32_t id_fwd = idesc_f16(128, kFirst ? 128 : kN, false, true, true);
+  // ---------------- hidden layers 2..L (tensor cores): one N = 128 UMMA per K slice
+  constexpr uint32_t id_fwd = idesc_f16(128, 128, false, true, true);
   for (int l = 0; l < p.L - 1; ++l) {
-    if (!stage<kFirst ? kStageFwdCat : kStageFwd>(c, l, id_fwd)) return false;
+    if (!stage<kStageFwd>(c, l, id_fwd)) return false;
     const float bias = S->bh[l][u];
 #pragma unroll
     for (int h8 = 0; h8 < kHalf; h8 += 8) {
-      float v[kCh][8], sg[8];
+      float v[kCh][8], w[kCh][8], sg[8];
 #pragma unroll
-      for (int ch = 0; ch < kCh; ++ch) tmem_ld8(taddr(tb, lb, kAcc + ch * kSm + s0 + h8), v[ch]);
-      if (kFirst) {  // add W h_lo
-        float w[kCh][8];
-#pragma unroll
-        for (int ch = 0; ch < kCh; ++ch) tmem_ld8(taddr(tb, lb, kAcc + 64 + ch * kSm + s0 + h8), w[ch]);
-        tmem_ld_wait();
-#pragma unroll
-        for (int ch = 0; ch < kCh; ++ch)
-#pragma unroll
-          for (int i = 0; i < 8; i += 2)
-            unpk2(add2(pk2(v[ch][i], v[ch][i + 1]), pk2(w[ch][i], w[ch][i + 1])), v[ch][i], v[ch][i + 1]);
+      for (int ch = 0; ch < kCh; ++ch) {
+        tmem_ld8(taddr(tb, lb, kAcc + ch * kSm + s0 + h8), v[ch]);
+        tmem_ld8(taddr(tb, lb, kAcc + 64 + ch * kSm + s0 + h8), w[ch]);
       }
       tmem_ld_wait();
 #pragma unroll
+      for (int ch = 0; ch < kCh; ++ch)
+#pragma unroll
+        for (int i = 0; i < 8; i += 2)
+          unpk2(add2(pk2(v[ch][i], v[ch][i + 1]), pk2(w[ch][i], w[ch][i + 1])), v[ch][i], v[ch][i + 1]);
+#pragma unroll
       for (int i = 0; i < 8; i += 2) unpk2(add2(pk2(v[0][i], v[0][i + 1]), pk2(bias, bias)), v[0][i], v[0][i + 1]);
       act8<kM, kFirst, kCh>(v, sg);
-      tmem_st8(taddr(tb, lb, kSigB + (l + 1) * kSm + s0 + h8), sg);
+      tmem_st8(taddr(tb, lb, kSig + l * kSm + s0 + h8), sg);
 #pragma unroll
-      for (int ch = 0; ch < kCh; ++ch) split_store8(c.Hhi, c.Hlo, u, ch * kSm + s0 + h8, v[ch]);
+      for (int ch = 0; ch < kCh; ++ch) {
+        const int n = ch * kSm + s0 + h8;
+        split_store8(c.H, u, n, 64 + n, v[ch]);
+      }
     }
     tmem_st_wait();
   }
-  // ---------------- output layer: PRJ[n][0] = w_out . h_L[:, n]
+  // ---------------- output layer: PRJ[n][0] = w_out . h_L[:, n], hi rows + lo rows
   if (!stage<kStageProj>(c, 0, 0)) return false;
   if (c.half == 0) {
     float v[8];
-    tmem_ld8(taddr(tb, lb, kPrj), v);
+    tmem_ld8(taddr(tb, lb, kAcc), v);
     tmem_ld_wait();
-    if (u < kN) G->gout[u / kSm][u % kSm] = v[0];
+    G->gp[u] = v[0];
   }
   group_sync(c.g);
   // ---------------- Step 2 and the residual rho_j
@@ -398,62 +403,75 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
     if (c.gt < ns) {
       const int j = o0 + t * kSm + c.gt;
       if (kFirst) {
-        const float lap = G->gout[kM + 1][c.gt];
+        const int nl = (kM + 1) * kSm + c.gt;
+        const float lap = G->gp[nl] + G->gp[64 + nl];
         double df;
         if (p.pde == CROM_PDE_HEAT) {
           df = p.dt * (double)alpha * (double)lap;
         } else {
           double adv = 0.0;
-          for (int k = 0; k < kM; ++k) adv += (double)p.vel[(size_t)j * kM + k] * (double)G->gout[1 + k][c.gt];
+          for (int k = 0; k < kM; ++k) {
+            const int nk = (1 + k) * kSm + c.gt;
+            adv += (double)p.vel[(size_t)j * kM + k] * (double)(G->gp[nk] + G->gp[64 + nk]);
+          }
           df = p.dt * (-adv + (double)alpha * (double)lap);
         }
         p.df[j] = df;
         rho = (float)(-df);
       } else {
-        rho = (float)((double)G->gout[1][c.gt] - p.df[j]);
+        const int nd = kSm + c.gt;
+        rho = (float)((double)(G->gp[nd] + G->gp[64 + nd]) - p.df[j]);
       }
     }
     G->rho[c.gt] = rho;
   }
-  // ---------------- reverse pass for dg/dq at q^(k)
+  // ---------------- reverse pass for dg/dq at q^(k); delta hi in columns 0..kSm-1, lo in kSm..2kSm-1
 #pragma unroll
   for (int h8 = 0; h8 < kHalf; h8 += 8) {
     float sg[8];
-    tmem_ld8(taddr(tb, lb, kSigB + (p.L - 1) * kSm + s0 + h8), sg);
+    tmem_ld8(taddr(tb, lb, kSig + (p.L - 2) * kSm + s0 + h8), sg);
     tmem_ld_wait();
 #pragma unroll
     for (int i = 0; i < 8; ++i) sg[i] *= c.wo;
-    split_store8(c.Hhi, c.Hlo, u, s0 + h8, sg);  // delta_L
+    split_store8(c.H, u, s0 + h8, kSm + s0 + h8, sg);  // delta_L
   }
-  constexpr uint32_t id_bwd = idesc_f16(128, kSm, true, true, true);
+  constexpr uint32_t id_bwd = idesc_f16(128, 2 * kSm, true, true, true);
   for (int l = p.L - 2; l >= 0; --l) {
     // accumulator = W_{l+2}^T delta_{l+2}; times s'(z_{l+1}) gives delta_{l+1}
     if (!stage<kStageBwd>(c, l, id_bwd)) return false;
+    const float cc = G->c1[u];
 #pragma unroll
     for (int h8 = 0; h8 < kHalf; h8 += 8) {
-      float v[8], sg[8];
+      float v[8], w[8], sg[8];
       tmem_ld8(taddr(tb, lb, kAcc + s0 + h8), v);
-      tmem_ld8(taddr(tb, lb, kSigB + l * kSm + s0 + h8), sg);
+      tmem_ld8(taddr(tb, lb, kAcc + kSm + s0 + h8), w);
+      if (l > 0) tmem_ld8(taddr(tb, lb, kSig + (l - 1) * kSm + s0 + h8), sg);
+      else sig1_8<kM>(c, G, cc, s0 + h8, sg);
       tmem_ld_wait();
 #pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] *= sg[i];
-      split_store8(c.Hhi, c.Hlo, u, s0 + h8, v);
+      for (int i = 0; i < 8; i += 2)
+        unpk2(mul2(add2(pk2(v[i], v[i + 1]), pk2(w[i], w[i + 1])), pk2(sg[i], sg[i + 1])), v[i], v[i + 1]);
+      split_store8(c.H, u, s0 + h8, kSm + s0 + h8, v);
     }
   }
-  // J[s][j] = sum_u W_1q[u][j] delta_1[u][s]
+  // J[s][j] = sum_u W_1q[u][j] delta_1[u][s]: rows s (hi) and kSm + s (lo)
   if (!stage<kStageProj>(c, 0, 0)) return false;
-  if (c.gw == 0) {
+  if (c.gw < 2 * kSm / 32) {
     float v[16];
-    tmem_ld16(taddr(tb, 0, kPrj), v);
+    tmem_ld16(taddr(tb, lb, kAcc), v);
     tmem_ld_wait();
-    if (c.gt < kSm) {
+    const int part = u / kSm, s = u % kSm;
 #pragma unroll
-      for (int j = 0; j < 15; ++j) G->jt[c.gt][j] = v[j + 1];
-    }
+    for (int j = 0; j < 15; ++j) G->jt[part][s][j] = v[j + 1];
   }
   group_sync(c.g);
   // ---------------- this tile's normal-equation terms
-  if (ea >= 0) acc += dot_exact(&G->jt[0][ea], 16, eb >= 0 ? &G->jt[0][eb] : G->rho, eb >= 0 ? 16 : 1, ns);
+  if (ea >= 0) {
+    const float* a0 = &G->jt[0][0][ea];
+    const float* a1 = &G->jt[1][0][ea];
+    if (eb >= 0) acc += dot_exact(a0, a1, 16, &G->jt[0][0][eb], &G->jt[1][0][eb], 16, ns);
+    else acc += dot_exact(a0, a1, 16, G->rho, G->zero, 1, ns);
+  }
   return true;
 }
 
@@ -474,8 +492,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
 
   uint8_t* Wimg = sm;
   uint8_t* Hbase = sm + ((p.img_bytes + 1023) & ~1023);
-  c.Hhi = Hbase + (size_t)c.g * 2 * kHBuf;
-  c.Hlo = c.Hhi + kHBuf;
+  c.H = Hbase + (size_t)c.g * 2 * kHBuf;  // two 64-column blocks: hi parts, then lo parts
   c.S = reinterpret_cast<Shared*>(Hbase + (size_t)kGroups * 2 * kHBuf);
   c.G = reinterpret_cast<Group*>(c.S + 1) + c.g;
   Shared* S = c.S;
@@ -489,6 +506,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
     mbar_init(&G->bar_mma, 1);
     fence_mbar_init();
   }
+  if (c.gt < kSMax) G->zero[c.gt] = 0.f;
   if (tid < 32) {
     tmem_alloc(&S->tmem_base, kTmemCols);
     tmem_relinquish();
@@ -515,8 +533,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
   c.dW_k = smem_desc_sw128(wbase, 16, 1024);       // W_l as K-major A
   c.dW_mn = smem_desc_sw128(wbase, 16384, 1024);   // W_l^T as MN-major A
   c.dP = smem_desc_sw128(wbase + (uint32_t)(L - 1) * kTcLayerBytes, 16, 1024);
-  c.dHhi = smem_desc_sw128(smem_u32(c.Hhi), 16384, 1024);
-  c.dHlo = smem_desc_sw128(smem_u32(c.Hlo), 16384, 1024);
+  c.dH = smem_desc_sw128(smem_u32(c.H), 16384, 1024);
   c.wx0 = S->w1x[0][c.u];
   c.wx1 = (kM > 1) ? S->w1x[1][c.u] : 0.f;
   c.wsq = c.wx0 * c.wx0 + c.wx1 * c.wx1;
