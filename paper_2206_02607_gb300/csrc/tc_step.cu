@@ -153,24 +153,30 @@ __device__ __forceinline__ void split_store8(uint8_t* H, int k, int n_hi, int n_
   *reinterpret_cast<uint4*>(H + mn_offset(k, n_lo)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
 }
 
-// e^x - 1: degree-5 Taylor polynomial for |x| < 1/16 (truncation < 1.3e-9
-// relative), the library function otherwise.
-__device__ __forceinline__ float expm1_small(float x) {
-  if (fabsf(x) < 0.0625f)
-    return x * fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f), 0.5f), 1.f);
-  return expm1f(x);
+// e^x - 1 for |x| < 1/16 by its degree-5 Taylor polynomial (truncation < 1.3e-9
+// relative).
+__device__ __forceinline__ float expm1_taylor(float x) {
+  return x * fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f), 0.5f), 1.f);
 }
-
-// s(a) - s(a - d) without cancellation, given e = exp(min(a, 0)): the difference
-// channel carries h(q^(k)) - h(q_n), so the residual g(y, q^(k)) - g(y, q_n) - Delta f
-// keeps its relative accuracy although the two evaluations agree to many digits.
-__device__ __forceinline__ float elu_diff(float a, float d, float e) {
+// s(a) - s(a - d) for the cases the inline path leaves: mixed signs of a and
+// a - d, or both non-positive with |d| >= 1/16.  Kept out of line: these cases are
+// rare, and inlining them at every activation multiplies the kernel's code size.
+__device__ __noinline__ float elu_diff_slow(float a, float d, float e) {
   const float b = a - d;
-  if (a > 0.f && b > 0.f) return d;
-  if (a <= 0.f && b <= 0.f) return -e * expm1_small(-d);
+  if (a <= 0.f && b <= 0.f) return -e * expm1f(-d);
   const float sa = a > 0.f ? a : expm1f(a);
   const float sb = b > 0.f ? b : expm1f(b);
   return sa - sb;
+}
+// s(a) - s(a - d) without cancellation, given e = exp(min(a, 0)): the difference
+// channel carries h(q^(k)) - h(q_n), so the residual g(y, q^(k)) - g(y, q_n) - Delta f
+// keeps its relative accuracy although the two evaluations agree to many digits.
+// Both positive: d; both non-positive: e^a - e^(a-d) = -e^a (e^(-d) - 1).
+__device__ __forceinline__ float elu_diff(float a, float d, float e) {
+  const float b = a - d;
+  if (a > 0.f && b > 0.f) return d;
+  if (a <= 0.f && b <= 0.f && fabsf(d) < 0.0625f) return -e * expm1_taylor(-d);
+  return elu_diff_slow(a, d, e);
 }
 
 // Forward activation chain of 8 samples of one hidden unit, in place, on packed
@@ -214,9 +220,11 @@ __device__ __forceinline__ void act8(float (&v)[kCh][8], float (&sg)[8]) {
 // MN-major (reverse pass, W_l^T read from the same image); B is the MN-major
 // activation buffer holding the hi and lo parts side by side along N, so each
 // UMMA yields W h_hi and W h_lo in separate accumulator columns.
+// The K-slice loops stay rolled: the issuing thread runs this code once per
+// stage, and a compact loop stays in the instruction cache between stages.
 template <bool kAMN>
 __device__ __forceinline__ void issue_layer(uint32_t d, uint64_t a0, uint64_t b0, uint32_t idesc) {
-#pragma unroll
+#pragma unroll 1
   for (int kk = 0; kk < 8; ++kk)
     umma_f16(d, desc_add(a0, kAMN ? mnmajor_kslice(kk) : kmajor_kslice(128, kk)), desc_add(b0, mnmajor_kslice(kk)),
              idesc, kk > 0);
@@ -226,7 +234,7 @@ __device__ __forceinline__ void issue_layer(uint32_t d, uint64_t a0, uint64_t b0
 // matching lo part.
 __device__ __forceinline__ void issue_proj(uint32_t d, uint64_t a0, uint64_t p0) {
   constexpr uint32_t id = idesc_f16(128, 16, true, false, true);
-#pragma unroll
+#pragma unroll 1
   for (int kk = 0; kk < 8; ++kk)
     umma_f16(d, desc_add(a0, mnmajor_kslice(kk)), desc_add(p0, kmajor_kslice(16, kk)), id, kk > 0);
 }
@@ -331,7 +339,7 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
   // ---------------- layer 1 (CUDA cores)
   {
     const float cc = G->c1[u], dz = G->dz1[u];
-#pragma unroll
+#pragma unroll 1
     for (int h8 = 0; h8 < kHalf; h8 += 8) {
       // layer-1 pre-activation channels: z = W_1x x + W_1q q + b_1, dz/dx_k = W_1[:, k],
       // Laplacian 0; later iterations: the difference channel's W_1q (q^(k) - q_n)
@@ -362,7 +370,7 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
   for (int l = 0; l < p.L - 1; ++l) {
     if (!stage<kStageFwd>(c, l, id_fwd)) return false;
     const float bias = S->bh[l][u];
-#pragma unroll
+#pragma unroll 1
     for (int h8 = 0; h8 < kHalf; h8 += 8) {
       float v[kCh][8], w[kCh][8], sg[8];
 #pragma unroll
@@ -426,7 +434,7 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
     G->rho[c.gt] = rho;
   }
   // ---------------- reverse pass for dg/dq at q^(k); delta hi in columns 0..kSm-1, lo in kSm..2kSm-1
-#pragma unroll
+#pragma unroll 1
   for (int h8 = 0; h8 < kHalf; h8 += 8) {
     float sg[8];
     tmem_ld8(taddr(tb, lb, kSig + (p.L - 2) * kSm + s0 + h8), sg);
@@ -440,7 +448,7 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
     // accumulator = W_{l+2}^T delta_{l+2}; times s'(z_{l+1}) gives delta_{l+1}
     if (!stage<kStageBwd>(c, l, id_bwd)) return false;
     const float cc = G->c1[u];
-#pragma unroll
+#pragma unroll 1
     for (int h8 = 0; h8 < kHalf; h8 += 8) {
       float v[8], w[8], sg[8];
       tmem_ld8(taddr(tb, lb, kAcc + s0 + h8), v);
