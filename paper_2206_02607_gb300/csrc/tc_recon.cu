@@ -210,29 +210,26 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
       tc_fence_before();
       group_sync(g);
       bool done = true;
-      if ((gt >> 5) == 0) {  // one thread issues, the first warp waits, the rest wait at the barrier
-        if (gt == 0) {
-          tc_fence_after();
-          if (!last) {
-            // The lo buffer follows the hi buffer at the operand's 64-column block
-            // stride, so one UMMA with N = 128 multiplies both parts at once: columns
-            // 0..63 of the accumulator get W h_hi, columns 64..127 get W h_lo.
-            const uint64_t a0 = desc_add(dW, (uint32_t)l * kTcLayerBytes);
+      if ((gt >> 5) == 0) {  // the first warp issues (one elected lane) and waits, the rest wait at the barrier
+        tc_fence_after();
+        if (!last) {
+          // The lo buffer follows the hi buffer at the operand's 64-column block
+          // stride, so one UMMA with N = 128 multiplies both parts at once: columns
+          // 0..63 of the accumulator get W h_hi, columns 64..127 get W h_lo.
+          const uint64_t a0 = desc_add(dW, (uint32_t)l * kTcLayerBytes);
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk)
+            umma_f16_warp(tb + kAccCol, desc_add(a0, kmajor_kslice(128, kk)), desc_add(dHhi, mnmajor_kslice(kk)),
+                          id_layer, kk != 0);
+        } else {
+#pragma unroll
+          for (int part = 0; part <= kSplit; ++part)
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk)
-              umma_f16(tb + kAccCol, desc_add(a0, kmajor_kslice(128, kk)), desc_add(dHhi, mnmajor_kslice(kk)),
-                       id_layer, kk != 0);
-          } else {
-#pragma unroll
-            for (int part = 0; part <= kSplit; ++part)
-#pragma unroll
-              for (int kk = 0; kk < 8; ++kk)
-                umma_f16(tb + kOutCol, desc_add(part ? dHlo : dHhi, mnmajor_kslice(kk)),
-                         desc_add(dP, kmajor_kslice(16, kk)), id_out, (part | kk) != 0);
-          }
-          umma_commit(&G->bar_mma);
+              umma_f16_warp(tb + kOutCol, desc_add(part ? dHlo : dHhi, mnmajor_kslice(kk)),
+                            desc_add(dP, kmajor_kslice(16, kk)), id_out, (part | kk) != 0);
         }
-        __syncwarp();
+        umma_commit_warp(&G->bar_mma);
         done = mbar_wait(&G->bar_mma, phase, kWaitLimit);
       }
       ok = group_sync_and(g, done);

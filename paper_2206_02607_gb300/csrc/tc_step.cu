@@ -216,27 +216,26 @@ __device__ __forceinline__ void act8(float (&v)[kCh][8], float (&sg)[8]) {
   }
 }
 
-// D = A * B^T over K = 128, one UMMA per K slice.  A is K-major (forward, W_l) or
+// D = A * B^T over K = 128, one UMMA per K slice, issued by warp-converged code
+// (all lanes run it, an elected lane issues).  A is K-major (forward, W_l) or
 // MN-major (reverse pass, W_l^T read from the same image); B is the MN-major
 // activation buffer holding the hi and lo parts side by side along N, so each
 // UMMA yields W h_hi and W h_lo in separate accumulator columns.
-// The K-slice loops stay rolled: the issuing thread runs this code once per
-// stage, and a compact loop stays in the instruction cache between stages.
 template <bool kAMN>
 __device__ __forceinline__ void issue_layer(uint32_t d, uint64_t a0, uint64_t b0, uint32_t idesc) {
-#pragma unroll 1
+#pragma unroll
   for (int kk = 0; kk < 8; ++kk)
-    umma_f16(d, desc_add(a0, kAMN ? mnmajor_kslice(kk) : kmajor_kslice(128, kk)), desc_add(b0, mnmajor_kslice(kk)),
-             idesc, kk > 0);
+    umma_f16_warp(d, desc_add(a0, kAMN ? mnmajor_kslice(kk) : kmajor_kslice(128, kk)),
+                  desc_add(b0, mnmajor_kslice(kk)), idesc, kk > 0);
 }
 // PRJ[n][j] = sum_u H[u][n] P[j][u]: the activation buffer (both 64-column blocks)
 // is the MN-major A operand, so row n < 64 projects a hi part and row 64 + n the
 // matching lo part.
 __device__ __forceinline__ void issue_proj(uint32_t d, uint64_t a0, uint64_t p0) {
   constexpr uint32_t id = idesc_f16(128, 16, true, false, true);
-#pragma unroll 1
+#pragma unroll
   for (int kk = 0; kk < 8; ++kk)
-    umma_f16(d, desc_add(a0, mnmajor_kslice(kk)), desc_add(p0, kmajor_kslice(16, kk)), id, kk > 0);
+    umma_f16_warp(d, desc_add(a0, mnmajor_kslice(kk)), desc_add(p0, kmajor_kslice(16, kk)), id, kk > 0);
 }
 
 // Per-thread view of the group it belongs to.
@@ -252,8 +251,8 @@ struct Lane {
 };
 
 // One UMMA stage of the group: fence the epilogue's shared-memory writes, meet,
-// one thread issues and commits, the first warp waits on the mbarrier, the rest at
-// the group barrier.  Returns the group-uniform completion flag.
+// the first warp issues and commits (one elected lane) and waits on the mbarrier,
+// the rest wait at the group barrier.  Returns the group-uniform completion flag.
 enum StageKind { kStageFwd = 0, kStageBwd = 1, kStageProj = 2 };
 template <StageKind kKind>
 __device__ __forceinline__ bool stage(Lane& c, int layer, uint32_t idesc) {
@@ -262,17 +261,14 @@ __device__ __forceinline__ bool stage(Lane& c, int layer, uint32_t idesc) {
   group_sync(c.g);
   bool done = true;
   if (c.gw == 0) {
-    if (c.gt == 0) {
-      tc_fence_after();
-      if (kKind == kStageFwd)
-        issue_layer<false>(c.tb + kAcc, desc_add(c.dW_k, (uint32_t)layer * kTcLayerBytes), c.dH, idesc);
-      else if (kKind == kStageBwd)
-        issue_layer<true>(c.tb + kAcc, desc_add(c.dW_mn, (uint32_t)layer * kTcLayerBytes), c.dH, idesc);
-      else
-        issue_proj(c.tb + kAcc, c.dH, c.dP);
-      umma_commit(&c.G->bar_mma);
-    }
-    __syncwarp();
+    tc_fence_after();
+    if (kKind == kStageFwd)
+      issue_layer<false>(c.tb + kAcc, desc_add(c.dW_k, (uint32_t)layer * kTcLayerBytes), c.dH, idesc);
+    else if (kKind == kStageBwd)
+      issue_layer<true>(c.tb + kAcc, desc_add(c.dW_mn, (uint32_t)layer * kTcLayerBytes), c.dH, idesc);
+    else
+      issue_proj(c.tb + kAcc, c.dH, c.dP);
+    umma_commit_warp(&c.G->bar_mma);
     done = mbar_wait(&c.G->bar_mma, c.phase, kWaitLimit);
   }
   done = group_sync_and(c.g, done);
