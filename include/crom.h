@@ -87,16 +87,33 @@ typedef struct {
 } crom_decoder_desc;
 
 /* One latent step.
- *  pde      : CROM_PDE_HEAT     Delta f_j = dt * alpha_i * Lap g(y_j, q_n)
- *             CROM_PDE_ADVDIFF  Delta f_j = dt * (-vel_j . grad g + alpha_i * Lap g)
- *             (alpha_i plays the role of nu for advection-diffusion)
+ *  pde      : CROM_PDE_HEAT     Delta f_j = dt * alpha * Lap g(y_j, q_n)
+ *             CROM_PDE_ADVDIFF  Delta f_j = dt * (-vel_j . grad g + alpha * Lap g)
+ *             (alpha plays the role of nu for advection-diffusion)
  *  gn_iters : Gauss-Newton iterations per step, 1..16 (1 = the linearised least
  *             squares of paper App. C.2)
- *  dt       : time step (finite, > 0) */
+ *  dt       : time step (finite, > 0)
+ *  coef_per_sample : 0 — alpha holds one coefficient per instance, alpha[i];
+ *             1 — alpha holds one per integration sample, alpha[j] = nu(y_j), for
+ *             spatially varying coefficients u_t = nu(x) Lap u (paper App. G, the 1D
+ *             thermodynamics example, and App. H, the image-diffusion example, with
+ *             nu piecewise constant over regions); the caller evaluates nu at the
+ *             fixed sample set once.
+ *  line_search : 0 — full Gauss-Newton steps; L in 1..16 — each iteration takes
+ *             the first step length a = 1, 1/2, ..., 2^-L along the GN direction
+ *             delta that satisfies the sufficient-decrease (Armijo) condition
+ *             phi(q + a delta) <= phi(q) + 1e-4 a (J^T rho).delta, phi = 1/2 sum_j rho_j^2
+ *             (the paper's backtracking line search, §4.3); if none does, q is
+ *             kept and the instance's remaining iterations are skipped.  Each
+ *             trial costs one value-only pass over the instance's samples.
+ *             Available with CROM_PREC_BF16X2 (the FP32 path returns
+ *             CROM_ERR_UNSUPPORTED). */
 typedef struct {
   int pde;
   int gn_iters;
   double dt;
+  int coef_per_sample;
+  int line_search;
 } crom_step_desc;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -197,11 +214,18 @@ int crom_step_noalloc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, dou
  *                              velocities ax (between cells (i,j),(i+1,j)) and ay
  *                              (between (i,j),(i,j+1)), [n_batch][nx][ny] each,
  *                              plus central diffusion.
+ *  CROM_FOM_HEAT1D_DIRICHLET_FIELD, CROM_FOM_HEAT2D_NEUMANN_FIELD
+ *                              the two heat models with a spatially varying
+ *                              coefficient, u_t = nu(x) Lap u (paper App. G,
+ *                              thermodynamics, and App. H, image diffusion): coef
+ *                              holds nu at every node, [n_batch][nx][ny].
  * nx >= 3, n_batch <= 65535.  The result is in u when the call's work completes. */
 typedef enum {
   CROM_FOM_HEAT1D_DIRICHLET = 0,
   CROM_FOM_HEAT2D_NEUMANN = 1,
-  CROM_FOM_ADVDIFF2D_PERIODIC = 2
+  CROM_FOM_ADVDIFF2D_PERIODIC = 2,
+  CROM_FOM_HEAT1D_DIRICHLET_FIELD = 3,
+  CROM_FOM_HEAT2D_NEUMANN_FIELD = 4
 } crom_fom_kind;
 
 int crom_fom_step(int kind, int n_batch, int nx, int ny, const float* coef, const float* ax, const float* ay,

@@ -186,9 +186,10 @@ def lls_qr(J, b):
 
 # ------------------------------------------------------------ Step 2: PDE update
 
-def heat_delta_f(ev: Evaluation, alpha: float, dt: float):
+def heat_delta_f(ev: Evaluation, alpha, dt: float):
     """Forward Euler increment of u_t = alpha * Lap u with the network Laplacian
-    (App. G.2/G.3 and App. H.2/H.3): Delta f_j = dt * alpha * sum_k d2g/dx_k^2."""
+    (App. G.2/G.3 and App. H.2/H.3): Delta f_j = dt * alpha * sum_k d2g/dx_k^2.
+    alpha is a scalar or one value per sample (nu(y_j) for u_t = nu(x) Lap u)."""
     return dt * alpha * ev.lap
 
 
@@ -200,13 +201,25 @@ def advdiff_delta_f(ev: Evaluation, vel, nu: float, dt: float):
 
 # ------------------------------------------------------- one latent step (Alg. 3)
 
+ARMIJO_C1 = 1e-4   # sufficient-decrease constant of the backtracking line search
+
+
 def crom_step(decoder, q_n, Y, dt: float, gn_iters: int, alpha: float = 1.0,
-              pde: str = "heat", vel=None, nu: float = 0.0, return_info: bool = False):
+              pde: str = "heat", vel=None, nu: float = 0.0, return_info: bool = False,
+              line_search: int = 0):
     """One latent-space step q_n -> q_{n+1} (Algorithm 3 = Algorithms 4, then the PDE
     update, then Algorithm 5).
 
     decoder: callable (X, q) -> Evaluation (an MLPDecoder, or any test decoder).
-    Y: [M, m] integration samples.  Returns (q_{n+1}, status[, info])."""
+    Y: [M, m] integration samples.  Returns (q_{n+1}, status[, info]).
+
+    line_search = L > 0 equips each Gauss-Newton iteration with a standard
+    backtracking line search (§4.3 / App. C; Nocedal & Wright, Alg. 3.1): with
+    phi(q) = 1/2 sum_j (g(y_j, q) - target_j)^2, v = J^T rho and the GN direction
+    delta, the step length a = 1, 1/2, ..., 2^-L is the first that satisfies
+    phi(q + a delta) <= phi(q) + c1 a v.delta (c1 = 1e-4).  If none does, q is kept
+    and the remaining iterations are skipped (the direction no longer decreases phi
+    at any tried length)."""
     q_n = np.asarray(q_n, np.float64)
     Y = np.asarray(Y, np.float64)
     r = q_n.shape[0]
@@ -223,7 +236,7 @@ def crom_step(decoder, q_n, Y, dt: float, gn_iters: int, alpha: float = 1.0,
     # Step 3: Gauss-Newton on sum_j (g(y_j, q) - target_j)^2 from q^(0) = q_n.
     q = q_n.copy()
     status = STATUS_OK
-    deltas = []
+    deltas, trials = [], []
     for k in range(gn_iters):
         if k > 0:
             ev = decoder(Y, q)
@@ -234,21 +247,47 @@ def crom_step(decoder, q_n, Y, dt: float, gn_iters: int, alpha: float = 1.0,
         delta, status = cholesky_solve(A, -v)
         if status != STATUS_OK:
             break
-        q = q + delta
-        deltas.append(delta)
+        if line_search <= 0:
+            q = q + delta
+            deltas.append(delta)
+            continue
+        phi0 = 0.5 * float(rho @ rho)
+        slope = float(v @ delta)
+        a, accepted, tried = 1.0, False, []
+        for _ in range(line_search + 1):
+            q_try = q + a * delta
+            r_try = decoder(Y, q_try).g - target
+            phi = 0.5 * float(r_try @ r_try)
+            bound = phi0 + ARMIJO_C1 * a * slope
+            tried.append((a, phi, bound))
+            if phi <= bound:
+                accepted = True
+                break
+            a *= 0.5
+        trials.append(tried)
+        if not accepted:
+            break
+        deltas.append(q_try - q)
+        q = q_try
     if return_info:
-        return q, status, {"delta_f": df, "deltas": deltas}
+        return q, status, {"delta_f": df, "deltas": deltas, "line_search_trials": trials}
     return q, status
 
 
-def crom_step_batched(decoder, q, s_off, samples, alpha, dt, gn_iters):
-    """Independent heat steps for a batch of instances sharing one decoder."""
+def crom_step_batched(decoder, q, s_off, samples, alpha, dt, gn_iters, alpha_per_sample: bool = False,
+                      line_search: int = 0):
+    """Independent heat steps for a batch of instances sharing one decoder.
+
+    alpha: one diffusion coefficient per instance, or (alpha_per_sample) one per
+    integration sample, nu(y_j), for the spatially varying coefficient of
+    u_t = nu(x) Lap u (App. G thermodynamics, App. H image diffusion)."""
     q = np.asarray(q, np.float64)
     out = np.empty_like(q)
     status = np.zeros(q.shape[0], np.int32)
     for i in range(q.shape[0]):
         Y = samples[s_off[i]:s_off[i + 1]]
-        out[i], status[i] = crom_step(decoder, q[i], Y, dt, gn_iters, alpha=float(alpha[i]))
+        a = np.asarray(alpha[s_off[i]:s_off[i + 1]], np.float64) if alpha_per_sample else float(alpha[i])
+        out[i], status[i] = crom_step(decoder, q[i], Y, dt, gn_iters, alpha=a, line_search=line_search)
     return out, status
 
 

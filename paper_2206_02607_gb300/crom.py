@@ -38,6 +38,8 @@ CROM_WANT_DQ = 16
 CROM_FOM_HEAT1D_DIRICHLET = 0
 CROM_FOM_HEAT2D_NEUMANN = 1
 CROM_FOM_ADVDIFF2D_PERIODIC = 2
+CROM_FOM_HEAT1D_DIRICHLET_FIELD = 3
+CROM_FOM_HEAT2D_NEUMANN_FIELD = 4
 
 EXPORTED = ("crom_version", "crom_last_error", "crom_create", "crom_destroy", "crom_set_weights",
             "crom_decode", "crom_step", "crom_rollout", "crom_step_noalloc", "crom_fom_step", "crom_trainer_create",
@@ -57,7 +59,8 @@ class crom_decoder_desc(ctypes.Structure):
 
 
 class crom_step_desc(ctypes.Structure):
-    _fields_ = [("pde", ctypes.c_int), ("gn_iters", ctypes.c_int), ("dt", ctypes.c_double)]
+    _fields_ = [("pde", ctypes.c_int), ("gn_iters", ctypes.c_int), ("dt", ctypes.c_double),
+                ("coef_per_sample", ctypes.c_int), ("line_search", ctypes.c_int)]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -176,11 +179,11 @@ def crom_decode(ctx: CromContext, q, pt_off, x, want: int, out, stream=None):
 
 def crom_step(ctx: CromContext, q, alpha, s_off, samples, status, *, dt: float, gn_iters: int,
               max_samples: int, pde: int = CROM_PDE_HEAT, vel=None, precision: int = CROM_PREC_FP32,
-              stream=None):
+              coef_per_sample: bool = False, line_search: int = 0, stream=None):
     import torch
     _need(q, torch.float64, "q"); _need(alpha, torch.float32, "alpha"); _need(s_off, torch.int32, "s_off")
     _need(samples, torch.float32, "samples"); _need(status, torch.int32, "status"); _need(vel, torch.float32, "vel")
-    desc = crom_step_desc(pde, gn_iters, dt)
+    desc = crom_step_desc(pde, gn_iters, dt, int(bool(coef_per_sample)), int(line_search))
     _check(_LIB.crom_step(ctx.handle, ctypes.byref(desc), precision, q.shape[0], _ptr(q), _ptr(alpha),
                           _ptr(vel), _ptr(s_off), _ptr(samples), samples.shape[0], max_samples, _ptr(status),
                           _stream(stream)))
@@ -188,25 +191,26 @@ def crom_step(ctx: CromContext, q, alpha, s_off, samples, status, *, dt: float, 
 
 def crom_rollout(ctx: CromContext, q, alpha, s_off, samples, status, *, n_steps: int, dt: float, gn_iters: int,
                  max_samples: int, pde: int = CROM_PDE_HEAT, vel=None, precision: int = CROM_PREC_FP32,
-                 stream=None):
+                 coef_per_sample: bool = False, line_search: int = 0, stream=None):
     """n_steps latent steps replayed from a CUDA graph cached in the context."""
     import torch
     _need(q, torch.float64, "q"); _need(alpha, torch.float32, "alpha"); _need(s_off, torch.int32, "s_off")
     _need(samples, torch.float32, "samples"); _need(status, torch.int32, "status"); _need(vel, torch.float32, "vel")
-    desc = crom_step_desc(pde, gn_iters, dt)
+    desc = crom_step_desc(pde, gn_iters, dt, int(bool(coef_per_sample)), int(line_search))
     _check(_LIB.crom_rollout(ctx.handle, ctypes.byref(desc), precision, n_steps, q.shape[0], _ptr(q), _ptr(alpha),
                              _ptr(vel), _ptr(s_off), _ptr(samples), samples.shape[0], max_samples, _ptr(status),
                              _stream(stream)))
 
 
 def crom_step_noalloc(ctx: CromContext, q, alpha, s_off, samples, status, *, dt: float, gn_iters: int,
-                      max_samples: int, pde: int = CROM_PDE_HEAT, vel=None, stream=None):
+                      max_samples: int, pde: int = CROM_PDE_HEAT, vel=None, coef_per_sample: bool = False,
+                      stream=None):
     """The FP32 step with its scratch in the library's fixed device array: for
     callers that must not allocate device memory while stepping (see crom.h)."""
     import torch
     _need(q, torch.float64, "q"); _need(alpha, torch.float32, "alpha"); _need(s_off, torch.int32, "s_off")
     _need(samples, torch.float32, "samples"); _need(status, torch.int32, "status"); _need(vel, torch.float32, "vel")
-    desc = crom_step_desc(pde, gn_iters, dt)
+    desc = crom_step_desc(pde, gn_iters, dt, int(bool(coef_per_sample)), 0)
     _check(_LIB.crom_step_noalloc(ctx.handle, ctypes.byref(desc), q.shape[0], _ptr(q), _ptr(alpha), _ptr(vel),
                                   _ptr(s_off), _ptr(samples), samples.shape[0], max_samples, _ptr(status),
                                   _stream(stream)))

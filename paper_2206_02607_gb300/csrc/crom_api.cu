@@ -262,6 +262,12 @@ int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_in
   if (!(step->dt > 0.0) || !isfinite(step->dt)) return fail(CROM_ERR_INVALID_ARG, "crom_step: dt must be finite and > 0");
   if (step->gn_iters < 1 || step->gn_iters > 16) return fail(CROM_ERR_INVALID_ARG, "crom_step: gn_iters must be in 1..16");
   if (step->pde != CROM_PDE_HEAT && step->pde != CROM_PDE_ADVDIFF) return fail(CROM_ERR_INVALID_ARG, "crom_step: unknown pde");
+  if (step->coef_per_sample != 0 && step->coef_per_sample != 1)
+    return fail(CROM_ERR_INVALID_ARG, "crom_step: coef_per_sample must be 0 or 1");
+  if (step->line_search < 0 || step->line_search > 16)
+    return fail(CROM_ERR_INVALID_ARG, "crom_step: line_search must be in 0..16");
+  if (step->line_search > 0 && precision != CROM_PREC_BF16X2)
+    return fail(CROM_ERR_UNSUPPORTED, "crom_step: the line search is available with CROM_PREC_BF16X2");
   if (n_inst == 0) return CROM_OK;
   if (!q || !alpha || !s_off || !status || (n_samples > 0 && !samples))
     return fail(CROM_ERR_INVALID_ARG, "crom_step: null array");
@@ -295,6 +301,12 @@ int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n
   if (!(step->dt > 0.0) || !isfinite(step->dt)) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: dt must be finite and > 0");
   if (step->gn_iters < 1 || step->gn_iters > 16) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: gn_iters must be in 1..16");
   if (step->pde != CROM_PDE_HEAT && step->pde != CROM_PDE_ADVDIFF) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: unknown pde");
+  if (step->coef_per_sample != 0 && step->coef_per_sample != 1)
+    return fail(CROM_ERR_INVALID_ARG, "crom_rollout: coef_per_sample must be 0 or 1");
+  if (step->line_search < 0 || step->line_search > 16)
+    return fail(CROM_ERR_INVALID_ARG, "crom_rollout: line_search must be in 0..16");
+  if (step->line_search > 0 && precision != CROM_PREC_BF16X2)
+    return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: the line search is available with CROM_PREC_BF16X2");
   if (!q || !alpha || !s_off || !status || (n_samples > 0 && !samples))
     return fail(CROM_ERR_INVALID_ARG, "crom_rollout: null array");
   if (step->pde == CROM_PDE_ADVDIFF && !vel) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: advection needs vel");
@@ -309,11 +321,11 @@ int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n
   cudaStream_t s = (cudaStream_t)stream;
   // The key: every argument that the recorded launches depend on.
   struct Key {
-    int precision, n_steps, n_inst, n_samples, max_samples, pde, gn_iters;
+    int precision, n_steps, n_inst, n_samples, max_samples, pde, gn_iters, coef_per_sample, line_search;
     double dt;
     const void *q, *alpha, *vel, *s_off, *samples, *status, *weights;
-  } key{precision, n_steps, n_inst, n_samples, max_samples, step->pde, step->gn_iters, step->dt,
-        q, alpha, vel, s_off, samples, status, ctx->w.w1};
+  } key{precision, n_steps, n_inst, n_samples, max_samples, step->pde, step->gn_iters, step->coef_per_sample,
+        step->line_search, step->dt, q, alpha, vel, s_off, samples, status, ctx->w.w1};
   std::vector<unsigned char> kb(sizeof(Key));
   memcpy(kb.data(), &key, sizeof(Key));
   cudaError_t e;
@@ -366,6 +378,12 @@ int crom_step_noalloc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, dou
     return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: gn_iters must be in 1..16");
   if (step->pde != CROM_PDE_HEAT && step->pde != CROM_PDE_ADVDIFF)
     return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: unknown pde");
+  if (step->coef_per_sample != 0 && step->coef_per_sample != 1)
+    return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: coef_per_sample must be 0 or 1");
+  if (step->line_search < 0 || step->line_search > 16)
+    return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: line_search must be in 0..16");
+  if (step->line_search > 0)
+    return fail(CROM_ERR_UNSUPPORTED, "crom_step_noalloc: the line search is available with CROM_PREC_BF16X2");
   if (n_inst == 0) return CROM_OK;
   if (!q || !alpha || !s_off || !status || (n_samples > 0 && !samples))
     return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: null array");
@@ -387,11 +405,11 @@ int crom_step_noalloc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, dou
 
 int crom_fom_step(int kind, int n_batch, int nx, int ny, const float* coef, const float* ax, const float* ay,
                   double dt, int n_steps, float* u, float* tmp, crom_stream stream) {
-  if (kind < CROM_FOM_HEAT1D_DIRICHLET || kind > CROM_FOM_ADVDIFF2D_PERIODIC)
+  if (kind < CROM_FOM_HEAT1D_DIRICHLET || kind > CROM_FOM_HEAT2D_NEUMANN_FIELD)
     return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: unknown kind");
   if (n_batch < 0 || n_batch > 65535 || n_steps < 0) return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: bad batch or step count");
   if (nx < 3) return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: nx must be >= 3");
-  if (kind == CROM_FOM_HEAT1D_DIRICHLET ? ny != 1 : ny != nx)
+  if ((kind == CROM_FOM_HEAT1D_DIRICHLET || kind == CROM_FOM_HEAT1D_DIRICHLET_FIELD) ? ny != 1 : ny != nx)
     return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: ny must be 1 (1D) or nx (2D)");
   if (!(dt > 0.0) || !isfinite(dt)) return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: dt must be finite and > 0");
   if (n_batch == 0 || n_steps == 0) return CROM_OK;

@@ -14,13 +14,17 @@
 //      first-order upwind fluxes with face velocities ax[i][j] (between cells
 //      (i, j) and (i+1, j)) and ay[i][j] (between (i, j) and (i, j+1)), central
 //      diffusion: u += dt * (-div(a u) + nu * Lap_h u).
+//  * the heat models with a spatially varying coefficient nu(x) (App. G and H):
+//      the same stencils with nu read per node.
 // Layout: fields [n_batch][nx][ny] FP32 row-major (j fastest); face velocities
-// [n_batch][nx][ny]; coefficients nu/alpha per field.
+// [n_batch][nx][ny]; coefficients nu/alpha per field, or per node (same layout
+// as the fields) for the *_FIELD kinds.
 #include "crom_internal.h"
 
 namespace crom {
 namespace {
 
+template <bool kField>
 __global__ void heat1d_kernel(const float* __restrict__ u, float* __restrict__ out, const float* __restrict__ coef,
                               int P, float r_over) {
   // r_over = dt / dx^2
@@ -31,11 +35,13 @@ __global__ void heat1d_kernel(const float* __restrict__ u, float* __restrict__ o
   float v = 0.f;
   if (i > 0 && i < P - 1) {
     const float c = ub[i];
-    v = fmaf(r_over * coef[b], ub[i - 1] + ub[i + 1] - 2.f * c, c);
+    const float nu = kField ? coef[(size_t)b * P + i] : coef[b];
+    v = fmaf(r_over * nu, ub[i - 1] + ub[i + 1] - 2.f * c, c);
   }
   out[(size_t)b * P + i] = v;
 }
 
+template <bool kField>
 __global__ void heat2d_neumann_kernel(const float* __restrict__ u, float* __restrict__ out,
                                       const float* __restrict__ coef, int n, float r_over) {
   // r_over = dt / h^2; block = 32 x 8 nodes, j fastest
@@ -49,7 +55,9 @@ __global__ void heat2d_neumann_kernel(const float* __restrict__ u, float* __rest
   const float c = ub[(size_t)i * n + j];
   const float lap = (ub[(size_t)im * n + j] + ub[(size_t)ip * n + j] - 2.f * c) +
                     (ub[(size_t)i * n + jm] + ub[(size_t)i * n + jp] - 2.f * c);
-  out[(size_t)b * n * n + (size_t)i * n + j] = fmaf(r_over * coef[b], lap, c);
+  const size_t at = (size_t)b * n * n + (size_t)i * n + j;
+  const float nu = kField ? coef[at] : coef[b];
+  out[at] = fmaf(r_over * nu, lap, c);
 }
 
 __global__ void advdiff2d_kernel(const float* __restrict__ u, float* __restrict__ out,
@@ -86,14 +94,20 @@ cudaError_t launch_fom(int kind, int n_batch, int nx, int ny, const float* coef,
   float* src = u;
   float* dst = tmp;
   for (int k = 0; k < n_steps; ++k) {
-    if (kind == CROM_FOM_HEAT1D_DIRICHLET) {
+    if (kind == CROM_FOM_HEAT1D_DIRICHLET || kind == CROM_FOM_HEAT1D_DIRICHLET_FIELD) {
       const double dx = 1.0 / (nx - 1);
       dim3 grid((nx + 255) / 256, n_batch);
-      heat1d_kernel<<<grid, 256, 0, s>>>(src, dst, coef, nx, (float)(dt / (dx * dx)));
-    } else if (kind == CROM_FOM_HEAT2D_NEUMANN) {
+      if (kind == CROM_FOM_HEAT1D_DIRICHLET)
+        heat1d_kernel<false><<<grid, 256, 0, s>>>(src, dst, coef, nx, (float)(dt / (dx * dx)));
+      else
+        heat1d_kernel<true><<<grid, 256, 0, s>>>(src, dst, coef, nx, (float)(dt / (dx * dx)));
+    } else if (kind == CROM_FOM_HEAT2D_NEUMANN || kind == CROM_FOM_HEAT2D_NEUMANN_FIELD) {
       const double h = 1.0 / (nx - 1);
       dim3 grid((nx + 31) / 32, (nx + 7) / 8, n_batch);
-      heat2d_neumann_kernel<<<grid, dim3(32, 8), 0, s>>>(src, dst, coef, nx, (float)(dt / (h * h)));
+      if (kind == CROM_FOM_HEAT2D_NEUMANN)
+        heat2d_neumann_kernel<false><<<grid, dim3(32, 8), 0, s>>>(src, dst, coef, nx, (float)(dt / (h * h)));
+      else
+        heat2d_neumann_kernel<true><<<grid, dim3(32, 8), 0, s>>>(src, dst, coef, nx, (float)(dt / (h * h)));
     } else {
       const double h = 1.0 / nx;
       dim3 grid((nx + 31) / 32, (nx + 7) / 8, n_batch);

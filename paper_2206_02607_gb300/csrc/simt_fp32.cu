@@ -61,6 +61,7 @@ struct FwdParams {
   // step
   int iter;
   int pde;
+  int coef_per_sample;  // alpha indexed by sample (1) or by instance (0)
   double dt;
   const float* alpha;
   const float* vel;
@@ -331,7 +332,7 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
       const size_t j = (size_t)(first + s);
       if (p.iter == 0) {
         double df;
-        const double a = (double)p.alpha[inst];
+        const double a = (double)p.alpha[p.coef_per_sample ? j : (size_t)inst];
         if (p.pde == CROM_PDE_HEAT) {
           df = p.dt * a * (double)c[o2];
         } else {
@@ -566,6 +567,7 @@ cudaError_t launch_step_fp32(crom_ctx* ctx, const crom_step_desc* step, int n_in
   p.x = samples;
   p.n_inst = n_inst;
   p.pde = step->pde;
+  p.coef_per_sample = step->coef_per_sample;
   p.dt = step->dt;
   p.alpha = alpha;
   p.vel = vel;
@@ -680,6 +682,7 @@ cudaError_t launch_step_fp32_noalloc(const crom_ctx* ctx, const crom_step_desc* 
   p.x = samples;
   p.n_inst = n_inst;
   p.pde = step->pde;
+  p.coef_per_sample = step->coef_per_sample;
   p.dt = step->dt;
   p.alpha = alpha;
   p.vel = vel;

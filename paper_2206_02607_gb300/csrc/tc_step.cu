@@ -66,6 +66,7 @@ constexpr uint32_t kGroupCols = 256;     // TMEM columns per group
 constexpr uint32_t kAcc = 0;
 constexpr uint32_t kSig = 128;
 constexpr uint32_t kWaitLimit = 1u << 25;
+constexpr double kArmijoC1 = 1e-4;      // sufficient-decrease constant of the line search
 constexpr size_t kHBuf = (size_t)kTcWidth * 64 * 2;  // one 64-column bf16 MN-major block, 16 KB
 
 struct StepParams {
@@ -79,7 +80,9 @@ struct StepParams {
   const float* wout;
   float bout;
   int pde;
+  int coef_per_sample;  // alpha indexed by sample (1) or by instance (0)
   int gn_iters;
+  int line_search;  // backtracking halvings per GN iteration (0: full steps)
   double dt;
   int n_inst;
   double* q;
@@ -110,6 +113,9 @@ struct __align__(16) Group {
   int s_status;
   double qn[16];
   double qcur[16];
+  double qtry[16];    // line search: trial point q + a delta
+  double delta[16];   // line search: the GN direction
+  double phi0, phi, slope;
   double amat[15 * 16];
   double invd[16];
   float c1[kTcWidth];
@@ -316,7 +322,7 @@ __device__ __forceinline__ void sig1_8(const Lane& c, const Group* G, float cc, 
 
 // One tile of kSm samples of one GN iteration: forward pass, PDE update / residual,
 // reverse pass, Jacobian projection and this tile's share of J^T J and J^T rho.
-template <int kM, int kSm, bool kFirst>
+template <int kM, int kSm, bool kFirst, bool kValueOnly = false>
 __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, int t, int ns, float alpha, int ea,
                                          int eb, double& acc) {
   constexpr int kCh = kFirst ? 2 + kM : 2;  // iteration 0: v, dx_1..dx_m, Lap; later: v(q^(k)), diff
@@ -409,6 +415,7 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
       if (kFirst) {
         const int nl = (kM + 1) * kSm + c.gt;
         const float lap = G->gp[nl] + G->gp[64 + nl];
+        if (p.coef_per_sample) alpha = p.alpha[j];
         double df;
         if (p.pde == CROM_PDE_HEAT) {
           df = p.dt * (double)alpha * (double)lap;
@@ -428,6 +435,11 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
       }
     }
     G->rho[c.gt] = rho;
+  }
+  if (kValueOnly) {  // line-search trial: only sum_j rho_j^2 is needed
+    group_sync(c.g);
+    if (ea == -3) acc += dot_exact(G->rho, G->zero, 1, G->rho, G->zero, 1, ns);
+    return true;
   }
   // ---------------- reverse pass for dg/dq at q^(k); delta hi in columns 0..kSm-1, lo in kSm..2kSm-1
 #pragma unroll 1
@@ -475,8 +487,25 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
     const float* a1 = &G->jt[1][0][ea];
     if (eb >= 0) acc += dot_exact(a0, a1, 16, &G->jt[0][0][eb], &G->jt[1][0][eb], 16, ns);
     else acc += dot_exact(a0, a1, 16, G->rho, G->zero, 1, ns);
+  } else if (ea == -3) {
+    acc += dot_exact(G->rho, G->zero, 1, G->rho, G->zero, 1, ns);  // rho^T rho for the line search
   }
   return true;
+}
+
+// Layer-1 constants of the tile passes at the point q: c1 = b_1 + W_1q q (value
+// channel) and dz1 = W_1q (q - q_n) (difference channel), FP64 sums rounded once.
+__device__ __forceinline__ void set_layer1(const Lane& c, const Shared* S, Group* G, const double* q, int r,
+                                           const float* b1) {
+  if (c.half == 0) {
+    double cc = (double)b1[c.u], dz = 0.0;
+    for (int j = 0; j < r; ++j) {
+      cc += (double)S->w1q[j][c.u] * q[j];
+      dz += (double)S->w1q[j][c.u] * (q[j] - G->qn[j]);
+    }
+    G->c1[c.u] = (float)cc;
+    G->dz1[c.u] = (float)dz;
+  }
 }
 
 template <int kM>
@@ -552,6 +581,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
     ea = a; eb = a + rem;
   } else if (c.gt < n_entries) {
     ea = c.gt - ntri; eb = -2;
+  } else if (c.gt == n_entries && p.line_search > 0) {
+    ea = -3;  // rho^T rho, the line search's objective
   }
 
   while (ok) {
@@ -573,19 +604,11 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
       G->qcur[c.gt] = v;
     }
     if (c.gt == 0) G->s_status = CROM_OK;
-    const float alpha = p.alpha[inst];
+    const float alpha = p.coef_per_sample ? 0.f : p.alpha[inst];  // per-sample values are read in the tile
     group_sync(c.g);
 
     for (int it = 0; it < p.gn_iters && ok; ++it) {
-      if (c.half == 0) {
-        double cc = (double)p.b1[c.u], dz = 0.0;
-        for (int j = 0; j < r; ++j) {
-          cc += (double)S->w1q[j][c.u] * G->qcur[j];
-          dz += (double)S->w1q[j][c.u] * (G->qcur[j] - G->qn[j]);
-        }
-        G->c1[c.u] = (float)cc;
-        G->dz1[c.u] = (float)dz;
-      }
+      set_layer1(c, S, G, G->qcur, r, p.b1);
       double acc = 0.0;
       if (it == 0) {
         const int nt = (M + kS0 - 1) / kS0;
@@ -605,15 +628,52 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
         } else {
           G->amat[ea * R + r] = -acc;
         }
+      } else if (ea == -3) {
+        G->phi0 = 0.5 * acc;
       }
       group_sync(c.g);
       if (c.gw == 0) {
+        const double minus_v = c.gt < r ? G->amat[c.gt * R + r] : 0.0;  // -(J^T rho)_k
         const int st = chol_solve_warp(G->amat, G->invd, r, c.gt);
-        if (st == CROM_OK && c.gt < r) G->qcur[c.gt] += G->amat[c.gt * R + r];
+        if (st == CROM_OK && c.gt < r) {
+          const double d = G->amat[c.gt * R + r];
+          if (p.line_search > 0) G->delta[c.gt] = d;
+          else G->qcur[c.gt] += d;
+        }
+        if (p.line_search > 0) {  // slope = (J^T rho) . delta
+          double sl = st == CROM_OK && c.gt < r ? -minus_v * G->amat[c.gt * R + r] : 0.0;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) sl += __shfl_xor_sync(0xffffffffu, sl, o);
+          if (c.gt == 0) G->slope = sl;
+        }
         if (c.gt == 0) G->s_status = st;
       }
       group_sync(c.g);
       if (G->s_status != CROM_OK) break;
+      if (p.line_search > 0) {
+        // Backtracking (Armijo) along delta: a = 1, 1/2, ..., 2^-line_search.
+        bool accepted = false;
+        double a = 1.0;
+        for (int trial = 0; trial <= p.line_search && ok; ++trial, a *= 0.5) {
+          if (c.gt < r) G->qtry[c.gt] = G->qcur[c.gt] + a * G->delta[c.gt];
+          group_sync(c.g);
+          set_layer1(c, S, G, G->qtry, r, p.b1);
+          double acc_phi = 0.0;
+          const int nt = (M + kS1 - 1) / kS1;
+          for (int t = 0; t < nt && ok; ++t)
+            ok = run_tile<kM, kS1, false, true>(c, p, o0, t, min(kS1, M - t * kS1), alpha, ea, eb, acc_phi);
+          if (!ok) break;
+          if (ea == -3) G->phi = 0.5 * acc_phi;
+          group_sync(c.g);
+          if (G->phi <= G->phi0 + kArmijoC1 * a * G->slope) {
+            if (c.gt < r) G->qcur[c.gt] = G->qtry[c.gt];
+            accepted = true;
+            break;
+          }
+        }
+        group_sync(c.g);
+        if (!ok || !accepted) break;  // no acceptable length: keep q and stop iterating
+      }
     }  // GN iterations
     if (!ok) break;
     if (c.gt < r) p.q[(size_t)inst * r + c.gt] = G->qcur[c.gt];
@@ -710,7 +770,9 @@ cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst
   p.wout = ctx->w.wout;
   p.bout = ctx->w.bout;
   p.pde = step->pde;
+  p.coef_per_sample = step->coef_per_sample;
   p.gn_iters = step->gn_iters;
+  p.line_search = step->line_search;
   p.dt = step->dt;
   p.n_inst = n_inst;
   p.q = q;

@@ -79,7 +79,7 @@ def increment_errors(params, m, q0, Y, q_gpu, q_ref, dt, alpha):
     dec = O.MLPDecoder(params, m)
     ev = dec(Y, q0)
     J = ev.gq
-    df = dt * float(alpha) * ev.lap
+    df = dt * np.asarray(alpha, np.float64) * ev.lap   # alpha: scalar or one value per sample
     d_gpu, d_ref = q_gpu - q0, q_ref - q0
     inc = float(np.linalg.norm(d_gpu - d_ref) / np.linalg.norm(d_ref))
     res = float(np.linalg.norm(J @ (d_gpu - d_ref)) / np.linalg.norm(df))

@@ -1,0 +1,107 @@
+"""Backtracking line search in the batched tensor-core step (paper §4.3: Gauss-Newton
+with a standard backtracking line search) against the FP64 oracle.
+
+The accept / reject decisions compare two objective values; the GPU forms them
+from FP32 network evaluations, the oracle in FP64.  Decisions are compared only
+where the oracle's margin |phi - bound| / bound exceeds 1e-3, far above the FP32
+evaluation error; everywhere the objective must not increase."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import crom_oracle as O
+from workloads import gen
+
+from helpers import StepInputs, increment_errors, make_ctx, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c():
+    from paper_2206_02607_gb300 import build
+    build()
+    from paper_2206_02607_gb300 import crom
+    return crom
+
+
+def _run(c, w, dt, gn_iters, line_search):
+    import torch
+    d = StepInputs(w)
+    c.crom_step(make_ctx(w.spec, w.params), d.q, d.alpha, d.s_off, d.samples, d.status, dt=dt, gn_iters=gn_iters,
+                max_samples=d.max_samples, precision=c.CROM_PREC_BF16X2, line_search=line_search)
+    torch.cuda.synchronize()
+    return d.q.cpu().numpy(), d.status.cpu().numpy()
+
+
+def test_full_steps_accepted_leave_the_step_unchanged(c):
+    """At the bench's time step the full GN step always satisfies the decrease
+    condition: with one iteration the result is bit-identical to no line search."""
+    w = gen.heat2d_batched(n_inst=16, m_lo=20, m_hi=400)
+    qa, sa = _run(c, w, w.dt, 1, 0)
+    qb, sb = _run(c, w, w.dt, 1, 4)
+    assert np.array_equal(sa, sb) and np.array_equal(qa, qb)
+
+
+def _phi(dec, Y, q, qn, df):
+    r = dec.value(Y, q) - dec.value(Y, qn) - df
+    return 0.5 * float(r @ r)
+
+
+def test_backtracking_matches_oracle_decisions(c):
+    """dt = 0.1 makes most full steps overshoot: one GN iteration with up to 6
+    halvings, compared with the oracle where its decisions are clear."""
+    w = gen.heat2d_batched(n_inst=12, m_lo=20, m_hi=120, bias_std=0.1)
+    dt = 0.1
+    q1, st = _run(c, w, dt, 1, 6)
+    dec = O.MLPDecoder(w.params, 2)
+    compared, backtracked = 0, 0
+    for i in range(w.n_inst):
+        Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
+        ref, rst, info = O.crom_step(dec, w.q0[i], Y, dt, 1, alpha=float(w.alpha[i]), line_search=6,
+                                     return_info=True)
+        assert st[i] == rst
+        trials = info["line_search_trials"][0]
+        if min(abs(p - b) / abs(b) for (_, p, b) in trials) < 1e-3:
+            continue
+        compared += 1
+        backtracked += len(trials) > 1
+        inc, res, kappa, margin = increment_errors(w.params, 2, w.q0[i], Y, q1[i], ref, dt, w.alpha[i])
+        assert res < (3e-3 if margin > 1e-4 else 5e-2), (i, inc, res, kappa, margin, len(trials))
+    assert compared >= 8 and backtracked >= 4, (compared, backtracked)
+
+
+def test_objective_never_increases(c):
+    """Three iterations with the line search at dt = 0.1: phi(q_{n+1}) <= phi(q_n)
+    (evaluated in FP64) for every instance."""
+    w = gen.heat2d_batched(n_inst=10, m_lo=20, m_hi=200, bias_std=0.1)
+    dt = 0.1
+    q1, st = _run(c, w, dt, 3, 8)
+    dec = O.MLPDecoder(w.params, 2)
+    for i in range(w.n_inst):
+        Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
+        assert st[i] == 0
+        ev = dec(Y, w.q0[i])
+        df = dt * float(w.alpha[i]) * ev.lap
+        phi_n = 0.5 * float(df @ df)
+        phi_1 = _phi(dec, Y, q1[i], w.q0[i], df)
+        assert phi_1 <= phi_n * (1 + 1e-6), (i, phi_1, phi_n)
+        # and it lands close to the oracle's three-iteration result
+        ref, _ = O.crom_step(dec, w.q0[i], Y, dt, 3, alpha=float(w.alpha[i]), line_search=8)
+        assert _phi(dec, Y, q1[i], w.q0[i], df) <= _phi(dec, Y, ref, w.q0[i], df) * 1.05 + 1e-12 * phi_n
+
+
+def test_line_search_argument_checks(c):
+    import torch
+    w = gen.heat2d_batched(n_inst=2, m_lo=20, m_hi=30)
+    ctx = make_ctx(w.spec, w.params)
+    d = StepInputs(w)
+    args = lambda prec, desc: (ctx.handle, ctypes.byref(desc), prec, w.n_inst, d.q.data_ptr(), d.alpha.data_ptr(),
+                               None, d.s_off.data_ptr(), d.samples.data_ptr(), int(w.sizes.sum()), d.max_samples,
+                               d.status.data_ptr(), None)
+    rc = c.raw_call("crom_step", *args(c.CROM_PREC_FP32, c.crom_step_desc(c.CROM_PDE_HEAT, 1, 1e-5, 0, 2)))
+    assert rc == c.CROM_ERR_UNSUPPORTED and "line search" in c.last_error()
+    rc = c.raw_call("crom_step", *args(c.CROM_PREC_BF16X2, c.crom_step_desc(c.CROM_PDE_HEAT, 1, 1e-5, 0, 17)))
+    assert rc == c.CROM_ERR_INVALID_ARG
+    torch.cuda.synchronize()

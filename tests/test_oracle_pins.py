@@ -396,3 +396,129 @@ def test_reconstruct_matches_value_channel():
     R = O.reconstruct(dec, codes, X)
     for c in range(3):
         np.testing.assert_allclose(R[c], dec(X, codes[c]).g, rtol=1e-13, atol=1e-15)
+
+
+# ------------------------------------------------------------------ f3: spatially varying nu(x)
+
+def test_fom_heat1d_field_energy_balance():
+    """u_t = nu(x) u_xx (App. G) with nu piecewise constant over 3 regions: the
+    discrete heat content sum_i u_i / nu_i changes by exactly dt/dx^2 times the
+    boundary fluxes -(u_1 + u_{P-2}) per step (interior telescoping sum with
+    Dirichlet-0 ends): stored energy + escaped energy = total, step by step."""
+    P = 201
+    dx = 1 / (P - 1)
+    x = np.arange(P) * dx
+    nu = gen.piecewise_nu(x[:, None], [0.2, 1.0, 0.6]).astype(np.float64)
+    _, u = gen.sine_modes_1d(P, np.random.default_rng(5))
+    dt = dx ** 2 / 4
+    for _ in range(60):
+        v = O.fom_heat1d_step(u, dt, nu)
+        stored = np.sum((v[1:-1] - u[1:-1]) / nu[1:-1])
+        escaped = -dt / dx ** 2 * (u[1] + u[-2])
+        assert abs(stored - escaped) < 1e-11 * (abs(escaped) + np.sum(np.abs(u)))
+        u = v
+
+
+def test_fom_heat_field_domain_of_dependence():
+    """A bump inside one region evolves exactly as with that region's constant nu
+    while its support (one node per step) stays inside the region."""
+    P = 301
+    dx = 1 / (P - 1)
+    x = np.arange(P) * dx
+    nu = gen.piecewise_nu(x[:, None], [0.3, 0.9, 0.5]).astype(np.float64)
+    u0 = np.where(np.abs(x - 0.5) < 0.05, np.cos((x - 0.5) / 0.05 * np.pi / 2) ** 2, 0.0)
+    dt = dx ** 2 / 4
+    a, b = u0.copy(), u0.copy()
+    for _ in range(20):   # support grows from |x - 0.5| < 0.05 by 20 dx = 0.067 < 1/6 - 0.05
+        a = O.fom_heat1d_step(a, dt, nu)
+        b = O.fom_heat1d_step(b, dt, nu[P // 2])   # the middle region's value
+    assert np.array_equal(a, b)
+    # 2D Neumann with a 4-region field: trapezoid-weighted sum of u / nu is conserved
+    n = 48
+    h = 1 / (n - 1)
+    t = np.arange(n) * h
+    X1, X2 = np.meshgrid(t, t, indexing="ij")
+    nu2 = gen.piecewise_nu(np.stack([X1.ravel(), X2.ravel()], 1), [0.2, 0.0, 0.2, 0.1]).reshape(n, n).astype(np.float64)
+    nu2 = np.where(nu2 == 0, 1.0, nu2)   # a zero region has no heat capacity weight; use 1 there (u unchanged)
+    w = np.ones(n); w[0] = w[-1] = 0.5
+    W = np.outer(w, w)
+    v = gen.gaussian_bumps_2d(n, np.random.default_rng(6))
+    m0 = np.sum(W * v / nu2)
+    for _ in range(30):
+        v = O.fom_heat2d_neumann_step(v, h ** 2 / 8, nu2)
+    assert abs(np.sum(W * v / nu2) - m0) < 1e-12 * abs(m0)
+
+
+def test_step_per_sample_coefficient_sine_decoder():
+    """Per-sample nu(y_j) in the latent step: for the sine decoder (linear in q) the
+    step is q_n + argmin ||S d - dt nu .* Lap g||, with S and Lap g written from the
+    sine formulas here (one GN iteration is exact; a second leaves q unchanged)."""
+    r = 4
+    dec = FourierDecoder1D(r)
+    Y = (np.arange(1, 16) / 16.0)[:, None]
+    nu = gen.piecewise_nu(Y, [0.2, 1.0, 0.5]).astype(np.float64)
+    q0 = np.random.default_rng(8).standard_normal(r)
+    dt = 1e-4
+    k = np.arange(1, r + 1)
+    S = np.sin(np.pi * np.outer(Y[:, 0], k))
+    lap = -(S * (np.pi * k) ** 2) @ q0
+    d_ref = np.linalg.lstsq(S, dt * nu * lap, rcond=None)[0]
+    for gn in (1, 2):
+        q1, st = O.crom_step(dec, q0, Y, dt, gn, alpha=nu)
+        assert st == O.STATUS_OK and rel(q1 - q0, d_ref) < 1e-10
+    # the region values matter: constant nu = 1 gives a different step
+    q_const, _ = O.crom_step(dec, q0, Y, dt, 1, alpha=1.0)
+    assert rel(q_const - q0, d_ref) > 0.1
+
+
+# ------------------------------------------------------------------ f1: backtracking line search
+
+class CubicDecoder:
+    """g(x, q) = q^3 + c x^2 (r = 1, m = 1): Lap g = 2c, dg/dq = 3 q^2 - a toy
+    nonlinearity whose Gauss-Newton steps can be followed by hand."""
+
+    def __init__(self, c):
+        self.c = c
+
+    def __call__(self, X, q):
+        x = np.asarray(X, np.float64)[:, 0]
+        q0 = float(np.asarray(q)[0])
+        g = q0 ** 3 + self.c * x ** 2
+        return O.Evaluation(g, (2 * self.c * x)[:, None], np.full((x.size, 1), 2 * self.c),
+                            np.full((x.size, 1), 3 * q0 ** 2))
+
+
+def test_line_search_by_hand_on_cubic():
+    """q_n = 1, Delta f = 2 dt alpha c = 9: the residual is rho(q) = q^3 - 10 at every
+    sample.  GN: delta = 3; a = 1 gives q = 4, rho = 54 (phi grows): rejected;
+    a = 1/2 gives q = 2.5, rho = 5.625: accepted.  Next: delta = -5.625/18.75 = -0.3,
+    accepted at a = 1, q = 2.2.  Without the line search: q = 4, then 4 - 54/48."""
+    dec = CubicDecoder(4.5)
+    Y = np.linspace(0.1, 0.9, 7)[:, None]
+    q, st, info = O.crom_step(dec, [1.0], Y, 1.0, 1, alpha=1.0, line_search=3, return_info=True)
+    assert st == O.STATUS_OK and q[0] == 2.5
+    assert [t[0] for t in info["line_search_trials"][0]] == [1.0, 0.5]
+    q, st = O.crom_step(dec, [1.0], Y, 1.0, 2, alpha=1.0, line_search=3)
+    assert abs(q[0] - 2.2) < 1e-14
+    q, st = O.crom_step(dec, [1.0], Y, 1.0, 2, alpha=1.0, line_search=0)
+    assert q[0] == 4.0 - 54.0 / 48.0
+    # no acceptable length among a = 1, 1/2 (target 1000): q stays, iterations stop
+    dec2 = CubicDecoder(499.5)
+    q, st, info = O.crom_step(dec2, [1.0], Y, 1.0, 3, alpha=1.0, line_search=1, return_info=True)
+    assert st == O.STATUS_OK and q[0] == 1.0 and len(info["line_search_trials"]) == 1
+
+
+def test_line_search_accepts_full_step_for_linear_decoders():
+    """For a decoder linear in q the objective is quadratic and the GN step is its
+    exact minimiser, phi(q + delta) = phi(q) + v.delta / 2 <= phi(q) + c1 v.delta:
+    the line search takes a = 1 in the first iteration.  Later iterations start at
+    the minimiser, where delta and the decrease are rounding noise: they may stop
+    the search, which leaves q at the minimiser."""
+    dec = FourierDecoder1D(5, offset=True)
+    Y = (np.arange(1, 14) / 14.0)[:, None]
+    q0 = np.random.default_rng(11).standard_normal(5)
+    a, sa = O.crom_step(dec, q0, Y, 1e-3, 3, alpha=0.7, line_search=0)
+    b, sb, info = O.crom_step(dec, q0, Y, 1e-3, 3, alpha=0.7, line_search=4, return_info=True)
+    assert sa == sb == O.STATUS_OK and rel(b - q0, a - q0) < 1e-12
+    first = info["line_search_trials"][0]
+    assert len(first) == 1 and first[0][0] == 1.0

@@ -34,7 +34,7 @@ __all__ = [
     "DecoderSpec", "bf16_round", "xavier_decoder", "pack_params", "param_count",
     "interior_nodes_1d", "interior_nodes_2d", "gaussian_bumps_2d", "sine_modes_1d",
     "StepWorkload", "heat1d_small", "heat2d_single", "heat2d_batched", "recon_dense",
-    "grid_points_2d", "ragged_offsets",
+    "grid_points_2d", "ragged_offsets", "piecewise_nu",
 ]
 
 
@@ -148,6 +148,16 @@ def gaussian_bumps_2d(n: int, rng, count: int = 8):
     for k in range(count):
         u += a[k] * np.exp(-((X1 - c[k, 0]) ** 2 + (X2 - c[k, 1]) ** 2) / (2 * s[k] ** 2))
     return u
+
+
+def piecewise_nu(x, values) -> np.ndarray:
+    """nu at points x [N][m] for a coefficient that is piecewise constant over
+    len(values) equal-width regions of [0, 1] along x_1 (region k holds
+    k/R <= x_1 < (k+1)/R, the last one closed).  Returns float32 [N]."""
+    values = np.asarray(values, np.float32)
+    R = values.shape[0]
+    k = np.clip(np.floor(np.asarray(x, np.float64)[:, 0] * R).astype(np.int64), 0, R - 1)
+    return values[k]
 
 
 def ragged_offsets(sizes) -> np.ndarray:
