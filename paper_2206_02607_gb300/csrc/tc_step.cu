@@ -396,7 +396,8 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
         split_store8(c.H, u, n, 64 + n, v[ch]);
       }
     }
-    tmem_st_wait();
+    // the s'(z) stores complete in the background: nothing reads those columns
+    // before the reverse pass, which waits for them
   }
   // ---------------- output layer: PRJ[n][0] = w_out . h_L[:, n], hi rows + lo rows
   if (!stage<kStageProj>(c, 0, 0)) return false;
@@ -436,6 +437,7 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
     }
     G->rho[c.gt] = rho;
   }
+  tmem_st_wait();  // s'(z) of the forward pass is in TMEM
   if (kValueOnly) {  // line-search trial: only sum_j rho_j^2 is needed
     group_sync(c.g);
     if (ea == -3) acc += dot_exact(G->rho, G->zero, 1, G->rho, G->zero, 1, ns);
