@@ -163,7 +163,7 @@ int crom_decode(crom_ctx* ctx, int n_inst, const double* q, const int* pt_off, c
  *   context grows its scratch on first use, so the first call for a given size
  *   must not be made during stream capture.
  * precision CROM_PREC_BF16X2: one persistent launch per step; each CTA takes
- *   whole instances from a queue (|M_i| <= 2048). */
+ *   whole instances from a queue. */
 int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_inst, double* q,
               const float* alpha, const float* vel, const int* s_off, const float* samples,
               int n_samples, int max_samples, int* status, crom_stream stream);
@@ -268,6 +268,34 @@ int crom_encode(crom_trainer* tr, int n, const float* snaps, float* q, crom_stre
  * precision FP32 (any shape), BF16X2 or BF16 (tensor cores; width 128). */
 int crom_reconstruct(crom_ctx* ctx, int precision, int n_codes, const double* q, int n_pts,
                      const float* x, float* out, crom_stream stream);
+
+/* Robust integration-sample selection (paper App. B, Algorithm 1): greedy
+ * growth of the sample set M from n_init starting nodes.  Each round computes,
+ * for the current M, res[i] = sum over training parameters mu of
+ * |g(x_i, q_T(mu)) - f_FOM(x_i, T; mu)| at every FOM node, where q_T(mu) is the
+ * latent state after n_steps steps (`step`, `precision`) from q0[mu] with
+ * samples M; Metric = mean(res) + max(res).  While Metric >= target and
+ * |M| < max_samples, the n_try nodes with the largest res (not in M; ties to the
+ * lower index) are tried, each as M + {x_i}, and the one with the smallest Metric
+ * (ties to the earlier) is added.  A set whose rollout reports a non-OK step
+ * status has Metric = +inf.  All candidate sets x parameters of a round run as one
+ * batched rollout (one instance each), then one dense reconstruction.
+ *  q0        [n_params][r] FP64, device
+ *  coef      [n_params] FP32 (coef_per_sample = 0) or [n_params][n_nodes]
+ *            (coef_per_sample = 1: nu at every node), device
+ *  nodes     [n_nodes][m] FP32 node coordinates, device
+ *  fom_final [n_params][n_nodes] FP32 FOM fields at the final step, device
+ *  init_idx  [n_init] distinct node indices, host
+ *  idx_out   [max_samples] host: the selected node indices in order of addition
+ *            (the initial ones first); count_out, metric_out host scalars.
+ * step->pde must be CROM_PDE_HEAT; precision FP32 (no line search) or BF16X2.
+ * Limits: 1 <= n_try <= 64, n_init <= max_samples <= min(n_nodes, 4096),
+ * n_try * n_params <= 65535.  The call allocates its work buffers and returns
+ * after the work on `stream` completed (not usable during stream capture). */
+int crom_robust_samples(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_params, const double* q0,
+                        const float* coef, int n_steps, int n_nodes, const float* nodes, const float* fom_final,
+                        int n_init, const int* init_idx, int n_try, double target, int max_samples, int* idx_out,
+                        int* count_out, double* metric_out, crom_stream stream);
 
 #ifdef __cplusplus
 }

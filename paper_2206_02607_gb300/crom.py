@@ -45,7 +45,7 @@ EXPORTED = ("crom_version", "crom_last_error", "crom_create", "crom_destroy", "c
             "crom_decode", "crom_step", "crom_rollout", "crom_step_noalloc", "crom_fom_step", "crom_trainer_create",
             "crom_trainer_destroy", "crom_trainer_param_count", "crom_trainer_set_params",
             "crom_trainer_get_params", "crom_trainer_get_grads", "crom_train_step", "crom_encode",
-            "crom_reconstruct")
+            "crom_reconstruct", "crom_robust_samples")
 
 
 class CromError(RuntimeError):
@@ -87,6 +87,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.crom_train_step.argtypes = [vp, vp, vp, vp, ctypes.c_float, vp, vp]
     lib.crom_encode.argtypes = [vp, i, vp, vp, vp]
     lib.crom_reconstruct.argtypes = [vp, i, i, vp, i, vp, vp, vp]
+    lib.crom_robust_samples.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, i, vp, vp, i, i, vp, vp, i, vp, i,
+                                        d, i, vp, vp, vp, vp]
     for name in EXPORTED:
         if name not in ("crom_version", "crom_last_error"):
             getattr(lib, name).restype = i
@@ -295,6 +297,29 @@ def crom_reconstruct(ctx: CromContext, q, x, out, precision: int = CROM_PREC_FP3
     _need(q, torch.float64, "q"); _need(x, torch.float32, "x"); _need(out, torch.float32, "out")
     _check(_LIB.crom_reconstruct(ctx.handle, precision, q.shape[0], _ptr(q), x.shape[0], _ptr(x), _ptr(out),
                                  _stream(stream)))
+
+
+def crom_robust_samples(ctx: CromContext, q0, coef, nodes, fom_final, init_idx, *, dt: float, gn_iters: int,
+                        n_steps: int, n_try: int, target: float, max_samples: int,
+                        precision: int = CROM_PREC_FP32, coef_per_sample: bool = False, line_search: int = 0,
+                        stream=None):
+    """Greedy robust sample selection (see crom.h).  q0 [n_params, r] float64,
+    coef [n_params] or [n_params, n_nodes] float32, nodes [n_nodes, m] float32,
+    fom_final [n_params, n_nodes] float32 (CUDA tensors); init_idx: host ints.
+    Returns (indices, metric)."""
+    import torch
+    _need(q0, torch.float64, "q0"); _need(coef, torch.float32, "coef"); _need(nodes, torch.float32, "nodes")
+    _need(fom_final, torch.float32, "fom_final")
+    init = (ctypes.c_int * max(len(init_idx), 1))(*[int(i) for i in init_idx])
+    out = (ctypes.c_int * max_samples)()
+    count = ctypes.c_int()
+    met = ctypes.c_double()
+    desc = crom_step_desc(CROM_PDE_HEAT, gn_iters, dt, int(bool(coef_per_sample)), int(line_search))
+    _check(_LIB.crom_robust_samples(ctx.handle, ctypes.byref(desc), precision, q0.shape[0], _ptr(q0), _ptr(coef),
+                                    n_steps, nodes.shape[0], _ptr(nodes), _ptr(fom_final), len(init_idx), init,
+                                    n_try, float(target), max_samples, out, ctypes.byref(count),
+                                    ctypes.byref(met), _stream(stream)))
+    return [out[k] for k in range(count.value)], met.value
 
 
 def raw_call(name: str, *args) -> int:

@@ -75,6 +75,23 @@ struct DeviceGuard {
   }
 };
 
+// Device allocations freed together when the holder goes out of scope; the first
+// failure is kept in err and later requests return nullptr.
+struct DeviceAllocs {
+  std::vector<void*> ptrs;
+  cudaError_t err = cudaSuccess;
+  template <class T>
+  T* get(size_t n) {
+    void* p = nullptr;
+    if (err == cudaSuccess) err = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T));
+    if (p) ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  ~DeviceAllocs() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+
 bool tc_shape_ok(const crom_decoder_desc& d) {
   return d.width == kTcWidth && d.hidden >= 2 && d.hidden <= 5 && d.m >= 1 && d.m <= 2 &&
          d.r >= 1 && d.r <= kTcProjRows - 1;
@@ -548,6 +565,137 @@ int crom_reconstruct(crom_ctx* ctx, int precision, int n_codes, const double* q,
     return fail(CROM_ERR_UNSUPPORTED, "crom_reconstruct: unknown precision");
   }
   if (e != cudaSuccess) return cuda_fail(e, "crom_reconstruct");
+  return CROM_OK;
+}
+
+int crom_robust_samples(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_params, const double* q0,
+                        const float* coef, int n_steps, int n_nodes, const float* nodes, const float* fom_final,
+                        int n_init, const int* init_idx, int n_try, double target, int max_samples, int* idx_out,
+                        int* count_out, double* metric_out, crom_stream stream) {
+  const char* fn = "crom_robust_samples";
+  if (!ctx || !step || !init_idx || !idx_out || !count_out || !metric_out)
+    return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": null argument");
+  if (!ctx->has_weights) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": weights not set");
+  if (!q0 || !coef || !nodes || !fom_final) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": null array");
+  if (n_params < 1 || n_steps < 0 || n_nodes < 1 || n_init < 0 || n_try < 1 || n_try > 64 || max_samples < n_init ||
+      max_samples > 4096 || max_samples > n_nodes || (size_t)n_try * n_params > 65535 || !(target >= 0.0))
+    return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": bad sizes (n_params, n_nodes >= 1; 1 <= n_try <= 64; "
+                                                        "n_init <= max_samples <= min(n_nodes, 4096); target >= 0)");
+  if (step->pde != CROM_PDE_HEAT || step->line_search < 0 || step->line_search > 16 || step->gn_iters < 1 ||
+      step->gn_iters > 16 || !(step->dt > 0.0) || !isfinite(step->dt) ||
+      (step->coef_per_sample != 0 && step->coef_per_sample != 1))
+    return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": needs a heat step with valid gn_iters, dt, coefficient mode");
+  if (precision == CROM_PREC_BF16X2) {
+    if (!tc_shape_ok(ctx->desc) || !ctx->w.tc_img)
+      return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": BF16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15");
+  } else if (precision != CROM_PREC_FP32 || step->line_search > 0) {
+    return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": precision FP32 (no line search) or BF16X2");
+  }
+  std::vector<int> M(init_idx, init_idx + n_init);
+  {
+    std::vector<char> seen(n_nodes, 0);
+    for (int i : M) {
+      if (i < 0 || i >= n_nodes || seen[i]) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": bad initial index");
+      seen[i] = 1;
+    }
+  }
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int m = ctx->desc.m, r = ctx->desc.r;
+  const int max_inst = n_try * n_params;
+  const size_t max_samp = (size_t)max_inst * max_samples;
+  // Work buffers for one batch of candidate sets (freed on every exit path).
+  DeviceAllocs buf;
+  int* d_idx = buf.get<int>(max_samp);
+  int* d_param = buf.get<int>(max_samp);
+  float* d_samples = buf.get<float>(max_samp * m);
+  float* d_alpha_s = buf.get<float>(max_samp);
+  int* d_off = buf.get<int>(max_inst + 1);
+  double* d_q = buf.get<double>((size_t)max_inst * r);
+  float* d_alpha = buf.get<float>(max_inst);
+  int* d_status = buf.get<int>(max_inst);
+  float* d_out = buf.get<float>((size_t)max_inst * n_nodes);
+  double* d_res = buf.get<double>((size_t)(n_try + 1) * n_nodes);
+  double* d_metric = buf.get<double>(n_try);
+  int* d_taken = buf.get<int>(n_nodes);
+  int* d_cand = buf.get<int>(n_try);
+  if (buf.err != cudaSuccess) return cuda_fail(buf.err, fn);
+  crom_step_desc sd = *step;
+
+  // Metric of each candidate set (sets[c] = M plus extra[c], extra -1 = none);
+  // their residual rows land in d_res rows 0..C-1.
+  auto evaluate = [&](const std::vector<int>& extra, std::vector<double>& metrics) -> cudaError_t {
+    const int C = (int)extra.size(), n_inst = C * n_params;
+    std::vector<int> h_idx, h_param, h_off(1, 0);
+    int max_s = 1;
+    for (int c = 0; c < C; ++c)
+      for (int mu = 0; mu < n_params; ++mu) {
+        for (int i : M) { h_idx.push_back(i); h_param.push_back(mu); }
+        if (extra[c] >= 0) { h_idx.push_back(extra[c]); h_param.push_back(mu); }
+        h_off.push_back((int)h_idx.size());
+        max_s = std::max(max_s, h_off.back() - h_off[h_off.size() - 2]);
+      }
+    const int n_s = (int)h_idx.size();
+    cudaError_t e = cudaMemcpyAsync(d_idx, h_idx.data(), (size_t)n_s * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_param, h_param.data(), (size_t)n_s * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, h_off.data(), h_off.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = launch_sampling_gather(nodes, d_idx, d_param, n_s, m, n_nodes, sd.coef_per_sample ? coef : nullptr,
+                                 d_samples, d_alpha_s, s);
+    if (e == cudaSuccess)
+      e = launch_sampling_replicate(q0, sd.coef_per_sample ? nullptr : coef, n_params, n_inst, r, d_q, d_alpha, s);
+    const float* a = sd.coef_per_sample ? d_alpha_s : d_alpha;
+    if (e == cudaSuccess && n_steps == 0) e = cudaMemsetAsync(d_status, 0, (size_t)n_inst * sizeof(int), s);
+    for (int t = 0; t < n_steps && e == cudaSuccess; ++t)
+      e = precision == CROM_PREC_BF16X2
+              ? launch_step_tc(ctx, &sd, n_inst, d_q, a, nullptr, d_off, d_samples, n_s, max_s, d_status, s)
+              : launch_step_fp32(ctx, &sd, n_inst, d_q, a, nullptr, d_off, d_samples, n_s, max_s, d_status, s);
+    if (e == cudaSuccess) e = launch_recon_fp32(ctx, n_inst, d_q, n_nodes, nodes, d_out, s);
+    if (e == cudaSuccess) e = launch_sampling_metric(d_out, fom_final, d_status, C, n_params, n_nodes, d_res, d_metric, s);
+    metrics.assign(C, 0.0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(metrics.data(), d_metric, C * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+  };
+
+  std::vector<double> met;
+  cudaError_t e = evaluate(std::vector<int>{-1}, met);
+  if (e != cudaSuccess) return cuda_fail(e, fn);
+  double cur = met[0];
+  // d_res row 0 holds the residual of M; the candidates' rows go after it.
+  while (!(cur < target) && (int)M.size() < max_samples) {
+    std::vector<char> taken(n_nodes, 0);
+    for (int i : M) taken[i] = 1;
+    std::vector<int> h_taken(taken.begin(), taken.end());
+    e = cudaMemcpyAsync(d_taken, h_taken.data(), (size_t)n_nodes * sizeof(int), cudaMemcpyHostToDevice, s);
+    const int k = std::min(n_try, n_nodes - (int)M.size());
+    if (e == cudaSuccess) e = launch_sampling_topk(d_res, d_taken, n_nodes, k, d_cand, s);
+    std::vector<int> cand(k, -1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cand.data(), d_cand, k * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, fn);
+    cand.erase(std::remove(cand.begin(), cand.end(), -1), cand.end());
+    if (cand.empty()) break;
+    // candidates' residual rows 1..k: shift the batch by one row
+    double* base_res = d_res;
+    d_res = base_res + n_nodes;
+    e = evaluate(cand, met);
+    d_res = base_res;
+    if (e != cudaSuccess) return cuda_fail(e, fn);
+    int best = 0;
+    for (int c = 1; c < (int)cand.size(); ++c)
+      if (met[c] < met[best]) best = c;
+    M.push_back(cand[best]);
+    cur = met[best];
+    e = cudaMemcpyAsync(d_res, d_res + (size_t)(1 + best) * n_nodes, (size_t)n_nodes * sizeof(double),
+                        cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, fn);
+  }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, fn);
+  std::copy(M.begin(), M.end(), idx_out);
+  *count_out = (int)M.size();
+  *metric_out = cur;
   return CROM_OK;
 }
 

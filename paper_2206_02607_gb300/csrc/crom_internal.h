@@ -145,4 +145,14 @@ cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst
 cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const double* q, int n_pts,
                             const float* x, float* out, cudaStream_t s);
 
+// Robust-sample selection kernels (sampling.cu).
+cudaError_t launch_sampling_gather(const float* nodes, const int* idx, const int* param_of, int n, int m,
+                                   int n_nodes, const float* coef_nodes, float* samples, float* alpha_s,
+                                   cudaStream_t s);
+cudaError_t launch_sampling_replicate(const double* q0, const float* coef, int n_params, int n_inst, int r,
+                                      double* q, float* alpha, cudaStream_t s);
+cudaError_t launch_sampling_metric(const float* out, const float* fom, const int* status, int n_cand, int n_params,
+                                   int n_nodes, double* res, double* metric, cudaStream_t s);
+cudaError_t launch_sampling_topk(const double* res, int* taken, int n_nodes, int k, int* out, cudaStream_t s);
+
 }  // namespace crom
