@@ -77,14 +77,36 @@ enum {
   CROM_WANT_DQ = 16u
 };
 
+/* Hidden-layer activation (paper App. D: ELU or SIREN, both continuously
+ * differentiable).  ELU: s(z) = z (z > 0), e^z - 1 otherwise.  SIREN:
+ * s(z) = sin(omega0 z) with omega0 = 30 by default (Sitzmann et al.). */
+typedef enum { CROM_ACT_ELU = 0, CROM_ACT_SIREN = 1 } crom_activation;
+
 /* Decoder shape: m spatial dims (1..3), r latent dims (1..32), width of the
- * hidden layers, hidden = number of ELU hidden layers (1..8).  Output dim d = 1. */
+ * hidden layers, hidden = number of hidden layers (1..8), their activation, and
+ * omega0 for SIREN (0 selects 30; ignored for ELU).  Output dim d = 1; the
+ * output layer is linear.  Derivatives are taken with respect to the decoder's
+ * input coordinates x (for SIREN the paper feeds x scaled to [-1, 1]; the
+ * caller states the PDE in the coordinates it feeds). */
 typedef struct {
   int m;
   int r;
   int width;
   int hidden;
+  int activation;
+  float omega0;
 } crom_decoder_desc;
+
+/* Tangent-space velocity of the field (paper App. L, "Solid Mechanics": the second-order-in-time
+ * elastodynamics ROM): v(x_p) = (dg/dq)(x_p, q_i) . qdot_i with
+ * qdot_i = (q_i - q_prev_i) / dt (q_prev = q gives qdot = 0, the start of a
+ * rollout).  Points as in crom_decode (instance i owns points
+ * pt_off[i] .. pt_off[i+1]-1); q, q_prev [n_inst][r] FP64; out [n_pts] FP32.
+ * FP32 evaluation of the r Jacobian channels, contraction in FP64.  The
+ * context keeps an r x n_pts scratch (grown on demand: do not call during
+ * stream capture with a larger n_pts than before). */
+int crom_tangent_velocity(crom_ctx* ctx, int n_inst, const double* q, const double* q_prev, double dt,
+                          const int* pt_off, const float* x, int n_pts, float* out, crom_stream stream);
 
 /* One latent step.
  *  pde      : CROM_PDE_HEAT     Delta f_j = dt * alpha * Lap g(y_j, q_n)

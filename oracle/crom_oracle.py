@@ -8,10 +8,11 @@ independent solver used by the pins).
 
 What it follows (section / equation / algorithm of arXiv 2206.02607):
 
-* Decoder g(x, q): an MLP R^{m+r} -> R with ELU hidden layers and a linear output
-  layer (App. D).  ELU with alpha = 1 (Clevert et al.):
+* Decoder g(x, q): an MLP R^{m+r} -> R with ELU or SIREN hidden layers and a
+  linear output layer (App. D).  ELU with alpha = 1 (Clevert et al.):
   s(z) = z (z > 0) else expm1(z); s'(z) = 1 (z > 0) else e^z; s''(z) = 0 (z > 0) else e^z.
-  The tie z = 0 takes the negative branch.
+  The tie z = 0 takes the negative branch.  SIREN (Sitzmann et al., omega0 = 30):
+  s(z) = sin(omega0 z); s'(z) = omega0 cos(omega0 z); s''(z) = -omega0^2 sin(omega0 z).
 * Step 1, network inference (§4.1, Algorithm 4): value, spatial gradient and the
   latent Jacobian dg/dq at every integration sample.  Derivatives are carried
   layer by layer with the value in one forward pass, which is Algorithm 2
@@ -47,9 +48,9 @@ STATUS_SINGULAR = 3
 STATUS_NONFINITE = 4
 
 __all__ = [
-    "elu", "elu_d1", "elu_d2", "Evaluation", "MLPDecoder", "cholesky_solve", "lls_qr",
+    "elu", "elu_d1", "elu_d2", "siren", "siren_d1", "siren_d2", "Evaluation", "MLPDecoder", "cholesky_solve", "lls_qr",
     "heat_delta_f", "advdiff_delta_f", "crom_step", "crom_rollout", "crom_step_batched",
-    "reconstruct", "fom_heat1d_step", "fom_heat2d_neumann_step", "fom_advdiff2d_step",
+    "reconstruct", "tangent_velocity", "fom_heat1d_step", "fom_heat2d_neumann_step", "fom_advdiff2d_step",
     "STATUS_OK", "STATUS_BAD_ARG", "STATUS_SINGULAR", "STATUS_NONFINITE",
 ]
 
@@ -69,6 +70,19 @@ def elu_d1(z):
 def elu_d2(z):
     """Second derivative of ELU."""
     return np.where(z > 0, 0.0, np.exp(np.minimum(z, 0.0)))
+
+
+def siren(z, w0=30.0):
+    """SIREN activation sin(omega0 z) (App. D)."""
+    return np.sin(w0 * z)
+
+
+def siren_d1(z, w0=30.0):
+    return w0 * np.cos(w0 * z)
+
+
+def siren_d2(z, w0=30.0):
+    return -w0 * w0 * np.sin(w0 * z)
 
 
 # ---------------------------------------------------------------- decoder (Step 1)
@@ -95,11 +109,18 @@ class MLPDecoder:
     params: list of (W [out][in], b [out]); layer 1 input is (x_1..x_m, q_1..q_r).
     """
 
-    def __init__(self, params, m: int):
+    def __init__(self, params, m: int, activation: str = "elu", omega0: float = 30.0):
         self.params = [(np.asarray(W, np.float64), np.asarray(b, np.float64)) for W, b in params]
         self.m = m
         self.r = self.params[0][0].shape[1] - m
         self.width = self.params[0][0].shape[0]
+        if activation == "elu":
+            self.acts = (elu, elu_d1, elu_d2)
+        elif activation == "siren":
+            w0 = float(omega0)
+            self.acts = (lambda z: siren(z, w0), lambda z: siren_d1(z, w0), lambda z: siren_d2(z, w0))
+        else:
+            raise ValueError(activation)
 
     def __call__(self, X, Q) -> Evaluation:
         return self.evaluate(X, Q)
@@ -119,7 +140,7 @@ class MLPDecoder:
         d2z_x = [np.zeros_like(z) for _ in range(m)]
         dz_q = [np.broadcast_to(W1[:, m + j], z.shape) for j in range(r)]
         for W, b in self.params[1:]:
-            s0, s1, s2 = elu(z), elu_d1(z), elu_d2(z)
+            s0, s1, s2 = self.acts[0](z), self.acts[1](z), self.acts[2](z)
             h = s0
             dh_x = [s1 * dz_x[k] for k in range(m)]
             d2h_x = [s2 * dz_x[k] ** 2 + s1 * d2z_x[k] for k in range(m)]
@@ -142,7 +163,7 @@ class MLPDecoder:
         h = np.concatenate([X, Q], axis=1)
         for li, (W, b) in enumerate(self.params):
             z = h @ W.T + b
-            h = elu(z) if li + 1 < len(self.params) else z
+            h = self.acts[0](z) if li + 1 < len(self.params) else z
         return h[:, 0]
 
 
@@ -301,6 +322,13 @@ def crom_rollout(decoder, q0, Y, dt, gn_iters, steps, alpha=1.0):
             raise RuntimeError(f"oracle step failed with status {st}")
         traj.append(q)
     return np.stack(traj)
+
+
+def tangent_velocity(decoder, X, q, q_prev, dt: float):
+    """Velocity of the field on the manifold's tangent space (App. L, Solid
+    Mechanics): v(x) = dg/dq(x, q_n) . qdot with qdot = (q_n - q_{n-1}) / dt."""
+    qdot = (np.asarray(q, np.float64) - np.asarray(q_prev, np.float64)) / dt
+    return decoder(X, q).gq @ qdot
 
 
 # ------------------------------------------------------------ reconstruction

@@ -38,6 +38,8 @@ CROM_WANT_DQ = 16
 CROM_FOM_HEAT1D_DIRICHLET = 0
 CROM_FOM_HEAT2D_NEUMANN = 1
 CROM_FOM_ADVDIFF2D_PERIODIC = 2
+CROM_ACT_ELU = 0
+CROM_ACT_SIREN = 1
 CROM_FOM_HEAT1D_DIRICHLET_FIELD = 3
 CROM_FOM_HEAT2D_NEUMANN_FIELD = 4
 
@@ -45,7 +47,7 @@ EXPORTED = ("crom_version", "crom_last_error", "crom_create", "crom_destroy", "c
             "crom_decode", "crom_step", "crom_rollout", "crom_step_noalloc", "crom_fom_step", "crom_trainer_create",
             "crom_trainer_destroy", "crom_trainer_param_count", "crom_trainer_set_params",
             "crom_trainer_get_params", "crom_trainer_get_grads", "crom_train_step", "crom_encode",
-            "crom_reconstruct", "crom_robust_samples")
+            "crom_reconstruct", "crom_robust_samples", "crom_tangent_velocity")
 
 
 class CromError(RuntimeError):
@@ -55,7 +57,8 @@ class CromError(RuntimeError):
 
 
 class crom_decoder_desc(ctypes.Structure):
-    _fields_ = [("m", ctypes.c_int), ("r", ctypes.c_int), ("width", ctypes.c_int), ("hidden", ctypes.c_int)]
+    _fields_ = [("m", ctypes.c_int), ("r", ctypes.c_int), ("width", ctypes.c_int), ("hidden", ctypes.c_int),
+                ("activation", ctypes.c_int), ("omega0", ctypes.c_float)]
 
 
 class crom_step_desc(ctypes.Structure):
@@ -87,6 +90,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.crom_train_step.argtypes = [vp, vp, vp, vp, ctypes.c_float, vp, vp]
     lib.crom_encode.argtypes = [vp, i, vp, vp, vp]
     lib.crom_reconstruct.argtypes = [vp, i, i, vp, i, vp, vp, vp]
+    lib.crom_tangent_velocity.argtypes = [vp, i, vp, vp, d, vp, vp, i, vp, vp]
     lib.crom_robust_samples.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, i, vp, vp, i, i, vp, vp, i, vp, i,
                                         d, i, vp, vp, vp, vp]
     for name in EXPORTED:
@@ -133,8 +137,9 @@ def crom_version() -> int:
 class CromContext:
     """Owns a crom_ctx (decoder shape + weights on one device)."""
 
-    def __init__(self, m: int, r: int, width: int, hidden: int, device: int = 0):
-        self.desc = crom_decoder_desc(m, r, width, hidden)
+    def __init__(self, m: int, r: int, width: int, hidden: int, device: int = 0, activation: int = 0,
+                 omega0: float = 30.0):
+        self.desc = crom_decoder_desc(m, r, width, hidden, activation, omega0 if activation else 0.0)
         self.handle = ctypes.c_void_p()
         _check(_LIB.crom_create(ctypes.byref(self.handle), ctypes.byref(self.desc), device))
         self.device = device
@@ -151,8 +156,8 @@ class CromContext:
             pass
 
 
-def crom_create(m, r, width, hidden, device=0) -> CromContext:
-    return CromContext(m, r, width, hidden, device)
+def crom_create(m, r, width, hidden, device=0, activation=0, omega0=30.0) -> CromContext:
+    return CromContext(m, r, width, hidden, device, activation, omega0)
 
 
 def crom_destroy(ctx: CromContext):
@@ -297,6 +302,15 @@ def crom_reconstruct(ctx: CromContext, q, x, out, precision: int = CROM_PREC_FP3
     _need(q, torch.float64, "q"); _need(x, torch.float32, "x"); _need(out, torch.float32, "out")
     _check(_LIB.crom_reconstruct(ctx.handle, precision, q.shape[0], _ptr(q), x.shape[0], _ptr(x), _ptr(out),
                                  _stream(stream)))
+
+
+def crom_tangent_velocity(ctx: CromContext, q, q_prev, pt_off, x, out, *, dt: float, stream=None):
+    """v(x_p) = dg/dq(x_p, q_i) . (q_i - q_prev_i) / dt (see crom.h)."""
+    import torch
+    _need(q, torch.float64, "q"); _need(q_prev, torch.float64, "q_prev"); _need(pt_off, torch.int32, "pt_off")
+    _need(x, torch.float32, "x"); _need(out, torch.float32, "out")
+    _check(_LIB.crom_tangent_velocity(ctx.handle, q.shape[0], _ptr(q), _ptr(q_prev), dt, _ptr(pt_off), _ptr(x),
+                                      x.shape[0], _ptr(out), _stream(stream)))
 
 
 def crom_robust_samples(ctx: CromContext, q0, coef, nodes, fom_final, init_idx, *, dt: float, gn_iters: int,

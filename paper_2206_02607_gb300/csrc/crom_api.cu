@@ -94,7 +94,7 @@ struct DeviceAllocs {
 
 bool tc_shape_ok(const crom_decoder_desc& d) {
   return d.width == kTcWidth && d.hidden >= 2 && d.hidden <= 5 && d.m >= 1 && d.m <= 2 &&
-         d.r >= 1 && d.r <= kTcProjRows - 1;
+         d.r >= 1 && d.r <= kTcProjRows - 1 && d.activation == CROM_ACT_ELU;
 }
 
 }  // namespace
@@ -111,11 +111,15 @@ const char* crom_last_error(void) { return g_last_error.c_str(); }
 int crom_create(crom_ctx** out, const crom_decoder_desc* desc, int device) {
   if (!out || !desc) return fail(CROM_ERR_INVALID_ARG, "crom_create: null argument");
   *out = nullptr;
-  const crom_decoder_desc d = *desc;
+  crom_decoder_desc d = *desc;
   if (d.m < 1 || d.m > 3 || d.r < 1 || d.r > 32 || d.width < 32 || d.width > 256 ||
       d.width % 32 != 0 || d.hidden < 1 || d.hidden > 8)
     return fail(CROM_ERR_INVALID_ARG,
                 "crom_create: need 1<=m<=3, 1<=r<=32, width%32==0 in [32,256], 1<=hidden<=8");
+  if (d.activation != CROM_ACT_ELU && d.activation != CROM_ACT_SIREN)
+    return fail(CROM_ERR_INVALID_ARG, "crom_create: unknown activation");
+  if (!(d.omega0 >= 0.f) || !isfinite(d.omega0)) return fail(CROM_ERR_INVALID_ARG, "crom_create: bad omega0");
+  if (d.activation == CROM_ACT_SIREN && d.omega0 == 0.f) d.omega0 = 30.f;
   int n = 0;
   cudaError_t e = cudaGetDeviceCount(&n);
   if (e != cudaSuccess || n == 0) return fail(CROM_ERR_CUDA, "crom_create: no CUDA device");
@@ -153,6 +157,7 @@ int crom_destroy(crom_ctx* ctx) {
     cudaFree(ctx->counters);
     cudaFree(ctx->targets);
     cudaFree(ctx->qbase);
+    cudaFree(ctx->tangent);
     cudaFree(ctx->order);
     cudaFree(ctx->queue);
     if (ctx->rollout_exec) cudaGraphExecDestroy(ctx->rollout_exec);
@@ -270,6 +275,34 @@ int crom_decode(crom_ctx* ctx, int n_inst, const double* q, const int* pt_off, c
   return CROM_OK;
 }
 
+int crom_tangent_velocity(crom_ctx* ctx, int n_inst, const double* q, const double* q_prev, double dt,
+                          const int* pt_off, const float* x, int n_pts, float* out, crom_stream stream) {
+  const char* fn = "crom_tangent_velocity";
+  if (!ctx) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": null context");
+  if (!ctx->has_weights) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": weights not set");
+  if (n_inst < 0 || n_pts < 0) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": negative size");
+  if (!(dt > 0.0) || !isfinite(dt)) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": dt must be finite and > 0");
+  if (n_pts == 0) return CROM_OK;
+  if (n_inst == 0 || !q || !q_prev || !pt_off || !x || !out)
+    return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": null array or no instance for the points");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t need = (size_t)ctx->desc.r * n_pts;
+  if (need > ctx->tangent_cap) {
+    cudaFree(ctx->tangent);
+    ctx->tangent = nullptr;
+    ctx->tangent_cap = 0;
+    cudaError_t e = cudaMalloc(&ctx->tangent, need * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(e, fn);
+    ctx->tangent_cap = need;
+  }
+  cudaError_t e = launch_decode_fp32(ctx, n_inst, q, pt_off, x, n_pts, CROM_WANT_DQ, ctx->tangent, s);
+  if (e == cudaSuccess)
+    e = launch_tangent_contract(ctx->tangent, q, q_prev, dt, pt_off, n_inst, ctx->desc.r, n_pts, out, s);
+  if (e != cudaSuccess) return cuda_fail(e, fn);
+  return CROM_OK;
+}
+
 int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_inst, double* q,
               const float* alpha, const float* vel, const int* s_off, const float* samples,
               int n_samples, int max_samples, int* status, crom_stream stream) {
@@ -297,7 +330,7 @@ int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_in
     e = launch_step_fp32(ctx, step, n_inst, q, alpha, vel, s_off, samples, n_samples, max_samples, status, s);
   } else if (precision == CROM_PREC_BF16X2) {
     if (!tc_shape_ok(ctx->desc) || !ctx->w.tc_img)
-      return fail(CROM_ERR_UNSUPPORTED, "crom_step: BF16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15");
+      return fail(CROM_ERR_UNSUPPORTED, "crom_step: BF16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15, ELU");
     e = launch_step_tc(ctx, step, n_inst, q, alpha, vel, s_off, samples, n_samples, max_samples, status, s);
   } else {
     return fail(CROM_ERR_UNSUPPORTED, "crom_step: precision not available for the step");
@@ -330,7 +363,7 @@ int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n
   if (max_samples < 1) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: max_samples must be >= 1");
   if (precision == CROM_PREC_BF16X2) {
     if (!tc_shape_ok(ctx->desc) || !ctx->w.tc_img)
-      return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: BF16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15");
+      return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: BF16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15, ELU");
   } else if (precision != CROM_PREC_FP32) {
     return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: precision not available for the step");
   }
@@ -446,6 +479,8 @@ int crom_trainer_create(crom_trainer** out, const crom_decoder_desc* dec, int P,
   const crom_decoder_desc d = *dec;
   if (d.m < 1 || d.m > 3 || d.r < 1 || d.r > 32 || d.width < 1 || d.width > 1024 || d.hidden < 1 || d.hidden > 8)
     return fail(CROM_ERR_INVALID_ARG, "crom_trainer_create: bad decoder shape");
+  if (d.activation != CROM_ACT_ELU)
+    return fail(CROM_ERR_UNSUPPORTED, "crom_trainer_create: the training step is built for ELU decoders");
   if (P < 38 || B < 1 || S < 1 || (long long)B * S > (1LL << 26))
     return fail(CROM_ERR_INVALID_ARG, "crom_trainer_create: need P >= 38 (one convolution of length >= 32), "
                                       "B, S >= 1, B*S <= 2^26");
@@ -559,7 +594,7 @@ int crom_reconstruct(crom_ctx* ctx, int precision, int n_codes, const double* q,
     e = launch_recon_fp32(ctx, n_codes, q, n_pts, x, out, s);
   } else if (precision == CROM_PREC_BF16X2 || precision == CROM_PREC_BF16) {
     if (!tc_shape_ok(ctx->desc) || !ctx->w.tc_img)
-      return fail(CROM_ERR_UNSUPPORTED, "crom_reconstruct: tensor-core path needs width 128, 2<=hidden<=5, m<=2");
+      return fail(CROM_ERR_UNSUPPORTED, "crom_reconstruct: tensor-core path needs width 128, 2<=hidden<=5, m<=2, ELU");
     e = launch_recon_tc(ctx, precision == CROM_PREC_BF16X2 ? 1 : 0, n_codes, q, n_pts, x, out, s);
   } else {
     return fail(CROM_ERR_UNSUPPORTED, "crom_reconstruct: unknown precision");

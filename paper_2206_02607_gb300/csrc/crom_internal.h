@@ -53,6 +53,8 @@ struct crom_ctx {
   size_t targets_cap = 0;
   double* qbase = nullptr;     // [n_inst][r]: q_n kept for the difference channel
   size_t qbase_cap = 0;
+  float* tangent = nullptr;    // [r][n_pts]: dg/dq rows for the tangent velocity
+  size_t tangent_cap = 0;
   // Scratch of the tensor-core step: instance order (largest |M_i| first) and the
   // queue counter / timeout flag.
   int* order = nullptr;
@@ -125,6 +127,10 @@ cudaError_t launch_step_fp32(crom_ctx* ctx, const crom_step_desc* step, int n_in
                              const float* alpha, const float* vel, const int* s_off,
                              const float* samples, int n_samples, int max_samples, int* status,
                              cudaStream_t s);
+
+// v_p = (dg/dq)(x_p, q_i) . (q_i - q_prev_i) / dt from dq [r][n_pts] (decode output).
+cudaError_t launch_tangent_contract(const float* dq, const double* q, const double* q_prev, double dt,
+                                    const int* pt_off, int n_inst, int r, int n_pts, float* out, cudaStream_t s);
 
 // FP32 step with its scratch in a fixed-size device array (no allocation).
 size_t noalloc_scratch_capacity();

@@ -55,6 +55,8 @@ struct FwdParams {
   const float* x;   // [n][m]
   int n_pts;
   int n_inst;
+  int act;        // CROM_ACT_ELU or CROM_ACT_SIREN
+  float omega0;   // SIREN frequency
   // decode / recon
   float* out;
   unsigned want;
@@ -102,6 +104,21 @@ __device__ __forceinline__ float elu_diff(float a, float d) {
   return sa - sb;
 }
 
+// SIREN, s(z) = sin(w z): s' = w cos(w z), s'' = -w^2 sin(w z).
+__device__ __forceinline__ void siren3(float z, float w, float& s0, float& s1, float& s2) {
+  float sn, cs;
+  sincosf(w * z, &sn, &cs);
+  s0 = sn;
+  s1 = w * cs;
+  s2 = -w * w * sn;
+}
+
+// sin(w a) - sin(w (a - d)) = 2 cos(w (a - d/2)) sin(w d / 2), without the
+// cancellation of the direct difference.
+__device__ __forceinline__ float siren_diff(float a, float d, float w) {
+  return 2.f * cosf(w * (a - 0.5f * d)) * sinf(0.5f * w * d);
+}
+
 // Apply the activation chain in place to row `row` (pre-activation channels of
 // one hidden unit) for the samples s0, s0 + ds, ... < S.
 __device__ __forceinline__ void activate_row(float* row, const FwdParams& p, int sbeg, int ds) {
@@ -110,9 +127,14 @@ __device__ __forceinline__ void activate_row(float* row, const FwdParams& p, int
     float* c = row + s * C;
     float s0, s1, s2;
     const float za = c[0];
-    elu3(za, s0, s1, s2);
+    if (p.act == CROM_ACT_SIREN) {
+      siren3(za, p.omega0, s0, s1, s2);
+      if (p.diff) c[1] = siren_diff(za, c[1], p.omega0);
+    } else {
+      elu3(za, s0, s1, s2);
+      if (p.diff) c[1] = elu_diff(za, c[1]);
+    }
     c[0] = s0;
-    if (p.diff) c[1] = elu_diff(za, c[1]);
     const int ox = 1 + p.diff;
     float zx[kMaxM];
     float sq = 0.f;
@@ -456,6 +478,8 @@ void fill_decoder(FwdParams& p, const crom_ctx* ctx) {
   p.bh = ctx->w.bh;
   p.wout = ctx->w.wout;
   p.bout = ctx->w.bout;
+  p.act = ctx->desc.activation;
+  p.omega0 = ctx->desc.omega0;
 }
 
 // Largest tile that keeps the two activation buffers within 200 KB.
@@ -467,6 +491,28 @@ int pick_samples(int W, int C, int m, int r, int want) {
 }
 
 }  // namespace
+
+namespace {
+__global__ void tangent_contract_kernel(const float* __restrict__ dq, const double* __restrict__ q,
+                                        const double* __restrict__ q_prev, double inv_dt,
+                                        const int* __restrict__ pt_off, int n_inst, int r, int n_pts,
+                                        float* __restrict__ out) {
+  const int pt = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= n_pts) return;
+  const int i = find_instance(pt_off, n_inst, pt);
+  double v = 0.0;
+  for (int j = 0; j < r; ++j)
+    v += (double)dq[(size_t)j * n_pts + pt] * ((q[(size_t)i * r + j] - q_prev[(size_t)i * r + j]) * inv_dt);
+  out[pt] = (float)v;
+}
+}  // namespace
+
+cudaError_t launch_tangent_contract(const float* dq, const double* q, const double* q_prev, double dt,
+                                    const int* pt_off, int n_inst, int r, int n_pts, float* out, cudaStream_t s) {
+  tangent_contract_kernel<<<(n_pts + 255) / 256, 256, 0, s>>>(dq, q, q_prev, 1.0 / dt, pt_off, n_inst, r, n_pts,
+                                                              out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_decode_fp32(const crom_ctx* ctx, int n_inst, const double* q, const int* pt_off,
                                const float* x, int n_pts, unsigned want, float* out, cudaStream_t s) {

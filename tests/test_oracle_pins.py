@@ -522,3 +522,71 @@ def test_line_search_accepts_full_step_for_linear_decoders():
     assert sa == sb == O.STATUS_OK and rel(b - q0, a - q0) < 1e-12
     first = info["line_search_trials"][0]
     assert len(first) == 1 and first[0][0] == 1.0
+
+
+# ------------------------------------------------------------------ f4: SIREN decoders
+
+def test_siren_decoder_derivatives_vs_autodiff_and_closed_form():
+    """SIREN (sin(30 z)) hidden layers: every channel against reverse-mode autodiff
+    of an independently written torch FP64 forward pass; a one-hidden-layer decoder
+    against its closed form Lap g = -w0^2 sum_u w_u |a_u|^2 sin(w0 z_u)."""
+    torch = pytest.importorskip("torch")
+    spec = gen.DecoderSpec(2, 4, 32, 3)
+    params = gen.siren_decoder(spec, seed=5)
+    dec = O.MLPDecoder(params, 2, activation="siren")
+    rng = np.random.default_rng(6)
+    X = rng.uniform(-1, 1, size=(8, 2))
+    q = rng.standard_normal(4)
+    ev = dec(X, q)
+    Wt = [(torch.tensor(W), torch.tensor(b)) for W, b in params]
+
+    def f(xq):
+        h = xq
+        for li, (W, b) in enumerate(Wt):
+            z = W @ h + b
+            h = torch.sin(30.0 * z) if li + 1 < len(Wt) else z
+        return h[0]
+
+    for i in range(X.shape[0]):
+        xq = torch.tensor(np.concatenate([X[i], q]), requires_grad=True)
+        grad = torch.autograd.functional.jacobian(f, xq).numpy()
+        hess = torch.autograd.functional.hessian(f, xq).numpy()
+        np.testing.assert_allclose(ev.g[i], f(xq).item(), rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(ev.gx[i], grad[:2], rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(ev.gq[i], grad[2:], rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(ev.gxx[i], np.diag(hess)[:2], rtol=1e-10, atol=1e-10)
+    # one hidden layer: closed forms
+    spec1 = gen.DecoderSpec(2, 3, 16, 1)
+    (W1, b1), (Wo, bo) = gen.siren_decoder(spec1, seed=7)
+    dec1 = O.MLPDecoder([(W1, b1), (Wo, bo)], 2, activation="siren")
+    ev1 = dec1(X, q[:3])
+    z = X @ W1[:, :2].T + q[:3] @ W1[:, 2:].T + b1
+    w = Wo[0]
+    np.testing.assert_allclose(ev1.g, np.sin(30 * z) @ w + bo[0], rtol=1e-13, atol=1e-14)
+    lap = -900.0 * (np.sin(30 * z) * (W1[:, 0] ** 2 + W1[:, 1] ** 2)) @ w
+    np.testing.assert_allclose(ev1.lap, lap, rtol=1e-12, atol=1e-12)
+    gq = 30.0 * (np.cos(30 * z) * w) @ W1[:, 2:]
+    np.testing.assert_allclose(ev1.gq, gq, rtol=1e-12, atol=1e-12)
+
+
+def test_tangent_velocity_closed_form_and_difference_quotient():
+    """v = dg/dq . (q_n - q_{n-1}) / dt: exact for a decoder linear in q (the sine
+    decoder: v = sum_k qdot_k sin(k pi x)); for an MLP it is the limit of the
+    difference quotient (g(x, q_n) - g(x, q_n - eps qdot dt)) / (eps dt)."""
+    dec = FourierDecoder1D(4)
+    X = np.linspace(0.05, 0.95, 11)[:, None]
+    rng = np.random.default_rng(13)
+    q, qp = rng.standard_normal(4), rng.standard_normal(4)
+    v = O.tangent_velocity(dec, X, q, qp, 0.01)
+    S = np.sin(np.pi * np.outer(X[:, 0], np.arange(1, 5)))
+    assert rel(v, S @ ((q - qp) / 0.01)) < 1e-14
+    spec = gen.DecoderSpec(2, 3, 32, 3)
+    mlp = O.MLPDecoder(gen.xavier_decoder(spec, seed=2, bias_std=0.2), 2)
+    X2 = rng.uniform(0, 1, size=(40, 2))
+    q, qp = rng.standard_normal(3), rng.standard_normal(3)
+    dt, eps = 0.1, 1e-6
+    v = O.tangent_velocity(mlp, X2, q, qp, dt)
+    qdot = (q - qp) / dt
+    fd = (mlp.value(X2, q + eps * qdot) - mlp.value(X2, q - eps * qdot)) / (2 * eps)
+    keep = _kink_margin(mlp.params, X2, q[None, :], 2) > 1e-4   # ELU is C^1: stay off kinks
+    assert rel(v[keep], fd[keep]) < 1e-7

@@ -31,7 +31,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = [
-    "DecoderSpec", "bf16_round", "xavier_decoder", "pack_params", "param_count",
+    "DecoderSpec", "bf16_round", "xavier_decoder", "siren_decoder", "pack_params", "param_count",
     "interior_nodes_1d", "interior_nodes_2d", "gaussian_bumps_2d", "sine_modes_1d",
     "StepWorkload", "heat1d_small", "heat2d_single", "heat2d_batched", "recon_dense",
     "grid_points_2d", "ragged_offsets", "piecewise_nu",
@@ -84,6 +84,27 @@ def xavier_decoder(spec: DecoderSpec, seed: int, bias_std: float = 0.0,
         std = np.sqrt(2.0 / (fan_in + fan_out))
         W = rng.standard_normal((fan_out, fan_in)) * std
         b = rng.standard_normal(fan_out) * bias_std if bias_std > 0 else np.zeros(fan_out)
+        if bf16_exact:
+            W, b = bf16_round(W), bf16_round(b)
+        else:
+            W, b = W.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)
+        params.append((W, b))
+    return params
+
+
+def siren_decoder(spec: DecoderSpec, seed: int, omega0: float = 30.0, bf16_exact: bool = False):
+    """SIREN initialisation (Sitzmann et al., the paper's "default initialization
+    (omega0 = 30)"): layer 1 W ~ U(-1/fan_in, 1/fan_in); later layers
+    W ~ U(-sqrt(6/fan_in)/omega0, +sqrt(6/fan_in)/omega0); biases
+    U(-1/sqrt(fan_in), 1/sqrt(fan_in)).  Same layout as xavier_decoder."""
+    rng = np.random.default_rng(seed)
+    dims = spec.dims
+    params = []
+    for l in range(len(dims) - 1):
+        fan_in, fan_out = dims[l], dims[l + 1]
+        lim = 1.0 / fan_in if l == 0 else np.sqrt(6.0 / fan_in) / omega0
+        W = rng.uniform(-lim, lim, size=(fan_out, fan_in))
+        b = rng.uniform(-1.0 / np.sqrt(fan_in), 1.0 / np.sqrt(fan_in), size=fan_out)
         if bf16_exact:
             W, b = bf16_round(W), bf16_round(b)
         else:
