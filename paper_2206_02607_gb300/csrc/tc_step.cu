@@ -53,7 +53,8 @@ namespace {
 using namespace tc;
 
 constexpr int kGroups = 2;
-constexpr int kGT = 256;                 // threads per group
+constexpr int kTPU = 2;                  // threads per hidden unit (warps w and w+4 share a lane quadrant)
+constexpr int kGT = 128 * kTPU;          // threads per group
 constexpr int kThreads = kGroups * kGT;
 constexpr int kS0 = 16;                  // samples per tile at GN iteration 0 (4 channels)
 constexpr int kS1 = 32;                  // samples per tile at later iterations (2 channels)
@@ -143,20 +144,27 @@ __device__ __forceinline__ bool group_sync_and(int g, bool pred) {
   return r != 0;
 }
 
-// Eight consecutive columns of row k as a bf16 hi/lo pair: the hi parts go to
-// columns n_hi..n_hi+7, the lo parts to n_lo..n_lo+7 of the MN-major operand H
-// (columns >= 64 lie in the next 64-column block); one 16-byte chunk each.
-__device__ __forceinline__ void split_store8(uint8_t* H, int k, int n_hi, int n_lo, const float* v) {
-  uint32_t hi[4], lo[4];
+// kC (4 or 8) consecutive columns of row k as a bf16 hi/lo pair: the hi parts go
+// to columns n_hi.., the lo parts to n_lo.. of the MN-major operand H (columns
+// >= 64 lie in the next 64-column block); one 2 kC-byte chunk each.
+template <int kC>
+__device__ __forceinline__ void split_store(uint8_t* H, int k, int n_hi, int n_lo, const float* v) {
+  uint32_t hi[kC / 2], lo[kC / 2];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < kC / 2; ++j) {
     hi[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
     float a, b;
     unpk2(sub2(pk2(v[2 * j], v[2 * j + 1]), pk2(bf16_lo_f(hi[j]), bf16_hi_f(hi[j]))), a, b);
     lo[j] = pack_bf16(a, b);
   }
-  *reinterpret_cast<uint4*>(H + mn_offset(k, n_hi)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-  *reinterpret_cast<uint4*>(H + mn_offset(k, n_lo)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  if constexpr (kC == 8) {
+    *reinterpret_cast<uint4*>(H + mn_offset(k, n_hi)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(H + mn_offset(k, n_lo)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  } else {
+    static_assert(kC == 4, "chunks of 4 or 8 columns");
+    *reinterpret_cast<uint2*>(H + mn_offset(k, n_hi)) = make_uint2(hi[0], hi[1]);
+    *reinterpret_cast<uint2*>(H + mn_offset(k, n_lo)) = make_uint2(lo[0], lo[1]);
+  }
 }
 
 // e^x - 1 for |x| < 1/16 by its degree-5 Taylor polynomial (truncation < 1.3e-9
@@ -185,15 +193,15 @@ __device__ __forceinline__ float elu_diff(float a, float d, float e) {
   return elu_diff_slow(a, d, e);
 }
 
-// Forward activation chain of 8 samples of one hidden unit, in place, on packed
+// Forward activation chain of kC samples of one hidden unit, in place, on packed
 // pairs.  v[0] holds the value channel's pre-activation z (bias included); at
 // iteration 0 v[1..m] the gradient channels dz/dx_k and v[kCh-1] the Laplacian
 // channel; later v[1] the difference channel.  sg receives s'(z).
 //   h = s(z); dh/dx_k = s'(z) dz/dx_k; Lap h = s''(z) sum_k (dz/dx_k)^2 + s'(z) Lap z.
-template <int kM, bool kFirst, int kCh>
-__device__ __forceinline__ void act8(float (&v)[kCh][8], float (&sg)[8]) {
+template <int kM, bool kFirst, int kCh, int kC>
+__device__ __forceinline__ void act(float (&v)[kCh][kC], float (&sg)[kC]) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < kC / 2; ++j) {
     const int i0 = 2 * j, i1 = 2 * j + 1;
     const float z0 = v[0][i0], z1 = v[0][i1];
     float e0, e1;
@@ -246,7 +254,7 @@ __device__ __forceinline__ void issue_proj(uint32_t d, uint64_t a0, uint64_t p0)
 
 // Per-thread view of the group it belongs to.
 struct Lane {
-  int g, gt, gw, u, half;
+  int g, gt, gw, u, part;
   uint32_t lane_base, tb;
   uint8_t* H;
   Shared* S;
@@ -302,12 +310,12 @@ __device__ __forceinline__ double dot_exact(const float* a0, const float* a1, in
   return (double)s + (double)comp;
 }
 
-// s'(z_1) of eight samples of this thread's unit, recomputed exactly as the
+// s'(z_1) of kC samples of this thread's unit, recomputed exactly as the
 // forward pass formed it (same FP32 operations), for the last reverse step.
-template <int kM>
-__device__ __forceinline__ void sig1_8(const Lane& c, const Group* G, float cc, int s, float (&sg)[8]) {
+template <int kM, int kC>
+__device__ __forceinline__ void sig1(const Lane& c, const Group* G, float cc, int s, float (&sg)[kC]) {
 #pragma unroll
-  for (int i = 0; i < 8; i += 2) {
+  for (int i = 0; i < kC; i += 2) {
     float z0 = fmaf(c.wx0, G->xs[0][s + i], cc), z1 = fmaf(c.wx0, G->xs[0][s + i + 1], cc);
     if (kM > 1) {
       z0 = fmaf(c.wx1, G->xs[1][s + i], z0);
@@ -327,11 +335,12 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
                                          int eb, double& acc) {
   constexpr int kCh = kFirst ? 2 + kM : 2;  // iteration 0: v, dx_1..dx_m, Lap; later: v(q^(k)), diff
   constexpr int kN = kCh * kSm;             // hi columns 0..kN-1, lo columns 64..64+kN-1
-  constexpr int kHalf = kSm / 2;            // samples of this thread
-  static_assert(kN <= 64 && kHalf % 8 == 0 && kSig + 4 * kSm <= kGroupCols, "tile shape");
+  constexpr int kPer = kSm / kTPU;          // samples of this thread
+  constexpr int kC = kPer < 8 ? kPer : 8;    // samples per chunk
+  static_assert(kN <= 64 && kPer % kC == 0 && kC % 4 == 0 && kSig + 4 * kSm <= kGroupCols, "tile shape");
   Group* G = c.G;
   const Shared* S = c.S;
-  const int u = c.u, s0 = c.half * kHalf;
+  const int u = c.u, s0 = c.part * kPer;
   const uint32_t lb = c.lane_base, tb = c.tb;
   if (c.gt < kSm) {
     const int s = c.gt < ns ? c.gt : 0;
@@ -342,12 +351,12 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
   {
     const float cc = G->c1[u], dz = G->dz1[u];
 #pragma unroll 1
-    for (int h8 = 0; h8 < kHalf; h8 += 8) {
+    for (int h8 = 0; h8 < kPer; h8 += kC) {
       // layer-1 pre-activation channels: z = W_1x x + W_1q q + b_1, dz/dx_k = W_1[:, k],
       // Laplacian 0; later iterations: the difference channel's W_1q (q^(k) - q_n)
-      float v[kCh][8], sg[8];
+      float v[kCh][kC], sg[kC];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < kC; ++i) {
         float z = fmaf(c.wx0, G->xs[0][s0 + h8 + i], cc);
         if (kM > 1) z = fmaf(c.wx1, G->xs[1][s0 + h8 + i], z);
         v[0][i] = z;
@@ -359,11 +368,11 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
           v[1][i] = dz;
         }
       }
-      act8<kM, kFirst, kCh>(v, sg);
+      act<kM, kFirst, kCh, kC>(v, sg);
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) {
         const int n = ch * kSm + s0 + h8;
-        split_store8(c.H, u, n, 64 + n, v[ch]);
+        split_store<kC>(c.H, u, n, 64 + n, v[ch]);
       }
     }
   }
@@ -373,27 +382,27 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
     if (!stage<kStageFwd>(c, l, id_fwd)) return false;
     const float bias = S->bh[l][u];
 #pragma unroll 1
-    for (int h8 = 0; h8 < kHalf; h8 += 8) {
-      float v[kCh][8], w[kCh][8], sg[8];
+    for (int h8 = 0; h8 < kPer; h8 += kC) {
+      float v[kCh][kC], w[kCh][kC], sg[kC];
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) {
-        tmem_ld8(taddr(tb, lb, kAcc + ch * kSm + s0 + h8), v[ch]);
-        tmem_ld8(taddr(tb, lb, kAcc + 64 + ch * kSm + s0 + h8), w[ch]);
+        tmem_ldc(taddr(tb, lb, kAcc + ch * kSm + s0 + h8), v[ch]);
+        tmem_ldc(taddr(tb, lb, kAcc + 64 + ch * kSm + s0 + h8), w[ch]);
       }
       tmem_ld_wait();
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch)
 #pragma unroll
-        for (int i = 0; i < 8; i += 2)
+        for (int i = 0; i < kC; i += 2)
           unpk2(add2(pk2(v[ch][i], v[ch][i + 1]), pk2(w[ch][i], w[ch][i + 1])), v[ch][i], v[ch][i + 1]);
 #pragma unroll
-      for (int i = 0; i < 8; i += 2) unpk2(add2(pk2(v[0][i], v[0][i + 1]), pk2(bias, bias)), v[0][i], v[0][i + 1]);
-      act8<kM, kFirst, kCh>(v, sg);
-      tmem_st8(taddr(tb, lb, kSig + l * kSm + s0 + h8), sg);
+      for (int i = 0; i < kC; i += 2) unpk2(add2(pk2(v[0][i], v[0][i + 1]), pk2(bias, bias)), v[0][i], v[0][i + 1]);
+      act<kM, kFirst, kCh, kC>(v, sg);
+      tmem_stc(taddr(tb, lb, kSig + l * kSm + s0 + h8), sg);
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) {
         const int n = ch * kSm + s0 + h8;
-        split_store8(c.H, u, n, 64 + n, v[ch]);
+        split_store<kC>(c.H, u, n, 64 + n, v[ch]);
       }
     }
     // the s'(z) stores complete in the background: nothing reads those columns
@@ -401,7 +410,7 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
   }
   // ---------------- output layer: PRJ[n][0] = w_out . h_L[:, n], hi rows + lo rows
   if (!stage<kStageProj>(c, 0, 0)) return false;
-  if (c.half == 0) {
+  if (c.part == 0) {
     float v[8];
     tmem_ld8(taddr(tb, lb, kAcc), v);
     tmem_ld_wait();
@@ -445,13 +454,13 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
   }
   // ---------------- reverse pass for dg/dq at q^(k); delta hi in columns 0..kSm-1, lo in kSm..2kSm-1
 #pragma unroll 1
-  for (int h8 = 0; h8 < kHalf; h8 += 8) {
-    float sg[8];
-    tmem_ld8(taddr(tb, lb, kSig + (p.L - 2) * kSm + s0 + h8), sg);
+  for (int h8 = 0; h8 < kPer; h8 += kC) {
+    float sg[kC];
+    tmem_ldc(taddr(tb, lb, kSig + (p.L - 2) * kSm + s0 + h8), sg);
     tmem_ld_wait();
 #pragma unroll
-    for (int i = 0; i < 8; ++i) sg[i] *= c.wo;
-    split_store8(c.H, u, s0 + h8, kSm + s0 + h8, sg);  // delta_L
+    for (int i = 0; i < kC; ++i) sg[i] *= c.wo;
+    split_store<kC>(c.H, u, s0 + h8, kSm + s0 + h8, sg);  // delta_L
   }
   constexpr uint32_t id_bwd = idesc_f16(128, 2 * kSm, true, true, true);
   for (int l = p.L - 2; l >= 0; --l) {
@@ -459,17 +468,17 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
     if (!stage<kStageBwd>(c, l, id_bwd)) return false;
     const float cc = G->c1[u];
 #pragma unroll 1
-    for (int h8 = 0; h8 < kHalf; h8 += 8) {
-      float v[8], w[8], sg[8];
-      tmem_ld8(taddr(tb, lb, kAcc + s0 + h8), v);
-      tmem_ld8(taddr(tb, lb, kAcc + kSm + s0 + h8), w);
-      if (l > 0) tmem_ld8(taddr(tb, lb, kSig + (l - 1) * kSm + s0 + h8), sg);
-      else sig1_8<kM>(c, G, cc, s0 + h8, sg);
+    for (int h8 = 0; h8 < kPer; h8 += kC) {
+      float v[kC], w[kC], sg[kC];
+      tmem_ldc(taddr(tb, lb, kAcc + s0 + h8), v);
+      tmem_ldc(taddr(tb, lb, kAcc + kSm + s0 + h8), w);
+      if (l > 0) tmem_ldc(taddr(tb, lb, kSig + (l - 1) * kSm + s0 + h8), sg);
+      else sig1<kM, kC>(c, G, cc, s0 + h8, sg);
       tmem_ld_wait();
 #pragma unroll
-      for (int i = 0; i < 8; i += 2)
+      for (int i = 0; i < kC; i += 2)
         unpk2(mul2(add2(pk2(v[i], v[i + 1]), pk2(w[i], w[i + 1])), pk2(sg[i], sg[i + 1])), v[i], v[i + 1]);
-      split_store8(c.H, u, s0 + h8, kSm + s0 + h8, v);
+      split_store<kC>(c.H, u, s0 + h8, kSm + s0 + h8, v);
     }
   }
   // J[s][j] = sum_u W_1q[u][j] delta_1[u][s]: rows s (hi) and kSm + s (lo)
@@ -499,7 +508,7 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
 // channel) and dz1 = W_1q (q - q_n) (difference channel), FP64 sums rounded once.
 __device__ __forceinline__ void set_layer1(const Lane& c, const Shared* S, Group* G, const double* q, int r,
                                            const float* b1) {
-  if (c.half == 0) {
+  if (c.part == 0) {
     double cc = (double)b1[c.u], dz = 0.0;
     for (int j = 0; j < r; ++j) {
       cc += (double)S->w1q[j][c.u] * q[j];
@@ -521,7 +530,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
   c.gt = tid % kGT;
   c.gw = c.gt >> 5;
   const int lq = c.gw & 3;        // TMEM lane quadrant of this warp
-  c.half = c.gw >> 2;              // which half of a tile's samples
+  c.part = c.gw >> 2;              // which part of a tile's samples
   c.u = lq * 32 + (c.gt & 31);     // hidden unit = TMEM lane
   c.lane_base = (uint32_t)lq * 32;
 
