@@ -418,15 +418,20 @@ def main():
                          .astype(np.int32), device="cuda")
     coords_t = torch.tensor(gen.grid_points_2d(nt_side), device="cuda")
     loss_t = torch.zeros(1, dtype=torch.float64, device="cuda")
-    crom.crom_train_step(tr, snaps_t, idx_t, coords_t, 1e-4, loss_t)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(3):
+    def time_train(prec, reps):
+        tr.set_precision(prec)
         crom.crom_train_step(tr, snaps_t, idx_t, coords_t, 1e-4, loss_t)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    train_ms = e0.elapsed_time(e1) / 3
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            crom.crom_train_step(tr, snaps_t, idx_t, coords_t, 1e-4, loss_t)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    train_ms_fp32 = time_train(crom.CROM_PREC_FP32, 3)
+    train_ms = time_train(crom.CROM_PREC_TF32, 10)
     pts = Bt * St
     train_flops = pts * 6 * (2 * (2 + rt) * wt + 2 * (Lt - 1) * wt * wt + 2 * wt) / 2
     tr.close()
@@ -464,8 +469,10 @@ def main():
                               "workload": "512 periodic 256^2 fields, 16 B per node-step (u, ax, ay read, u written)"},
             "training": {"point_samples_per_s": pts / (train_ms * 1e-3), "ms_per_step": train_ms,
                          "tflops_algorithmic": train_flops / (train_ms * 1e-3) / 1e12,
+                         "precision": "TF32 tensor-core GEMMs (cuBLAS), FP32 elsewhere",
+                         "fp32_ms_per_step": train_ms_fp32,
                          "workload": "64 snapshots x 4096 points, decoder R^{2+16}->R width 256 x 5 ELU, "
-                                     "strided-conv encoder, FP32 CUDA cores, Adam"},
+                                     "strided-conv encoder, Adam"},
             "roofline": {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                          "frac": achieved_tf / peak_tf, "traffic": None,
                          "note": f"step kernel, algorithmic FLOPs {step_flops_per_sample()} per sample x "

@@ -61,8 +61,11 @@ typedef enum {
  *           FP32 activation/derivative chains, FP64 normal equations.
  *           width == 128, 2 <= hidden <= 5, m <= 2, r <= 15.
  *  BF16   : as BF16X2 with the high part only (one MMA per layer).  Dense
- *           reconstruction only. */
-typedef enum { CROM_PREC_FP32 = 0, CROM_PREC_BF16X2 = 1, CROM_PREC_BF16 = 2 } crom_precision;
+ *           reconstruction only.
+ *  TF32   : training step only: the dense products on the tensor cores with
+ *           TF32 operands (10-bit mantissa) and FP32 accumulation, through cuBLAS
+ *           (plain GEMMs); every other step of the training pass in FP32. */
+typedef enum { CROM_PREC_FP32 = 0, CROM_PREC_BF16X2 = 1, CROM_PREC_BF16 = 2, CROM_PREC_TF32 = 3 } crom_precision;
 
 typedef enum { CROM_PDE_HEAT = 0, CROM_PDE_ADVDIFF = 1 } crom_pde;
 
@@ -282,6 +285,11 @@ int crom_trainer_get_grads(crom_trainer* tr, float* grads, size_t n, int on_devi
  * double, may be NULL) receives the loss before the update. */
 int crom_train_step(crom_trainer* tr, const float* snaps, const int* pt_idx, const float* coords, float lr,
                     double* loss_out, crom_stream stream);
+/* Arithmetic of the trainer's dense products: CROM_PREC_FP32 (default; the
+ * library's FP32 CUDA-core GEMM, split-K weight gradients reduced in a fixed
+ * order) or CROM_PREC_TF32 (cuBLAS TF32 tensor-core GEMMs; the bias / ELU /
+ * s'(z) epilogues, loss, convolutions and Adam stay in the library's kernels). */
+int crom_trainer_set_precision(crom_trainer* tr, int precision);
 /* Encoder only: q [n][r] FP32 for n <= B snapshots [n][P] (initial latent codes). */
 int crom_encode(crom_trainer* tr, int n, const float* snaps, float* q, crom_stream stream);
 

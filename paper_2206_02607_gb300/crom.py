@@ -24,6 +24,7 @@ CROM_ERR_UNSUPPORTED = 6
 CROM_PREC_FP32 = 0
 CROM_PREC_BF16X2 = 1
 CROM_PREC_BF16 = 2
+CROM_PREC_TF32 = 3
 
 CROM_PDE_HEAT = 0
 CROM_PDE_ADVDIFF = 1
@@ -47,7 +48,7 @@ EXPORTED = ("crom_version", "crom_last_error", "crom_create", "crom_destroy", "c
             "crom_decode", "crom_step", "crom_rollout", "crom_step_noalloc", "crom_fom_step", "crom_trainer_create",
             "crom_trainer_destroy", "crom_trainer_param_count", "crom_trainer_set_params",
             "crom_trainer_get_params", "crom_trainer_get_grads", "crom_train_step", "crom_encode",
-            "crom_reconstruct", "crom_robust_samples", "crom_tangent_velocity")
+            "crom_reconstruct", "crom_robust_samples", "crom_tangent_velocity", "crom_trainer_set_precision")
 
 
 class CromError(RuntimeError):
@@ -85,6 +86,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.crom_trainer_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(crom_decoder_desc), i, i, i, i]
     lib.crom_trainer_destroy.argtypes = [vp]
     lib.crom_trainer_param_count.argtypes = [vp, ctypes.POINTER(sz)]
+    lib.crom_trainer_set_precision.argtypes = [vp, i]
     for name in ("crom_trainer_set_params", "crom_trainer_get_params", "crom_trainer_get_grads"):
         getattr(lib, name).argtypes = [vp, vp, sz, i, vp]
     lib.crom_train_step.argtypes = [vp, vp, vp, vp, ctypes.c_float, vp, vp]
@@ -252,6 +254,10 @@ class CromTrainer:
             _check(fn(self.handle, _ptr(arr), arr.numel(), 1, _stream(stream)))
         else:
             _check(fn(self.handle, arr.ctypes.data_as(ctypes.c_void_p), arr.size, 0, _stream(stream)))
+
+    def set_precision(self, precision: int):
+        """CROM_PREC_FP32 (default) or CROM_PREC_TF32 for the dense products."""
+        _check(_LIB.crom_trainer_set_precision(self.handle, precision))
 
     def set_params(self, params, stream=None):
         import numpy as np

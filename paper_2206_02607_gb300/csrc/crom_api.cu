@@ -517,6 +517,16 @@ int crom_trainer_destroy(crom_trainer* tr) {
   return CROM_OK;
 }
 
+int crom_trainer_set_precision(crom_trainer* tr, int precision) {
+  if (!tr) return fail(CROM_ERR_INVALID_ARG, "crom_trainer_set_precision: null trainer");
+  if (precision != CROM_PREC_FP32 && precision != CROM_PREC_TF32)
+    return fail(CROM_ERR_UNSUPPORTED, "crom_trainer_set_precision: FP32 or TF32");
+  DeviceGuard g(tr->device);
+  if (trainer_set_precision(tr, precision) != CROM_OK)
+    return fail(CROM_ERR_CUDA, "crom_trainer_set_precision: cuBLAS handle creation failed");
+  return CROM_OK;
+}
+
 int crom_trainer_param_count(const crom_trainer* tr, size_t* n) {
   if (!tr || !n) return fail(CROM_ERR_INVALID_ARG, "crom_trainer_param_count: null argument");
   *n = trainer_param_count(tr);

@@ -94,6 +94,8 @@ struct crom_trainer {
   double* partial = nullptr;
   double* loss_dev = nullptr;
   std::vector<void*> owned;
+  int precision = CROM_PREC_FP32;  // of the dense products (FP32 or TF32)
+  void* blas = nullptr;            // cuBLAS handle for TF32, created on demand
 };
 
 namespace crom {
@@ -104,6 +106,7 @@ void set_error(const std::string& msg);
 size_t trainer_param_count(const crom_trainer* t);
 cudaError_t trainer_alloc(crom_trainer* t);
 void trainer_free(crom_trainer* t);
+int trainer_set_precision(crom_trainer* t, int precision);
 cudaError_t trainer_encode(crom_trainer* t, int nb, const float* snaps, float* q_out, cudaStream_t s);
 cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx, const float* coords, float lr,
                          double* loss_out, cudaStream_t s);

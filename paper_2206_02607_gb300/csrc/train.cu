@@ -16,7 +16,10 @@
 // The dense contractions go through one tiled FP32 GEMM with strided operands
 // and fused epilogues (bias + ELU, multiply by s'(z)); weight gradients reduce
 // over the B*S points with a fixed split along K and a second pass that adds
-// the splits in order, so a step is deterministic.
+// the splits in order, so a step is deterministic.  With CROM_PREC_TF32 the same
+// contractions are plain cuBLAS GEMMs on the TF32 tensor cores, followed by the
+// epilogue as an elementwise kernel.
+#include <cublas_v2.h>
 #include <math.h>
 
 #include <vector>
@@ -97,6 +100,24 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
       }
     }
   }
+}
+
+// Elementwise epilogues after a library GEMM (C row-major, M x N, ldc).
+__global__ void epi_bias_elu_kernel(float* C, long M, int N, long ldc, const float* bias, float* H) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= M * N) return;
+  const long i = t / N;
+  const int j = (int)(t % N);
+  const long o = i * ldc + j;
+  const float v = C[o] + bias[j];
+  C[o] = v;
+  H[o] = elu_f(v);
+}
+__global__ void epi_times_elud_kernel(float* C, long M, int N, long ldc, const float* Zp) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= M * N) return;
+  const long o = (t / N) * ldc + (t % N);
+  C[o] *= elu_d(Zp[o]);
 }
 
 // out[e] = sum_s parts[s * stride + e] (in split order), then optionally out[e] = val.
@@ -322,12 +343,36 @@ cudaError_t trainer_alloc(crom_trainer* t) {
 void trainer_free(crom_trainer* t) {
   for (void* p : t->owned) cudaFree(p);
   t->owned.clear();
+  if (t->blas) cublasDestroy(static_cast<cublasHandle_t>(t->blas));
+  t->blas = nullptr;
 }
 
 // C = A * B (strided operands) with an epilogue; K split over kSplitK partials when requested.
-static cudaError_t gemm(cudaStream_t s, int M, int N, int K, const float* A, long sai, long sak, const float* B,
-                        long sbk, long sbj, float* C, long ldc, int epi, const float* bias, float* H,
-                        const float* Zp, float* split = nullptr) {
+// A[i][k] = A[i * sai + k * sak], B[k][j] = B[k * sbk + j * sbj]; one of each pair of
+// strides is 1 (row-major or transposed storage).
+static cudaError_t gemm(crom_trainer* t, cudaStream_t s, int M, int N, int K, const float* A, long sai, long sak,
+                        const float* B, long sbk, long sbj, float* C, long ldc, int epi, const float* bias,
+                        float* H, const float* Zp, float* split = nullptr) {
+  if (t->precision == CROM_PREC_TF32) {
+    // Row-major C = A B is column-major C^T = B^T A^T: cuBLAS computes the N x M
+    // column-major product op(B') op(A') with B' = B and A' = A viewed column-major.
+    cublasHandle_t h = static_cast<cublasHandle_t>(t->blas);
+    if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    const cublasOperation_t opB = sbj == 1 ? CUBLAS_OP_N : CUBLAS_OP_T;
+    const int ldb = (int)(sbj == 1 ? sbk : sbj);
+    const cublasOperation_t opA = (sak == 1 || M == 1) ? CUBLAS_OP_N : CUBLAS_OP_T;
+    const int lda = (int)((sak == 1 || M == 1) ? (M == 1 ? K : sai) : sak);
+    const float one = 1.f, zero = 0.f;
+    cublasStatus_t st = cublasGemmEx(h, opB, opA, N, M, K, &one, B, CUDA_R_32F, ldb, A, CUDA_R_32F, lda, &zero, C,
+                                     CUDA_R_32F, (int)ldc, CUBLAS_COMPUTE_32F_FAST_TF32, CUBLAS_GEMM_DEFAULT);
+    if (st != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    const long n = (long)M * N;
+    if (epi == kEpiBiasElu)
+      epi_bias_elu_kernel<<<blocks(n, 256), 256, 0, s>>>(C, M, N, ldc, bias, H);
+    else if (epi == kEpiTimesEluD)
+      epi_times_elud_kernel<<<blocks(n, 256), 256, 0, s>>>(C, M, N, ldc, Zp);
+    return cudaGetLastError();
+  }
   dim3 grid(blocks(N, kTile), blocks(M, kTile), split ? kSplitK : 1);
   if (split) {
     gemm_kernel<<<grid, 256, 0, s>>>(M, N, K, A, sai, sak, B, sbk, sbj, split, ldc, (long)M * ldc, kEpiStore,
@@ -337,6 +382,16 @@ static cudaError_t gemm(cudaStream_t s, int M, int N, int K, const float* A, lon
     gemm_kernel<<<grid, 256, 0, s>>>(M, N, K, A, sai, sak, B, sbk, sbj, C, ldc, 0, epi, bias, H, Zp);
   }
   return cudaGetLastError();
+}
+
+int trainer_set_precision(crom_trainer* t, int precision) {
+  if (precision == CROM_PREC_TF32 && !t->blas) {
+    cublasHandle_t h = nullptr;
+    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return CROM_ERR_CUDA;
+    t->blas = h;
+  }
+  t->precision = precision;
+  return CROM_OK;
 }
 
 cudaError_t trainer_encode(crom_trainer* t, int nb, const float* snaps, float* q_out, cudaStream_t s) {
@@ -350,11 +405,11 @@ cudaError_t trainer_encode(crom_trainer* t, int nb, const float* snaps, float* q
     x = t->conv_h[c - 1];
   }
   const int Ll = t->lens.back();
-  cudaError_t e = gemm(s, nb, 32, Ll, x, Ll, 1, t->params + t->lay.d1w, 1, Ll, t->d1z, 32, kEpiBiasElu,
+  cudaError_t e = gemm(t, s, nb, 32, Ll, x, Ll, 1, t->params + t->lay.d1w, 1, Ll, t->d1z, 32, kEpiBiasElu,
                        t->params + t->lay.d1b, t->d1h, nullptr);
   if (e != cudaSuccess) return e;
   // q = W2 h1 + b2: reuse the bias epilogue by writing Z = q and discarding ELU into edh scratch
-  return gemm(s, nb, r, 32, t->d1h, 32, 1, t->params + t->lay.d2w, 1, 32, q_out, r, kEpiBiasElu,
+  return gemm(t, s, nb, r, 32, t->d1h, 32, 1, t->params + t->lay.d2w, 1, 32, q_out, r, kEpiBiasElu,
               t->params + t->lay.d2b, t->ed1, nullptr);
 }
 
@@ -374,7 +429,7 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
   const float* hin = t->in0;
   int kin = m + r;
   for (int l = 0; l < L; ++l) {
-    e = gemm(s, (int)N, w, kin, hin, kin, 1, p + lay.dec_w[l], 1, kin, t->Z[l], w, kEpiBiasElu, p + lay.dec_b[l],
+    e = gemm(t, s, (int)N, w, kin, hin, kin, 1, p + lay.dec_w[l], 1, kin, t->Z[l], w, kEpiBiasElu, p + lay.dec_b[l],
              t->H[l], nullptr);
     if (e != cudaSuccess) return e;
     hin = t->H[l];
@@ -385,7 +440,7 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
   loss_final_kernel<<<1, 32, 0, s>>>(t->partial, (int)blocks(N, 8), N, loss_out ? loss_out : t->loss_dev);
   // ---- decoder reverse pass
   // output layer: gW_out[u] = sum_n dg[n] H_L[n][u], gb_out = sum dg
-  e = gemm(s, 1, w, (int)N, t->dg, 0, 1, t->H[L - 1], w, 1, gr + lay.dec_w[L], w, kEpiStore, nullptr, nullptr,
+  e = gemm(t, s, 1, w, (int)N, t->dg, 0, 1, t->H[L - 1], w, 1, gr + lay.dec_w[L], w, kEpiStore, nullptr, nullptr,
            nullptr, t->split);
   if (e != cudaSuccess) return e;
   colsum_kernel<<<1, 256, 0, s>>>(t->dg, N, 1, gr + lay.dec_b[L]);
@@ -396,17 +451,17 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
     const float* hprev = (l == 0) ? t->in0 : t->H[l - 1];
     const int kprev = (l == 0) ? m + r : w;
     // gW_l [w][kprev] = delta^T hprev (K = N, split), gb_l = column sums of delta
-    e = gemm(s, w, kprev, (int)N, dcur, 1, w, hprev, kprev, 1, gr + lay.dec_w[l], kprev, kEpiStore, nullptr,
+    e = gemm(t, s, w, kprev, (int)N, dcur, 1, w, hprev, kprev, 1, gr + lay.dec_w[l], kprev, kEpiStore, nullptr,
              nullptr, nullptr, t->split);
     if (e != cudaSuccess) return e;
     colsum_kernel<<<w, 256, 0, s>>>(dcur, N, w, gr + lay.dec_b[l]);
     if (l > 0) {
       // delta_{l-1} = (delta_l W_l) * s'(Z_{l-1})
-      e = gemm(s, (int)N, w, w, dcur, w, 1, p + lay.dec_w[l], w, 1, dnext, w, kEpiTimesEluD, nullptr, nullptr,
+      e = gemm(t, s, (int)N, w, w, dcur, w, 1, p + lay.dec_w[l], w, 1, dnext, w, kEpiTimesEluD, nullptr, nullptr,
                t->Z[l - 1]);
     } else {
       // input gradient din = delta_1 W_1  [N][m + r]
-      e = gemm(s, (int)N, m + r, w, dcur, w, 1, p + lay.dec_w[0], m + r, 1, t->din, m + r, kEpiStore, nullptr,
+      e = gemm(t, s, (int)N, m + r, w, dcur, w, 1, p + lay.dec_w[0], m + r, 1, t->din, m + r, kEpiStore, nullptr,
                nullptr, nullptr);
     }
     if (e != cudaSuccess) return e;
@@ -418,20 +473,20 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
   // ---- encoder reverse pass
   // dense 2: gW2 = dq^T h1, gb2 = sum dq, dz1 = (dq W2) * s'(z1)
   const int Ll = t->lens.back();
-  if ((e = gemm(s, r, 32, B, t->dq, 1, r, t->d1h, 32, 1, gr + lay.d2w, 32, kEpiStore, nullptr, nullptr, nullptr)) !=
+  if ((e = gemm(t, s, r, 32, B, t->dq, 1, r, t->d1h, 32, 1, gr + lay.d2w, 32, kEpiStore, nullptr, nullptr, nullptr)) !=
       cudaSuccess)
     return e;
   colsum_kernel<<<r, 256, 0, s>>>(t->dq, B, r, gr + lay.d2b);
-  if ((e = gemm(s, B, 32, r, t->dq, r, 1, p + lay.d2w, 32, 1, t->ed1, 32, kEpiTimesEluD, nullptr, nullptr,
+  if ((e = gemm(t, s, B, 32, r, t->dq, r, 1, p + lay.d2w, 32, 1, t->ed1, 32, kEpiTimesEluD, nullptr, nullptr,
                 t->d1z)) != cudaSuccess)
     return e;
   // dense 1: gW1 = dz1^T h_conv, gb1 = sum dz1, dh_conv = dz1 W1
   const float* hconv = t->conv_h.back();
-  if ((e = gemm(s, 32, Ll, B, t->ed1, 1, 32, hconv, Ll, 1, gr + lay.d1w, Ll, kEpiStore, nullptr, nullptr,
+  if ((e = gemm(t, s, 32, Ll, B, t->ed1, 1, 32, hconv, Ll, 1, gr + lay.d1w, Ll, kEpiStore, nullptr, nullptr,
                 nullptr)) != cudaSuccess)
     return e;
   colsum_kernel<<<32, 256, 0, s>>>(t->ed1, B, 32, gr + lay.d1b);
-  if ((e = gemm(s, B, Ll, 32, t->ed1, 32, 1, p + lay.d1w, Ll, 1, t->edh, Ll, kEpiStore, nullptr, nullptr,
+  if ((e = gemm(t, s, B, Ll, 32, t->ed1, 32, 1, p + lay.d1w, Ll, 1, t->edh, Ll, kEpiStore, nullptr, nullptr,
                 nullptr)) != cudaSuccess)
     return e;
   // convolutions, last to first

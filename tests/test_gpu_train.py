@@ -115,3 +115,36 @@ def test_training_reduces_the_loss(c):
         losses.append(l.item())
     assert np.mean(losses[-5:]) < 0.7 * np.mean(losses[:5]), losses
     tr.close()
+
+
+def test_train_step_tf32_tensor_cores(c):
+    """The same step with the dense products on the TF32 tensor cores (cuBLAS):
+    TF32 rounds GEMM operands to 10-bit mantissas (2^-11 relative), so loss and
+    gradients are held to relative L2 <= 1e-2 per group; the first Adam step
+    (-lr sign(g) where |g| is not small) matches where |g| > 1e-2 max |g|."""
+    import torch
+    cfg = dict(seed=1, n=64, r=8, width=64, hidden=4, B=5, S=300)
+    enc, dec, snaps, pt_idx, coords = make_problem(**cfg)
+    n, B, S = cfg["n"], cfg["B"], cfg["S"]
+    tr = c.CromTrainer(2, cfg["r"], cfg["width"], cfg["hidden"], n * n, B, S)
+    tr.set_precision(c.CROM_PREC_TF32)
+    p0 = T.flatten(enc, dec)
+    tr.set_params(p0.astype(np.float32))
+    loss_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lr = 1e-3
+    c.crom_train_step(tr, dev(snaps, torch.float32), dev(pt_idx, torch.int32), dev(coords, torch.float32), lr,
+                      loss_dev)
+    torch.cuda.synchronize()
+    loss, eg, dg = T.loss_and_grads(enc, dec, snaps.astype(np.float64), pt_idx, coords.astype(np.float64), 2)
+    assert abs(loss_dev.item() - loss) < 1e-2 * loss
+    g_ref = T.flatten(eg, dg)
+    g_gpu = tr.get_grads().astype(np.float64)
+    for sl in groups(enc, dec):
+        assert rel_l2(g_gpu[sl], g_ref[sl]) < 1e-2, sl
+    p1_ref, _, _ = T.adam_step(p0, g_ref, np.zeros_like(p0), np.zeros_like(p0), 1, lr)
+    p1 = tr.get_params().astype(np.float64)
+    big = np.abs(g_ref) > 1e-2 * np.abs(g_ref).max()
+    np.testing.assert_allclose(p1[big] - p0[big], p1_ref[big] - p0[big], rtol=1e-2, atol=1e-7)
+    with pytest.raises(c.CromError):
+        tr.set_precision(c.CROM_PREC_BF16X2)
+    tr.close()
