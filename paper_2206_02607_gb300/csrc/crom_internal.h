@@ -93,6 +93,7 @@ struct crom_trainer {
   float *edh = nullptr, *edx = nullptr, *ed1 = nullptr;
   double* partial = nullptr;
   double* loss_dev = nullptr;
+  double* red = nullptr;  // partial sums of the deterministic column / convolution reductions
   std::vector<void*> owned;
   int precision = CROM_PREC_FP32;  // of the dense products (FP32 or TF32)
   void* blas = nullptr;            // cuBLAS handle for TF32, created on demand

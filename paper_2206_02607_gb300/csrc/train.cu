@@ -130,21 +130,34 @@ __global__ void sum_splits_kernel(const float* parts, int splits, long stride, l
 }
 
 // Column sums of X [rows][cols] in fixed order: out[c] = sum_r X[r][c] (one block per column).
-__global__ void colsum_kernel(const float* X, long rows, int cols, float* out) {
-  const int c = blockIdx.x;
+// Column sums of X [rows][cols] in two fixed-order passes (deterministic):
+// colsum_part_kernel: block (32 columns x 8 row lanes) per (column group, row chunk),
+// coalesced across columns; colsum_final_kernel adds the chunk partials in order.
+constexpr int kColChunks = 128;
+__global__ void colsum_part_kernel(const float* X, long rows, int cols, double* part) {
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  const long per = (rows + gridDim.y - 1) / gridDim.y;
+  const long r0 = (long)blockIdx.y * per, r1 = min(rows, r0 + per);
   double s = 0.0;
-  for (long r = threadIdx.x; r < rows; r += blockDim.x) s += (double)X[r * cols + c];
-  __shared__ double red[256];
-  red[threadIdx.x] = s;
+  if (c < cols)
+    for (long r = r0 + threadIdx.y; r < r1; r += 8) s += (double)X[r * cols + c];
+  __shared__ double red[8][33];
+  red[threadIdx.y][threadIdx.x] = s;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+  if (threadIdx.y == 0 && c < cols) {
+    double t = 0.0;
+    for (int y = 0; y < 8; ++y) t += red[y][threadIdx.x];
+    part[(long)blockIdx.y * cols + c] = t;
   }
-  if (threadIdx.x == 0) out[c] = (float)red[0];
+}
+__global__ void colsum_final_kernel(const double* part, int chunks, int cols, float* out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  double t = 0.0;
+  for (int k = 0; k < chunks; ++k) t += part[(long)k * cols + c];
+  out[c] = (float)t;
 }
 
-// Strided convolution y[b][i] = bias + sum_k w[k] x[b][4i + k]; z stored, ELU(z) stored.
 __global__ void conv_fwd_kernel(const float* x, int Lin, int Lout, int B, const float* w, float* z, float* h) {
   const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (e >= (long)B * Lout) return;
@@ -173,10 +186,15 @@ __global__ void conv_dx_kernel(const float* dz, int Lin, int Lout, int B, const 
   dx[e] = s;
 }
 // Parameter gradients of one convolution: gw[k] = sum_{b,i} dz[b][i] x[b][4i+k], gb = sum dz.
-__global__ void conv_grad_kernel(const float* dz, const float* x, int Lin, int Lout, int B, float* gw) {
+// Gradient of one convolution's 6 weights and bias: sums over B * Lout outputs,
+// split into gridDim.y fixed chunks (partials part[chunk][7]) and added in order.
+__global__ void conv_grad_part_kernel(const float* dz, const float* x, int Lin, int Lout, int B, double* part) {
   const int k = blockIdx.x;  // 0..6 (6 = bias)
+  const long n = (long)B * Lout;
+  const long per = (n + gridDim.y - 1) / gridDim.y;
+  const long e0 = (long)blockIdx.y * per, e1 = min(n, e0 + per);
   double s = 0.0;
-  for (long e = threadIdx.x; e < (long)B * Lout; e += blockDim.x) {
+  for (long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int b = (int)(e / Lout), i = (int)(e % Lout);
     s += (double)dz[e] * (k < 6 ? (double)x[(long)b * Lin + 4 * i + k] : 1.0);
   }
@@ -187,10 +205,16 @@ __global__ void conv_grad_kernel(const float* dz, const float* x, int Lin, int L
     if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) gw[k] = (float)red[0];
+  if (threadIdx.x == 0) part[(long)blockIdx.y * 7 + k] = red[0];
+}
+__global__ void conv_grad_final_kernel(const double* part, int chunks, float* gw) {
+  const int k = threadIdx.x;
+  if (k >= 7) return;
+  double t = 0.0;
+  for (int c = 0; c < chunks; ++c) t += part[(long)c * 7 + k];
+  gw[k] = (float)t;
 }
 
-// Decoder input rows [x_j ; q_b] for the B*S sampled points, and the targets.
 __global__ void gather_kernel(const float* snaps, const int* pt_idx, const float* coords, const float* q, int B,
                               int S, int P, int m, int r, float* in, float* target) {
   const long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -229,15 +253,19 @@ __global__ void output_loss_kernel(const float* H, int w, long N, const float* w
     partial[blockIdx.x] = s;
   }
 }
+// loss = sum(partial) / N: 1024 threads, strided partial sums, fixed tree.
 __global__ void loss_final_kernel(const double* partial, int n, long N, double* loss) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += partial[i];
-    *loss = s / (double)N;
+  __shared__ double red[1024];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) *loss = red[0] / (double)N;
 }
-
-// delta_L[n][u] = dg[n] w_out[u] s'(z_L[n][u]); output-layer gradients.
 __global__ void out_delta_kernel(const float* dg, const float* wout, const float* Z, int w, long N, float* delta) {
   const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (e >= N * w) return;
@@ -247,15 +275,24 @@ __global__ void out_delta_kernel(const float* dg, const float* wout, const float
 }
 
 // dq[b][j] = sum over the S points of snapshot b of din[n][m + j]  (fixed order).
+// dq[b][j] = sum_s din[b S + s][m + j]: one block per snapshot, 256 row lanes,
+// fixed-order tree per latent component.
 __global__ void dq_kernel(const float* din, int B, int S, int m, int r, float* dq) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= B * r) return;
-  const int b = e / r, j = e % r;
-  float s = 0.f;
-  for (int i = 0; i < S; ++i) s += din[((long)b * S + i) * (m + r) + m + j];
-  dq[e] = s;
+  const int b = blockIdx.x;
+  __shared__ double red[256];
+  for (int j = 0; j < r; ++j) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < S; i += blockDim.x) s += (double)din[((long)b * S + i) * (m + r) + m + j];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) dq[(long)b * r + j] = (float)red[0];
+    __syncthreads();
+  }
 }
-
 __global__ void adam_kernel(float* p, const float* g, float* m, float* v, long n, float lr, float c1, float c2) {
   const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (e >= n) return;
@@ -276,8 +313,8 @@ size_t trainer_param_count(const crom_trainer* t) { return (size_t)t->lay.total;
 cudaError_t trainer_alloc(crom_trainer* t) {
   auto A = [&](size_t bytes) -> void* {
     void* p = nullptr;
-    if (cudaMalloc(&p, bytes > 0 ? bytes : 16) != cudaSuccess) return nullptr;
-    t->owned.push_back(p);
+    if (cudaMalloc(&p, bytes > 0 ? bytes : 16) != cudaSuccess) p = nullptr;
+    t->owned.push_back(p);  // a failed allocation leaves a nullptr here for the check below
     return p;
   };
   const int m = t->dec.m, r = t->dec.r, w = t->dec.width, L = t->dec.hidden;
@@ -333,6 +370,7 @@ cudaError_t trainer_alloc(crom_trainer* t) {
   t->ed1 = (float*)A((size_t)t->B * 32 * 4);
   t->partial = (double*)A((size_t)blocks(N, 8) * 8);
   t->loss_dev = (double*)A(8);
+  t->red = (double*)A((size_t)kColChunks * std::max(std::max(w, 32), std::max(r, 7)) * 8);
   for (void* p : t->owned)
     if (!p) return cudaErrorMemoryAllocation;
   cudaError_t e = cudaMemset(t->am, 0, o * 4);
@@ -382,6 +420,13 @@ static cudaError_t gemm(crom_trainer* t, cudaStream_t s, int M, int N, int K, co
     gemm_kernel<<<grid, 256, 0, s>>>(M, N, K, A, sai, sak, B, sbk, sbj, C, ldc, 0, epi, bias, H, Zp);
   }
   return cudaGetLastError();
+}
+
+// Deterministic column sums (two passes through t->red).
+static void colsum(crom_trainer* t, cudaStream_t s, const float* X, long rows, int cols, float* out) {
+  const int chunks = (int)std::min<long>(kColChunks, std::max<long>(rows, 1));
+  colsum_part_kernel<<<dim3(blocks(cols, 32), chunks), dim3(32, 8), 0, s>>>(X, rows, cols, t->red);
+  colsum_final_kernel<<<blocks(cols, 128), 128, 0, s>>>(t->red, chunks, cols, out);
 }
 
 int trainer_set_precision(crom_trainer* t, int precision) {
@@ -437,13 +482,13 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
   }
   output_loss_kernel<<<blocks(N, 8), 256, 0, s>>>(t->H[L - 1], w, N, p + lay.dec_w[L], p + lay.dec_b[L], t->target,
                                                    t->dg, t->partial);
-  loss_final_kernel<<<1, 32, 0, s>>>(t->partial, (int)blocks(N, 8), N, loss_out ? loss_out : t->loss_dev);
+  loss_final_kernel<<<1, 1024, 0, s>>>(t->partial, (int)blocks(N, 8), N, loss_out ? loss_out : t->loss_dev);
   // ---- decoder reverse pass
   // output layer: gW_out[u] = sum_n dg[n] H_L[n][u], gb_out = sum dg
   e = gemm(t, s, 1, w, (int)N, t->dg, 0, 1, t->H[L - 1], w, 1, gr + lay.dec_w[L], w, kEpiStore, nullptr, nullptr,
            nullptr, t->split);
   if (e != cudaSuccess) return e;
-  colsum_kernel<<<1, 256, 0, s>>>(t->dg, N, 1, gr + lay.dec_b[L]);
+  colsum(t, s, t->dg, N, 1, gr + lay.dec_b[L]);
   out_delta_kernel<<<blocks(N * w, 256), 256, 0, s>>>(t->dg, p + lay.dec_w[L], t->Z[L - 1], w, N, t->delta);
   float* dcur = t->delta;
   float* dnext = t->delta2;
@@ -454,7 +499,7 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
     e = gemm(t, s, w, kprev, (int)N, dcur, 1, w, hprev, kprev, 1, gr + lay.dec_w[l], kprev, kEpiStore, nullptr,
              nullptr, nullptr, t->split);
     if (e != cudaSuccess) return e;
-    colsum_kernel<<<w, 256, 0, s>>>(dcur, N, w, gr + lay.dec_b[l]);
+    colsum(t, s, dcur, N, w, gr + lay.dec_b[l]);
     if (l > 0) {
       // delta_{l-1} = (delta_l W_l) * s'(Z_{l-1})
       e = gemm(t, s, (int)N, w, w, dcur, w, 1, p + lay.dec_w[l], w, 1, dnext, w, kEpiTimesEluD, nullptr, nullptr,
@@ -469,14 +514,14 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
     dcur = dnext;
     dnext = tmp;
   }
-  dq_kernel<<<blocks((long)B * r, 128), 128, 0, s>>>(t->din, B, S, m, r, t->dq);
+  dq_kernel<<<B, 256, 0, s>>>(t->din, B, S, m, r, t->dq);
   // ---- encoder reverse pass
   // dense 2: gW2 = dq^T h1, gb2 = sum dq, dz1 = (dq W2) * s'(z1)
   const int Ll = t->lens.back();
   if ((e = gemm(t, s, r, 32, B, t->dq, 1, r, t->d1h, 32, 1, gr + lay.d2w, 32, kEpiStore, nullptr, nullptr, nullptr)) !=
       cudaSuccess)
     return e;
-  colsum_kernel<<<r, 256, 0, s>>>(t->dq, B, r, gr + lay.d2b);
+  colsum(t, s, t->dq, B, r, gr + lay.d2b);
   if ((e = gemm(t, s, B, 32, r, t->dq, r, 1, p + lay.d2w, 32, 1, t->ed1, 32, kEpiTimesEluD, nullptr, nullptr,
                 t->d1z)) != cudaSuccess)
     return e;
@@ -485,7 +530,7 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
   if ((e = gemm(t, s, 32, Ll, B, t->ed1, 1, 32, hconv, Ll, 1, gr + lay.d1w, Ll, kEpiStore, nullptr, nullptr,
                 nullptr)) != cudaSuccess)
     return e;
-  colsum_kernel<<<32, 256, 0, s>>>(t->ed1, B, 32, gr + lay.d1b);
+  colsum(t, s, t->ed1, B, 32, gr + lay.d1b);
   if ((e = gemm(t, s, B, Ll, 32, t->ed1, 32, 1, p + lay.d1w, Ll, 1, t->edh, Ll, kEpiStore, nullptr, nullptr,
                 nullptr)) != cudaSuccess)
     return e;
@@ -495,7 +540,11 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
     const long n = (long)B * Lout;
     conv_dz_kernel<<<blocks(n, 256), 256, 0, s>>>(t->edh, t->conv_z[c - 1], n, t->edx);  // dz in edx
     const float* xin = (c == 1) ? snaps : t->conv_h[c - 2];
-    conv_grad_kernel<<<7, 256, 0, s>>>(t->edx, xin, Lin, Lout, B, gr + lay.conv[c - 1]);
+    {
+      const int chunks = (int)std::min<long>(kColChunks, std::max<long>((long)B * Lout / 1024, 1));
+      conv_grad_part_kernel<<<dim3(7, chunks), 256, 0, s>>>(t->edx, xin, Lin, Lout, B, t->red);
+      conv_grad_final_kernel<<<1, 32, 0, s>>>(t->red, chunks, gr + lay.conv[c - 1]);
+    }
     if (c > 1) conv_dx_kernel<<<blocks((long)B * Lin, 256), 256, 0, s>>>(t->edx, Lin, Lout, B,
                                                                          p + lay.conv[c - 1], t->edh);
   }
