@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--n-inst", type=int, default=1024)
     ap.add_argument("--n-codes", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", default=None, choices=["step", "recon", "plain"],
+    ap.add_argument("--fom-fields", type=int, default=512)
+    ap.add_argument("--only", default=None, choices=["step", "recon", "plain", "fom"],
                     help="run only one part (warmup + steps launches) for profiling; prints a short JSON line")
     return ap.parse_args()
 
@@ -74,6 +75,18 @@ def run_only(args):
         torch.cuda.synchronize()
         print(json.dumps({"only": args.only, "instances": w.n_inst, "calls": n,
                           "status_all_ok": bool((st.cpu().numpy() == 0).all())}))
+    elif args.only == "fom":
+        nb, nn = args.fom_fields, 256
+        rng = np.random.default_rng(0)
+        u = torch.tensor(rng.uniform(0, 1, size=(nb, nn, nn)).astype(np.float32), device="cuda")
+        ax = torch.tensor(rng.uniform(-0.5, 0.5, size=(nb, nn, nn)).astype(np.float32), device="cuda")
+        ay = torch.tensor(rng.uniform(-0.5, 0.5, size=(nb, nn, nn)).astype(np.float32), device="cuda")
+        nu = torch.full((nb,), 5e-3, dtype=torch.float32, device="cuda")
+        tmp = torch.empty_like(u)
+        crom.crom_fom_step(crom.CROM_FOM_ADVDIFF2D_PERIODIC, u, tmp, nu, dt=2.5e-5, n_steps=n, ax=ax, ay=ay)
+        torch.cuda.synchronize()
+        print(json.dumps({"only": "fom", "fields": nb, "nodes": nn * nn, "steps": n}))
+        return
     else:
         spec, params, codes, X = gen.recon_dense(n_codes=args.n_codes)
         ctx = crom.crom_create(spec.m, spec.r, spec.width, spec.hidden, 0)

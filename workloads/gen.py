@@ -157,11 +157,11 @@ def sine_modes_1d(P: int, rng, modes: int = 4):
     return a, u0
 
 
-def gaussian_bumps_2d(n: int, rng, count: int = 8):
-    """Sum of Gaussian bumps on the n x n grid: centres U[0,1]^2, sigma ~ U(0.03, 0.1),
+def gaussian_bumps_2d(n: int, rng, count: int = 8, sigma=(0.03, 0.1)):
+    """Sum of Gaussian bumps on the n x n grid: centres U[0,1]^2, sigma ~ U(sigma),
     amplitude ~ U(0.5, 1)."""
     c = rng.uniform(0.0, 1.0, size=(count, 2))
-    s = rng.uniform(0.03, 0.1, size=count)
+    s = rng.uniform(sigma[0], sigma[1], size=count)
     a = rng.uniform(0.5, 1.0, size=count)
     t = np.arange(n) / (n - 1)
     X1, X2 = np.meshgrid(t, t, indexing="ij")
