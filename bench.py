@@ -37,6 +37,12 @@ METRIC = "instance-steps/s, batched BF16 vs plain FP32 same GB300, rel-L2<=1e-3 
 WORKLOAD = "heat2d_batched_1024inst_M32-512_r8_w128_L5_gn2"
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one step_tc_kernel launch on the
+# 1024-instance workload, from an ncu capture of the current kernel (2,547,200 B read,
+# 0 B written); to be re-taken whenever the kernel changes.
+STEP_KERNEL_DRAM_BYTES = 2547200
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -487,9 +493,12 @@ def main():
                          "workload": "64 snapshots x 4096 points, decoder R^{2+16}->R width 256 x 5 ELU, "
                                      "strided-conv encoder, Adam"},
             "roofline": {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                         "frac": achieved_tf / peak_tf, "traffic": None,
+                         "frac": achieved_tf / peak_tf,
+                         "traffic": STEP_KERNEL_DRAM_BYTES if args.n_inst == 1024 and world == 1 else None,
                          "note": f"step kernel, algorithmic FLOPs {step_flops_per_sample()} per sample x "
-                                 f"{int(w.sizes.sum())} samples; peak = {peak_kind} bf16 burst"},
+                                 f"{int(w.sizes.sum())} samples; peak = {peak_kind} bf16 burst; traffic = "
+                                 "dram read+write bytes per launch from one ncu capture of this kernel at this "
+                                 "workload (profiles/step_tc_kernel_heat2d_512inst.md)"},
             "e2e": {"value": e2e_value, "unit": "instance-steps/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": 2 * args.steps,
