@@ -498,7 +498,7 @@ def main():
                          "note": f"step kernel, algorithmic FLOPs {step_flops_per_sample()} per sample x "
                                  f"{int(w.sizes.sum())} samples; peak = {peak_kind} bf16 burst; traffic = "
                                  "dram read+write bytes per launch from one ncu capture of this kernel at this "
-                                 "workload (profiles/step_tc_kernel_heat2d_512inst.md)"},
+                                 "workload"},
             "e2e": {"value": e2e_value, "unit": "instance-steps/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": 2 * args.steps,

@@ -34,11 +34,13 @@
 //  FP64; the r x r system is solved by an FP64 Cholesky factorisation spread
 //  over a warp; q is updated in FP64.
 //
-// The output layer w_out . h_L and the projection W_1q^T delta_1 share one
-// 16-row bf16 matrix P (row 0 = w_out, rows 1..r = W_1q columns); their UMMA
-// reads the activation buffer as the M = 128 operand, hi parts in rows 0..63 and
-// lo parts in rows 64..127 (or, after the reverse pass, in rows kS..2kS-1), and
-// the epilogue adds the two rows.
+// The output layer w_out . h_L is formed on the CUDA cores in the last forward
+// epilogue, in FP32 from h_L itself, for the channels the residual needs (a warp
+// butterfly over the 32 units of each warp, then the four lane quadrants' partial
+// sums).  The projection J = W_1q^T delta_1 is a UMMA against the 16-row bf16
+// matrix P (rows 1..r = W_1q columns) that reads the activation buffer as the
+// M = 128 operand, delta's hi parts in rows 0..kS-1 and lo parts in rows
+// kS..2kS-1; the epilogue adds the two rows.
 #include <math.h>
 
 #include <algorithm>
@@ -122,7 +124,6 @@ struct __align__(16) Group {
   float c1[kTcWidth];
   float dz1[kTcWidth];
   float xs[2][kSMax];
-  float gp[128];          // output-layer projection: hi rows 0..63, lo rows 64..127
   float rho[kSMax];
   float zero[kSMax];
   float jt[2][kSMax][16];  // Jacobian rows from the hi and the lo parts of delta_1
@@ -310,6 +311,24 @@ __device__ __forceinline__ double dot_exact(const float* a0, const float* a1, in
   return (double)s + (double)comp;
 }
 
+// Sum over the 32 lanes of a warp (32 hidden units) of 8 per-lane values v[s]: three
+// exchange rounds halve the set each time (offsets 16, 8, 4), two more add across the
+// remaining lanes (offsets 2, 1).  Lane l ends with the total of sample (l >> 2) & 7.
+__device__ __forceinline__ float warp_sum8(const float (&v)[8], int lane) {
+  float a[4], b[2];
+  const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+    a[s] = (u16 ? v[s + 4] : v[s]) + __shfl_xor_sync(0xffffffffu, u16 ? v[s] : v[s + 4], 16);
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+    b[s] = (u8 ? a[s + 2] : a[s]) + __shfl_xor_sync(0xffffffffu, u8 ? a[s] : a[s + 2], 8);
+  float t = (u4 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, u4 ? b[0] : b[1], 4);
+  t += __shfl_xor_sync(0xffffffffu, t, 2);
+  t += __shfl_xor_sync(0xffffffffu, t, 1);
+  return t;
+}
+
 // s'(z_1) of kC samples of this thread's unit, recomputed exactly as the
 // forward pass formed it (same FP32 operations), for the last reverse step.
 template <int kM, int kC>
@@ -399,49 +418,65 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
       for (int i = 0; i < kC; i += 2) unpk2(add2(pk2(v[0][i], v[0][i + 1]), pk2(bias, bias)), v[0][i], v[0][i + 1]);
       act<kM, kFirst, kCh, kC>(v, sg);
       tmem_stc(taddr(tb, lb, kSig + l * kSm + s0 + h8), sg);
+      if (l < p.L - 2) {
 #pragma unroll
-      for (int ch = 0; ch < kCh; ++ch) {
-        const int n = ch * kSm + s0 + h8;
-        split_store<kC>(c.H, u, n, 64 + n, v[ch]);
+        for (int ch = 0; ch < kCh; ++ch) {
+          const int n = ch * kSm + s0 + h8;
+          split_store<kC>(c.H, u, n, 64 + n, v[ch]);
+        }
+      } else {
+        // output layer on the CUDA cores, in FP32 from h_L itself: this warp's share
+        // (32 units) of w_out . h_L for the channels the residual needs; the four
+        // lane quadrants' shares meet in shared memory (the Jacobian buffer is free
+        // until the projection of this tile)
+        static_assert(kC == 8, "the output-layer reduction works on chunks of 8 samples");
+        const int lane = c.gt & 31, lq = c.gw & 3, sl = s0 + h8 + ((lane >> 2) & 7);
+        float* pr = &G->jt[0][0][0];
+#pragma unroll
+        for (int ch = 1; ch < kCh; ++ch) {
+          // iteration 0: the gradient channels only for advection, the Laplacian always;
+          // later: the difference channel
+          const bool need = !kFirst || ch == kCh - 1 || p.pde != CROM_PDE_HEAT;
+          if (need) {
+            float wv[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) wv[i] = c.wo * v[ch][i];
+            const float t = warp_sum8(wv, lane);
+            if ((lane & 3) == 0) pr[((ch - 1) * 4 + lq) * kSm + sl] = t;
+          }
+        }
       }
     }
     // the s'(z) stores complete in the background: nothing reads those columns
     // before the reverse pass, which waits for them
   }
-  // ---------------- output layer: PRJ[n][0] = w_out . h_L[:, n], hi rows + lo rows
-  if (!stage<kStageProj>(c, 0, 0)) return false;
-  if (c.part == 0) {
-    float v[8];
-    tmem_ld8(taddr(tb, lb, kAcc), v);
-    tmem_ld_wait();
-    G->gp[u] = v[0];
-  }
   group_sync(c.g);
+  // output channel ch (>= 1) of tile sample s: the four quadrants' partial sums
+  auto gout = [&](int ch, int s) {
+    const float* pr = &G->jt[0][0][0];
+    const int b = (ch - 1) * 4 * kSm + s;
+    return (pr[b] + pr[b + kSm]) + (pr[b + 2 * kSm] + pr[b + 3 * kSm]);
+  };
   // ---------------- Step 2 and the residual rho_j
   if (c.gt < kSm) {
     float rho = 0.f;
     if (c.gt < ns) {
       const int j = o0 + t * kSm + c.gt;
       if (kFirst) {
-        const int nl = (kM + 1) * kSm + c.gt;
-        const float lap = G->gp[nl] + G->gp[64 + nl];
+        const float lap = gout(kCh - 1, c.gt);
         if (p.coef_per_sample) alpha = p.alpha[j];
         double df;
         if (p.pde == CROM_PDE_HEAT) {
           df = p.dt * (double)alpha * (double)lap;
         } else {
           double adv = 0.0;
-          for (int k = 0; k < kM; ++k) {
-            const int nk = (1 + k) * kSm + c.gt;
-            adv += (double)p.vel[(size_t)j * kM + k] * (double)(G->gp[nk] + G->gp[64 + nk]);
-          }
+          for (int k = 0; k < kM; ++k) adv += (double)p.vel[(size_t)j * kM + k] * (double)gout(1 + k, c.gt);
           df = p.dt * (-adv + (double)alpha * (double)lap);
         }
         p.df[j] = df;
         rho = (float)(-df);
       } else {
-        const int nd = kSm + c.gt;
-        rho = (float)((double)(G->gp[nd] + G->gp[64 + nd]) - p.df[j]);
+        rho = (float)((double)gout(1, c.gt) - p.df[j]);
       }
     }
     G->rho[c.gt] = rho;
