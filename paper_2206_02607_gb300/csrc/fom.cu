@@ -87,6 +87,63 @@ __global__ void advdiff2d_kernel(const float* __restrict__ u, float* __restrict_
   out[base + (size_t)i * n + j] = fmaf(dt, fmaf(coef[b], lap, -div), c);
 }
 
+// The same update, marching: each warp owns 32 consecutive columns j and a strip of
+// kRows rows i, keeps u at rows i-1, i, i+1 and the x-face velocity of row i-1 in
+// registers, and takes the j-neighbours from the adjacent lanes (the two columns
+// beyond the warp from memory).  Every field value and face velocity is read once
+// per strip (plus two halo rows), so the kernel streams 16 B per node-step.
+// Requires n % 32 == 0 and n % (kRows * kWarps) == 0.
+constexpr int kRows = 32, kWarps = 4;
+__global__ void __launch_bounds__(32 * kWarps) advdiff2d_march_kernel(
+    const float* __restrict__ u, float* __restrict__ out, const float* __restrict__ ax,
+    const float* __restrict__ ay, const float* __restrict__ coef, int n, float dt, float inv_h, float inv_h2) {
+  const int b = blockIdx.z;
+  const int lane = threadIdx.x;
+  const int j = blockIdx.x * 32 + lane;
+  const int i0 = (blockIdx.y * kWarps + threadIdx.y) * kRows;
+  const size_t base = (size_t)b * n * n;
+  const float* ub = u + base;
+  const float* axb = ax + base;
+  const float* ayb = ay + base;
+  float* ob = out + base;
+  const float nu = coef[b];
+  const int jl = blockIdx.x * 32 == 0 ? n - 1 : blockIdx.x * 32 - 1;   // column left of the warp
+  const int jr = blockIdx.x * 32 + 32 == n ? 0 : blockIdx.x * 32 + 32; // column right of the warp
+  int im = i0 == 0 ? n - 1 : i0 - 1;
+  float uim = ub[(size_t)im * n + j];
+  float c = ub[(size_t)i0 * n + j];
+  float a_l = axb[(size_t)im * n + j];
+#pragma unroll 4
+  for (int k = 0; k < kRows; ++k) {
+    const int i = i0 + k;
+    const int ip = i == n - 1 ? 0 : i + 1;
+    const float uip = ub[(size_t)ip * n + j];
+    const float a_r = axb[(size_t)i * n + j];
+    const float b_r = ayb[(size_t)i * n + j];
+    // halo columns: lane 0 needs column jl, lane 31 column jr
+    const float halo_u = lane == 0 ? ub[(size_t)i * n + jl] : (lane == 31 ? ub[(size_t)i * n + jr] : 0.f);
+    const float halo_b = lane == 0 ? ayb[(size_t)i * n + jl] : 0.f;
+    float ujm = __shfl_up_sync(0xffffffffu, c, 1);
+    float ujp = __shfl_down_sync(0xffffffffu, c, 1);
+    float b_l = __shfl_up_sync(0xffffffffu, b_r, 1);
+    if (lane == 0) {
+      ujm = halo_u;
+      b_l = halo_b;
+    }
+    if (lane == 31) ujp = halo_u;
+    const float fr = a_r * (a_r > 0.f ? c : uip);
+    const float fl = a_l * (a_l > 0.f ? uim : c);
+    const float gr = b_r * (b_r > 0.f ? c : ujp);
+    const float gl = b_l * (b_l > 0.f ? ujm : c);
+    const float div = (fr - fl + gr - gl) * inv_h;
+    const float lap = (uim + uip + ujm + ujp - 4.f * c) * inv_h2;
+    ob[(size_t)i * n + j] = fmaf(dt, fmaf(nu, lap, -div), c);
+    uim = c;
+    c = uip;
+    a_l = a_r;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_fom(int kind, int n_batch, int nx, int ny, const float* coef, const float* ax, const float* ay,
@@ -110,9 +167,15 @@ cudaError_t launch_fom(int kind, int n_batch, int nx, int ny, const float* coef,
         heat2d_neumann_kernel<true><<<grid, dim3(32, 8), 0, s>>>(src, dst, coef, nx, (float)(dt / (h * h)));
     } else {
       const double h = 1.0 / nx;
-      dim3 grid((nx + 31) / 32, (nx + 7) / 8, n_batch);
-      advdiff2d_kernel<<<grid, dim3(32, 8), 0, s>>>(src, dst, ax, ay, coef, nx, (float)dt, (float)(1.0 / h),
-                                                    (float)(1.0 / (h * h)));
+      if (nx % 32 == 0 && nx % (kRows * kWarps) == 0) {
+        dim3 grid(nx / 32, nx / (kRows * kWarps), n_batch);
+        advdiff2d_march_kernel<<<grid, dim3(32, kWarps), 0, s>>>(src, dst, ax, ay, coef, nx, (float)dt,
+                                                                 (float)(1.0 / h), (float)(1.0 / (h * h)));
+      } else {
+        dim3 grid((nx + 31) / 32, (nx + 7) / 8, n_batch);
+        advdiff2d_kernel<<<grid, dim3(32, 8), 0, s>>>(src, dst, ax, ay, coef, nx, (float)dt, (float)(1.0 / h),
+                                                      (float)(1.0 / (h * h)));
+      }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

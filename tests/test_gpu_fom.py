@@ -94,8 +94,8 @@ def _faces(n, rng, nb):
     return np.stack(ax), np.stack(ay)
 
 
-def test_advdiff_matches_oracle_conserves_mass_and_translates(c):
-    n = 96
+@pytest.mark.parametrize("n", [96, 128, 256])   # 128 and 256: the marching kernel (n % 128 == 0)
+def test_advdiff_matches_oracle_conserves_mass_and_translates(c, n):
     h = 1 / n
     rng = np.random.default_rng(9)
     ax, ay = _faces(n, rng, 2)
@@ -118,6 +118,13 @@ def test_advdiff_matches_oracle_conserves_mass_and_translates(c):
     got = run(c, c.CROM_FOM_ADVDIFF2D_PERIODIC, u1, np.array([0.0]), (1 / 16) / a, 1,
               np.full((1, 16, 16), a, np.float32), np.zeros((1, 16, 16), np.float32))
     np.testing.assert_allclose(got[0], np.roll(u1[0], 1, axis=0), rtol=0, atol=1e-6)
+    # ... in both directions on the marching kernel's grid (lane-to-lane and halo neighbours)
+    u2 = rng.uniform(size=(2, 128, 128)).astype(np.float32)
+    vx = np.stack([np.full((128, 128), a, np.float32), np.zeros((128, 128), np.float32)])
+    vy = np.stack([np.zeros((128, 128), np.float32), np.full((128, 128), -a, np.float32)])
+    got = run(c, c.CROM_FOM_ADVDIFF2D_PERIODIC, u2, np.array([0.0, 0.0]), (1 / 128) / a, 1, vx, vy)
+    np.testing.assert_allclose(got[0], np.roll(u2[0], 1, axis=0), rtol=0, atol=1e-6)
+    np.testing.assert_allclose(got[1], np.roll(u2[1], -1, axis=1), rtol=0, atol=1e-6)
 
 
 def test_fom_rejects_bad_arguments(c):
