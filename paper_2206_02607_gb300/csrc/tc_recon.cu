@@ -12,8 +12,9 @@
 //     N = 64 points, K = 128), A = W_l (K-major, resident), B = H (MN-major,
 //     written by the previous epilogue; the hi and lo parts side by side as one
 //     N = 128 operand, added in the epilogue); epilogue: bias, ELU, bf16 split, store;
-//   output: D[n][0] = sum_u H_L[u][n] w_out[u] by one more UMMA (M = 128 rows
-//     of which the 64 points are used, N = 16 rows of the projection matrix).
+//   output layer: w_out . h_L on the CUDA cores in the last hidden layer's
+//     epilogue, in FP32 from h_L itself (a warp butterfly over the 32 units of
+//     each warp, then the four lane quadrants' partial sums), written coalesced.
 // Precision: each activation operand h is stored as hi = bf16(h) and
 // lo = bf16(h - hi) and both are multiplied into the same FP32 accumulator
 // (kSplit = 1); kSplit = 0 keeps the high part only.
@@ -36,7 +37,6 @@ constexpr int kTileN = 64;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kGroupCols = 256;
 constexpr uint32_t kAccCol = 0;    // W h_hi in columns 0..63, W h_lo in 64..127
-constexpr uint32_t kOutCol = 128;
 constexpr uint32_t kWaitLimit = 1u << 25;
 constexpr size_t kHBuf = (size_t)kTcWidth * kTileN * 2;  // one bf16 operand buffer, 16 KB
 
@@ -48,6 +48,7 @@ struct ReconParams {
   const float* w1;  // [128][m+r]
   const float* b1;
   const float* bh;  // [(hidden-1)][128]
+  const float* wout;  // [128]
   float bout;
   const double* q;  // [n_codes][r]
   const float* x;   // [n_pts][m]
@@ -63,6 +64,7 @@ struct __align__(16) Shared {
   int pad;
   float bh[4][kTcWidth];
   float w1x[2][kTcWidth];
+  float wout[kTcWidth];
 };
 
 struct __align__(16) Group {
@@ -70,12 +72,30 @@ struct __align__(16) Group {
   int pad[2];
   float c1[kTcWidth];
   float xs[2][kTileN];
+  float outp[4][kTileN];  // output layer: partial sums of the four lane quadrants
 };
 
-// The output UMMA reads 128 rows of a 64-row operand; the rows beyond are unused
-// but the reads must stay inside shared memory.
 constexpr size_t kTailBytes = sizeof(Shared) + kGroups * sizeof(Group);
-constexpr size_t kTailPad = kTailBytes >= kHBuf ? 0 : kHBuf - kTailBytes;
+
+// Sum over the 32 lanes of a warp (32 hidden units) of 16 per-lane values v[s]:
+// four exchange rounds halve the set (offsets 16, 8, 4, 2), one more adds across
+// the lane pair (offset 1).  Lane l ends with the total of point (l >> 1) & 15.
+__device__ __forceinline__ float warp_sum16(const float (&v)[16], int lane) {
+  float a[8], b[4], c[2];
+  const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4, u2 = lane & 2;
+#pragma unroll
+  for (int s = 0; s < 8; ++s)
+    a[s] = (u16 ? v[s + 8] : v[s]) + __shfl_xor_sync(0xffffffffu, u16 ? v[s] : v[s + 8], 16);
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+    b[s] = (u8 ? a[s + 4] : a[s]) + __shfl_xor_sync(0xffffffffu, u8 ? a[s] : a[s + 4], 8);
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+    c[s] = (u4 ? b[s + 2] : b[s]) + __shfl_xor_sync(0xffffffffu, u4 ? b[s] : b[s + 2], 4);
+  float t = (u2 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, u2 ? c[0] : c[1], 2);
+  t += __shfl_xor_sync(0xffffffffu, t, 1);
+  return t;
+}
 
 __device__ __forceinline__ void group_sync(int g) {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGT) : "memory");
@@ -149,6 +169,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
   if (tid < kTcWidth) {
     for (int l = 0; l < p.n_hidden_mats; ++l) S->bh[l][tid] = p.bh[l * kTcWidth + tid];
     for (int k = 0; k < m; ++k) S->w1x[k][tid] = p.w1[tid * (m + r) + k];
+    S->wout[tid] = p.wout[tid];
   }
   tc_fence_before();
   __syncthreads();
@@ -166,14 +187,13 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
   const uint32_t wbase = smem_u32(Wimg);
   // Base UMMA descriptors; every operand slice is base + a compile-time offset.
   const uint64_t dW = smem_desc_sw128(wbase, 16, 1024);
-  const uint64_t dP = smem_desc_sw128(wbase + (uint32_t)p.n_hidden_mats * kTcLayerBytes, 16, 1024);
   const uint64_t dHhi = smem_desc_sw128(smem_u32(Hhi), 16384, 1024);
-  const uint64_t dHlo = smem_desc_sw128(smem_u32(Hlo), 16384, 1024);
   constexpr uint32_t id_layer = idesc_f16(128, kSplit ? 2 * kTileN : kTileN, false, true, true);
-  constexpr uint32_t id_out = idesc_f16(128, 16, true, false, true);
   int cur_code = -1;
   float c = 0.f;
   const float wx0 = S->w1x[0][u], wx1 = (m > 1) ? S->w1x[1][u] : 0.f;
+  const float wo = S->wout[u];
+  const int lane = gt & 31;
   const int n_tiles = p.n_codes * p.tiles_per_code;
 
   for (int tile = blockIdx.x * kGroups + g; tile < n_tiles && ok; tile += gridDim.x * kGroups) {
@@ -203,32 +223,23 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
       }
       store_split16<kSplit>(Hhi, Hlo, u, n0, h);
     }
-    // ---- hidden layers and the output layer on the tensor cores
-    for (int l = 0; l <= p.n_hidden_mats; ++l) {
-      const bool last = (l == p.n_hidden_mats);
+    // ---- hidden layers on the tensor cores; the output layer in the last epilogue
+    for (int l = 0; l < p.n_hidden_mats; ++l) {
+      const bool last = (l == p.n_hidden_mats - 1);
       fence_proxy_async_smem();
       tc_fence_before();
       group_sync(g);
       bool done = true;
       if ((gt >> 5) == 0) {  // the first warp issues (one elected lane) and waits, the rest wait at the barrier
         tc_fence_after();
-        if (!last) {
-          // The lo buffer follows the hi buffer at the operand's 64-column block
-          // stride, so one UMMA with N = 128 multiplies both parts at once: columns
-          // 0..63 of the accumulator get W h_hi, columns 64..127 get W h_lo.
-          const uint64_t a0 = desc_add(dW, (uint32_t)l * kTcLayerBytes);
+        // The lo buffer follows the hi buffer at the operand's 64-column block
+        // stride, so one UMMA with N = 128 multiplies both parts at once: columns
+        // 0..63 of the accumulator get W h_hi, columns 64..127 get W h_lo.
+        const uint64_t a0 = desc_add(dW, (uint32_t)l * kTcLayerBytes);
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk)
-            umma_f16_warp(tb + kAccCol, desc_add(a0, kmajor_kslice(128, kk)), desc_add(dHhi, mnmajor_kslice(kk)),
-                          id_layer, kk != 0);
-        } else {
-#pragma unroll
-          for (int part = 0; part <= kSplit; ++part)
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk)
-              umma_f16_warp(tb + kOutCol, desc_add(part ? dHlo : dHhi, mnmajor_kslice(kk)),
-                            desc_add(dP, kmajor_kslice(16, kk)), id_out, (part | kk) != 0);
-        }
+        for (int kk = 0; kk < 8; ++kk)
+          umma_f16_warp(tb + kAccCol, desc_add(a0, kmajor_kslice(128, kk)), desc_add(dHhi, mnmajor_kslice(kk)),
+                        id_layer, kk != 0);
         umma_commit_warp(&G->bar_mma);
         done = mbar_wait(&G->bar_mma, phase, kWaitLimit);
       }
@@ -236,32 +247,43 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
       phase ^= 1;
       tc_fence_after();
       if (!ok) break;
-      if (!last) {
-        const float bias = S->bh[l][u];
+      const float bias = S->bh[l][u];
 #pragma unroll 1
-        for (int n0 = nbeg; n0 < nbeg + kTileN / 2; n0 += 16) {
-          float v[16], w[16];
-          tmem_ld16(taddr(tb, lane_base, kAccCol + n0), v);
-          if (kSplit) tmem_ld16(taddr(tb, lane_base, kAccCol + kTileN + n0), w);
-          tmem_ld_wait();
-          f32x2 h[8];
-          const f32x2 b2 = pk2(bias, bias);
+      for (int n0 = nbeg; n0 < nbeg + kTileN / 2; n0 += 16) {
+        float v[16], w[16];
+        tmem_ld16(taddr(tb, lane_base, kAccCol + n0), v);
+        if (kSplit) tmem_ld16(taddr(tb, lane_base, kAccCol + kTileN + n0), w);
+        tmem_ld_wait();
+        f32x2 h[8];
+        const f32x2 b2 = pk2(bias, bias);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float e0, e1;
+          f32x2 z = add2(pk2(v[2 * j], v[2 * j + 1]), b2);
+          if (kSplit) z = add2(z, pk2(w[2 * j], w[2 * j + 1]));
+          h[j] = elu2(z, e0, e1);
+        }
+        if (!last) {
+          store_split16<kSplit>(Hhi, Hlo, u, n0, h);
+        } else {
+          float wv[16];
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            float e0, e1;
-            f32x2 z = add2(pk2(v[2 * j], v[2 * j + 1]), b2);
-            if (kSplit) z = add2(z, pk2(w[2 * j], w[2 * j + 1]));
-            h[j] = elu2(z, e0, e1);
+            unpk2(h[j], wv[2 * j], wv[2 * j + 1]);
+            wv[2 * j] *= wo;
+            wv[2 * j + 1] *= wo;
           }
-          store_split16<kSplit>(Hhi, Hlo, u, n0, h);
+          const float t = warp_sum16(wv, lane);
+          if ((lane & 1) == 0) G->outp[lq][n0 + ((lane >> 1) & 15)] = t;
         }
-      } else if (half == 0) {
-        float v[16];
-        tmem_ld16(taddr(tb, lane_base, kOutCol), v);
-        tmem_ld_wait();
-        const int n = p0 + u;
-        if (u < kTileN && n < p.n_pts) p.out[(size_t)code * p.n_pts + n] = v[0] + p.bout;
       }
+    }
+    if (!ok) break;
+    group_sync(g);
+    if (gt < kTileN) {
+      const int n = p0 + gt;
+      const float o = (G->outp[0][gt] + G->outp[1][gt]) + (G->outp[2][gt] + G->outp[3][gt]);
+      if (n < p.n_pts) p.out[(size_t)code * p.n_pts + n] = o + p.bout;
     }
   }
   if (!ok && gt == 0) atomicExch(p.flag, 1);
@@ -283,6 +305,7 @@ cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const d
   p.w1 = ctx->w.w1;
   p.b1 = ctx->w.b1;
   p.bh = ctx->w.bh;
+  p.wout = ctx->w.wout;
   p.bout = ctx->w.bout;
   p.q = q;
   p.x = x;
@@ -292,7 +315,7 @@ cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const d
   p.tiles_per_code = (n_pts + kTileN - 1) / kTileN;
   p.flag = ctx->queue + 2;
   const size_t smem = 1024 + (((size_t)p.img_bytes + 1023) & ~(size_t)1023) + (size_t)kGroups * 2 * kHBuf +
-                      kTailBytes + kTailPad;
+                      kTailBytes;
   const long long tiles = (long long)n_codes * p.tiles_per_code;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   const int grid = (int)std::min<long long>((tiles + kGroups - 1) / kGroups, ctx->num_sms);
