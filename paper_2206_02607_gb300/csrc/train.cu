@@ -120,6 +120,30 @@ __global__ void epi_times_elud_kernel(float* C, long M, int N, long ldc, const f
   C[o] *= elu_d(Zp[o]);
 }
 
+// The same epilogues four columns at a time (N % 4 == 0, ldc % 4 == 0, 16-byte
+// aligned rows): rows over blockIdx.y / threadIdx.y, column quads over x.
+__global__ void epi_bias_elu4_kernel(float* C, long M, int N4, long ldc, const float* bias, float* H) {
+  for (long i = (long)blockIdx.y * blockDim.y + threadIdx.y; i < M; i += (long)gridDim.y * blockDim.y)
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < N4; q += gridDim.x * blockDim.x) {
+      float4* cp = reinterpret_cast<float4*>(C + i * ldc) + q;
+      const float4 b = reinterpret_cast<const float4*>(bias)[q];
+      float4 z = *cp;
+      z.x += b.x; z.y += b.y; z.z += b.z; z.w += b.w;
+      *cp = z;
+      reinterpret_cast<float4*>(H + i * ldc)[q] = make_float4(elu_f(z.x), elu_f(z.y), elu_f(z.z), elu_f(z.w));
+    }
+}
+__global__ void epi_times_elud4_kernel(float* C, long M, int N4, long ldc, const float* Zp) {
+  for (long i = (long)blockIdx.y * blockDim.y + threadIdx.y; i < M; i += (long)gridDim.y * blockDim.y)
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < N4; q += gridDim.x * blockDim.x) {
+      float4* cp = reinterpret_cast<float4*>(C + i * ldc) + q;
+      const float4 zp = reinterpret_cast<const float4*>(Zp + i * ldc)[q];
+      float4 v = *cp;
+      v.x *= elu_d(zp.x); v.y *= elu_d(zp.y); v.z *= elu_d(zp.z); v.w *= elu_d(zp.w);
+      *cp = v;
+    }
+}
+
 // out[e] = sum_s parts[s * stride + e] (in split order), then optionally out[e] = val.
 __global__ void sum_splits_kernel(const float* parts, int splits, long stride, long n, float* out) {
   const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -149,6 +173,29 @@ __global__ void colsum_part_kernel(const float* X, long rows, int cols, double* 
     for (int y = 0; y < 8; ++y) t += red[y][threadIdx.x];
     part[(long)blockIdx.y * cols + c] = t;
   }
+}
+// Column sums four columns at a time (cols % 4 == 0): block (64 column quads x 4
+// row lanes) per (column-quad group, row chunk).
+__global__ void colsum_part4_kernel(const float* X, long rows, int cols, double* part) {
+  const int q = blockIdx.x * 64 + threadIdx.x, cols4 = cols / 4;
+  const long per = (rows + gridDim.y - 1) / gridDim.y;
+  const long r0 = (long)blockIdx.y * per, r1 = min(rows, r0 + per);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  if (q < cols4)
+    for (long r = r0 + threadIdx.y; r < r1; r += 4) {
+      const float4 v = reinterpret_cast<const float4*>(X + r * cols)[q];
+      s0 += v.x; s1 += v.y; s2 += v.z; s3 += v.w;
+    }
+  __shared__ double red[4][64][4];
+  red[threadIdx.y][threadIdx.x][0] = s0;
+  red[threadIdx.y][threadIdx.x][1] = s1;
+  red[threadIdx.y][threadIdx.x][2] = s2;
+  red[threadIdx.y][threadIdx.x][3] = s3;
+  __syncthreads();
+  if (threadIdx.y == 0 && q < cols4)
+    for (int e = 0; e < 4; ++e)
+      part[(long)blockIdx.y * cols + 4 * q + e] =
+          (red[0][threadIdx.x][e] + red[1][threadIdx.x][e]) + (red[2][threadIdx.x][e] + red[3][threadIdx.x][e]);
 }
 __global__ void colsum_final_kernel(const double* part, int chunks, int cols, float* out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -405,10 +452,16 @@ static cudaError_t gemm(crom_trainer* t, cudaStream_t s, int M, int N, int K, co
                                      CUDA_R_32F, (int)ldc, CUBLAS_COMPUTE_32F_FAST_TF32, CUBLAS_GEMM_DEFAULT);
     if (st != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
     const long n = (long)M * N;
-    if (epi == kEpiBiasElu)
-      epi_bias_elu_kernel<<<blocks(n, 256), 256, 0, s>>>(C, M, N, ldc, bias, H);
-    else if (epi == kEpiTimesEluD)
-      epi_times_elud_kernel<<<blocks(n, 256), 256, 0, s>>>(C, M, N, ldc, Zp);
+    const bool vec = N % 4 == 0 && ldc % 4 == 0 && ((uintptr_t)C & 15) == 0 && (!H || ((uintptr_t)H & 15) == 0) &&
+                     (!Zp || ((uintptr_t)Zp & 15) == 0) && (!bias || ((uintptr_t)bias & 15) == 0);
+    const dim3 vb(64, 4), vg(blocks(N / 4, 64), (unsigned)std::min<long>(blocks(M, 4), 4096));
+    if (epi == kEpiBiasElu) {
+      if (vec) epi_bias_elu4_kernel<<<vg, vb, 0, s>>>(C, M, N / 4, ldc, bias, H);
+      else epi_bias_elu_kernel<<<blocks(n, 256), 256, 0, s>>>(C, M, N, ldc, bias, H);
+    } else if (epi == kEpiTimesEluD) {
+      if (vec) epi_times_elud4_kernel<<<vg, vb, 0, s>>>(C, M, N / 4, ldc, Zp);
+      else epi_times_elud_kernel<<<blocks(n, 256), 256, 0, s>>>(C, M, N, ldc, Zp);
+    }
     return cudaGetLastError();
   }
   dim3 grid(blocks(N, kTile), blocks(M, kTile), split ? kSplitK : 1);
@@ -425,7 +478,10 @@ static cudaError_t gemm(crom_trainer* t, cudaStream_t s, int M, int N, int K, co
 // Deterministic column sums (two passes through t->red).
 static void colsum(crom_trainer* t, cudaStream_t s, const float* X, long rows, int cols, float* out) {
   const int chunks = (int)std::min<long>(kColChunks, std::max<long>(rows, 1));
-  colsum_part_kernel<<<dim3(blocks(cols, 32), chunks), dim3(32, 8), 0, s>>>(X, rows, cols, t->red);
+  if (cols % 4 == 0 && ((uintptr_t)X & 15) == 0)
+    colsum_part4_kernel<<<dim3(blocks(cols / 4, 64), chunks), dim3(64, 4), 0, s>>>(X, rows, cols, t->red);
+  else
+    colsum_part_kernel<<<dim3(blocks(cols, 32), chunks), dim3(32, 8), 0, s>>>(X, rows, cols, t->red);
   colsum_final_kernel<<<blocks(cols, 128), 128, 0, s>>>(t->red, chunks, cols, out);
 }
 
