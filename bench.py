@@ -268,6 +268,10 @@ def main():
         crom.crom_step(ctx, q if qq is None else qq, alpha, s_off, samples, status, dt=w.dt,
                        gn_iters=w.gn_iters, max_samples=max_s, precision=prec)
 
+    # ---- tile shape of the tensor-core step: measured on this batch (outside the timed region)
+    tile_s0, tile_s1, tile_ms = crom.crom_autotune(ctx, q, alpha, s_off, samples, status, dt=w.dt,
+                                                   gn_iters=w.gn_iters, max_samples=max_s)
+
     # ---- device-resident timing, L2 flushed before each timed step
     for _ in range(args.warmup):
         step()
@@ -470,7 +474,9 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "global_batch": world * w.n_inst, "samples_per_step": int(w.sizes.sum()),
                        "parallelism": f"instances sharded, {w.n_inst} per GPU" if world > 1 else "single GPU",
-                       "l2": "flushed (256 MB write) before every timed step"},
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "tiles": {"s0": tile_s0, "s1": tile_s1, "autotuned": True,
+                                 "ms_per_step_s1_32_16": [round(tile_ms[0], 4), round(tile_ms[1], 4)]}},
             "status_all_ok": bool(np.all(st == 0)),
             "accuracy_vs_fp64_oracle": acc,
             "plain_fp32_single": {"value": plain_value, "unit": "instance-steps/s", "us_per_step": plain_ms * 1e3,

@@ -205,6 +205,26 @@ int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n
                  const float* alpha, const float* vel, const int* s_off, const float* samples, int n_samples,
                  int max_samples, int* status, crom_stream stream);
 
+/* Sample-tile shape of the tensor-core step (CROM_PREC_BF16X2): s0 samples per
+ * tile in the first Gauss-Newton iteration (4 channels: 16, fixed by the 64
+ * operand columns of a tile), s1 in later ones (2 channels: 32 or 16).  Larger
+ * tiles issue half as many UMMA stages; smaller ones waste less on the ragged last
+ * tile of each instance.  crom_set_step_tiles fixes the shape; crom_get_step_tiles
+ * reads it and, into ms[2] (may be NULL), the per-step times that the last
+ * crom_autotune measured for s1 = 32 and 16 (-1 when not measured). */
+int crom_set_step_tiles(crom_ctx* ctx, int s0, int s1);
+int crom_get_step_tiles(const crom_ctx* ctx, int* s0, int* s1, float* ms);
+
+/* Autotuner of the tile shape: times the BF16X2 step on the given batch (same
+ * arguments as crom_step; q is read, not updated: the trials run on a copy; status
+ * is overwritten) for every tile shape, five steps each after one warm-up, and
+ * keeps the fastest in the context.  Blocks until the timing completes; allocates
+ * a copy of q (not during stream capture).  The rollout graph cache is keyed on the
+ * tile shape, so a re-tuned context records a new graph. */
+int crom_autotune(crom_ctx* ctx, const crom_step_desc* step, int n_inst, const double* q, const float* alpha,
+                  const float* vel, const int* s_off, const float* samples, int n_samples, int max_samples,
+                  int* status, crom_stream stream);
+
 /* crom_step with precision CROM_PREC_FP32, for callers that cannot allocate
  * device memory when they step: code recording the step into a CUDA graph during
  * stream capture (where cudaMalloc is not allowed), hosts whose memory policy

@@ -48,7 +48,8 @@ EXPORTED = ("crom_version", "crom_last_error", "crom_create", "crom_destroy", "c
             "crom_decode", "crom_step", "crom_rollout", "crom_step_noalloc", "crom_fom_step", "crom_trainer_create",
             "crom_trainer_destroy", "crom_trainer_param_count", "crom_trainer_set_params",
             "crom_trainer_get_params", "crom_trainer_get_grads", "crom_train_step", "crom_encode",
-            "crom_reconstruct", "crom_robust_samples", "crom_tangent_velocity", "crom_trainer_set_precision")
+            "crom_reconstruct", "crom_robust_samples", "crom_tangent_velocity", "crom_trainer_set_precision",
+            "crom_set_step_tiles", "crom_get_step_tiles", "crom_autotune")
 
 
 class CromError(RuntimeError):
@@ -93,6 +94,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.crom_encode.argtypes = [vp, i, vp, vp, vp]
     lib.crom_reconstruct.argtypes = [vp, i, i, vp, i, vp, vp, vp]
     lib.crom_tangent_velocity.argtypes = [vp, i, vp, vp, d, vp, vp, i, vp, vp]
+    lib.crom_set_step_tiles.argtypes = [vp, i, i]
+    lib.crom_get_step_tiles.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float)]
+    lib.crom_autotune.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, vp, vp, vp, vp, vp, i, i, vp, vp]
     lib.crom_robust_samples.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, i, vp, vp, i, i, vp, vp, i, vp, i,
                                         d, i, vp, vp, vp, vp]
     for name in EXPORTED:
@@ -308,6 +312,32 @@ def crom_reconstruct(ctx: CromContext, q, x, out, precision: int = CROM_PREC_FP3
     _need(q, torch.float64, "q"); _need(x, torch.float32, "x"); _need(out, torch.float32, "out")
     _check(_LIB.crom_reconstruct(ctx.handle, precision, q.shape[0], _ptr(q), x.shape[0], _ptr(x), _ptr(out),
                                  _stream(stream)))
+
+
+def crom_set_step_tiles(ctx: CromContext, s0: int, s1: int):
+    _check(_LIB.crom_set_step_tiles(ctx.handle, s0, s1))
+
+
+def crom_get_step_tiles(ctx: CromContext):
+    """(s0, s1, [ms for s1 = 32, ms for s1 = 16]) of the context's tensor-core step."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    ms = (ctypes.c_float * 2)()
+    _check(_LIB.crom_get_step_tiles(ctx.handle, ctypes.byref(a), ctypes.byref(b), ms))
+    return a.value, b.value, [ms[0], ms[1]]
+
+
+def crom_autotune(ctx: CromContext, q, alpha, s_off, samples, status, *, dt: float, gn_iters: int,
+                  max_samples: int, pde: int = CROM_PDE_HEAT, vel=None, coef_per_sample: bool = False,
+                  line_search: int = 0, stream=None):
+    """Measure the tensor-core step's tile shapes on this batch and keep the fastest."""
+    import torch
+    _need(q, torch.float64, "q"); _need(alpha, torch.float32, "alpha"); _need(s_off, torch.int32, "s_off")
+    _need(samples, torch.float32, "samples"); _need(status, torch.int32, "status"); _need(vel, torch.float32, "vel")
+    desc = crom_step_desc(pde, gn_iters, dt, int(bool(coef_per_sample)), int(line_search))
+    _check(_LIB.crom_autotune(ctx.handle, ctypes.byref(desc), q.shape[0], _ptr(q), _ptr(alpha), _ptr(vel),
+                              _ptr(s_off), _ptr(samples), samples.shape[0], max_samples, _ptr(status),
+                              _stream(stream)))
+    return crom_get_step_tiles(ctx)
 
 
 def crom_tangent_velocity(ctx: CromContext, q, q_prev, pt_off, x, out, *, dt: float, stream=None):

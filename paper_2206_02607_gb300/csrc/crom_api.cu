@@ -371,11 +371,11 @@ int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n
   cudaStream_t s = (cudaStream_t)stream;
   // The key: every argument that the recorded launches depend on.
   struct Key {
-    int precision, n_steps, n_inst, n_samples, max_samples, pde, gn_iters, coef_per_sample, line_search;
+    int precision, n_steps, n_inst, n_samples, max_samples, pde, gn_iters, coef_per_sample, line_search, tiles;
     double dt;
     const void *q, *alpha, *vel, *s_off, *samples, *status, *weights;
   } key{precision, n_steps, n_inst, n_samples, max_samples, step->pde, step->gn_iters, step->coef_per_sample,
-        step->line_search, step->dt, q, alpha, vel, s_off, samples, status, ctx->w.w1};
+        step->line_search, ctx->tc_tile_s1, step->dt, q, alpha, vel, s_off, samples, status, ctx->w.w1};
   std::vector<unsigned char> kb(sizeof(Key));
   memcpy(kb.data(), &key, sizeof(Key));
   cudaError_t e;
@@ -413,6 +413,88 @@ int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n
   }
   e = cudaGraphLaunch(ctx->rollout_exec, s);
   if (e != cudaSuccess) return cuda_fail(e, "crom_rollout (launch)");
+  return CROM_OK;
+}
+
+int crom_set_step_tiles(crom_ctx* ctx, int s0, int s1) {
+  if (!ctx) return fail(CROM_ERR_INVALID_ARG, "crom_set_step_tiles: null context");
+  if (s0 != 16 || (s1 != 16 && s1 != 32))
+    return fail(CROM_ERR_UNSUPPORTED, "crom_set_step_tiles: tiles (16, 32) or (16, 16)");
+  ctx->tc_tile_s1 = s1;
+  return CROM_OK;
+}
+
+int crom_get_step_tiles(const crom_ctx* ctx, int* s0, int* s1, float* ms) {
+  if (!ctx || !s0 || !s1) return fail(CROM_ERR_INVALID_ARG, "crom_get_step_tiles: null argument");
+  *s0 = 16;
+  *s1 = ctx->tc_tile_s1;
+  if (ms) {
+    ms[0] = ctx->tune_ms[0];
+    ms[1] = ctx->tune_ms[1];
+  }
+  return CROM_OK;
+}
+
+int crom_autotune(crom_ctx* ctx, const crom_step_desc* step, int n_inst, const double* q, const float* alpha,
+                  const float* vel, const int* s_off, const float* samples, int n_samples, int max_samples,
+                  int* status, crom_stream stream) {
+  const char* fn = "crom_autotune";
+  if (!ctx || !step || !q) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": null argument");
+  if (!tc_shape_ok(ctx->desc) || !ctx->w.tc_img)
+    return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": the tensor-core step needs width 128, 2<=hidden<=5, "
+                                                        "m<=2, r<=15, ELU");
+  if (n_inst <= 0) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": empty batch");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceAllocs buf;
+  double* qs = buf.get<double>((size_t)n_inst * ctx->desc.r);  // the caller's q is left untouched
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = buf.err;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int variants[2] = {32, 16};
+  const int saved = ctx->tc_tile_s1;
+  float best_ms = 0.f;
+  int best = saved;
+  for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+    ctx->tc_tile_s1 = variants[v];
+    const size_t qb = (size_t)n_inst * ctx->desc.r * sizeof(double);
+    e = cudaMemcpyAsync(qs, q, qb, cudaMemcpyDeviceToDevice, s);
+    int rc = CROM_OK;
+    if (e == cudaSuccess)  // warm-up (first launch of this variant, shared-memory attribute)
+      rc = crom_step(ctx, step, CROM_PREC_BF16X2, n_inst, qs, alpha, vel, s_off, samples, n_samples, max_samples,
+                     status, stream);
+    if (rc != CROM_OK) {
+      ctx->tc_tile_s1 = saved;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return rc;
+    }
+    const int reps = 5;
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int k = 0; k < reps && e == cudaSuccess; ++k) {
+      e = cudaMemcpyAsync(qs, q, qb, cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess &&
+          crom_step(ctx, step, CROM_PREC_BF16X2, n_inst, qs, alpha, vel, s_off, samples, n_samples, max_samples,
+                    status, stream) != CROM_OK)
+        e = cudaErrorUnknown;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess) {
+      ctx->tune_ms[v] = ms / reps;
+      if (v == 0 || ms < best_ms) {
+        best_ms = ms;
+        best = variants[v];
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  ctx->tc_tile_s1 = e == cudaSuccess ? best : saved;
+  if (e != cudaSuccess) return cuda_fail(e, fn);
   return CROM_OK;
 }
 

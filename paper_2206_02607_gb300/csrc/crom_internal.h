@@ -60,6 +60,11 @@ struct crom_ctx {
   int* order = nullptr;
   size_t order_cap = 0;
   int* queue = nullptr;
+  // Sample-tile shape of the tensor-core step for GN iterations >= 1 (32 or 16),
+  // set by crom_set_step_tiles or measured by crom_autotune; the timings of the last
+  // crom_autotune per variant (ms, < 0 = not measured).
+  int tc_tile_s1 = 32;
+  float tune_ms[2] = {-1.f, -1.f};
   // Cached rollout graph and the arguments it was recorded with.
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t rollout_exec = nullptr;

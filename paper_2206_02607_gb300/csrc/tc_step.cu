@@ -59,7 +59,8 @@ constexpr int kTPU = 2;                  // threads per hidden unit (warps w and
 constexpr int kGT = 128 * kTPU;          // threads per group
 constexpr int kThreads = kGroups * kGT;
 constexpr int kS0 = 16;                  // samples per tile at GN iteration 0 (4 channels)
-constexpr int kS1 = 32;                  // samples per tile at later iterations (2 channels)
+// Samples per tile at later iterations (2 channels): 32 or 16, a template parameter
+// of the kernel chosen per context (crom_autotune measures both).
 constexpr int kSMax = 32;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kGroupCols = 256;     // TMEM columns per group
@@ -396,7 +397,8 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
     }
   }
   // ---------------- hidden layers 2..L (tensor cores): one N = 128 UMMA per K slice
-  constexpr uint32_t id_fwd = idesc_f16(128, 128, false, true, true);
+  // N spans the hi block (columns 0..63) and the used lo columns (64..64+kN-1)
+  constexpr uint32_t id_fwd = idesc_f16(128, 64 + kN, false, true, true);
   for (int l = 0; l < p.L - 1; ++l) {
     if (!stage<kStageFwd>(c, l, id_fwd)) return false;
     const float bias = S->bh[l][u];
@@ -554,7 +556,7 @@ __device__ __forceinline__ void set_layer1(const Lane& c, const Shared* S, Group
   }
 }
 
-template <int kM>
+template <int kM, int kS1>
 __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -833,16 +835,15 @@ cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst
   p.df = ctx->targets;
   const size_t smem = tc_step_smem_bytes(p.img_bytes);
   const int grid = std::min((n_inst + kGroups - 1) / kGroups, ctx->num_sms);
-  if (ctx->desc.m == 2) {
-    e = cudaFuncSetAttribute(step_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    step_tc_kernel<2><<<grid, kThreads, smem, s>>>(p);
-  } else {
-    e = cudaFuncSetAttribute(step_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    step_tc_kernel<1><<<grid, kThreads, smem, s>>>(p);
-  }
-  return cudaGetLastError();
+  auto launch = [&](auto kernel) -> cudaError_t {
+    cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    kernel<<<grid, kThreads, smem, s>>>(p);
+    return cudaGetLastError();
+  };
+  const bool small_tiles = ctx->tc_tile_s1 == 16;
+  if (ctx->desc.m == 2) return small_tiles ? launch(step_tc_kernel<2, 16>) : launch(step_tc_kernel<2, 32>);
+  return small_tiles ? launch(step_tc_kernel<1, 16>) : launch(step_tc_kernel<1, 32>);
 }
 
 }  // namespace crom
