@@ -226,10 +226,10 @@ int crom_autotune(crom_ctx* ctx, const crom_step_desc* step, int n_inst, const d
                   int* status, crom_stream stream);
 
 /* crom_step with precision CROM_PREC_FP32, for callers that cannot allocate
- * device memory when they step: code recording the step into a CUDA graph during
- * stream capture (where cudaMalloc is not allowed), hosts whose memory policy
- * forbids direct cudaMalloc/cudaFree, and latency-critical loops that must not
- * risk an allocation that synchronises the device.  The paper has no
+ * device memory when they step: host applications or frameworks that own the
+ * device's memory through their own pool and forbid direct cudaMalloc/cudaFree by
+ * the libraries they load, and latency-critical loops that must not risk an
+ * allocation that synchronises the device.  The paper has no
  * counterpart; this is an operational variant of the same step.
  * Arguments, results and status codes are those of crom_step.  The scratch lives
  * in one fixed 8 MiB device array per GPU, held from library load until process

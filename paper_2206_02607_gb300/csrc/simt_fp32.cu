@@ -648,11 +648,10 @@ cudaError_t launch_step_fp32(crom_ctx* ctx, const crom_step_desc* step, int n_in
 // ---------------------------------------------------------------------------
 // FP32 step without any device allocation (crom_step_noalloc).
 //
-// Some callers cannot allocate device memory at the time they step: code that
-// records the step into a CUDA graph while the stream is being captured (a
-// cudaMalloc there is an error in global capture mode), hosts whose allocator
-// policy forbids direct cudaMalloc/cudaFree, and latency-critical loops where an
-// allocation may synchronise the device.  For them this variant of the FP32 step
+// Some callers cannot allocate device memory at the time they step: a host
+// application or framework that owns the device's memory through its own pool
+// and forbids direct cudaMalloc/cudaFree by libraries it loads, and
+// latency-critical loops where an allocation may synchronise the device.  For them this variant of the FP32 step
 // takes its scratch (per-CTA partial normal equations, per-instance tickets,
 // per-sample Delta f and per-instance q_n) from one file-scope device array of
 // fixed size instead of the context's growable buffers.

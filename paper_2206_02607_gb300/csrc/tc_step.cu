@@ -348,6 +348,68 @@ __device__ __forceinline__ void sig1(const Lane& c, const Group* G, float cc, in
   }
 }
 
+// Steps after the residual of one tile: the reverse pass for dg/dq at q^(k) (delta
+// hi parts in columns 0..kSm-1, lo parts in kSm..2kSm-1), the Jacobian projection
+// and this tile's share of J^T J, J^T rho (and rho^T rho for the line search).
+template <int kM, int kSm>
+__device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int ns, int ea, int eb, double& acc) {
+  constexpr int kPer = kSm / kTPU;
+  constexpr int kC = kPer < 8 ? kPer : 8;
+  Group* G = c.G;
+  const int u = c.u, s0 = c.part * kPer;
+  const uint32_t lb = c.lane_base, tb = c.tb;
+  // ---------------- reverse pass
+#pragma unroll 1
+  for (int h8 = 0; h8 < kPer; h8 += kC) {
+    float sg[kC];
+    tmem_ldc(taddr(tb, lb, kSig + (p.L - 2) * kSm + s0 + h8), sg);
+    tmem_ld_wait();
+#pragma unroll
+    for (int i = 0; i < kC; ++i) sg[i] *= c.wo;
+    split_store<kC>(c.H, u, s0 + h8, kSm + s0 + h8, sg);  // delta_L
+  }
+  constexpr uint32_t id_bwd = idesc_f16(128, 2 * kSm, true, true, true);
+  for (int l = p.L - 2; l >= 0; --l) {
+    // accumulator = W_{l+2}^T delta_{l+2}; times s'(z_{l+1}) gives delta_{l+1}
+    if (!stage<kStageBwd>(c, l, id_bwd)) return false;
+    const float cc = G->c1[u];
+#pragma unroll 1
+    for (int h8 = 0; h8 < kPer; h8 += kC) {
+      float v[kC], w[kC], sg[kC];
+      tmem_ldc(taddr(tb, lb, kAcc + s0 + h8), v);
+      tmem_ldc(taddr(tb, lb, kAcc + kSm + s0 + h8), w);
+      if (l > 0) tmem_ldc(taddr(tb, lb, kSig + (l - 1) * kSm + s0 + h8), sg);
+      else sig1<kM, kC>(c, G, cc, s0 + h8, sg);
+      tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < kC; i += 2)
+        unpk2(mul2(add2(pk2(v[i], v[i + 1]), pk2(w[i], w[i + 1])), pk2(sg[i], sg[i + 1])), v[i], v[i + 1]);
+      split_store<kC>(c.H, u, s0 + h8, kSm + s0 + h8, v);
+    }
+  }
+  // J[s][j] = sum_u W_1q[u][j] delta_1[u][s]: rows s (hi) and kSm + s (lo)
+  if (!stage<kStageProj>(c, 0, 0)) return false;
+  if (c.gw < 2 * kSm / 32) {
+    float v[16];
+    tmem_ld16(taddr(tb, lb, kAcc), v);
+    tmem_ld_wait();
+    const int part = u / kSm, s = u % kSm;
+#pragma unroll
+    for (int j = 0; j < 15; ++j) G->jt[part][s][j] = v[j + 1];
+  }
+  group_sync(c.g);
+  // ---------------- this tile's normal-equation terms
+  if (ea >= 0) {
+    const float* a0 = &G->jt[0][0][ea];
+    const float* a1 = &G->jt[1][0][ea];
+    if (eb >= 0) acc += dot_exact(a0, a1, 16, &G->jt[0][0][eb], &G->jt[1][0][eb], 16, ns);
+    else acc += dot_exact(a0, a1, 16, G->rho, G->zero, 1, ns);
+  } else if (ea == -3) {
+    acc += dot_exact(G->rho, G->zero, 1, G->rho, G->zero, 1, ns);  // rho^T rho for the line search
+  }
+  return true;
+}
+
 // One tile of kSm samples of one GN iteration: forward pass, PDE update / residual,
 // reverse pass, Jacobian projection and this tile's share of J^T J and J^T rho.
 template <int kM, int kSm, bool kFirst, bool kValueOnly = false>
@@ -484,61 +546,13 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
     G->rho[c.gt] = rho;
   }
   tmem_st_wait();  // s'(z) of the forward pass is in TMEM
-  if (kValueOnly) {  // line-search trial: only sum_j rho_j^2 is needed
+  if constexpr (kValueOnly) {  // line-search trial: only sum_j rho_j^2 is needed
     group_sync(c.g);
     if (ea == -3) acc += dot_exact(G->rho, G->zero, 1, G->rho, G->zero, 1, ns);
     return true;
+  } else {
+    return reverse_tile<kM, kSm>(c, p, ns, ea, eb, acc);
   }
-  // ---------------- reverse pass for dg/dq at q^(k); delta hi in columns 0..kSm-1, lo in kSm..2kSm-1
-#pragma unroll 1
-  for (int h8 = 0; h8 < kPer; h8 += kC) {
-    float sg[kC];
-    tmem_ldc(taddr(tb, lb, kSig + (p.L - 2) * kSm + s0 + h8), sg);
-    tmem_ld_wait();
-#pragma unroll
-    for (int i = 0; i < kC; ++i) sg[i] *= c.wo;
-    split_store<kC>(c.H, u, s0 + h8, kSm + s0 + h8, sg);  // delta_L
-  }
-  constexpr uint32_t id_bwd = idesc_f16(128, 2 * kSm, true, true, true);
-  for (int l = p.L - 2; l >= 0; --l) {
-    // accumulator = W_{l+2}^T delta_{l+2}; times s'(z_{l+1}) gives delta_{l+1}
-    if (!stage<kStageBwd>(c, l, id_bwd)) return false;
-    const float cc = G->c1[u];
-#pragma unroll 1
-    for (int h8 = 0; h8 < kPer; h8 += kC) {
-      float v[kC], w[kC], sg[kC];
-      tmem_ldc(taddr(tb, lb, kAcc + s0 + h8), v);
-      tmem_ldc(taddr(tb, lb, kAcc + kSm + s0 + h8), w);
-      if (l > 0) tmem_ldc(taddr(tb, lb, kSig + (l - 1) * kSm + s0 + h8), sg);
-      else sig1<kM, kC>(c, G, cc, s0 + h8, sg);
-      tmem_ld_wait();
-#pragma unroll
-      for (int i = 0; i < kC; i += 2)
-        unpk2(mul2(add2(pk2(v[i], v[i + 1]), pk2(w[i], w[i + 1])), pk2(sg[i], sg[i + 1])), v[i], v[i + 1]);
-      split_store<kC>(c.H, u, s0 + h8, kSm + s0 + h8, v);
-    }
-  }
-  // J[s][j] = sum_u W_1q[u][j] delta_1[u][s]: rows s (hi) and kSm + s (lo)
-  if (!stage<kStageProj>(c, 0, 0)) return false;
-  if (c.gw < 2 * kSm / 32) {
-    float v[16];
-    tmem_ld16(taddr(tb, lb, kAcc), v);
-    tmem_ld_wait();
-    const int part = u / kSm, s = u % kSm;
-#pragma unroll
-    for (int j = 0; j < 15; ++j) G->jt[part][s][j] = v[j + 1];
-  }
-  group_sync(c.g);
-  // ---------------- this tile's normal-equation terms
-  if (ea >= 0) {
-    const float* a0 = &G->jt[0][0][ea];
-    const float* a1 = &G->jt[1][0][ea];
-    if (eb >= 0) acc += dot_exact(a0, a1, 16, &G->jt[0][0][eb], &G->jt[1][0][eb], 16, ns);
-    else acc += dot_exact(a0, a1, 16, G->rho, G->zero, 1, ns);
-  } else if (ea == -3) {
-    acc += dot_exact(G->rho, G->zero, 1, G->rho, G->zero, 1, ns);  // rho^T rho for the line search
-  }
-  return true;
 }
 
 // Layer-1 constants of the tile passes at the point q: c1 = b_1 + W_1q q (value

@@ -87,12 +87,22 @@ RES_TOL = 3e-3
 
 
 def _check_instance(w, i, q1_i, ref_i):
+    """Least-squares perturbation theory (Golub & Van Loan, Thm. 5.3.1) bounds the
+    J-space error of a projection solved with relative data errors eps by about
+    eps (2 + 3 kappa) and the increment error by about eps kappa (2 + kappa tan theta),
+    tan theta = ||Delta f - J d|| / ||J d||: the q and residual tolerances hold up to
+    kappa = 1e4 and grow linearly beyond (decoders with large r or 1D inputs reach
+    kappa ~ 1e5); the increment's is 1e-2 or that bound with eps = 1e-6 (the bf16
+    hi/lo operands carry 2^-17 relative error per element), whichever is larger."""
     Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
-    assert rel_l2(q1_i, ref_i) < 1e-5
     inc, res, kappa, margin = increment_errors(w.params, w.spec.m, w.q0[i], Y, q1_i, ref_i, w.dt, w.alpha[i])
-    assert res < RES_TOL, (i, res, kappa, margin)
-    if kappa < 1e3:
-        assert inc < 1e-2, (i, inc, kappa)
+    grow = max(1.0, kappa / 1e4)
+    assert rel_l2(q1_i, ref_i) < 1e-5 * grow, (i, rel_l2(q1_i, ref_i), kappa)
+    assert res < RES_TOL * grow, (i, res, kappa, margin)
+    ev = O.MLPDecoder(w.params, w.spec.m)(Y, w.q0[i])
+    jd = ev.gq @ (ref_i - w.q0[i])
+    tan_theta = np.linalg.norm(w.dt * np.asarray(w.alpha[i], np.float64) * ev.lap - jd) / np.linalg.norm(jd)
+    assert inc < max(1e-2, 1e-6 * kappa * (2 + kappa * tan_theta)), (i, inc, kappa, tan_theta)
 
 
 def _check_step(w, q1, st):
@@ -283,3 +293,62 @@ def test_autotune_measures_both_tile_shapes_and_leaves_q():
     assert np.array_equal(q.cpu().numpy(), w.q0)          # the trials ran on a copy
     q1, st = run_steps(ctx, subset(w, np.arange(12)), 1, c.CROM_PREC_BF16X2)
     _check_step(subset(w, np.arange(12)), q1, st)
+
+
+@pytest.mark.parametrize("m,r,hidden", [(2, 1, 2), (2, 15, 5), (2, 15, 2), (1, 8, 3), (1, 4, 5), (2, 4, 3),
+                                        (2, 12, 3), (2, 8, 4)])
+def test_step_tc_decoder_shapes(m, r, hidden):
+    """The tensor-core step over the shapes it accepts: r = 1 and the largest r = 15,
+    2 to 5 hidden layers, 1D and 2D inputs; uneven |M_i| around the tile sizes, the
+    smallest |M_i| = r for r = 15.  (A 1D decoder with r = 15 is left out: its
+    Jacobian at 15..16 points has kappa ~ 1e9, where whether the FP64 Cholesky
+    declares the system singular depends on the rounding of J itself.)"""
+    c = crom()
+    spec = gen.DecoderSpec(m, r, 128, hidden)
+    params = gen.xavier_decoder(spec, seed=10 * r + hidden, bias_std=0.1, bf16_exact=True)
+    rng = np.random.default_rng(r + 100 * hidden)
+    sizes = [max(r, 15), 16, 33, 64, 130]
+    if m == 1:
+        samples = np.concatenate([gen.interior_nodes_1d(256, s, rng) for s in sizes])
+    else:
+        samples = np.concatenate([gen.interior_nodes_2d(128, s, rng) for s in sizes])
+    w = gen.StepWorkload("shape", spec, params, rng.standard_normal((len(sizes), r)),
+                         rng.uniform(0.5, 2.0, len(sizes)).astype(np.float32), gen.ragged_offsets(sizes), samples,
+                         1e-5, 2, 1)
+    ctx = make_ctx(spec, params)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_BF16X2)
+    _check_step(w, q1, st)
+
+
+def test_step_tc_advection_diffusion_matches_oracle():
+    """Delta f_j = dt (-a(y_j) . grad g + nu Lap g) on the tensor-core path (the
+    gradient channels' outputs enter the residual), several instances."""
+    import torch
+    c = crom()
+    spec = gen.DecoderSpec(2, 8, 128, 5)
+    params = gen.xavier_decoder(spec, seed=13, bias_std=0.1, bf16_exact=True)
+    ctx = make_ctx(spec, params)
+    rng = np.random.default_rng(8)
+    sizes = [40, 90, 200]
+    Y = np.concatenate([gen.interior_nodes_2d(128, s, rng) for s in sizes])
+    vel = rng.standard_normal((Y.shape[0], 2)).astype(np.float32)
+    q0 = rng.standard_normal((3, 8))
+    nu = np.array([0.02, 0.005, 0.01], np.float32)
+    off = gen.ragged_offsets(sizes)
+    q = dev(q0, torch.float64)
+    st = torch.empty(3, dtype=torch.int32, device="cuda")
+    dt = 1e-4
+    c.crom_step(ctx, q, dev(nu, torch.float32), dev(off, torch.int32), dev(Y, torch.float32), st,
+                dt=dt, gn_iters=2, max_samples=200, pde=c.CROM_PDE_ADVDIFF, vel=dev(vel, torch.float32),
+                precision=c.CROM_PREC_BF16X2)
+    torch.cuda.synchronize()
+    q1 = q.cpu().numpy()
+    dec = O.MLPDecoder(params, 2)
+    for i in range(3):
+        sl = slice(off[i], off[i + 1])
+        ref, rst = O.crom_step(dec, q0[i], Y[sl], dt, 2, pde="advdiff", vel=vel[sl], nu=float(nu[i]))
+        assert st[i].item() == 0 and rst == 0
+        ev = dec(Y[sl], q0[i])
+        df = O.advdiff_delta_f(ev, vel[sl], float(nu[i]), dt)
+        res = np.linalg.norm(ev.gq @ (q1[i] - ref)) / np.linalg.norm(df)
+        assert rel_l2(q1[i], ref) < 1e-5 and res < RES_TOL, (i, res)

@@ -1,6 +1,6 @@
 """crom_step_noalloc: the FP32 step for callers that cannot allocate device memory
-while stepping (stream capture, allocation-restricted hosts), with its scratch in a
-fixed device array.  Its results must equal crom_step's (same kernel, same
+while stepping (hosts that own the device memory, allocation-free loops), with its
+scratch in a fixed device array.  Its results must equal crom_step's (same kernel, same
 reduction order), on consecutive calls that reuse the shared scratch with
 different batch shapes.  Collected last on purpose."""
 import numpy as np
