@@ -382,18 +382,23 @@ def main():
     dcodes = torch.tensor(codes, device="cuda")
     dX = torch.tensor(X, device="cuda")
     out = torch.empty((codes.shape[0], X.shape[0]), dtype=torch.float32, device="cuda")
-    crom.crom_reconstruct(ctxr, dcodes, dX, out, precision=crom.CROM_PREC_BF16X2)
-    torch.cuda.synchronize()
-    rt = []
-    for _ in range(3):
-        flush.fill_(1)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        crom.crom_reconstruct(ctxr, dcodes, dX, out, precision=crom.CROM_PREC_BF16X2)
-        e1.record(stream)
+
+    def time_recon(prec):
+        crom.crom_reconstruct(ctxr, dcodes, dX, out, precision=prec)
         torch.cuda.synchronize()
-        rt.append(e0.elapsed_time(e1))
-    recon_ms = float(np.median(rt))
+        rt = []
+        for _ in range(3):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            crom.crom_reconstruct(ctxr, dcodes, dX, out, precision=prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rt.append(e0.elapsed_time(e1))
+        return float(np.median(rt))
+
+    recon_ms_bf16 = time_recon(crom.CROM_PREC_BF16)
+    recon_ms = time_recon(crom.CROM_PREC_BF16X2)
     recon_pts = codes.shape[0] * X.shape[0]
     recon_flops = recon_pts * 2 * (2 * 128 + 4 * 128 * 128 + 128)
 
@@ -485,7 +490,10 @@ def main():
             "dense_reconstruction": {"points_per_s": recon_pts / (recon_ms * 1e-3), "ms": recon_ms,
                                      "tflops_algorithmic": recon_flops / (recon_ms * 1e-3) / 1e12,
                                      "frac_of_measured_bf16": recon_flops / (recon_ms * 1e-3) / 1e12 / peak_tf,
-                                     "workload": "1024^2 points x 64 codes, BF16X2"},
+                                     "workload": "1024^2 points x 64 codes, BF16X2",
+                                     "bf16_single_ms": recon_ms_bf16,
+                                     "bf16_single_frac_of_measured_bf16":
+                                         recon_flops / (recon_ms_bf16 * 1e-3) / 1e12 / peak_tf},
             "graph_rollout": {"value": w.n_inst / (roll_ms * 1e-3), "unit": "instance-steps/s",
                               "ms_per_step": roll_ms, "steps_per_graph": n_roll,
                               "note": "crom_rollout: 100 steps replayed from a cached CUDA graph, no L2 flush"},

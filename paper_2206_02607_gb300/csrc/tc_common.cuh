@@ -295,6 +295,22 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 __device__ __forceinline__ float bf16_lo_f(uint32_t v) { return __uint_as_float(v << 16); }
+// The low parts of a hi/lo split: hi = pack_bf16(x0, x1) holds the bf16 roundings of
+// x0 (low half) and x1; returns bf16(x0 - hi_0), bf16(x1 - hi_1) packed the same way.
+// Each difference is exact in FP32 and is formed by one mixed-precision FMA
+// (hi_k * -1 + x_k with bf16 factors and an FP32 addend, sm_100 and later).
+__device__ __forceinline__ uint32_t pack_bf16_lo(uint32_t hi, float x0, float x1) {
+  uint32_t lo;
+  asm("{\n\t.reg .b16 h0, h1, m1;\n\t.reg .f32 d0, d1;\n\t"
+      "mov.b32 {h0, h1}, %1;\n\t"
+      "mov.b16 m1, 0xBF80;\n\t"
+      "fma.rn.f32.bf16 d0, h0, m1, %2;\n\t"
+      "fma.rn.f32.bf16 d1, h1, m1, %3;\n\t"
+      "cvt.rn.bf16x2.f32 %0, d1, d0;\n\t}"
+      : "=r"(lo)
+      : "r"(hi), "f"(x0), "f"(x1));
+  return lo;
+}
 __device__ __forceinline__ float bf16_hi_f(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
 
 }  // namespace tc

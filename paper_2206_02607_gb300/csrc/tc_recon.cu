@@ -123,10 +123,7 @@ __device__ __forceinline__ void store_split16(uint8_t* Hhi, uint8_t* Hlo, int k,
     float a, b;
     unpk2(h[j], a, b);
     hi[j] = pack_bf16(a, b);
-    if (kSplit) {
-      unpk2(sub2(h[j], pk2(bf16_lo_f(hi[j]), bf16_hi_f(hi[j]))), a, b);
-      lo[j] = pack_bf16(a, b);
-    }
+    if (kSplit) lo[j] = pack_bf16_lo(hi[j], a, b);
   }
   *reinterpret_cast<uint4*>(Hhi + mn_offset(k, n0)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
   *reinterpret_cast<uint4*>(Hhi + mn_offset(k, n0 + 8)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);

@@ -9,8 +9,9 @@
 // threads (warps w and w + 4 of the group share a lane quadrant), each taking
 // half of the samples of a tile.
 //
-// Per instance, per Gauss-Newton iteration k, per tile of samples (16 at
-// iteration 0, 32 later; paper §4, Algorithm 3):
+// Per instance, per Gauss-Newton iteration k, per tile of samples (paper §4,
+// Algorithm 3; at iteration 0 forward tiles of 16 samples, taken in pairs by one
+// reverse pass over 32; later 32-sample tiles, or 16 as the autotuner picks):
 //
 //  Step 1 (network inference): a forward pass whose UMMA columns are
 //  (channel, sample) pairs, D[u][n] = sum_k W_l[u][k] H[k][n] (M = 128 units,
@@ -62,6 +63,7 @@ constexpr int kS0 = 16;                  // samples per tile at GN iteration 0 (
 // Samples per tile at later iterations (2 channels): 32 or 16, a template parameter
 // of the kernel chosen per context (crom_autotune measures both).
 constexpr int kSMax = 32;
+static_assert(2 * kS0 <= kSMax, "iteration 0 pairs two forward tiles in one reverse pass");
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kGroupCols = 256;     // TMEM columns per group
 // Accumulator in columns 0..127 (forward: W h_hi in 0..63, W h_lo in 64..127;
@@ -155,9 +157,7 @@ __device__ __forceinline__ void split_store(uint8_t* H, int k, int n_hi, int n_l
 #pragma unroll
   for (int j = 0; j < kC / 2; ++j) {
     hi[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
-    float a, b;
-    unpk2(sub2(pk2(v[2 * j], v[2 * j + 1]), pk2(bf16_lo_f(hi[j]), bf16_hi_f(hi[j]))), a, b);
-    lo[j] = pack_bf16(a, b);
+    lo[j] = pack_bf16_lo(hi[j], v[2 * j], v[2 * j + 1]);
   }
   if constexpr (kC == 8) {
     *reinterpret_cast<uint4*>(H + mn_offset(k, n_hi)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
@@ -348,10 +348,12 @@ __device__ __forceinline__ void sig1(const Lane& c, const Group* G, float cc, in
   }
 }
 
-// Steps after the residual of one tile: the reverse pass for dg/dq at q^(k) (delta
-// hi parts in columns 0..kSm-1, lo parts in kSm..2kSm-1), the Jacobian projection
-// and this tile's share of J^T J, J^T rho (and rho^T rho for the line search).
-template <int kM, int kSm>
+// Steps after the residual of kSm samples (the group's sample slots 0..kSm-1): the
+// reverse pass for dg/dq at q^(k) (delta hi parts in columns 0..kSm-1, lo parts in
+// kSm..2kSm-1), the Jacobian projection and these samples' share of J^T J, J^T rho
+// (and rho^T rho for the line search).  s'(z_l) of hidden layer l + 2 is read from
+// TMEM column kSig + l * kSS + slot.
+template <int kM, int kSm, int kSS>
 __device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int ns, int ea, int eb, double& acc) {
   constexpr int kPer = kSm / kTPU;
   constexpr int kC = kPer < 8 ? kPer : 8;
@@ -362,7 +364,7 @@ __device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int n
 #pragma unroll 1
   for (int h8 = 0; h8 < kPer; h8 += kC) {
     float sg[kC];
-    tmem_ldc(taddr(tb, lb, kSig + (p.L - 2) * kSm + s0 + h8), sg);
+    tmem_ldc(taddr(tb, lb, kSig + (p.L - 2) * kSS + s0 + h8), sg);
     tmem_ld_wait();
 #pragma unroll
     for (int i = 0; i < kC; ++i) sg[i] *= c.wo;
@@ -378,7 +380,7 @@ __device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int n
       float v[kC], w[kC], sg[kC];
       tmem_ldc(taddr(tb, lb, kAcc + s0 + h8), v);
       tmem_ldc(taddr(tb, lb, kAcc + kSm + s0 + h8), w);
-      if (l > 0) tmem_ldc(taddr(tb, lb, kSig + (l - 1) * kSm + s0 + h8), sg);
+      if (l > 0) tmem_ldc(taddr(tb, lb, kSig + (l - 1) * kSS + s0 + h8), sg);
       else sig1<kM, kC>(c, G, cc, s0 + h8, sg);
       tmem_ld_wait();
 #pragma unroll
@@ -410,23 +412,27 @@ __device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int n
   return true;
 }
 
-// One tile of kSm samples of one GN iteration: forward pass, PDE update / residual,
-// reverse pass, Jacobian projection and this tile's share of J^T J and J^T rho.
-template <int kM, int kSm, bool kFirst, bool kValueOnly = false>
-__device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, int t, int ns, float alpha, int ea,
-                                         int eb, double& acc) {
+// Forward pass of one tile of kSm samples (global sample indices j0 .. j0 + ns - 1,
+// ns >= 1; the tile's padding repeats its first sample), then Step 2 and the
+// residual rho_j.  The tile occupies the group's sample slots so .. so + kSm - 1
+// (coordinates xs, residual rho, and the TMEM columns kSig + l * kSS + slot that keep
+// s'(z) of hidden layer l + 2 for the reverse pass), so that two tiles of iteration
+// 0 can share one reverse pass.
+template <int kM, int kSm, bool kFirst, int kSS>
+__device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j0, int so, int ns, float alpha) {
   constexpr int kCh = kFirst ? 2 + kM : 2;  // iteration 0: v, dx_1..dx_m, Lap; later: v(q^(k)), diff
   constexpr int kN = kCh * kSm;             // hi columns 0..kN-1, lo columns 64..64+kN-1
   constexpr int kPer = kSm / kTPU;          // samples of this thread
   constexpr int kC = kPer < 8 ? kPer : 8;    // samples per chunk
-  static_assert(kN <= 64 && kPer % kC == 0 && kC % 4 == 0 && kSig + 4 * kSm <= kGroupCols, "tile shape");
+  static_assert(kN <= 64 && kPer % kC == 0 && kC % 4 == 0 && kSS >= kSm && kSig + 4 * kSS <= kGroupCols,
+                "tile shape");
   Group* G = c.G;
   const Shared* S = c.S;
   const int u = c.u, s0 = c.part * kPer;
   const uint32_t lb = c.lane_base, tb = c.tb;
   if (c.gt < kSm) {
     const int s = c.gt < ns ? c.gt : 0;
-    for (int k = 0; k < kM; ++k) G->xs[k][c.gt] = p.x[(size_t)(o0 + t * kSm + s) * kM + k];
+    for (int k = 0; k < kM; ++k) G->xs[k][so + c.gt] = p.x[(size_t)(j0 + s) * kM + k];
   }
   group_sync(c.g);
   // ---------------- layer 1 (CUDA cores)
@@ -439,8 +445,8 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
       float v[kCh][kC], sg[kC];
 #pragma unroll
       for (int i = 0; i < kC; ++i) {
-        float z = fmaf(c.wx0, G->xs[0][s0 + h8 + i], cc);
-        if (kM > 1) z = fmaf(c.wx1, G->xs[1][s0 + h8 + i], z);
+        float z = fmaf(c.wx0, G->xs[0][so + s0 + h8 + i], cc);
+        if (kM > 1) z = fmaf(c.wx1, G->xs[1][so + s0 + h8 + i], z);
         v[0][i] = z;
         if (kFirst) {
           v[1][i] = c.wx0;
@@ -481,7 +487,7 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
 #pragma unroll
       for (int i = 0; i < kC; i += 2) unpk2(add2(pk2(v[0][i], v[0][i + 1]), pk2(bias, bias)), v[0][i], v[0][i + 1]);
       act<kM, kFirst, kCh, kC>(v, sg);
-      tmem_stc(taddr(tb, lb, kSig + l * kSm + s0 + h8), sg);
+      tmem_stc(taddr(tb, lb, kSig + l * kSS + so + s0 + h8), sg);
       if (l < p.L - 2) {
 #pragma unroll
         for (int ch = 0; ch < kCh; ++ch) {
@@ -525,7 +531,7 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
   if (c.gt < kSm) {
     float rho = 0.f;
     if (c.gt < ns) {
-      const int j = o0 + t * kSm + c.gt;
+      const int j = j0 + c.gt;
       if (kFirst) {
         const float lap = gout(kCh - 1, c.gt);
         if (p.coef_per_sample) alpha = p.alpha[j];
@@ -543,16 +549,42 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
         rho = (float)((double)gout(1, c.gt) - p.df[j]);
       }
     }
-    G->rho[c.gt] = rho;
+    G->rho[so + c.gt] = rho;
   }
   tmem_st_wait();  // s'(z) of the forward pass is in TMEM
+  return true;
+}
+
+// One tile of kSm samples of one GN iteration k >= 1: forward pass, PDE update /
+// residual, reverse pass, Jacobian projection and this tile's share of J^T J and
+// J^T rho; or, for a line-search trial (kValueOnly), the forward pass and rho^T rho.
+template <int kM, int kSm, bool kValueOnly = false>
+__device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, int t, int ns, float alpha, int ea,
+                                         int eb, double& acc) {
+  if (!forward_tile<kM, kSm, false, kSm>(c, p, o0 + t * kSm, 0, ns, alpha)) return false;
   if constexpr (kValueOnly) {  // line-search trial: only sum_j rho_j^2 is needed
     group_sync(c.g);
-    if (ea == -3) acc += dot_exact(G->rho, G->zero, 1, G->rho, G->zero, 1, ns);
+    if (ea == -3) acc += dot_exact(c.G->rho, c.G->zero, 1, c.G->rho, c.G->zero, 1, ns);
     return true;
   } else {
-    return reverse_tile<kM, kSm>(c, p, ns, ea, eb, acc);
+    return reverse_tile<kM, kSm, kSm>(c, p, ns, ea, eb, acc);
   }
+}
+
+// Samples 2 kS0 * t .. of GN iteration 0 (ns >= 1 of them, at most 2 kS0): two
+// forward tiles of kS0 samples (the second only if ns > kS0) into sample slots
+// 0..kS0-1 and kS0..2kS0-1, then one reverse pass and projection over all of them:
+// the four-channel forward pass needs narrow tiles to fit one N = 128 UMMA, the
+// reverse pass does not.
+template <int kM>
+__device__ __forceinline__ bool run_pair(Lane& c, const StepParams& p, int o0, int t, int ns, float alpha, int ea,
+                                         int eb, double& acc) {
+  constexpr int kSS = 2 * kS0;
+  const int j0 = o0 + t * kSS;
+  if (!forward_tile<kM, kS0, true, kSS>(c, p, j0, 0, min(ns, kS0), alpha)) return false;
+  if (ns <= kS0) return reverse_tile<kM, kS0, kSS>(c, p, ns, ea, eb, acc);
+  if (!forward_tile<kM, kS0, true, kSS>(c, p, j0 + kS0, kS0, ns - kS0, alpha)) return false;
+  return reverse_tile<kM, kSS, kSS>(c, p, ns, ea, eb, acc);
 }
 
 // Layer-1 constants of the tile passes at the point q: c1 = b_1 + W_1q q (value
@@ -673,13 +705,13 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
       set_layer1(c, S, G, G->qcur, r, p.b1);
       double acc = 0.0;
       if (it == 0) {
-        const int nt = (M + kS0 - 1) / kS0;
+        const int nt = (M + 2 * kS0 - 1) / (2 * kS0);
         for (int t = 0; t < nt && ok; ++t)
-          ok = run_tile<kM, kS0, true>(c, p, o0, t, min(kS0, M - t * kS0), alpha, ea, eb, acc);
+          ok = run_pair<kM>(c, p, o0, t, min(2 * kS0, M - t * 2 * kS0), alpha, ea, eb, acc);
       } else {
         const int nt = (M + kS1 - 1) / kS1;
         for (int t = 0; t < nt && ok; ++t)
-          ok = run_tile<kM, kS1, false>(c, p, o0, t, min(kS1, M - t * kS1), alpha, ea, eb, acc);
+          ok = run_tile<kM, kS1>(c, p, o0, t, min(kS1, M - t * kS1), alpha, ea, eb, acc);
       }
       if (!ok) break;
       const int R = r + 1;
@@ -723,7 +755,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
           double acc_phi = 0.0;
           const int nt = (M + kS1 - 1) / kS1;
           for (int t = 0; t < nt && ok; ++t)
-            ok = run_tile<kM, kS1, false, true>(c, p, o0, t, min(kS1, M - t * kS1), alpha, ea, eb, acc_phi);
+            ok = run_tile<kM, kS1, true>(c, p, o0, t, min(kS1, M - t * kS1), alpha, ea, eb, acc_phi);
           if (!ok) break;
           if (ea == -3) G->phi = 0.5 * acc_phi;
           group_sync(c.g);
