@@ -25,8 +25,10 @@ __device__ __forceinline__ int chol_solve_warp(double* A, double* invd, int r, i
   for (int j = 0; j < r; ++j) {
     const double d = A[j * R + j];
     if (!(d > tol)) return CROM_ERR_SINGULAR;
-    const double ljj = sqrt(d);
-    const double inv = 1.0 / ljj;
+    // one reciprocal square root instead of a square root and a division: FP64 is
+    // a slow pipe on this GPU, and each of these is a sequence of FP64 instructions
+    const double inv = rsqrt(d);
+    const double ljj = d * inv;
     __syncwarp();
     if (lane == 0) {
       A[j * R + j] = ljj;

@@ -293,23 +293,41 @@ __device__ __forceinline__ bool stage(Lane& c, int layer, uint32_t idesc) {
   return done;
 }
 
+// s + p = t + err exactly (Knuth's two-sum); t replaces s, err is added to comp.
+__device__ __forceinline__ void two_sum_into(float& s, float& comp, float p) {
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  comp += __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+}
+
 // Exact product-sum of up to kSMax FP32 pairs: two-product (a*b = p + e exactly by
 // one FMA) and a compensated (two-sum) accumulation of the p, in FP32; returned in
 // FP64.  Relative error ~2^-46, well below the FP32 inputs' own rounding.  Each
-// factor is the FP32 sum of two parts (a0 + a1, b0 + b1).
+// factor is the FP32 sum of two parts (a0 + a1, b0 + b1).  Four interleaved
+// accumulators (element i goes to i mod 4) shorten the dependent chain; they are
+// merged by two-sums in a fixed order.
 __device__ __forceinline__ double dot_exact(const float* a0, const float* a1, int sa, const float* b0,
                                             const float* b1, int sb, int n) {
-  float s = 0.f, comp = 0.f;
-  for (int i = 0; i < n; ++i) {
-    const float x = __fadd_rn(a0[i * sa], a1[i * sa]), y = __fadd_rn(b0[i * sb], b1[i * sb]);
-    const float p = __fmul_rn(x, y);  // rounded product (kept out of FMA contraction)
-    const float e = fmaf(x, y, -p);   // its exact rounding error
-    const float t = __fadd_rn(s, p);
-    const float bp = __fsub_rn(t, s);
-    comp += __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp)) + e;
-    s = t;
+  float s[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int i0 = 0; i0 < n; i0 += 4) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = i0 + k;
+      if (i < n) {
+        const float x = __fadd_rn(a0[i * sa], a1[i * sa]), y = __fadd_rn(b0[i * sb], b1[i * sb]);
+        const float p = __fmul_rn(x, y);  // rounded product (kept out of FMA contraction)
+        const float e = fmaf(x, y, -p);   // its exact rounding error
+        two_sum_into(s[k], comp[k], p);
+        comp[k] += e;
+      }
+    }
   }
-  return (double)s + (double)comp;
+  two_sum_into(s[0], comp[0], s[1]);
+  two_sum_into(s[2], comp[2], s[3]);
+  two_sum_into(s[0], comp[0], s[2]);
+  comp[0] += comp[1] + (comp[2] + comp[3]);
+  return (double)s[0] + (double)comp[0];
 }
 
 // Sum over the 32 lanes of a warp (32 hidden units) of 8 per-lane values v[s]: three
@@ -430,9 +448,15 @@ __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j
   const Shared* S = c.S;
   const int u = c.u, s0 = c.part * kPer;
   const uint32_t lb = c.lane_base, tb = c.tb;
+  // Step 2's per-sample inputs are loaded here, so that their latency overlaps the
+  // forward pass: Delta f_j of iteration 0 (later iterations), alpha_j (per-sample
+  // coefficient)
+  double df_j = 0.0;
   if (c.gt < kSm) {
     const int s = c.gt < ns ? c.gt : 0;
     for (int k = 0; k < kM; ++k) G->xs[k][so + c.gt] = p.x[(size_t)(j0 + s) * kM + k];
+    if (!kFirst) df_j = p.df[j0 + s];
+    else if (p.coef_per_sample) alpha = p.alpha[j0 + s];
   }
   group_sync(c.g);
   // ---------------- layer 1 (CUDA cores)
@@ -534,7 +558,6 @@ __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j
       const int j = j0 + c.gt;
       if (kFirst) {
         const float lap = gout(kCh - 1, c.gt);
-        if (p.coef_per_sample) alpha = p.alpha[j];
         double df;
         if (p.pde == CROM_PDE_HEAT) {
           df = p.dt * (double)alpha * (double)lap;
@@ -546,7 +569,7 @@ __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j
         p.df[j] = df;
         rho = (float)(-df);
       } else {
-        rho = (float)((double)gout(1, c.gt) - p.df[j]);
+        rho = (float)((double)gout(1, c.gt) - df_j);
       }
     }
     G->rho[so + c.gt] = rho;
@@ -588,16 +611,17 @@ __device__ __forceinline__ bool run_pair(Lane& c, const StepParams& p, int o0, i
 }
 
 // Layer-1 constants of the tile passes at the point q: c1 = b_1 + W_1q q (value
-// channel) and dz1 = W_1q (q - q_n) (difference channel), FP64 sums rounded once.
+// channel, by the unit's first thread) and dz1 = W_1q (q - q_n) (difference channel,
+// by its second), FP64 sums rounded once.
 __device__ __forceinline__ void set_layer1(const Lane& c, const Shared* S, Group* G, const double* q, int r,
                                            const float* b1) {
   if (c.part == 0) {
-    double cc = (double)b1[c.u], dz = 0.0;
-    for (int j = 0; j < r; ++j) {
-      cc += (double)S->w1q[j][c.u] * q[j];
-      dz += (double)S->w1q[j][c.u] * (q[j] - G->qn[j]);
-    }
+    double cc = (double)b1[c.u];
+    for (int j = 0; j < r; ++j) cc = fma((double)S->w1q[j][c.u], q[j], cc);
     G->c1[c.u] = (float)cc;
+  } else {
+    double dz = 0.0;
+    for (int j = 0; j < r; ++j) dz = fma((double)S->w1q[j][c.u], q[j] - G->qn[j], dz);
     G->dz1[c.u] = (float)dz;
   }
 }
