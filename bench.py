@@ -481,7 +481,7 @@ def main():
                        "parallelism": f"instances sharded, {w.n_inst} per GPU" if world > 1 else "single GPU",
                        "l2": "flushed (256 MB write) before every timed step",
                        "tiles": {"s0": tile_s0, "s1": tile_s1, "autotuned": True,
-                                 "ms_per_step_s1_32_16": [round(tile_ms[0], 4), round(tile_ms[1], 4)]}},
+                                 "ms_per_step_large_small_s1": [round(tile_ms[0], 4), round(tile_ms[1], 4)]}},
             "status_all_ok": bool(np.all(st == 0)),
             "accuracy_vs_fp64_oracle": acc,
             "plain_fp32_single": {"value": plain_value, "unit": "instance-steps/s", "us_per_step": plain_ms * 1e3,

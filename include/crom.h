@@ -206,12 +206,13 @@ int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n
                  int max_samples, int* status, crom_stream stream);
 
 /* Sample-tile shape of the tensor-core step (CROM_PREC_BF16X2): s0 samples per
- * tile in the first Gauss-Newton iteration (4 channels: 16, fixed by the 64
- * operand columns of a tile), s1 in later ones (2 channels: 32 or 16).  Larger
- * tiles issue half as many UMMA stages; smaller ones waste less on the ragged last
- * tile of each instance.  crom_set_step_tiles fixes the shape; crom_get_step_tiles
- * reads it and, into ms[2] (may be NULL), the per-step times that the last
- * crom_autotune measured for s1 = 32 and 16 (-1 when not measured). */
+ * forward tile in the first Gauss-Newton iteration (4 channels: 8, fixed by the
+ * 32 hi-part operand columns of a tile; two such tiles share one reverse pass),
+ * s1 in later ones (2 channels: 16 or 8).  Larger tiles issue half as many UMMA
+ * stages; smaller ones waste less on the ragged last tile of each instance.
+ * crom_set_step_tiles fixes the shape (default (8, 16)); crom_get_step_tiles reads
+ * it and, into ms[2] (may be NULL), the per-step times that the last crom_autotune
+ * measured for s1 = 16 and 8 (-1 when not measured). */
 int crom_set_step_tiles(crom_ctx* ctx, int s0, int s1);
 int crom_get_step_tiles(const crom_ctx* ctx, int* s0, int* s1, float* ms);
 

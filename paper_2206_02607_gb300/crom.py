@@ -319,7 +319,7 @@ def crom_set_step_tiles(ctx: CromContext, s0: int, s1: int):
 
 
 def crom_get_step_tiles(ctx: CromContext):
-    """(s0, s1, [ms for s1 = 32, ms for s1 = 16]) of the context's tensor-core step."""
+    """(s0, s1, [ms for the large s1, ms for the small s1]) of the context's tensor-core step."""
     a, b = ctypes.c_int(), ctypes.c_int()
     ms = (ctypes.c_float * 2)()
     _check(_LIB.crom_get_step_tiles(ctx.handle, ctypes.byref(a), ctypes.byref(b), ms))

@@ -418,15 +418,17 @@ int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n
 
 int crom_set_step_tiles(crom_ctx* ctx, int s0, int s1) {
   if (!ctx) return fail(CROM_ERR_INVALID_ARG, "crom_set_step_tiles: null context");
-  if (s0 != 16 || (s1 != 16 && s1 != 32))
-    return fail(CROM_ERR_UNSUPPORTED, "crom_set_step_tiles: tiles (16, 32) or (16, 16)");
+  if (s0 != crom::kTcTileS0 || (s1 != crom::kTcTileS1Large && s1 != crom::kTcTileS1Small))
+    return fail(CROM_ERR_UNSUPPORTED, "crom_set_step_tiles: tiles (" + std::to_string(crom::kTcTileS0) + ", " +
+                                          std::to_string(crom::kTcTileS1Large) + ") or (" + std::to_string(crom::kTcTileS0) +
+                                          ", " + std::to_string(crom::kTcTileS1Small) + ")");
   ctx->tc_tile_s1 = s1;
   return CROM_OK;
 }
 
 int crom_get_step_tiles(const crom_ctx* ctx, int* s0, int* s1, float* ms) {
   if (!ctx || !s0 || !s1) return fail(CROM_ERR_INVALID_ARG, "crom_get_step_tiles: null argument");
-  *s0 = 16;
+  *s0 = crom::kTcTileS0;
   *s1 = ctx->tc_tile_s1;
   if (ms) {
     ms[0] = ctx->tune_ms[0];
@@ -452,7 +454,7 @@ int crom_autotune(crom_ctx* ctx, const crom_step_desc* step, int n_inst, const d
   cudaError_t e = buf.err;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  const int variants[2] = {32, 16};
+  const int variants[2] = {crom::kTcTileS1Large, crom::kTcTileS1Small};
   const int saved = ctx->tc_tile_s1;
   float best_ms = 0.f;
   int best = saved;

@@ -20,6 +20,12 @@ namespace crom {
 //                          row 0 = w_out, rows 1..r = W_1[:, m+j] (dg/dq projection)
 constexpr int kTcWidth = 128;
 constexpr int kTcLayerBytes = kTcWidth * kTcWidth * 2;
+// Sample tiles of the tensor-core step: kTcTileS0 samples per forward tile at GN
+// iteration 0 (two of them share one reverse pass); kTcTileS1Large or
+// kTcTileS1Small samples per tile at later iterations.
+constexpr int kTcTileS0 = 8;
+constexpr int kTcTileS1Large = 16;
+constexpr int kTcTileS1Small = 8;
 constexpr int kTcProjRows = 16;
 constexpr int kTcProjBytes = kTcProjRows * kTcWidth * 2;
 
@@ -60,10 +66,11 @@ struct crom_ctx {
   int* order = nullptr;
   size_t order_cap = 0;
   int* queue = nullptr;
-  // Sample-tile shape of the tensor-core step for GN iterations >= 1 (32 or 16),
-  // set by crom_set_step_tiles or measured by crom_autotune; the timings of the last
-  // crom_autotune per variant (ms, < 0 = not measured).
-  int tc_tile_s1 = 32;
+  // Sample-tile shape of the tensor-core step for GN iterations >= 1
+  // (kTcTileS1Large or kTcTileS1Small), set by crom_set_step_tiles or measured by
+  // crom_autotune; the timings of the last crom_autotune per variant (ms, < 0 = not
+  // measured).
+  int tc_tile_s1 = crom::kTcTileS1Large;
   float tune_ms[2] = {-1.f, -1.f};
   // Cached rollout graph and the arguments it was recorded with.
   cudaStream_t cap_stream = nullptr;

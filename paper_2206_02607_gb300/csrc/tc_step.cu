@@ -1,22 +1,21 @@
 // Batched latent step on the tcgen05 tensor cores (crom_step, CROM_PREC_BF16X2).
 //
 // One persistent launch per step, one CTA per SM holding the decoder's bf16
-// hidden matrices in shared memory.  The CTA runs two independent groups of 256
+// hidden matrices in shared memory.  The CTA runs four independent groups of 128
 // threads; each group takes whole instances from a queue ordered by |M_i|
-// (largest first) and has its own operand buffers, TMEM columns, mbarrier and
-// named barrier, so the UMMAs of one group overlap the CUDA-core epilogue of the
-// other.  Inside a group, hidden unit u is TMEM lane u and is served by two
-// threads (warps w and w + 4 of the group share a lane quadrant), each taking
-// half of the samples of a tile.
+// (largest first) and has its own 64-column operand block, 128 TMEM columns,
+// mbarrier and named barrier, so the UMMAs of one group overlap the CUDA-core
+// epilogues of the others.  Inside a group, hidden unit u is TMEM lane u and
+// thread u of the group.
 //
 // Per instance, per Gauss-Newton iteration k, per tile of samples (paper §4,
-// Algorithm 3; at iteration 0 forward tiles of 16 samples, taken in pairs by one
-// reverse pass over 32; later 32-sample tiles, or 16 as the autotuner picks):
+// Algorithm 3; at iteration 0 forward tiles of 8 samples, taken in pairs by one
+// reverse pass over 16; later 16-sample tiles, or 8 as the autotuner picks):
 //
 //  Step 1 (network inference): a forward pass whose UMMA columns are
 //  (channel, sample) pairs, D[u][n] = sum_k W_l[u][k] H[k][n] (M = 128 units,
-//  K = 128, 64 columns of bf16 hi parts followed by 64 columns of lo parts, one
-//  N = 128 UMMA per K slice).  Iteration 0 carries the value, dg/dx_k and a single
+//  K = 128, 32 columns of bf16 hi parts followed by 32 columns of lo parts, one
+//  N = 64 UMMA per K slice).  Iteration 0 carries the value, dg/dx_k and a single
 //  Laplacian channel (d2z = W d2h with d2h = s''(z) sum_k (dz/dx_k)^2 + s'(z) d2z,
 //  the m diagonal second-derivative channels of Algorithm 2 summed); iteration
 //  k >= 1 carries the value at q^(k) and the difference channel
@@ -41,7 +40,8 @@
 // sums).  The projection J = W_1q^T delta_1 is a UMMA against the 16-row bf16
 // matrix P (rows 1..r = W_1q columns) that reads the activation buffer as the
 // M = 128 operand, delta's hi parts in rows 0..kS-1 and lo parts in rows
-// kS..2kS-1; the epilogue adds the two rows.
+// kS..2kS-1 (rows from 64 on read the next 16 KB of shared memory and are not
+// used); the epilogue adds the two rows.
 #include <math.h>
 
 #include <algorithm>
@@ -55,25 +55,29 @@ namespace {
 
 using namespace tc;
 
-constexpr int kGroups = 2;
-constexpr int kTPU = 2;                  // threads per hidden unit (warps w and w+4 share a lane quadrant)
+constexpr int kGroups = 4;
+constexpr int kTPU = 1;                  // threads per hidden unit
 constexpr int kGT = 128 * kTPU;          // threads per group
 constexpr int kThreads = kGroups * kGT;
-constexpr int kS0 = 16;                  // samples per tile at GN iteration 0 (4 channels)
-// Samples per tile at later iterations (2 channels): 32 or 16, a template parameter
-// of the kernel chosen per context (crom_autotune measures both).
-constexpr int kSMax = 32;
-static_assert(2 * kS0 <= kSMax, "iteration 0 pairs two forward tiles in one reverse pass");
+constexpr int kS0 = kTcTileS0;           // samples per forward tile at GN iteration 0 (4 channels)
+// Samples per tile at later iterations (2 channels): kTcTileS1Large or
+// kTcTileS1Small, a template parameter of the kernel chosen per context
+// (crom_autotune measures both).
+constexpr int kSMax = 2 * kTcTileS0;
+static_assert(kTcTileS1Large <= kSMax && 2 * kS0 <= kSMax, "sample slots");
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kGroupCols = 256;     // TMEM columns per group
-// Accumulator in columns 0..127 (forward: W h_hi in 0..63, W h_lo in 64..127;
+constexpr uint32_t kGroupCols = 128;     // TMEM columns per group
+// Accumulator in columns 0..63 (forward: W h_hi in 0..31, W h_lo in 32..63;
 // reverse: hi part in 0..kS-1, lo part in kS..2kS-1; projections: 16 columns);
-// s'(z_l) of hidden layers l = 2..L (<= 5), kS columns each, from column 128.
+// s'(z_l) of hidden layers l = 2..L (<= 5), kS columns each, from column 64.
 constexpr uint32_t kAcc = 0;
-constexpr uint32_t kSig = 128;
+constexpr uint32_t kSig = 64;
+// Forward operand block of a group: 64 columns, the bf16 hi parts of the (channel,
+// sample) pairs in columns 0..kLo-1 and their lo parts in kLo..2 kLo-1.
+constexpr int kLo = 32;
 constexpr uint32_t kWaitLimit = 1u << 25;
 constexpr double kArmijoC1 = 1e-4;      // sufficient-decrease constant of the line search
-constexpr size_t kHBuf = (size_t)kTcWidth * 64 * 2;  // one 64-column bf16 MN-major block, 16 KB
+constexpr size_t kHBuf = (size_t)kTcWidth * 64 * 2;  // one 64-column bf16 MN-major block (16 KB) per group
 
 struct StepParams {
   const uint8_t* img;
@@ -108,7 +112,6 @@ struct __align__(16) Shared {
   uint32_t tmem_base;
   int pad;
   float w1x[2][kTcWidth];
-  float w1q[16][kTcWidth];
   float bh[4][kTcWidth];
   float wout[kTcWidth];
 };
@@ -266,6 +269,14 @@ struct Lane {
   uint32_t phase;
 };
 
+// Normal-equation entries owned by a thread (up to two: r = 15 has 135 of them and
+// a group 128 threads): (ea, eb) of J^T J, (ea, -2) of J^T rho, ea = -3 for rho^T rho
+// (the line search's objective), ea = -1 for none; acc holds the running sums.
+struct Own {
+  int ea[2], eb[2];
+  double acc[2];
+};
+
 // One UMMA stage of the group: fence the epilogue's shared-memory writes, meet,
 // the first warp issues and commits (one elected lane) and waits on the mbarrier,
 // the rest wait at the group barrier.  Returns the group-uniform completion flag.
@@ -372,7 +383,7 @@ __device__ __forceinline__ void sig1(const Lane& c, const Group* G, float cc, in
 // (and rho^T rho for the line search).  s'(z_l) of hidden layer l + 2 is read from
 // TMEM column kSig + l * kSS + slot.
 template <int kM, int kSm, int kSS>
-__device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int ns, int ea, int eb, double& acc) {
+__device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int ns, Own& o) {
   constexpr int kPer = kSm / kTPU;
   constexpr int kC = kPer < 8 ? kPer : 8;
   Group* G = c.G;
@@ -409,23 +420,29 @@ __device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int n
   }
   // J[s][j] = sum_u W_1q[u][j] delta_1[u][s]: rows s (hi) and kSm + s (lo)
   if (!stage<kStageProj>(c, 0, 0)) return false;
-  if (c.gw < 2 * kSm / 32) {
+  if (c.gw < (2 * kSm + 31) / 32) {
     float v[16];
     tmem_ld16(taddr(tb, lb, kAcc), v);
     tmem_ld_wait();
     const int part = u / kSm, s = u % kSm;
+    if (u < 2 * kSm) {
 #pragma unroll
-    for (int j = 0; j < 15; ++j) G->jt[part][s][j] = v[j + 1];
+      for (int j = 0; j < 15; ++j) G->jt[part][s][j] = v[j + 1];
+    }
   }
   group_sync(c.g);
   // ---------------- this tile's normal-equation terms
-  if (ea >= 0) {
-    const float* a0 = &G->jt[0][0][ea];
-    const float* a1 = &G->jt[1][0][ea];
-    if (eb >= 0) acc += dot_exact(a0, a1, 16, &G->jt[0][0][eb], &G->jt[1][0][eb], 16, ns);
-    else acc += dot_exact(a0, a1, 16, G->rho, G->zero, 1, ns);
-  } else if (ea == -3) {
-    acc += dot_exact(G->rho, G->zero, 1, G->rho, G->zero, 1, ns);  // rho^T rho for the line search
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int ea = o.ea[e], eb = o.eb[e];
+    if (ea >= 0) {
+      const float* a0 = &G->jt[0][0][ea];
+      const float* a1 = &G->jt[1][0][ea];
+      if (eb >= 0) o.acc[e] += dot_exact(a0, a1, 16, &G->jt[0][0][eb], &G->jt[1][0][eb], 16, ns);
+      else o.acc[e] += dot_exact(a0, a1, 16, G->rho, G->zero, 1, ns);
+    } else if (ea == -3) {
+      o.acc[e] += dot_exact(G->rho, G->zero, 1, G->rho, G->zero, 1, ns);  // rho^T rho for the line search
+    }
   }
   return true;
 }
@@ -439,10 +456,10 @@ __device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int n
 template <int kM, int kSm, bool kFirst, int kSS>
 __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j0, int so, int ns, float alpha) {
   constexpr int kCh = kFirst ? 2 + kM : 2;  // iteration 0: v, dx_1..dx_m, Lap; later: v(q^(k)), diff
-  constexpr int kN = kCh * kSm;             // hi columns 0..kN-1, lo columns 64..64+kN-1
+  constexpr int kN = kCh * kSm;             // hi columns 0..kN-1, lo columns kLo..kLo+kN-1
   constexpr int kPer = kSm / kTPU;          // samples of this thread
   constexpr int kC = kPer < 8 ? kPer : 8;    // samples per chunk
-  static_assert(kN <= 64 && kPer % kC == 0 && kC % 4 == 0 && kSS >= kSm && kSig + 4 * kSS <= kGroupCols,
+  static_assert(kN <= kLo && kPer % kC == 0 && kC % 4 == 0 && kSS >= kSm && kSig + 4 * kSS <= kGroupCols,
                 "tile shape");
   Group* G = c.G;
   const Shared* S = c.S;
@@ -484,13 +501,14 @@ __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) {
         const int n = ch * kSm + s0 + h8;
-        split_store<kC>(c.H, u, n, 64 + n, v[ch]);
+        split_store<kC>(c.H, u, n, kLo + n, v[ch]);
       }
     }
   }
-  // ---------------- hidden layers 2..L (tensor cores): one N = 128 UMMA per K slice
-  // N spans the hi block (columns 0..63) and the used lo columns (64..64+kN-1)
-  constexpr uint32_t id_fwd = idesc_f16(128, 64 + kN, false, true, true);
+  // ---------------- hidden layers 2..L (tensor cores): one UMMA per K slice whose N
+  // spans the hi columns (0..kLo-1) and the used lo columns (kLo..kLo+kN-1), rounded
+  // up to a multiple of 16
+  constexpr uint32_t id_fwd = idesc_f16(128, kLo + ((kN + 15) & ~15), false, true, true);
   for (int l = 0; l < p.L - 1; ++l) {
     if (!stage<kStageFwd>(c, l, id_fwd)) return false;
     const float bias = S->bh[l][u];
@@ -500,7 +518,7 @@ __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) {
         tmem_ldc(taddr(tb, lb, kAcc + ch * kSm + s0 + h8), v[ch]);
-        tmem_ldc(taddr(tb, lb, kAcc + 64 + ch * kSm + s0 + h8), w[ch]);
+        tmem_ldc(taddr(tb, lb, kAcc + kLo + ch * kSm + s0 + h8), w[ch]);
       }
       tmem_ld_wait();
 #pragma unroll
@@ -516,7 +534,7 @@ __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j
 #pragma unroll
         for (int ch = 0; ch < kCh; ++ch) {
           const int n = ch * kSm + s0 + h8;
-          split_store<kC>(c.H, u, n, 64 + n, v[ch]);
+          split_store<kC>(c.H, u, n, kLo + n, v[ch]);
         }
       } else {
         // output layer on the CUDA cores, in FP32 from h_L itself: this warp's share
@@ -582,15 +600,16 @@ __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j
 // residual, reverse pass, Jacobian projection and this tile's share of J^T J and
 // J^T rho; or, for a line-search trial (kValueOnly), the forward pass and rho^T rho.
 template <int kM, int kSm, bool kValueOnly = false>
-__device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, int t, int ns, float alpha, int ea,
-                                         int eb, double& acc) {
+__device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, int t, int ns, float alpha, Own& o) {
   if (!forward_tile<kM, kSm, false, kSm>(c, p, o0 + t * kSm, 0, ns, alpha)) return false;
   if constexpr (kValueOnly) {  // line-search trial: only sum_j rho_j^2 is needed
     group_sync(c.g);
-    if (ea == -3) acc += dot_exact(c.G->rho, c.G->zero, 1, c.G->rho, c.G->zero, 1, ns);
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+      if (o.ea[e] == -3) o.acc[e] += dot_exact(c.G->rho, c.G->zero, 1, c.G->rho, c.G->zero, 1, ns);
     return true;
   } else {
-    return reverse_tile<kM, kSm, kSm>(c, p, ns, ea, eb, acc);
+    return reverse_tile<kM, kSm, kSm>(c, p, ns, o);
   }
 }
 
@@ -600,28 +619,29 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
 // the four-channel forward pass needs narrow tiles to fit one N = 128 UMMA, the
 // reverse pass does not.
 template <int kM>
-__device__ __forceinline__ bool run_pair(Lane& c, const StepParams& p, int o0, int t, int ns, float alpha, int ea,
-                                         int eb, double& acc) {
+__device__ __forceinline__ bool run_pair(Lane& c, const StepParams& p, int o0, int t, int ns, float alpha, Own& o) {
   constexpr int kSS = 2 * kS0;
   const int j0 = o0 + t * kSS;
   if (!forward_tile<kM, kS0, true, kSS>(c, p, j0, 0, min(ns, kS0), alpha)) return false;
-  if (ns <= kS0) return reverse_tile<kM, kS0, kSS>(c, p, ns, ea, eb, acc);
+  if (ns <= kS0) return reverse_tile<kM, kS0, kSS>(c, p, ns, o);
   if (!forward_tile<kM, kS0, true, kSS>(c, p, j0 + kS0, kS0, ns - kS0, alpha)) return false;
-  return reverse_tile<kM, kSS, kSS>(c, p, ns, ea, eb, acc);
+  return reverse_tile<kM, kSS, kSS>(c, p, ns, o);
 }
 
 // Layer-1 constants of the tile passes at the point q: c1 = b_1 + W_1q q (value
-// channel, by the unit's first thread) and dz1 = W_1q (q - q_n) (difference channel,
-// by its second), FP64 sums rounded once.
-__device__ __forceinline__ void set_layer1(const Lane& c, const Shared* S, Group* G, const double* q, int r,
-                                           const float* b1) {
-  if (c.part == 0) {
-    double cc = (double)b1[c.u];
-    for (int j = 0; j < r; ++j) cc = fma((double)S->w1q[j][c.u], q[j], cc);
+// channel) and dz1 = W_1q (q - q_n) (difference channel), FP64 sums rounded once;
+// W_1q is read from global memory (L1-cached: once per GN iteration).
+template <int kM>
+__device__ __forceinline__ void set_layer1(const Lane& c, const StepParams& p, Group* G, const double* q) {
+  const float* w = p.w1 + (size_t)c.u * (kM + p.r) + kM;
+  if (kTPU == 1 || c.part == 0) {
+    double cc = (double)p.b1[c.u];
+    for (int j = 0; j < p.r; ++j) cc = fma((double)w[j], q[j], cc);
     G->c1[c.u] = (float)cc;
-  } else {
+  }
+  if (kTPU == 1 || c.part == 1) {
     double dz = 0.0;
-    for (int j = 0; j < r; ++j) dz = fma((double)S->w1q[j][c.u], q[j] - G->qn[j], dz);
+    for (int j = 0; j < p.r; ++j) dz = fma((double)w[j], q[j] - G->qn[j], dz);
     G->dz1[c.u] = (float)dz;
   }
 }
@@ -643,8 +663,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
 
   uint8_t* Wimg = sm;
   uint8_t* Hbase = sm + ((p.img_bytes + 1023) & ~1023);
-  c.H = Hbase + (size_t)c.g * 2 * kHBuf;  // two 64-column blocks: hi parts, then lo parts
-  c.S = reinterpret_cast<Shared*>(Hbase + (size_t)kGroups * 2 * kHBuf);
+  c.H = Hbase + (size_t)c.g * kHBuf;  // this group's 64-column operand block
+  c.S = reinterpret_cast<Shared*>(Hbase + (size_t)kGroups * kHBuf);
   c.G = reinterpret_cast<Group*>(c.S + 1) + c.g;
   Shared* S = c.S;
   Group* G = c.G;
@@ -665,7 +685,6 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
   if (tid < kTcWidth) {
     for (int l = 0; l < L - 1; ++l) S->bh[l][tid] = p.bh[l * kTcWidth + tid];
     for (int k = 0; k < kM; ++k) S->w1x[k][tid] = p.w1[tid * (kM + r) + k];
-    for (int j = 0; j < r; ++j) S->w1q[j][tid] = p.w1[tid * (kM + r) + kM + j];
     S->wout[tid] = p.wout[tid];
   }
   tc_fence_before();
@@ -690,17 +709,24 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
   c.wsq = c.wx0 * c.wx0 + c.wx1 * c.wx1;
   c.wo = S->wout[c.u];
   const int ntri = r * (r + 1) / 2;
-  const int n_entries = ntri + r;  // <= 135 < kGT
-  // normal-equation entry owned by this thread: (ea, eb) of J^T J, or (ea, -2) of J^T rho
-  int ea = -1, eb = -1;
-  if (c.gt < ntri) {
-    int a = 0, rem = c.gt;
-    while (rem >= r - a) { rem -= r - a; ++a; }
-    ea = a; eb = a + rem;
-  } else if (c.gt < n_entries) {
-    ea = c.gt - ntri; eb = -2;
-  } else if (c.gt == n_entries && p.line_search > 0) {
-    ea = -3;  // rho^T rho, the line search's objective
+  const int n_entries = ntri + r;  // <= 135; with the line search's rho^T rho <= 136 <= 2 kGT
+  // normal-equation entries k = c.gt and c.gt + kGT owned by this thread
+  Own own;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int k = c.gt + e * kGT;
+    int ea = -1, eb = -1;
+    if (k < ntri) {
+      int a = 0, rem = k;
+      while (rem >= r - a) { rem -= r - a; ++a; }
+      ea = a; eb = a + rem;
+    } else if (k < n_entries) {
+      ea = k - ntri; eb = -2;
+    } else if (k == n_entries && p.line_search > 0) {
+      ea = -3;  // rho^T rho, the line search's objective
+    }
+    own.ea[e] = ea;
+    own.eb[e] = eb;
   }
 
   while (ok) {
@@ -726,28 +752,32 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
     group_sync(c.g);
 
     for (int it = 0; it < p.gn_iters && ok; ++it) {
-      set_layer1(c, S, G, G->qcur, r, p.b1);
-      double acc = 0.0;
+      set_layer1<kM>(c, p, G, G->qcur);
+      own.acc[0] = own.acc[1] = 0.0;
       if (it == 0) {
         const int nt = (M + 2 * kS0 - 1) / (2 * kS0);
         for (int t = 0; t < nt && ok; ++t)
-          ok = run_pair<kM>(c, p, o0, t, min(2 * kS0, M - t * 2 * kS0), alpha, ea, eb, acc);
+          ok = run_pair<kM>(c, p, o0, t, min(2 * kS0, M - t * 2 * kS0), alpha, own);
       } else {
         const int nt = (M + kS1 - 1) / kS1;
         for (int t = 0; t < nt && ok; ++t)
-          ok = run_tile<kM, kS1>(c, p, o0, t, min(kS1, M - t * kS1), alpha, ea, eb, acc);
+          ok = run_tile<kM, kS1>(c, p, o0, t, min(kS1, M - t * kS1), alpha, own);
       }
       if (!ok) break;
       const int R = r + 1;
-      if (ea >= 0) {
-        if (eb >= 0) {
-          G->amat[ea * R + eb] = acc;
-          G->amat[eb * R + ea] = acc;
-        } else {
-          G->amat[ea * R + r] = -acc;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int ea = own.ea[e], eb = own.eb[e];
+        if (ea >= 0) {
+          if (eb >= 0) {
+            G->amat[ea * R + eb] = own.acc[e];
+            G->amat[eb * R + ea] = own.acc[e];
+          } else {
+            G->amat[ea * R + r] = -own.acc[e];
+          }
+        } else if (ea == -3) {
+          G->phi0 = 0.5 * own.acc[e];
         }
-      } else if (ea == -3) {
-        G->phi0 = 0.5 * acc;
       }
       group_sync(c.g);
       if (c.gw == 0) {
@@ -775,13 +805,15 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
         for (int trial = 0; trial <= p.line_search && ok; ++trial, a *= 0.5) {
           if (c.gt < r) G->qtry[c.gt] = G->qcur[c.gt] + a * G->delta[c.gt];
           group_sync(c.g);
-          set_layer1(c, S, G, G->qtry, r, p.b1);
-          double acc_phi = 0.0;
+          set_layer1<kM>(c, p, G, G->qtry);
+          own.acc[0] = own.acc[1] = 0.0;
           const int nt = (M + kS1 - 1) / kS1;
           for (int t = 0; t < nt && ok; ++t)
-            ok = run_tile<kM, kS1, true>(c, p, o0, t, min(kS1, M - t * kS1), alpha, ea, eb, acc_phi);
+            ok = run_tile<kM, kS1, true>(c, p, o0, t, min(kS1, M - t * kS1), alpha, own);
           if (!ok) break;
-          if (ea == -3) G->phi = 0.5 * acc_phi;
+#pragma unroll
+          for (int e = 0; e < 2; ++e)
+            if (own.ea[e] == -3) G->phi = 0.5 * own.acc[e];
           group_sync(c.g);
           if (G->phi <= G->phi0 + kArmijoC1 * a * G->slope) {
             if (c.gt < r) G->qcur[c.gt] = G->qtry[c.gt];
@@ -851,7 +883,7 @@ __global__ void order_kernel(const int* off, int n_inst, int* order, int* status
 }  // namespace
 
 size_t tc_step_smem_bytes(int img_bytes) {
-  return 1024 + (((size_t)img_bytes + 1023) & ~(size_t)1023) + (size_t)kGroups * 2 * kHBuf + sizeof(Shared) +
+  return 1024 + (((size_t)img_bytes + 1023) & ~(size_t)1023) + (size_t)kGroups * kHBuf + sizeof(Shared) +
          kGroups * sizeof(Group);
 }
 
@@ -911,9 +943,10 @@ cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst
     kernel<<<grid, kThreads, smem, s>>>(p);
     return cudaGetLastError();
   };
-  const bool small_tiles = ctx->tc_tile_s1 == 16;
-  if (ctx->desc.m == 2) return small_tiles ? launch(step_tc_kernel<2, 16>) : launch(step_tc_kernel<2, 32>);
-  return small_tiles ? launch(step_tc_kernel<1, 16>) : launch(step_tc_kernel<1, 32>);
+  constexpr int kLarge = kTcTileS1Large, kSmall = kTcTileS1Small;
+  const bool small_tiles = ctx->tc_tile_s1 == kSmall;
+  if (ctx->desc.m == 2) return small_tiles ? launch(step_tc_kernel<2, kSmall>) : launch(step_tc_kernel<2, kLarge>);
+  return small_tiles ? launch(step_tc_kernel<1, kSmall>) : launch(step_tc_kernel<1, kLarge>);
 }
 
 }  // namespace crom

@@ -261,20 +261,27 @@ def test_step_tc_large_instance():
     _check_step(w, q1, st)
 
 
+# Sample tiles of the tensor-core step: TILE_S0 samples per forward tile at GN
+# iteration 0, TILE_S1 (large, small) later.
+TILE_S0, TILE_S1 = 8, (16, 8)
+
+
 @pytest.mark.parametrize("gn_iters", [2, 3])
 def test_step_tc_small_tiles_matches_oracle(gn_iters):
-    """The (16, 16) sample-tile variant of the step (16-sample tiles in every GN
-    iteration) against the oracle on uneven |M_i|."""
+    """The small sample-tile variant of the step (TILE_S1[1] samples per tile after
+    iteration 0) against the oracle on uneven |M_i|; other shapes are rejected."""
     c = crom()
     w = gen.heat2d_batched(n_inst=20, m_lo=8, m_hi=300, bias_std=0.1)
     w.gn_iters = gn_iters
     ctx = make_ctx(w.spec, w.params)
-    c.crom_set_step_tiles(ctx, 16, 16)
-    assert c.crom_get_step_tiles(ctx)[:2] == (16, 16)
+    assert c.crom_get_step_tiles(ctx)[:2] == (TILE_S0, TILE_S1[0])
+    c.crom_set_step_tiles(ctx, TILE_S0, TILE_S1[1])
+    assert c.crom_get_step_tiles(ctx)[:2] == (TILE_S0, TILE_S1[1])
     q1, st = run_steps(ctx, w, 1, c.CROM_PREC_BF16X2)
     _check_step(w, q1, st)
-    with pytest.raises(c.CromError):
-        c.crom_set_step_tiles(ctx, 16, 8)
+    for bad in ((TILE_S0, 4), (TILE_S0, 32), (16, TILE_S1[0])):
+        with pytest.raises(c.CromError):
+            c.crom_set_step_tiles(ctx, *bad)
 
 
 def test_autotune_measures_both_tile_shapes_and_leaves_q():
@@ -288,8 +295,8 @@ def test_autotune_measures_both_tile_shapes_and_leaves_q():
                                  dev(w.samples, torch.float32), status, dt=w.dt, gn_iters=w.gn_iters,
                                  max_samples=int(w.sizes.max()))
     torch.cuda.synchronize()
-    assert s0 == 16 and s1 in (16, 32) and min(ms) > 0
-    assert s1 == (32 if ms[0] <= ms[1] else 16)
+    assert s0 == TILE_S0 and s1 in TILE_S1 and min(ms) > 0
+    assert s1 == (TILE_S1[0] if ms[0] <= ms[1] else TILE_S1[1])
     assert np.array_equal(q.cpu().numpy(), w.q0)          # the trials ran on a copy
     q1, st = run_steps(ctx, subset(w, np.arange(12)), 1, c.CROM_PREC_BF16X2)
     _check_step(subset(w, np.arange(12)), q1, st)
