@@ -144,6 +144,76 @@ __global__ void __launch_bounds__(32 * kWarps) advdiff2d_march_kernel(
   }
 }
 
+// The marching update with four columns per lane (float4 loads and stores): a warp
+// owns 128 consecutive columns and a strip of kRows rows; within a lane the column
+// neighbours are the adjacent components, across lanes they come from a shuffle of
+// the first / last component, and the two columns beyond the warp from memory.
+// Requires n % 128 == 0, n % (kRows4 * kWarps4) == 0 and 16-byte aligned arrays.
+constexpr int kRows4 = 32, kWarps4 = 4;
+__device__ __forceinline__ float upwind(float a, float up, float down) { return a * (a > 0.f ? up : down); }
+__global__ void __launch_bounds__(32 * kWarps4) advdiff2d_march4_kernel(
+    const float* __restrict__ u, float* __restrict__ out, const float* __restrict__ ax,
+    const float* __restrict__ ay, const float* __restrict__ coef, int n, float dt, float inv_h, float inv_h2) {
+  const int b = blockIdx.z;
+  const int lane = threadIdx.x;
+  const int j0 = blockIdx.x * 128;
+  const int j = j0 + 4 * lane;
+  const int i0 = (blockIdx.y * kWarps4 + threadIdx.y) * kRows4;
+  const size_t base = (size_t)b * n * n;
+  const float* ub = u + base;
+  const float* axb = ax + base;
+  const float* ayb = ay + base;
+  float* ob = out + base;
+  const float nu = coef[b];
+  const int jl = j0 == 0 ? n - 1 : j0 - 1;          // column left of the warp
+  const int jr = j0 + 128 == n ? 0 : j0 + 128;      // column right of the warp
+  auto ld4 = [&](const float* p, int i) { return *reinterpret_cast<const float4*>(p + (size_t)i * n + j); };
+  const int im0 = i0 == 0 ? n - 1 : i0 - 1;
+  float4 uim = ld4(ub, im0);
+  float4 c = ld4(ub, i0);
+  float4 a_l = ld4(axb, im0);
+#pragma unroll 4
+  for (int k = 0; k < kRows4; ++k) {
+    const int i = i0 + k;
+    const int ip = i == n - 1 ? 0 : i + 1;
+    const float4 uip = ld4(ub, ip);
+    const float4 a_r = ld4(axb, i);
+    const float4 b_r = ld4(ayb, i);
+    // halo columns: lane 0 needs column jl (u and the y-face velocity), lane 31 column jr (u)
+    const float halo_u = lane == 0 ? ub[(size_t)i * n + jl] : (lane == 31 ? ub[(size_t)i * n + jr] : 0.f);
+    const float halo_b = lane == 0 ? ayb[(size_t)i * n + jl] : 0.f;
+    float ujm0 = __shfl_up_sync(0xffffffffu, c.w, 1);
+    float ujp3 = __shfl_down_sync(0xffffffffu, c.x, 1);
+    float b_l0 = __shfl_up_sync(0xffffffffu, b_r.w, 1);
+    if (lane == 0) {
+      ujm0 = halo_u;
+      b_l0 = halo_b;
+    }
+    if (lane == 31) ujp3 = halo_u;
+    const float cv[4] = {c.x, c.y, c.z, c.w};
+    const float um[4] = {uim.x, uim.y, uim.z, uim.w};
+    const float up[4] = {uip.x, uip.y, uip.z, uip.w};
+    const float ar[4] = {a_r.x, a_r.y, a_r.z, a_r.w};
+    const float al[4] = {a_l.x, a_l.y, a_l.z, a_l.w};
+    const float br[4] = {b_r.x, b_r.y, b_r.z, b_r.w};
+    const float jm[4] = {ujm0, c.x, c.y, c.z};
+    const float jp[4] = {c.y, c.z, c.w, ujp3};
+    const float bl[4] = {b_l0, b_r.x, b_r.y, b_r.z};
+    float o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float div = (upwind(ar[q], cv[q], up[q]) - upwind(al[q], um[q], cv[q]) + upwind(br[q], cv[q], jp[q]) -
+                         upwind(bl[q], jm[q], cv[q])) * inv_h;
+      const float lap = (um[q] + up[q] + jm[q] + jp[q] - 4.f * cv[q]) * inv_h2;
+      o[q] = fmaf(dt, fmaf(nu, lap, -div), cv[q]);
+    }
+    *reinterpret_cast<float4*>(ob + (size_t)i * n + j) = make_float4(o[0], o[1], o[2], o[3]);
+    uim = c;
+    c = uip;
+    a_l = a_r;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_fom(int kind, int n_batch, int nx, int ny, const float* coef, const float* ax, const float* ay,
@@ -167,7 +237,13 @@ cudaError_t launch_fom(int kind, int n_batch, int nx, int ny, const float* coef,
         heat2d_neumann_kernel<true><<<grid, dim3(32, 8), 0, s>>>(src, dst, coef, nx, (float)(dt / (h * h)));
     } else {
       const double h = 1.0 / nx;
-      if (nx % 32 == 0 && nx % (kRows * kWarps) == 0) {
+      auto aligned16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+      if (nx % 128 == 0 && nx % (kRows4 * kWarps4) == 0 && aligned16(src) && aligned16(dst) && aligned16(ax) &&
+          aligned16(ay)) {
+        dim3 grid(nx / 128, nx / (kRows4 * kWarps4), n_batch);
+        advdiff2d_march4_kernel<<<grid, dim3(32, kWarps4), 0, s>>>(src, dst, ax, ay, coef, nx, (float)dt,
+                                                                   (float)(1.0 / h), (float)(1.0 / (h * h)));
+      } else if (nx % 32 == 0 && nx % (kRows * kWarps) == 0) {
         dim3 grid(nx / 32, nx / (kRows * kWarps), n_batch);
         advdiff2d_march_kernel<<<grid, dim3(32, kWarps), 0, s>>>(src, dst, ax, ay, coef, nx, (float)dt,
                                                                  (float)(1.0 / h), (float)(1.0 / (h * h)));
