@@ -1,17 +1,18 @@
 // Dense reconstruction g(x_p, q_c) on the tcgen05 tensor cores (value channel only).
 //
 // Persistent kernel, one CTA per SM with the decoder's bf16 hidden matrices in
-// shared memory, two independent groups of 256 threads (one tile of 64 points
-// each, own operand buffers / TMEM columns / mbarrier / named barrier) so that
-// one group's UMMAs overlap the other's epilogue.  Hidden unit u is TMEM lane u
-// and is served by two threads of the group, each taking 32 of the tile's
-// points.  A tile is 64 points of one code:
+// shared memory, two independent groups of 256 threads (one tile each, own
+// operand buffers / TMEM columns / mbarrier / named barrier) so that one group's
+// UMMAs overlap the other's epilogue.  Hidden unit u is TMEM lane u and is served
+// by two threads of the group, each taking half of the tile's points.  A tile is
+// 64 points of one code with hi/lo operand parts, 128 points with hi parts only:
 //   layer 1 (K = m + r, too small for UMMA) on CUDA cores: the q part of
 //     W_1 [x; q] + b_1 is hoisted per code; h = ELU(W_1x x + c);
 //   layers 2..L: D[u][n] = sum_k W_l[u][k] H[k][n] by UMMA (M = 128 units,
-//     N = 64 points, K = 128), A = W_l (K-major, resident), B = H (MN-major,
-//     written by the previous epilogue; the hi and lo parts side by side as one
-//     N = 128 operand, added in the epilogue); epilogue: bias, ELU, bf16 split, store;
+//     N = 128, K = 128), A = W_l (K-major, resident), B = H (MN-major, written by
+//     the previous epilogue: the hi and lo parts of 64 points side by side, added
+//     in the epilogue, or the hi parts of 128 points); epilogue: bias, ELU, bf16
+//     split, store;
 //   output layer: w_out . h_L on the CUDA cores in the last hidden layer's
 //     epilogue, in FP32 from h_L itself (a warp butterfly over the 32 units of
 //     each warp, then the four lane quadrants' partial sums), written coalesced.
@@ -33,12 +34,16 @@ using namespace tc;
 constexpr int kGroups = 2;
 constexpr int kGT = 256;  // two threads per TMEM lane, each half of the tile's points
 constexpr int kThreads = kGroups * kGT;
-constexpr int kTileN = 64;
+// Points per tile: 64 with hi/lo operand parts (N = 128 = 64 hi + 64 lo columns),
+// 128 with hi parts only (N = 128 points); the accumulator and operand blocks are
+// the same size either way.
+constexpr int kTileSplit = 64, kTileHi = 128;
+constexpr int kTileN = kTileHi;  // sizes of the per-tile arrays
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kGroupCols = 256;
-constexpr uint32_t kAccCol = 0;    // W h_hi in columns 0..63, W h_lo in 64..127
+constexpr uint32_t kAccCol = 0;    // W h_hi in columns 0..63, W h_lo in 64..127 (hi only: 128 points)
 constexpr uint32_t kWaitLimit = 1u << 25;
-constexpr size_t kHBuf = (size_t)kTcWidth * kTileN * 2;  // one bf16 operand buffer, 16 KB
+constexpr size_t kHBuf = (size_t)kTcWidth * 64 * 2;  // one 64-column bf16 operand block, 16 KB
 
 struct ReconParams {
   const uint8_t* img;
@@ -141,7 +146,8 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
   const int g = tid / kGT, gt = tid % kGT;
   const int lq = (gt >> 5) & 3, half = gt >> 7;
   const int u = lq * 32 + (gt & 31);           // hidden unit = TMEM lane
-  const int nbeg = half * (kTileN / 2);        // this thread's 32 points of the tile
+  constexpr int kTile = kSplit ? kTileSplit : kTileHi;
+  const int nbeg = half * (kTile / 2);         // this thread's half of the tile's points
   const uint32_t lane_base = (uint32_t)lq * 32;
   const int m = p.m, r = p.r;
   uint8_t* Wimg = sm;
@@ -185,7 +191,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
   // Base UMMA descriptors; every operand slice is base + a compile-time offset.
   const uint64_t dW = smem_desc_sw128(wbase, 16, 1024);
   const uint64_t dHhi = smem_desc_sw128(smem_u32(Hhi), 16384, 1024);
-  constexpr uint32_t id_layer = idesc_f16(128, kSplit ? 2 * kTileN : kTileN, false, true, true);
+  constexpr uint32_t id_layer = idesc_f16(128, 128, false, true, true);
   int cur_code = -1;
   float c = 0.f;
   const float wx0 = S->w1x[0][u], wx1 = (m > 1) ? S->w1x[1][u] : 0.f;
@@ -195,21 +201,21 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
 
   for (int tile = blockIdx.x * kGroups + g; tile < n_tiles && ok; tile += gridDim.x * kGroups) {
     const int code = tile / p.tiles_per_code;
-    const int p0 = (tile % p.tiles_per_code) * kTileN;
+    const int p0 = (tile % p.tiles_per_code) * kTile;
     if (code != cur_code) {
       double cc = (double)p.b1[u];
       for (int j = 0; j < r; ++j) cc += (double)p.w1[u * (m + r) + m + j] * p.q[(size_t)code * r + j];
       c = (float)cc;
       cur_code = code;
     }
-    if (gt < kTileN) {
+    if (gt < kTile) {
       const int n = p0 + gt;
       for (int k = 0; k < m; ++k) G->xs[k][gt] = (n < p.n_pts) ? p.x[(size_t)n * m + k] : 0.f;
     }
     group_sync(g);
     // ---- layer 1 on CUDA cores
 #pragma unroll 1
-    for (int n0 = nbeg; n0 < nbeg + kTileN / 2; n0 += 16) {
+    for (int n0 = nbeg; n0 < nbeg + kTile / 2; n0 += 16) {
       f32x2 h[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
@@ -246,10 +252,10 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
       if (!ok) break;
       const float bias = S->bh[l][u];
 #pragma unroll 1
-      for (int n0 = nbeg; n0 < nbeg + kTileN / 2; n0 += 16) {
+      for (int n0 = nbeg; n0 < nbeg + kTile / 2; n0 += 16) {
         float v[16], w[16];
         tmem_ld16(taddr(tb, lane_base, kAccCol + n0), v);
-        if (kSplit) tmem_ld16(taddr(tb, lane_base, kAccCol + kTileN + n0), w);
+        if (kSplit) tmem_ld16(taddr(tb, lane_base, kAccCol + kTileSplit + n0), w);
         tmem_ld_wait();
         f32x2 h[8];
         const f32x2 b2 = pk2(bias, bias);
@@ -277,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
     }
     if (!ok) break;
     group_sync(g);
-    if (gt < kTileN) {
+    if (gt < kTile) {
       const int n = p0 + gt;
       const float o = (G->outp[0][gt] + G->outp[1][gt]) + (G->outp[2][gt] + G->outp[3][gt]);
       if (n < p.n_pts) p.out[(size_t)code * p.n_pts + n] = o + p.bout;
@@ -309,7 +315,8 @@ cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const d
   p.out = out;
   p.n_pts = n_pts;
   p.n_codes = n_codes;
-  p.tiles_per_code = (n_pts + kTileN - 1) / kTileN;
+  const int tile_pts = split ? kTileSplit : kTileHi;
+  p.tiles_per_code = (n_pts + tile_pts - 1) / tile_pts;
   p.flag = ctx->queue + 2;
   const size_t smem = 1024 + (((size_t)p.img_bytes + 1023) & ~(size_t)1023) + (size_t)kGroups * 2 * kHBuf +
                       kTailBytes;
