@@ -155,6 +155,20 @@ __global__ void sum_splits_kernel(const float* parts, int splits, long stride, l
 
 // Column sums of X [rows][cols] in fixed order: out[c] = sum_r X[r][c] (one block per column).
 // Column sums of X [rows][cols] in two fixed-order passes (deterministic):
+// Compensated (Kahan) FP32 accumulation: the running sum s - c stays within a few
+// ulps of the exact sum whatever the number of terms, in FP32 instructions (FP64 is
+// a slow pipe on this GPU: per-element FP64 adds made these reductions FP64-bound).
+struct CompSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = __fsub_rn(v, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // colsum_part_kernel: block (32 columns x 8 row lanes) per (column group, row chunk),
 // coalesced across columns; colsum_final_kernel adds the chunk partials in order.
 constexpr int kColChunks = 128;
@@ -162,11 +176,11 @@ __global__ void colsum_part_kernel(const float* X, long rows, int cols, double* 
   const int c = blockIdx.x * 32 + threadIdx.x;
   const long per = (rows + gridDim.y - 1) / gridDim.y;
   const long r0 = (long)blockIdx.y * per, r1 = min(rows, r0 + per);
-  double s = 0.0;
+  CompSum s;
   if (c < cols)
-    for (long r = r0 + threadIdx.y; r < r1; r += 8) s += (double)X[r * cols + c];
+    for (long r = r0 + threadIdx.y; r < r1; r += 8) s.add(X[r * cols + c]);
   __shared__ double red[8][33];
-  red[threadIdx.y][threadIdx.x] = s;
+  red[threadIdx.y][threadIdx.x] = s.value();
   __syncthreads();
   if (threadIdx.y == 0 && c < cols) {
     double t = 0.0;
@@ -180,17 +194,20 @@ __global__ void colsum_part4_kernel(const float* X, long rows, int cols, double*
   const int q = blockIdx.x * 64 + threadIdx.x, cols4 = cols / 4;
   const long per = (rows + gridDim.y - 1) / gridDim.y;
   const long r0 = (long)blockIdx.y * per, r1 = min(rows, r0 + per);
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  CompSum s0, s1, s2, s3;
   if (q < cols4)
     for (long r = r0 + threadIdx.y; r < r1; r += 4) {
       const float4 v = reinterpret_cast<const float4*>(X + r * cols)[q];
-      s0 += v.x; s1 += v.y; s2 += v.z; s3 += v.w;
+      s0.add(v.x);
+      s1.add(v.y);
+      s2.add(v.z);
+      s3.add(v.w);
     }
   __shared__ double red[4][64][4];
-  red[threadIdx.y][threadIdx.x][0] = s0;
-  red[threadIdx.y][threadIdx.x][1] = s1;
-  red[threadIdx.y][threadIdx.x][2] = s2;
-  red[threadIdx.y][threadIdx.x][3] = s3;
+  red[threadIdx.y][threadIdx.x][0] = s0.value();
+  red[threadIdx.y][threadIdx.x][1] = s1.value();
+  red[threadIdx.y][threadIdx.x][2] = s2.value();
+  red[threadIdx.y][threadIdx.x][3] = s3.value();
   __syncthreads();
   if (threadIdx.y == 0 && q < cols4)
     for (int e = 0; e < 4; ++e)
@@ -240,13 +257,18 @@ __global__ void conv_grad_part_kernel(const float* dz, const float* x, int Lin, 
   const long n = (long)B * Lout;
   const long per = (n + gridDim.y - 1) / gridDim.y;
   const long e0 = (long)blockIdx.y * per, e1 = min(n, e0 + per);
-  double s = 0.0;
+  // products split exactly into p + err (one FMA), the p summed with compensation
+  CompSum s;
+  float err = 0.f;
   for (long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int b = (int)(e / Lout), i = (int)(e % Lout);
-    s += (double)dz[e] * (k < 6 ? (double)x[(long)b * Lin + 4 * i + k] : 1.0);
+    const float a = dz[e], xv = k < 6 ? x[(long)b * Lin + 4 * i + k] : 1.f;
+    const float p = __fmul_rn(a, xv);
+    err += fmaf(a, xv, -p);
+    s.add(p);
   }
   __shared__ double red[256];
-  red[threadIdx.x] = s;
+  red[threadIdx.x] = s.value() + (double)err;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
@@ -320,6 +342,21 @@ __global__ void out_delta_kernel(const float* dg, const float* wout, const float
   const int u = (int)(e % w);
   delta[e] = dg[n] * wout[u] * elu_d(Z[e]);
 }
+// The same, four units per thread (w % 4 == 0, N * w / 4 < 2^31, 16-byte aligned):
+// quad e covers row e / (w / 4), units 4 (e % (w / 4)) ..
+__global__ void out_delta4_kernel(const float* dg, const float* wout, const float* Z, int w, unsigned n_quads,
+                                  float* delta) {
+  const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_quads) return;
+  const unsigned q = (unsigned)w / 4;
+  const long n = e / q;
+  const int u = 4 * (int)(e % q);
+  const float d = dg[n];
+  const float4 z = *reinterpret_cast<const float4*>(Z + n * w + u);
+  const float4 wo = *reinterpret_cast<const float4*>(wout + u);
+  *reinterpret_cast<float4*>(delta + n * w + u) =
+      make_float4(d * wo.x * elu_d(z.x), d * wo.y * elu_d(z.y), d * wo.z * elu_d(z.z), d * wo.w * elu_d(z.w));
+}
 
 // dq[b][j] = sum over the S points of snapshot b of din[n][m + j]  (fixed order).
 // dq[b][j] = sum_s din[b S + s][m + j]: one block per snapshot, 256 row lanes,
@@ -328,9 +365,9 @@ __global__ void dq_kernel(const float* din, int B, int S, int m, int r, float* d
   const int b = blockIdx.x;
   __shared__ double red[256];
   for (int j = 0; j < r; ++j) {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < S; i += blockDim.x) s += (double)din[((long)b * S + i) * (m + r) + m + j];
-    red[threadIdx.x] = s;
+    CompSum s;
+    for (int i = threadIdx.x; i < S; i += blockDim.x) s.add(din[((long)b * S + i) * (m + r) + m + j]);
+    red[threadIdx.x] = s.value();
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
       if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
@@ -545,7 +582,13 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
            nullptr, t->split);
   if (e != cudaSuccess) return e;
   colsum(t, s, t->dg, N, 1, gr + lay.dec_b[L]);
-  out_delta_kernel<<<blocks(N * w, 256), 256, 0, s>>>(t->dg, p + lay.dec_w[L], t->Z[L - 1], w, N, t->delta);
+  const float* wout = p + lay.dec_w[L];
+  if (w % 4 == 0 && N * (w / 4) < (1L << 31) && ((uintptr_t)wout & 15) == 0 && ((uintptr_t)t->Z[L - 1] & 15) == 0 &&
+      ((uintptr_t)t->delta & 15) == 0)
+    out_delta4_kernel<<<blocks(N * (w / 4), 256), 256, 0, s>>>(t->dg, wout, t->Z[L - 1], w,
+                                                               (unsigned)(N * (w / 4)), t->delta);
+  else
+    out_delta_kernel<<<blocks(N * w, 256), 256, 0, s>>>(t->dg, p + lay.dec_w[L], t->Z[L - 1], w, N, t->delta);
   float* dcur = t->delta;
   float* dnext = t->delta2;
   for (int l = L - 1; l >= 0; --l) {
