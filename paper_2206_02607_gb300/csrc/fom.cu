@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(32 * kWarps) advdiff2d_march_kernel(
 // the first / last component, and the two columns beyond the warp from memory.
 // Requires n % 128 == 0, n % (kRows4 * kWarps4) == 0 and 16-byte aligned arrays.
 constexpr int kRows4 = 32, kWarps4 = 4;
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 __device__ __forceinline__ float upwind(float a, float up, float down) { return a * (a > 0.f ? up : down); }
 __global__ void __launch_bounds__(32 * kWarps4) advdiff2d_march4_kernel(
     const float* __restrict__ u, float* __restrict__ out, const float* __restrict__ ax,
@@ -214,6 +215,63 @@ __global__ void __launch_bounds__(32 * kWarps4) advdiff2d_march4_kernel(
   }
 }
 
+// 2D heat with zero-flux (mirror) boundaries, marching with four columns per lane
+// as above: the mirror ghosts are u_{-1} = u_1 and u_n = u_{n-2} in both directions
+// (row 0 takes row 1 as its upper neighbour, row n-1 row n-2 as its lower one; in
+// column 0 and n-1 the lane's own component j = 1 or n-2 is the missing neighbour).
+// kField: the coefficient is read per node (float4), else per field.
+// Requires n % 128 == 0, n % (kRows4 * kWarps4) == 0 and 16-byte aligned arrays.
+template <bool kField>
+__global__ void __launch_bounds__(32 * kWarps4) heat2d_march4_kernel(const float* __restrict__ u,
+                                                                    float* __restrict__ out,
+                                                                    const float* __restrict__ coef, int n,
+                                                                    float r_over) {
+  const int b = blockIdx.z;
+  const int lane = threadIdx.x;
+  const int j0 = blockIdx.x * 128;
+  const int j = j0 + 4 * lane;
+  const int i0 = (blockIdx.y * kWarps4 + threadIdx.y) * kRows4;
+  const size_t base = (size_t)b * n * n;
+  const float* ub = u + base;
+  float* ob = out + base;
+  const float nu_b = kField ? 0.f : coef[b];
+  const bool left_edge = j0 == 0, right_edge = j0 + 128 == n;
+  auto ld4 = [&](const float* p, int i) { return *reinterpret_cast<const float4*>(p + (size_t)i * n + j); };
+  float4 uim = ld4(ub, i0 == 0 ? 1 : i0 - 1);
+  float4 c = ld4(ub, i0);
+#pragma unroll 4
+  for (int k = 0; k < kRows4; ++k) {
+    const int i = i0 + k;
+    const float4 uip = ld4(ub, i == n - 1 ? n - 2 : i + 1);
+    // halo columns: lane 0 needs column j0 - 1, lane 31 column j0 + 128 (inside the field)
+    const float halo = (lane == 0 && !left_edge) ? ub[(size_t)i * n + j0 - 1]
+                       : (lane == 31 && !right_edge) ? ub[(size_t)i * n + j0 + 128] : 0.f;
+    float ujm0 = __shfl_up_sync(0xffffffffu, c.w, 1);
+    float ujp3 = __shfl_down_sync(0xffffffffu, c.x, 1);
+    if (lane == 0) ujm0 = left_edge ? c.y : halo;
+    if (lane == 31) ujp3 = right_edge ? c.z : halo;
+    const float cv[4] = {c.x, c.y, c.z, c.w};
+    const float um[4] = {uim.x, uim.y, uim.z, uim.w};
+    const float up[4] = {uip.x, uip.y, uip.z, uip.w};
+    const float jm[4] = {ujm0, c.x, c.y, c.z};
+    const float jp[4] = {c.y, c.z, c.w, ujp3};
+    float nu[4] = {nu_b, nu_b, nu_b, nu_b};
+    if (kField) {
+      const float4 f = ld4(coef + base, i);
+      nu[0] = f.x; nu[1] = f.y; nu[2] = f.z; nu[3] = f.w;
+    }
+    float o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float lap = (um[q] + up[q] - 2.f * cv[q]) + (jm[q] + jp[q] - 2.f * cv[q]);
+      o[q] = fmaf(r_over * nu[q], lap, cv[q]);
+    }
+    *reinterpret_cast<float4*>(ob + (size_t)i * n + j) = make_float4(o[0], o[1], o[2], o[3]);
+    uim = c;
+    c = uip;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_fom(int kind, int n_batch, int nx, int ny, const float* coef, const float* ax, const float* ay,
@@ -230,14 +288,23 @@ cudaError_t launch_fom(int kind, int n_batch, int nx, int ny, const float* coef,
         heat1d_kernel<true><<<grid, 256, 0, s>>>(src, dst, coef, nx, (float)(dt / (dx * dx)));
     } else if (kind == CROM_FOM_HEAT2D_NEUMANN || kind == CROM_FOM_HEAT2D_NEUMANN_FIELD) {
       const double h = 1.0 / (nx - 1);
-      dim3 grid((nx + 31) / 32, (nx + 7) / 8, n_batch);
-      if (kind == CROM_FOM_HEAT2D_NEUMANN)
-        heat2d_neumann_kernel<false><<<grid, dim3(32, 8), 0, s>>>(src, dst, coef, nx, (float)(dt / (h * h)));
-      else
-        heat2d_neumann_kernel<true><<<grid, dim3(32, 8), 0, s>>>(src, dst, coef, nx, (float)(dt / (h * h)));
+      const bool field = kind == CROM_FOM_HEAT2D_NEUMANN_FIELD;
+      if (nx % 128 == 0 && nx % (kRows4 * kWarps4) == 0 && aligned16(src) && aligned16(dst) &&
+          (!field || aligned16(coef))) {
+        dim3 grid4(nx / 128, nx / (kRows4 * kWarps4), n_batch);
+        if (field)
+          heat2d_march4_kernel<true><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, (float)(dt / (h * h)));
+        else
+          heat2d_march4_kernel<false><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, (float)(dt / (h * h)));
+      } else {
+        dim3 grid((nx + 31) / 32, (nx + 7) / 8, n_batch);
+        if (field)
+          heat2d_neumann_kernel<true><<<grid, dim3(32, 8), 0, s>>>(src, dst, coef, nx, (float)(dt / (h * h)));
+        else
+          heat2d_neumann_kernel<false><<<grid, dim3(32, 8), 0, s>>>(src, dst, coef, nx, (float)(dt / (h * h)));
+      }
     } else {
       const double h = 1.0 / nx;
-      auto aligned16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
       if (nx % 128 == 0 && nx % (kRows4 * kWarps4) == 0 && aligned16(src) && aligned16(dst) && aligned16(ax) &&
           aligned16(ay)) {
         dim3 grid(nx / 128, nx / (kRows4 * kWarps4), n_batch);

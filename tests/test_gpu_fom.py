@@ -71,8 +71,8 @@ def test_heat2d_neumann_matches_oracle_and_conserves_mass(c):
         assert abs(np.sum(W * got[b]) - m0) < 2e-5 * abs(m0)
 
 
-def test_heat2d_neumann_cosine_mode_closed_form(c):
-    n = 64
+@pytest.mark.parametrize("n", [64, 256])   # 256: the four-columns-per-lane marching kernel
+def test_heat2d_neumann_cosine_mode_closed_form(c, n):
     h = 1 / (n - 1)
     t = np.arange(n) * h
     X1, X2 = np.meshgrid(t, t, indexing="ij")
