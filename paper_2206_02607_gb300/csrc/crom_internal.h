@@ -106,6 +106,7 @@ struct crom_trainer {
   double* partial = nullptr;
   double* loss_dev = nullptr;
   double* red = nullptr;  // partial sums of the deterministic column / convolution reductions
+  double* colpart = nullptr;  // per-block column partial sums fused into the TF32 epilogues
   std::vector<void*> owned;
   int precision = CROM_PREC_FP32;  // of the dense products (FP32 or TF32)
   void* blas = nullptr;            // cuBLAS handle for TF32, created on demand

@@ -36,6 +36,20 @@ constexpr int kSplitK = 32;
 __device__ __forceinline__ float elu_f(float z) { return z > 0.f ? z : expm1f(z); }
 __device__ __forceinline__ float elu_d(float z) { return z > 0.f ? 1.f : expf(z); }
 
+// Compensated (Kahan) FP32 accumulation: the running sum s - c stays within a few
+// ulps of the exact sum whatever the number of terms, in FP32 instructions (FP64 is
+// a slow pipe on this GPU: per-element FP64 adds made these reductions FP64-bound).
+struct CompSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = __fsub_rn(v, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 enum Epi { kEpiStore = 0, kEpiBiasElu = 1, kEpiTimesEluD = 2 };
 
 // C[i][j] = sum_k A(i, k) B(k, j), A(i, k) = A[i*sai + k*sak], B(k, j) = B[k*sbk + j*sbj].
@@ -144,6 +158,115 @@ __global__ void epi_times_elud4_kernel(float* C, long M, int N4, long ldc, const
     }
 }
 
+// The TF32 path's "x s'(z)" epilogue and output-layer delta with the column sums of
+// the result fused in (the bias gradients of the next layer down): blocks of 64
+// column quads x 4 row lanes, a fixed grid of kEpiRowBlocks row blocks striding over
+// the rows; each thread keeps compensated sums of its four columns, the block adds
+// its four row lanes and writes part[blockIdx.y][cols]; colsum_blocks_final_kernel
+// adds the row blocks in order.
+constexpr int kEpiRowBlocks = 4096;
+__device__ __forceinline__ void colpart_store(CompSum (&cs)[4], int q, int N4, double* part) {
+  __shared__ double red[4][64][4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) red[threadIdx.y][threadIdx.x][e] = cs[e].value();
+  __syncthreads();
+  if (threadIdx.y == 0 && q < N4)
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      part[(long)blockIdx.y * 4 * N4 + 4 * q + e] =
+          (red[0][threadIdx.x][e] + red[1][threadIdx.x][e]) + (red[2][threadIdx.x][e] + red[3][threadIdx.x][e]);
+}
+__global__ void epi_times_elud4_colsum_kernel(float* C, long M, int N4, long ldc, const float* Zp, double* part) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  CompSum cs[4];
+  if (q < N4)
+    for (long i = (long)blockIdx.y * blockDim.y + threadIdx.y; i < M; i += (long)gridDim.y * blockDim.y) {
+      float4* cp = reinterpret_cast<float4*>(C + i * ldc) + q;
+      const float4 zp = reinterpret_cast<const float4*>(Zp + i * ldc)[q];
+      float4 v = *cp;
+      v.x *= elu_d(zp.x); v.y *= elu_d(zp.y); v.z *= elu_d(zp.z); v.w *= elu_d(zp.w);
+      *cp = v;
+      cs[0].add(v.x); cs[1].add(v.y); cs[2].add(v.z); cs[3].add(v.w);
+    }
+  colpart_store(cs, q, N4, part);
+}
+__global__ void out_delta4_colsum_kernel(const float* dg, const float* wout, const float* Z, long N, int w4,
+                                         float* delta, double* part) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  CompSum cs[4];
+  if (q < w4) {
+    const float4 wo = reinterpret_cast<const float4*>(wout)[q];
+    for (long n = (long)blockIdx.y * blockDim.y + threadIdx.y; n < N; n += (long)gridDim.y * blockDim.y) {
+      const float d = dg[n];
+      const float4 z = reinterpret_cast<const float4*>(Z + n * 4 * w4)[q];
+      const float4 v = make_float4(d * wo.x * elu_d(z.x), d * wo.y * elu_d(z.y), d * wo.z * elu_d(z.z),
+                                   d * wo.w * elu_d(z.w));
+      reinterpret_cast<float4*>(delta + n * 4 * w4)[q] = v;
+      cs[0].add(v.x); cs[1].add(v.y); cs[2].add(v.z); cs[3].add(v.w);
+    }
+  }
+  colpart_store(cs, q, w4, part);
+}
+// The last hidden layer's bias + ELU epilogue (TF32 path, width <= 256) with the
+// output layer fused in: g_n = w_out . h_n + b_out, dL/dg_n = 2 (g_n - t_n) / N, and
+// per-block sums of (g_n - t_n)^2 (partial[blockIdx.y], added in order by
+// loss_final_kernel).  Blocks of 64 column quads x 4 rows, kEpiRowBlocks row blocks
+// striding over the rows; a row's 64 threads (two warps) reduce w_out . h by shuffles.
+__global__ void epi_bias_elu4_out_kernel(float* C, long M, int N4, long ldc, const float* bias, float* H,
+                                         const float* wout, const float* bout, const float* target, float* dg,
+                                         double* partial) {
+  const int q = threadIdx.x;
+  __shared__ float rowpart[4][2];
+  __shared__ double sqpart[4];
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 b = q < N4 ? reinterpret_cast<const float4*>(bias)[q] : zero4;
+  const float4 wo = q < N4 ? reinterpret_cast<const float4*>(wout)[q] : zero4;
+  double sq = 0.0;
+  for (long i0 = (long)blockIdx.y * 4; i0 < M; i0 += (long)gridDim.y * 4) {  // same trip count for the block
+    const long i = i0 + threadIdx.y;
+    float dot = 0.f;
+    if (i < M && q < N4) {
+      float4* cp = reinterpret_cast<float4*>(C + i * ldc) + q;
+      float4 z = *cp;
+      z.x += b.x; z.y += b.y; z.z += b.z; z.w += b.w;
+      *cp = z;
+      const float4 h = make_float4(elu_f(z.x), elu_f(z.y), elu_f(z.z), elu_f(z.w));
+      reinterpret_cast<float4*>(H + i * ldc)[q] = h;
+      dot = fmaf(wo.w, h.w, fmaf(wo.z, h.z, fmaf(wo.y, h.y, wo.x * h.x)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    if ((threadIdx.x & 31) == 0) rowpart[threadIdx.y][threadIdx.x >> 5] = dot;
+    __syncthreads();
+    if (threadIdx.x == 0 && i < M) {
+      const float res = (rowpart[threadIdx.y][0] + rowpart[threadIdx.y][1]) + bout[0] - target[i];
+      dg[i] = 2.f * res / (float)M;
+      sq += (double)res * (double)res;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sqpart[threadIdx.y] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y] = (sqpart[0] + sqpart[1]) + (sqpart[2] + sqpart[3]);
+}
+
+// out[c] = sum over the row blocks of part[blk][c], in order (a fixed tree over 256
+// threads of contiguous block ranges).
+__global__ void colsum_blocks_final_kernel(const double* part, int nblk, int cols, float* out) {
+  const int c = blockIdx.x;
+  __shared__ double red[256];
+  const int per = (nblk + 255) / 256;
+  double s = 0.0;
+  for (int k = threadIdx.x * per; k < min(nblk, (int)(threadIdx.x + 1) * per); ++k) s += part[(long)k * cols + c];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = (float)red[0];
+}
+
 // out[e] = sum_s parts[s * stride + e] (in split order), then optionally out[e] = val.
 __global__ void sum_splits_kernel(const float* parts, int splits, long stride, long n, float* out) {
   const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -155,19 +278,6 @@ __global__ void sum_splits_kernel(const float* parts, int splits, long stride, l
 
 // Column sums of X [rows][cols] in fixed order: out[c] = sum_r X[r][c] (one block per column).
 // Column sums of X [rows][cols] in two fixed-order passes (deterministic):
-// Compensated (Kahan) FP32 accumulation: the running sum s - c stays within a few
-// ulps of the exact sum whatever the number of terms, in FP32 instructions (FP64 is
-// a slow pipe on this GPU: per-element FP64 adds made these reductions FP64-bound).
-struct CompSum {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float v) {
-    const float y = __fsub_rn(v, c);
-    const float t = __fadd_rn(s, y);
-    c = __fsub_rn(__fsub_rn(t, s), y);
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
 
 // colsum_part_kernel: block (32 columns x 8 row lanes) per (column group, row chunk),
 // coalesced across columns; colsum_final_kernel adds the chunk partials in order.
@@ -452,9 +562,10 @@ cudaError_t trainer_alloc(crom_trainer* t) {
   t->edh = (float*)A((size_t)t->B * t->lens[0] * 4);
   t->edx = (float*)A((size_t)t->B * t->lens[0] * 4);
   t->ed1 = (float*)A((size_t)t->B * 32 * 4);
-  t->partial = (double*)A((size_t)blocks(N, 8) * 8);
+  t->partial = (double*)A((size_t)std::max<long>(blocks(N, 8), kEpiRowBlocks) * 8);
   t->loss_dev = (double*)A(8);
   t->red = (double*)A((size_t)kColChunks * std::max(std::max(w, 32), std::max(r, 7)) * 8);
+  t->colpart = (double*)A((size_t)kEpiRowBlocks * w * 8);
   for (void* p : t->owned)
     if (!p) return cudaErrorMemoryAllocation;
   cudaError_t e = cudaMemset(t->am, 0, o * 4);
@@ -474,7 +585,8 @@ void trainer_free(crom_trainer* t) {
 // strides is 1 (row-major or transposed storage).
 static cudaError_t gemm(crom_trainer* t, cudaStream_t s, int M, int N, int K, const float* A, long sai, long sak,
                         const float* B, long sbk, long sbj, float* C, long ldc, int epi, const float* bias,
-                        float* H, const float* Zp, float* split = nullptr) {
+                        float* H, const float* Zp, float* split = nullptr, bool* colpart_done = nullptr) {
+  if (colpart_done) *colpart_done = false;
   if (t->precision == CROM_PREC_TF32) {
     // Row-major C = A B is column-major C^T = B^T A^T: cuBLAS computes the N x M
     // column-major product op(B') op(A') with B' = B and A' = A viewed column-major.
@@ -496,8 +608,14 @@ static cudaError_t gemm(crom_trainer* t, cudaStream_t s, int M, int N, int K, co
       if (vec) epi_bias_elu4_kernel<<<vg, vb, 0, s>>>(C, M, N / 4, ldc, bias, H);
       else epi_bias_elu_kernel<<<blocks(n, 256), 256, 0, s>>>(C, M, N, ldc, bias, H);
     } else if (epi == kEpiTimesEluD) {
-      if (vec) epi_times_elud4_kernel<<<vg, vb, 0, s>>>(C, M, N / 4, ldc, Zp);
-      else epi_times_elud_kernel<<<blocks(n, 256), 256, 0, s>>>(C, M, N, ldc, Zp);
+      if (vec && colpart_done && N / 4 <= 64) {  // with the column sums of the result (one block column)
+        epi_times_elud4_colsum_kernel<<<dim3(1, kEpiRowBlocks), vb, 0, s>>>(C, M, N / 4, ldc, Zp, t->colpart);
+        *colpart_done = true;
+      } else if (vec) {
+        epi_times_elud4_kernel<<<vg, vb, 0, s>>>(C, M, N / 4, ldc, Zp);
+      } else {
+        epi_times_elud_kernel<<<blocks(n, 256), 256, 0, s>>>(C, M, N, ldc, Zp);
+      }
     }
     return cudaGetLastError();
   }
@@ -566,16 +684,29 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
   gather_kernel<<<blocks(N, 256), 256, 0, s>>>(snaps, pt_idx, coords, t->q, B, S, P, m, r, t->in0, t->target);
   const float* hin = t->in0;
   int kin = m + r;
+  // TF32 path: the output layer and loss are fused into the last hidden layer's epilogue
+  auto a16 = [](const void* ptr) { return ((uintptr_t)ptr & 15) == 0; };
+  const bool fuse_out = t->precision == CROM_PREC_TF32 && w % 4 == 0 && w / 4 <= 64 && a16(t->Z[L - 1]) &&
+                        a16(t->H[L - 1]) && a16(p + lay.dec_b[L - 1]) && a16(p + lay.dec_w[L]);
   for (int l = 0; l < L; ++l) {
-    e = gemm(t, s, (int)N, w, kin, hin, kin, 1, p + lay.dec_w[l], 1, kin, t->Z[l], w, kEpiBiasElu, p + lay.dec_b[l],
-             t->H[l], nullptr);
+    const bool out_here = fuse_out && l == L - 1;
+    e = gemm(t, s, (int)N, w, kin, hin, kin, 1, p + lay.dec_w[l], 1, kin, t->Z[l], w,
+             out_here ? kEpiStore : kEpiBiasElu, p + lay.dec_b[l], t->H[l], nullptr);
     if (e != cudaSuccess) return e;
+    if (out_here)
+      epi_bias_elu4_out_kernel<<<dim3(1, kEpiRowBlocks), dim3(64, 4), 0, s>>>(
+          t->Z[l], N, w / 4, w, p + lay.dec_b[l], t->H[l], p + lay.dec_w[L], p + lay.dec_b[L], t->target, t->dg,
+          t->partial);
     hin = t->H[l];
     kin = w;
   }
-  output_loss_kernel<<<blocks(N, 8), 256, 0, s>>>(t->H[L - 1], w, N, p + lay.dec_w[L], p + lay.dec_b[L], t->target,
-                                                   t->dg, t->partial);
-  loss_final_kernel<<<1, 1024, 0, s>>>(t->partial, (int)blocks(N, 8), N, loss_out ? loss_out : t->loss_dev);
+  if (fuse_out) {
+    loss_final_kernel<<<1, 1024, 0, s>>>(t->partial, kEpiRowBlocks, N, loss_out ? loss_out : t->loss_dev);
+  } else {
+    output_loss_kernel<<<blocks(N, 8), 256, 0, s>>>(t->H[L - 1], w, N, p + lay.dec_w[L], p + lay.dec_b[L], t->target,
+                                                     t->dg, t->partial);
+    loss_final_kernel<<<1, 1024, 0, s>>>(t->partial, (int)blocks(N, 8), N, loss_out ? loss_out : t->loss_dev);
+  }
   // ---- decoder reverse pass
   // output layer: gW_out[u] = sum_n dg[n] H_L[n][u], gb_out = sum dg
   e = gemm(t, s, 1, w, (int)N, t->dg, 0, 1, t->H[L - 1], w, 1, gr + lay.dec_w[L], w, kEpiStore, nullptr, nullptr,
@@ -583,12 +714,21 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
   if (e != cudaSuccess) return e;
   colsum(t, s, t->dg, N, 1, gr + lay.dec_b[L]);
   const float* wout = p + lay.dec_w[L];
-  if (w % 4 == 0 && N * (w / 4) < (1L << 31) && ((uintptr_t)wout & 15) == 0 && ((uintptr_t)t->Z[L - 1] & 15) == 0 &&
-      ((uintptr_t)t->delta & 15) == 0)
+  const bool vec_out = w % 4 == 0 && ((uintptr_t)wout & 15) == 0 && ((uintptr_t)t->Z[L - 1] & 15) == 0 &&
+                       ((uintptr_t)t->delta & 15) == 0;
+  // column sums of delta fused into the kernel that writes it (TF32 path), else a
+  // separate deterministic pass
+  bool have_part = false;
+  if (t->precision == CROM_PREC_TF32 && vec_out && w / 4 <= 64) {
+    out_delta4_colsum_kernel<<<dim3(1, kEpiRowBlocks), dim3(64, 4), 0, s>>>(t->dg, wout, t->Z[L - 1], N, w / 4,
+                                                                            t->delta, t->colpart);
+    have_part = true;
+  } else if (vec_out && N * (w / 4) < (1L << 31)) {
     out_delta4_kernel<<<blocks(N * (w / 4), 256), 256, 0, s>>>(t->dg, wout, t->Z[L - 1], w,
                                                                (unsigned)(N * (w / 4)), t->delta);
-  else
-    out_delta_kernel<<<blocks(N * w, 256), 256, 0, s>>>(t->dg, p + lay.dec_w[L], t->Z[L - 1], w, N, t->delta);
+  } else {
+    out_delta_kernel<<<blocks(N * w, 256), 256, 0, s>>>(t->dg, wout, t->Z[L - 1], w, N, t->delta);
+  }
   float* dcur = t->delta;
   float* dnext = t->delta2;
   for (int l = L - 1; l >= 0; --l) {
@@ -598,11 +738,15 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
     e = gemm(t, s, w, kprev, (int)N, dcur, 1, w, hprev, kprev, 1, gr + lay.dec_w[l], kprev, kEpiStore, nullptr,
              nullptr, nullptr, t->split);
     if (e != cudaSuccess) return e;
-    colsum(t, s, dcur, N, w, gr + lay.dec_b[l]);
+    if (have_part)
+      colsum_blocks_final_kernel<<<w, 256, 0, s>>>(t->colpart, kEpiRowBlocks, w, gr + lay.dec_b[l]);
+    else
+      colsum(t, s, dcur, N, w, gr + lay.dec_b[l]);
+    have_part = false;
     if (l > 0) {
       // delta_{l-1} = (delta_l W_l) * s'(Z_{l-1})
       e = gemm(t, s, (int)N, w, w, dcur, w, 1, p + lay.dec_w[l], w, 1, dnext, w, kEpiTimesEluD, nullptr, nullptr,
-               t->Z[l - 1]);
+               t->Z[l - 1], nullptr, &have_part);
     } else {
       // input gradient din = delta_1 W_1  [N][m + r]
       e = gemm(t, s, (int)N, m + r, w, dcur, w, 1, p + lay.dec_w[0], m + r, 1, t->din, m + r, kEpiStore, nullptr,
