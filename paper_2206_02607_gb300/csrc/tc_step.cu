@@ -616,7 +616,8 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
 // Samples 2 kS0 * t .. of GN iteration 0 (ns >= 1 of them, at most 2 kS0): two
 // forward tiles of kS0 samples (the second only if ns > kS0) into sample slots
 // 0..kS0-1 and kS0..2kS0-1, then one reverse pass and projection over all of them:
-// the four-channel forward pass needs narrow tiles to fit one N = 128 UMMA, the
+// the four-channel forward pass needs narrow tiles to fit the 32 hi columns of one
+// N = 64 UMMA, the
 // reverse pass does not.
 template <int kM>
 __device__ __forceinline__ bool run_pair(Lane& c, const StepParams& p, int o0, int t, int ns, float alpha, Own& o) {
