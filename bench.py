@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--n-codes", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fom-fields", type=int, default=512)
+    ap.add_argument("--tiles", default="auto",
+                    help="sample tiles of the tensor-core step: auto (measured by crom_autotune) or s0,s1 "
+                         "(fixed; profilers distort the autotuner's timings)")
     ap.add_argument("--only", default=None, choices=["step", "recon", "plain", "fom"],
                     help="run only one part (warmup + steps launches) for profiling; prints a short JSON line")
     return ap.parse_args()
@@ -269,8 +272,12 @@ def main():
                        gn_iters=w.gn_iters, max_samples=max_s, precision=prec)
 
     # ---- tile shape of the tensor-core step: measured on this batch (outside the timed region)
-    tile_s0, tile_s1, tile_ms = crom.crom_autotune(ctx, q, alpha, s_off, samples, status, dt=w.dt,
-                                                   gn_iters=w.gn_iters, max_samples=max_s)
+    if args.tiles == "auto":
+        tile_s0, tile_s1, tile_ms = crom.crom_autotune(ctx, q, alpha, s_off, samples, status, dt=w.dt,
+                                                       gn_iters=w.gn_iters, max_samples=max_s)
+    else:
+        crom.crom_set_step_tiles(ctx, *[int(v) for v in args.tiles.split(",")])
+        tile_s0, tile_s1, tile_ms = crom.crom_get_step_tiles(ctx)
 
     # ---- device-resident timing, L2 flushed before each timed step
     for _ in range(args.warmup):
@@ -497,7 +504,7 @@ def main():
             "config": {"workload": WORKLOAD, "global_batch": world * w.n_inst, "samples_per_step": int(w.sizes.sum()),
                        "parallelism": f"instances sharded, {w.n_inst} per GPU" if world > 1 else "single GPU",
                        "l2": "flushed (256 MB write) before every timed step",
-                       "tiles": {"s0": tile_s0, "s1": tile_s1, "autotuned": True,
+                       "tiles": {"s0": tile_s0, "s1": tile_s1, "autotuned": args.tiles == "auto",
                                  "ms_per_step_large_small_s1": [round(tile_ms[0], 4), round(tile_ms[1], 4)]}},
             "status_all_ok": bool(np.all(st == 0)),
             "accuracy_vs_fp64_oracle": acc,
