@@ -92,6 +92,31 @@ def test_objective_never_increases(c):
         assert _phi(dec, Y, q1[i], w.q0[i], df) <= _phi(dec, Y, ref, w.q0[i], df) * 1.05 + 1e-12 * phi_n
 
 
+def test_objective_never_increases_r15(c):
+    """r = 15: 120 + 15 normal-equation entries plus rho^T rho exceed a group's 128
+    threads, so the line search's objective is owned by a thread's second entry; the
+    statuses match the oracle's and the objective never increases."""
+    spec = gen.DecoderSpec(2, 15, 128, 5)
+    params = gen.xavier_decoder(spec, seed=21, bias_std=0.1, bf16_exact=True)
+    rng = np.random.default_rng(21)
+    sizes = [40, 77, 150, 220]
+    samples = np.concatenate([gen.interior_nodes_2d(128, s, rng) for s in sizes])
+    dt = 0.1
+    w = gen.StepWorkload("r15", spec, params, rng.standard_normal((len(sizes), 15)) * 0.5,
+                         rng.uniform(0.5, 2.0, len(sizes)).astype(np.float32), gen.ragged_offsets(sizes), samples,
+                         dt, 3, 1)
+    q1, st = _run(c, w, dt, 3, 8)
+    dec = O.MLPDecoder(w.params, 2)
+    for i in range(w.n_inst):
+        Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
+        _, rst = O.crom_step(dec, w.q0[i], Y, dt, 3, alpha=float(w.alpha[i]), line_search=8)
+        assert st[i] == rst == 0
+        ev = dec(Y, w.q0[i])
+        df = dt * float(w.alpha[i]) * ev.lap
+        phi_n = 0.5 * float(df @ df)
+        assert _phi(dec, Y, q1[i], w.q0[i], df) <= phi_n * (1 + 1e-6), i
+
+
 def test_line_search_argument_checks(c):
     import torch
     w = gen.heat2d_batched(n_inst=2, m_lo=20, m_hi=30)
