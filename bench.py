@@ -339,14 +339,17 @@ def main():
         hq_out.copy_(dq, non_blocking=True); hst.copy_(status, non_blocking=True)
         torch.cuda.current_stream().synchronize()
 
-    for _ in range(2):
+    # wall-clock timing of host-synchronised steps: at least 100 of them, so that a
+    # host-side hiccup of a few ms does not dominate a short run
+    n_e2e = max(args.steps, 100)
+    for _ in range(5):
         e2e_step()
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(n_e2e):
         e2e_step()
     barrier()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
     e2e_value = world * w.n_inst / (e2e_ms * 1e-3)
 
     # ---- kernel-only duration of the step kernel for the roofline (same stream)
@@ -541,7 +544,7 @@ def main():
                                  "dram read+write bytes per launch from one ncu capture of this kernel at this "
                                  "workload"},
             "e2e": {"value": e2e_value, "unit": "instance-steps/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
+                    "d2h_bytes_per_step": int(d2h), "steps": n_e2e},
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
