@@ -183,3 +183,36 @@ def test_marching_kernels_match_unaligned_fallback(c, kind):
     fast, slow = go(0), go(1)
     assert np.all(np.isfinite(fast)) and np.all(np.isfinite(slow))
     assert rel_l2(fast, slow) < 1e-6
+
+
+@pytest.mark.parametrize("kind", ["advdiff", "heat"])
+def test_bench_size_fields_sampled(c, kind):
+    """The bench's full-order launches (512 periodic 256^2 fields with face velocities,
+    1024 zero-flux 256^2 fields), two steps; four fields (first, last, two inside) are
+    recomputed by the oracle and every value of every field must be finite."""
+    import torch
+    n = 256
+    nb = 512 if kind == "advdiff" else 1024
+    rng = np.random.default_rng(0)
+    u0 = rng.uniform(0, 1, size=(nb, n, n)).astype(np.float32)
+    u = dev(u0, torch.float32)
+    tmp = torch.empty_like(u)
+    if kind == "advdiff":
+        ax = rng.uniform(-0.5, 0.5, size=(nb, n, n)).astype(np.float32)
+        ay = rng.uniform(-0.5, 0.5, size=(nb, n, n)).astype(np.float32)
+        nu, dt = 5e-3, 2.5e-5
+        c.crom_fom_step(c.CROM_FOM_ADVDIFF2D_PERIODIC, u, tmp, torch.full((nb,), nu, device="cuda"), dt=dt, n_steps=2,
+                        ax=dev(ax, torch.float32), ay=dev(ay, torch.float32))
+    else:
+        nu, dt = 1.0, (1 / (n - 1)) ** 2 / 8
+        c.crom_fom_step(c.CROM_FOM_HEAT2D_NEUMANN, u, tmp, torch.full((nb,), nu, device="cuda"), dt=dt, n_steps=2)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(u).all().item())
+    for b in (0, 1, nb // 2 + 3, nb - 1):
+        ref = u0[b].astype(np.float64)
+        for _ in range(2):
+            if kind == "advdiff":
+                ref = O.fom_advdiff2d_step(ref, ax[b].astype(np.float64), ay[b].astype(np.float64), nu, dt)
+            else:
+                ref = O.fom_heat2d_neumann_step(ref, dt, nu)
+        assert rel_l2(u[b].cpu().numpy().astype(np.float64), ref) < 1e-6, b
