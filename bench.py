@@ -320,33 +320,21 @@ def main():
             incs.append(np.linalg.norm((qg[i] - w.q0[i]) - (ref - w.q0[i])) / np.linalg.norm(ref - w.q0[i]))
         acc = {"q_rel_l2_max": float(max(errs)), "increment_rel_l2_max": float(max(incs)), "instances": 6}
 
-    # ---- end to end through the C ABI with pinned host buffers: the step's inputs
-    # packed in one pinned staging buffer (q, status slot, alpha, offsets, samples at
-    # 256-byte aligned offsets), one host-to-device copy per step, and one
-    # device-to-host copy of the contiguous (q, status) result
-    parts = [np.ascontiguousarray(w.q0, np.float64), np.zeros(w.n_inst, np.int32),
-             np.ascontiguousarray(w.alpha, np.float32), np.ascontiguousarray(w.s_off, np.int32),
-             np.ascontiguousarray(w.samples, np.float32)]
-    offs, tot = [], 0
-    for a in parts:
-        offs.append(tot)
-        tot += (a.nbytes + 255) // 256 * 256
-    h_in = torch.empty(tot, dtype=torch.uint8).pin_memory()
-    for a, o in zip(parts, offs):
-        h_in[o:o + a.nbytes].copy_(torch.from_numpy(a.view(np.uint8).reshape(-1)))
-    d_in = torch.empty(tot, dtype=torch.uint8, device="cuda")
-    views = [d_in[o:o + a.nbytes].view(torch.from_numpy(a[:0]).dtype).view(a.shape) for a, o in zip(parts, offs)]
-    dq, dst_e2e, da, do, ds = views
-    res_bytes = offs[1] + parts[1].nbytes                  # q, padding, status
-    h_out = torch.empty(res_bytes, dtype=torch.uint8).pin_memory()
-    h2d, d2h = tot, res_bytes
+    # ---- end to end through the C ABI on host arrays (crom_step_host: the library
+    # copies the pinned inputs in, steps, copies q and status out and synchronises)
+    hq0 = torch.tensor(w.q0, dtype=torch.float64)
+    hq = hq0.clone().pin_memory()
+    ha = torch.tensor(w.alpha).pin_memory()
+    ho = torch.tensor(w.s_off).pin_memory()
+    hs = torch.tensor(w.samples).pin_memory()
+    hst = torch.empty(w.n_inst, dtype=torch.int32).pin_memory()
+    h2d = hq.numel() * 8 + ha.numel() * 4 + ho.numel() * 4 + hs.numel() * 4
+    d2h = hq.numel() * 8 + hst.numel() * 4
 
     def e2e_step():
-        d_in.copy_(h_in, non_blocking=True)
-        crom.crom_step(ctx, dq, da, do, ds, dst_e2e, dt=w.dt, gn_iters=w.gn_iters, max_samples=max_s,
-                       precision=crom.CROM_PREC_BF16X2)
-        h_out.copy_(d_in[:res_bytes], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        hq.copy_(hq0)  # every step starts from the same state
+        crom.crom_step_host(ctx, hq, ha, ho, hs, hst, dt=w.dt, gn_iters=w.gn_iters, max_samples=max_s,
+                            precision=crom.CROM_PREC_BF16X2)
 
     # wall-clock timing of host-synchronised steps: at least 100 of them, so that a
     # host-side hiccup of a few ms does not dominate a short run
@@ -359,6 +347,7 @@ def main():
         e2e_step()
     barrier()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
+    e2e_ok = bool((hst.numpy() == 0).all())
     e2e_value = world * w.n_inst / (e2e_ms * 1e-3)
 
     # ---- kernel-only duration of the step kernel for the roofline (same stream)
@@ -553,7 +542,8 @@ def main():
                                  "dram read+write bytes per launch from one ncu capture of this kernel at this "
                                  "workload"},
             "e2e": {"value": e2e_value, "unit": "instance-steps/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h), "steps": n_e2e},
+                    "d2h_bytes_per_step": int(d2h), "steps": n_e2e, "status_all_ok": e2e_ok,
+                    "call": "crom_step_host (pinned host arrays; copies, step and synchronisation inside the call)"},
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,

@@ -226,6 +226,21 @@ int crom_autotune(crom_ctx* ctx, const crom_step_desc* step, int n_inst, const d
                   const float* vel, const int* s_off, const float* samples, int n_samples, int max_samples,
                   int* status, crom_stream stream);
 
+/* crom_step on host arrays (the same step, paper §4, Algorithm 3): q, alpha, vel,
+ * s_off, samples and status are host pointers with the layouts of crom_step.  The
+ * call checks s_off on the host (starts at 0, never decreases, ends at n_samples),
+ * copies the inputs into a device staging buffer owned by the context (allocated
+ * or grown on first use, freed by crom_destroy), runs crom_step on `stream`,
+ * copies q and status back and waits for the stream before returning, so q and
+ * status are valid when it returns.  Pinned host memory (cudaHostAlloc,
+ * torch.Tensor.pin_memory) makes the copies asynchronous DMA; pageable memory
+ * works too.  The staging buffer is shared by the context's calls: calls on one
+ * context must not run concurrently from several host threads.  The call synchronises the stream: it cannot be recorded into a CUDA
+ * graph.  Status codes as crom_step. */
+int crom_step_host(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_inst, double* q,
+                   const float* alpha, const float* vel, const int* s_off, const float* samples, int n_samples,
+                   int max_samples, int* status, crom_stream stream);
+
 /* crom_step with precision CROM_PREC_FP32, for callers that cannot allocate
  * device memory when they step: host applications or frameworks that own the
  * device's memory through their own pool and forbid direct cudaMalloc/cudaFree by

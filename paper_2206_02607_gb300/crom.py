@@ -45,7 +45,8 @@ CROM_FOM_HEAT1D_DIRICHLET_FIELD = 3
 CROM_FOM_HEAT2D_NEUMANN_FIELD = 4
 
 EXPORTED = ("crom_version", "crom_last_error", "crom_create", "crom_destroy", "crom_set_weights",
-            "crom_decode", "crom_step", "crom_rollout", "crom_step_noalloc", "crom_fom_step", "crom_trainer_create",
+            "crom_decode", "crom_step", "crom_step_host", "crom_rollout", "crom_step_noalloc", "crom_fom_step",
+            "crom_trainer_create",
             "crom_trainer_destroy", "crom_trainer_param_count", "crom_trainer_set_params",
             "crom_trainer_get_params", "crom_trainer_get_grads", "crom_train_step", "crom_encode",
             "crom_reconstruct", "crom_robust_samples", "crom_tangent_velocity", "crom_trainer_set_precision",
@@ -82,6 +83,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.crom_decode.argtypes = [vp, i, vp, vp, vp, i, u, vp, vp]
     lib.crom_step.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, i, vp, vp, vp, vp, vp, i, i, vp, vp]
     lib.crom_step_noalloc.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, vp, vp, vp, vp, vp, i, i, vp, vp]
+    lib.crom_step_host.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, i, vp, vp, vp, vp, vp, i, i, vp, vp]
     lib.crom_rollout.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, i, i, vp, vp, vp, vp, vp, i, i, vp, vp]
     lib.crom_fom_step.argtypes = [i, i, i, i, vp, vp, vp, d, i, vp, vp, vp]
     lib.crom_trainer_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(crom_decoder_desc), i, i, i, i]
@@ -200,6 +202,29 @@ def crom_step(ctx: CromContext, q, alpha, s_off, samples, status, *, dt: float, 
     _check(_LIB.crom_step(ctx.handle, ctypes.byref(desc), precision, q.shape[0], _ptr(q), _ptr(alpha),
                           _ptr(vel), _ptr(s_off), _ptr(samples), samples.shape[0], max_samples, _ptr(status),
                           _stream(stream)))
+
+
+def _need_host(t, dtype, name):
+    import torch
+    if t is None:
+        return
+    if t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous host (CPU) tensor of {dtype}")
+
+
+def crom_step_host(ctx: CromContext, q, alpha, s_off, samples, status, *, dt: float, gn_iters: int,
+                   max_samples: int, pde: int = CROM_PDE_HEAT, vel=None, precision: int = CROM_PREC_FP32,
+                   coef_per_sample: bool = False, line_search: int = 0, stream=None):
+    """crom_step on host (CPU, preferably pinned) tensors; q and status are updated in
+    place when the call returns (the library stages the copies and synchronises)."""
+    import torch
+    _need_host(q, torch.float64, "q"); _need_host(alpha, torch.float32, "alpha")
+    _need_host(s_off, torch.int32, "s_off"); _need_host(samples, torch.float32, "samples")
+    _need_host(status, torch.int32, "status"); _need_host(vel, torch.float32, "vel")
+    desc = crom_step_desc(pde, gn_iters, dt, int(bool(coef_per_sample)), int(line_search))
+    _check(_LIB.crom_step_host(ctx.handle, ctypes.byref(desc), precision, q.shape[0], _ptr(q), _ptr(alpha),
+                               _ptr(vel), _ptr(s_off), _ptr(samples), samples.shape[0], max_samples, _ptr(status),
+                               _stream(stream)))
 
 
 def crom_rollout(ctx: CromContext, q, alpha, s_off, samples, status, *, n_steps: int, dt: float, gn_iters: int,

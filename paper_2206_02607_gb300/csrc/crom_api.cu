@@ -158,6 +158,7 @@ int crom_destroy(crom_ctx* ctx) {
     cudaFree(ctx->targets);
     cudaFree(ctx->qbase);
     cudaFree(ctx->tangent);
+    cudaFree(ctx->host_stage);
     cudaFree(ctx->order);
     cudaFree(ctx->queue);
     if (ctx->rollout_exec) cudaGraphExecDestroy(ctx->rollout_exec);
@@ -336,6 +337,68 @@ int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_in
     return fail(CROM_ERR_UNSUPPORTED, "crom_step: precision not available for the step");
   }
   if (e != cudaSuccess) return cuda_fail(e, "crom_step");
+  return CROM_OK;
+}
+
+int crom_step_host(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_inst, double* q,
+                   const float* alpha, const float* vel, const int* s_off, const float* samples, int n_samples,
+                   int max_samples, int* status, crom_stream stream) {
+  const char* fn = "crom_step_host";
+  if (!ctx || !step) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": null argument");
+  if (n_inst < 0 || n_samples < 0) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": negative size");
+  if (n_inst == 0) return CROM_OK;
+  if (!q || !alpha || !s_off || !status || (n_samples > 0 && !samples))
+    return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": null array");
+  if (step->pde == CROM_PDE_ADVDIFF && !vel)
+    return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": advection needs vel");
+  // the offsets are on the host here, so they can be checked before anything runs
+  if (s_off[0] != 0 || s_off[n_inst] != n_samples)
+    return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": s_off must start at 0 and end at n_samples");
+  for (int i = 0; i < n_inst; ++i)
+    if (s_off[i + 1] < s_off[i]) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": s_off must not decrease");
+  const int m = ctx->desc.m, r = ctx->desc.r;
+  const size_t n_alpha = step->coef_per_sample ? (size_t)n_samples : (size_t)n_inst;
+  // packed staging: q, status, alpha, offsets, samples, velocities at 256-byte offsets
+  const size_t sizes[6] = {(size_t)n_inst * r * sizeof(double), (size_t)n_inst * sizeof(int), n_alpha * sizeof(float),
+                           (size_t)(n_inst + 1) * sizeof(int), (size_t)n_samples * m * sizeof(float),
+                           step->pde == CROM_PDE_ADVDIFF ? (size_t)n_samples * m * sizeof(float) : 0};
+  size_t off[6], total = 0;
+  for (int k = 0; k < 6; ++k) {
+    off[k] = total;
+    total += (sizes[k] + 255) / 256 * 256;
+  }
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (total > ctx->host_stage_cap) {
+    e = cudaStreamSynchronize(s);  // the previous staging buffer may still be in use on this stream
+    if (e == cudaSuccess) {
+      cudaFree(ctx->host_stage);
+      ctx->host_stage = nullptr;
+      ctx->host_stage_cap = 0;
+      e = cudaMalloc(&ctx->host_stage, total);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, fn);
+    ctx->host_stage_cap = total;
+  }
+  uint8_t* d = ctx->host_stage;
+  const void* src[6] = {q, nullptr, alpha, s_off, samples, vel};
+  for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+    if (src[k] && sizes[k]) e = cudaMemcpyAsync(d + off[k], src[k], sizes[k], cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, fn);
+  const int rc = crom_step(ctx, step, precision, n_inst, reinterpret_cast<double*>(d + off[0]),
+                           reinterpret_cast<const float*>(d + off[2]),
+                           sizes[5] ? reinterpret_cast<const float*>(d + off[5]) : nullptr,
+                           reinterpret_cast<const int*>(d + off[3]), reinterpret_cast<const float*>(d + off[4]),
+                           n_samples, max_samples, reinterpret_cast<int*>(d + off[1]), stream);
+  if (rc != CROM_OK) {
+    cudaStreamSynchronize(s);  // the input copies read the caller's arrays: finish them before returning
+    return rc;
+  }
+  e = cudaMemcpyAsync(q, d + off[0], sizes[0], cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(status, d + off[1], sizes[1], cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, fn);
   return CROM_OK;
 }
 

@@ -61,6 +61,8 @@ struct crom_ctx {
   size_t qbase_cap = 0;
   float* tangent = nullptr;    // [r][n_pts]: dg/dq rows for the tangent velocity
   size_t tangent_cap = 0;
+  uint8_t* host_stage = nullptr;  // crom_step_host: device copies of the caller's host arrays
+  size_t host_stage_cap = 0;
   // Scratch of the tensor-core step: instance order (largest |M_i| first) and the
   // queue counter / timeout flag.
   int* order = nullptr;
