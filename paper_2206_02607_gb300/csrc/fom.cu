@@ -148,10 +148,12 @@ __global__ void __launch_bounds__(32 * kWarps) advdiff2d_march_kernel(
 // owns 128 consecutive columns and a strip of kRows rows; within a lane the column
 // neighbours are the adjacent components, across lanes they come from a shuffle of
 // the first / last component, and the two columns beyond the warp from memory.
-// Requires n % 128 == 0, n % (kRows4 * kWarps4) == 0 and 16-byte aligned arrays.
+// kRowsA rows per warp.  Requires n % 128 == 0, n % (kRowsA * kWarps4) == 0 and
+// 16-byte aligned arrays.
 constexpr int kRows4 = 32, kWarps4 = 4;
 inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 __device__ __forceinline__ float upwind(float a, float up, float down) { return a * (a > 0.f ? up : down); }
+template <int kRowsA>
 __global__ void __launch_bounds__(32 * kWarps4) advdiff2d_march4_kernel(
     const float* __restrict__ u, float* __restrict__ out, const float* __restrict__ ax,
     const float* __restrict__ ay, const float* __restrict__ coef, int n, float dt, float inv_h, float inv_h2) {
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(32 * kWarps4) advdiff2d_march4_kernel(
   const int lane = threadIdx.x;
   const int j0 = blockIdx.x * 128;
   const int j = j0 + 4 * lane;
-  const int i0 = (blockIdx.y * kWarps4 + threadIdx.y) * kRows4;
+  const int i0 = (blockIdx.y * kWarps4 + threadIdx.y) * kRowsA;
   const size_t base = (size_t)b * n * n;
   const float* ub = u + base;
   const float* axb = ax + base;
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(32 * kWarps4) advdiff2d_march4_kernel(
   float4 c = ld4(ub, i0);
   float4 a_l = ld4(axb, im0);
 #pragma unroll 4
-  for (int k = 0; k < kRows4; ++k) {
+  for (int k = 0; k < kRowsA; ++k) {
     const int i = i0 + k;
     const int ip = i == n - 1 ? 0 : i + 1;
     const float4 uip = ld4(ub, ip);
@@ -219,9 +221,11 @@ __global__ void __launch_bounds__(32 * kWarps4) advdiff2d_march4_kernel(
 // as above: the mirror ghosts are u_{-1} = u_1 and u_n = u_{n-2} in both directions
 // (row 0 takes row 1 as its upper neighbour, row n-1 row n-2 as its lower one; in
 // column 0 and n-1 the lane's own component j = 1 or n-2 is the missing neighbour).
-// kField: the coefficient is read per node (float4), else per field.
-// Requires n % 128 == 0, n % (kRows4 * kWarps4) == 0 and 16-byte aligned arrays.
-template <bool kField>
+// kField: the coefficient is read per node (float4), else per field.  kRowsH rows
+// per warp (64 where the side allows, so that a batch of 256^2 fields needs fewer
+// blocks than fit on the GPU at once).
+// Requires n % 128 == 0, n % (kRowsH * kWarps4) == 0 and 16-byte aligned arrays.
+template <bool kField, int kRowsH>
 __global__ void __launch_bounds__(32 * kWarps4) heat2d_march4_kernel(const float* __restrict__ u,
                                                                     float* __restrict__ out,
                                                                     const float* __restrict__ coef, int n,
@@ -230,7 +234,7 @@ __global__ void __launch_bounds__(32 * kWarps4) heat2d_march4_kernel(const float
   const int lane = threadIdx.x;
   const int j0 = blockIdx.x * 128;
   const int j = j0 + 4 * lane;
-  const int i0 = (blockIdx.y * kWarps4 + threadIdx.y) * kRows4;
+  const int i0 = (blockIdx.y * kWarps4 + threadIdx.y) * kRowsH;
   const size_t base = (size_t)b * n * n;
   const float* ub = u + base;
   float* ob = out + base;
@@ -240,7 +244,7 @@ __global__ void __launch_bounds__(32 * kWarps4) heat2d_march4_kernel(const float
   float4 uim = ld4(ub, i0 == 0 ? 1 : i0 - 1);
   float4 c = ld4(ub, i0);
 #pragma unroll 4
-  for (int k = 0; k < kRows4; ++k) {
+  for (int k = 0; k < kRowsH; ++k) {
     const int i = i0 + k;
     const float4 uip = ld4(ub, i == n - 1 ? n - 2 : i + 1);
     // halo columns: lane 0 needs column j0 - 1, lane 31 column j0 + 128 (inside the field)
@@ -289,13 +293,21 @@ cudaError_t launch_fom(int kind, int n_batch, int nx, int ny, const float* coef,
     } else if (kind == CROM_FOM_HEAT2D_NEUMANN || kind == CROM_FOM_HEAT2D_NEUMANN_FIELD) {
       const double h = 1.0 / (nx - 1);
       const bool field = kind == CROM_FOM_HEAT2D_NEUMANN_FIELD;
-      if (nx % 128 == 0 && nx % (kRows4 * kWarps4) == 0 && aligned16(src) && aligned16(dst) &&
+      const float ro = (float)(dt / (h * h));
+      if (nx % 128 == 0 && nx % (16 * kWarps4) == 0 && aligned16(src) && aligned16(dst) &&
           (!field || aligned16(coef))) {
+        dim3 grid4(nx / 128, nx / (16 * kWarps4), n_batch);
+        if (field)
+          heat2d_march4_kernel<true, 16><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, ro);
+        else
+          heat2d_march4_kernel<false, 16><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, ro);
+      } else if (nx % 128 == 0 && nx % (kRows4 * kWarps4) == 0 && aligned16(src) && aligned16(dst) &&
+                 (!field || aligned16(coef))) {
         dim3 grid4(nx / 128, nx / (kRows4 * kWarps4), n_batch);
         if (field)
-          heat2d_march4_kernel<true><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, (float)(dt / (h * h)));
+          heat2d_march4_kernel<true, kRows4><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, ro);
         else
-          heat2d_march4_kernel<false><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, (float)(dt / (h * h)));
+          heat2d_march4_kernel<false, kRows4><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, ro);
       } else {
         dim3 grid((nx + 31) / 32, (nx + 7) / 8, n_batch);
         if (field)
@@ -305,11 +317,11 @@ cudaError_t launch_fom(int kind, int n_batch, int nx, int ny, const float* coef,
       }
     } else {
       const double h = 1.0 / nx;
-      if (nx % 128 == 0 && nx % (kRows4 * kWarps4) == 0 && aligned16(src) && aligned16(dst) && aligned16(ax) &&
+      if (nx % 128 == 0 && nx % (16 * kWarps4) == 0 && aligned16(src) && aligned16(dst) && aligned16(ax) &&
           aligned16(ay)) {
-        dim3 grid(nx / 128, nx / (kRows4 * kWarps4), n_batch);
-        advdiff2d_march4_kernel<<<grid, dim3(32, kWarps4), 0, s>>>(src, dst, ax, ay, coef, nx, (float)dt,
-                                                                   (float)(1.0 / h), (float)(1.0 / (h * h)));
+        dim3 grid(nx / 128, nx / (16 * kWarps4), n_batch);
+        advdiff2d_march4_kernel<16><<<grid, dim3(32, kWarps4), 0, s>>>(src, dst, ax, ay, coef, nx, (float)dt,
+                                                                       (float)(1.0 / h), (float)(1.0 / (h * h)));
       } else if (nx % 32 == 0 && nx % (kRows * kWarps) == 0) {
         dim3 grid(nx / 32, nx / (kRows * kWarps), n_batch);
         advdiff2d_march_kernel<<<grid, dim3(32, kWarps), 0, s>>>(src, dst, ax, ay, coef, nx, (float)dt,
