@@ -294,13 +294,13 @@ cudaError_t launch_fom(int kind, int n_batch, int nx, int ny, const float* coef,
       const double h = 1.0 / (nx - 1);
       const bool field = kind == CROM_FOM_HEAT2D_NEUMANN_FIELD;
       const float ro = (float)(dt / (h * h));
-      if (nx % 128 == 0 && nx % (8 * kWarps4) == 0 && aligned16(src) && aligned16(dst) &&
+      if (nx % 128 == 0 && nx % (4 * kWarps4) == 0 && aligned16(src) && aligned16(dst) &&
           (!field || aligned16(coef))) {
-        dim3 grid4(nx / 128, nx / (8 * kWarps4), n_batch);
+        dim3 grid4(nx / 128, nx / (4 * kWarps4), n_batch);
         if (field)
-          heat2d_march4_kernel<true, 8><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, ro);
+          heat2d_march4_kernel<true, 4><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, ro);
         else
-          heat2d_march4_kernel<false, 8><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, ro);
+          heat2d_march4_kernel<false, 4><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, ro);
       } else if (nx % 128 == 0 && nx % (kRows4 * kWarps4) == 0 && aligned16(src) && aligned16(dst) &&
                  (!field || aligned16(coef))) {
         dim3 grid4(nx / 128, nx / (kRows4 * kWarps4), n_batch);
@@ -317,10 +317,10 @@ cudaError_t launch_fom(int kind, int n_batch, int nx, int ny, const float* coef,
       }
     } else {
       const double h = 1.0 / nx;
-      if (nx % 128 == 0 && nx % (8 * kWarps4) == 0 && aligned16(src) && aligned16(dst) && aligned16(ax) &&
+      if (nx % 128 == 0 && nx % (4 * kWarps4) == 0 && aligned16(src) && aligned16(dst) && aligned16(ax) &&
           aligned16(ay)) {
-        dim3 grid(nx / 128, nx / (8 * kWarps4), n_batch);
-        advdiff2d_march4_kernel<8><<<grid, dim3(32, kWarps4), 0, s>>>(src, dst, ax, ay, coef, nx, (float)dt,
+        dim3 grid(nx / 128, nx / (4 * kWarps4), n_batch);
+        advdiff2d_march4_kernel<4><<<grid, dim3(32, kWarps4), 0, s>>>(src, dst, ax, ay, coef, nx, (float)dt,
                                                                        (float)(1.0 / h), (float)(1.0 / (h * h)));
       } else if (nx % 32 == 0 && nx % (kRows * kWarps) == 0) {
         dim3 grid(nx / 32, nx / (kRows * kWarps), n_batch);
