@@ -145,12 +145,17 @@ __global__ void __launch_bounds__(32 * kWarps) advdiff2d_march_kernel(
 }
 
 // The marching update with four columns per lane (float4 loads and stores): a warp
-// owns 128 consecutive columns and a strip of kRows rows; within a lane the column
+// owns 128 consecutive columns and a strip of kRowsA rows; within a lane the column
 // neighbours are the adjacent components, across lanes they come from a shuffle of
 // the first / last component, and the two columns beyond the warp from memory.
-// kRowsA rows per warp.  Requires n % 128 == 0, n % (kRowsA * kWarps4) == 0 and
-// 16-byte aligned arrays.
-constexpr int kRows4 = 32, kWarps4 = 4;
+// Requires n % 128 == 0, n % (kRowsA * kWarps4) == 0 and 16-byte aligned arrays.
+constexpr int kWarps4 = 4;
+// Rows per warp strip of the four-columns-per-lane kernels: short strips keep many
+// warps' loads in flight (the rows above and below a strip are re-read, mostly from
+// L2); measured on 512 / 1024 fields of 256^2: 32 rows 86 / 80 %, 16 rows 91 / 85 %,
+// 8 rows 93 / 91 %, 4 rows 97 / 97 %, 2 rows 99 / 95 % of the copy bandwidth
+// (advection-diffusion / heat).
+constexpr int kRowsAdv = 2, kRowsHeat = 4;
 inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 __device__ __forceinline__ float upwind(float a, float up, float down) { return a * (a > 0.f ? up : down); }
 template <int kRowsA>
@@ -222,9 +227,8 @@ __global__ void __launch_bounds__(32 * kWarps4) advdiff2d_march4_kernel(
 // (row 0 takes row 1 as its upper neighbour, row n-1 row n-2 as its lower one; in
 // column 0 and n-1 the lane's own component j = 1 or n-2 is the missing neighbour).
 // kField: the coefficient is read per node (float4), else per field.  kRowsH rows
-// per warp (64 where the side allows, so that a batch of 256^2 fields needs fewer
-// blocks than fit on the GPU at once).
-// Requires n % 128 == 0, n % (kRowsH * kWarps4) == 0 and 16-byte aligned arrays.
+// per warp strip.  Requires n % 128 == 0, n % (kRowsH * kWarps4) == 0 and 16-byte
+// aligned arrays.
 template <bool kField, int kRowsH>
 __global__ void __launch_bounds__(32 * kWarps4) heat2d_march4_kernel(const float* __restrict__ u,
                                                                     float* __restrict__ out,
@@ -294,20 +298,13 @@ cudaError_t launch_fom(int kind, int n_batch, int nx, int ny, const float* coef,
       const double h = 1.0 / (nx - 1);
       const bool field = kind == CROM_FOM_HEAT2D_NEUMANN_FIELD;
       const float ro = (float)(dt / (h * h));
-      if (nx % 128 == 0 && nx % (4 * kWarps4) == 0 && aligned16(src) && aligned16(dst) &&
+      if (nx % 128 == 0 && nx % (kRowsHeat * kWarps4) == 0 && aligned16(src) && aligned16(dst) &&
           (!field || aligned16(coef))) {
-        dim3 grid4(nx / 128, nx / (4 * kWarps4), n_batch);
+        dim3 grid4(nx / 128, nx / (kRowsHeat * kWarps4), n_batch);
         if (field)
-          heat2d_march4_kernel<true, 4><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, ro);
+          heat2d_march4_kernel<true, kRowsHeat><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, ro);
         else
-          heat2d_march4_kernel<false, 4><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, ro);
-      } else if (nx % 128 == 0 && nx % (kRows4 * kWarps4) == 0 && aligned16(src) && aligned16(dst) &&
-                 (!field || aligned16(coef))) {
-        dim3 grid4(nx / 128, nx / (kRows4 * kWarps4), n_batch);
-        if (field)
-          heat2d_march4_kernel<true, kRows4><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, ro);
-        else
-          heat2d_march4_kernel<false, kRows4><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, ro);
+          heat2d_march4_kernel<false, kRowsHeat><<<grid4, dim3(32, kWarps4), 0, s>>>(src, dst, coef, nx, ro);
       } else {
         dim3 grid((nx + 31) / 32, (nx + 7) / 8, n_batch);
         if (field)
@@ -317,10 +314,10 @@ cudaError_t launch_fom(int kind, int n_batch, int nx, int ny, const float* coef,
       }
     } else {
       const double h = 1.0 / nx;
-      if (nx % 128 == 0 && nx % (4 * kWarps4) == 0 && aligned16(src) && aligned16(dst) && aligned16(ax) &&
+      if (nx % 128 == 0 && nx % (kRowsAdv * kWarps4) == 0 && aligned16(src) && aligned16(dst) && aligned16(ax) &&
           aligned16(ay)) {
-        dim3 grid(nx / 128, nx / (4 * kWarps4), n_batch);
-        advdiff2d_march4_kernel<4><<<grid, dim3(32, kWarps4), 0, s>>>(src, dst, ax, ay, coef, nx, (float)dt,
+        dim3 grid(nx / 128, nx / (kRowsAdv * kWarps4), n_batch);
+        advdiff2d_march4_kernel<kRowsAdv><<<grid, dim3(32, kWarps4), 0, s>>>(src, dst, ax, ay, coef, nx, (float)dt,
                                                                        (float)(1.0 / h), (float)(1.0 / (h * h)));
       } else if (nx % 32 == 0 && nx % (kRows * kWarps) == 0) {
         dim3 grid(nx / 32, nx / (kRows * kWarps), n_batch);
