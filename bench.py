@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--tiles", default="auto",
                     help="sample tiles of the tensor-core step: auto (measured by crom_autotune) or s0,s1 "
                          "(fixed; profilers distort the autotuner's timings)")
-    ap.add_argument("--only", default=None, choices=["step", "recon", "plain", "fom"],
+    ap.add_argument("--only", default=None, choices=["step", "recon", "plain", "fom", "heat"],
                     help="run only one part (warmup + steps launches) for profiling; prints a short JSON line")
     return ap.parse_args()
 
@@ -95,6 +95,16 @@ def run_only(args):
         crom.crom_fom_step(crom.CROM_FOM_ADVDIFF2D_PERIODIC, u, tmp, nu, dt=2.5e-5, n_steps=n, ax=ax, ay=ay)
         torch.cuda.synchronize()
         print(json.dumps({"only": "fom", "fields": nb, "nodes": nn * nn, "steps": n}))
+        return
+    elif args.only == "heat":
+        nb, nn = args.fom_fields, 256
+        rng = np.random.default_rng(0)
+        u = torch.tensor(rng.uniform(0, 1, size=(nb, nn, nn)).astype(np.float32), device="cuda")
+        tmp = torch.empty_like(u)
+        al = torch.full((nb,), 1.0, dtype=torch.float32, device="cuda")
+        crom.crom_fom_step(crom.CROM_FOM_HEAT2D_NEUMANN, u, tmp, al, dt=(1.0 / (nn - 1)) ** 2 / 8, n_steps=n)
+        torch.cuda.synchronize()
+        print(json.dumps({"only": "heat", "fields": nb, "nodes": nn * nn, "steps": n}))
         return
     else:
         spec, params, codes, X = gen.recon_dense(n_codes=args.n_codes)
