@@ -3,8 +3,9 @@
 // over independent fields.  These are the data generators and the judges of
 // rollout error; every update is a 5-point (3-point in 1D) stencil, so the
 // kernels are bound by memory traffic: one read and one write of u per node and
-// step (plus the two face velocities for advection).  Neighbour values are
-// served by L1/L2.
+// step (plus the two face velocities for advection).  The 2D kernels for sides
+// that are multiples of 128 march down short row strips with neighbours in
+// registers and lanes; the others serve neighbour values from L1/L2.
 //
 //  * heat 1D, Dirichlet 0: nodes x_i = i/(P-1); interior
 //      u_i += dt * nu * (u_{i-1} + u_{i+1} - 2 u_i) / dx^2, boundary nodes = 0.
