@@ -57,11 +57,11 @@ typedef enum {
  *           equations.  Any shape with width % 32 == 0, width <= 256.
  *  BF16X2 : tcgen05 tensor cores, bf16 operands with FP32 accumulation.  Every
  *           activation operand is split into a bf16 high part and a bf16 low part
- *           (two MMAs into one accumulator), weights are rounded once to bf16.
- *           FP32 activation/derivative chains, FP64 normal equations.
- *           width == 128, 2 <= hidden <= 5, m <= 2, r <= 15.
- *  BF16   : as BF16X2 with the high part only (one MMA per layer).  Dense
- *           reconstruction only.
+ *           (multiplied by the same MMAs into separate FP32 accumulator columns,
+ *           added in the epilogue), weights are rounded once to bf16.  FP32
+ *           activation/derivative chains, FP64 normal equations.
+ *           width == 128, 2 <= hidden <= 5, m <= 2, r <= 15, ELU.
+ *  BF16   : as BF16X2 with the high parts only.  Dense reconstruction only.
  *  TF32   : training step only: the dense products on the tensor cores with
  *           TF32 operands (10-bit mantissa) and FP32 accumulation, through cuBLAS
  *           (plain GEMMs); every other step of the training pass in FP32. */
