@@ -187,8 +187,9 @@ int crom_decode(crom_ctx* ctx, int n_inst, const double* q, const int* pt_off, c
  *   instance over several CTAs (the last CTA to finish reduces and solves); the
  *   context grows its scratch on first use, so the first call for a given size
  *   must not be made during stream capture.
- * precision CROM_PREC_BF16X2: one persistent launch per step; each CTA takes
- *   whole instances from a queue. */
+ * precision CROM_PREC_BF16X2: one persistent launch per step (plus a small
+ *   ordering kernel); each of a CTA's four 128-thread groups takes whole
+ *   instances, largest |M_i| first, from a queue. */
 int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_inst, double* q,
               const float* alpha, const float* vel, const int* s_off, const float* samples,
               int n_samples, int max_samples, int* status, crom_stream stream);
