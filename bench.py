@@ -237,6 +237,112 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def measure_next_rows(crom, gen, ctx, w, q0, alpha, s_off, samples, status, stream, flush, local):
+    """The paper's further rows on the bench's GPU, each on a workload of its own
+    (CUDA events; L2 flushed before each timed step on the 1024-instance batch):
+    f1 the backtracking line search, f3 a per-sample coefficient, f4 a SIREN decoder
+    (FP32 path) and the tangent velocity, f2 greedy robust sample selection."""
+    import torch
+    out = {}
+    max_s = int(w.sizes.max())
+    q = torch.empty_like(q0)
+
+    def timed(fn, reps, flush_l2=True):
+        fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(reps):
+            if flush_l2:
+                flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / reps
+
+    # f1: line search (value-only trial passes).  At the bench's dt the first GN
+    # iteration accepts its full step; the second starts at the least-squares optimum,
+    # where the decrease is at rounding level, so its trials backtrack to the last
+    # halving and keep q.  At dt = 0.1 most full steps overshoot and backtrack.
+    for name, dt in (("line_search_bench_dt", w.dt), ("line_search_dt_0.1", 0.1)):
+        def f1():
+            q.copy_(q0)
+            crom.crom_step(ctx, q, alpha, s_off, samples, status, dt=dt, gn_iters=w.gn_iters, max_samples=max_s,
+                           precision=crom.CROM_PREC_BF16X2, line_search=4)
+        ms = timed(f1, 5)
+        out[name] = {"ms_per_step": ms, "instance_steps_per_s": w.n_inst / (ms * 1e-3), "halvings_max": 4,
+                     "workload": f"1024 instances of the step's workload, dt = {dt:g}, 2 GN iterations, "
+                                 "up to 4 halvings"}
+    # f3: per-sample coefficient nu(y_j) (the instance's alpha repeated at its samples)
+    alpha_s = torch.repeat_interleave(alpha, torch.tensor(w.sizes, device="cuda"))
+
+    def f3():
+        q.copy_(q0)
+        crom.crom_step(ctx, q, alpha_s, s_off, samples, status, dt=w.dt, gn_iters=w.gn_iters, max_samples=max_s,
+                       precision=crom.CROM_PREC_BF16X2, coef_per_sample=True)
+    ms = timed(f3, 5)
+    out["coef_per_sample"] = {"ms_per_step": ms, "instance_steps_per_s": w.n_inst / (ms * 1e-3),
+                              "workload": "1024 instances, alpha per sample"}
+    # f4: SIREN decoder (omega0 = 30) on the FP32 CUDA-core path, 64 instances
+    spec = gen.DecoderSpec(2, 8, 128, 5)
+    ctx_s = crom.crom_create(2, 8, 128, 5, local, activation=crom.CROM_ACT_SIREN, omega0=30.0)
+    crom.crom_set_weights(ctx_s, gen.pack_params(gen.siren_decoder(spec, seed=3)))
+    n64 = 64
+    s64 = torch.tensor((2.0 * w.samples[:w.s_off[n64]] - 1.0).astype(np.float32), device="cuda")
+    q64 = (q0[:n64] * 0.5).contiguous()
+    qs = torch.empty_like(q64)
+
+    def f4():
+        qs.copy_(q64)
+        crom.crom_step(ctx_s, qs, alpha[:n64].contiguous(), s_off[:n64 + 1].contiguous(), s64, status[:n64],
+                       dt=1e-6, gn_iters=w.gn_iters, max_samples=max_s, precision=crom.CROM_PREC_FP32)
+    ms = timed(f4, 5, flush_l2=False)
+    out["siren_fp32_step"] = {"ms_per_step": ms, "instance_steps_per_s": n64 / (ms * 1e-3),
+                              "workload": "64 instances of the step's workload on [-1, 1]^2, SIREN width 128 x 5"}
+    ctx_s.close()
+    # f4: tangent velocity dg/dq . qdot at the integration samples of the 1024 instances
+    # (FP32 Jacobian channels, FP64 contraction)
+    n_pts = int(w.s_off[-1])
+    vout = torch.empty(n_pts, device="cuda")
+    qprev = q0 * 0.999
+
+    def f4t():
+        crom.crom_tangent_velocity(ctx, q0, qprev, s_off, samples, vout, dt=1e-3)
+    ms = timed(f4t, 5)
+    out["tangent_velocity"] = {"ms": ms, "points_per_s": n_pts / (ms * 1e-3),
+                               "workload": f"the {n_pts} integration samples of the 1024 instances, r = 8"}
+    # f2: greedy robust sampling (Algorithm 1) on a 1D heat problem: 257 nodes, 4
+    # training parameters, 8 initial samples grown to 24, 8 candidates per round,
+    # 20-step candidate rollouts; the "full-order" fields are synthetic sines
+    spec1 = gen.DecoderSpec(1, 4, 128, 3)
+    ctx1 = crom.crom_create(1, 4, 128, 3, local)
+    crom.crom_set_weights(ctx1, gen.pack_params(gen.xavier_decoder(spec1, seed=9, bias_std=0.1, bf16_exact=True)))
+    P = 257
+    xs = np.arange(P) / (P - 1)
+    nodes = torch.tensor(xs.astype(np.float32)[:, None], device="cuda")
+    rng = np.random.default_rng(21)
+    q0r = torch.tensor(rng.standard_normal((4, 4)) * 0.5, device="cuda")
+    coef = torch.tensor(rng.uniform(0.5, 1.5, 4).astype(np.float32), device="cuda")
+    fom = torch.tensor(np.stack([np.sin((k + 1) * np.pi * xs) * 0.1 for k in range(4)]).astype(np.float32),
+                       device="cuda")
+    init = list(np.linspace(8, P - 9, 8).astype(int))
+    for prec_name in ("CROM_PREC_FP32", "CROM_PREC_BF16X2"):
+        t0 = time.perf_counter()
+        idx, met = crom.crom_robust_samples(ctx1, q0r, coef, nodes, fom, init, dt=3e-4, gn_iters=1, n_steps=20,
+                                            n_try=8, target=0.0, max_samples=24,
+                                            precision=getattr(crom, prec_name))
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        rounds = len(idx) - len(init)
+        out["robust_sampling_" + prec_name[10:].lower()] = {
+            "s": sec, "rounds": rounds, "candidate_rollouts_per_s": rounds * 8 * 4 / sec,
+            "workload": "1D heat, 257 nodes, 4 parameters, |M| 8 -> 24, 8 candidates per round, 20-step rollouts"}
+    ctx1.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -499,6 +605,8 @@ def main():
     train_flops = pts * 6 * (2 * (2 + rt) * wt + 2 * (Lt - 1) * wt * wt + 2 * wt) / 2
     tr.close()
 
+    next_rows = measure_next_rows(crom, gen, ctx, w, q0, alpha, s_off, samples, status, stream, flush, local)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, done, ns, el = cpu_oracle_rate(w, budget_s=12.0)
@@ -535,6 +643,7 @@ def main():
             "fom_advdiff2d": {"node_steps_per_s": fom_nodes / (fom_ms * 1e-3), "ms_per_step": fom_ms,
                               "gbs_algorithmic": fom_gbs, "frac_of_measured_hbm": fom_gbs / hbm,
                               "workload": "512 periodic 256^2 fields, 16 B per node-step (u, ax, ay read, u written)"},
+            "next_rows": next_rows,
             "fom_heat2d": {"node_steps_per_s": heat_nodes / (heat_ms * 1e-3), "ms_per_step": heat_ms,
                            "gbs_algorithmic": heat_gbs, "frac_of_measured_hbm": heat_gbs / hbm,
                            "workload": "1024 zero-flux 256^2 fields, 8 B per node-step (u read and written)"},
