@@ -263,9 +263,9 @@ def measure_next_rows(crom, gen, ctx, w, q0, alpha, s_off, samples, status, stre
         return tot / reps
 
     # f1: line search (value-only trial passes).  At the bench's dt the first GN
-    # iteration accepts its full step; the second starts at the least-squares optimum,
-    # where the decrease is at rounding level, so its trials backtrack to the last
-    # halving and keep q.  At dt = 0.1 most full steps overshoot and backtrack.
+    # iteration accepts its full step; in the second the trial objective equals the
+    # Armijo bound up to rounding, so the decisions there can go either way.  At
+    # dt = 0.1 most full steps overshoot and backtrack.
     for name, dt in (("line_search_bench_dt", w.dt), ("line_search_dt_0.1", 0.1)):
         def f1():
             q.copy_(q0)
