@@ -303,7 +303,7 @@ def measure_next_rows(crom, gen, ctx, w, q0, alpha, s_off, samples, status, stre
                               "workload": "64 instances of the step's workload on [-1, 1]^2, SIREN width 128 x 5"}
     ctx_s.close()
     # f4: tangent velocity dg/dq . qdot at the integration samples of the 1024 instances
-    # (FP32 Jacobian channels, FP64 contraction)
+    # (one FP32 forward-mode directional channel seeded with W_1q qdot)
     n_pts = int(w.s_off[-1])
     vout = torch.empty(n_pts, device="cuda")
     qprev = q0 * 0.999

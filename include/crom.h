@@ -105,9 +105,11 @@ typedef struct {
  * qdot_i = (q_i - q_prev_i) / dt (q_prev = q gives qdot = 0, the start of a
  * rollout).  Points as in crom_decode (instance i owns points
  * pt_off[i] .. pt_off[i+1]-1); q, q_prev [n_inst][r] FP64; out [n_pts] FP32.
- * FP32 evaluation of the r Jacobian channels, contraction in FP64.  The
- * context keeps an r x n_pts scratch (grown on demand: do not call during
- * stream capture with a larger n_pts than before). */
+ * One forward-mode directional channel in FP32 (the layer-1 seed W_1q qdot_i
+ * formed in FP64 and rounded once), i.e. the Jacobian-vector product without the
+ * r Jacobian columns.  The context keeps an n_inst x width scratch for the seeds
+ * (grown on demand: do not call during stream capture with more instances than
+ * before). */
 int crom_tangent_velocity(crom_ctx* ctx, int n_inst, const double* q, const double* q_prev, double dt,
                           const int* pt_off, const float* x, int n_pts, float* out, crom_stream stream);
 

@@ -288,7 +288,7 @@ int crom_tangent_velocity(crom_ctx* ctx, int n_inst, const double* q, const doub
     return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": null array or no instance for the points");
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t need = (size_t)ctx->desc.r * n_pts;
+  const size_t need = (size_t)n_inst * ctx->desc.width;  // layer-1 seeds W_1q qdot_i
   if (need > ctx->tangent_cap) {
     cudaFree(ctx->tangent);
     ctx->tangent = nullptr;
@@ -297,9 +297,7 @@ int crom_tangent_velocity(crom_ctx* ctx, int n_inst, const double* q, const doub
     if (e != cudaSuccess) return cuda_fail(e, fn);
     ctx->tangent_cap = need;
   }
-  cudaError_t e = launch_decode_fp32(ctx, n_inst, q, pt_off, x, n_pts, CROM_WANT_DQ, ctx->tangent, s);
-  if (e == cudaSuccess)
-    e = launch_tangent_contract(ctx->tangent, q, q_prev, dt, pt_off, n_inst, ctx->desc.r, n_pts, out, s);
+  cudaError_t e = launch_tangent_fp32(ctx, n_inst, q, q_prev, dt, pt_off, x, n_pts, ctx->tangent, out, s);
   if (e != cudaSuccess) return cuda_fail(e, fn);
   return CROM_OK;
 }

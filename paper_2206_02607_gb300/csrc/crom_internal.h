@@ -59,7 +59,7 @@ struct crom_ctx {
   size_t targets_cap = 0;
   double* qbase = nullptr;     // [n_inst][r]: q_n kept for the difference channel
   size_t qbase_cap = 0;
-  float* tangent = nullptr;    // [r][n_pts]: dg/dq rows for the tangent velocity
+  float* tangent = nullptr;    // [n_inst][width]: layer-1 seeds W_1q qdot_i of the tangent velocity
   size_t tangent_cap = 0;
   uint8_t* host_stage = nullptr;  // crom_step_host: device copies of the caller's host arrays
   size_t host_stage_cap = 0;
@@ -148,8 +148,9 @@ cudaError_t launch_step_fp32(crom_ctx* ctx, const crom_step_desc* step, int n_in
                              cudaStream_t s);
 
 // v_p = (dg/dq)(x_p, q_i) . (q_i - q_prev_i) / dt from dq [r][n_pts] (decode output).
-cudaError_t launch_tangent_contract(const float* dq, const double* q, const double* q_prev, double dt,
-                                    const int* pt_off, int n_inst, int r, int n_pts, float* out, cudaStream_t s);
+cudaError_t launch_tangent_fp32(const crom_ctx* ctx, int n_inst, const double* q, const double* q_prev, double dt,
+                                const int* pt_off, const float* x, int n_pts, float* seed, float* out,
+                                cudaStream_t s);
 
 // FP32 step with its scratch in a fixed-size device array (no allocation).
 size_t noalloc_scratch_capacity();

@@ -60,6 +60,9 @@ struct FwdParams {
   // decode / recon
   float* out;
   unsigned want;
+  // decode of a directional derivative (nq == 1): the one latent channel is seeded
+  // with jvp_seed[instance][unit] = (W_1q u_i)[unit] instead of a W_1q column
+  const float* jvp_seed;
   // step
   int iter;
   int pde;
@@ -164,7 +167,11 @@ __device__ int find_instance(const int* off, int n_inst, int point) {
   return lo;
 }
 
-__global__ void fwd_fp32_kernel(FwdParams p) {
+// kJvp: the tangent-velocity decode, whose directional channel is seeded per
+// instance (kept out of the other instantiation, whose register budget it would
+// change).
+template <bool kJvp>
+__device__ __forceinline__ void fwd_fp32_body(const FwdParams& p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int W = p.width, S = p.S, C = p.C, LD = p.LD, m = p.m, r = p.r;
   // KS threads per hidden unit: thread (u, ks) owns unit u and the ks-th slice of
@@ -260,7 +267,12 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
       const int n2 = (p.second == kSecondPerK) ? m : (p.second == kSecondLap ? 1 : 0);
       for (int k = 0; k < n2; ++k) ch[o + k] = 0.f;
       o += n2;
-      for (int j = 0; j < p.nq; ++j) ch[o + j] = w1[m + j];
+      if (kJvp) {
+        const int code = find_instance(p.off, p.n_inst, first + (s < ns ? s : 0));
+        ch[o] = __ldg(&p.jvp_seed[(size_t)code * W + u]);
+      } else {
+        for (int j = 0; j < p.nq; ++j) ch[o + j] = w1[m + j];
+      }
     }
     activate_row(row, p, ks, KS);
   }
@@ -339,8 +351,8 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
         for (int k = 0; k < n2; ++k) lap += c[o2 + k];
         p.out[(row++) * N + pt] = lap;
       }
-      if (p.want & CROM_WANT_DQ)
-        for (int j = 0; j < r; ++j) p.out[(row++) * N + pt] = c[oq + j];
+      if (p.want & CROM_WANT_DQ)  // r rows, or the one directional row of a tangent decode
+        for (int j = 0; j < p.nq; ++j) p.out[(row++) * N + pt] = c[oq + j];
     }
     return;
   }
@@ -443,6 +455,10 @@ __global__ void fwd_fp32_kernel(FwdParams p) {
   }
 }
 
+__global__ void fwd_fp32_kernel(FwdParams p) { fwd_fp32_body<false>(p); }
+// up to 1024 threads per CTA: the bound keeps it within 64 registers
+__global__ void __launch_bounds__(1024) fwd_fp32_jvp_kernel(FwdParams p) { fwd_fp32_body<true>(p); }
+
 size_t fwd_smem_bytes(int W, int S, int C, int m, int r, int* LD_out) {
   const int NP = S * C;
   const int NPP = (NP + 15) & ~15;
@@ -458,12 +474,12 @@ size_t fwd_smem_bytes(int W, int S, int C, int m, int r, int* LD_out) {
 
 cudaError_t launch_fwd(FwdParams& p, dim3 grid, cudaStream_t s) {
   size_t smem = fwd_smem_bytes(p.width, p.S, p.C, p.m, p.r, &p.LD);
+  auto kernel = p.jvp_seed ? fwd_fp32_jvp_kernel : fwd_fp32_kernel;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(fwd_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  fwd_fp32_kernel<<<grid, p.width * kKSplit, smem, s>>>(p);
+  kernel<<<grid, p.width * kKSplit, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -493,25 +509,47 @@ int pick_samples(int W, int C, int m, int r, int want) {
 }  // namespace
 
 namespace {
-__global__ void tangent_contract_kernel(const float* __restrict__ dq, const double* __restrict__ q,
-                                        const double* __restrict__ q_prev, double inv_dt,
-                                        const int* __restrict__ pt_off, int n_inst, int r, int n_pts,
-                                        float* __restrict__ out) {
-  const int pt = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pt >= n_pts) return;
-  const int i = find_instance(pt_off, n_inst, pt);
+// Layer-1 seed of the directional derivative along qdot_i = (q_i - q_prev_i) / dt:
+// seed[i][u] = sum_j W_1[u][m + j] qdot_i[j], an FP64 sum rounded once.
+__global__ void jvp_seed_kernel(const float* __restrict__ w1, int m, int r, int W, const double* __restrict__ q,
+                                const double* __restrict__ q_prev, double inv_dt, int n_inst, float* seed) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_inst * W) return;
+  const int i = e / W, u = e % W;
   double v = 0.0;
   for (int j = 0; j < r; ++j)
-    v += (double)dq[(size_t)j * n_pts + pt] * ((q[(size_t)i * r + j] - q_prev[(size_t)i * r + j]) * inv_dt);
-  out[pt] = (float)v;
+    v += (double)w1[(size_t)u * (m + r) + m + j] * ((q[(size_t)i * r + j] - q_prev[(size_t)i * r + j]) * inv_dt);
+  seed[e] = (float)v;
 }
 }  // namespace
 
-cudaError_t launch_tangent_contract(const float* dq, const double* q, const double* q_prev, double dt,
-                                    const int* pt_off, int n_inst, int r, int n_pts, float* out, cudaStream_t s) {
-  tangent_contract_kernel<<<(n_pts + 255) / 256, 256, 0, s>>>(dq, q, q_prev, 1.0 / dt, pt_off, n_inst, r, n_pts,
-                                                              out);
-  return cudaGetLastError();
+// Tangent velocity v = dg/dq . qdot as one forward-mode directional channel (the
+// DQ channel machinery with the seed W_1q qdot instead of r columns of W_1q).
+cudaError_t launch_tangent_fp32(const crom_ctx* ctx, int n_inst, const double* q, const double* q_prev, double dt,
+                                const int* pt_off, const float* x, int n_pts, float* seed, float* out,
+                                cudaStream_t s) {
+  FwdParams p{};
+  p.mode = kModeDecode;
+  fill_decoder(p, ctx);
+  const int W = p.width;
+  jvp_seed_kernel<<<(n_inst * W + 255) / 256, 256, 0, s>>>(p.w1, p.m, p.r, W, q, q_prev, 1.0 / dt, n_inst, seed);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  p.nx = 0;
+  p.second = kSecondNone;
+  p.nq = 1;
+  p.C = ChannelSet{p.nx, p.second, p.nq}.count(p.m);
+  p.S = pick_samples(p.width, p.C, p.m, p.r, 8);
+  p.q = q;
+  p.off = pt_off;
+  p.x = x;
+  p.n_pts = n_pts;
+  p.n_inst = n_inst;
+  p.out = out;
+  p.want = CROM_WANT_DQ;
+  p.jvp_seed = seed;
+  dim3 grid((n_pts + p.S - 1) / p.S, 1);
+  return launch_fwd(p, grid, s);
 }
 
 cudaError_t launch_decode_fp32(const crom_ctx* ctx, int n_inst, const double* q, const int* pt_off,
