@@ -73,3 +73,26 @@ def test_step_host_rejects_bad_offsets(c):
         c.crom_step_host(ctx, torch.tensor(w.q0, device="cuda"), torch.tensor(w.alpha), torch.tensor(good),
                          torch.tensor(w.samples), torch.zeros(3, dtype=torch.int32), dt=w.dt, gn_iters=2,
                          max_samples=64)
+
+
+def test_step_host_advection_and_per_sample_coefficient(c):
+    """The optional arrays travel too: advection velocities (one per sample and
+    dimension) and a per-sample coefficient; equal to crom_step bit for bit."""
+    import torch
+    w = gen.heat2d_batched(n_inst=12, m_lo=20, m_hi=200)
+    ctx = make_ctx(w.spec, w.params)
+    rng = np.random.default_rng(4)
+    vel = rng.standard_normal((w.samples.shape[0], 2)).astype(np.float32)
+    nu = rng.uniform(0.005, 0.02, w.samples.shape[0]).astype(np.float32)
+    kw = dict(dt=1e-4, gn_iters=2, max_samples=int(w.sizes.max()), pde=c.CROM_PDE_ADVDIFF,
+              coef_per_sample=True, precision=c.CROM_PREC_BF16X2)
+    d = StepInputs(w)
+    c.crom_step(ctx, d.q, torch.tensor(nu, device="cuda"), d.s_off, d.samples, d.status,
+                vel=torch.tensor(vel, device="cuda"), **kw)
+    torch.cuda.synchronize()
+    hq = torch.tensor(w.q0)
+    hst = torch.full((w.n_inst,), -1, dtype=torch.int32)
+    c.crom_step_host(ctx, hq, torch.tensor(nu), torch.tensor(w.s_off), torch.tensor(w.samples), hst,
+                     vel=torch.tensor(vel), **kw)
+    assert np.array_equal(hst.numpy(), d.status.cpu().numpy()) and np.all(hst.numpy() == c.CROM_OK)
+    assert np.array_equal(hq.numpy(), d.q.cpu().numpy())
