@@ -1,17 +1,17 @@
 // Dense reconstruction g(x_p, q_c) on the tcgen05 tensor cores (value channel only).
 //
 // Persistent kernel, one CTA per SM with the decoder's bf16 hidden matrices in
-// shared memory, two independent groups of 256 threads (one tile each, own
-// operand buffers / TMEM columns / mbarrier / named barrier) so that one group's
-// UMMAs overlap the other's epilogue.  Hidden unit u is TMEM lane u and is served
-// by two threads of the group, each taking half of the tile's points.  A tile is
-// 64 points of one code with hi/lo operand parts, 128 points with hi parts only:
+// shared memory, four independent groups of 128 threads (one tile each, own
+// 64-column operand block / 128 TMEM columns / mbarrier / named barrier) so that
+// one group's UMMAs overlap the others' epilogues.  Hidden unit u is TMEM lane u
+// and thread u of its group.  A tile is 32 points of one code with hi/lo operand
+// parts, 64 points with hi parts only:
 //   layer 1 (K = m + r, too small for UMMA) on CUDA cores: the q part of
 //     W_1 [x; q] + b_1 is hoisted per code; h = ELU(W_1x x + c);
 //   layers 2..L: D[u][n] = sum_k W_l[u][k] H[k][n] by UMMA (M = 128 units,
-//     N = 128, K = 128), A = W_l (K-major, resident), B = H (MN-major, written by
-//     the previous epilogue: the hi and lo parts of 64 points side by side, added
-//     in the epilogue, or the hi parts of 128 points); epilogue: bias, ELU, bf16
+//     N = 64, K = 128), A = W_l (K-major, resident), B = H (MN-major, written by
+//     the previous epilogue: the hi and lo parts of 32 points side by side, added
+//     in the epilogue, or the hi parts of 64 points); epilogue: bias, ELU, bf16
 //     split, store;
 //   output layer: w_out . h_L on the CUDA cores in the last hidden layer's
 //     epilogue, in FP32 from h_L itself (a warp butterfly over the 32 units of
@@ -31,17 +31,17 @@ namespace {
 
 using namespace tc;
 
-constexpr int kGroups = 2;
-constexpr int kGT = 256;  // two threads per TMEM lane, each half of the tile's points
+constexpr int kGroups = 4;
+constexpr int kGT = 128;  // one thread per TMEM lane (hidden unit), all of the tile's points
 constexpr int kThreads = kGroups * kGT;
-// Points per tile: 64 with hi/lo operand parts (N = 128 = 64 hi + 64 lo columns),
-// 128 with hi parts only (N = 128 points); the accumulator and operand blocks are
-// the same size either way.
-constexpr int kTileSplit = 64, kTileHi = 128;
+// Points per tile: 32 with hi/lo operand parts (N = 64 = 32 hi + 32 lo columns),
+// 64 with hi parts only (N = 64 points); one 64-column operand block and 64
+// accumulator columns per group either way.
+constexpr int kTileSplit = 32, kTileHi = 64;
 constexpr int kTileN = kTileHi;  // sizes of the per-tile arrays
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kGroupCols = 256;
-constexpr uint32_t kAccCol = 0;    // W h_hi in columns 0..63, W h_lo in 64..127 (hi only: 128 points)
+constexpr uint32_t kGroupCols = 128;
+constexpr uint32_t kAccCol = 0;    // W h_hi in columns 0..31, W h_lo in 32..63 (hi only: 64 points)
 constexpr uint32_t kWaitLimit = 1u << 25;
 constexpr size_t kHBuf = (size_t)kTcWidth * 64 * 2;  // one 64-column bf16 operand block, 16 KB
 
@@ -118,10 +118,11 @@ __device__ __forceinline__ bool group_sync_and(int g, bool pred) {
   return r != 0;
 }
 
-// Sixteen consecutive columns n0..n0+15 of row k, given as 8 packed pairs, stored as
-// bf16 hi (and lo = bf16(h - hi) when kSplit) operand parts.
+// Sixteen consecutive columns of row k, given as 8 packed pairs, stored as bf16 hi
+// parts at columns n0..n0+15 (and lo = bf16(h - hi) parts at nl..nl+15 when kSplit)
+// of the MN-major operand H.
 template <int kSplit>
-__device__ __forceinline__ void store_split16(uint8_t* Hhi, uint8_t* Hlo, int k, int n0, const f32x2 (&h)[8]) {
+__device__ __forceinline__ void store_split16(uint8_t* H, int k, int n0, int nl, const f32x2 (&h)[8]) {
   uint32_t hi[8], lo[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
@@ -130,11 +131,11 @@ __device__ __forceinline__ void store_split16(uint8_t* Hhi, uint8_t* Hlo, int k,
     hi[j] = pack_bf16(a, b);
     if (kSplit) lo[j] = pack_bf16_lo(hi[j], a, b);
   }
-  *reinterpret_cast<uint4*>(Hhi + mn_offset(k, n0)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-  *reinterpret_cast<uint4*>(Hhi + mn_offset(k, n0 + 8)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+  *reinterpret_cast<uint4*>(H + mn_offset(k, n0)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+  *reinterpret_cast<uint4*>(H + mn_offset(k, n0 + 8)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
   if (kSplit) {
-    *reinterpret_cast<uint4*>(Hlo + mn_offset(k, n0)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-    *reinterpret_cast<uint4*>(Hlo + mn_offset(k, n0 + 8)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+    *reinterpret_cast<uint4*>(H + mn_offset(k, nl)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    *reinterpret_cast<uint4*>(H + mn_offset(k, nl + 8)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
   }
 }
 
@@ -144,17 +145,15 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x;
   const int g = tid / kGT, gt = tid % kGT;
-  const int lq = (gt >> 5) & 3, half = gt >> 7;
+  const int lq = (gt >> 5) & 3;
   const int u = lq * 32 + (gt & 31);           // hidden unit = TMEM lane
   constexpr int kTile = kSplit ? kTileSplit : kTileHi;
-  const int nbeg = half * (kTile / 2);         // this thread's half of the tile's points
   const uint32_t lane_base = (uint32_t)lq * 32;
   const int m = p.m, r = p.r;
   uint8_t* Wimg = sm;
   uint8_t* Hbase = sm + ((p.img_bytes + 1023) & ~1023);
-  uint8_t* Hhi = Hbase + (size_t)g * 2 * kHBuf;
-  uint8_t* Hlo = Hhi + kHBuf;
-  Shared* S = reinterpret_cast<Shared*>(Hbase + (size_t)kGroups * 2 * kHBuf);
+  uint8_t* H = Hbase + (size_t)g * kHBuf;  // this group's 64-column operand block
+  Shared* S = reinterpret_cast<Shared*>(Hbase + (size_t)kGroups * kHBuf);
   Group* G = reinterpret_cast<Group*>(S + 1) + g;
 
   if (tid == 0) {
@@ -190,8 +189,8 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
   const uint32_t wbase = smem_u32(Wimg);
   // Base UMMA descriptors; every operand slice is base + a compile-time offset.
   const uint64_t dW = smem_desc_sw128(wbase, 16, 1024);
-  const uint64_t dHhi = smem_desc_sw128(smem_u32(Hhi), 16384, 1024);
-  constexpr uint32_t id_layer = idesc_f16(128, 128, false, true, true);
+  const uint64_t dH = smem_desc_sw128(smem_u32(H), 16384, 1024);
+  constexpr uint32_t id_layer = idesc_f16(128, 64, false, true, true);
   int cur_code = -1;
   float c = 0.f;
   const float wx0 = S->w1x[0][u], wx1 = (m > 1) ? S->w1x[1][u] : 0.f;
@@ -215,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
     group_sync(g);
     // ---- layer 1 on CUDA cores
 #pragma unroll 1
-    for (int n0 = nbeg; n0 < nbeg + kTile / 2; n0 += 16) {
+    for (int n0 = 0; n0 < kTile; n0 += 16) {
       f32x2 h[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
@@ -224,7 +223,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
         float e0, e1;
         h[j] = elu2(z, e0, e1);
       }
-      store_split16<kSplit>(Hhi, Hlo, u, n0, h);
+      store_split16<kSplit>(H, u, n0, kTileSplit + n0, h);
     }
     // ---- hidden layers on the tensor cores; the output layer in the last epilogue
     for (int l = 0; l < p.n_hidden_mats; ++l) {
@@ -235,13 +234,13 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
       bool done = true;
       if ((gt >> 5) == 0) {  // the first warp issues (one elected lane) and waits, the rest wait at the barrier
         tc_fence_after();
-        // The lo buffer follows the hi buffer at the operand's 64-column block
-        // stride, so one UMMA with N = 128 multiplies both parts at once: columns
-        // 0..63 of the accumulator get W h_hi, columns 64..127 get W h_lo.
+        // The lo parts follow the hi parts in the same 64-column block, so one UMMA
+        // with N = 64 multiplies both at once: accumulator columns 0..31 get W h_hi,
+        // columns 32..63 W h_lo (hi only: 64 points).
         const uint64_t a0 = desc_add(dW, (uint32_t)l * kTcLayerBytes);
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
-          umma_f16_warp(tb + kAccCol, desc_add(a0, kmajor_kslice(128, kk)), desc_add(dHhi, mnmajor_kslice(kk)),
+          umma_f16_warp(tb + kAccCol, desc_add(a0, kmajor_kslice(128, kk)), desc_add(dH, mnmajor_kslice(kk)),
                         id_layer, kk != 0);
         umma_commit_warp(&G->bar_mma);
         done = mbar_wait(&G->bar_mma, phase, kWaitLimit);
@@ -252,7 +251,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
       if (!ok) break;
       const float bias = S->bh[l][u];
 #pragma unroll 1
-      for (int n0 = nbeg; n0 < nbeg + kTile / 2; n0 += 16) {
+      for (int n0 = 0; n0 < kTile; n0 += 16) {
         float v[16], w[16];
         tmem_ld16(taddr(tb, lane_base, kAccCol + n0), v);
         if (kSplit) tmem_ld16(taddr(tb, lane_base, kAccCol + kTileSplit + n0), w);
@@ -267,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
           h[j] = elu2(z, e0, e1);
         }
         if (!last) {
-          store_split16<kSplit>(Hhi, Hlo, u, n0, h);
+          store_split16<kSplit>(H, u, n0, kTileSplit + n0, h);
         } else {
           float wv[16];
 #pragma unroll
@@ -318,7 +317,7 @@ cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const d
   const int tile_pts = split ? kTileSplit : kTileHi;
   p.tiles_per_code = (n_pts + tile_pts - 1) / tile_pts;
   p.flag = ctx->queue + 2;
-  const size_t smem = 1024 + (((size_t)p.img_bytes + 1023) & ~(size_t)1023) + (size_t)kGroups * 2 * kHBuf +
+  const size_t smem = 1024 + (((size_t)p.img_bytes + 1023) & ~(size_t)1023) + (size_t)kGroups * kHBuf +
                       kTailBytes;
   const long long tiles = (long long)n_codes * p.tiles_per_code;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
