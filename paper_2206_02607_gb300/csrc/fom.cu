@@ -1,7 +1,7 @@
 // Full-order models on the GPU: explicit finite differences + forward Euler
 // (paper App. G.2 for the 1D heat equation, App. H.2 for the 2D form), batched
-// over independent fields.  These are the data generators and the judges of
-// rollout error; every update is a 5-point (3-point in 1D) stencil, so the
+// over independent fields.  These generate the training data and the reference
+// solutions that rollouts are compared with; every update is a 5-point (3-point in 1D) stencil, so the
 // kernels are bound by memory traffic: one read and one write of u per node and
 // step (plus the two face velocities for advection).  The 2D kernels for sides
 // that are multiples of 128 march down short row strips with neighbours in
