@@ -35,6 +35,9 @@ constexpr int kSplitK = 32;
 
 __device__ __forceinline__ float elu_f(float z) { return z > 0.f ? z : expm1f(z); }
 __device__ __forceinline__ float elu_d(float z) { return z > 0.f ? 1.f : expf(z); }
+// s'(z) from h = s(z): 1 where h > 0, else e^z = h + 1 (the TF32 path keeps only h
+// of each hidden layer, not z).
+__device__ __forceinline__ float elu_d_h(float h) { return h > 0.f ? 1.f : h + 1.f; }
 
 // Compensated (Kahan) FP32 accumulation: the running sum s - c stays within a few
 // ulps of the exact sum whatever the number of terms, in FP32 instructions (FP64 is
@@ -50,11 +53,13 @@ struct CompSum {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-enum Epi { kEpiStore = 0, kEpiBiasElu = 1, kEpiTimesEluD = 2 };
+enum Epi { kEpiStore = 0, kEpiBiasElu = 1, kEpiTimesEluD = 2, kEpiBias = 3 };
 
 // C[i][j] = sum_k A(i, k) B(k, j), A(i, k) = A[i*sai + k*sak], B(k, j) = B[k*sbk + j*sbj].
 // Epilogues: kEpiStore (C row-major, ldc); kEpiBiasElu (Z = C + bias[j] stored in C,
-// ELU(Z) stored in H); kEpiTimesEluD (C *= s'(Zp[i][j])).  blockIdx.z splits K into
+// ELU(Z) stored in H); kEpiTimesEluD (C *= s'(Zp[i][j])).  (The TF32 path's
+// elementwise kernels below differ: its bias + ELU stores only H, its "x s'" reads H,
+// and kEpiBias, C += bias, serves its linear layer.)  blockIdx.z splits K into
 // gridDim.z contiguous ranges writing to C + z * split_stride (kEpiStore only).
 __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const float* __restrict__ A, long sai,
                                                    long sak, const float* __restrict__ B, long sbk, long sbj,
@@ -116,7 +121,9 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
   }
 }
 
-// Elementwise epilogues after a library GEMM (C row-major, M x N, ldc).
+// Elementwise epilogues after a library GEMM (C row-major, M x N, ldc) in the TF32
+// path: bias + ELU writes h (the scalar form also leaves z in C), and "x s'(z)"
+// takes s' from h (Hp).
 __global__ void epi_bias_elu_kernel(float* C, long M, int N, long ldc, const float* bias, float* H) {
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= M * N) return;
@@ -127,11 +134,17 @@ __global__ void epi_bias_elu_kernel(float* C, long M, int N, long ldc, const flo
   C[o] = v;
   H[o] = elu_f(v);
 }
-__global__ void epi_times_elud_kernel(float* C, long M, int N, long ldc, const float* Zp) {
+__global__ void epi_bias_kernel(float* C, long M, int N, long ldc, const float* bias) {
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= M * N) return;
   const long o = (t / N) * ldc + (t % N);
-  C[o] *= elu_d(Zp[o]);
+  C[o] += bias[t % N];
+}
+__global__ void epi_times_elud_kernel(float* C, long M, int N, long ldc, const float* Hp) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= M * N) return;
+  const long o = (t / N) * ldc + (t % N);
+  C[o] *= elu_d_h(Hp[o]);
 }
 
 // The same epilogues four columns at a time (N % 4 == 0, ldc % 4 == 0, 16-byte
@@ -143,17 +156,16 @@ __global__ void epi_bias_elu4_kernel(float* C, long M, int N4, long ldc, const f
       const float4 b = reinterpret_cast<const float4*>(bias)[q];
       float4 z = *cp;
       z.x += b.x; z.y += b.y; z.z += b.z; z.w += b.w;
-      *cp = z;
       reinterpret_cast<float4*>(H + i * ldc)[q] = make_float4(elu_f(z.x), elu_f(z.y), elu_f(z.z), elu_f(z.w));
     }
 }
-__global__ void epi_times_elud4_kernel(float* C, long M, int N4, long ldc, const float* Zp) {
+__global__ void epi_times_elud4_kernel(float* C, long M, int N4, long ldc, const float* Hp) {
   for (long i = (long)blockIdx.y * blockDim.y + threadIdx.y; i < M; i += (long)gridDim.y * blockDim.y)
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < N4; q += gridDim.x * blockDim.x) {
       float4* cp = reinterpret_cast<float4*>(C + i * ldc) + q;
-      const float4 zp = reinterpret_cast<const float4*>(Zp + i * ldc)[q];
+      const float4 hp = reinterpret_cast<const float4*>(Hp + i * ldc)[q];
       float4 v = *cp;
-      v.x *= elu_d(zp.x); v.y *= elu_d(zp.y); v.z *= elu_d(zp.z); v.w *= elu_d(zp.w);
+      v.x *= elu_d_h(hp.x); v.y *= elu_d_h(hp.y); v.z *= elu_d_h(hp.z); v.w *= elu_d_h(hp.w);
       *cp = v;
     }
 }
@@ -176,21 +188,21 @@ __device__ __forceinline__ void colpart_store(CompSum (&cs)[4], int q, int N4, d
       part[(long)blockIdx.y * 4 * N4 + 4 * q + e] =
           (red[0][threadIdx.x][e] + red[1][threadIdx.x][e]) + (red[2][threadIdx.x][e] + red[3][threadIdx.x][e]);
 }
-__global__ void epi_times_elud4_colsum_kernel(float* C, long M, int N4, long ldc, const float* Zp, double* part) {
+__global__ void epi_times_elud4_colsum_kernel(float* C, long M, int N4, long ldc, const float* Hp, double* part) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   CompSum cs[4];
   if (q < N4)
     for (long i = (long)blockIdx.y * blockDim.y + threadIdx.y; i < M; i += (long)gridDim.y * blockDim.y) {
       float4* cp = reinterpret_cast<float4*>(C + i * ldc) + q;
-      const float4 zp = reinterpret_cast<const float4*>(Zp + i * ldc)[q];
+      const float4 hp = reinterpret_cast<const float4*>(Hp + i * ldc)[q];
       float4 v = *cp;
-      v.x *= elu_d(zp.x); v.y *= elu_d(zp.y); v.z *= elu_d(zp.z); v.w *= elu_d(zp.w);
+      v.x *= elu_d_h(hp.x); v.y *= elu_d_h(hp.y); v.z *= elu_d_h(hp.z); v.w *= elu_d_h(hp.w);
       *cp = v;
       cs[0].add(v.x); cs[1].add(v.y); cs[2].add(v.z); cs[3].add(v.w);
     }
   colpart_store(cs, q, N4, part);
 }
-__global__ void out_delta4_colsum_kernel(const float* dg, const float* wout, const float* Z, long N, int w4,
+__global__ void out_delta4_colsum_kernel(const float* dg, const float* wout, const float* Hl, long N, int w4,
                                          float* delta, double* part) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   CompSum cs[4];
@@ -198,9 +210,9 @@ __global__ void out_delta4_colsum_kernel(const float* dg, const float* wout, con
     const float4 wo = reinterpret_cast<const float4*>(wout)[q];
     for (long n = (long)blockIdx.y * blockDim.y + threadIdx.y; n < N; n += (long)gridDim.y * blockDim.y) {
       const float d = dg[n];
-      const float4 z = reinterpret_cast<const float4*>(Z + n * 4 * w4)[q];
-      const float4 v = make_float4(d * wo.x * elu_d(z.x), d * wo.y * elu_d(z.y), d * wo.z * elu_d(z.z),
-                                   d * wo.w * elu_d(z.w));
+      const float4 h = reinterpret_cast<const float4*>(Hl + n * 4 * w4)[q];
+      const float4 v = make_float4(d * wo.x * elu_d_h(h.x), d * wo.y * elu_d_h(h.y), d * wo.z * elu_d_h(h.z),
+                                   d * wo.w * elu_d_h(h.w));
       reinterpret_cast<float4*>(delta + n * 4 * w4)[q] = v;
       cs[0].add(v.x); cs[1].add(v.y); cs[2].add(v.z); cs[3].add(v.w);
     }
@@ -226,10 +238,8 @@ __global__ void epi_bias_elu4_out_kernel(float* C, long M, int N4, long ldc, con
     const long i = i0 + threadIdx.y;
     float dot = 0.f;
     if (i < M && q < N4) {
-      float4* cp = reinterpret_cast<float4*>(C + i * ldc) + q;
-      float4 z = *cp;
+      float4 z = reinterpret_cast<const float4*>(C + i * ldc)[q];
       z.x += b.x; z.y += b.y; z.z += b.z; z.w += b.w;
-      *cp = z;
       const float4 h = make_float4(elu_f(z.x), elu_f(z.y), elu_f(z.z), elu_f(z.w));
       reinterpret_cast<float4*>(H + i * ldc)[q] = h;
       dot = fmaf(wo.w, h.w, fmaf(wo.z, h.z, fmaf(wo.y, h.y, wo.x * h.x)));
@@ -445,16 +455,21 @@ __global__ void loss_final_kernel(const double* partial, int n, long N, double* 
   }
   if (threadIdx.x == 0) *loss = red[0] / (double)N;
 }
-__global__ void out_delta_kernel(const float* dg, const float* wout, const float* Z, int w, long N, float* delta) {
+// ZH holds z of the last hidden layer (kFromH false) or h (the TF32 path).
+template <bool kFromH>
+__device__ __forceinline__ float elu_d_zh(float v) { return kFromH ? elu_d_h(v) : elu_d(v); }
+template <bool kFromH>
+__global__ void out_delta_kernel(const float* dg, const float* wout, const float* ZH, int w, long N, float* delta) {
   const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (e >= N * w) return;
   const long n = e / w;
   const int u = (int)(e % w);
-  delta[e] = dg[n] * wout[u] * elu_d(Z[e]);
+  delta[e] = dg[n] * wout[u] * elu_d_zh<kFromH>(ZH[e]);
 }
 // The same, four units per thread (w % 4 == 0, N * w / 4 < 2^31, 16-byte aligned):
 // quad e covers row e / (w / 4), units 4 (e % (w / 4)) ..
-__global__ void out_delta4_kernel(const float* dg, const float* wout, const float* Z, int w, unsigned n_quads,
+template <bool kFromH>
+__global__ void out_delta4_kernel(const float* dg, const float* wout, const float* ZH, int w, unsigned n_quads,
                                   float* delta) {
   const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_quads) return;
@@ -462,10 +477,11 @@ __global__ void out_delta4_kernel(const float* dg, const float* wout, const floa
   const long n = e / q;
   const int u = 4 * (int)(e % q);
   const float d = dg[n];
-  const float4 z = *reinterpret_cast<const float4*>(Z + n * w + u);
+  const float4 z = *reinterpret_cast<const float4*>(ZH + n * w + u);
   const float4 wo = *reinterpret_cast<const float4*>(wout + u);
   *reinterpret_cast<float4*>(delta + n * w + u) =
-      make_float4(d * wo.x * elu_d(z.x), d * wo.y * elu_d(z.y), d * wo.z * elu_d(z.z), d * wo.w * elu_d(z.w));
+      make_float4(d * wo.x * elu_d_zh<kFromH>(z.x), d * wo.y * elu_d_zh<kFromH>(z.y),
+                  d * wo.z * elu_d_zh<kFromH>(z.z), d * wo.w * elu_d_zh<kFromH>(z.w));
 }
 
 // dq[b][j] = sum over the S points of snapshot b of din[n][m + j]  (fixed order).
@@ -607,6 +623,8 @@ static cudaError_t gemm(crom_trainer* t, cudaStream_t s, int M, int N, int K, co
     if (epi == kEpiBiasElu) {
       if (vec) epi_bias_elu4_kernel<<<vg, vb, 0, s>>>(C, M, N / 4, ldc, bias, H);
       else epi_bias_elu_kernel<<<blocks(n, 256), 256, 0, s>>>(C, M, N, ldc, bias, H);
+    } else if (epi == kEpiBias) {
+      epi_bias_kernel<<<blocks(n, 256), 256, 0, s>>>(C, M, N, ldc, bias);
     } else if (epi == kEpiTimesEluD) {
       if (vec && colpart_done && N / 4 <= 64) {  // with the column sums of the result (one block column)
         epi_times_elud4_colsum_kernel<<<dim3(1, kEpiRowBlocks), vb, 0, s>>>(C, M, N / 4, ldc, Zp, t->colpart);
@@ -664,9 +682,10 @@ cudaError_t trainer_encode(crom_trainer* t, int nb, const float* snaps, float* q
   cudaError_t e = gemm(t, s, nb, 32, Ll, x, Ll, 1, t->params + t->lay.d1w, 1, Ll, t->d1z, 32, kEpiBiasElu,
                        t->params + t->lay.d1b, t->d1h, nullptr);
   if (e != cudaSuccess) return e;
-  // q = W2 h1 + b2: reuse the bias epilogue by writing Z = q and discarding ELU into edh scratch
-  return gemm(t, s, nb, r, 32, t->d1h, 32, 1, t->params + t->lay.d2w, 1, 32, q_out, r, kEpiBiasElu,
-              t->params + t->lay.d2b, t->ed1, nullptr);
+  // q = W2 h1 + b2: the TF32 path has a bias-only epilogue; the FP32 GEMM reuses its
+  // bias + ELU epilogue (Z = q in C, the ELU discarded into the ed1 scratch)
+  return gemm(t, s, nb, r, 32, t->d1h, 32, 1, t->params + t->lay.d2w, 1, 32, q_out, r,
+              t->precision == CROM_PREC_TF32 ? kEpiBias : kEpiBiasElu, t->params + t->lay.d2b, t->ed1, nullptr);
 }
 
 cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx, const float* coords, float lr,
@@ -674,6 +693,8 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
   const int m = t->dec.m, r = t->dec.r, w = t->dec.width, L = t->dec.hidden;
   const int B = t->B, S = t->S, P = t->P;
   const long N = (long)B * S;
+  // the TF32 path keeps h, not z, of the hidden layers: s'(z) comes from h
+  const bool tf32 = t->precision == CROM_PREC_TF32;
   const TrainerLayout& lay = t->lay;
   float* p = t->params;
   float* gr = t->grads;
@@ -714,20 +735,23 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
   if (e != cudaSuccess) return e;
   colsum(t, s, t->dg, N, 1, gr + lay.dec_b[L]);
   const float* wout = p + lay.dec_w[L];
-  const bool vec_out = w % 4 == 0 && ((uintptr_t)wout & 15) == 0 && ((uintptr_t)t->Z[L - 1] & 15) == 0 &&
+  const float* zh = tf32 ? t->H[L - 1] : t->Z[L - 1];  // s'(z) of the last hidden layer from h or z
+  const bool vec_out = w % 4 == 0 && ((uintptr_t)wout & 15) == 0 && ((uintptr_t)zh & 15) == 0 &&
                        ((uintptr_t)t->delta & 15) == 0;
   // column sums of delta fused into the kernel that writes it (TF32 path), else a
   // separate deterministic pass
   bool have_part = false;
-  if (t->precision == CROM_PREC_TF32 && vec_out && w / 4 <= 64) {
-    out_delta4_colsum_kernel<<<dim3(1, kEpiRowBlocks), dim3(64, 4), 0, s>>>(t->dg, wout, t->Z[L - 1], N, w / 4,
-                                                                            t->delta, t->colpart);
+  if (tf32 && vec_out && w / 4 <= 64) {
+    out_delta4_colsum_kernel<<<dim3(1, kEpiRowBlocks), dim3(64, 4), 0, s>>>(t->dg, wout, zh, N, w / 4, t->delta,
+                                                                            t->colpart);
     have_part = true;
   } else if (vec_out && N * (w / 4) < (1L << 31)) {
-    out_delta4_kernel<<<blocks(N * (w / 4), 256), 256, 0, s>>>(t->dg, wout, t->Z[L - 1], w,
-                                                               (unsigned)(N * (w / 4)), t->delta);
+    const unsigned nq = (unsigned)(N * (w / 4));
+    if (tf32) out_delta4_kernel<true><<<blocks(N * (w / 4), 256), 256, 0, s>>>(t->dg, wout, zh, w, nq, t->delta);
+    else out_delta4_kernel<false><<<blocks(N * (w / 4), 256), 256, 0, s>>>(t->dg, wout, zh, w, nq, t->delta);
   } else {
-    out_delta_kernel<<<blocks(N * w, 256), 256, 0, s>>>(t->dg, wout, t->Z[L - 1], w, N, t->delta);
+    if (tf32) out_delta_kernel<true><<<blocks(N * w, 256), 256, 0, s>>>(t->dg, wout, zh, w, N, t->delta);
+    else out_delta_kernel<false><<<blocks(N * w, 256), 256, 0, s>>>(t->dg, wout, zh, w, N, t->delta);
   }
   float* dcur = t->delta;
   float* dnext = t->delta2;
@@ -744,9 +768,9 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
       colsum(t, s, dcur, N, w, gr + lay.dec_b[l]);
     have_part = false;
     if (l > 0) {
-      // delta_{l-1} = (delta_l W_l) * s'(Z_{l-1})
+      // delta_{l-1} = (delta_l W_l) * s'(Z_{l-1})  (s' from H_{l-1} in the TF32 path)
       e = gemm(t, s, (int)N, w, w, dcur, w, 1, p + lay.dec_w[l], w, 1, dnext, w, kEpiTimesEluD, nullptr, nullptr,
-               t->Z[l - 1], nullptr, &have_part);
+               tf32 ? t->H[l - 1] : t->Z[l - 1], nullptr, &have_part);
     } else {
       // input gradient din = delta_1 W_1  [N][m + r]
       e = gemm(t, s, (int)N, m + r, w, dcur, w, 1, p + lay.dec_w[0], m + r, 1, t->din, m + r, kEpiStore, nullptr,
@@ -766,7 +790,7 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
     return e;
   colsum(t, s, t->dq, B, r, gr + lay.d2b);
   if ((e = gemm(t, s, B, 32, r, t->dq, r, 1, p + lay.d2w, 32, 1, t->ed1, 32, kEpiTimesEluD, nullptr, nullptr,
-                t->d1z)) != cudaSuccess)
+                tf32 ? t->d1h : t->d1z)) != cudaSuccess)
     return e;
   // dense 1: gW1 = dz1^T h_conv, gb1 = sum dz1, dh_conv = dz1 W1
   const float* hconv = t->conv_h.back();
