@@ -233,6 +233,62 @@ def test_cosine_decoder_step_closed_form_2d():
     assert st == O.STATUS_OK and rel(q1, q0 * (1 - dt * alpha * lam)) < 1e-12
 
 
+class PlaneWaveDecoder2D:
+    """g(x, q) = q_1 sin(theta) + q_2 cos(theta), theta = 2 pi (k x1 + l x2): linear in q;
+    grad g = 2 pi (k, l) (q_1 cos - q_2 sin), d2g/dx_i^2 = -(2 pi k_i)^2 g."""
+
+    def __init__(self, k, l):
+        self.k, self.l = k, l
+
+    def __call__(self, X, q):
+        X = np.asarray(X, np.float64)
+        th = 2 * np.pi * (self.k * X[:, 0] + self.l * X[:, 1])
+        J = np.stack([np.sin(th), np.cos(th)], 1)
+        g = J @ q
+        dth = q[0] * np.cos(th) - q[1] * np.sin(th)
+        kk = 2 * np.pi * np.array([self.k, self.l], np.float64)
+        return O.Evaluation(g, dth[:, None] * kk[None, :], -(kk[None, :] ** 2) * g[:, None], J)
+
+
+def test_advection_diffusion_step_closed_form_and_continuous_limit():
+    """O5 (advection-diffusion): for u_t + a . grad u = nu Lap u with a uniform velocity,
+    a plane wave travels along a and decays: with z = q_1 + i q_2,
+    z(t) = exp(-(nu lam + i w) t) z(0), lam = 4 pi^2 (k^2 + l^2), w = 2 pi (a_1 k + a_2 l).
+    The decoder is linear in q, so each latent step is the forward Euler factor
+    1 - dt (nu lam + i w) exactly, and n steps converge to z(t) at first order.
+    k != l and a_1 != a_2, so swapped velocity components, a wrong sign on the
+    advection term or a dropped diffusion term each fail."""
+    k, l = 1, 2
+    a, nu = np.array([0.7, -0.3]), 0.02
+    dec = PlaneWaveDecoder2D(k, l)
+    rng = np.random.default_rng(41)
+    Y = rng.uniform(0, 1, size=(23, 2))
+    vel = np.tile(a, (Y.shape[0], 1))           # one velocity per sample, here uniform
+    q0 = np.array([0.8, -0.45])
+    lam = 4 * np.pi ** 2 * (k * k + l * l)
+    w = 2 * np.pi * (a[0] * k + a[1] * l)
+    z0 = complex(q0[0], q0[1])
+    dt = 1e-3
+    q1, st, info = O.crom_step(dec, q0, Y, dt, 2, pde="advdiff", vel=vel, nu=nu, return_info=True)
+    z1 = (1 - dt * (nu * lam + 1j * w)) * z0
+    assert st == O.STATUS_OK and rel(q1, [z1.real, z1.imag]) < 1e-12
+    assert np.abs(info["deltas"][1]).max() < 1e-14     # the second GN iteration is a no-op
+    # n steps: the discrete closed form, and first-order convergence to the continuous wave
+    T = 0.05
+    errs = []
+    for n in (50, 100, 200):
+        q = q0.copy()
+        for _ in range(n):
+            q, st = O.crom_step(dec, q, Y, T / n, 1, pde="advdiff", vel=vel, nu=nu)
+            assert st == O.STATUS_OK
+        zn = (1 - T / n * (nu * lam + 1j * w)) ** n * z0
+        assert rel(q, [zn.real, zn.imag]) < 1e-11
+        zt = np.exp(-(nu * lam + 1j * w) * T) * z0
+        errs.append(abs(complex(q[0], q[1]) - zt))
+    assert 1.8 < errs[0] / errs[1] < 2.2 and 1.8 < errs[1] / errs[2] < 2.2
+    assert errs[-1] < 5e-3 * abs(z0)
+
+
 @pytest.mark.parametrize("r", [1, 2])
 def test_gn_converges_to_brute_force_minimiser(r):
     """O6: converged GN (20 iterations) equals the brute-force minimiser of the NLS
