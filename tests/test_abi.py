@@ -61,3 +61,10 @@ def test_no_device_is_a_cuda_error_not_a_fallback(lib):
     h = ctypes.c_void_p()
     d = lib.crom_decoder_desc(2, 8, 128, 5)
     assert lib.raw_call("crom_create", ctypes.byref(h), ctypes.byref(d), 0) == lib.CROM_ERR_CUDA
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the built library the binding raises instead of computing anything."""
+    from paper_2206_02607_gb300 import crom
+    with pytest.raises(ImportError):
+        crom.load_library(str(tmp_path / "libcrom.so"))
