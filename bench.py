@@ -526,9 +526,9 @@ def main():
     recon_pts = codes.shape[0] * X.shape[0]
     recon_flops = recon_pts * 2 * (2 * 128 + 4 * 128 * 128 + 128)
 
-    # ---- rollout: 100 steps of the same batch replayed from one cached CUDA graph
+    # ---- rollout: 1000 steps of the same batch replayed from one cached CUDA graph
     qr = q0.clone()
-    n_roll = 100
+    n_roll = 1000
     crom.crom_rollout(ctx, qr, alpha, s_off, samples, status, n_steps=n_roll, dt=w.dt, gn_iters=w.gn_iters,
                       max_samples=max_s, precision=crom.CROM_PREC_BF16X2)   # records the graph
     torch.cuda.synchronize()
@@ -639,7 +639,7 @@ def main():
                                          recon_flops / (recon_ms_bf16 * 1e-3) / 1e12 / peak_tf},
             "graph_rollout": {"value": w.n_inst / (roll_ms * 1e-3), "unit": "instance-steps/s",
                               "ms_per_step": roll_ms, "steps_per_graph": n_roll,
-                              "note": "crom_rollout: 100 steps replayed from a cached CUDA graph, no L2 flush"},
+                              "note": "crom_rollout: 1000 steps replayed from a cached CUDA graph, no L2 flush"},
             "fom_advdiff2d": {"node_steps_per_s": fom_nodes / (fom_ms * 1e-3), "ms_per_step": fom_ms,
                               "gbs_algorithmic": fom_gbs, "frac_of_measured_hbm": fom_gbs / hbm,
                               "workload": "512 periodic 256^2 fields, 16 B per node-step (u, ax, ay read, u written)"},

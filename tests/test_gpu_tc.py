@@ -189,6 +189,39 @@ def test_step_tc_rollout_within_1e3():
         assert rel_l2(qT[i] - w.q0[i], traj[-1] - w.q0[i]) < 1e-2
 
 
+def test_rollout_1000_step_graph_full_batch():
+    """The batched workload end to end: all 1024 instances advanced 1000 steps by one
+    cached CUDA graph, bit-identical to 1000 crom_step calls; the instance with the
+    smallest |M_i| and one of about a hundred samples (several tiles and a ragged
+    tail) recomputed by the oracle over all 1000 steps.
+    The heat equation is dissipative, so the per-step errors (<= 2e-7 relative in q)
+    add up at most linearly: q_T within 1e-3, the increment q_T - q_0 within 1e-2."""
+    import torch
+    c = crom()
+    w = gen.heat2d_batched(n_inst=1024)
+    ctx = make_ctx(w.spec, w.params)
+    steps = 1000
+    q = dev(w.q0, torch.float64)
+    st = torch.full((w.n_inst,), -1, dtype=torch.int32, device="cuda")
+    c.crom_rollout(ctx, q, dev(w.alpha, torch.float32), dev(w.s_off, torch.int32), dev(w.samples, torch.float32),
+                   st, n_steps=steps, dt=w.dt, gn_iters=w.gn_iters, max_samples=int(w.sizes.max()),
+                   precision=c.CROM_PREC_BF16X2)
+    torch.cuda.synchronize()
+    qT, stT = q.cpu().numpy(), st.cpu().numpy()
+    assert np.all(stT == 0) and np.all(np.isfinite(qT))
+    q_ref, st_ref = run_steps(ctx, w, steps, c.CROM_PREC_BF16X2)
+    assert np.array_equal(qT, q_ref) and np.array_equal(stT, st_ref)
+    dec = O.MLPDecoder(w.params, 2)
+    order = np.argsort(w.sizes, kind="stable")
+    mid = next(int(j) for j in order if w.sizes[j] >= 90 and w.sizes[j] % 16)
+    for i in (int(order[0]), mid):
+        Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
+        traj = O.crom_rollout(dec, w.q0[i], Y, w.dt, w.gn_iters, steps, alpha=float(w.alpha[i]))
+        e_q, e_inc = rel_l2(qT[i], traj[-1]), rel_l2(qT[i] - w.q0[i], traj[-1] - w.q0[i])
+        print(f"instance {i} |M|={Y.shape[0]}: q_T {e_q:.3e}, increment {e_inc:.3e}")
+        assert e_q < 1e-3 and e_inc < 1e-2, (i, e_q, e_inc)
+
+
 @pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_BF16X2"])
 def test_rollout_graph_equals_repeated_steps(prec_name):
     """crom_rollout (a cached CUDA graph of n steps) gives bit-identical results to n
