@@ -284,15 +284,17 @@ def test_step_tc_rejects_unsupported():
     assert e.value.code == c.CROM_ERR_INVALID_ARG
 
 
-def test_step_tc_large_instance():
-    """One instance with 5000 samples (many tiles, far above the batched sizes)."""
+@pytest.mark.parametrize("n_samples", [2048, 5000])
+def test_step_tc_large_instance(n_samples):
+    """One instance with 2048 samples (the single-instance sample set of the precision
+    workload) or 5000 (many tiles, far above the batched sizes)."""
     c = crom()
     spec = gen.DecoderSpec(2, 8, 128, 5)
     params = gen.xavier_decoder(spec, seed=0, bias_std=0.05, bf16_exact=True)
     rng = np.random.default_rng(2)
-    Y = gen.interior_nodes_2d(128, 5000, rng)
+    Y = gen.interior_nodes_2d(128, n_samples, rng)
     w = gen.StepWorkload("big", spec, params, rng.standard_normal((1, 8)), np.ones(1, np.float32),
-                         gen.ragged_offsets([5000]), Y, 1e-5, 2, 1)
+                         gen.ragged_offsets([n_samples]), Y, 1e-5, 2, 1)
     ctx = make_ctx(spec, params)
     q1, st = run_steps(ctx, w, 1, c.CROM_PREC_BF16X2)
     _check_step(w, q1, st)
