@@ -143,6 +143,27 @@ def test_step_heat2d_single_config():
     assert rel_l2(q20[0] - w.q0[0], traj[-1] - w.q0[0]) < 1e-3
 
 
+def test_step_heat2d_single_config_full_rollout():
+    """The 2D heat configuration over its whole length, 1000 steps, as one cached CUDA
+    graph on the FP32 path, against the oracle's 1000 steps.  The heat equation is
+    dissipative, so per-step errors add up at most linearly: q_T within 1e-4, the
+    increment q_T - q_0 within 1e-3."""
+    import torch
+    c = crom()
+    w = gen.heat2d_single()
+    ctx = make_ctx(w.spec, w.params)
+    d = StepInputs(w)
+    c.crom_rollout(ctx, d.q, d.alpha, d.s_off, d.samples, d.status, n_steps=w.steps, dt=w.dt,
+                   gn_iters=w.gn_iters, max_samples=d.max_samples, precision=c.CROM_PREC_FP32)
+    torch.cuda.synchronize()
+    qT, st = d.q.cpu().numpy(), d.status.cpu().numpy()
+    assert st[0] == 0 and np.all(np.isfinite(qT))
+    traj = O.crom_rollout(O.MLPDecoder(w.params, 2), w.q0[0], w.samples, w.dt, w.gn_iters, w.steps)
+    e_q, e_inc = rel_l2(qT[0], traj[-1]), rel_l2(qT[0] - w.q0[0], traj[-1] - w.q0[0])
+    print(f"1000-step FP32 rollout: q_T {e_q:.3e}, increment {e_inc:.3e}")
+    assert e_q < 1e-4 and e_inc < 1e-3, (e_q, e_inc)
+
+
 def test_step_batched_ragged_matches_oracle():
     """Many instances with uneven |M_i| spanning several CTA tiles and ragged tails."""
     c = crom()
