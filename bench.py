@@ -209,29 +209,104 @@ def cpu_oracle_rate(w, budget_s=12.0, max_inst=512):
     return rate_samples / mean_all, done, samples, el
 
 
+# ---- the FP64 oracle on every host core: a process pool (spawn start method: a
+# forked child of a process that has used CUDA can hang), one numpy thread per
+# worker, each worker stepping whole instances of the workload
+_POOL_W = None
+
+
+def _pool_init(params, m, q0, s_off, samples, alpha, dt, gn_iters):
+    global _POOL_W
+    _POOL_W = (params, m, q0, s_off, samples, alpha, dt, gn_iters)
+
+
+def _pool_steps(idx):
+    from oracle import crom_oracle as O
+    params, m, q0, s_off, samples, alpha, dt, gn_iters = _POOL_W
+    dec = O.MLPDecoder(params, m)
+    n = 0
+    for i in idx:
+        Y = samples[s_off[i]:s_off[i + 1]]
+        O.crom_step(dec, q0[i], Y, dt, gn_iters, alpha=float(alpha[i]))
+        n += Y.shape[0]
+    return n
+
+
+class OraclePool:
+    """The oracle as it stands, run on all host cores (one instance per task)."""
+
+    def __init__(self, w, cores=None):
+        import multiprocessing as mp
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"      # inherited by the workers: one thread each
+        self.cores = cores or os.cpu_count() or 1
+        self.w = w
+        self.pool = mp.get_context("spawn").Pool(
+            self.cores, initializer=_pool_init,
+            initargs=(w.params, w.spec.m, w.q0, w.s_off, w.samples, w.alpha, w.dt, w.gn_iters))
+        # start-up outside any timing; every wait on the pool is bounded (a worker that
+        # dies leaves a plain map() waiting forever)
+        self.pool.map_async(_pool_steps, [[] for _ in range(self.cores)]).get(timeout=300)
+
+    def rate(self, n_inst):
+        """Steps the first n_inst instances once; returns (instance-steps/s normalised by
+        the workload's mean |M_i|, samples, seconds)."""
+        idx = [[i] for i in range(min(n_inst, self.w.n_inst))]
+        t0 = time.perf_counter()
+        samples = sum(self.pool.map_async(_pool_steps, idx, chunksize=1).get(timeout=600))
+        el = time.perf_counter() - t0
+        return samples / el / float(np.mean(self.w.sizes)), samples, el
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def bench_config(n_inst, world, samples_per_step):
+    """The workload's config, shared by both arms of the bench."""
+    return {"workload": WORKLOAD, "global_batch": world * n_inst, "samples_per_step": samples_per_step,
+            "parallelism": f"instances sharded, {n_inst} per GPU" if world > 1 else "single GPU",
+            "l2": "flushed (256 MB write) before every timed step (GPU arm)"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
     from workloads import gen
     w = gen.heat2d_batched(n_inst=args.n_inst)
+    pool = OraclePool(w)
+    n_sample = 4 * pool.cores        # instances per reference step: a bounded sample of the batch
     times = []
-    inst_done = 0
     for k in range(args.warmup + args.steps):
-        rate, done, samples, el = cpu_oracle_rate(w, budget_s=3.0, max_inst=64)
+        rate, samples, el = pool.rate(n_sample)
         if k >= args.warmup:
             times.append(rate)
-            inst_done += done
+    pool.close()
     value = float(np.mean(times))
     line = {"metric": METRIC, "value": value, "unit": "instance-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * args.n_inst / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "global_batch": args.n_inst, "parallelism": "none",
-                       "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": "instance-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: the FP64 numpy oracle on the first instances of the "
-                                       f"workload for ~3 s, normalised by mean |M_i|"},
+            "config": bench_config(args.n_inst, 1, int(w.sizes.sum())),
+            "cpu_baseline": {"value": value, "unit": "instance-steps/s", "cores": pool.cores, "kind": "oracle",
+                             "cpu": cpu_model(),
+                             "sample": f"each step: the FP64 numpy oracle on the first {n_sample} instances of "
+                                       f"the workload, one instance per task on {pool.cores} worker processes; "
+                                       f"rate normalised by the workload's mean |M_i| (ms_per_step is the full "
+                                       f"{args.n_inst}-instance batch at that rate)"},
             "e2e": {"value": value, "unit": "instance-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -609,10 +684,18 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, done, ns, el = cpu_oracle_rate(w, budget_s=12.0)
-        cpu = {"value": rate, "unit": "instance-steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"FP64 numpy oracle, one step of the first {done} instances ({ns} samples, "
-                         f"{el:.1f} s), normalised by the workload's mean |M_i|"}
+        rate1, done, ns, el = cpu_oracle_rate(w, budget_s=8.0)
+        pool = OraclePool(w)
+        n_all = min(w.n_inst, 16 * pool.cores)
+        rate_all, ns_all, el_all = pool.rate(n_all)
+        pool.close()
+        cpu = {"value": rate_all, "unit": "instance-steps/s", "cores": pool.cores, "kind": "oracle",
+               "cpu": cpu_model(),
+               "sample": f"FP64 numpy oracle, one step of the first {n_all} instances ({ns_all} samples, "
+                         f"{el_all:.1f} s) on {pool.cores} worker processes (one numpy thread each), normalised "
+                         f"by the workload's mean |M_i|",
+               "single_thread": {"value": rate1, "cores": 1,
+                                 "sample": f"one step of the first {done} instances ({ns} samples, {el:.1f} s)"}}
 
     if rank == 0:
         line = {
@@ -620,11 +703,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16x2 (bf16 hi/lo operands, f32 accum, f64 solve)",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": world * w.n_inst, "samples_per_step": int(w.sizes.sum()),
-                       "parallelism": f"instances sharded, {w.n_inst} per GPU" if world > 1 else "single GPU",
-                       "l2": "flushed (256 MB write) before every timed step",
-                       "tiles": {"s0": tile_s0, "s1": tile_s1, "autotuned": args.tiles == "auto",
-                                 "ms_per_step_large_small_s1": [round(tile_ms[0], 4), round(tile_ms[1], 4)]}},
+            "config": bench_config(w.n_inst, world, int(w.sizes.sum())),
+            "tiles": {"s0": tile_s0, "s1": tile_s1, "autotuned": args.tiles == "auto",
+                      "ms_per_step_large_small_s1": [round(tile_ms[0], 4), round(tile_ms[1], 4)]},
             "status_all_ok": bool(np.all(st == 0)),
             "accuracy_vs_fp64_oracle": acc,
             "plain_fp32_single": {"value": plain_value, "unit": "instance-steps/s", "us_per_step": plain_ms * 1e3,

@@ -53,6 +53,7 @@ size_t kmajor_sw128(int row, int k, int rows) {
 }
 
 void free_weights(crom_ctx* ctx) {
+  ++ctx->scratch_gen;  // a recorded rollout refers to these buffers
   auto& w = ctx->w;
   cudaFree(w.w1);
   cudaFree(w.b1);
@@ -326,6 +327,9 @@ int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_in
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
   if (precision == CROM_PREC_FP32) {
+    if (step_fp32_max_tiles(ctx, n_inst, max_samples) > 65535)
+      return fail(CROM_ERR_INVALID_ARG, "crom_step: max_samples too large for the FP32 step's grid (at most 65535 "
+                                        "CTAs per instance); use CROM_PREC_BF16X2 or split the instance");
     e = launch_step_fp32(ctx, step, n_inst, q, alpha, vel, s_off, samples, n_samples, max_samples, status, s);
   } else if (precision == CROM_PREC_BF16X2) {
     if (!tc_shape_ok(ctx->desc) || !ctx->w.tc_img)
@@ -427,18 +431,49 @@ int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n
       return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: BF16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15, ELU");
   } else if (precision != CROM_PREC_FP32) {
     return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: precision not available for the step");
+  } else if (step_fp32_max_tiles(ctx, n_inst, max_samples) > 65535) {
+    return fail(CROM_ERR_INVALID_ARG, "crom_rollout: max_samples too large for the FP32 step's grid (at most 65535 "
+                                      "CTAs per instance)");
   }
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   // The key: every argument that the recorded launches depend on.
+  // The key: every argument that the recorded launches depend on, and the
+  // generation of the context's weights and scratch (a reallocation by a later
+  // crom_step, crom_autotune, crom_robust_samples or crom_set_weights on this
+  // context frees the buffers an older recording refers to).
   struct Key {
     int precision, n_steps, n_inst, n_samples, max_samples, pde, gn_iters, coef_per_sample, line_search, tiles;
     double dt;
-    const void *q, *alpha, *vel, *s_off, *samples, *status, *weights;
-  } key{precision, n_steps, n_inst, n_samples, max_samples, step->pde, step->gn_iters, step->coef_per_sample,
-        step->line_search, ctx->tc_tile_s1, step->dt, q, alpha, vel, s_off, samples, status, ctx->w.w1};
-  std::vector<unsigned char> kb(sizeof(Key));
-  memcpy(kb.data(), &key, sizeof(Key));
+    const void *q, *alpha, *vel, *s_off, *samples, *status;
+    unsigned long long gen;
+  };
+  auto make_key = [&]() {
+    Key key{};
+    memset(&key, 0, sizeof(Key));  // padding bytes take part in the comparison
+    key.precision = precision;
+    key.n_steps = n_steps;
+    key.n_inst = n_inst;
+    key.n_samples = n_samples;
+    key.max_samples = max_samples;
+    key.pde = step->pde;
+    key.gn_iters = step->gn_iters;
+    key.coef_per_sample = step->coef_per_sample;
+    key.line_search = step->line_search;
+    key.tiles = ctx->tc_tile_s1;
+    key.dt = step->dt;
+    key.q = q;
+    key.alpha = alpha;
+    key.vel = vel;
+    key.s_off = s_off;
+    key.samples = samples;
+    key.status = status;
+    key.gen = ctx->scratch_gen;
+    std::vector<unsigned char> kb(sizeof(Key));
+    memcpy(kb.data(), &key, sizeof(Key));
+    return kb;
+  };
+  const std::vector<unsigned char> kb = make_key();
   cudaError_t e;
   if (!ctx->rollout_exec || kb != ctx->rollout_key) {
     if (!ctx->cap_stream) {
@@ -470,7 +505,9 @@ int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n
     if (e != cudaSuccess) return cuda_fail(e, "crom_rollout (instantiate)");
     if (ctx->rollout_exec) cudaGraphExecDestroy(ctx->rollout_exec);
     ctx->rollout_exec = exec;
-    ctx->rollout_key = kb;
+    // taken after recording: a first use that grew the scratch while recording has
+    // bumped the generation, and the recording refers to the new buffers
+    ctx->rollout_key = make_key();
   }
   e = cudaGraphLaunch(ctx->rollout_exec, s);
   if (e != cudaSuccess) return cuda_fail(e, "crom_rollout (launch)");
@@ -585,6 +622,9 @@ int crom_step_noalloc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, dou
   if (step->pde == CROM_PDE_ADVDIFF && !vel)
     return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: advection needs vel");
   if (max_samples < 1) return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: max_samples must be >= 1");
+  if (step_fp32_max_tiles(ctx, n_inst, max_samples) > 65535)
+    return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: max_samples too large for the FP32 step's grid (at most "
+                                      "65535 CTAs per instance)");
   DeviceGuard g(ctx->device);
   size_t need = 0;
   cudaError_t e = launch_step_fp32_noalloc(ctx, step, n_inst, q, alpha, vel, s_off, samples, n_samples,

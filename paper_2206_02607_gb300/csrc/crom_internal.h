@@ -74,6 +74,10 @@ struct crom_ctx {
   // measured).
   int tc_tile_s1 = crom::kTcTileS1Large;
   float tune_ms[2] = {-1.f, -1.f};
+  // Bumped whenever a device buffer that a recorded launch refers to (weights or
+  // step scratch) is freed and reallocated: part of the rollout graph's key, so a
+  // graph recorded before the change is never replayed against freed memory.
+  unsigned long long scratch_gen = 0;
   // Cached rollout graph and the arguments it was recorded with.
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t rollout_exec = nullptr;
@@ -146,6 +150,9 @@ cudaError_t launch_step_fp32(crom_ctx* ctx, const crom_step_desc* step, int n_in
                              const float* alpha, const float* vel, const int* s_off,
                              const float* samples, int n_samples, int max_samples, int* status,
                              cudaStream_t s);
+// Second grid dimension (CTAs per instance) of the FP32 step for a batch; the
+// launch needs it <= 65535.
+int step_fp32_max_tiles(const crom_ctx* ctx, int n_inst, int max_samples);
 
 // v_p = (dg/dq)(x_p, q_i) . (q_i - q_prev_i) / dt from dq [r][n_pts] (decode output).
 cudaError_t launch_tangent_fp32(const crom_ctx* ctx, int n_inst, const double* q, const double* q_prev, double dt,

@@ -73,6 +73,7 @@ struct FwdParams {
   int max_samples;
   double* qio;
   int* status;
+  int n_samples;  // length of the sample arrays: every instance's range must lie inside
   double* partials;
   int max_tiles;
   int n_entries;
@@ -201,7 +202,7 @@ __device__ __forceinline__ void fwd_fp32_body(const FwdParams& p) {
     const int o0 = __ldg(&p.off[inst]);
     msz = __ldg(&p.off[inst + 1]) - o0;
     if (p.iter == 0) {
-      if (msz < r || msz > p.max_samples) {
+      if (msz < r || msz > p.max_samples || o0 < 0 || o0 + msz > p.n_samples) {
         if (t == 0 && tid == 0) p.status[inst] = CROM_ERR_INVALID_ARG;
         return;
       }
@@ -593,6 +594,22 @@ cudaError_t launch_recon_fp32(const crom_ctx* ctx, int n_codes, const double* q,
   return launch_fwd(p, grid, s);
 }
 
+// Samples per CTA of the FP32 step: enough CTAs to cover the GPU at least twice
+// when possible, within the shared-memory budget of the first iteration's channels.
+int step_samples_per_cta(const crom_ctx* ctx, int n_inst, int max_samples) {
+  const int m = ctx->desc.m, r = ctx->desc.r;
+  const int C0 = ChannelSet{m, kSecondLap, r}.count(m);
+  int S = 4;
+  while (S > 1 && (long long)n_inst * ((max_samples + S - 1) / S) < 2LL * ctx->num_sms) S >>= 1;
+  return pick_samples(ctx->desc.width, C0, m, r, S);
+}
+
+int step_fp32_max_tiles(const crom_ctx* ctx, int n_inst, int max_samples) {
+  const int S = step_samples_per_cta(ctx, n_inst, max_samples);
+  const long long t = ((long long)max_samples + S - 1) / S;
+  return t > (1LL << 30) ? (1 << 30) : (int)t;
+}
+
 cudaError_t launch_step_fp32(crom_ctx* ctx, const crom_step_desc* step, int n_inst, double* q,
                              const float* alpha, const float* vel, const int* s_off,
                              const float* samples, int n_samples, int max_samples, int* status,
@@ -601,11 +618,7 @@ cudaError_t launch_step_fp32(crom_ctx* ctx, const crom_step_desc* step, int n_in
   p.mode = kModeStep;
   fill_decoder(p, ctx);
   const int m = p.m, r = p.r;
-  const int C0 = ChannelSet{m, kSecondLap, r}.count(m);
-  // Samples per CTA: enough CTAs to cover the GPU at least twice when possible.
-  int S = 4;
-  while (S > 1 && (long long)n_inst * ((max_samples + S - 1) / S) < 2LL * ctx->num_sms) S >>= 1;
-  S = pick_samples(p.width, C0, m, r, S);
+  const int S = step_samples_per_cta(ctx, n_inst, max_samples);
   const int max_tiles = (max_samples + S - 1) / S;
   const int n_entries = r * (r + 1) / 2 + r;
 
@@ -613,6 +626,7 @@ cudaError_t launch_step_fp32(crom_ctx* ctx, const crom_step_desc* step, int n_in
   const size_t need_part = (size_t)n_inst * max_tiles * n_entries;
   if (need_part > ctx->partials_cap) {
     if (ctx->partials) cudaFree(ctx->partials);
+    ++ctx->scratch_gen;
     ctx->partials = nullptr;
     ctx->partials_cap = 0;
     cudaError_t e = cudaMalloc(&ctx->partials, need_part * sizeof(double));
@@ -621,6 +635,7 @@ cudaError_t launch_step_fp32(crom_ctx* ctx, const crom_step_desc* step, int n_in
   }
   if ((size_t)n_inst > ctx->counters_cap) {
     if (ctx->counters) cudaFree(ctx->counters);
+    ++ctx->scratch_gen;
     ctx->counters = nullptr;
     ctx->counters_cap = 0;
     cudaError_t e = cudaMalloc(&ctx->counters, (size_t)n_inst * sizeof(int));
@@ -631,6 +646,7 @@ cudaError_t launch_step_fp32(crom_ctx* ctx, const crom_step_desc* step, int n_in
   }
   if ((size_t)n_samples > ctx->targets_cap) {
     if (ctx->targets) cudaFree(ctx->targets);
+    ++ctx->scratch_gen;
     ctx->targets = nullptr;
     ctx->targets_cap = 0;
     cudaError_t e = cudaMalloc(&ctx->targets, (size_t)n_samples * sizeof(double));
@@ -639,6 +655,7 @@ cudaError_t launch_step_fp32(crom_ctx* ctx, const crom_step_desc* step, int n_in
   }
   if ((size_t)n_inst * r > ctx->qbase_cap) {
     if (ctx->qbase) cudaFree(ctx->qbase);
+    ++ctx->scratch_gen;
     ctx->qbase = nullptr;
     ctx->qbase_cap = 0;
     cudaError_t e = cudaMalloc(&ctx->qbase, (size_t)n_inst * r * sizeof(double));
@@ -658,6 +675,7 @@ cudaError_t launch_step_fp32(crom_ctx* ctx, const crom_step_desc* step, int n_in
   p.max_samples = max_samples;
   p.qio = q;
   p.status = status;
+  p.n_samples = n_samples;
   p.partials = ctx->partials;
   p.max_tiles = max_tiles;
   p.n_entries = n_entries;
@@ -740,10 +758,7 @@ cudaError_t launch_step_fp32_noalloc(const crom_ctx* ctx, const crom_step_desc* 
   p.mode = kModeStep;
   fill_decoder(p, ctx);
   const int m = p.m, r = p.r;
-  const int C0 = ChannelSet{m, kSecondLap, r}.count(m);
-  int S = 4;
-  while (S > 1 && (long long)n_inst * ((max_samples + S - 1) / S) < 2LL * ctx->num_sms) S >>= 1;
-  S = pick_samples(p.width, C0, m, r, S);
+  const int S = step_samples_per_cta(ctx, n_inst, max_samples);
   const int max_tiles = (max_samples + S - 1) / S;
   const int n_entries = r * (r + 1) / 2 + r;
   // layout inside the static array
@@ -772,6 +787,7 @@ cudaError_t launch_step_fp32_noalloc(const crom_ctx* ctx, const crom_step_desc* 
   p.max_samples = max_samples;
   p.qio = q;
   p.status = status;
+  p.n_samples = n_samples;
   p.partials = reinterpret_cast<double*>(b + off_part);
   p.max_tiles = max_tiles;
   p.n_entries = n_entries;

@@ -101,6 +101,7 @@ struct StepParams {
   const int* off;
   const float* x;
   int max_samples;
+  int n_samples;  // length of the sample arrays: every instance's range must lie inside
   int* status;
   const int* order;
   int* queue;   // [0] work counter, [1] timeout flag
@@ -739,7 +740,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
     const int inst = p.order[idx];
     const int o0 = p.off[inst];
     const int M = p.off[inst + 1] - o0;
-    if (M < r || M > p.max_samples) {
+    if (M < r || M > p.max_samples || o0 < 0 || o0 + M > p.n_samples) {
       if (c.gt == 0) p.status[inst] = CROM_ERR_INVALID_ARG;
       continue;
     }
@@ -893,6 +894,7 @@ cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst
                            int n_samples, int max_samples, int* status, cudaStream_t s) {
   if ((size_t)n_inst > ctx->order_cap) {
     if (ctx->order) cudaFree(ctx->order);
+    ++ctx->scratch_gen;
     ctx->order = nullptr;
     ctx->order_cap = 0;
     cudaError_t e = cudaMalloc(&ctx->order, (size_t)n_inst * sizeof(int));
@@ -901,6 +903,7 @@ cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst
   }
   if ((size_t)n_samples > ctx->targets_cap) {
     if (ctx->targets) cudaFree(ctx->targets);
+    ++ctx->scratch_gen;
     ctx->targets = nullptr;
     ctx->targets_cap = 0;
     cudaError_t e = cudaMalloc(&ctx->targets, (size_t)std::max(n_samples, 1) * sizeof(double));
@@ -932,6 +935,7 @@ cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst
   p.off = s_off;
   p.x = samples;
   p.max_samples = max_samples;
+  p.n_samples = n_samples;
   p.status = status;
   p.order = ctx->order;
   p.queue = ctx->queue;

@@ -527,6 +527,39 @@ def test_step_per_sample_coefficient_sine_decoder():
     assert rel(q_const - q0, d_ref) > 0.1
 
 
+
+@pytest.mark.parametrize("per_sample", [False, True])
+def test_step_batched_closed_form_per_instance(per_sample):
+    """crom_step_batched against the sine decoder's least-squares closed form, one
+    instance at a time: uneven sizes in no particular order (a larger instance after
+    a smaller one, one at |M| = r, one below r), each instance with its own samples,
+    q_n and coefficient.  With per-sample coefficients every sample has a different
+    nu(y_j), so handing an instance its neighbour's samples or coefficients, or
+    indexing the coefficient by instance, changes the step."""
+    r = 4
+    dec = FourierDecoder1D(r)
+    rng = np.random.default_rng(21)
+    sizes = [9, 15, r, 2, 11]
+    Ys = [np.sort(rng.uniform(0.02, 0.98, size=n))[:, None] for n in sizes]
+    samples = np.concatenate(Ys)
+    off = gen.ragged_offsets(sizes)
+    q = rng.standard_normal((len(sizes), r))
+    dt = 1e-4
+    alpha = rng.uniform(0.2, 1.0, size=samples.shape[0] if per_sample else len(sizes))
+    got, st = O.crom_step_batched(dec, q, off, samples, alpha, dt, 1, alpha_per_sample=per_sample)
+    k = np.arange(1, r + 1)
+    for i, Y in enumerate(Ys):
+        if sizes[i] < r:
+            assert st[i] == O.STATUS_BAD_ARG and np.array_equal(got[i], q[i])
+            continue
+        nu = alpha[off[i]:off[i + 1]] if per_sample else alpha[i]
+        S = np.sin(np.pi * np.outer(Y[:, 0], k))
+        lap = -(S * (np.pi * k) ** 2) @ q[i]
+        d_ref = np.linalg.lstsq(S, dt * nu * lap, rcond=None)[0]
+        assert st[i] == O.STATUS_OK
+        assert rel(got[i] - q[i], d_ref) < 1e-10, i
+
+
 # ------------------------------------------------------------------ f1: backtracking line search
 
 class CubicDecoder:
