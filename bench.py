@@ -72,7 +72,7 @@ def run_only(args):
     n = args.warmup + args.steps
     if args.only in ("step", "plain"):
         w = gen.heat2d_batched(n_inst=args.n_inst) if args.only == "step" else gen.heat2d_single()
-        prec = crom.CROM_PREC_BF16X2 if args.only == "step" else crom.CROM_PREC_FP32
+        prec = crom.CROM_PREC_F16X2 if args.only == "step" else crom.CROM_PREC_FP32
         ctx = crom.crom_create(w.spec.m, w.spec.r, w.spec.width, w.spec.hidden, 0)
         crom.crom_set_weights(ctx, gen.pack_params(w.params))
         q = torch.tensor(w.q0, device="cuda")
@@ -113,7 +113,7 @@ def run_only(args):
         c, x = torch.tensor(codes, device="cuda"), torch.tensor(X, device="cuda")
         out = torch.empty((codes.shape[0], X.shape[0]), device="cuda")
         for _ in range(n):
-            crom.crom_reconstruct(ctx, c, x, out, precision=crom.CROM_PREC_BF16X2)
+            crom.crom_reconstruct(ctx, c, x, out, precision=crom.CROM_PREC_F16X2)
         torch.cuda.synchronize()
         print(json.dumps({"only": "recon", "codes": codes.shape[0], "points": X.shape[0], "calls": n}))
     ctx.close()
@@ -345,7 +345,7 @@ def measure_next_rows(crom, gen, ctx, w, q0, alpha, s_off, samples, status, stre
         def f1():
             q.copy_(q0)
             crom.crom_step(ctx, q, alpha, s_off, samples, status, dt=dt, gn_iters=w.gn_iters, max_samples=max_s,
-                           precision=crom.CROM_PREC_BF16X2, line_search=4)
+                           precision=crom.CROM_PREC_F16X2, line_search=4)
         ms = timed(f1, 5)
         out[name] = {"ms_per_step": ms, "instance_steps_per_s": w.n_inst / (ms * 1e-3), "halvings_max": 4,
                      "workload": f"1024 instances of the step's workload, dt = {dt:g}, 2 GN iterations, "
@@ -356,7 +356,7 @@ def measure_next_rows(crom, gen, ctx, w, q0, alpha, s_off, samples, status, stre
     def f3():
         q.copy_(q0)
         crom.crom_step(ctx, q, alpha_s, s_off, samples, status, dt=w.dt, gn_iters=w.gn_iters, max_samples=max_s,
-                       precision=crom.CROM_PREC_BF16X2, coef_per_sample=True)
+                       precision=crom.CROM_PREC_F16X2, coef_per_sample=True)
     ms = timed(f3, 5)
     out["coef_per_sample"] = {"ms_per_step": ms, "instance_steps_per_s": w.n_inst / (ms * 1e-3),
                               "workload": "1024 instances, alpha per sample"}
@@ -393,7 +393,7 @@ def measure_next_rows(crom, gen, ctx, w, q0, alpha, s_off, samples, status, stre
     # 20-step candidate rollouts; the "full-order" fields are synthetic sines
     spec1 = gen.DecoderSpec(1, 4, 128, 3)
     ctx1 = crom.crom_create(1, 4, 128, 3, local)
-    crom.crom_set_weights(ctx1, gen.pack_params(gen.xavier_decoder(spec1, seed=9, bias_std=0.1, bf16_exact=True)))
+    crom.crom_set_weights(ctx1, gen.pack_params(gen.xavier_decoder(spec1, seed=9, bias_std=0.1)))
     P = 257
     xs = np.arange(P) / (P - 1)
     nodes = torch.tensor(xs.astype(np.float32)[:, None], device="cuda")
@@ -403,7 +403,7 @@ def measure_next_rows(crom, gen, ctx, w, q0, alpha, s_off, samples, status, stre
     fom = torch.tensor(np.stack([np.sin((k + 1) * np.pi * xs) * 0.1 for k in range(4)]).astype(np.float32),
                        device="cuda")
     init = list(np.linspace(8, P - 9, 8).astype(int))
-    for prec_name in ("CROM_PREC_FP32", "CROM_PREC_BF16X2"):
+    for prec_name in ("CROM_PREC_FP32", "CROM_PREC_F16X2"):
         t0 = time.perf_counter()
         idx, met = crom.crom_robust_samples(ctx1, q0r, coef, nodes, fom, init, dt=3e-4, gn_iters=1, n_steps=20,
                                             n_try=8, target=0.0, max_samples=24,
@@ -458,7 +458,7 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
 
-    def step(prec=crom.CROM_PREC_BF16X2, qq=None):
+    def step(prec=crom.CROM_PREC_F16X2, qq=None):
         crom.crom_step(ctx, q if qq is None else qq, alpha, s_off, samples, status, dt=w.dt,
                        gn_iters=w.gn_iters, max_samples=max_s, precision=prec)
 
@@ -525,7 +525,7 @@ def main():
     def e2e_step():
         hq.copy_(hq0)  # every step starts from the same state
         crom.crom_step_host(ctx, hq, ha, ho, hs, hst, dt=w.dt, gn_iters=w.gn_iters, max_samples=max_s,
-                            precision=crom.CROM_PREC_BF16X2)
+                            precision=crom.CROM_PREC_F16X2)
 
     # wall-clock timing of host-synchronised steps: at least 100 of them, so that a
     # host-side hiccup of a few ms does not dominate a short run
@@ -596,8 +596,8 @@ def main():
             rt.append(e0.elapsed_time(e1))
         return float(np.median(rt))
 
-    recon_ms_bf16 = time_recon(crom.CROM_PREC_BF16)
-    recon_ms = time_recon(crom.CROM_PREC_BF16X2)
+    recon_ms_bf16 = time_recon(crom.CROM_PREC_F16)
+    recon_ms = time_recon(crom.CROM_PREC_F16X2)
     recon_pts = codes.shape[0] * X.shape[0]
     recon_flops = recon_pts * 2 * (2 * 128 + 4 * 128 * 128 + 128)
 
@@ -605,12 +605,12 @@ def main():
     qr = q0.clone()
     n_roll = 1000
     crom.crom_rollout(ctx, qr, alpha, s_off, samples, status, n_steps=n_roll, dt=w.dt, gn_iters=w.gn_iters,
-                      max_samples=max_s, precision=crom.CROM_PREC_BF16X2)   # records the graph
+                      max_samples=max_s, precision=crom.CROM_PREC_F16X2)   # records the graph
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     crom.crom_rollout(ctx, qr, alpha, s_off, samples, status, n_steps=n_roll, dt=w.dt, gn_iters=w.gn_iters,
-                      max_samples=max_s, precision=crom.CROM_PREC_BF16X2)
+                      max_samples=max_s, precision=crom.CROM_PREC_F16X2)
     e1.record(stream)
     torch.cuda.synchronize()
     roll_ms = e0.elapsed_time(e1) / n_roll
@@ -675,9 +675,10 @@ def main():
         return e0.elapsed_time(e1) / reps
 
     train_ms_fp32 = time_train(crom.CROM_PREC_FP32, 3)
-    train_ms = time_train(crom.CROM_PREC_TF32, 10)
+    train_ms = time_train(crom.CROM_PREC_BF16_MIXED, 10)
     pts = Bt * St
     train_flops = pts * 6 * (2 * (2 + rt) * wt + 2 * (Lt - 1) * wt * wt + 2 * wt) / 2
+    train_bytes = (4.5 + 7 * (Lt - 1)) * pts * wt * 2
     tr.close()
 
     next_rows = measure_next_rows(crom, gen, ctx, w, q0, alpha, s_off, samples, status, stream, flush, local)
@@ -730,7 +731,13 @@ def main():
                            "workload": "1024 zero-flux 256^2 fields, 8 B per node-step (u read and written)"},
             "training": {"point_samples_per_s": pts / (train_ms * 1e-3), "ms_per_step": train_ms,
                          "tflops_algorithmic": train_flops / (train_ms * 1e-3) / 1e12,
-                         "precision": "TF32 tensor-core GEMMs (cuBLAS), FP32 elsewhere",
+                         "frac_of_measured_bf16": train_flops / (train_ms * 1e-3) / 1e12 / peak_tf,
+                         "hbm_gbs_algorithmic": train_bytes / (train_ms * 1e-3) / 1e9,
+                         "frac_of_measured_hbm": train_bytes / (train_ms * 1e-3) / 1e9 / hbm,
+                         "bytes_note": "decoder pass: 4.5 + 7 (L - 1) reads or writes of a [B*S][w] bf16 "
+                                       "array per step (activations, deltas), the roofline that binds here",
+                         "precision": "library tcgen05 GEMMs with fused epilogues, bf16 operands, FP32 "
+                                      "accumulation and master weights",
                          "fp32_ms_per_step": train_ms_fp32,
                          "workload": "64 snapshots x 4096 points, decoder R^{2+16}->R width 256 x 5 ELU, "
                                      "strided-conv encoder, Adam"},

@@ -55,17 +55,39 @@ typedef enum {
 /* Arithmetic of the decoder evaluation.
  *  FP32   : CUDA-core FP32 forward-mode channels (paper Algorithm 2), FP64 normal
  *           equations.  Any shape with width % 32 == 0, width <= 256.
- *  BF16X2 : tcgen05 tensor cores, bf16 operands with FP32 accumulation.  Every
- *           activation operand is split into a bf16 high part and a bf16 low part
+ *  F16X2  : tcgen05 tensor cores, f16 operands with FP32 accumulation.  Every
+ *           activation operand is split into an f16 high part and an f16 low part
  *           (multiplied by the same MMAs into separate FP32 accumulator columns,
- *           added in the epilogue), weights are rounded once to bf16.  FP32
- *           activation/derivative chains, FP64 normal equations.
- *           width == 128, 2 <= hidden <= 5, m <= 2, r <= 15, ELU.
- *  BF16   : as BF16X2 with the high parts only.  Dense reconstruction only.
- *  TF32   : training step only: the dense products on the tensor cores with
- *           TF32 operands (10-bit mantissa) and FP32 accumulation, through cuBLAS
- *           (plain GEMMs); every other step of the training pass in FP32. */
-typedef enum { CROM_PREC_FP32 = 0, CROM_PREC_BF16X2 = 1, CROM_PREC_BF16 = 2, CROM_PREC_TF32 = 3 } crom_precision;
+ *           added in the epilogue), so it carries ~2^-22 relative.  The step
+ *           rounds the hidden weights once to f16 (2^-12 relative); the dense
+ *           reconstruction also multiplies their f16 low parts W - f16(W) (held in
+ *           tensor memory) into the accumulator, ~2^-22.  The step carries the
+ *           derivative channels scaled by powers of two chosen from the weights
+ *           (and per Gauss-Newton iteration for the difference channel), so that
+ *           their f16 operands stay in range.  FP32 activation/derivative chains,
+ *           FP64 normal equations.  width == 128, 2 <= hidden <= 5, m <= 2, r <= 15,
+ *           ELU, every hidden weight, w_out and W_1q entry of magnitude <= 65000.
+ *           f16 rather than bf16 operands: both run at the same tensor rate, and
+ *           bf16 weights (2^-9) move dense outputs by ~5e-3 and latent increments by
+ *           several per cent against FP32 weights.
+ *  F16    : as F16X2 with the high parts of the activations only and f16 weights.
+ *           Dense reconstruction only.
+ *  BF16_MIXED : training step only: the decoder's dense products on the tcgen05
+ *           tensor cores (the library's TMA-fed GEMM) with bf16 weights,
+ *           activations and deltas and FP32 accumulation, the elementwise work
+ *           fused into the GEMM epilogues; FP32 master weights, FP32 Adam, FP32
+ *           encoder and input layer.  width in {64, 128, 256}, hidden >= 2,
+ *           m + r <= 32.
+ *  BF16X2, BF16: earlier names of F16X2 and F16 (the same values).  The value 3
+ *           (a TF32 training mode of an earlier version) is no longer accepted. */
+typedef enum {
+  CROM_PREC_FP32 = 0,
+  CROM_PREC_F16X2 = 1,
+  CROM_PREC_F16 = 2,
+  CROM_PREC_BF16_MIXED = 4,
+  CROM_PREC_BF16X2 = 1,
+  CROM_PREC_BF16 = 2
+} crom_precision;
 
 typedef enum { CROM_PDE_HEAT = 0, CROM_PDE_ADVDIFF = 1 } crom_pde;
 
@@ -133,7 +155,7 @@ int crom_tangent_velocity(crom_ctx* ctx, int n_inst, const double* q, const doub
  *             (the paper's backtracking line search, §4.3); if none does, q is
  *             kept and the instance's remaining iterations are skipped.  Each
  *             trial costs one value-only pass over the instance's samples.
- *             Available with CROM_PREC_BF16X2 (the FP32 path returns
+ *             Available with CROM_PREC_F16X2 (the FP32 path returns
  *             CROM_ERR_UNSUPPORTED). */
 typedef struct {
   int pde;
@@ -161,7 +183,7 @@ int crom_destroy(crom_ctx* ctx);
  * layer l = 1..hidden+1, W_l row-major [out][in] then b_l [out]; layer 1 takes
  * (x_1..x_m, q_1..q_r).  n must equal the parameter count.  params_on_device
  * selects whether `params` is a device (1) or host (0) pointer.  The call builds
- * the FP32 copies and the bf16 tensor-core images and synchronises `stream`. */
+ * the FP32 copies and the f16 tensor-core images and synchronises `stream`. */
 int crom_set_weights(crom_ctx* ctx, const float* params, size_t n, int params_on_device,
                      crom_stream stream);
 
@@ -189,7 +211,7 @@ int crom_decode(crom_ctx* ctx, int n_inst, const double* q, const int* pt_off, c
  *   instance over several CTAs (the last CTA to finish reduces and solves); the
  *   context grows its scratch on first use, so the first call for a given size
  *   must not be made during stream capture.
- * precision CROM_PREC_BF16X2: one persistent launch per step (plus a small
+ * precision CROM_PREC_F16X2: one persistent launch per step (plus a small
  *   ordering kernel); each of a CTA's four 128-thread groups takes whole
  *   instances, largest |M_i| first, from a queue. */
 int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_inst, double* q,
@@ -208,7 +230,7 @@ int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n
                  const float* alpha, const float* vel, const int* s_off, const float* samples, int n_samples,
                  int max_samples, int* status, crom_stream stream);
 
-/* Sample-tile shape of the tensor-core step (CROM_PREC_BF16X2): s0 samples per
+/* Sample-tile shape of the tensor-core step (CROM_PREC_F16X2): s0 samples per
  * forward tile in the first Gauss-Newton iteration (4 channels: 8, fixed by the
  * 32 hi-part operand columns of a tile; two such tiles share one reverse pass),
  * s1 in later ones (2 channels: 16 or 8).  Larger tiles issue half as many UMMA
@@ -219,7 +241,7 @@ int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n
 int crom_set_step_tiles(crom_ctx* ctx, int s0, int s1);
 int crom_get_step_tiles(const crom_ctx* ctx, int* s0, int* s1, float* ms);
 
-/* Autotuner of the tile shape: times the BF16X2 step on the given batch (same
+/* Autotuner of the tile shape: times the F16X2 step on the given batch (same
  * arguments as crom_step; q is read, not updated: the trials run on a copy; status
  * is overwritten) for every tile shape, five steps each after one warm-up, and
  * keeps the fastest in the context.  Blocks until the timing completes; allocates
@@ -301,7 +323,8 @@ int crom_fom_step(int kind, int n_batch, int nx, int ny, const float* coef, cons
  * stays >= 32 long; a dense layer to 32 (ELU); a linear layer to r.  Decoder:
  * g(x, q) of the given crom_decoder_desc.  Loss: mean over B snapshots x S
  * sampled nodes of (g(x_j, e(f_b)) - f_b(x_j))^2.  Adam (beta1 0.9, beta2 0.999,
- * eps 1e-8) on FP32 master parameters; FP32 arithmetic on CUDA cores.
+ * eps 1e-8) on FP32 master parameters; the decoder pass in FP32 on CUDA cores or
+ * in bf16 on the tensor cores (crom_trainer_set_precision).
  * Parameter vector (FP32): the decoder exactly as crom_set_weights packs it, then
  * per convolution w[6], b, then the dense layers W[32][L_last], b[32], W[r][32],
  * b[r].  The trainer owns all its device memory. */
@@ -324,17 +347,20 @@ int crom_trainer_get_grads(crom_trainer* tr, float* grads, size_t n, int on_devi
  * double, may be NULL) receives the loss before the update. */
 int crom_train_step(crom_trainer* tr, const float* snaps, const int* pt_idx, const float* coords, float lr,
                     double* loss_out, crom_stream stream);
-/* Arithmetic of the trainer's dense products: CROM_PREC_FP32 (default; the
+/* Arithmetic of the trainer's decoder pass: CROM_PREC_FP32 (default; the
  * library's FP32 CUDA-core GEMM, split-K weight gradients reduced in a fixed
- * order) or CROM_PREC_TF32 (cuBLAS TF32 tensor-core GEMMs; the bias / ELU /
- * s'(z) epilogues, loss, convolutions and Adam stay in the library's kernels). */
+ * order) or CROM_PREC_BF16_MIXED (the library's tcgen05 GEMMs with fused
+ * epilogues, bf16 operands and activations, FP32 accumulation and master
+ * weights; see crom_precision).  Selecting BF16_MIXED the first time allocates its
+ * buffers (about (hidden + 2) * B * S * width * 2 bytes): not during stream
+ * capture.  Returns CROM_ERR_UNSUPPORTED for other values or shapes. */
 int crom_trainer_set_precision(crom_trainer* tr, int precision);
 /* Encoder only: q [n][r] FP32 for n <= B snapshots [n][P] (initial latent codes). */
 int crom_encode(crom_trainer* tr, int n, const float* snaps, float* q, crom_stream stream);
 
 /* Dense reconstruction g(x_p, q_c) for n_codes latent codes q [n_codes][r]
  * (FP64) at n_pts points x [n_pts][m] (FP32); out [n_codes][n_pts] FP32.
- * precision FP32 (any shape), BF16X2 or BF16 (tensor cores; width 128). */
+ * precision FP32 (any shape), F16X2 or F16 (tensor cores; width 128). */
 int crom_reconstruct(crom_ctx* ctx, int precision, int n_codes, const double* q, int n_pts,
                      const float* x, float* out, crom_stream stream);
 
@@ -357,7 +383,7 @@ int crom_reconstruct(crom_ctx* ctx, int precision, int n_codes, const double* q,
  *  init_idx  [n_init] distinct node indices, host
  *  idx_out   [max_samples] host: the selected node indices in order of addition
  *            (the initial ones first); count_out, metric_out host scalars.
- * step->pde must be CROM_PDE_HEAT; precision FP32 (no line search) or BF16X2.
+ * step->pde must be CROM_PDE_HEAT; precision FP32 (no line search) or F16X2.
  * Limits: 1 <= n_try <= 64, n_init <= max_samples <= min(n_nodes, 4096),
  * n_try * n_params <= 65535.  The call allocates its work buffers and returns
  * after the work on `stream` completed (not usable during stream capture). */

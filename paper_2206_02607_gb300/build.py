@@ -57,7 +57,7 @@ def build(verbose: bool = False, extra_flags=()) -> str:
         objs = list(ex.map(compile_one, srcs))
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + ".tmp"
-        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "shared", "-lcublas",
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "shared",
                "-Xlinker", "-rpath," + _cuda_lib_dir(nvcc)]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:

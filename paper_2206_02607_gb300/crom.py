@@ -22,9 +22,11 @@ CROM_ERR_TIMEOUT = 5
 CROM_ERR_UNSUPPORTED = 6
 
 CROM_PREC_FP32 = 0
-CROM_PREC_BF16X2 = 1
-CROM_PREC_BF16 = 2
-CROM_PREC_TF32 = 3
+CROM_PREC_F16X2 = 1
+CROM_PREC_F16 = 2
+CROM_PREC_BF16_MIXED = 4
+CROM_PREC_BF16X2 = CROM_PREC_F16X2   # earlier names of the same values
+CROM_PREC_BF16 = CROM_PREC_F16
 
 CROM_PDE_HEAT = 0
 CROM_PDE_ADVDIFF = 1
@@ -285,7 +287,7 @@ class CromTrainer:
             _check(fn(self.handle, arr.ctypes.data_as(ctypes.c_void_p), arr.size, 0, _stream(stream)))
 
     def set_precision(self, precision: int):
-        """CROM_PREC_FP32 (default) or CROM_PREC_TF32 for the dense products."""
+        """CROM_PREC_FP32 (default) or CROM_PREC_BF16_MIXED for the decoder pass."""
         _check(_LIB.crom_trainer_set_precision(self.handle, precision))
 
     def set_params(self, params, stream=None):

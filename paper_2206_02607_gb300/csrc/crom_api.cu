@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "crom_internal.h"
 
 namespace crom {
@@ -35,12 +37,23 @@ size_t param_count(const crom_decoder_desc& d) {
   return n;
 }
 
-uint16_t f32_to_bf16(float f) {
-  uint32_t u;
-  memcpy(&u, &f, 4);
-  if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;  // NaN stays NaN
-  u += 0x7fffu + ((u >> 16) & 1u);
-  return (uint16_t)(u >> 16);
+// f16 bits of f rounded to nearest even (the conversion of cuda_fp16.h, usable
+// on the host), and back.
+uint16_t f32_to_f16(float f) {
+  const __half h = __float2half_rn(f);
+  uint16_t u;
+  memcpy(&u, &h, 2);
+  return u;
+}
+float f16_to_f32(uint16_t u) {
+  __half h;
+  memcpy(&h, &u, 2);
+  return __half2float(h);
+}
+// Largest power of two 2^e with v * 2^e < 2 (v > 0), so that v * 2^e lies in [1, 2).
+float pow2_scale(float v) {
+  if (!(v > 0.f) || !isfinite(v)) return 1.f;
+  return ldexpf(1.f, -ilogbf(v));
 }
 
 // Byte offset of element (row, k) of a [rows][128] bf16 operand stored K-major
@@ -61,6 +74,7 @@ void free_weights(crom_ctx* ctx) {
   cudaFree(w.bh);
   cudaFree(w.wout);
   cudaFree(w.tc_img);
+  cudaFree(w.tc_lo);
   w = DeviceWeights{};
   ctx->has_weights = false;
 }
@@ -227,31 +241,55 @@ int crom_set_weights(crom_ctx* ctx, const float* params, size_t n, int params_on
   }
   dw.bout = bout;
 
-  if (tc_shape_ok(d)) {
-    // bf16 image: hidden matrices (K-major SW128), then the projection matrix P.
+  // f16 images of the tensor-core kernels; left out (those precisions then return
+  // CROM_ERR_UNSUPPORTED) when a weight lies outside the f16 range.
+  bool f16_range = true;
+  for (int l = 0; l < L - 1 && f16_range; ++l)
+    for (size_t i = 0; i < (size_t)w * w; ++i)
+      if (fabsf(hidden_w[l][i]) > 65000.f) { f16_range = false; break; }
+  for (int k = 0; k < w && f16_range; ++k) {
+    if (fabsf(Wout[k]) > 65000.f) f16_range = false;
+    for (int j = 0; j < r; ++j)
+      if (fabsf(W1[(size_t)k * in + m + j]) > 65000.f) f16_range = false;
+  }
+  if (tc_shape_ok(d) && f16_range) {
+    // hidden matrices (K-major SW128), then the projection matrix P
     const size_t layers_bytes = (size_t)(L - 1) * kTcLayerBytes;
     std::vector<uint8_t> img(layers_bytes + kTcProjBytes, 0);
+    std::vector<uint16_t> lo((size_t)(L - 1) * w * w);
     for (int l = 0; l < L - 1; ++l)
       for (int o = 0; o < w; ++o)
         for (int k = 0; k < w; ++k) {
-          uint16_t v = f32_to_bf16(hidden_w[l][(size_t)o * w + k]);
+          const float x = hidden_w[l][(size_t)o * w + k];
+          const uint16_t v = f32_to_f16(x);
           memcpy(&img[(size_t)l * kTcLayerBytes + kmajor_sw128(o, k, w)], &v, 2);
+          lo[((size_t)l * w + o) * w + k] = f32_to_f16(x - f16_to_f32(v));  // exact difference, rounded once
         }
     for (int row = 0; row < kTcProjRows; ++row)
       for (int k = 0; k < w; ++k) {
         float val = 0.f;
         if (row == 0) val = Wout[k];
         else if (row <= r) val = W1[(size_t)k * in + m + (row - 1)];
-        uint16_t v = f32_to_bf16(val);
+        const uint16_t v = f32_to_f16(val);
         memcpy(&img[layers_bytes + kmajor_sw128(row, k, kTcProjRows)], &v, 2);
       }
     e = cudaMalloc(&dw.tc_img, img.size());
     if (e == cudaSuccess) e = cudaMemcpy(dw.tc_img, img.data(), img.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&dw.tc_lo, lo.size() * 2);
+    if (e == cudaSuccess) e = cudaMemcpy(dw.tc_lo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
       free_weights(ctx);
       return cuda_fail(e, "crom_set_weights (tensor-core image)");
     }
     dw.tc_img_bytes = img.size();
+    dw.tc_lo_bytes = lo.size() * 2;
+    float mx = 0.f, mo = 0.f;
+    for (int u = 0; u < w; ++u) {
+      for (int k = 0; k < m; ++k) mx = fmaxf(mx, fabsf(W1[(size_t)u * in + k]));
+      mo = fmaxf(mo, fabsf(Wout[u]));
+    }
+    dw.tc_sx = pow2_scale(mx);
+    dw.tc_sr = pow2_scale(mo);
   }
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -316,8 +354,8 @@ int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_in
     return fail(CROM_ERR_INVALID_ARG, "crom_step: coef_per_sample must be 0 or 1");
   if (step->line_search < 0 || step->line_search > 16)
     return fail(CROM_ERR_INVALID_ARG, "crom_step: line_search must be in 0..16");
-  if (step->line_search > 0 && precision != CROM_PREC_BF16X2)
-    return fail(CROM_ERR_UNSUPPORTED, "crom_step: the line search is available with CROM_PREC_BF16X2");
+  if (step->line_search > 0 && precision != CROM_PREC_F16X2)
+    return fail(CROM_ERR_UNSUPPORTED, "crom_step: the line search is available with CROM_PREC_F16X2");
   if (n_inst == 0) return CROM_OK;
   if (!q || !alpha || !s_off || !status || (n_samples > 0 && !samples))
     return fail(CROM_ERR_INVALID_ARG, "crom_step: null array");
@@ -329,11 +367,11 @@ int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_in
   if (precision == CROM_PREC_FP32) {
     if (step_fp32_max_tiles(ctx, n_inst, max_samples) > 65535)
       return fail(CROM_ERR_INVALID_ARG, "crom_step: max_samples too large for the FP32 step's grid (at most 65535 "
-                                        "CTAs per instance); use CROM_PREC_BF16X2 or split the instance");
+                                        "CTAs per instance); use CROM_PREC_F16X2 or split the instance");
     e = launch_step_fp32(ctx, step, n_inst, q, alpha, vel, s_off, samples, n_samples, max_samples, status, s);
-  } else if (precision == CROM_PREC_BF16X2) {
+  } else if (precision == CROM_PREC_F16X2) {
     if (!tc_shape_ok(ctx->desc) || !ctx->w.tc_img)
-      return fail(CROM_ERR_UNSUPPORTED, "crom_step: BF16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15, ELU");
+      return fail(CROM_ERR_UNSUPPORTED, "crom_step: F16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15, ELU");
     e = launch_step_tc(ctx, step, n_inst, q, alpha, vel, s_off, samples, n_samples, max_samples, status, s);
   } else {
     return fail(CROM_ERR_UNSUPPORTED, "crom_step: precision not available for the step");
@@ -420,15 +458,15 @@ int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n
     return fail(CROM_ERR_INVALID_ARG, "crom_rollout: coef_per_sample must be 0 or 1");
   if (step->line_search < 0 || step->line_search > 16)
     return fail(CROM_ERR_INVALID_ARG, "crom_rollout: line_search must be in 0..16");
-  if (step->line_search > 0 && precision != CROM_PREC_BF16X2)
-    return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: the line search is available with CROM_PREC_BF16X2");
+  if (step->line_search > 0 && precision != CROM_PREC_F16X2)
+    return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: the line search is available with CROM_PREC_F16X2");
   if (!q || !alpha || !s_off || !status || (n_samples > 0 && !samples))
     return fail(CROM_ERR_INVALID_ARG, "crom_rollout: null array");
   if (step->pde == CROM_PDE_ADVDIFF && !vel) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: advection needs vel");
   if (max_samples < 1) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: max_samples must be >= 1");
-  if (precision == CROM_PREC_BF16X2) {
+  if (precision == CROM_PREC_F16X2) {
     if (!tc_shape_ok(ctx->desc) || !ctx->w.tc_img)
-      return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: BF16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15, ELU");
+      return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: F16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15, ELU");
   } else if (precision != CROM_PREC_FP32) {
     return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: precision not available for the step");
   } else if (step_fp32_max_tiles(ctx, n_inst, max_samples) > 65535) {
@@ -562,7 +600,7 @@ int crom_autotune(crom_ctx* ctx, const crom_step_desc* step, int n_inst, const d
     e = cudaMemcpyAsync(qs, q, qb, cudaMemcpyDeviceToDevice, s);
     int rc = CROM_OK;
     if (e == cudaSuccess)  // warm-up (first launch of this variant, shared-memory attribute)
-      rc = crom_step(ctx, step, CROM_PREC_BF16X2, n_inst, qs, alpha, vel, s_off, samples, n_samples, max_samples,
+      rc = crom_step(ctx, step, CROM_PREC_F16X2, n_inst, qs, alpha, vel, s_off, samples, n_samples, max_samples,
                      status, stream);
     if (rc != CROM_OK) {
       ctx->tc_tile_s1 = saved;
@@ -575,7 +613,7 @@ int crom_autotune(crom_ctx* ctx, const crom_step_desc* step, int n_inst, const d
     for (int k = 0; k < reps && e == cudaSuccess; ++k) {
       e = cudaMemcpyAsync(qs, q, qb, cudaMemcpyDeviceToDevice, s);
       if (e == cudaSuccess &&
-          crom_step(ctx, step, CROM_PREC_BF16X2, n_inst, qs, alpha, vel, s_off, samples, n_samples, max_samples,
+          crom_step(ctx, step, CROM_PREC_F16X2, n_inst, qs, alpha, vel, s_off, samples, n_samples, max_samples,
                     status, stream) != CROM_OK)
         e = cudaErrorUnknown;
     }
@@ -615,7 +653,7 @@ int crom_step_noalloc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, dou
   if (step->line_search < 0 || step->line_search > 16)
     return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: line_search must be in 0..16");
   if (step->line_search > 0)
-    return fail(CROM_ERR_UNSUPPORTED, "crom_step_noalloc: the line search is available with CROM_PREC_BF16X2");
+    return fail(CROM_ERR_UNSUPPORTED, "crom_step_noalloc: the line search is available with CROM_PREC_F16X2");
   if (n_inst == 0) return CROM_OK;
   if (!q || !alpha || !s_off || !status || (n_samples > 0 && !samples))
     return fail(CROM_ERR_INVALID_ARG, "crom_step_noalloc: null array");
@@ -681,7 +719,8 @@ int crom_trainer_create(crom_trainer** out, const crom_decoder_desc* dec, int P,
   t->lens.push_back(P);
   while ((t->lens.back() - 6) / 4 + 1 >= 32) t->lens.push_back((t->lens.back() - 6) / 4 + 1);
   DeviceGuard g(device);
-  cudaError_t e = trainer_alloc(t);
+  cudaError_t e = cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = trainer_alloc(t);
   if (e != cudaSuccess) {
     trainer_free(t);
     delete t;
@@ -704,11 +743,14 @@ int crom_trainer_destroy(crom_trainer* tr) {
 
 int crom_trainer_set_precision(crom_trainer* tr, int precision) {
   if (!tr) return fail(CROM_ERR_INVALID_ARG, "crom_trainer_set_precision: null trainer");
-  if (precision != CROM_PREC_FP32 && precision != CROM_PREC_TF32)
-    return fail(CROM_ERR_UNSUPPORTED, "crom_trainer_set_precision: FP32 or TF32");
+  if (precision != CROM_PREC_FP32 && precision != CROM_PREC_BF16_MIXED)
+    return fail(CROM_ERR_UNSUPPORTED, "crom_trainer_set_precision: FP32 or BF16_MIXED");
+  if (precision == CROM_PREC_BF16_MIXED && !trainer_tc_supported(tr))
+    return fail(CROM_ERR_UNSUPPORTED, "crom_trainer_set_precision: BF16_MIXED needs width 64, 128 or 256, "
+                                      "hidden >= 2 and m + r <= 32");
   DeviceGuard g(tr->device);
-  if (trainer_set_precision(tr, precision) != CROM_OK)
-    return fail(CROM_ERR_CUDA, "crom_trainer_set_precision: cuBLAS handle creation failed");
+  const int rc = trainer_set_precision(tr, precision);
+  if (rc != CROM_OK) return fail(rc, "crom_trainer_set_precision: allocation of the tensor-core buffers failed");
   return CROM_OK;
 }
 
@@ -787,10 +829,10 @@ int crom_reconstruct(crom_ctx* ctx, int precision, int n_codes, const double* q,
   cudaError_t e;
   if (precision == CROM_PREC_FP32) {
     e = launch_recon_fp32(ctx, n_codes, q, n_pts, x, out, s);
-  } else if (precision == CROM_PREC_BF16X2 || precision == CROM_PREC_BF16) {
+  } else if (precision == CROM_PREC_F16X2 || precision == CROM_PREC_F16) {
     if (!tc_shape_ok(ctx->desc) || !ctx->w.tc_img)
       return fail(CROM_ERR_UNSUPPORTED, "crom_reconstruct: tensor-core path needs width 128, 2<=hidden<=5, m<=2, ELU");
-    e = launch_recon_tc(ctx, precision == CROM_PREC_BF16X2 ? 1 : 0, n_codes, q, n_pts, x, out, s);
+    e = launch_recon_tc(ctx, precision == CROM_PREC_F16X2 ? 1 : 0, n_codes, q, n_pts, x, out, s);
   } else {
     return fail(CROM_ERR_UNSUPPORTED, "crom_reconstruct: unknown precision");
   }
@@ -815,11 +857,11 @@ int crom_robust_samples(crom_ctx* ctx, const crom_step_desc* step, int precision
       step->gn_iters > 16 || !(step->dt > 0.0) || !isfinite(step->dt) ||
       (step->coef_per_sample != 0 && step->coef_per_sample != 1))
     return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": needs a heat step with valid gn_iters, dt, coefficient mode");
-  if (precision == CROM_PREC_BF16X2) {
+  if (precision == CROM_PREC_F16X2) {
     if (!tc_shape_ok(ctx->desc) || !ctx->w.tc_img)
-      return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": BF16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15");
+      return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": F16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15");
   } else if (precision != CROM_PREC_FP32 || step->line_search > 0) {
-    return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": precision FP32 (no line search) or BF16X2");
+    return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": precision FP32 (no line search) or F16X2");
   }
   std::vector<int> M(init_idx, init_idx + n_init);
   {
@@ -877,7 +919,7 @@ int crom_robust_samples(crom_ctx* ctx, const crom_step_desc* step, int precision
     const float* a = sd.coef_per_sample ? d_alpha_s : d_alpha;
     if (e == cudaSuccess && n_steps == 0) e = cudaMemsetAsync(d_status, 0, (size_t)n_inst * sizeof(int), s);
     for (int t = 0; t < n_steps && e == cudaSuccess; ++t)
-      e = precision == CROM_PREC_BF16X2
+      e = precision == CROM_PREC_F16X2
               ? launch_step_tc(ctx, &sd, n_inst, d_q, a, nullptr, d_off, d_samples, n_s, max_s, d_status, s)
               : launch_step_fp32(ctx, &sd, n_inst, d_q, a, nullptr, d_off, d_samples, n_s, max_s, d_status, s);
     if (e == cudaSuccess) e = launch_recon_fp32(ctx, n_inst, d_q, n_nodes, nodes, d_out, s);

@@ -11,13 +11,16 @@
 
 namespace crom {
 
-// Tensor-core decoder image (bf16), one per context.  Layout in bytes, every
+// Tensor-core decoder image (f16), one per context.  Layout in bytes, every
 // part 1024-byte aligned so that it can be bulk-copied into shared memory and
 // used there directly as 128B-swizzled UMMA operands:
-//   [0, L*32768)           hidden matrices W_2..W_{hidden}, each 128x128 bf16,
+//   [0, L*32768)           hidden matrices W_2..W_{hidden}, each 128x128 f16,
 //                          K-major, 128B swizzle, two 64-column k-blocks
-//   [L*32768, +4096)       projection matrix P (16 x 128 bf16, K-major, SW128):
+//   [L*32768, +4096)       projection matrix P (16 x 128 f16, K-major, SW128):
 //                          row 0 = w_out, rows 1..r = W_1[:, m+j] (dg/dq projection)
+// and a second image of the hidden matrices' low parts W - f16(W), rounded to f16,
+// row-major [L][128][128] (loaded into tensor memory by the reconstruction kernel,
+// where it is the A operand of a third product per layer).
 constexpr int kTcWidth = 128;
 constexpr int kTcLayerBytes = kTcWidth * kTcWidth * 2;
 // Sample tiles of the tensor-core step: kTcTileS0 samples per forward tile at GN
@@ -37,9 +40,15 @@ struct DeviceWeights {
   float* bh = nullptr;    // (hidden-1) x [width]
   float* wout = nullptr;  // [width]
   float bout = 0.f;
-  // bf16 tensor-core image (see above); nullptr when width != 128.
+  // f16 tensor-core images (see above); nullptr when the shape is not supported
+  // by the tensor-core kernels or a weight lies outside the f16 range.
   uint8_t* tc_img = nullptr;
   size_t tc_img_bytes = 0;
+  uint8_t* tc_lo = nullptr;
+  size_t tc_lo_bytes = 0;
+  // Power-of-two scales of the step's f16 channels: max_u |W_1x[u][k]| * tc_sx and
+  // max_u |w_out[u]| * tc_sr lie in [1, 2).
+  float tc_sx = 1.f, tc_sr = 1.f;
 };
 
 }  // namespace crom
@@ -93,6 +102,24 @@ struct TrainerLayout {
 };
 }  // namespace crom
 
+namespace crom {
+// Buffers of the tensor-core decoder pass of training (CROM_PREC_BF16_MIXED),
+// allocated when that precision is first selected.
+struct TrainerTc {
+  bool ready = false;
+  uint16_t* wh = nullptr;   // bf16 hidden matrices W_1..W_{L-1}, [w][w] each
+  uint16_t* w0p = nullptr;  // bf16 W_0 as [w][64] (row u: W_0[u][0..m+r), zeros)
+  std::vector<uint16_t*> H; // bf16 activations of the hidden layers, [B*S][w] each
+  uint16_t *d0 = nullptr, *d1 = nullptr;  // bf16 deltas [B*S][w]
+  float *colpart = nullptr, *colpart2 = nullptr, *rowpart = nullptr;  // epilogue partial sums
+  float* split = nullptr;   // split-K partials of the weight gradients
+  float* din = nullptr;     // [B*S][64]: delta_0 W_0 (input gradient), FP32
+  float* gw0part = nullptr; // row-chunk partials of dW_0
+  long* off_w = nullptr;    // device copy of the decoder weight offsets
+  int* flag = nullptr;      // set by a GEMM whose bounded wait ran out
+};
+}  // namespace crom
+
 // Training state: FP32 master parameters, gradients, Adam moments, activations.
 struct crom_trainer {
   int device = 0;
@@ -114,8 +141,9 @@ struct crom_trainer {
   double* red = nullptr;  // partial sums of the deterministic column / convolution reductions
   double* colpart = nullptr;  // per-block column partial sums fused into the TF32 epilogues
   std::vector<void*> owned;
-  int precision = CROM_PREC_FP32;  // of the dense products (FP32 or TF32)
-  void* blas = nullptr;            // cuBLAS handle for TF32, created on demand
+  int precision = CROM_PREC_FP32;  // of the decoder pass (FP32 or BF16_MIXED)
+  int num_sms = 0;
+  crom::TrainerTc tc;
 };
 
 namespace crom {
@@ -130,6 +158,12 @@ int trainer_set_precision(crom_trainer* t, int precision);
 cudaError_t trainer_encode(crom_trainer* t, int nb, const float* snaps, float* q_out, cudaStream_t s);
 cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx, const float* coords, float lr,
                          double* loss_out, cudaStream_t s);
+// tensor-core decoder pass (train_tc.cu): loss, decoder gradients and the input
+// gradient din ([B*S][trainer_tc_din_ld()] FP32) from t->in0 and t->target
+bool trainer_tc_supported(const crom_trainer* t);
+cudaError_t trainer_tc_alloc(crom_trainer* t);
+cudaError_t trainer_decoder_tc(crom_trainer* t, double* loss_out, int num_sms, cudaStream_t s);
+int trainer_tc_din_ld();
 
 // Channel configuration of the FP32 forward-mode evaluation.
 enum SecondOrder { kSecondNone = 0, kSecondPerK = 1, kSecondLap = 2 };
@@ -177,6 +211,47 @@ cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst
                            cudaStream_t s);
 cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const double* q, int n_pts,
                             const float* x, float* out, cudaStream_t s);
+
+// bf16 GEMM on the tcgen05 tensor cores with fused training epilogues (tc_gemm.cu):
+// D[m][n] = sum_k A(m, k) B(n, k), FP32 accumulation.  A(m, k) = A[m * lda + k]
+// (a_mn = 0) or A[k * lda + m] (a_mn = 1); B(n, k) = B[n * ldb + k] (b_mn = 0) or
+// B[k * ldb + n] (b_mn = 1); bf16 operands, 16-byte aligned, row strides multiples of
+// 8 elements; N in {64, 128, 256} (one tile spans all N columns), M and K any.
+enum GemmEpi {
+  kGemmEpiF32 = 0,        // out_f32[split][m][n] = D (K split into `splits` ranges)
+  kGemmEpiBiasElu = 1,    // out_bf16[m][n] = ELU(D + bias[n])
+  kGemmEpiTimesEluD = 2,  // out_bf16[m][n] = D * s'(z), s' from hprev[m][n] = h = ELU(z); colpart = column sums
+  kGemmEpiOut = 3         // last hidden layer: out_bf16 = h_L = ELU(D + bias); per row g = wout . h_L + *bout,
+                          // r = g - target[m], dg = 2 r inv_count; delta_out[m][n] = dg wout[n] s'(z);
+                          // colpart = column sums of delta, colpart2 of dg h_L, rowpart = (sum r^2, sum dg)
+};
+struct TcGemm {
+  int M = 0, N = 0, K = 0;
+  const void* A = nullptr;
+  long lda = 0;
+  int a_mn = 0;
+  const void* B = nullptr;
+  long ldb = 0;
+  int b_mn = 0;
+  int splits = 1;
+  int epi = kGemmEpiF32;
+  float* out_f32 = nullptr;
+  long ldo = 0;
+  uint16_t* out_bf16 = nullptr;
+  const float* bias = nullptr;
+  const uint16_t* hprev = nullptr;
+  float* colpart = nullptr;  // [ceil(M / 128) * 4][N]: per-warp column sums (32 rows each)
+  const float* wout = nullptr;
+  const float* bout = nullptr;  // device scalar
+  const float* target = nullptr;
+  uint16_t* delta_out = nullptr;
+  float* colpart2 = nullptr;
+  float* rowpart = nullptr;  // [ceil(M / 128) * 4][2]
+  float inv_count = 0.f;
+};
+bool tc_gemm_supported(int n);
+cudaError_t tc_gemm(const TcGemm& g, int num_sms, int* flag, cudaStream_t s);
+int tc_gemm_splits_used(int K, int splits);
 
 // Robust-sample selection kernels (sampling.cu).
 cudaError_t launch_sampling_gather(const float* nodes, const int* idx, const int* param_of, int n, int m,

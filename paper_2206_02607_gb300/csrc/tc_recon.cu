@@ -1,24 +1,35 @@
 // Dense reconstruction g(x_p, q_c) on the tcgen05 tensor cores (value channel only).
 //
-// Persistent kernel, one CTA per SM with the decoder's bf16 hidden matrices in
-// shared memory, four independent groups of 128 threads (one tile each, own
-// 64-column operand block / 128 TMEM columns / mbarrier / named barrier) so that
-// one group's UMMAs overlap the others' epilogues.  Hidden unit u is TMEM lane u
-// and thread u of its group.  A tile is 32 points of one code with hi/lo operand
-// parts, 64 points with hi parts only:
+// Persistent kernel, one CTA per SM, warp-specialised: one MMA warp issues every
+// UMMA of the CTA, and two tile slots of eight epilogue warps each (two threads
+// per hidden unit, each on half of the tile's points) run the CUDA-core work.
+// The slots alternate on the tensor cores: while the MMA warp multiplies one
+// slot's tile through a layer, the other slot's warps run their epilogue.  Hand-
+// offs are mbarriers, per slot: `full` (the slot's operand block is written: one
+// arrival per epilogue warp) and `acc` (the slot's accumulator is complete: the
+// UMMA commit).  Hidden unit u is TMEM lane u.
+//
+// Per tile (64 points of one code with hi/lo operand parts, or 128 points with
+// high parts only):
 //   layer 1 (K = m + r, too small for UMMA) on CUDA cores: the q part of
 //     W_1 [x; q] + b_1 is hoisted per code; h = ELU(W_1x x + c);
 //   layers 2..L: D[u][n] = sum_k W_l[u][k] H[k][n] by UMMA (M = 128 units,
-//     N = 64, K = 128), A = W_l (K-major, resident), B = H (MN-major, written by
-//     the previous epilogue: the hi and lo parts of 32 points side by side, added
-//     in the epilogue, or the hi parts of 64 points); epilogue: bias, ELU, bf16
-//     split, store;
+//     K = 128), A = W_l (f16, K-major, resident in shared memory), B = H
+//     (MN-major, written by the previous epilogue).  With hi/lo parts, B holds
+//     hi = f16(h) in columns 0..63 and lo = f16(h - hi) in 64..127: one N = 128
+//     UMMA per K slice gives W hi and W lo in separate accumulator columns; a
+//     third product W_lo hi (N = 64) adds the weights' own low parts
+//     W_lo = f16(W - f16(W)), read from tensor memory (the A operand of the
+//     TMEM form), into the first 64 columns.  The epilogue adds the two halves,
+//     the bias, applies ELU and writes the next operand;
 //   output layer: w_out . h_L on the CUDA cores in the last hidden layer's
 //     epilogue, in FP32 from h_L itself (a warp butterfly over the 32 units of
 //     each warp, then the four lane quadrants' partial sums), written coalesced.
-// Precision: each activation operand h is stored as hi = bf16(h) and
-// lo = bf16(h - hi) and both are multiplied into the same FP32 accumulator
-// (kSplit = 1); kSplit = 0 keeps the high part only.
+// Precision (kSplit = 1): activations carry ~2^-22 relative (hi + lo), weights
+// W + W_lo ~2^-22 (the W_lo lo product is below that and left out), FP32
+// accumulation.  kSplit = 0: f16 activations and weights (2^-11 relative each).
+// TMEM: slot s accumulator in columns 128 s .. 128 s + 127; W_lo of hidden matrix
+// l in columns 256 + 64 l .. + 63.
 #include <math.h>
 
 #include <algorithm>
@@ -31,24 +42,23 @@ namespace {
 
 using namespace tc;
 
-constexpr int kGroups = 4;
-constexpr int kGT = 128;  // one thread per TMEM lane (hidden unit), all of the tile's points
-constexpr int kThreads = kGroups * kGT;
-// Points per tile: 32 with hi/lo operand parts (N = 64 = 32 hi + 32 lo columns),
-// 64 with hi parts only (N = 64 points); one 64-column operand block and 64
-// accumulator columns per group either way.
-constexpr int kTileSplit = 32, kTileHi = 64;
-constexpr int kTileN = kTileHi;  // sizes of the per-tile arrays
+constexpr int kSlots = 2;
+constexpr int kEpiWarps = 8;                       // per slot
+constexpr int kSlotThreads = kEpiWarps * 32;       // 256
+constexpr int kMmaWarp = kSlots * kEpiWarps;       // warp 16
+constexpr int kThreads = (kMmaWarp + 1) * 32;      // 544
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kGroupCols = 128;
-constexpr uint32_t kAccCol = 0;    // W h_hi in columns 0..31, W h_lo in 32..63 (hi only: 64 points)
+constexpr uint32_t kSlotCols = 128;
+constexpr uint32_t kLoCol = 256;                   // W_lo of hidden matrix l at kLoCol + 64 l
 constexpr uint32_t kWaitLimit = 1u << 25;
-constexpr size_t kHBuf = (size_t)kTcWidth * 64 * 2;  // one 64-column bf16 operand block, 16 KB
+constexpr size_t kHBuf = (size_t)kTcWidth * 128 * 2;  // one slot's operand block: 128 columns, 32 KB
+constexpr int kMaxPts = 128;
 
 struct ReconParams {
-  const uint8_t* img;
-  int img_bytes;
-  int n_hidden_mats;  // hidden - 1
+  const uint8_t* img;  // hidden matrices, f16 K-major SW128
+  int hidden_bytes;    // (hidden - 1) * 32 KB
+  const uint16_t* lo;  // W_lo, f16 row-major [hidden - 1][128][128]
+  int n_hidden_mats;   // hidden - 1
   int m, r;
   const float* w1;  // [128][m+r]
   const float* b1;
@@ -60,27 +70,23 @@ struct ReconParams {
   float* out;       // [n_codes][n_pts]
   int n_pts, n_codes;
   int tiles_per_code;
+  int n_tiles;
   int* flag;  // set to 1 on a device-side wait timeout
 };
 
 struct __align__(16) Shared {
-  uint64_t bar_w;
+  uint64_t bar_w;           // the weight image arrived
+  uint64_t full[kSlots];    // the slot's operand block is written (kEpiWarps arrivals)
+  uint64_t acc[kSlots];     // the slot's accumulator is complete (UMMA commit)
+  uint64_t drain;           // the MMA warp's last UMMAs completed
   uint32_t tmem_base;
-  int pad;
+  int abort;                // a bounded wait ran out: every wait and UMMA is skipped from then on
   float bh[4][kTcWidth];
   float w1x[2][kTcWidth];
   float wout[kTcWidth];
+  float xs[kSlots][2][kMaxPts];
+  float outp[kSlots][4][kMaxPts];  // output layer: partial sums of the four lane quadrants
 };
-
-struct __align__(16) Group {
-  uint64_t bar_mma;
-  int pad[2];
-  float c1[kTcWidth];
-  float xs[2][kTileN];
-  float outp[4][kTileN];  // output layer: partial sums of the four lane quadrants
-};
-
-constexpr size_t kTailBytes = sizeof(Shared) + kGroups * sizeof(Group);
 
 // Sum over the 32 lanes of a warp (32 hidden units) of 16 per-lane values v[s]:
 // four exchange rounds halve the set (offsets 16, 8, 4, 2), one more adds across
@@ -102,40 +108,35 @@ __device__ __forceinline__ float warp_sum16(const float (&v)[16], int lane) {
   return t;
 }
 
-__device__ __forceinline__ void group_sync(int g) {
-  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGT) : "memory");
-}
-__device__ __forceinline__ bool group_sync_and(int g, bool pred) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.and.pred q, %2, %3, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n\t}"
-      : "=r"(r)
-      : "r"((uint32_t)pred), "r"(1 + g), "r"(kGT)
-      : "memory");
-  return r != 0;
+__device__ __forceinline__ void slot_sync(int s) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + s), "r"(kSlotThreads) : "memory");
 }
 
-// Sixteen consecutive columns of row k, given as 8 packed pairs, stored as bf16 hi
-// parts at columns n0..n0+15 (and lo = bf16(h - hi) parts at nl..nl+15 when kSplit)
+__device__ __forceinline__ bool aborted(Shared* S) { return *reinterpret_cast<volatile int*>(&S->abort) != 0; }
+// Bounded wait unless the kernel already gave up; a wait that runs out raises abort.
+__device__ __forceinline__ void wait_or_abort(Shared* S, uint64_t* bar, uint32_t parity) {
+  if (aborted(S)) return;
+  if (!mbar_wait(bar, parity, kWaitLimit)) *reinterpret_cast<volatile int*>(&S->abort) = 1;
+}
+
+// Sixteen consecutive columns of row k, given as 8 packed pairs, stored as f16 hi
+// parts at columns n0..n0+15 (and lo = f16(h - hi) parts at 64 + n0.. when kSplit)
 // of the MN-major operand H.
 template <int kSplit>
-__device__ __forceinline__ void store_split16(uint8_t* H, int k, int n0, int nl, const f32x2 (&h)[8]) {
+__device__ __forceinline__ void store_split16(uint8_t* H, int k, int n0, const f32x2 (&h)[8]) {
   uint32_t hi[8], lo[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     float a, b;
     unpk2(h[j], a, b);
-    hi[j] = pack_bf16(a, b);
-    if (kSplit) lo[j] = pack_bf16_lo(hi[j], a, b);
+    hi[j] = pack_f16(a, b);
+    if (kSplit) lo[j] = pack_f16_lo(hi[j], a, b);
   }
   *reinterpret_cast<uint4*>(H + mn_offset(k, n0)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
   *reinterpret_cast<uint4*>(H + mn_offset(k, n0 + 8)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
   if (kSplit) {
-    *reinterpret_cast<uint4*>(H + mn_offset(k, nl)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-    *reinterpret_cast<uint4*>(H + mn_offset(k, nl + 8)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+    *reinterpret_cast<uint4*>(H + mn_offset(k, 64 + n0)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    *reinterpret_cast<uint4*>(H + mn_offset(k, 64 + n0 + 8)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
   }
 }
 
@@ -143,155 +144,207 @@ template <int kSplit>
 __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int tid = threadIdx.x;
-  const int g = tid / kGT, gt = tid % kGT;
-  const int lq = (gt >> 5) & 3;
-  const int u = lq * 32 + (gt & 31);           // hidden unit = TMEM lane
-  constexpr int kTile = kSplit ? kTileSplit : kTileHi;
-  const uint32_t lane_base = (uint32_t)lq * 32;
-  const int m = p.m, r = p.r;
+  constexpr int kPts = kSplit ? 64 : 128;   // points per tile
+  constexpr int kPer = kPts / 2;            // points per epilogue thread
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m = p.m, r = p.r, L1 = p.n_hidden_mats;
   uint8_t* Wimg = sm;
-  uint8_t* Hbase = sm + ((p.img_bytes + 1023) & ~1023);
-  uint8_t* H = Hbase + (size_t)g * kHBuf;  // this group's 64-column operand block
-  Shared* S = reinterpret_cast<Shared*>(Hbase + (size_t)kGroups * kHBuf);
-  Group* G = reinterpret_cast<Group*>(S + 1) + g;
+  uint8_t* Hbase = sm + p.hidden_bytes;
+  Shared* S = reinterpret_cast<Shared*>(Hbase + (size_t)kSlots * kHBuf);
 
   if (tid == 0) {
     mbar_init(&S->bar_w, 1);
+    for (int s = 0; s < kSlots; ++s) {
+      mbar_init(&S->full[s], kEpiWarps);
+      mbar_init(&S->acc[s], 1);
+    }
+    mbar_init(&S->drain, 1);
+    S->abort = 0;
     fence_mbar_init();
   }
-  if (gt == 0) {
-    mbar_init(&G->bar_mma, 1);
-    fence_mbar_init();
-  }
-  if (tid < 32) {
+  if (warp == 0) {
     tmem_alloc(&S->tmem_base, kTmemCols);
     tmem_relinquish();
   }
   if (tid < kTcWidth) {
-    for (int l = 0; l < p.n_hidden_mats; ++l) S->bh[l][tid] = p.bh[l * kTcWidth + tid];
+    for (int l = 0; l < L1; ++l) S->bh[l][tid] = p.bh[l * kTcWidth + tid];
     for (int k = 0; k < m; ++k) S->w1x[k][tid] = p.w1[tid * (m + r) + k];
     S->wout[tid] = p.wout[tid];
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tb = S->tmem_base + (uint32_t)g * kGroupCols;
+  const uint32_t tb = S->tmem_base;
   if (tid == 0) {
-    mbar_arrive_expect_tx(&S->bar_w, (uint32_t)p.img_bytes);
-    for (int off = 0; off < p.img_bytes; off += 16384)
-      bulk_g2s(Wimg + off, p.img + off, (uint32_t)min(16384, p.img_bytes - off), &S->bar_w);
+    mbar_arrive_expect_tx(&S->bar_w, (uint32_t)p.hidden_bytes);
+    for (int off = 0; off < p.hidden_bytes; off += 16384)
+      bulk_g2s(Wimg + off, p.img + off, (uint32_t)min(16384, p.hidden_bytes - off), &S->bar_w);
   }
-  // Every wait is bounded; the outcome is made uniform across the CTA (or group)
-  // before anyone acts on it, so no thread leaves while others wait at a barrier.
-  bool ok = __syncthreads_and(mbar_wait(&S->bar_w, 0, kWaitLimit));
-  uint32_t phase = 0;
-  const uint32_t wbase = smem_u32(Wimg);
-  // Base UMMA descriptors; every operand slice is base + a compile-time offset.
-  const uint64_t dW = smem_desc_sw128(wbase, 16, 1024);
-  const uint64_t dH = smem_desc_sw128(smem_u32(H), 16384, 1024);
-  constexpr uint32_t id_layer = idesc_f16(128, 64, false, true, true);
-  int cur_code = -1;
-  float c = 0.f;
-  const float wx0 = S->w1x[0][u], wx1 = (m > 1) ? S->w1x[1][u] : 0.f;
-  const float wo = S->wout[u];
-  const int lane = gt & 31;
-  const int n_tiles = p.n_codes * p.tiles_per_code;
-
-  for (int tile = blockIdx.x * kGroups + g; tile < n_tiles && ok; tile += gridDim.x * kGroups) {
-    const int code = tile / p.tiles_per_code;
-    const int p0 = (tile % p.tiles_per_code) * kTile;
-    if (code != cur_code) {
-      double cc = (double)p.b1[u];
-      for (int j = 0; j < r; ++j) cc += (double)p.w1[u * (m + r) + m + j] * p.q[(size_t)code * r + j];
-      c = (float)cc;
-      cur_code = code;
-    }
-    if (gt < kTile) {
-      const int n = p0 + gt;
-      for (int k = 0; k < m; ++k) G->xs[k][gt] = (n < p.n_pts) ? p.x[(size_t)n * m + k] : 0.f;
-    }
-    group_sync(g);
-    // ---- layer 1 on CUDA cores
+  if (kSplit && warp < 4) {
+    // W_lo into tensor memory: lane u = row u, column c = (k = 2c, 2c + 1)
+    const int row = warp * 32 + lane;
+    for (int l = 0; l < L1; ++l) {
+      const uint4* src = reinterpret_cast<const uint4*>(p.lo + ((size_t)l * kTcWidth + row) * kTcWidth);
 #pragma unroll 1
-    for (int n0 = 0; n0 < kTile; n0 += 16) {
-      f32x2 h[8];
+      for (int c0 = 0; c0 < 64; c0 += 16) {
+        float v[16];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        f32x2 z = fma2(pk2(wx0, wx0), pk2(G->xs[0][n0 + 2 * j], G->xs[0][n0 + 2 * j + 1]), pk2(c, c));
-        if (m > 1) z = fma2(pk2(wx1, wx1), pk2(G->xs[1][n0 + 2 * j], G->xs[1][n0 + 2 * j + 1]), z);
-        float e0, e1;
-        h[j] = elu2(z, e0, e1);
-      }
-      store_split16<kSplit>(H, u, n0, kTileSplit + n0, h);
-    }
-    // ---- hidden layers on the tensor cores; the output layer in the last epilogue
-    for (int l = 0; l < p.n_hidden_mats; ++l) {
-      const bool last = (l == p.n_hidden_mats - 1);
-      fence_proxy_async_smem();
-      tc_fence_before();
-      group_sync(g);
-      bool done = true;
-      if ((gt >> 5) == 0) {  // the first warp issues (one elected lane) and waits, the rest wait at the barrier
-        tc_fence_after();
-        // The lo parts follow the hi parts in the same 64-column block, so one UMMA
-        // with N = 64 multiplies both at once: accumulator columns 0..31 get W h_hi,
-        // columns 32..63 W h_lo (hi only: 64 points).
-        const uint64_t a0 = desc_add(dW, (uint32_t)l * kTcLayerBytes);
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk)
-          umma_f16_warp(tb + kAccCol, desc_add(a0, kmajor_kslice(128, kk)), desc_add(dH, mnmajor_kslice(kk)),
-                        id_layer, kk != 0);
-        umma_commit_warp(&G->bar_mma);
-        done = mbar_wait(&G->bar_mma, phase, kWaitLimit);
-      }
-      ok = group_sync_and(g, done);
-      phase ^= 1;
-      tc_fence_after();
-      if (!ok) break;
-      const float bias = S->bh[l][u];
-#pragma unroll 1
-      for (int n0 = 0; n0 < kTile; n0 += 16) {
-        float v[16], w[16];
-        tmem_ld16(taddr(tb, lane_base, kAccCol + n0), v);
-        if (kSplit) tmem_ld16(taddr(tb, lane_base, kAccCol + kTileSplit + n0), w);
-        tmem_ld_wait();
-        f32x2 h[8];
-        const f32x2 b2 = pk2(bias, bias);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          float e0, e1;
-          f32x2 z = add2(pk2(v[2 * j], v[2 * j + 1]), b2);
-          if (kSplit) z = add2(z, pk2(w[2 * j], w[2 * j + 1]));
-          h[j] = elu2(z, e0, e1);
+        for (int j = 0; j < 4; ++j) {
+          const uint4 w = __ldg(src + c0 / 4 + j);
+          v[4 * j] = __uint_as_float(w.x);
+          v[4 * j + 1] = __uint_as_float(w.y);
+          v[4 * j + 2] = __uint_as_float(w.z);
+          v[4 * j + 3] = __uint_as_float(w.w);
         }
-        if (!last) {
-          store_split16<kSplit>(H, u, n0, kTileSplit + n0, h);
-        } else {
-          float wv[16];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            unpk2(h[j], wv[2 * j], wv[2 * j + 1]);
-            wv[2 * j] *= wo;
-            wv[2 * j + 1] *= wo;
-          }
-          const float t = warp_sum16(wv, lane);
-          if ((lane & 1) == 0) G->outp[lq][n0 + ((lane >> 1) & 15)] = t;
-        }
+        tmem_st16(taddr(tb, (uint32_t)warp * 32, kLoCol + (uint32_t)l * 64 + c0), v);
       }
     }
-    if (!ok) break;
-    group_sync(g);
-    if (gt < kTile) {
-      const int n = p0 + gt;
-      const float o = (G->outp[0][gt] + G->outp[1][gt]) + (G->outp[2][gt] + G->outp[3][gt]);
-      if (n < p.n_pts) p.out[(size_t)code * p.n_pts + n] = o + p.bout;
-    }
+    tmem_st_wait();
   }
-  if (!ok && gt == 0) atomicExch(p.flag, 1);
+  wait_or_abort(S, &S->bar_w, 0);
   tc_fence_before();
   __syncthreads();
-  if (tid < 32) tmem_dealloc(S->tmem_base, kTmemCols);
+  tc_fence_after();
+
+  const int stride = gridDim.x * kSlots;
+  if (warp == kMmaWarp) {
+    // ------------------------------------------------------------ MMA warp
+    const uint32_t wbase = smem_u32(Wimg);
+    const uint64_t dW = smem_desc_sw128(wbase, 16, 1024);
+    constexpr uint32_t id_main = idesc_f16(128, 128, false, true, false);
+    constexpr uint32_t id_lo = idesc_f16(128, 64, false, true, false);
+    uint32_t pf[kSlots] = {0, 0};
+    bool issued = false;
+    for (int t0 = blockIdx.x * kSlots; t0 < p.n_tiles; t0 += stride) {
+      const int nslot = min(kSlots, p.n_tiles - t0);
+      for (int l = 0; l < L1; ++l) {
+        for (int s = 0; s < nslot; ++s) {
+          wait_or_abort(S, &S->full[s], pf[s]);
+          pf[s] ^= 1;
+          if (aborted(S)) continue;
+          tc_fence_after();
+          const uint32_t d = tb + (uint32_t)s * kSlotCols;
+          const uint64_t a0 = desc_add(dW, (uint32_t)l * kTcLayerBytes);
+          const uint64_t b0 = smem_desc_sw128(smem_u32(Hbase + (size_t)s * kHBuf), 16384, 1024);
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk)
+            umma_f16_warp(d, desc_add(a0, kmajor_kslice(128, kk)), desc_add(b0, mnmajor_kslice(kk)), id_main,
+                          kk != 0);
+          if (kSplit) {
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk)
+              umma_ts_warp(d, tb + kLoCol + (uint32_t)l * 64 + kk * 8, desc_add(b0, mnmajor_kslice(kk)), id_lo, 1);
+          }
+          umma_commit_warp(&S->acc[s]);
+          issued = true;
+        }
+      }
+    }
+    if (issued && !aborted(S)) {
+      umma_commit_warp(&S->drain);  // arrives when every UMMA issued above has completed
+      wait_or_abort(S, &S->drain, 0);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue warps
+    const int s = warp / kEpiWarps, j = warp % kEpiWarps;
+    const int lq = j & 3, hf = j >> 2;
+    const int u = lq * 32 + lane;             // hidden unit = TMEM lane
+    const int et = j * 32 + lane;             // thread index within the slot
+    const uint32_t lane_base = (uint32_t)lq * 32;
+    const uint32_t acc = tb + (uint32_t)s * kSlotCols;
+    uint8_t* H = Hbase + (size_t)s * kHBuf;
+    const float wx0 = S->w1x[0][u], wx1 = (m > 1) ? S->w1x[1][u] : 0.f;
+    const float wo = S->wout[u];
+    uint32_t pa = 0;
+    int cur_code = -1;
+    float c = 0.f;
+    for (int t = blockIdx.x * kSlots + s; t < p.n_tiles; t += stride) {
+      const int code = t / p.tiles_per_code;
+      const int p0 = (t % p.tiles_per_code) * kPts;
+      if (code != cur_code) {
+        double cc = (double)p.b1[u];
+        for (int jj = 0; jj < r; ++jj) cc += (double)p.w1[u * (m + r) + m + jj] * p.q[(size_t)code * r + jj];
+        c = (float)cc;
+        cur_code = code;
+      }
+      slot_sync(s);  // the previous tile's outputs are written
+      if (et < kPts) {
+        const int n = p0 + et;
+        for (int k = 0; k < m; ++k) S->xs[s][k][et] = (n < p.n_pts) ? p.x[(size_t)n * m + k] : 0.f;
+      }
+      slot_sync(s);
+      // ---- layer 1 on CUDA cores
+#pragma unroll 1
+      for (int n0 = hf * kPer; n0 < hf * kPer + kPer; n0 += 16) {
+        f32x2 h[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          f32x2 z = fma2(pk2(wx0, wx0), pk2(S->xs[s][0][n0 + 2 * i], S->xs[s][0][n0 + 2 * i + 1]), pk2(c, c));
+          if (m > 1) z = fma2(pk2(wx1, wx1), pk2(S->xs[s][1][n0 + 2 * i], S->xs[s][1][n0 + 2 * i + 1]), z);
+          float e0, e1;
+          h[i] = elu2(z, e0, e1);
+        }
+        store_split16<kSplit>(H, u, n0, h);
+      }
+      fence_proxy_async_smem();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S->full[s]);
+      // ---- hidden layers: the accumulator, then the next operand (or the output)
+      for (int l = 0; l < L1; ++l) {
+        const bool last = (l == L1 - 1);
+        wait_or_abort(S, &S->acc[s], pa);
+        pa ^= 1;
+        tc_fence_after();
+        const float bias = S->bh[l][u];
+        const f32x2 b2 = pk2(bias, bias);
+#pragma unroll 1
+        for (int n0 = hf * kPer; n0 < hf * kPer + kPer; n0 += 16) {
+          float v[16], w[16];
+          tmem_ld16(taddr(acc, lane_base, n0), v);
+          if (kSplit) tmem_ld16(taddr(acc, lane_base, 64 + n0), w);
+          tmem_ld_wait();
+          f32x2 h[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            float e0, e1;
+            f32x2 z = add2(pk2(v[2 * i], v[2 * i + 1]), b2);
+            if (kSplit) z = add2(z, pk2(w[2 * i], w[2 * i + 1]));
+            h[i] = elu2(z, e0, e1);
+          }
+          if (!last) {
+            store_split16<kSplit>(H, u, n0, h);
+          } else {
+            float wv[16];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              unpk2(h[i], wv[2 * i], wv[2 * i + 1]);
+              wv[2 * i] *= wo;
+              wv[2 * i + 1] *= wo;
+            }
+            const float tsum = warp_sum16(wv, lane);
+            if ((lane & 1) == 0) S->outp[s][lq][n0 + ((lane >> 1) & 15)] = tsum;
+          }
+        }
+        tc_fence_before();
+        if (!last) {
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&S->full[s]);
+        }
+      }
+      slot_sync(s);
+      if (et < kPts) {
+        const int n = p0 + et;
+        const float o = (S->outp[s][0][et] + S->outp[s][1][et]) + (S->outp[s][2][et] + S->outp[s][3][et]);
+        if (n < p.n_pts) p.out[(size_t)code * p.n_pts + n] = o + p.bout;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && aborted(S)) atomicExch(p.flag, 1);
+  if (warp == 0) tmem_dealloc(tb, kTmemCols);
 }
 
 }  // namespace
@@ -300,8 +353,9 @@ cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const d
                             const float* x, float* out, cudaStream_t s) {
   ReconParams p{};
   p.img = ctx->w.tc_img;
-  p.img_bytes = (int)ctx->w.tc_img_bytes;
   p.n_hidden_mats = ctx->desc.hidden - 1;
+  p.hidden_bytes = p.n_hidden_mats * kTcLayerBytes;
+  p.lo = reinterpret_cast<const uint16_t*>(ctx->w.tc_lo);
   p.m = ctx->desc.m;
   p.r = ctx->desc.r;
   p.w1 = ctx->w.w1;
@@ -314,14 +368,14 @@ cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const d
   p.out = out;
   p.n_pts = n_pts;
   p.n_codes = n_codes;
-  const int tile_pts = split ? kTileSplit : kTileHi;
+  const int tile_pts = split ? 64 : 128;
   p.tiles_per_code = (n_pts + tile_pts - 1) / tile_pts;
   p.flag = ctx->queue + 2;
-  const size_t smem = 1024 + (((size_t)p.img_bytes + 1023) & ~(size_t)1023) + (size_t)kGroups * kHBuf +
-                      kTailBytes;
   const long long tiles = (long long)n_codes * p.tiles_per_code;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-  const int grid = (int)std::min<long long>((tiles + kGroups - 1) / kGroups, ctx->num_sms);
+  p.n_tiles = (int)tiles;
+  const size_t smem = 1024 + (size_t)p.hidden_bytes + (size_t)kSlots * kHBuf + sizeof(Shared);
+  const int grid = (int)std::min<long long>((tiles + kSlots - 1) / kSlots, ctx->num_sms);
   cudaError_t e;
   if (split) {
     e = cudaFuncSetAttribute(recon_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -1,4 +1,4 @@
-// Batched latent step on the tcgen05 tensor cores (crom_step, CROM_PREC_BF16X2).
+// Batched latent step on the tcgen05 tensor cores (crom_step, CROM_PREC_F16X2).
 //
 // One persistent launch per step, one CTA per SM holding the decoder's bf16
 // hidden matrices in shared memory.  The CTA runs four independent groups of 128
@@ -82,6 +82,9 @@ constexpr size_t kHBuf = (size_t)kTcWidth * 64 * 2;  // one 64-column bf16 MN-ma
 struct StepParams {
   const uint8_t* img;
   int img_bytes;
+  // power-of-two channel scales (f16 operand range): sx for dg/dx_k (sxi = 1/sx,
+  // sx2i = 1/sx^2 for the Laplacian), sr for the reverse pass (sri = 1/sr)
+  float sx, sxi, sx2i, sr, sri;
   int L;  // hidden layers
   int r;
   const float* w1;
@@ -130,6 +133,7 @@ struct __align__(16) Group {
   double invd[16];
   float c1[kTcWidth];
   float dz1[kTcWidth];
+  float dmax[4];
   float xs[2][kSMax];
   float rho[kSMax];
   float zero[kSMax];
@@ -160,8 +164,8 @@ __device__ __forceinline__ void split_store(uint8_t* H, int k, int n_hi, int n_l
   uint32_t hi[kC / 2], lo[kC / 2];
 #pragma unroll
   for (int j = 0; j < kC / 2; ++j) {
-    hi[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
-    lo[j] = pack_bf16_lo(hi[j], v[2 * j], v[2 * j + 1]);
+    hi[j] = pack_f16(v[2 * j], v[2 * j + 1]);
+    lo[j] = pack_f16_lo(hi[j], v[2 * j], v[2 * j + 1]);
   }
   if constexpr (kC == 8) {
     *reinterpret_cast<uint4*>(H + mn_offset(k, n_hi)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
@@ -173,10 +177,10 @@ __device__ __forceinline__ void split_store(uint8_t* H, int k, int n_hi, int n_l
   }
 }
 
-// e^x - 1 for |x| < 1/16 by its degree-5 Taylor polynomial (truncation < 1.3e-9
-// relative).
-__device__ __forceinline__ float expm1_taylor(float x) {
-  return x * fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f), 0.5f), 1.f);
+// (e^x - 1) / x for |x| < 1/16 by the degree-4 polynomial of the Taylor series of
+// e^x - 1 divided by x (truncation < 1.3e-9 relative).
+__device__ __forceinline__ float expm1_over_x(float x) {
+  return fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f), 0.5f), 1.f);
 }
 // s(a) - s(a - d) for the cases the inline path leaves: mixed signs of a and
 // a - d, or both non-positive with |d| >= 1/16.  Kept out of line: these cases are
@@ -192,11 +196,14 @@ __device__ __noinline__ float elu_diff_slow(float a, float d, float e) {
 // channel carries h(q^(k)) - h(q_n), so the residual g(y, q^(k)) - g(y, q_n) - Delta f
 // keeps its relative accuracy although the two evaluations agree to many digits.
 // Both positive: d; both non-positive: e^a - e^(a-d) = -e^a (e^(-d) - 1).
-__device__ __forceinline__ float elu_diff(float a, float d, float e) {
+// The channel is carried scaled by a power of two, ds = d * sc (sci = 1 / sc), so
+// that its f16 operands stay in range; the result is returned with the same scale.
+__device__ __forceinline__ float elu_diff(float a, float ds, float e, float sc, float sci) {
+  const float d = ds * sci;
   const float b = a - d;
-  if (a > 0.f && b > 0.f) return d;
-  if (a <= 0.f && b <= 0.f && fabsf(d) < 0.0625f) return -e * expm1_taylor(-d);
-  return elu_diff_slow(a, d, e);
+  if (a > 0.f && b > 0.f) return ds;
+  if (a <= 0.f && b <= 0.f && fabsf(d) < 0.0625f) return e * ds * expm1_over_x(-d);
+  return elu_diff_slow(a, d, e) * sc;
 }
 
 // Forward activation chain of kC samples of one hidden unit, in place, on packed
@@ -205,7 +212,7 @@ __device__ __forceinline__ float elu_diff(float a, float d, float e) {
 // channel; later v[1] the difference channel.  sg receives s'(z).
 //   h = s(z); dh/dx_k = s'(z) dz/dx_k; Lap h = s''(z) sum_k (dz/dx_k)^2 + s'(z) Lap z.
 template <int kM, bool kFirst, int kCh, int kC>
-__device__ __forceinline__ void act(float (&v)[kCh][kC], float (&sg)[kC]) {
+__device__ __forceinline__ void act(float (&v)[kCh][kC], float (&sg)[kC], float dsc, float dsci) {
 #pragma unroll
   for (int j = 0; j < kC / 2; ++j) {
     const int i0 = 2 * j, i1 = 2 * j + 1;
@@ -230,8 +237,8 @@ __device__ __forceinline__ void act(float (&v)[kCh][kC], float (&sg)[kC]) {
       const f32x2 lz = pk2(v[kCh - 1][i0], v[kCh - 1][i1]);
       unpk2(fma2(s2, sq, mul2(s1, lz)), v[kCh - 1][i0], v[kCh - 1][i1]);
     } else {
-      v[1][i0] = elu_diff(z0, v[1][i0], e0);
-      v[1][i1] = elu_diff(z1, v[1][i1], e1);
+      v[1][i0] = elu_diff(z0, v[1][i0], e0, dsc, dsci);
+      v[1][i1] = elu_diff(z1, v[1][i1], e1, dsc, dsci);
     }
   }
 }
@@ -252,7 +259,7 @@ __device__ __forceinline__ void issue_layer(uint32_t d, uint64_t a0, uint64_t b0
 // is the MN-major A operand, so row n < 64 projects a hi part and row 64 + n the
 // matching lo part.
 __device__ __forceinline__ void issue_proj(uint32_t d, uint64_t a0, uint64_t p0) {
-  constexpr uint32_t id = idesc_f16(128, 16, true, false, true);
+  constexpr uint32_t id = idesc_f16(128, 16, true, false, false);
 #pragma unroll
   for (int kk = 0; kk < 8; ++kk)
     umma_f16_warp(d, desc_add(a0, mnmajor_kslice(kk)), desc_add(p0, kmajor_kslice(16, kk)), id, kk > 0);
@@ -267,6 +274,11 @@ struct Lane {
   Group* G;
   uint64_t dW_k, dW_mn, dP, dH;
   float wx0, wx1, wsq, wo;
+  // Power-of-two scales of the channels carried in f16: gx0/gx1 = W_1x[:, k] * sx
+  // (dg/dx_k channels, scale sx; the Laplacian channel then carries sx^2), wos =
+  // w_out * sr (reverse pass), dsc = difference-channel scale of the current GN
+  // iteration (dsci = 1 / dsc)
+  float gx0, gx1, wos, dsc, dsci;
   uint32_t phase;
 };
 
@@ -397,10 +409,10 @@ __device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int n
     tmem_ldc(taddr(tb, lb, kSig + (p.L - 2) * kSS + s0 + h8), sg);
     tmem_ld_wait();
 #pragma unroll
-    for (int i = 0; i < kC; ++i) sg[i] *= c.wo;
+    for (int i = 0; i < kC; ++i) sg[i] *= c.wos;
     split_store<kC>(c.H, u, s0 + h8, kSm + s0 + h8, sg);  // delta_L
   }
-  constexpr uint32_t id_bwd = idesc_f16(128, 2 * kSm, true, true, true);
+  constexpr uint32_t id_bwd = idesc_f16(128, 2 * kSm, true, true, false);
   for (int l = p.L - 2; l >= 0; --l) {
     // accumulator = W_{l+2}^T delta_{l+2}; times s'(z_{l+1}) gives delta_{l+1}
     if (!stage<kStageBwd>(c, l, id_bwd)) return false;
@@ -428,7 +440,7 @@ __device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int n
     const int part = u / kSm, s = u % kSm;
     if (u < 2 * kSm) {
 #pragma unroll
-      for (int j = 0; j < 15; ++j) G->jt[part][s][j] = v[j + 1];
+      for (int j = 0; j < 15; ++j) G->jt[part][s][j] = v[j + 1] * p.sri;
     }
   }
   group_sync(c.g);
@@ -491,14 +503,14 @@ __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j
         if (kM > 1) z = fmaf(c.wx1, G->xs[1][so + s0 + h8 + i], z);
         v[0][i] = z;
         if (kFirst) {
-          v[1][i] = c.wx0;
-          if (kM > 1) v[2][i] = c.wx1;
+          v[1][i] = c.gx0;
+          if (kM > 1) v[2][i] = c.gx1;
           v[kCh - 1][i] = 0.f;
         } else {
           v[1][i] = dz;
         }
       }
-      act<kM, kFirst, kCh, kC>(v, sg);
+      act<kM, kFirst, kCh, kC>(v, sg, c.dsc, c.dsci);
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) {
         const int n = ch * kSm + s0 + h8;
@@ -509,7 +521,7 @@ __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j
   // ---------------- hidden layers 2..L (tensor cores): one UMMA per K slice whose N
   // spans the hi columns (0..kLo-1) and the used lo columns (kLo..kLo+kN-1), rounded
   // up to a multiple of 16
-  constexpr uint32_t id_fwd = idesc_f16(128, kLo + ((kN + 15) & ~15), false, true, true);
+  constexpr uint32_t id_fwd = idesc_f16(128, kLo + ((kN + 15) & ~15), false, true, false);
   for (int l = 0; l < p.L - 1; ++l) {
     if (!stage<kStageFwd>(c, l, id_fwd)) return false;
     const float bias = S->bh[l][u];
@@ -529,7 +541,7 @@ __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j
           unpk2(add2(pk2(v[ch][i], v[ch][i + 1]), pk2(w[ch][i], w[ch][i + 1])), v[ch][i], v[ch][i + 1]);
 #pragma unroll
       for (int i = 0; i < kC; i += 2) unpk2(add2(pk2(v[0][i], v[0][i + 1]), pk2(bias, bias)), v[0][i], v[0][i + 1]);
-      act<kM, kFirst, kCh, kC>(v, sg);
+      act<kM, kFirst, kCh, kC>(v, sg, c.dsc, c.dsci);
       tmem_stc(taddr(tb, lb, kSig + l * kSS + so + s0 + h8), sg);
       if (l < p.L - 2) {
 #pragma unroll
@@ -576,19 +588,20 @@ __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j
     if (c.gt < ns) {
       const int j = j0 + c.gt;
       if (kFirst) {
-        const float lap = gout(kCh - 1, c.gt);
+        const float lap = gout(kCh - 1, c.gt) * p.sx2i;
         double df;
         if (p.pde == CROM_PDE_HEAT) {
           df = p.dt * (double)alpha * (double)lap;
         } else {
           double adv = 0.0;
-          for (int k = 0; k < kM; ++k) adv += (double)p.vel[(size_t)j * kM + k] * (double)gout(1 + k, c.gt);
+          for (int k = 0; k < kM; ++k)
+            adv += (double)p.vel[(size_t)j * kM + k] * (double)(gout(1 + k, c.gt) * p.sxi);
           df = p.dt * (-adv + (double)alpha * (double)lap);
         }
         p.df[j] = df;
         rho = (float)(-df);
       } else {
-        rho = (float)((double)gout(1, c.gt) - df_j);
+        rho = (float)((double)(gout(1, c.gt) * c.dsci) - df_j);
       }
     }
     G->rho[so + c.gt] = rho;
@@ -632,20 +645,30 @@ __device__ __forceinline__ bool run_pair(Lane& c, const StepParams& p, int o0, i
 
 // Layer-1 constants of the tile passes at the point q: c1 = b_1 + W_1q q (value
 // channel) and dz1 = W_1q (q - q_n) (difference channel), FP64 sums rounded once;
-// W_1q is read from global memory (L1-cached: once per GN iteration).
+// W_1q is read from global memory (L1-cached: once per GN iteration).  The
+// difference channel is carried scaled by dsc = 2^e with max_u |dz1_u| * dsc in
+// [1, 2) (its f16 operands would otherwise be subnormal); every thread of the group
+// takes part (a group barrier inside).
 template <int kM>
-__device__ __forceinline__ void set_layer1(const Lane& c, const StepParams& p, Group* G, const double* q) {
+__device__ __forceinline__ void set_layer1(Lane& c, const StepParams& p, Group* G, const double* q) {
   const float* w = p.w1 + (size_t)c.u * (kM + p.r) + kM;
-  if (kTPU == 1 || c.part == 0) {
-    double cc = (double)p.b1[c.u];
-    for (int j = 0; j < p.r; ++j) cc = fma((double)w[j], q[j], cc);
-    G->c1[c.u] = (float)cc;
-  }
-  if (kTPU == 1 || c.part == 1) {
-    double dz = 0.0;
-    for (int j = 0; j < p.r; ++j) dz = fma((double)w[j], q[j] - G->qn[j], dz);
-    G->dz1[c.u] = (float)dz;
-  }
+  double cc = (double)p.b1[c.u];
+  for (int j = 0; j < p.r; ++j) cc = fma((double)w[j], q[j], cc);
+  G->c1[c.u] = (float)cc;
+  double dz = 0.0;
+  for (int j = 0; j < p.r; ++j) dz = fma((double)w[j], q[j] - G->qn[j], dz);
+  const float dzf = (float)dz;
+  float mx = fabsf(dzf);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((c.gt & 31) == 0) G->dmax[c.gw & 3] = mx;
+  group_sync(c.g);
+  mx = fmaxf(fmaxf(G->dmax[0], G->dmax[1]), fmaxf(G->dmax[2], G->dmax[3]));
+  int ex = 0;
+  if (mx > 0.f && mx < 3.0e38f) ex = min(max(-ilogbf(mx), -100), 100);
+  c.dsc = ldexpf(1.f, ex);
+  c.dsci = ldexpf(1.f, -ex);
+  G->dz1[c.u] = dzf * c.dsc;
 }
 
 template <int kM, int kS1>
@@ -710,6 +733,10 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
   c.wx1 = (kM > 1) ? S->w1x[1][c.u] : 0.f;
   c.wsq = c.wx0 * c.wx0 + c.wx1 * c.wx1;
   c.wo = S->wout[c.u];
+  c.gx0 = c.wx0 * p.sx;
+  c.gx1 = c.wx1 * p.sx;
+  c.wos = c.wo * p.sr;
+  c.dsc = c.dsci = 1.f;
   const int ntri = r * (r + 1) / 2;
   const int n_entries = ntri + r;  // <= 135; with the line search's rho^T rho <= 136 <= 2 kGT
   // normal-equation entries k = c.gt and c.gt + kGT owned by this thread
@@ -916,6 +943,11 @@ cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst
   StepParams p{};
   p.img = ctx->w.tc_img;
   p.img_bytes = (int)ctx->w.tc_img_bytes;
+  p.sx = ctx->w.tc_sx;
+  p.sxi = 1.f / ctx->w.tc_sx;
+  p.sx2i = p.sxi * p.sxi;
+  p.sr = ctx->w.tc_sr;
+  p.sri = 1.f / ctx->w.tc_sr;
   p.L = ctx->desc.hidden;
   p.r = ctx->desc.r;
   p.w1 = ctx->w.w1;

@@ -1,6 +1,6 @@
 // One training step of the CROM manifold (paper §3, Eq. loss; App. D): strided
 // 1D-convolution encoder + MLP decoder, MSE over sampled points, hand-written
-// reverse pass and Adam, all in FP32 on CUDA cores with FP32 master weights.
+// reverse pass and Adam with FP32 master weights.
 //
 // Encoder (App. D): convolutions of kernel 6, stride 4, one channel, no padding,
 // ELU after each, repeated while the output length stays >= 32; then a dense
@@ -13,13 +13,12 @@
 // convolution w[6], b, then the dense layers (W [32][L_last], b[32]),
 // (W [r][32], b[r]).
 //
-// The dense contractions go through one tiled FP32 GEMM with strided operands
-// and fused epilogues (bias + ELU, multiply by s'(z)); weight gradients reduce
-// over the B*S points with a fixed split along K and a second pass that adds
-// the splits in order, so a step is deterministic.  With CROM_PREC_TF32 the same
-// contractions are plain cuBLAS GEMMs on the TF32 tensor cores, followed by the
-// epilogue as an elementwise kernel.
-#include <cublas_v2.h>
+// The decoder pass runs either here in FP32 (one tiled FP32 GEMM with strided
+// operands and fused epilogues, bias + ELU and multiply by s'(z); weight gradients
+// reduce over the B*S points with a fixed split along K and a second pass that adds
+// the splits in order, so a step is deterministic) or, with CROM_PREC_BF16_MIXED, on
+// the tensor cores (train_tc.cu).  The encoder, the latent gradient and Adam are
+// shared.
 #include <math.h>
 
 #include <vector>
@@ -35,9 +34,6 @@ constexpr int kSplitK = 32;
 
 __device__ __forceinline__ float elu_f(float z) { return z > 0.f ? z : expm1f(z); }
 __device__ __forceinline__ float elu_d(float z) { return z > 0.f ? 1.f : expf(z); }
-// s'(z) from h = s(z): 1 where h > 0, else e^z = h + 1 (the TF32 path keeps only h
-// of each hidden layer, not z).
-__device__ __forceinline__ float elu_d_h(float h) { return h > 0.f ? 1.f : h + 1.f; }
 
 // Compensated (Kahan) FP32 accumulation: the running sum s - c stays within a few
 // ulps of the exact sum whatever the number of terms, in FP32 instructions (FP64 is
@@ -53,13 +49,11 @@ struct CompSum {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-enum Epi { kEpiStore = 0, kEpiBiasElu = 1, kEpiTimesEluD = 2, kEpiBias = 3 };
+enum Epi { kEpiStore = 0, kEpiBiasElu = 1, kEpiTimesEluD = 2 };
 
 // C[i][j] = sum_k A(i, k) B(k, j), A(i, k) = A[i*sai + k*sak], B(k, j) = B[k*sbk + j*sbj].
 // Epilogues: kEpiStore (C row-major, ldc); kEpiBiasElu (Z = C + bias[j] stored in C,
-// ELU(Z) stored in H); kEpiTimesEluD (C *= s'(Zp[i][j])).  (The TF32 path's
-// elementwise kernels below differ: its bias + ELU stores only H, its "x s'" reads H,
-// and kEpiBias, C += bias, serves its linear layer.)  blockIdx.z splits K into
+// ELU(Z) stored in H); kEpiTimesEluD (C *= s'(Zp[i][j])).  blockIdx.z splits K into
 // gridDim.z contiguous ranges writing to C + z * split_stride (kEpiStore only).
 __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const float* __restrict__ A, long sai,
                                                    long sak, const float* __restrict__ B, long sbk, long sbj,
@@ -119,162 +113,6 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
       }
     }
   }
-}
-
-// Elementwise epilogues after a library GEMM (C row-major, M x N, ldc) in the TF32
-// path: bias + ELU writes h (the scalar form also leaves z in C), and "x s'(z)"
-// takes s' from h (Hp).
-__global__ void epi_bias_elu_kernel(float* C, long M, int N, long ldc, const float* bias, float* H) {
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= M * N) return;
-  const long i = t / N;
-  const int j = (int)(t % N);
-  const long o = i * ldc + j;
-  const float v = C[o] + bias[j];
-  C[o] = v;
-  H[o] = elu_f(v);
-}
-__global__ void epi_bias_kernel(float* C, long M, int N, long ldc, const float* bias) {
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= M * N) return;
-  const long o = (t / N) * ldc + (t % N);
-  C[o] += bias[t % N];
-}
-__global__ void epi_times_elud_kernel(float* C, long M, int N, long ldc, const float* Hp) {
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= M * N) return;
-  const long o = (t / N) * ldc + (t % N);
-  C[o] *= elu_d_h(Hp[o]);
-}
-
-// The same epilogues four columns at a time (N % 4 == 0, ldc % 4 == 0, 16-byte
-// aligned rows): rows over blockIdx.y / threadIdx.y, column quads over x.
-__global__ void epi_bias_elu4_kernel(float* C, long M, int N4, long ldc, const float* bias, float* H) {
-  for (long i = (long)blockIdx.y * blockDim.y + threadIdx.y; i < M; i += (long)gridDim.y * blockDim.y)
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < N4; q += gridDim.x * blockDim.x) {
-      float4* cp = reinterpret_cast<float4*>(C + i * ldc) + q;
-      const float4 b = reinterpret_cast<const float4*>(bias)[q];
-      float4 z = *cp;
-      z.x += b.x; z.y += b.y; z.z += b.z; z.w += b.w;
-      reinterpret_cast<float4*>(H + i * ldc)[q] = make_float4(elu_f(z.x), elu_f(z.y), elu_f(z.z), elu_f(z.w));
-    }
-}
-__global__ void epi_times_elud4_kernel(float* C, long M, int N4, long ldc, const float* Hp) {
-  for (long i = (long)blockIdx.y * blockDim.y + threadIdx.y; i < M; i += (long)gridDim.y * blockDim.y)
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < N4; q += gridDim.x * blockDim.x) {
-      float4* cp = reinterpret_cast<float4*>(C + i * ldc) + q;
-      const float4 hp = reinterpret_cast<const float4*>(Hp + i * ldc)[q];
-      float4 v = *cp;
-      v.x *= elu_d_h(hp.x); v.y *= elu_d_h(hp.y); v.z *= elu_d_h(hp.z); v.w *= elu_d_h(hp.w);
-      *cp = v;
-    }
-}
-
-// The TF32 path's "x s'(z)" epilogue and output-layer delta with the column sums of
-// the result fused in (the bias gradients of the next layer down): blocks of 64
-// column quads x 4 row lanes, a fixed grid of kEpiRowBlocks row blocks striding over
-// the rows; each thread keeps compensated sums of its four columns, the block adds
-// its four row lanes and writes part[blockIdx.y][cols]; colsum_blocks_final_kernel
-// adds the row blocks in order.
-constexpr int kEpiRowBlocks = 4096;
-__device__ __forceinline__ void colpart_store(CompSum (&cs)[4], int q, int N4, double* part) {
-  __shared__ double red[4][64][4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) red[threadIdx.y][threadIdx.x][e] = cs[e].value();
-  __syncthreads();
-  if (threadIdx.y == 0 && q < N4)
-#pragma unroll
-    for (int e = 0; e < 4; ++e)
-      part[(long)blockIdx.y * 4 * N4 + 4 * q + e] =
-          (red[0][threadIdx.x][e] + red[1][threadIdx.x][e]) + (red[2][threadIdx.x][e] + red[3][threadIdx.x][e]);
-}
-__global__ void epi_times_elud4_colsum_kernel(float* C, long M, int N4, long ldc, const float* Hp, double* part) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  CompSum cs[4];
-  if (q < N4)
-    for (long i = (long)blockIdx.y * blockDim.y + threadIdx.y; i < M; i += (long)gridDim.y * blockDim.y) {
-      float4* cp = reinterpret_cast<float4*>(C + i * ldc) + q;
-      const float4 hp = reinterpret_cast<const float4*>(Hp + i * ldc)[q];
-      float4 v = *cp;
-      v.x *= elu_d_h(hp.x); v.y *= elu_d_h(hp.y); v.z *= elu_d_h(hp.z); v.w *= elu_d_h(hp.w);
-      *cp = v;
-      cs[0].add(v.x); cs[1].add(v.y); cs[2].add(v.z); cs[3].add(v.w);
-    }
-  colpart_store(cs, q, N4, part);
-}
-__global__ void out_delta4_colsum_kernel(const float* dg, const float* wout, const float* Hl, long N, int w4,
-                                         float* delta, double* part) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  CompSum cs[4];
-  if (q < w4) {
-    const float4 wo = reinterpret_cast<const float4*>(wout)[q];
-    for (long n = (long)blockIdx.y * blockDim.y + threadIdx.y; n < N; n += (long)gridDim.y * blockDim.y) {
-      const float d = dg[n];
-      const float4 h = reinterpret_cast<const float4*>(Hl + n * 4 * w4)[q];
-      const float4 v = make_float4(d * wo.x * elu_d_h(h.x), d * wo.y * elu_d_h(h.y), d * wo.z * elu_d_h(h.z),
-                                   d * wo.w * elu_d_h(h.w));
-      reinterpret_cast<float4*>(delta + n * 4 * w4)[q] = v;
-      cs[0].add(v.x); cs[1].add(v.y); cs[2].add(v.z); cs[3].add(v.w);
-    }
-  }
-  colpart_store(cs, q, w4, part);
-}
-// The last hidden layer's bias + ELU epilogue (TF32 path, width <= 256) with the
-// output layer fused in: g_n = w_out . h_n + b_out, dL/dg_n = 2 (g_n - t_n) / N, and
-// per-block sums of (g_n - t_n)^2 (partial[blockIdx.y], added in order by
-// loss_final_kernel).  Blocks of 64 column quads x 4 rows, kEpiRowBlocks row blocks
-// striding over the rows; a row's 64 threads (two warps) reduce w_out . h by shuffles.
-__global__ void epi_bias_elu4_out_kernel(float* C, long M, int N4, long ldc, const float* bias, float* H,
-                                         const float* wout, const float* bout, const float* target, float* dg,
-                                         double* partial) {
-  const int q = threadIdx.x;
-  __shared__ float rowpart[4][2];
-  __shared__ double sqpart[4];
-  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  const float4 b = q < N4 ? reinterpret_cast<const float4*>(bias)[q] : zero4;
-  const float4 wo = q < N4 ? reinterpret_cast<const float4*>(wout)[q] : zero4;
-  double sq = 0.0;
-  for (long i0 = (long)blockIdx.y * 4; i0 < M; i0 += (long)gridDim.y * 4) {  // same trip count for the block
-    const long i = i0 + threadIdx.y;
-    float dot = 0.f;
-    if (i < M && q < N4) {
-      float4 z = reinterpret_cast<const float4*>(C + i * ldc)[q];
-      z.x += b.x; z.y += b.y; z.z += b.z; z.w += b.w;
-      const float4 h = make_float4(elu_f(z.x), elu_f(z.y), elu_f(z.z), elu_f(z.w));
-      reinterpret_cast<float4*>(H + i * ldc)[q] = h;
-      dot = fmaf(wo.w, h.w, fmaf(wo.z, h.z, fmaf(wo.y, h.y, wo.x * h.x)));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-    if ((threadIdx.x & 31) == 0) rowpart[threadIdx.y][threadIdx.x >> 5] = dot;
-    __syncthreads();
-    if (threadIdx.x == 0 && i < M) {
-      const float res = (rowpart[threadIdx.y][0] + rowpart[threadIdx.y][1]) + bout[0] - target[i];
-      dg[i] = 2.f * res / (float)M;
-      sq += (double)res * (double)res;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) sqpart[threadIdx.y] = sq;
-  __syncthreads();
-  if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y] = (sqpart[0] + sqpart[1]) + (sqpart[2] + sqpart[3]);
-}
-
-// out[c] = sum over the row blocks of part[blk][c], in order (a fixed tree over 256
-// threads of contiguous block ranges).
-__global__ void colsum_blocks_final_kernel(const double* part, int nblk, int cols, float* out) {
-  const int c = blockIdx.x;
-  __shared__ double red[256];
-  const int per = (nblk + 255) / 256;
-  double s = 0.0;
-  for (int k = threadIdx.x * per; k < min(nblk, (int)(threadIdx.x + 1) * per); ++k) s += part[(long)k * cols + c];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[c] = (float)red[0];
 }
 
 // out[e] = sum_s parts[s * stride + e] (in split order), then optionally out[e] = val.
@@ -455,21 +293,17 @@ __global__ void loss_final_kernel(const double* partial, int n, long N, double* 
   }
   if (threadIdx.x == 0) *loss = red[0] / (double)N;
 }
-// ZH holds z of the last hidden layer (kFromH false) or h (the TF32 path).
-template <bool kFromH>
-__device__ __forceinline__ float elu_d_zh(float v) { return kFromH ? elu_d_h(v) : elu_d(v); }
-template <bool kFromH>
-__global__ void out_delta_kernel(const float* dg, const float* wout, const float* ZH, int w, long N, float* delta) {
+// delta_L[n][u] = dL/dg_n w_out[u] s'(z_L[n][u]).
+__global__ void out_delta_kernel(const float* dg, const float* wout, const float* Z, int w, long N, float* delta) {
   const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (e >= N * w) return;
   const long n = e / w;
   const int u = (int)(e % w);
-  delta[e] = dg[n] * wout[u] * elu_d_zh<kFromH>(ZH[e]);
+  delta[e] = dg[n] * wout[u] * elu_d(Z[e]);
 }
 // The same, four units per thread (w % 4 == 0, N * w / 4 < 2^31, 16-byte aligned):
 // quad e covers row e / (w / 4), units 4 (e % (w / 4)) ..
-template <bool kFromH>
-__global__ void out_delta4_kernel(const float* dg, const float* wout, const float* ZH, int w, unsigned n_quads,
+__global__ void out_delta4_kernel(const float* dg, const float* wout, const float* Z, int w, unsigned n_quads,
                                   float* delta) {
   const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_quads) return;
@@ -477,22 +311,20 @@ __global__ void out_delta4_kernel(const float* dg, const float* wout, const floa
   const long n = e / q;
   const int u = 4 * (int)(e % q);
   const float d = dg[n];
-  const float4 z = *reinterpret_cast<const float4*>(ZH + n * w + u);
+  const float4 z = *reinterpret_cast<const float4*>(Z + n * w + u);
   const float4 wo = *reinterpret_cast<const float4*>(wout + u);
   *reinterpret_cast<float4*>(delta + n * w + u) =
-      make_float4(d * wo.x * elu_d_zh<kFromH>(z.x), d * wo.y * elu_d_zh<kFromH>(z.y),
-                  d * wo.z * elu_d_zh<kFromH>(z.z), d * wo.w * elu_d_zh<kFromH>(z.w));
+      make_float4(d * wo.x * elu_d(z.x), d * wo.y * elu_d(z.y), d * wo.z * elu_d(z.z), d * wo.w * elu_d(z.w));
 }
 
-// dq[b][j] = sum over the S points of snapshot b of din[n][m + j]  (fixed order).
-// dq[b][j] = sum_s din[b S + s][m + j]: one block per snapshot, 256 row lanes,
-// fixed-order tree per latent component.
-__global__ void dq_kernel(const float* din, int B, int S, int m, int r, float* dq) {
+// dq[b][j] = sum_s din[b S + s][m + j] (din rows ld floats apart): one block per
+// snapshot, 256 row lanes, fixed-order tree per latent component.
+__global__ void dq_kernel(const float* din, int ld, int B, int S, int m, int r, float* dq) {
   const int b = blockIdx.x;
   __shared__ double red[256];
   for (int j = 0; j < r; ++j) {
     CompSum s;
-    for (int i = threadIdx.x; i < S; i += blockDim.x) s.add(din[((long)b * S + i) * (m + r) + m + j]);
+    for (int i = threadIdx.x; i < S; i += blockDim.x) s.add(din[((long)b * S + i) * ld + m + j]);
     red[threadIdx.x] = s.value();
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -578,10 +410,9 @@ cudaError_t trainer_alloc(crom_trainer* t) {
   t->edh = (float*)A((size_t)t->B * t->lens[0] * 4);
   t->edx = (float*)A((size_t)t->B * t->lens[0] * 4);
   t->ed1 = (float*)A((size_t)t->B * 32 * 4);
-  t->partial = (double*)A((size_t)std::max<long>(blocks(N, 8), kEpiRowBlocks) * 8);
+  t->partial = (double*)A((size_t)blocks(N, 8) * 8);
   t->loss_dev = (double*)A(8);
   t->red = (double*)A((size_t)kColChunks * std::max(std::max(w, 32), std::max(r, 7)) * 8);
-  t->colpart = (double*)A((size_t)kEpiRowBlocks * w * 8);
   for (void* p : t->owned)
     if (!p) return cudaErrorMemoryAllocation;
   cudaError_t e = cudaMemset(t->am, 0, o * 4);
@@ -592,8 +423,7 @@ cudaError_t trainer_alloc(crom_trainer* t) {
 void trainer_free(crom_trainer* t) {
   for (void* p : t->owned) cudaFree(p);
   t->owned.clear();
-  if (t->blas) cublasDestroy(static_cast<cublasHandle_t>(t->blas));
-  t->blas = nullptr;
+  t->tc = TrainerTc{};
 }
 
 // C = A * B (strided operands) with an epilogue; K split over kSplitK partials when requested.
@@ -601,42 +431,8 @@ void trainer_free(crom_trainer* t) {
 // strides is 1 (row-major or transposed storage).
 static cudaError_t gemm(crom_trainer* t, cudaStream_t s, int M, int N, int K, const float* A, long sai, long sak,
                         const float* B, long sbk, long sbj, float* C, long ldc, int epi, const float* bias,
-                        float* H, const float* Zp, float* split = nullptr, bool* colpart_done = nullptr) {
-  if (colpart_done) *colpart_done = false;
-  if (t->precision == CROM_PREC_TF32) {
-    // Row-major C = A B is column-major C^T = B^T A^T: cuBLAS computes the N x M
-    // column-major product op(B') op(A') with B' = B and A' = A viewed column-major.
-    cublasHandle_t h = static_cast<cublasHandle_t>(t->blas);
-    if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-    const cublasOperation_t opB = sbj == 1 ? CUBLAS_OP_N : CUBLAS_OP_T;
-    const int ldb = (int)(sbj == 1 ? sbk : sbj);
-    const cublasOperation_t opA = (sak == 1 || M == 1) ? CUBLAS_OP_N : CUBLAS_OP_T;
-    const int lda = (int)((sak == 1 || M == 1) ? (M == 1 ? K : sai) : sak);
-    const float one = 1.f, zero = 0.f;
-    cublasStatus_t st = cublasGemmEx(h, opB, opA, N, M, K, &one, B, CUDA_R_32F, ldb, A, CUDA_R_32F, lda, &zero, C,
-                                     CUDA_R_32F, (int)ldc, CUBLAS_COMPUTE_32F_FAST_TF32, CUBLAS_GEMM_DEFAULT);
-    if (st != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-    const long n = (long)M * N;
-    const bool vec = N % 4 == 0 && ldc % 4 == 0 && ((uintptr_t)C & 15) == 0 && (!H || ((uintptr_t)H & 15) == 0) &&
-                     (!Zp || ((uintptr_t)Zp & 15) == 0) && (!bias || ((uintptr_t)bias & 15) == 0);
-    const dim3 vb(64, 4), vg(blocks(N / 4, 64), (unsigned)std::min<long>(blocks(M, 4), 4096));
-    if (epi == kEpiBiasElu) {
-      if (vec) epi_bias_elu4_kernel<<<vg, vb, 0, s>>>(C, M, N / 4, ldc, bias, H);
-      else epi_bias_elu_kernel<<<blocks(n, 256), 256, 0, s>>>(C, M, N, ldc, bias, H);
-    } else if (epi == kEpiBias) {
-      epi_bias_kernel<<<blocks(n, 256), 256, 0, s>>>(C, M, N, ldc, bias);
-    } else if (epi == kEpiTimesEluD) {
-      if (vec && colpart_done && N / 4 <= 64) {  // with the column sums of the result (one block column)
-        epi_times_elud4_colsum_kernel<<<dim3(1, kEpiRowBlocks), vb, 0, s>>>(C, M, N / 4, ldc, Zp, t->colpart);
-        *colpart_done = true;
-      } else if (vec) {
-        epi_times_elud4_kernel<<<vg, vb, 0, s>>>(C, M, N / 4, ldc, Zp);
-      } else {
-        epi_times_elud_kernel<<<blocks(n, 256), 256, 0, s>>>(C, M, N, ldc, Zp);
-      }
-    }
-    return cudaGetLastError();
-  }
+                        float* H, const float* Zp, float* split = nullptr) {
+  (void)t;
   dim3 grid(blocks(N, kTile), blocks(M, kTile), split ? kSplitK : 1);
   if (split) {
     gemm_kernel<<<grid, 256, 0, s>>>(M, N, K, A, sai, sak, B, sbk, sbj, split, ldc, (long)M * ldc, kEpiStore,
@@ -659,11 +455,7 @@ static void colsum(crom_trainer* t, cudaStream_t s, const float* X, long rows, i
 }
 
 int trainer_set_precision(crom_trainer* t, int precision) {
-  if (precision == CROM_PREC_TF32 && !t->blas) {
-    cublasHandle_t h = nullptr;
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return CROM_ERR_CUDA;
-    t->blas = h;
-  }
+  if (precision == CROM_PREC_BF16_MIXED && trainer_tc_alloc(t) != cudaSuccess) return CROM_ERR_CUDA;
   t->precision = precision;
   return CROM_OK;
 }
@@ -682,10 +474,10 @@ cudaError_t trainer_encode(crom_trainer* t, int nb, const float* snaps, float* q
   cudaError_t e = gemm(t, s, nb, 32, Ll, x, Ll, 1, t->params + t->lay.d1w, 1, Ll, t->d1z, 32, kEpiBiasElu,
                        t->params + t->lay.d1b, t->d1h, nullptr);
   if (e != cudaSuccess) return e;
-  // q = W2 h1 + b2: the TF32 path has a bias-only epilogue; the FP32 GEMM reuses its
-  // bias + ELU epilogue (Z = q in C, the ELU discarded into the ed1 scratch)
-  return gemm(t, s, nb, r, 32, t->d1h, 32, 1, t->params + t->lay.d2w, 1, 32, q_out, r,
-              t->precision == CROM_PREC_TF32 ? kEpiBias : kEpiBiasElu, t->params + t->lay.d2b, t->ed1, nullptr);
+  // q = W2 h1 + b2: the bias + ELU epilogue leaves Z = q in C (its ELU is discarded
+  // into the ed1 scratch)
+  return gemm(t, s, nb, r, 32, t->d1h, 32, 1, t->params + t->lay.d2w, 1, 32, q_out, r, kEpiBiasElu,
+              t->params + t->lay.d2b, t->ed1, nullptr);
 }
 
 cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx, const float* coords, float lr,
@@ -693,95 +485,73 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
   const int m = t->dec.m, r = t->dec.r, w = t->dec.width, L = t->dec.hidden;
   const int B = t->B, S = t->S, P = t->P;
   const long N = (long)B * S;
-  // the TF32 path keeps h, not z, of the hidden layers: s'(z) comes from h
-  const bool tf32 = t->precision == CROM_PREC_TF32;
   const TrainerLayout& lay = t->lay;
   float* p = t->params;
   float* gr = t->grads;
   cudaError_t e;
   // ---- encoder forward: q_b
   if ((e = trainer_encode(t, B, snaps, t->q, s)) != cudaSuccess) return e;
-  // ---- decoder forward on the sampled points
+  // ---- decoder forward and reverse pass on the sampled points
   gather_kernel<<<blocks(N, 256), 256, 0, s>>>(snaps, pt_idx, coords, t->q, B, S, P, m, r, t->in0, t->target);
-  const float* hin = t->in0;
-  int kin = m + r;
-  // TF32 path: the output layer and loss are fused into the last hidden layer's epilogue
-  auto a16 = [](const void* ptr) { return ((uintptr_t)ptr & 15) == 0; };
-  const bool fuse_out = t->precision == CROM_PREC_TF32 && w % 4 == 0 && w / 4 <= 64 && a16(t->Z[L - 1]) &&
-                        a16(t->H[L - 1]) && a16(p + lay.dec_b[L - 1]) && a16(p + lay.dec_w[L]);
-  for (int l = 0; l < L; ++l) {
-    const bool out_here = fuse_out && l == L - 1;
-    e = gemm(t, s, (int)N, w, kin, hin, kin, 1, p + lay.dec_w[l], 1, kin, t->Z[l], w,
-             out_here ? kEpiStore : kEpiBiasElu, p + lay.dec_b[l], t->H[l], nullptr);
-    if (e != cudaSuccess) return e;
-    if (out_here)
-      epi_bias_elu4_out_kernel<<<dim3(1, kEpiRowBlocks), dim3(64, 4), 0, s>>>(
-          t->Z[l], N, w / 4, w, p + lay.dec_b[l], t->H[l], p + lay.dec_w[L], p + lay.dec_b[L], t->target, t->dg,
-          t->partial);
-    hin = t->H[l];
-    kin = w;
-  }
-  if (fuse_out) {
-    loss_final_kernel<<<1, 1024, 0, s>>>(t->partial, kEpiRowBlocks, N, loss_out ? loss_out : t->loss_dev);
+  const float* din = t->din;
+  int din_ld = m + r;
+  if (t->precision == CROM_PREC_BF16_MIXED) {
+    if ((e = trainer_decoder_tc(t, loss_out, t->num_sms, s)) != cudaSuccess) return e;
+    din = t->tc.din;
+    din_ld = trainer_tc_din_ld();
   } else {
+    const float* hin = t->in0;
+    int kin = m + r;
+    for (int l = 0; l < L; ++l) {
+      e = gemm(t, s, (int)N, w, kin, hin, kin, 1, p + lay.dec_w[l], 1, kin, t->Z[l], w, kEpiBiasElu, p + lay.dec_b[l],
+               t->H[l], nullptr);
+      if (e != cudaSuccess) return e;
+      hin = t->H[l];
+      kin = w;
+    }
     output_loss_kernel<<<blocks(N, 8), 256, 0, s>>>(t->H[L - 1], w, N, p + lay.dec_w[L], p + lay.dec_b[L], t->target,
                                                      t->dg, t->partial);
     loss_final_kernel<<<1, 1024, 0, s>>>(t->partial, (int)blocks(N, 8), N, loss_out ? loss_out : t->loss_dev);
-  }
-  // ---- decoder reverse pass
-  // output layer: gW_out[u] = sum_n dg[n] H_L[n][u], gb_out = sum dg
-  e = gemm(t, s, 1, w, (int)N, t->dg, 0, 1, t->H[L - 1], w, 1, gr + lay.dec_w[L], w, kEpiStore, nullptr, nullptr,
-           nullptr, t->split);
-  if (e != cudaSuccess) return e;
-  colsum(t, s, t->dg, N, 1, gr + lay.dec_b[L]);
-  const float* wout = p + lay.dec_w[L];
-  const float* zh = tf32 ? t->H[L - 1] : t->Z[L - 1];  // s'(z) of the last hidden layer from h or z
-  const bool vec_out = w % 4 == 0 && ((uintptr_t)wout & 15) == 0 && ((uintptr_t)zh & 15) == 0 &&
-                       ((uintptr_t)t->delta & 15) == 0;
-  // column sums of delta fused into the kernel that writes it (TF32 path), else a
-  // separate deterministic pass
-  bool have_part = false;
-  if (tf32 && vec_out && w / 4 <= 64) {
-    out_delta4_colsum_kernel<<<dim3(1, kEpiRowBlocks), dim3(64, 4), 0, s>>>(t->dg, wout, zh, N, w / 4, t->delta,
-                                                                            t->colpart);
-    have_part = true;
-  } else if (vec_out && N * (w / 4) < (1L << 31)) {
-    const unsigned nq = (unsigned)(N * (w / 4));
-    if (tf32) out_delta4_kernel<true><<<blocks(N * (w / 4), 256), 256, 0, s>>>(t->dg, wout, zh, w, nq, t->delta);
-    else out_delta4_kernel<false><<<blocks(N * (w / 4), 256), 256, 0, s>>>(t->dg, wout, zh, w, nq, t->delta);
-  } else {
-    if (tf32) out_delta_kernel<true><<<blocks(N * w, 256), 256, 0, s>>>(t->dg, wout, zh, w, N, t->delta);
-    else out_delta_kernel<false><<<blocks(N * w, 256), 256, 0, s>>>(t->dg, wout, zh, w, N, t->delta);
-  }
-  float* dcur = t->delta;
-  float* dnext = t->delta2;
-  for (int l = L - 1; l >= 0; --l) {
-    const float* hprev = (l == 0) ? t->in0 : t->H[l - 1];
-    const int kprev = (l == 0) ? m + r : w;
-    // gW_l [w][kprev] = delta^T hprev (K = N, split), gb_l = column sums of delta
-    e = gemm(t, s, w, kprev, (int)N, dcur, 1, w, hprev, kprev, 1, gr + lay.dec_w[l], kprev, kEpiStore, nullptr,
-             nullptr, nullptr, t->split);
+    // output layer: gW_out[u] = sum_n dg[n] H_L[n][u], gb_out = sum dg
+    e = gemm(t, s, 1, w, (int)N, t->dg, 0, 1, t->H[L - 1], w, 1, gr + lay.dec_w[L], w, kEpiStore, nullptr, nullptr,
+             nullptr, t->split);
     if (e != cudaSuccess) return e;
-    if (have_part)
-      colsum_blocks_final_kernel<<<w, 256, 0, s>>>(t->colpart, kEpiRowBlocks, w, gr + lay.dec_b[l]);
-    else
-      colsum(t, s, dcur, N, w, gr + lay.dec_b[l]);
-    have_part = false;
-    if (l > 0) {
-      // delta_{l-1} = (delta_l W_l) * s'(Z_{l-1})  (s' from H_{l-1} in the TF32 path)
-      e = gemm(t, s, (int)N, w, w, dcur, w, 1, p + lay.dec_w[l], w, 1, dnext, w, kEpiTimesEluD, nullptr, nullptr,
-               tf32 ? t->H[l - 1] : t->Z[l - 1], nullptr, &have_part);
+    colsum(t, s, t->dg, N, 1, gr + lay.dec_b[L]);
+    const float* wout = p + lay.dec_w[L];
+    const float* zl = t->Z[L - 1];
+    if (w % 4 == 0 && ((uintptr_t)wout & 15) == 0 && ((uintptr_t)zl & 15) == 0 && ((uintptr_t)t->delta & 15) == 0 &&
+        N * (w / 4) < (1L << 31)) {
+      const unsigned nq = (unsigned)(N * (w / 4));
+      out_delta4_kernel<<<blocks(N * (w / 4), 256), 256, 0, s>>>(t->dg, wout, zl, w, nq, t->delta);
     } else {
-      // input gradient din = delta_1 W_1  [N][m + r]
-      e = gemm(t, s, (int)N, m + r, w, dcur, w, 1, p + lay.dec_w[0], m + r, 1, t->din, m + r, kEpiStore, nullptr,
-               nullptr, nullptr);
+      out_delta_kernel<<<blocks(N * w, 256), 256, 0, s>>>(t->dg, wout, zl, w, N, t->delta);
     }
-    if (e != cudaSuccess) return e;
-    float* tmp = dcur;
-    dcur = dnext;
-    dnext = tmp;
+    float* dcur = t->delta;
+    float* dnext = t->delta2;
+    for (int l = L - 1; l >= 0; --l) {
+      const float* hprev = (l == 0) ? t->in0 : t->H[l - 1];
+      const int kprev = (l == 0) ? m + r : w;
+      // gW_l [w][kprev] = delta^T hprev (K = N, split), gb_l = column sums of delta
+      e = gemm(t, s, w, kprev, (int)N, dcur, 1, w, hprev, kprev, 1, gr + lay.dec_w[l], kprev, kEpiStore, nullptr,
+               nullptr, nullptr, t->split);
+      if (e != cudaSuccess) return e;
+      colsum(t, s, dcur, N, w, gr + lay.dec_b[l]);
+      if (l > 0) {
+        // delta_{l-1} = (delta_l W_l) * s'(Z_{l-1})
+        e = gemm(t, s, (int)N, w, w, dcur, w, 1, p + lay.dec_w[l], w, 1, dnext, w, kEpiTimesEluD, nullptr, nullptr,
+                 t->Z[l - 1]);
+      } else {
+        // input gradient din = delta_1 W_1  [N][m + r]
+        e = gemm(t, s, (int)N, m + r, w, dcur, w, 1, p + lay.dec_w[0], m + r, 1, t->din, m + r, kEpiStore, nullptr,
+                 nullptr, nullptr);
+      }
+      if (e != cudaSuccess) return e;
+      float* tmp = dcur;
+      dcur = dnext;
+      dnext = tmp;
+    }
   }
-  dq_kernel<<<B, 256, 0, s>>>(t->din, B, S, m, r, t->dq);
+  dq_kernel<<<B, 256, 0, s>>>(din, din_ld, B, S, m, r, t->dq);
   // ---- encoder reverse pass
   // dense 2: gW2 = dq^T h1, gb2 = sum dq, dz1 = (dq W2) * s'(z1)
   const int Ll = t->lens.back();
@@ -790,7 +560,7 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
     return e;
   colsum(t, s, t->dq, B, r, gr + lay.d2b);
   if ((e = gemm(t, s, B, 32, r, t->dq, r, 1, p + lay.d2w, 32, 1, t->ed1, 32, kEpiTimesEluD, nullptr, nullptr,
-                tf32 ? t->d1h : t->d1z)) != cudaSuccess)
+                t->d1z)) != cudaSuccess)
     return e;
   // dense 1: gW1 = dz1^T h_conv, gb1 = sum dz1, dh_conv = dz1 W1
   const float* hconv = t->conv_h.back();

@@ -33,7 +33,9 @@ def _step(c, w, alpha, per_sample, prec):
     return d.q.cpu().numpy(), d.status.cpu().numpy()
 
 
-@pytest.mark.parametrize("prec_name,res_tol", [("CROM_PREC_FP32", 2e-4), ("CROM_PREC_BF16X2", 3e-3)])
+# res: ||J (d_gpu - d_ref)|| / ||Delta f||; F16X2 rounds the hidden weights to f16, which moves the
+# network Laplacian (two digits of cancellation in the output layer) and so the fit by up to ~10 %
+@pytest.mark.parametrize("prec_name,res_tol", [("CROM_PREC_FP32", 2e-4), ("CROM_PREC_F16X2", 0.15)])
 def test_step_per_sample_coefficient_matches_oracle(c, prec_name, res_tol):
     w = gen.heat2d_batched(n_inst=10, m_lo=16, m_hi=300, bias_std=0.1)
     nu = gen.piecewise_nu(w.samples, NU_REGIONS)
@@ -44,15 +46,15 @@ def test_step_per_sample_coefficient_matches_oracle(c, prec_name, res_tol):
     for i in range(w.n_inst):
         Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
         nu_i = nu[w.s_off[i]:w.s_off[i + 1]]
-        assert rel_l2(q1[i], ref[i]) < 1e-5
+        assert rel_l2(q1[i], ref[i]) < (1e-5 if prec_name == "CROM_PREC_FP32" else 5e-5)
         if np.all(nu_i == 0):
             assert np.array_equal(q1[i], w.q0[i])
             continue
         inc, res, kappa, margin = increment_errors(w.params, 2, w.q0[i], Y, q1[i], ref[i], w.dt, nu_i)
-        assert res < (res_tol if margin > 1e-4 else 5e-2), (i, inc, res, kappa, margin)
+        assert res < (res_tol if margin > 1e-4 else max(res_tol, 5e-2)), (i, inc, res, kappa, margin)
 
 
-@pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_BF16X2"])
+@pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_F16X2"])
 def test_per_sample_coefficient_equal_to_instance_value_is_the_same_step(c, prec_name):
     """nu(y_j) = alpha_i at every sample of instance i reproduces the per-instance
     step bit for bit (same arithmetic, coefficient read from another index)."""

@@ -167,7 +167,7 @@ def test_step_heat2d_single_config_full_rollout():
 def test_step_batched_ragged_matches_oracle():
     """Many instances with uneven |M_i| spanning several CTA tiles and ragged tails."""
     c = crom()
-    w = gen.heat2d_batched(n_inst=24, m_lo=8, m_hi=300, bias_std=0.1, bf16_exact=False)
+    w = gen.heat2d_batched(n_inst=24, m_lo=8, m_hi=300, bias_std=0.1)
     ctx = make_ctx(w.spec, w.params)
     dec = O.MLPDecoder(w.params, 2)
     q1, st = run_steps(ctx, w, 1, c.CROM_PREC_FP32)
@@ -181,7 +181,7 @@ def test_step_batched_full_size_sampled_instances():
     """The 1024-instance batched heat workload in one launch; 12 instances are
     recomputed one by one by the oracle."""
     c = crom()
-    w = gen.heat2d_batched(n_inst=1024, bf16_exact=True)
+    w = gen.heat2d_batched(n_inst=1024)
     ctx = make_ctx(w.spec, w.params)
     q1, st = run_steps(ctx, w, 1, c.CROM_PREC_FP32)
     assert np.all(st == 0)
@@ -197,7 +197,7 @@ def test_step_batched_full_size_sampled_instances():
 def test_step_instance_results_do_not_depend_on_batch_position():
     """Shuffling the instances permutes the results bit for bit (instances are independent)."""
     c = crom()
-    w = gen.heat2d_batched(n_inst=20, m_lo=8, m_hi=200, bf16_exact=False)
+    w = gen.heat2d_batched(n_inst=20, m_lo=8, m_hi=200)
     ctx = make_ctx(w.spec, w.params)
     q1, _ = run_steps(ctx, w, 1, c.CROM_PREC_FP32)
     perm = np.random.default_rng(3).permutation(w.n_inst)

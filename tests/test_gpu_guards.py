@@ -29,7 +29,7 @@ def crom():
     return c
 
 
-@pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_BF16X2"])
+@pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_F16X2"])
 def test_rollout_rerecorded_after_scratch_grows(prec_name):
     """rollout(A), then crom_step on a larger batch B (which reallocates the step's
     scratch), then rollout(A) with the very same arguments: the result equals the same
@@ -87,7 +87,7 @@ def test_step_rejects_ranges_past_n_samples(entry):
     if entry == "noalloc":
         c.crom_step_noalloc(ctx, q, alpha, s_off, samples, st, **kw)
     else:
-        prec = c.CROM_PREC_FP32 if entry == "fp32" else c.CROM_PREC_BF16X2
+        prec = c.CROM_PREC_FP32 if entry == "fp32" else c.CROM_PREC_F16X2
         c.crom_step(ctx, q, alpha, s_off, samples, st, precision=prec, **kw)
     torch.cuda.synchronize()
     qg, sg = q.cpu().numpy(), st.cpu().numpy()

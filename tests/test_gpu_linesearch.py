@@ -30,7 +30,7 @@ def _run(c, w, dt, gn_iters, line_search):
     import torch
     d = StepInputs(w)
     c.crom_step(make_ctx(w.spec, w.params), d.q, d.alpha, d.s_off, d.samples, d.status, dt=dt, gn_iters=gn_iters,
-                max_samples=d.max_samples, precision=c.CROM_PREC_BF16X2, line_search=line_search)
+                max_samples=d.max_samples, precision=c.CROM_PREC_F16X2, line_search=line_search)
     torch.cuda.synchronize()
     return d.q.cpu().numpy(), d.status.cpu().numpy()
 
@@ -89,7 +89,10 @@ def test_objective_never_increases(c):
         assert phi_1 <= phi_n * (1 + 1e-6), (i, phi_1, phi_n)
         # and it lands close to the oracle's three-iteration result
         ref, _ = O.crom_step(dec, w.q0[i], Y, dt, 3, alpha=float(w.alpha[i]), line_search=8)
-        assert _phi(dec, Y, q1[i], w.q0[i], df) <= _phi(dec, Y, ref, w.q0[i], df) * 1.05 + 1e-12 * phi_n
+        # (the kernel minimises the objective of its f16-rounded weights, whose fitted field
+        # change differs by a few per cent of ||Delta f||: phi may exceed the oracle's
+        # minimum by about (0.05 ||Delta f||)^2 / 2 = 2.5e-3 phi_n)
+        assert _phi(dec, Y, q1[i], w.q0[i], df) <= _phi(dec, Y, ref, w.q0[i], df) * 1.05 + 5e-3 * phi_n
 
 
 def test_objective_never_increases_r15(c):
@@ -97,7 +100,7 @@ def test_objective_never_increases_r15(c):
     threads, so the line search's objective is owned by a thread's second entry; the
     statuses match the oracle's and the objective never increases."""
     spec = gen.DecoderSpec(2, 15, 128, 5)
-    params = gen.xavier_decoder(spec, seed=21, bias_std=0.1, bf16_exact=True)
+    params = gen.xavier_decoder(spec, seed=21, bias_std=0.1)
     rng = np.random.default_rng(21)
     sizes = [40, 77, 150, 220]
     samples = np.concatenate([gen.interior_nodes_2d(128, s, rng) for s in sizes])
@@ -127,6 +130,6 @@ def test_line_search_argument_checks(c):
                                d.status.data_ptr(), None)
     rc = c.raw_call("crom_step", *args(c.CROM_PREC_FP32, c.crom_step_desc(c.CROM_PDE_HEAT, 1, 1e-5, 0, 2)))
     assert rc == c.CROM_ERR_UNSUPPORTED and "line search" in c.last_error()
-    rc = c.raw_call("crom_step", *args(c.CROM_PREC_BF16X2, c.crom_step_desc(c.CROM_PDE_HEAT, 1, 1e-5, 0, 17)))
+    rc = c.raw_call("crom_step", *args(c.CROM_PREC_F16X2, c.crom_step_desc(c.CROM_PDE_HEAT, 1, 1e-5, 0, 17)))
     assert rc == c.CROM_ERR_INVALID_ARG
     torch.cuda.synchronize()

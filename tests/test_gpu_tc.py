@@ -1,13 +1,15 @@
-"""GPU parity of the tcgen05 tensor-core paths (BF16X2 step, BF16X2 / BF16 dense
+"""GPU parity of the tcgen05 tensor-core paths (F16X2 step, F16X2 / F16 dense
 reconstruction) against the FP64 oracle, through the C ABI.
 
-The decoders here have bf16-representable weights, so both sides evaluate the
-same model; the remaining difference is the bf16 hi/lo rounding of activation
-operands (about 2^-17 relative per element) plus FP32 accumulation.
-Tolerances: dense values rel. L2 <= 1e-4 (BF16X2) and <= 1e-2 (BF16, high part
-only).  Latent step: q_{n+1} rel. L2 <= 1e-5 and increment q_{n+1} - q_n rel. L2
-<= 5e-3 (the Laplacian channel loses two digits to cancellation and cond(J) ~ 1e3
-amplifies operand rounding); rollouts: q_T rel. L2 <= 1e-3.
+Every decoder here has general FP32 weights, the form a trained decoder has; the
+oracle evaluates exactly those weights in FP64.  The kernels carry activation
+operands as f16 hi/lo pairs (~2^-22 relative); the step rounds its hidden
+weights to f16 (2^-12 relative) and the dense reconstruction adds their f16 low
+parts (~2^-22).  Tolerances: dense values rel. L2 <= 1e-4 (F16X2) and <= 3e-3
+(F16: single f16 activations and weights).  Latent step:
+the increment q_{n+1} - q_n moves with the weight rounding (J and the network
+Laplacian change by up to ~1e-1 relative): <= 3e-2 or the least-squares
+perturbation bound; q_{n+1} <= 5e-5.  Rollouts: q_T rel. L2 <= 1e-3.
 """
 import numpy as np
 import pytest
@@ -36,12 +38,12 @@ def test_reconstruct_tc_matches_oracle(hidden, m, n_pts, n_codes):
     import torch
     c = crom()
     spec = gen.DecoderSpec(m, 8, 128, hidden)
-    params = gen.xavier_decoder(spec, seed=hidden, bias_std=0.1, bf16_exact=True)
+    params = gen.xavier_decoder(spec, seed=hidden, bias_std=0.1)
     ctx = make_ctx(spec, params)
     X = np.random.default_rng(n_pts).uniform(0, 1, size=(n_pts, m)).astype(np.float32)
     codes = np.random.default_rng(7).standard_normal((n_codes, 8))
     ref = O.reconstruct(O.MLPDecoder(params, m), codes, X)
-    for prec, tol in ((c.CROM_PREC_BF16X2, 1e-4), (c.CROM_PREC_BF16, 1e-2)):
+    for prec, tol in ((c.CROM_PREC_F16X2, 1e-4), (c.CROM_PREC_F16, 3e-3)):
         out = torch.full((n_codes, n_pts), float("nan"), dtype=torch.float32, device="cuda")
         c.crom_reconstruct(ctx, dev(codes, torch.float64), dev(X, torch.float32), out, precision=prec)
         got = out.cpu().numpy()
@@ -64,7 +66,7 @@ def test_reconstruct_tc_full_grid_sampled():
     pi[:3] = [0, X.shape[0] - 1, 1023]
     dec = O.MLPDecoder(params, 2)
     ref = np.array([dec.value(X[p:p + 1], codes[k])[0] for k, p in zip(ci, pi)])
-    for prec, tol in ((c.CROM_PREC_BF16X2, 1e-4), (c.CROM_PREC_BF16, 1e-2)):
+    for prec, tol in ((c.CROM_PREC_F16X2, 1e-4), (c.CROM_PREC_F16, 3e-3)):
         out.fill_(float("nan"))
         c.crom_reconstruct(ctx, dev(codes, torch.float64), dev(X, torch.float32), out, precision=prec)
         torch.cuda.synchronize()
@@ -81,13 +83,17 @@ def test_reconstruct_tc_rejects_unsupported_shape():
     out = torch.empty((1, 4), dtype=torch.float32, device="cuda")
     with pytest.raises(c.CromError) as e:
         c.crom_reconstruct(ctx, torch.zeros((1, 8), dtype=torch.float64, device="cuda"),
-                           torch.zeros((4, 2), dtype=torch.float32, device="cuda"), out, precision=c.CROM_PREC_BF16X2)
+                           torch.zeros((4, 2), dtype=torch.float32, device="cuda"), out, precision=c.CROM_PREC_F16X2)
     assert e.value.code == c.CROM_ERR_UNSUPPORTED
 
 
-# ||J (d_gpu - d_ref)|| / ||Delta f||: measured 3e-5 .. 7e-4 on the 1024-instance
-# workload; the bf16 hi/lo operands carry ~2^-17 relative error per element.
-RES_TOL = 3e-3
+# ||J (d_gpu - d_ref)|| / ||Delta f||: the f16 weights (2^-12 relative) move the
+# network Laplacian by up to ~1e-1 relative on these random decoders (their output
+# layer cancels about two digits of the hidden Laplacians), and the fitted field
+# change with it: 0.5 .. 12 % measured up to cond(J) ~ 1e4.
+RES_TOL = 0.15
+# the hidden weights' f16 rounding (RMS 2^-12 / sqrt(3) relative)
+EPS_W = 2.0 ** -12 / np.sqrt(3.0)
 
 
 def _check_instance(w, i, q1_i, ref_i):
@@ -96,17 +102,17 @@ def _check_instance(w, i, q1_i, ref_i):
     eps (2 + 3 kappa) and the increment error by about eps kappa (2 + kappa tan theta),
     tan theta = ||Delta f - J d|| / ||J d||: the q and residual tolerances hold up to
     kappa = 1e4 and grow linearly beyond (decoders with large r or 1D inputs reach
-    kappa ~ 1e5); the increment's is 1e-2 or that bound with eps = 1e-6 (the bf16
-    hi/lo operands carry 2^-17 relative error per element), whichever is larger."""
+    kappa ~ 1e5); the increment's is 3e-2 or that bound with eps = EPS_W (the f16
+    weight rounding), whichever is larger."""
     Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
     inc, res, kappa, margin = increment_errors(w.params, w.spec.m, w.q0[i], Y, q1_i, ref_i, w.dt, w.alpha[i])
     grow = max(1.0, kappa / 1e4)
-    assert rel_l2(q1_i, ref_i) < 1e-5 * grow, (i, rel_l2(q1_i, ref_i), kappa)
+    assert rel_l2(q1_i, ref_i) < 5e-5 * grow, (i, rel_l2(q1_i, ref_i), kappa)
     assert res < RES_TOL * grow, (i, res, kappa, margin)
     ev = O.MLPDecoder(w.params, w.spec.m)(Y, w.q0[i])
     jd = ev.gq @ (ref_i - w.q0[i])
     tan_theta = np.linalg.norm(w.dt * np.asarray(w.alpha[i], np.float64) * ev.lap - jd) / np.linalg.norm(jd)
-    assert inc < max(1e-2, 1e-6 * kappa * (2 + kappa * tan_theta)), (i, inc, kappa, tan_theta)
+    assert inc < max(3e-2, EPS_W * kappa * (2 + kappa * tan_theta)), (i, inc, kappa, tan_theta)
 
 
 def _check_step(w, q1, st):
@@ -120,9 +126,9 @@ def _check_step(w, q1, st):
 
 def test_step_tc_single_instance_heat2d():
     c = crom()
-    w = gen.heat2d_single(bf16_exact=True)
+    w = gen.heat2d_single()
     ctx = make_ctx(w.spec, w.params)
-    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_BF16X2)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_F16X2)
     _check_step(w, q1, st)
 
 
@@ -133,21 +139,21 @@ def test_step_tc_batched_ragged(gn_iters):
     w = gen.heat2d_batched(n_inst=20, m_lo=8, m_hi=300, bias_std=0.1)
     w.gn_iters = gn_iters
     ctx = make_ctx(w.spec, w.params)
-    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_BF16X2)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_F16X2)
     _check_step(w, q1, st)
 
 
 def test_step_tc_one_dimensional_decoder():
     c = crom()
     spec = gen.DecoderSpec(1, 4, 128, 4)
-    params = gen.xavier_decoder(spec, seed=2, bias_std=0.1, bf16_exact=True)
+    params = gen.xavier_decoder(spec, seed=2, bias_std=0.1)
     rng = np.random.default_rng(1)
     sizes = [16, 40, 100]
     samples = np.concatenate([gen.interior_nodes_1d(256, s, rng) for s in sizes])
     w = gen.StepWorkload("1d", spec, params, rng.standard_normal((3, 4)), np.array([1.0, 0.5, 2.0], np.float32),
                          gen.ragged_offsets(sizes), samples, 1e-5, 2, 1)
     ctx = make_ctx(spec, params)
-    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_BF16X2)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_F16X2)
     _check_step(w, q1, st)
 
 
@@ -157,7 +163,7 @@ def test_step_tc_full_size_sampled_and_matches_fp32():
     c = crom()
     w = gen.heat2d_batched(n_inst=1024)
     ctx = make_ctx(w.spec, w.params)
-    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_BF16X2)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_F16X2)
     assert np.all(st == 0)
     dec = O.MLPDecoder(w.params, 2)
     for i in np.random.default_rng(1).choice(w.n_inst, size=10, replace=False):
@@ -167,26 +173,28 @@ def test_step_tc_full_size_sampled_and_matches_fp32():
         _check_instance(w, i, q1[i], ref)
     q32, st32 = run_steps(ctx, w, 1, c.CROM_PREC_FP32)
     assert np.all(st32 == 0)
-    assert rel_l2(q1, q32) < 1e-6
+    assert rel_l2(q1, q32) < 1e-5
     inc = np.linalg.norm((q1 - w.q0) - (q32 - w.q0), axis=1) / np.linalg.norm(q32 - w.q0, axis=1)
-    assert np.median(inc) < 2e-3
+    assert np.median(inc) < 3e-2
 
 
 def test_step_tc_rollout_within_1e3():
-    """100-step rollouts of 6 instances: q_T within 1e-3 relative L2 of the oracle."""
+    """100-step rollouts of 6 instances: q_T within 1e-3 relative L2 of the oracle; the
+    increment q_T - q_0 within 3e-2 (the f16 weights perturb the latent dynamics)."""
     c = crom()
     full = gen.heat2d_batched(n_inst=64)
     w = subset(full, np.array([0, 5, 17, 33, 48, 63]))
     ctx = make_ctx(w.spec, w.params)
     steps = 100
-    qT, st = run_steps(ctx, w, steps, c.CROM_PREC_BF16X2)
+    qT, st = run_steps(ctx, w, steps, c.CROM_PREC_F16X2)
     assert np.all(st == 0)
     dec = O.MLPDecoder(w.params, 2)
     for i in range(w.n_inst):
         Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
         traj = O.crom_rollout(dec, w.q0[i], Y, w.dt, w.gn_iters, steps, alpha=float(w.alpha[i]))
-        assert rel_l2(qT[i], traj[-1]) < 1e-3
-        assert rel_l2(qT[i] - w.q0[i], traj[-1] - w.q0[i]) < 1e-2
+        e_q, e_inc = rel_l2(qT[i], traj[-1]), rel_l2(qT[i] - w.q0[i], traj[-1] - w.q0[i])
+        print(f"instance {i}: q_T {e_q:.3e}, increment {e_inc:.3e}")
+        assert e_q < 1e-3 and e_inc < 3e-2, (i, e_q, e_inc)
 
 
 def test_rollout_1000_step_graph_full_batch():
@@ -194,8 +202,8 @@ def test_rollout_1000_step_graph_full_batch():
     cached CUDA graph, bit-identical to 1000 crom_step calls; the instance with the
     smallest |M_i| and one of about a hundred samples (several tiles and a ragged
     tail) recomputed by the oracle over all 1000 steps.
-    The heat equation is dissipative, so the per-step errors (<= 2e-7 relative in q)
-    add up at most linearly: q_T within 1e-3, the increment q_T - q_0 within 1e-2."""
+    The heat equation is dissipative, so the per-step errors (<= 2e-6 relative in q)
+    add up at most linearly: q_T within 1e-3, the increment q_T - q_0 within 3e-2."""
     import torch
     c = crom()
     w = gen.heat2d_batched(n_inst=1024)
@@ -205,11 +213,11 @@ def test_rollout_1000_step_graph_full_batch():
     st = torch.full((w.n_inst,), -1, dtype=torch.int32, device="cuda")
     c.crom_rollout(ctx, q, dev(w.alpha, torch.float32), dev(w.s_off, torch.int32), dev(w.samples, torch.float32),
                    st, n_steps=steps, dt=w.dt, gn_iters=w.gn_iters, max_samples=int(w.sizes.max()),
-                   precision=c.CROM_PREC_BF16X2)
+                   precision=c.CROM_PREC_F16X2)
     torch.cuda.synchronize()
     qT, stT = q.cpu().numpy(), st.cpu().numpy()
     assert np.all(stT == 0) and np.all(np.isfinite(qT))
-    q_ref, st_ref = run_steps(ctx, w, steps, c.CROM_PREC_BF16X2)
+    q_ref, st_ref = run_steps(ctx, w, steps, c.CROM_PREC_F16X2)
     assert np.array_equal(qT, q_ref) and np.array_equal(stT, st_ref)
     dec = O.MLPDecoder(w.params, 2)
     order = np.argsort(w.sizes, kind="stable")
@@ -219,10 +227,10 @@ def test_rollout_1000_step_graph_full_batch():
         traj = O.crom_rollout(dec, w.q0[i], Y, w.dt, w.gn_iters, steps, alpha=float(w.alpha[i]))
         e_q, e_inc = rel_l2(qT[i], traj[-1]), rel_l2(qT[i] - w.q0[i], traj[-1] - w.q0[i])
         print(f"instance {i} |M|={Y.shape[0]}: q_T {e_q:.3e}, increment {e_inc:.3e}")
-        assert e_q < 1e-3 and e_inc < 1e-2, (i, e_q, e_inc)
+        assert e_q < 1e-3 and e_inc < 3e-2, (i, e_q, e_inc)
 
 
-@pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_BF16X2"])
+@pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_F16X2"])
 def test_rollout_graph_equals_repeated_steps(prec_name):
     """crom_rollout (a cached CUDA graph of n steps) gives bit-identical results to n
     crom_step calls; a second call replays the cached graph and continues."""
@@ -246,7 +254,7 @@ def test_rollout_graph_equals_repeated_steps(prec_name):
 def test_step_tc_edge_cases_status():
     c = crom()
     spec = gen.DecoderSpec(2, 4, 128, 3)
-    params = gen.xavier_decoder(spec, seed=9, bias_std=0.1, bf16_exact=True)
+    params = gen.xavier_decoder(spec, seed=9, bias_std=0.1)
     ctx = make_ctx(spec, params)
     rng = np.random.default_rng(4)
     good = rng.uniform(0, 1, size=(50, 2)).astype(np.float32)
@@ -258,7 +266,7 @@ def test_step_tc_edge_cases_status():
     q0 = rng.standard_normal((5, 4))
     alpha = np.array([1.0, 1.0, 1.0, np.nan, 1.0], np.float32)
     w = gen.StepWorkload("edge", spec, params, q0, alpha, off, samples, 1e-4, 2, 1)
-    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_BF16X2)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_F16X2)
     assert list(st) == [c.CROM_OK, c.CROM_ERR_SINGULAR, c.CROM_ERR_INVALID_ARG, c.CROM_ERR_NONFINITE,
                         c.CROM_ERR_INVALID_ARG]
     assert np.array_equal(q1[1:], q0[1:])
@@ -273,14 +281,14 @@ def test_step_tc_rejects_unsupported():
     st = torch.empty(1, dtype=torch.int32, device="cuda")
     with pytest.raises(c.CromError) as e:
         c.crom_step(ctx, q, dev(w.alpha, torch.float32), dev(w.s_off, torch.int32), dev(w.samples, torch.float32),
-                    st, dt=w.dt, gn_iters=1, max_samples=16, precision=c.CROM_PREC_BF16X2)
+                    st, dt=w.dt, gn_iters=1, max_samples=16, precision=c.CROM_PREC_F16X2)
     assert e.value.code == c.CROM_ERR_UNSUPPORTED
-    w2 = gen.heat2d_single(bf16_exact=True)
+    w2 = gen.heat2d_single()
     ctx2 = make_ctx(w2.spec, w2.params)
     with pytest.raises(c.CromError) as e:
         c.crom_step(ctx2, dev(w2.q0, torch.float64), dev(w2.alpha, torch.float32), dev(w2.s_off, torch.int32),
                     dev(w2.samples, torch.float32), st, dt=w2.dt, gn_iters=2, max_samples=0,
-                    precision=c.CROM_PREC_BF16X2)
+                    precision=c.CROM_PREC_F16X2)
     assert e.value.code == c.CROM_ERR_INVALID_ARG
 
 
@@ -290,13 +298,13 @@ def test_step_tc_large_instance(n_samples):
     workload) or 5000 (many tiles, far above the batched sizes)."""
     c = crom()
     spec = gen.DecoderSpec(2, 8, 128, 5)
-    params = gen.xavier_decoder(spec, seed=0, bias_std=0.05, bf16_exact=True)
+    params = gen.xavier_decoder(spec, seed=0, bias_std=0.05)
     rng = np.random.default_rng(2)
     Y = gen.interior_nodes_2d(128, n_samples, rng)
     w = gen.StepWorkload("big", spec, params, rng.standard_normal((1, 8)), np.ones(1, np.float32),
                          gen.ragged_offsets([n_samples]), Y, 1e-5, 2, 1)
     ctx = make_ctx(spec, params)
-    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_BF16X2)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_F16X2)
     _check_step(w, q1, st)
 
 
@@ -316,7 +324,7 @@ def test_step_tc_small_tiles_matches_oracle(gn_iters):
     assert c.crom_get_step_tiles(ctx)[:2] == (TILE_S0, TILE_S1[0])
     c.crom_set_step_tiles(ctx, TILE_S0, TILE_S1[1])
     assert c.crom_get_step_tiles(ctx)[:2] == (TILE_S0, TILE_S1[1])
-    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_BF16X2)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_F16X2)
     _check_step(w, q1, st)
     for bad in ((TILE_S0, 4), (TILE_S0, 32), (16, TILE_S1[0])):
         with pytest.raises(c.CromError):
@@ -337,7 +345,7 @@ def test_autotune_measures_both_tile_shapes_and_leaves_q():
     assert s0 == TILE_S0 and s1 in TILE_S1 and min(ms) > 0
     assert s1 == (TILE_S1[0] if ms[0] <= ms[1] else TILE_S1[1])
     assert np.array_equal(q.cpu().numpy(), w.q0)          # the trials ran on a copy
-    q1, st = run_steps(ctx, subset(w, np.arange(12)), 1, c.CROM_PREC_BF16X2)
+    q1, st = run_steps(ctx, subset(w, np.arange(12)), 1, c.CROM_PREC_F16X2)
     _check_step(subset(w, np.arange(12)), q1, st)
 
 
@@ -351,7 +359,7 @@ def test_step_tc_decoder_shapes(m, r, hidden):
     declares the system singular depends on the rounding of J itself.)"""
     c = crom()
     spec = gen.DecoderSpec(m, r, 128, hidden)
-    params = gen.xavier_decoder(spec, seed=10 * r + hidden, bias_std=0.1, bf16_exact=True)
+    params = gen.xavier_decoder(spec, seed=10 * r + hidden, bias_std=0.1)
     rng = np.random.default_rng(r + 100 * hidden)
     sizes = [max(r, 15), 16, 33, 64, 130]
     if m == 1:
@@ -362,7 +370,7 @@ def test_step_tc_decoder_shapes(m, r, hidden):
                          rng.uniform(0.5, 2.0, len(sizes)).astype(np.float32), gen.ragged_offsets(sizes), samples,
                          1e-5, 2, 1)
     ctx = make_ctx(spec, params)
-    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_BF16X2)
+    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_F16X2)
     _check_step(w, q1, st)
 
 
@@ -372,7 +380,7 @@ def test_step_tc_advection_diffusion_matches_oracle():
     import torch
     c = crom()
     spec = gen.DecoderSpec(2, 8, 128, 5)
-    params = gen.xavier_decoder(spec, seed=13, bias_std=0.1, bf16_exact=True)
+    params = gen.xavier_decoder(spec, seed=13, bias_std=0.1)
     ctx = make_ctx(spec, params)
     rng = np.random.default_rng(8)
     sizes = [40, 90, 200]
@@ -386,7 +394,7 @@ def test_step_tc_advection_diffusion_matches_oracle():
     dt = 1e-4
     c.crom_step(ctx, q, dev(nu, torch.float32), dev(off, torch.int32), dev(Y, torch.float32), st,
                 dt=dt, gn_iters=2, max_samples=200, pde=c.CROM_PDE_ADVDIFF, vel=dev(vel, torch.float32),
-                precision=c.CROM_PREC_BF16X2)
+                precision=c.CROM_PREC_F16X2)
     torch.cuda.synchronize()
     q1 = q.cpu().numpy()
     dec = O.MLPDecoder(params, 2)
@@ -397,4 +405,5 @@ def test_step_tc_advection_diffusion_matches_oracle():
         ev = dec(Y[sl], q0[i])
         df = O.advdiff_delta_f(ev, vel[sl], float(nu[i]), dt)
         res = np.linalg.norm(ev.gq @ (q1[i] - ref)) / np.linalg.norm(df)
-        assert rel_l2(q1[i], ref) < 1e-5 and res < RES_TOL, (i, res)
+        # dt = 1e-4: ten times the heat tests' increment, so ten times their q tolerance
+        assert rel_l2(q1[i], ref) < 1e-4 and res < RES_TOL, (i, rel_l2(q1[i], ref), res)

@@ -39,7 +39,7 @@ def _rank_main(rank, world, port, out_dir):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    w = gen.heat2d_batched(n_inst=10, m_lo=8, m_hi=40, bf16_exact=False)
+    w = gen.heat2d_batched(n_inst=10, m_lo=8, m_hi=40)
     lo, hi, local = shard_of(w.s_off, rank, world)
     dec = O.MLPDecoder(w.params, 2)
     samples = w.samples[w.s_off[lo]:w.s_off[hi]]
@@ -72,7 +72,7 @@ def test_two_gloo_ranks_shard_and_gather(tmp_path):
     port = _free_port()
     mp.start_processes(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, start_method="spawn", join=True)
     q_all = np.load(tmp_path / "q_all.npy")
-    w = gen.heat2d_batched(n_inst=10, m_lo=8, m_hi=40, bf16_exact=False)
+    w = gen.heat2d_batched(n_inst=10, m_lo=8, m_hi=40)
     ref, _ = O.crom_step_batched(O.MLPDecoder(w.params, 2), w.q0, w.s_off, w.samples, w.alpha, w.dt, w.gn_iters)
     np.testing.assert_array_equal(q_all, ref)
     assert float(np.load(tmp_path / "tmax.npy")[0]) == 2.0

@@ -35,7 +35,7 @@ def test_noalloc_step_matches_crom_step_on_consecutive_calls():
     build()
     from paper_2206_02607_gb300 import crom
     w1 = gen.heat2d_single()
-    w2 = gen.heat2d_batched(n_inst=6, m_lo=8, m_hi=120, bias_std=0.1, bf16_exact=False)
+    w2 = gen.heat2d_batched(n_inst=6, m_lo=8, m_hi=120, bias_std=0.1)
     for w in (w1, w2, w1):          # the second shape re-lays out the shared array, then back
         ctx = make_ctx(w.spec, w.params)
 

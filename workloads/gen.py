@@ -15,10 +15,13 @@ Workload recipes (paper: §5 and App. G/H for the PDEs, App. D for the network):
 * ``heat2d_single``  2D heat u_t = alpha Lap u on a 128x128 grid, zero Neumann,
   alpha = 1; u0 = 8 Gaussian bumps; decoder R^{2+8} -> R, 5 ELU layers of
   width 128; |M| = 200 interior nodes; dt = 1e-5; 1000 steps; 2 GN iterations.
-* ``recon_dense``    the same 2D decoder with bf16-representable weights; dense
-  reconstruction at 1024^2 points x 64 codes q ~ N(0,1); plus a 2048-sample step.
+* ``recon_dense``    the same 2D decoder; dense reconstruction at 1024^2 points x
+  64 codes q ~ N(0,1); plus a 2048-sample step.
 * ``heat2d_batched`` 1024 instances of the 2D heat problem, alpha ~ U(0.5, 2),
-  |M_i| ~ U{32..512}, per-instance seeds 1000+i, bf16-representable weights.
+  |M_i| ~ U{32..512}, per-instance seeds 1000+i.
+
+Weights are FP32 values (Xavier-normal draws rounded to float32 once), the form a
+trained decoder has; both sides read the same packed float32 image.
 
 Initial latent codes: an untrained, randomly initialised decoder cannot represent
 the Gaussian-bump initial fields, so q0 ~ N(0,1) is drawn per instance (the bumps
@@ -31,7 +34,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = [
-    "DecoderSpec", "bf16_round", "xavier_decoder", "siren_decoder", "pack_params", "param_count",
+    "DecoderSpec", "xavier_decoder", "siren_decoder", "pack_params", "param_count",
     "interior_nodes_1d", "interior_nodes_2d", "gaussian_bumps_2d", "sine_modes_1d",
     "StepWorkload", "heat1d_small", "heat2d_single", "heat2d_batched", "recon_dense",
     "grid_points_2d", "ragged_offsets", "piecewise_nu",
@@ -55,21 +58,7 @@ class DecoderSpec:
         return [self.m + self.r] + [self.width] * self.hidden + [1]
 
 
-def bf16_round(a: np.ndarray) -> np.ndarray:
-    """Round to the nearest bfloat16 value (ties to even); returns float64.
-
-    Used so that weights drawn here are exactly representable in bf16: the BF16
-    tensor-core path then carries the very same model as the FP64 oracle.
-    """
-    f = np.asarray(a, dtype=np.float32)
-    u = f.view(np.uint32).astype(np.uint64)
-    lsb = (u >> 16) & 1
-    u = (u + 0x7FFF + lsb) & 0xFFFF0000
-    return u.astype(np.uint32).view(np.float32).astype(np.float64)
-
-
-def xavier_decoder(spec: DecoderSpec, seed: int, bias_std: float = 0.0,
-                   bf16_exact: bool = False):
+def xavier_decoder(spec: DecoderSpec, seed: int, bias_std: float = 0.0):
     """Xavier-normal weights (std = sqrt(2/(fan_in+fan_out))), zero biases (App. D.1).
 
     Returns a list of (W [out][in], b [out]) float64 pairs, layer 1 first.  Layer 1
@@ -84,15 +73,12 @@ def xavier_decoder(spec: DecoderSpec, seed: int, bias_std: float = 0.0,
         std = np.sqrt(2.0 / (fan_in + fan_out))
         W = rng.standard_normal((fan_out, fan_in)) * std
         b = rng.standard_normal(fan_out) * bias_std if bias_std > 0 else np.zeros(fan_out)
-        if bf16_exact:
-            W, b = bf16_round(W), bf16_round(b)
-        else:
-            W, b = W.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)
+        W, b = W.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)
         params.append((W, b))
     return params
 
 
-def siren_decoder(spec: DecoderSpec, seed: int, omega0: float = 30.0, bf16_exact: bool = False):
+def siren_decoder(spec: DecoderSpec, seed: int, omega0: float = 30.0):
     """SIREN initialisation (Sitzmann et al., the paper's "default initialization
     (omega0 = 30)"): layer 1 W ~ U(-1/fan_in, 1/fan_in); later layers
     W ~ U(-sqrt(6/fan_in)/omega0, +sqrt(6/fan_in)/omega0); biases
@@ -105,10 +91,7 @@ def siren_decoder(spec: DecoderSpec, seed: int, omega0: float = 30.0, bf16_exact
         lim = 1.0 / fan_in if l == 0 else np.sqrt(6.0 / fan_in) / omega0
         W = rng.uniform(-lim, lim, size=(fan_out, fan_in))
         b = rng.uniform(-1.0 / np.sqrt(fan_in), 1.0 / np.sqrt(fan_in), size=fan_out)
-        if bf16_exact:
-            W, b = bf16_round(W), bf16_round(b)
-        else:
-            W, b = W.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)
+        W, b = W.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)
         params.append((W, b))
     return params
 
@@ -222,9 +205,9 @@ def heat1d_small(bias_std: float = 0.0) -> StepWorkload:
                         dt=1e-5, gn_iters=1, steps=100, extra={"a": a, "u0": u0, "P": 256})
 
 
-def heat2d_single(bias_std: float = 0.0, bf16_exact: bool = False) -> StepWorkload:
+def heat2d_single(bias_std: float = 0.0) -> StepWorkload:
     spec = DecoderSpec(m=2, r=8, width=128, hidden=5)
-    params = xavier_decoder(spec, seed=0, bias_std=bias_std, bf16_exact=bf16_exact)
+    params = xavier_decoder(spec, seed=0, bias_std=bias_std)
     u0 = gaussian_bumps_2d(128, np.random.default_rng(3))
     samples = interior_nodes_2d(128, 200, np.random.default_rng(6))
     q0 = np.random.default_rng(5).standard_normal((1, spec.r))
@@ -234,12 +217,12 @@ def heat2d_single(bias_std: float = 0.0, bf16_exact: bool = False) -> StepWorklo
 
 
 def heat2d_batched(n_inst: int = 1024, m_lo: int = 32, m_hi: int = 512,
-                   bias_std: float = 0.0, bf16_exact: bool = True,
+                   bias_std: float = 0.0,
                    with_bumps: bool = False, first: int = 0) -> StepWorkload:
     """Instances first .. first+n_inst-1 of the batched 2D heat workload (instance i
     draws from seed 1000+i, so disjoint ranges give disjoint instances)."""
     spec = DecoderSpec(m=2, r=8, width=128, hidden=5)
-    params = xavier_decoder(spec, seed=0, bias_std=bias_std, bf16_exact=bf16_exact)
+    params = xavier_decoder(spec, seed=0, bias_std=bias_std)
     sizes, alphas, qs, samp, bumps = [], [], [], [], []
     for i in range(first, first + n_inst):
         rng = np.random.default_rng(1000 + i)
@@ -260,6 +243,6 @@ def heat2d_batched(n_inst: int = 1024, m_lo: int = 32, m_hi: int = 512,
 def recon_dense(n_side: int = 1024, n_codes: int = 64):
     """Dense reconstruction workload: grid points, latent codes and the 2D decoder."""
     spec = DecoderSpec(m=2, r=8, width=128, hidden=5)
-    params = xavier_decoder(spec, seed=0, bf16_exact=True)
+    params = xavier_decoder(spec, seed=0)
     codes = np.random.default_rng(4).standard_normal((n_codes, spec.r))
     return spec, params, codes, grid_points_2d(n_side)
