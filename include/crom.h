@@ -305,13 +305,20 @@ int crom_step_noalloc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, dou
  *                              coefficient, u_t = nu(x) Lap u (paper App. G,
  *                              thermodynamics, and App. H, image diffusion): coef
  *                              holds nu at every node, [n_batch][nx][ny].
+ *  CROM_FOM_ADVDIFF2D_PERIODIC_CENTRAL
+ *                              as CROM_FOM_ADVDIFF2D_PERIODIC with the face value
+ *                              the mean of the two cells (second order, no
+ *                              numerical diffusion; forward Euler is then stable
+ *                              for (a dt / h)^2 <= 2 nu dt / h^2 and
+ *                              nu dt / h^2 <= 1/4).
  * nx >= 3, n_batch <= 65535.  The result is in u when the call's work completes. */
 typedef enum {
   CROM_FOM_HEAT1D_DIRICHLET = 0,
   CROM_FOM_HEAT2D_NEUMANN = 1,
   CROM_FOM_ADVDIFF2D_PERIODIC = 2,
   CROM_FOM_HEAT1D_DIRICHLET_FIELD = 3,
-  CROM_FOM_HEAT2D_NEUMANN_FIELD = 4
+  CROM_FOM_HEAT2D_NEUMANN_FIELD = 4,
+  CROM_FOM_ADVDIFF2D_PERIODIC_CENTRAL = 5
 } crom_fom_kind;
 
 int crom_fom_step(int kind, int n_batch, int nx, int ny, const float* coef, const float* ax, const float* ay,

@@ -362,20 +362,25 @@ def fom_heat2d_neumann_step(u, dt: float, alpha=1.0):
     return u + dt * np.asarray(alpha, np.float64) * lap
 
 
-def fom_advdiff2d_step(u, ax_face, ay_face, nu: float, dt: float):
+def fom_advdiff2d_step(u, ax_face, ay_face, nu: float, dt: float, scheme: str = "upwind"):
     """2D periodic advection-diffusion u_t + div(a u) = nu Lap u on n x n cells of
-    width h = 1/n, forward Euler.  Advection in conservative first-order upwind
-    flux form with face velocities: ax_face[i, j] lives on the face between cells
-    (i, j) and (i+1, j); ay_face[i, j] between (i, j) and (i, j+1).  Diffusion by
-    the central 5-point stencil.  For a discretely divergence-free face field this
-    equals the advective form a . grad u."""
+    width h = 1/n, forward Euler.  Advection in conservative flux form with face
+    velocities: ax_face[i, j] lives on the face between cells (i, j) and (i+1, j);
+    ay_face[i, j] between (i, j) and (i, j+1); the face value of u is the upwind
+    cell's (scheme "upwind", first order) or the mean of the two cells ("central",
+    second order).  Diffusion by the central 5-point stencil.  For a discretely
+    divergence-free face field this equals the advective form a . grad u."""
     u = np.asarray(u, np.float64)
     n = u.shape[0]
     h = 1.0 / n
     up_x = np.roll(u, -1, axis=0)
     up_y = np.roll(u, -1, axis=1)
-    Fx = np.where(ax_face > 0, ax_face * u, ax_face * up_x)
-    Fy = np.where(ay_face > 0, ay_face * u, ay_face * up_y)
+    if scheme == "central":
+        Fx = ax_face * 0.5 * (u + up_x)
+        Fy = ay_face * 0.5 * (u + up_y)
+    else:
+        Fx = np.where(ax_face > 0, ax_face * u, ax_face * up_x)
+        Fy = np.where(ay_face > 0, ay_face * u, ay_face * up_y)
     div = (Fx - np.roll(Fx, 1, axis=0) + Fy - np.roll(Fy, 1, axis=1)) / h
     lap = (np.roll(u, 1, 0) + np.roll(u, -1, 0) + np.roll(u, 1, 1) + np.roll(u, -1, 1) - 4.0 * u) / h ** 2
     return u + dt * (-div + nu * lap)

@@ -45,6 +45,7 @@ CROM_ACT_ELU = 0
 CROM_ACT_SIREN = 1
 CROM_FOM_HEAT1D_DIRICHLET_FIELD = 3
 CROM_FOM_HEAT2D_NEUMANN_FIELD = 4
+CROM_FOM_ADVDIFF2D_PERIODIC_CENTRAL = 5
 
 EXPORTED = ("crom_version", "crom_last_error", "crom_create", "crom_destroy", "crom_set_weights",
             "crom_decode", "crom_step", "crom_step_host", "crom_rollout", "crom_step_noalloc", "crom_fom_step",

@@ -678,7 +678,7 @@ int crom_step_noalloc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, dou
 
 int crom_fom_step(int kind, int n_batch, int nx, int ny, const float* coef, const float* ax, const float* ay,
                   double dt, int n_steps, float* u, float* tmp, crom_stream stream) {
-  if (kind < CROM_FOM_HEAT1D_DIRICHLET || kind > CROM_FOM_HEAT2D_NEUMANN_FIELD)
+  if (kind < CROM_FOM_HEAT1D_DIRICHLET || kind > CROM_FOM_ADVDIFF2D_PERIODIC_CENTRAL)
     return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: unknown kind");
   if (n_batch < 0 || n_batch > 65535 || n_steps < 0) return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: bad batch or step count");
   if (nx < 3) return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: nx must be >= 3");
@@ -687,7 +687,7 @@ int crom_fom_step(int kind, int n_batch, int nx, int ny, const float* coef, cons
   if (!(dt > 0.0) || !isfinite(dt)) return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: dt must be finite and > 0");
   if (n_batch == 0 || n_steps == 0) return CROM_OK;
   if (!coef || !u || !tmp || u == tmp) return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: null or aliased array");
-  if (kind == CROM_FOM_ADVDIFF2D_PERIODIC && (!ax || !ay))
+  if ((kind == CROM_FOM_ADVDIFF2D_PERIODIC || kind == CROM_FOM_ADVDIFF2D_PERIODIC_CENTRAL) && (!ax || !ay))
     return fail(CROM_ERR_INVALID_ARG, "crom_fom_step: advection needs ax and ay");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(CROM_ERR_CUDA, "crom_fom_step: no CUDA device");

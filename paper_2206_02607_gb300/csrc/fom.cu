@@ -11,10 +11,12 @@
 //      u_i += dt * nu * (u_{i-1} + u_{i+1} - 2 u_i) / dx^2, boundary nodes = 0.
 //  * heat 2D, zero Neumann: nodes (i, j)/(n-1); mirror ghost nodes
 //      u_{-1} = u_1, u_n = u_{n-2}; u += dt * alpha * Lap_h u.
-//  * advection-diffusion 2D, periodic cells of width 1/n: conservative
-//      first-order upwind fluxes with face velocities ax[i][j] (between cells
-//      (i, j) and (i+1, j)) and ay[i][j] (between (i, j) and (i, j+1)), central
-//      diffusion: u += dt * (-div(a u) + nu * Lap_h u).
+//  * advection-diffusion 2D, periodic cells of width 1/n: conservative fluxes
+//      with face velocities ax[i][j] (between cells (i, j) and (i+1, j)) and
+//      ay[i][j] (between (i, j) and (i, j+1)), central diffusion:
+//      u += dt * (-div(a u) + nu * Lap_h u).  The face value is the upwind cell's
+//      (first order; its numerical diffusion |a| h / 2 is part of the model) or
+//      the mean of the two cells (second order, central).
 //  * the heat models with a spatially varying coefficient nu(x) (App. G and H):
 //      the same stencils with nu read per node.
 // Layout: fields [n_batch][nx][ny] FP32 row-major (j fastest); face velocities
@@ -61,6 +63,7 @@ __global__ void heat2d_neumann_kernel(const float* __restrict__ u, float* __rest
   out[at] = fmaf(r_over * nu, lap, c);
 }
 
+template <bool kCentral>
 __global__ void advdiff2d_kernel(const float* __restrict__ u, float* __restrict__ out,
                                  const float* __restrict__ ax, const float* __restrict__ ay,
                                  const float* __restrict__ coef, int n, float dt, float inv_h, float inv_h2) {
@@ -79,10 +82,10 @@ __global__ void advdiff2d_kernel(const float* __restrict__ u, float* __restrict_
   const float ujm = ub[(size_t)i * n + jm], ujp = ub[(size_t)i * n + jp];
   const float a_r = axb[(size_t)i * n + j], a_l = axb[(size_t)im * n + j];
   const float b_r = ayb[(size_t)i * n + j], b_l = ayb[(size_t)i * n + jm];
-  const float fr = a_r * (a_r > 0.f ? c : uip);    // flux through the face (i+1/2, j)
-  const float fl = a_l * (a_l > 0.f ? uim : c);    // flux through the face (i-1/2, j)
-  const float gr = b_r * (b_r > 0.f ? c : ujp);
-  const float gl = b_l * (b_l > 0.f ? ujm : c);
+  const float fr = face_flux<kCentral>(a_r, c, uip);    // flux through the face (i+1/2, j)
+  const float fl = face_flux<kCentral>(a_l, uim, c);    // flux through the face (i-1/2, j)
+  const float gr = face_flux<kCentral>(b_r, c, ujp);
+  const float gl = face_flux<kCentral>(b_l, ujm, c);
   const float div = (fr - fl + gr - gl) * inv_h;
   const float lap = (uim + uip + ujm + ujp - 4.f * c) * inv_h2;
   out[base + (size_t)i * n + j] = fmaf(dt, fmaf(coef[b], lap, -div), c);
@@ -95,6 +98,7 @@ __global__ void advdiff2d_kernel(const float* __restrict__ u, float* __restrict_
 // per strip (plus two halo rows), so the kernel streams 16 B per node-step.
 // Requires n % 32 == 0 and n % (kRows * kWarps) == 0.
 constexpr int kRows = 32, kWarps = 4;
+template <bool kCentral>
 __global__ void __launch_bounds__(32 * kWarps) advdiff2d_march_kernel(
     const float* __restrict__ u, float* __restrict__ out, const float* __restrict__ ax,
     const float* __restrict__ ay, const float* __restrict__ coef, int n, float dt, float inv_h, float inv_h2) {
@@ -132,10 +136,10 @@ __global__ void __launch_bounds__(32 * kWarps) advdiff2d_march_kernel(
       b_l = halo_b;
     }
     if (lane == 31) ujp = halo_u;
-    const float fr = a_r * (a_r > 0.f ? c : uip);
-    const float fl = a_l * (a_l > 0.f ? uim : c);
-    const float gr = b_r * (b_r > 0.f ? c : ujp);
-    const float gl = b_l * (b_l > 0.f ? ujm : c);
+    const float fr = face_flux<kCentral>(a_r, c, uip);
+    const float fl = face_flux<kCentral>(a_l, uim, c);
+    const float gr = face_flux<kCentral>(b_r, c, ujp);
+    const float gl = face_flux<kCentral>(b_l, ujm, c);
     const float div = (fr - fl + gr - gl) * inv_h;
     const float lap = (uim + uip + ujm + ujp - 4.f * c) * inv_h2;
     ob[(size_t)i * n + j] = fmaf(dt, fmaf(nu, lap, -div), c);
@@ -158,8 +162,13 @@ constexpr int kWarps4 = 4;
 // (advection-diffusion / heat).
 constexpr int kRowsAdv = 2, kRowsHeat = 4;
 inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
-__device__ __forceinline__ float upwind(float a, float up, float down) { return a * (a > 0.f ? up : down); }
-template <int kRowsA>
+// Flux a * u_face through a face between the cells `left` and `right` (a > 0 moves
+// from left to right): upwind takes the upstream cell, central the mean of the two.
+template <bool kCentral>
+__device__ __forceinline__ float face_flux(float a, float left, float right) {
+  return kCentral ? a * (0.5f * (left + right)) : a * (a > 0.f ? left : right);
+}
+template <int kRowsA, bool kCentral>
 __global__ void __launch_bounds__(32 * kWarps4) advdiff2d_march4_kernel(
     const float* __restrict__ u, float* __restrict__ out, const float* __restrict__ ax,
     const float* __restrict__ ay, const float* __restrict__ coef, int n, float dt, float inv_h, float inv_h2) {
@@ -211,8 +220,9 @@ __global__ void __launch_bounds__(32 * kWarps4) advdiff2d_march4_kernel(
     float o[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float div = (upwind(ar[q], cv[q], up[q]) - upwind(al[q], um[q], cv[q]) + upwind(br[q], cv[q], jp[q]) -
-                         upwind(bl[q], jm[q], cv[q])) * inv_h;
+      const float div = (face_flux<kCentral>(ar[q], cv[q], up[q]) - face_flux<kCentral>(al[q], um[q], cv[q]) +
+                         face_flux<kCentral>(br[q], cv[q], jp[q]) - face_flux<kCentral>(bl[q], jm[q], cv[q])) *
+                        inv_h;
       const float lap = (um[q] + up[q] + jm[q] + jp[q] - 4.f * cv[q]) * inv_h2;
       o[q] = fmaf(dt, fmaf(nu, lap, -div), cv[q]);
     }
@@ -315,19 +325,29 @@ cudaError_t launch_fom(int kind, int n_batch, int nx, int ny, const float* coef,
       }
     } else {
       const double h = 1.0 / nx;
+      const bool central = kind == CROM_FOM_ADVDIFF2D_PERIODIC_CENTRAL;
+      const float fdt = (float)dt, ih = (float)(1.0 / h), ih2 = (float)(1.0 / (h * h));
       if (nx % 128 == 0 && nx % (kRowsAdv * kWarps4) == 0 && aligned16(src) && aligned16(dst) && aligned16(ax) &&
           aligned16(ay)) {
         dim3 grid(nx / 128, nx / (kRowsAdv * kWarps4), n_batch);
-        advdiff2d_march4_kernel<kRowsAdv><<<grid, dim3(32, kWarps4), 0, s>>>(src, dst, ax, ay, coef, nx, (float)dt,
-                                                                       (float)(1.0 / h), (float)(1.0 / (h * h)));
+        if (central)
+          advdiff2d_march4_kernel<kRowsAdv, true><<<grid, dim3(32, kWarps4), 0, s>>>(src, dst, ax, ay, coef, nx, fdt,
+                                                                                   ih, ih2);
+        else
+          advdiff2d_march4_kernel<kRowsAdv, false><<<grid, dim3(32, kWarps4), 0, s>>>(src, dst, ax, ay, coef, nx, fdt,
+                                                                                    ih, ih2);
       } else if (nx % 32 == 0 && nx % (kRows * kWarps) == 0) {
         dim3 grid(nx / 32, nx / (kRows * kWarps), n_batch);
-        advdiff2d_march_kernel<<<grid, dim3(32, kWarps), 0, s>>>(src, dst, ax, ay, coef, nx, (float)dt,
-                                                                 (float)(1.0 / h), (float)(1.0 / (h * h)));
+        if (central)
+          advdiff2d_march_kernel<true><<<grid, dim3(32, kWarps), 0, s>>>(src, dst, ax, ay, coef, nx, fdt, ih, ih2);
+        else
+          advdiff2d_march_kernel<false><<<grid, dim3(32, kWarps), 0, s>>>(src, dst, ax, ay, coef, nx, fdt, ih, ih2);
       } else {
         dim3 grid((nx + 31) / 32, (nx + 7) / 8, n_batch);
-        advdiff2d_kernel<<<grid, dim3(32, 8), 0, s>>>(src, dst, ax, ay, coef, nx, (float)dt, (float)(1.0 / h),
-                                                      (float)(1.0 / (h * h)));
+        if (central)
+          advdiff2d_kernel<true><<<grid, dim3(32, 8), 0, s>>>(src, dst, ax, ay, coef, nx, fdt, ih, ih2);
+        else
+          advdiff2d_kernel<false><<<grid, dim3(32, 8), 0, s>>>(src, dst, ax, ay, coef, nx, fdt, ih, ih2);
       }
     }
     cudaError_t e = cudaGetLastError();

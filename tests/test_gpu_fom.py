@@ -127,6 +127,31 @@ def test_advdiff_matches_oracle_conserves_mass_and_translates(c, n):
     np.testing.assert_allclose(got[1], np.roll(u2[1], -1, axis=1), rtol=0, atol=1e-6)
 
 
+
+@pytest.mark.parametrize("n", [96, 128, 256])
+def test_advdiff_central_matches_oracle_and_conserves_mass(c, n):
+    """The second-order (central-flux) advection-diffusion model against the oracle's
+    central scheme; dt within both forward-Euler limits, (a dt/h)^2 <= 2 nu dt/h^2
+    and nu dt/h^2 <= 1/4, so FP32 and FP64 stay together over the steps."""
+    h = 1 / n
+    rng = np.random.default_rng(19)
+    ax, ay = _faces(n, rng, 2)
+    ax, ay = ax.astype(np.float32), ay.astype(np.float32)
+    u0 = rng.uniform(0, 1, size=(2, n, n))
+    nu = np.array([2e-3, 5e-3])
+    amax = max(np.abs(ax).max(), np.abs(ay).max())
+    dt = 0.5 * min(2 * nu.min() / amax ** 2, h * h / (4 * nu.max()))
+    got = run(c, c.CROM_FOM_ADVDIFF2D_PERIODIC_CENTRAL, u0, nu, dt, 30, ax, ay)
+    for b in range(2):
+        ref = u0[b].astype(np.float32).astype(np.float64)
+        for _ in range(30):
+            ref = O.fom_advdiff2d_step(ref, ax[b].astype(np.float64), ay[b].astype(np.float64), nu[b], dt,
+                                       scheme="central")
+        assert rel_l2(got[b], ref) < 1e-5
+        m0 = u0[b].astype(np.float32).astype(np.float64).sum()
+        assert abs(got[b].sum() - m0) < 1e-5 * m0
+
+
 def test_fom_rejects_bad_arguments(c):
     import torch
     u = torch.zeros((1, 8, 8), device="cuda")
@@ -141,7 +166,7 @@ def test_fom_rejects_bad_arguments(c):
                         dt=1e-3, n_steps=1)
 
 
-@pytest.mark.parametrize("kind", ["heat", "heat_field", "advdiff"])
+@pytest.mark.parametrize("kind", ["heat", "heat_field", "advdiff", "advdiff_central"])
 def test_marching_kernels_match_unaligned_fallback(c, kind):
     """Sides that are multiples of 128 with 16-byte aligned arrays take the
     four-columns-per-lane marching kernels; the same fields placed one float off
@@ -152,12 +177,12 @@ def test_marching_kernels_match_unaligned_fallback(c, kind):
     rng = np.random.default_rng(12)
     u0 = rng.uniform(size=(nb, n, n)).astype(np.float32)
     h = 1 / (n - 1)
-    if kind == "advdiff":
+    if kind.startswith("advdiff"):
         ax, ay = _faces(n, rng, nb)
         ax, ay = ax.astype(np.float32), ay.astype(np.float32)
         coef = np.array([1e-3, 5e-3, 2e-3], np.float32)
         dt = 0.2 * min((1 / n) / max(np.abs(ax).max(), np.abs(ay).max()), (1 / n) ** 2 / (4 * 5e-3))
-        k = c.CROM_FOM_ADVDIFF2D_PERIODIC
+        k = c.CROM_FOM_ADVDIFF2D_PERIODIC if kind == "advdiff" else c.CROM_FOM_ADVDIFF2D_PERIODIC_CENTRAL
     else:
         ax = ay = None
         coef = (rng.uniform(0.2, 1.0, size=(nb, n, n)) if kind == "heat_field" else np.array([1.0, 0.5, 2.0]))

@@ -1,0 +1,164 @@
+"""The learned-model workload end to end on the GPU (paper §3 manifold construction,
+§4 latent dynamics, App. C.1 encoder initial guess, App. I advection with forward
+Euler): the GPU full-order solver generates the snapshots, the strided-conv encoder
+and the r = 16, width-256 decoder are trained on them with the bf16 tensor-core
+training pass, and held-out diffusivities are rolled out in latent space and
+reconstructed on the full grid.
+
+Workload (workloads.gen.advdiff_learned): periodic 2D advection-diffusion on 256^2
+cells, one divergence-free velocity field from a random Fourier stream function
+(max face speed 1), one initial field of 8 periodic Gaussian bumps, 64 trajectories
+with nu ~ U(1e-3, 1e-2), dt = 2.5e-4, 2000 forward-Euler steps with a snapshot every
+10 (200 per trajectory); 56 trajectories train, the last 8 are held out.  The
+full-order model is the second-order (central-flux) scheme: first-order upwinding
+would add a numerical diffusion |a| h / 2 ~ 2e-3, above the smallest nu, which the
+latent dynamics (exact derivatives of the decoder) does not have.
+
+Decoders: the configured R^{2+16} -> R with five ELU layers of width 256 (rolled
+out with the FP32 step: its hidden matrices, 512 KB in 16 bits, do not fit the
+shared memory that the tensor-core step keeps them in), and R^{2+15} -> R of width
+128 (the tensor-core step's shape), each trained on the same snapshots.
+
+Latent dynamics: Delta f_j = dt (-a(y_j) . grad g + nu Lap g) at 1024 cell centres,
+in the decoder's standardised coordinates x' = (x - 1/2) / s (velocity a / s,
+diffusivity nu / s^2), the FOM's dt, 2 Gauss-Newton iterations; all 8 held-out
+trajectories advance together as 8 instances of one batched step.
+
+Bar: relative L2 of the reconstructed final field against the FOM's final field,
+for the FP32 and the F16X2 step."""
+import numpy as np
+import pytest
+
+from workloads import gen
+
+from helpers import dev, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+N_SAMPLES = 1024
+TRAIN_STEPS = 30000
+ROLLOUT_BAR = 1e-2
+
+
+@pytest.fixture(scope="module")
+def c():
+    from paper_2206_02607_gb300 import build
+    build()
+    from paper_2206_02607_gb300 import crom
+    return crom
+
+
+@pytest.fixture(scope="module")
+def trajectories(c):
+    """Full-order trajectories [64][201][256^2] on the device and their statistics."""
+    import torch
+    w = gen.advdiff_learned()
+    nt = len(w.nu)
+    u = dev(np.repeat(w.u0[None], nt, axis=0), torch.float32)
+    tmp = torch.empty_like(u)
+    ax = dev(np.repeat(w.ax[None], nt, axis=0), torch.float32)
+    ay = dev(np.repeat(w.ay[None], nt, axis=0), torch.float32)
+    nu = dev(w.nu, torch.float32)
+    snaps = [u.reshape(nt, -1).clone()]
+    for _ in range(w.steps // w.every):
+        c.crom_fom_step(c.CROM_FOM_ADVDIFF2D_PERIODIC_CENTRAL, u, tmp, nu, dt=w.dt, n_steps=w.every, ax=ax, ay=ay)
+        snaps.append(u.reshape(nt, -1).clone())
+    return w, torch.stack(snaps, dim=1)
+
+
+SHAPES = {"w256_r16": (256, 16), "w128_r15": (128, 15)}
+
+
+@pytest.fixture(scope="module", params=list(SHAPES))
+def learned(c, trajectories, request):
+    import torch
+    from oracle import train_oracle as T
+    w, traj = trajectories
+    n, P = w.n, w.n * w.n
+    train = traj[:w.n_train].reshape(-1, P)
+    mu, sigma = float(train.mean()), float(train.std())
+    train = ((train - mu) / sigma).contiguous()
+    # ---- training (standardised fields and coordinates, App. D)
+    X = gen.cell_centers_2d(n)
+    s = float(X[:, 0].std())
+    Xs = ((X - 0.5) / s).astype(np.float32)
+    width, r = SHAPES[request.param]
+    hidden, B, S = 5, 64, 4096
+    spec = gen.DecoderSpec(2, r, width, hidden)
+    tr = c.CromTrainer(2, r, width, hidden, P, B, S)
+    tr.set_precision(c.CROM_PREC_BF16_MIXED)
+    rng = np.random.default_rng(7)
+    lens = T.conv_lengths(P)
+    enc = {"conv": [(rng.standard_normal(6) * np.sqrt(2.0 / 6), 0.0) for _ in lens[1:]],
+           "dense": [(rng.standard_normal((32, lens[-1])) * np.sqrt(2.0 / (lens[-1] + 32)), np.zeros(32)),
+                     (rng.standard_normal((r, 32)) * np.sqrt(2.0 / (32 + r)), np.zeros(r))]}
+    dec = gen.xavier_decoder(spec, seed=11)
+    tr.set_params(T.flatten(enc, dec).astype(np.float32))
+    coords = dev(Xs, torch.float32)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    losses = []
+    for k in range(TRAIN_STEPS):
+        lr = 1e-3 if k < TRAIN_STEPS // 4 else 1e-3 * (2e-5 / 1e-3) ** ((k - TRAIN_STEPS // 4) /
+                                                                      (TRAIN_STEPS - TRAIN_STEPS // 4 - 1))
+        pick = torch.randint(0, train.shape[0], (B,), device="cuda", generator=g)
+        pts = torch.randint(0, P, (B, S), device="cuda", generator=g, dtype=torch.int32)
+        c.crom_train_step(tr, train[pick].contiguous(), pts, coords, lr, loss)
+        if k % 5000 == 0 or k == TRAIN_STEPS - 1:
+            losses.append(loss.item())
+    torch.cuda.synchronize()
+    params = tr.get_params()
+    held = traj[w.n_train:]                                             # [8][201][P]
+    q0 = torch.empty((held.shape[0], r), dtype=torch.float32, device="cuda")
+    c.crom_encode(tr, ((held[:, 0] - mu) / sigma).contiguous(), q0)
+    torch.cuda.synchronize()
+    print(f"training losses ({request.param}, standardised fields): {['%.2e' % v for v in losses]}")
+    tr.close()
+    return dict(w=w, spec=spec, params=params[:gen.param_count(spec)], q0=q0.cpu().numpy().astype(np.float64),
+                held=held.cpu().numpy().astype(np.float64), mu=mu, sigma=sigma, Xs=Xs, s=s, shape=request.param)
+
+
+@pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_F16X2"])
+def test_learned_advdiff_rollout_matches_full_order_solver(c, learned, prec_name):
+    import torch
+    L = learned
+    if prec_name == "CROM_PREC_F16X2" and L["shape"] != "w128_r15":
+        pytest.skip("the tensor-core step is built for width 128, r <= 15")
+    w, spec, mu, sigma, s = L["w"], L["spec"], L["mu"], L["sigma"], L["s"]
+    n, P = w.n, w.n * w.n
+    held, nh = L["held"], L["held"].shape[0]
+    ctx = c.crom_create(spec.m, spec.r, spec.width, spec.hidden)
+    c.crom_set_weights(ctx, L["params"])
+    Xd = dev(L["Xs"], torch.float32)
+    out = torch.empty((nh, P), dtype=torch.float32, device="cuda")
+
+    recon_prec = c.CROM_PREC_F16X2 if spec.width == 128 else c.CROM_PREC_FP32
+
+    def fields(q):
+        c.crom_reconstruct(ctx, q, Xd, out, precision=recon_prec)
+        torch.cuda.synchronize()
+        return out.cpu().numpy().astype(np.float64) * sigma + mu
+
+    q = dev(L["q0"], torch.float64)
+    fit0 = max(rel_l2(f, h[0]) for f, h in zip(fields(q), held))
+    # the same 1024 cell centres for every held-out trajectory; velocity and
+    # diffusivity in the decoder's coordinates
+    cells = np.random.default_rng(9).choice(P, size=N_SAMPLES, replace=False)
+    vel = gen.cell_velocity(w.ax, w.ay)[cells] / s
+    samples = np.tile(L["Xs"][cells], (nh, 1))
+    nu_eff = (w.nu[w.n_train:] / s ** 2).astype(np.float32)
+    status = torch.zeros(nh, dtype=torch.int32, device="cuda")
+    c.crom_rollout(ctx, q, dev(nu_eff, torch.float32), dev(np.arange(nh + 1, dtype=np.int32) * N_SAMPLES, torch.int32),
+                   dev(samples, torch.float32), status, n_steps=w.steps, dt=w.dt, gn_iters=2, max_samples=N_SAMPLES,
+                   pde=c.CROM_PDE_ADVDIFF, vel=dev(np.tile(vel, (nh, 1)), torch.float32),
+                   precision=getattr(c, prec_name))
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    final = fields(q)
+    errs = [rel_l2(f, h[-1]) for f, h in zip(final, held)]
+    moved = [rel_l2(h[-1], h[0]) for h in held]
+    print(f"learned advection-diffusion rollout ({L['shape']}, {prec_name}): encoder fit of u0 {fit0:.3e}, final-field errors "
+          f"{['%.2e' % e for e in errs]} (the fields change by {min(moved):.2e} .. {max(moved):.2e})")
+    assert max(errs) < ROLLOUT_BAR, errs
+    ctx.close()

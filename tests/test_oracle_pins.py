@@ -528,6 +528,33 @@ def test_step_per_sample_coefficient_sine_decoder():
 
 
 
+
+def test_fom_advdiff_central_fourier_multiplier():
+    """Central fluxes under a uniform velocity: the real Fourier mode
+    cos(th_x i + th_y j + phi) is an eigenvector of one step with the complex
+    multiplier mu = 1 - dt [i (a_x sin th_x + a_y sin th_y) / h
+    + 4 nu (sin^2(th_x / 2) + sin^2(th_y / 2)) / h^2]; after s steps the mode is
+    |mu|^s cos(. + s arg mu).  Upwinding, a dropped term or a sign flip fails it."""
+    n, ax, ay, nu, dt, steps = 32, 0.7, -0.4, 2e-3, 2e-3, 25
+    h = 1.0 / n
+    kx, ky, phi = 3, 5, 0.3
+    tx, ty = 2 * np.pi * kx / n, 2 * np.pi * ky / n
+    I, J = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    u = np.cos(tx * I + ty * J + phi)
+    axf, ayf = np.full((n, n), ax), np.full((n, n), ay)
+    for _ in range(steps):
+        u = O.fom_advdiff2d_step(u, axf, ayf, nu, dt, scheme="central")
+    mu = 1 - dt * (1j * (ax * np.sin(tx) + ay * np.sin(ty)) / h
+                   + 4 * nu * (np.sin(tx / 2) ** 2 + np.sin(ty / 2) ** 2) / h ** 2)
+    ref = np.abs(mu) ** steps * np.cos(tx * I + ty * J + phi + steps * np.angle(mu))
+    assert np.max(np.abs(u - ref)) < 1e-12
+    # the upwind scheme damps the same mode more (its numerical diffusion)
+    v = np.cos(tx * I + ty * J + phi)
+    for _ in range(steps):
+        v = O.fom_advdiff2d_step(v, axf, ayf, nu, dt)
+    assert np.linalg.norm(v) < np.linalg.norm(u) * 0.99
+
+
 @pytest.mark.parametrize("per_sample", [False, True])
 def test_step_batched_closed_form_per_instance(per_sample):
     """crom_step_batched against the sine decoder's least-squares closed form, one

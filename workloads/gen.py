@@ -19,6 +19,11 @@ Workload recipes (paper: §5 and App. G/H for the PDEs, App. D for the network):
   64 codes q ~ N(0,1); plus a 2048-sample step.
 * ``heat2d_batched`` 1024 instances of the 2D heat problem, alpha ~ U(0.5, 2),
   |M_i| ~ U{32..512}, per-instance seeds 1000+i.
+* ``advdiff_learned`` the learned-model workload: periodic 2D advection-diffusion
+  on 256^2 cells, one velocity field from a random Fourier stream function
+  (max |face velocity| = 1), one initial field of 8 periodic Gaussian bumps, 64
+  trajectories with nu ~ U(1e-3, 1e-2), dt = 2.5e-4, 2000 steps, a snapshot every
+  10 (56 trajectories for training, 8 held out).
 
 Weights are FP32 values (Xavier-normal draws rounded to float32 once), the form a
 trained decoder has; both sides read the same packed float32 image.
@@ -38,6 +43,8 @@ __all__ = [
     "interior_nodes_1d", "interior_nodes_2d", "gaussian_bumps_2d", "sine_modes_1d",
     "StepWorkload", "heat1d_small", "heat2d_single", "heat2d_batched", "recon_dense",
     "grid_points_2d", "ragged_offsets", "piecewise_nu",
+    "cell_centers_2d", "periodic_bumps_2d", "stream_function_faces", "cell_velocity", "AdvDiffWorkload",
+    "advdiff_learned",
 ]
 
 
@@ -246,3 +253,83 @@ def recon_dense(n_side: int = 1024, n_codes: int = 64):
     params = xavier_decoder(spec, seed=0)
     codes = np.random.default_rng(4).standard_normal((n_codes, spec.r))
     return spec, params, codes, grid_points_2d(n_side)
+
+
+def cell_centers_2d(n: int) -> np.ndarray:
+    """Centres ((i + 1/2)/n, (j + 1/2)/n) of the n x n periodic cells of [0,1)^2,
+    row-major (i slow, j fast), float32 [n*n][2]."""
+    t = (np.arange(n) + 0.5) / n
+    X1, X2 = np.meshgrid(t, t, indexing="ij")
+    return np.stack([X1.ravel(), X2.ravel()], axis=1).astype(np.float32)
+
+
+def periodic_bumps_2d(n: int, rng, count: int = 8, sigma=(0.03, 0.1)):
+    """Sum of Gaussian bumps on the periodic unit square at the cell centres: centres
+    U[0,1)^2, sigma ~ U(sigma), amplitude ~ U(0.5, 1), distances to the nearest
+    periodic image of each centre."""
+    c = rng.uniform(0.0, 1.0, size=(count, 2))
+    s = rng.uniform(sigma[0], sigma[1], size=count)
+    a = rng.uniform(0.5, 1.0, size=count)
+    t = (np.arange(n) + 0.5) / n
+    X1, X2 = np.meshgrid(t, t, indexing="ij")
+    u = np.zeros((n, n))
+    for k in range(count):
+        d1 = (X1 - c[k, 0] + 0.5) % 1.0 - 0.5
+        d2 = (X2 - c[k, 1] + 0.5) % 1.0 - 0.5
+        u += a[k] * np.exp(-(d1 ** 2 + d2 ** 2) / (2 * s[k] ** 2))
+    return u
+
+
+def stream_function_faces(n: int, rng, modes: int = 4):
+    """Face velocities of a random periodic stream function
+    psi(x, y) = sum_{k,l=1..modes} c_kl sin(2 pi (k x + l y) + phi_kl) / (k^2 + l^2),
+    c_kl ~ N(0,1), phi_kl ~ U(0, 2 pi), sampled at the cell corners
+    C[i][j] = psi((i+1)/n, (j+1)/n).  The face between cells (i,j) and (i+1,j) gets
+    ax[i][j] = n (C[i][j] - C[i][j-1]) (the mean of u = dpsi/dy over it), the face
+    between (i,j) and (i,j+1) gets ay[i][j] = -n (C[i][j] - C[i-1][j]) (v = -dpsi/dx),
+    so every cell's net outflow cancels exactly; both are scaled so that the largest
+    face speed is 1.  Returns (ax, ay) as float32 [n][n]."""
+    k = np.arange(1, modes + 1)
+    c = rng.standard_normal((modes, modes))
+    phi = rng.uniform(0.0, 2 * np.pi, size=(modes, modes))
+    t = (np.arange(n) + 1.0) / n
+    X, Y = np.meshgrid(t, t, indexing="ij")
+    C = np.zeros((n, n))
+    for a in range(modes):
+        for b in range(modes):
+            C += c[a, b] * np.sin(2 * np.pi * (k[a] * X + k[b] * Y) + phi[a, b]) / (k[a] ** 2 + k[b] ** 2)
+    ax = n * (C - np.roll(C, 1, axis=1))
+    ay = -n * (C - np.roll(C, 1, axis=0))
+    scale = 1.0 / max(np.abs(ax).max(), np.abs(ay).max())
+    return (ax * scale).astype(np.float32), (ay * scale).astype(np.float32)
+
+
+def cell_velocity(ax, ay) -> np.ndarray:
+    """Velocity at the cell centres, the mean of each cell's two faces per direction:
+    a_x[i][j] = (ax[i][j] + ax[i-1][j]) / 2, a_y[i][j] = (ay[i][j] + ay[i][j-1]) / 2;
+    float32 [n*n][2] row-major like cell_centers_2d."""
+    vx = 0.5 * (ax + np.roll(ax, 1, axis=0))
+    vy = 0.5 * (ay + np.roll(ay, 1, axis=1))
+    return np.stack([vx.ravel(), vy.ravel()], axis=1).astype(np.float32)
+
+
+@dataclass
+class AdvDiffWorkload:
+    """Inputs of the learned-model workload (trajectories differ only in nu)."""
+    n: int
+    ax: np.ndarray      # [n][n] float32 face velocities
+    ay: np.ndarray
+    u0: np.ndarray      # [n][n] float32 initial field
+    nu: np.ndarray      # [n_traj] float32
+    dt: float
+    steps: int
+    every: int
+    n_train: int
+
+
+def advdiff_learned(n: int = 256, n_traj: int = 64, n_train: int = 56, seed: int = 40) -> AdvDiffWorkload:
+    rng = np.random.default_rng(seed)
+    ax, ay = stream_function_faces(n, rng)
+    u0 = periodic_bumps_2d(n, rng).astype(np.float32)
+    nu = rng.uniform(1e-3, 1e-2, size=n_traj).astype(np.float32)
+    return AdvDiffWorkload(n, ax, ay, u0, nu, dt=2.5e-4, steps=2000, every=10, n_train=n_train)
