@@ -27,6 +27,13 @@
 namespace crom {
 namespace {
 
+// Flux a * u_face through a face between the cells `left` and `right` (a > 0 moves
+// from left to right): upwind takes the upstream cell, central the mean of the two.
+template <bool kCentral>
+__device__ __forceinline__ float face_flux(float a, float left, float right) {
+  return kCentral ? a * (0.5f * (left + right)) : a * (a > 0.f ? left : right);
+}
+
 template <bool kField>
 __global__ void heat1d_kernel(const float* __restrict__ u, float* __restrict__ out, const float* __restrict__ coef,
                               int P, float r_over) {
@@ -162,12 +169,6 @@ constexpr int kWarps4 = 4;
 // (advection-diffusion / heat).
 constexpr int kRowsAdv = 2, kRowsHeat = 4;
 inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
-// Flux a * u_face through a face between the cells `left` and `right` (a > 0 moves
-// from left to right): upwind takes the upstream cell, central the mean of the two.
-template <bool kCentral>
-__device__ __forceinline__ float face_flux(float a, float left, float right) {
-  return kCentral ? a * (0.5f * (left + right)) : a * (a > 0.f ? left : right);
-}
 template <int kRowsA, bool kCentral>
 __global__ void __launch_bounds__(32 * kWarps4) advdiff2d_march4_kernel(
     const float* __restrict__ u, float* __restrict__ out, const float* __restrict__ ax,
