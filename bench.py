@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--tiles", default="auto",
                     help="sample tiles of the tensor-core step: auto (measured by crom_autotune) or s0,s1 "
                          "(fixed; profilers distort the autotuner's timings)")
-    ap.add_argument("--only", default=None, choices=["step", "recon", "plain", "fom", "heat"],
+    ap.add_argument("--only", default=None, choices=["step", "recon", "plain", "fom", "heat", "train"],
                     help="run only one part (warmup + steps launches) for profiling; prints a short JSON line")
     return ap.parse_args()
 
@@ -84,6 +84,23 @@ def run_only(args):
         torch.cuda.synchronize()
         print(json.dumps({"only": args.only, "instances": w.n_inst, "calls": n,
                           "status_all_ok": bool((st.cpu().numpy() == 0).all())}))
+    elif args.only == "train":
+        # the learned-model training step (64 snapshots x 4096 points, width 256), bf16 tensor-core pass
+        Bt, St, nt_side, rt, wt, Lt = 64, 4096, 256, 16, 256, 5
+        rng = np.random.default_rng(0)
+        tr = crom.CromTrainer(2, rt, wt, Lt, nt_side * nt_side, Bt, St, 0)
+        tr.set_precision(crom.CROM_PREC_BF16_MIXED)
+        tr.set_params((rng.standard_normal(tr.n_params) * 0.05).astype(np.float32))
+        snaps_t = torch.tensor(rng.standard_normal((Bt, nt_side * nt_side)).astype(np.float32), device="cuda")
+        idx_t = torch.tensor(rng.integers(0, nt_side * nt_side, size=(Bt, St)).astype(np.int32), device="cuda")
+        coords_t = torch.tensor(gen.grid_points_2d(nt_side), device="cuda")
+        loss_t = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(n):
+            crom.crom_train_step(tr, snaps_t, idx_t, coords_t, 1e-4, loss_t)
+        torch.cuda.synchronize()
+        print(json.dumps({"only": "train", "steps": n, "loss": float(loss_t.item())}))
+        tr.close()
+        return
     elif args.only == "fom":
         nb, nn = args.fom_fields, 256
         rng = np.random.default_rng(0)

@@ -112,6 +112,7 @@ struct TrainerTc {
   std::vector<uint16_t*> H; // bf16 activations of the hidden layers, [B*S][w] each
   uint16_t *d0 = nullptr, *d1 = nullptr;  // bf16 deltas [B*S][w]
   float *colpart = nullptr, *colpart2 = nullptr, *rowpart = nullptr;  // epilogue partial sums
+  float* colmid = nullptr;  // first level of the column-sum reduction
   float* split = nullptr;   // split-K partials of the weight gradients
   float* din = nullptr;     // [B*S][64]: delta_0 W_0 (input gradient), FP32
   float* gw0part = nullptr; // row-chunk partials of dW_0

@@ -28,7 +28,7 @@ namespace crom {
 namespace {
 
 constexpr int kSplitsW = 64;      // K splits of the weight-gradient GEMMs
-constexpr int kGw0Chunks = 256;   // row chunks of the input-layer weight gradient
+constexpr int kGw0Chunks = 1024;  // row chunks of the input-layer weight gradient
 constexpr int kDinCols = 64;      // din = delta[0] W_0 padded to 64 columns
 
 inline unsigned nblk(long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -112,6 +112,27 @@ __global__ void sum_parts_kernel(const float* part, int nparts, long stride, lon
   out[e] = (float)s;
 }
 
+// Column sums of part [nparts][cols] in a fixed order, first level: block (x, y)
+// adds parts y * kColPer .. of columns 32 x .. (32 columns x 8 part lanes, the lanes
+// combined in order) into mid[y][col].  The second level adds mid's rows in order
+// (sum_parts_kernel).
+constexpr int kColPer = 128;
+__global__ void colsum_level1_kernel(const float* part, int nparts, int cols, float* mid) {
+  __shared__ double red[8][32];
+  const int col = blockIdx.x * 32 + threadIdx.x;
+  const int p0 = blockIdx.y * kColPer, p1 = min(nparts, p0 + kColPer);
+  double acc = 0.0;
+  if (col < cols)
+    for (int p = p0 + threadIdx.y; p < p1; p += 8) acc += part[(long)p * cols + col];
+  red[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && col < cols) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += red[k][threadIdx.x];
+    mid[(long)blockIdx.y * cols + col] = (float)t;
+  }
+}
+
 // loss = sum_p rowpart[p][0] * inv_count; gb_out = sum_p rowpart[p][1] (in order).
 __global__ void loss_parts_kernel(const float* rowpart, int nparts, double inv_count, double* loss, float* gbout) {
   __shared__ double red[2][256];
@@ -135,6 +156,13 @@ __global__ void loss_parts_kernel(const float* rowpart, int nparts, double inv_c
     *loss = red[0][0] * inv_count;
     *gbout = (float)red[1][0];
   }
+}
+
+// out[c] = sum over the parts of part[p][c] (deterministic two-level sum through mid)
+void colsum_parts(const float* part, int nparts, int cols, float* mid, float* out, cudaStream_t s) {
+  const int chunks = (nparts + kColPer - 1) / kColPer;
+  colsum_level1_kernel<<<dim3((cols + 31) / 32, chunks), dim3(32, 8), 0, s>>>(part, nparts, cols, mid);
+  sum_parts_kernel<<<nblk(cols, 256), 256, 0, s>>>(mid, chunks, cols, cols, out);
 }
 
 }  // namespace
@@ -163,6 +191,7 @@ cudaError_t trainer_tc_alloc(crom_trainer* t) {
   c.colpart = (float*)A((size_t)tiles_m * 4 * w * 4);
   c.colpart2 = (float*)A((size_t)tiles_m * 4 * w * 4);
   c.rowpart = (float*)A((size_t)tiles_m * 4 * 2 * 4);
+  c.colmid = (float*)A((size_t)((tiles_m * 4 + kColPer - 1) / kColPer) * w * 4);
   c.split = (float*)A((size_t)kSplitsW * w * w * 4);
   c.din = (float*)A((size_t)N * kDinCols * 4);
   c.gw0part = (float*)A((size_t)kGw0Chunks * w * kin * 4);
@@ -220,8 +249,8 @@ cudaError_t trainer_decoder_tc(crom_trainer* t, double* loss_out, int num_sms, c
   }
   loss_parts_kernel<<<1, 256, 0, s>>>(c.rowpart, parts, 1.0 / (double)N, loss_out ? loss_out : t->loss_dev,
                                       gr + lay.dec_b[L]);
-  sum_parts_kernel<<<nblk(w, 256), 256, 0, s>>>(c.colpart2, parts, w, w, gr + lay.dec_w[L]);   // dL/dw_out
-  sum_parts_kernel<<<nblk(w, 256), 256, 0, s>>>(c.colpart, parts, w, w, gr + lay.dec_b[L - 1]);
+  colsum_parts(c.colpart2, parts, w, c.colmid, gr + lay.dec_w[L], s);   // dL/dw_out
+  colsum_parts(c.colpart, parts, w, c.colmid, gr + lay.dec_b[L - 1], s);
   // ---- backward
   uint16_t* dcur = c.d0;
   uint16_t* dnext = c.d1;
@@ -262,7 +291,7 @@ cudaError_t trainer_decoder_tc(crom_trainer* t, double* loss_out, int num_sms, c
       g.hprev = c.H[h - 1];
       g.colpart = c.colpart;
       if ((e = tc_gemm(g, num_sms, c.flag, s)) != cudaSuccess) return e;
-      sum_parts_kernel<<<nblk(w, 256), 256, 0, s>>>(c.colpart, parts, w, w, gr + lay.dec_b[h - 1]);
+      colsum_parts(c.colpart, parts, w, c.colmid, gr + lay.dec_b[h - 1], s);
     }
     std::swap(dcur, dnext);
   }

@@ -36,7 +36,7 @@ from helpers import dev, rel_l2
 pytestmark = pytest.mark.gpu
 
 N_SAMPLES = 1024
-TRAIN_STEPS = 30000
+TRAIN_STEPS = 60000
 ROLLOUT_BAR = 1e-2
 
 
@@ -100,12 +100,13 @@ def learned(c, trajectories, request):
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
     losses = []
     for k in range(TRAIN_STEPS):
-        lr = 1e-3 if k < TRAIN_STEPS // 4 else 1e-3 * (2e-5 / 1e-3) ** ((k - TRAIN_STEPS // 4) /
-                                                                      (TRAIN_STEPS - TRAIN_STEPS // 4 - 1))
+        # 1e-3 for the first half, then a geometric decay to 1e-5
+        half = TRAIN_STEPS // 2
+        lr = 1e-3 if k < half else 1e-3 * (1e-5 / 1e-3) ** ((k - half) / (TRAIN_STEPS - half - 1))
         pick = torch.randint(0, train.shape[0], (B,), device="cuda", generator=g)
         pts = torch.randint(0, P, (B, S), device="cuda", generator=g, dtype=torch.int32)
         c.crom_train_step(tr, train[pick].contiguous(), pts, coords, lr, loss)
-        if k % 5000 == 0 or k == TRAIN_STEPS - 1:
+        if k % 10000 == 0 or k == TRAIN_STEPS - 1:
             losses.append(loss.item())
     torch.cuda.synchronize()
     params = tr.get_params()
