@@ -4,13 +4,14 @@
 //
 // Persistent, one CTA per SM, 192 threads in warp roles:
 //   warp 0   TMA producer: one elected lane loads the A and B boxes of each 64-wide
-//            K block (cp.async.bulk.tensor, 128-byte swizzle) into a 4-stage ring;
+//            K block (cp.async.bulk.tensor, 128-byte swizzle) into a 3-stage ring;
 //   warp 1   MMA issuer: four UMMAs (M = 128, N = BN, K = 16) per K block into one of
 //            two tensor-memory accumulators, commits free the ring stage and, after
 //            the tile's last block, hand the accumulator to the epilogue;
 //   warps 2-5 epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (one tile row per
-//            thread, all BN columns), applies the fused operation and writes global
-//            memory; then frees the accumulator.
+//            thread, all BN columns), applies the fused operation, frees the
+//            accumulator; bf16 rows go through a per-warp shared-memory staging
+//            area so that global loads and stores move whole rows (coalesced).
 // With two accumulators the epilogue of one tile overlaps the MMAs of the next.
 // Operands: A(m, k) K-major (A[m * lda + k]) or MN-major (A[k * lda + m]); B(n, k)
 // likewise; both are read through tensor maps whose boxes land in shared memory in
@@ -32,7 +33,7 @@ namespace {
 
 using namespace tc;
 
-constexpr int kBM = 128, kBK = 64, kStages = 4;
+constexpr int kBM = 128, kBK = 64, kStages = 3;
 constexpr int kGemmThreads = 192;
 constexpr uint32_t kWait = 1u << 26;
 
@@ -123,13 +124,68 @@ __device__ __forceinline__ void load_bf16x32(const uint16_t* src, float (&v)[32]
   }
 }
 
+// Per-warp staging of 32 bf16 rows of BN columns in shared memory, rows padded by
+// 16 bytes so that one lane per row writing 16 bytes is conflict-free.
+template <int kBN>
+struct Staging {
+  static constexpr int kSt = kBN + 8;  // row stride in elements
+  uint16_t* base;                      // this warp's 32 rows
+  __device__ __forceinline__ void put32(int lane, int c0, const float (&v)[32]) const {
+    uint32_t w[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) w[j] = (uint32_t)to_bf16(v[2 * j]) | ((uint32_t)to_bf16(v[2 * j + 1]) << 16);
+    uint4* d = reinterpret_cast<uint4*>(base + lane * kSt + c0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) d[j] = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+  }
+  __device__ __forceinline__ void get32(int lane, int c0, float (&v)[32]) const {
+    const uint4* sp = reinterpret_cast<const uint4*>(base + lane * kSt + c0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint4 q = sp[j];
+      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        v[8 * j + 2 * i] = __uint_as_float(w[i] << 16);
+        v[8 * j + 2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+      }
+    }
+  }
+  // rows row0 .. row0 + 31 (those < M) of the [M][ld] global array, whole rows per
+  // instruction (BN / 8 lanes per row)
+  __device__ __forceinline__ void store_rows(uint16_t* dst, long ld, int row0, int M, int lane) const {
+    __syncwarp();
+    constexpr int kLpr = kBN / 8, kRpi = 32 / kLpr;
+#pragma unroll 4
+    for (int r0 = 0; r0 < 32; r0 += kRpi) {
+      const int r = r0 + lane / kLpr, c = (lane % kLpr) * 8;
+      if (row0 + r < M)
+        *reinterpret_cast<uint4*>(dst + (long)(row0 + r) * ld + c) = *reinterpret_cast<const uint4*>(base + r * kSt + c);
+    }
+    __syncwarp();
+  }
+  __device__ __forceinline__ void load_rows(const uint16_t* src, long ld, int row0, int M, int lane) const {
+    __syncwarp();
+    constexpr int kLpr = kBN / 8, kRpi = 32 / kLpr;
+#pragma unroll 4
+    for (int r0 = 0; r0 < 32; r0 += kRpi) {
+      const int r = r0 + lane / kLpr, c = (lane % kLpr) * 8;
+      uint4 q = make_uint4(0u, 0u, 0u, 0u);
+      if (row0 + r < M) q = __ldg(reinterpret_cast<const uint4*>(src + (long)(row0 + r) * ld + c));
+      *reinterpret_cast<uint4*>(base + r * kSt + c) = q;
+    }
+    __syncwarp();
+  }
+};
+
 template <int kBN, int kEpi>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Args g) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr uint32_t kABytes = kBM * kBK * 2, kBBytes = kBN * kBK * 2, kStageBytes = kABytes + kBBytes;
-  Bars* bars = reinterpret_cast<Bars*>(sm + kStages * kStageBytes);
+  constexpr size_t kStgBytes = (size_t)4 * 32 * Staging<kBN>::kSt * 2;
+  Bars* bars = reinterpret_cast<Bars*>(sm + kStages * kStageBytes + kStgBytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -225,16 +281,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   } else {
     // ------------------------------------------------ epilogue
     const int q = warp & 3;  // TMEM lane quadrant of this warp
+    const Staging<kBN> stg{reinterpret_cast<uint16_t*>(sm + kStages * kStageBytes) + (warp - 2) * 32 * Staging<kBN>::kSt};
     uint32_t tphase[2] = {0, 0};
     int local = 0;
     for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++local) {
       const int acc = local & 1;
       const int mt = t % g.tiles_m, sp = t / g.tiles_m;
+      const int row0 = mt * kBM + q * 32;
+      const int row = row0 + lane;
+      const bool in = row < g.M;
+      // h_{l-1} of the tile's rows does not depend on the accumulator: read it first
+      if (kEpi == kGemmEpiTimesEluD) stg.load_rows(g.hprev, g.ldo, row0, g.M, lane);
       g_wait(bars, &bars->tfull[acc], tphase[acc]);
       tphase[acc] ^= 1;
       tc_fence_after();
-      const int row = mt * kBM + q * 32 + lane;
-      const bool in = row < g.M;
       const uint32_t ta = tb + (uint32_t)acc * kBN + ((uint32_t)(q * 32) << 16);
       float gval = 0.f, dg = 0.f, rr = 0.f;
       if (kEpi == kGemmEpiOut) {
@@ -250,8 +310,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             v[j] = h;
             gval = fmaf(__ldg(g.wout + c0 + j), h, gval);
           }
-          if (in) store_bf16x32(g.out_bf16 + (long)row * g.ldo + c0, v);
+          stg.put32(lane, c0, v);
         }
+        stg.store_rows(g.out_bf16, g.ldo, row0, g.M, lane);
         const float r = in ? (gval + __ldg(g.bout) - __ldg(g.target + row)) : 0.f;
         rr = r * r;
         dg = 2.f * r * g.inv_count;
@@ -270,13 +331,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         } else if (kEpi == kGemmEpiBiasElu) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = elu_g(v[j] + __ldg(g.bias + c0 + j));
-          if (in) store_bf16x32(g.out_bf16 + (long)row * g.ldo + c0, v);
+          stg.put32(lane, c0, v);
         } else if (kEpi == kGemmEpiTimesEluD) {
           float hp[32];
-          if (in) load_bf16x32(g.hprev + (long)row * g.ldo + c0, hp);
+          stg.get32(lane, c0, hp);
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = in ? v[j] * elud_from_h(hp[j]) : 0.f;
-          if (in) store_bf16x32(g.out_bf16 + (long)row * g.ldo + c0, v);
+          stg.put32(lane, c0, v);                    // in place of the h values just read
           const float cs = warp_colsum32(v, lane);  // column sums of delta over this warp's rows
           g.colpart[(long)(mt * 4 + q) * g.N + c0 + lane] = cs;
         } else {  // kGemmEpiOut: delta_L = dg w_out s'(z_L) and the column sums of dg h_L, delta_L
@@ -288,14 +349,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             dh[j] = in ? dg * h : 0.f;
             v[j] = in ? dg * __ldg(g.wout + c0 + j) * (z > 0.f ? 1.f : h + 1.f) : 0.f;
           }
-          if (in) store_bf16x32(g.delta_out + (long)row * g.ldo + c0, v);
+          stg.put32(lane, c0, v);
           const float cs = warp_colsum32(v, lane);
           g.colpart[(long)(mt * 4 + q) * g.N + c0 + lane] = cs;
           const float cs2 = warp_colsum32(dh, lane);
           g.colpart2[(long)(mt * 4 + q) * g.N + c0 + lane] = cs2;
         }
       }
+      // the accumulator is read: hand it back before the stores
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars->tempty[acc]);
+      if (kEpi == kGemmEpiBiasElu || kEpi == kGemmEpiTimesEluD) stg.store_rows(g.out_bf16, g.ldo, row0, g.M, lane);
       if (kEpi == kGemmEpiOut) {
+        stg.store_rows(g.delta_out, g.ldo, row0, g.M, lane);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           rr += __shfl_xor_sync(0xffffffffu, rr, o);
@@ -306,9 +373,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           g.rowpart[(mt * 4 + q) * 2 + 1] = dg;
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bars->tempty[acc]);
     }
   }
   // drain: the producer's last loads and the issuer's last UMMAs have been waited
@@ -355,7 +419,8 @@ bool make_map(CUtensorMap* m, const void* base, long inner, long outer, long ld,
 
 template <int kBN, int kEpi>
 cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tbm, const Args& a, int grid, cudaStream_t s) {
-  const size_t smem = 1024 + (size_t)kStages * (kBM * kBK * 2 + kBN * kBK * 2) + sizeof(Bars);
+  const size_t smem = 1024 + (size_t)kStages * (kBM * kBK * 2 + kBN * kBK * 2) +
+                      (size_t)4 * 32 * Staging<kBN>::kSt * 2 + sizeof(Bars);
   auto k = gemm_tc_kernel<kBN, kEpi>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -318,22 +318,19 @@ __global__ void out_delta4_kernel(const float* dg, const float* wout, const floa
 }
 
 // dq[b][j] = sum_s din[b S + s][m + j] (din rows ld floats apart): one block per
-// snapshot, 256 row lanes, fixed-order tree per latent component.
+// (snapshot, latent component), 256 row lanes with compensated sums, fixed-order tree.
 __global__ void dq_kernel(const float* din, int ld, int B, int S, int m, int r, float* dq) {
-  const int b = blockIdx.x;
+  const int b = blockIdx.x, j = blockIdx.y;
   __shared__ double red[256];
-  for (int j = 0; j < r; ++j) {
-    CompSum s;
-    for (int i = threadIdx.x; i < S; i += blockDim.x) s.add(din[((long)b * S + i) * ld + m + j]);
-    red[threadIdx.x] = s.value();
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) dq[(long)b * r + j] = (float)red[0];
+  CompSum s;
+  for (int i = threadIdx.x; i < S; i += blockDim.x) s.add(din[((long)b * S + i) * ld + m + j]);
+  red[threadIdx.x] = s.value();
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
+  if (threadIdx.x == 0) dq[(long)b * r + j] = (float)red[0];
 }
 __global__ void adam_kernel(float* p, const float* g, float* m, float* v, long n, float lr, float c1, float c2) {
   const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -551,7 +548,7 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
       dnext = tmp;
     }
   }
-  dq_kernel<<<B, 256, 0, s>>>(din, din_ld, B, S, m, r, t->dq);
+  dq_kernel<<<dim3(B, r), 256, 0, s>>>(din, din_ld, B, S, m, r, t->dq);
   // ---- encoder reverse pass
   // dense 2: gW2 = dq^T h1, gb2 = sum dq, dz1 = (dq W2) * s'(z1)
   const int Ll = t->lens.back();

@@ -28,7 +28,7 @@ namespace crom {
 namespace {
 
 constexpr int kSplitsW = 64;      // K splits of the weight-gradient GEMMs
-constexpr int kGw0Chunks = 1024;  // row chunks of the input-layer weight gradient
+constexpr int kGw0Chunks = 512;   // row chunks of the input-layer weight gradient
 constexpr int kDinCols = 64;      // din = delta[0] W_0 padded to 64 columns
 
 inline unsigned nblk(long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -55,52 +55,65 @@ __global__ void weights_bf16_kernel(const float* params, const long* off_w, int 
   }
 }
 
-// H[0][n][u] = ELU(W_0[u] . in[n] + b_0[u]) in bf16: one thread per unit, 8 rows per
-// block (the rows' inputs staged in shared memory).
+// H[0][n][u] = ELU(W_0[u] . in[n] + b_0[u]) in bf16: one thread per unit, 32 rows per
+// block (the rows' inputs staged in shared memory); the K = m + r <= 32 loops are
+// unrolled to their bound and predicated, so W_0's row stays in registers.
+constexpr int kRows0 = 32;
 __global__ void layer0_fwd_kernel(const float* in, long N, int kin, const float* W0, const float* b0, int w,
                                   uint16_t* H) {
-  __shared__ float xs[8][32];
+  __shared__ float xs[kRows0][33];
   const int u = threadIdx.x;
-  const long n0 = (long)blockIdx.x * 8;
-  for (int i = threadIdx.x; i < 8 * kin; i += blockDim.x) {
-    const long n = n0 + i / kin;
-    xs[i / kin][i % kin] = n < N ? in[n * kin + i % kin] : 0.f;
+  const long n0 = (long)blockIdx.x * kRows0;
+  for (int i = threadIdx.x; i < kRows0 * 32; i += blockDim.x) {
+    const long n = n0 + i / 32;
+    const int j = i % 32;
+    xs[i / 32][j] = (n < N && j < kin) ? in[n * kin + j] : 0.f;   // zeros beyond kin
   }
   __syncthreads();
   if (u >= w) return;
   float wr[32];
-  for (int j = 0; j < kin; ++j) wr[j] = W0[(long)u * kin + j];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) wr[j] = j < kin ? W0[(long)u * kin + j] : 0.f;
   const float b = b0[u];
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < kRows0; ++i) {
     const long n = n0 + i;
     if (n >= N) break;
     float z = b;
-    for (int j = 0; j < kin; ++j) z = fmaf(wr[j], xs[i][j], z);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) z = fmaf(wr[j], xs[i][j], z);
     H[n * w + u] = bf16_bits(z > 0.f ? z : expm1f(z));
   }
 }
 
-// dW_0 partials: part[c][u][j] = sum over the rows of chunk c of delta[n][u] in[n][j].
+// dW_0 partials: part[c][u][j] = sum over the rows of chunk c of delta[n][u] in[n][j]
+// (loops over j unrolled to 32 and predicated: the accumulators stay in registers).
 __global__ void gw0_part_kernel(const uint16_t* delta, const float* in, long N, int kin, int w, float* part) {
-  __shared__ float xs[64][32];
+  __shared__ float xs[64][33];
   const int u = threadIdx.x;
   const long per = (N + gridDim.x - 1) / gridDim.x;
   const long r0 = (long)blockIdx.x * per, r1 = (r0 + per < N ? r0 + per : N);
   float acc[32];
+#pragma unroll
   for (int j = 0; j < 32; ++j) acc[j] = 0.f;
   for (long b = r0; b < r1; b += 64) {
     const int nr = (int)(r1 - b < 64 ? r1 - b : 64);
     __syncthreads();
-    for (int i = threadIdx.x; i < nr * kin; i += blockDim.x) xs[i / kin][i % kin] = in[(b + i / kin) * kin + i % kin];
+    for (int i = threadIdx.x; i < 64 * 32; i += blockDim.x) {
+      const int row = i / 32, j = i % 32;
+      xs[row][j] = (row < nr && j < kin) ? in[(b + row) * kin + j] : 0.f;
+    }
     __syncthreads();
     if (u < w)
       for (int i = 0; i < nr; ++i) {
         const float d = bf16_val(delta[(b + i) * w + u]);
-        for (int j = 0; j < kin; ++j) acc[j] = fmaf(d, xs[i][j], acc[j]);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = fmaf(d, xs[i][j], acc[j]);
       }
   }
   if (u < w)
-    for (int j = 0; j < kin; ++j) part[((long)blockIdx.x * w + u) * kin + j] = acc[j];
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < kin) part[((long)blockIdx.x * w + u) * kin + j] = acc[j];
 }
 
 // out[e] = sum_p part[p * stride + e], in order of p (FP64 accumulation).
@@ -191,7 +204,8 @@ cudaError_t trainer_tc_alloc(crom_trainer* t) {
   c.colpart = (float*)A((size_t)tiles_m * 4 * w * 4);
   c.colpart2 = (float*)A((size_t)tiles_m * 4 * w * 4);
   c.rowpart = (float*)A((size_t)tiles_m * 4 * 2 * 4);
-  c.colmid = (float*)A((size_t)((tiles_m * 4 + kColPer - 1) / kColPer) * w * 4);
+  c.colmid = (float*)A((size_t)std::max<long>((tiles_m * 4 + kColPer - 1) / kColPer * w,
+                                              (long)(kGw0Chunks + kColPer - 1) / kColPer * w * kin) * 4);
   c.split = (float*)A((size_t)kSplitsW * w * w * 4);
   c.din = (float*)A((size_t)N * kDinCols * 4);
   c.gw0part = (float*)A((size_t)kGw0Chunks * w * kin * 4);
@@ -218,7 +232,7 @@ cudaError_t trainer_decoder_tc(crom_trainer* t, double* loss_out, int num_sms, c
   weights_bf16_kernel<<<nblk(std::max<long>((long)(L - 1) * w * w, (long)w * kDinCols), 256), 256, 0, s>>>(
       p, c.off_w, L, w, kin, c.wh, c.w0p);
   // ---- forward
-  layer0_fwd_kernel<<<nblk(N, 8), std::max(w, 64), 0, s>>>(t->in0, N, kin, p + lay.dec_w[0], p + lay.dec_b[0], w,
+  layer0_fwd_kernel<<<nblk(N, kRows0), std::max(w, 64), 0, s>>>(t->in0, N, kin, p + lay.dec_w[0], p + lay.dec_b[0], w,
                                                           c.H[0]);
   for (int h = 1; h < L; ++h) {
     TcGemm g;
@@ -297,8 +311,7 @@ cudaError_t trainer_decoder_tc(crom_trainer* t, double* loss_out, int num_sms, c
   }
   // ---- input layer: dW_0 on the CUDA cores, din = delta[0] W_0 on the tensor cores
   gw0_part_kernel<<<kGw0Chunks, std::max(w, 64), 0, s>>>(dcur, t->in0, N, kin, w, c.gw0part);
-  sum_parts_kernel<<<nblk((long)w * kin, 256), 256, 0, s>>>(c.gw0part, kGw0Chunks, (long)w * kin, (long)w * kin,
-                                                           gr + lay.dec_w[0]);
+  colsum_parts(c.gw0part, kGw0Chunks, w * kin, c.colmid, gr + lay.dec_w[0], s);
   TcGemm g;
   g.M = (int)N;
   g.N = kDinCols;
