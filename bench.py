@@ -5,8 +5,8 @@ Workload: 1024 independent 2D heat instances sharing one decoder R^{2+8} -> R
 samples, 2 Gauss-Newton iterations, dt = 1e-5 (seeded synthetic inputs from
 workloads.gen.heat2d_batched).  One bench step = one crom_step call advancing
 every instance by one latent step (decode with derivatives, PDE update,
-Gauss-Newton projection) on the tensor-core path (bf16 hi/lo operands, FP32
-accumulation, FP64 normal equations).
+Gauss-Newton projection) on the tensor-core path (f16 hi/lo activation operands,
+f16 weights, FP32 accumulation, FP64 normal equations).
 
 Printed (one JSON line on rank 0): instance-steps/s of that step with inputs
 resident in HBM (L2 flushed before every timed step), the same metric end to
@@ -38,9 +38,9 @@ WORKLOAD = "heat2d_batched_1024inst_M32-512_r8_w128_L5_gn2"
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one step_tc_kernel launch on the
-# 1024-instance workload, from an ncu capture of the current kernel (2,596,608 B read,
-# 0 B written); to be re-taken whenever the kernel changes.
-STEP_KERNEL_DRAM_BYTES = 2596608
+# 1024-instance workload, from an ncu capture of the current kernel; None until it has
+# been taken for the current kernel.
+STEP_KERNEL_DRAM_BYTES = None
 
 
 def parse():
@@ -613,7 +613,7 @@ def main():
             rt.append(e0.elapsed_time(e1))
         return float(np.median(rt))
 
-    recon_ms_bf16 = time_recon(crom.CROM_PREC_F16)
+    recon_ms_f16 = time_recon(crom.CROM_PREC_F16)
     recon_ms = time_recon(crom.CROM_PREC_F16X2)
     recon_pts = codes.shape[0] * X.shape[0]
     recon_flops = recon_pts * 2 * (2 * 128 + 4 * 128 * 128 + 128)
@@ -719,7 +719,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "instance-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x2 (bf16 hi/lo operands, f32 accum, f64 solve)",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16x2 (f16 hi/lo activation operands, f16 weights, f32 accum, f64 solve)",
             "data": "synthetic",
             "config": bench_config(w.n_inst, world, int(w.sizes.sum())),
             "tiles": {"s0": tile_s0, "s1": tile_s1, "autotuned": args.tiles == "auto",
@@ -732,10 +732,11 @@ def main():
             "dense_reconstruction": {"points_per_s": recon_pts / (recon_ms * 1e-3), "ms": recon_ms,
                                      "tflops_algorithmic": recon_flops / (recon_ms * 1e-3) / 1e12,
                                      "frac_of_measured_bf16": recon_flops / (recon_ms * 1e-3) / 1e12 / peak_tf,
-                                     "workload": "1024^2 points x 64 codes, BF16X2",
-                                     "bf16_single_ms": recon_ms_bf16,
-                                     "bf16_single_frac_of_measured_bf16":
-                                         recon_flops / (recon_ms_bf16 * 1e-3) / 1e12 / peak_tf},
+                                     "workload": "1024^2 points x 64 codes, F16X2 (f16 hi/lo activations, "
+                                                 "f16 hi+lo weights)",
+                                     "f16_single_ms": recon_ms_f16,
+                                     "f16_single_frac_of_measured_bf16":
+                                         recon_flops / (recon_ms_f16 * 1e-3) / 1e12 / peak_tf},
             "graph_rollout": {"value": w.n_inst / (roll_ms * 1e-3), "unit": "instance-steps/s",
                               "ms_per_step": roll_ms, "steps_per_graph": n_roll,
                               "note": "crom_rollout: 1000 steps replayed from a cached CUDA graph, no L2 flush"},
