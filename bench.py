@@ -512,21 +512,46 @@ def main():
     value = world * w.n_inst / (ms * 1e-3)
 
     # ---- accuracy of the timed configuration: sampled instances vs the FP64 oracle (rank 0)
-    acc = None
-    if rank == 0:
+    acc_ids = np.random.default_rng(0).choice(w.n_inst, size=6, replace=False)
+    acc_ref = {}
+
+    def accuracy(prec):
         from oracle import crom_oracle as O
         qa = q0.clone()
-        step(qq=qa)
+        step(prec, qq=qa)
         torch.cuda.synchronize()
         qg = qa.cpu().numpy()
         dec = O.MLPDecoder(w.params, 2)
         errs, incs = [], []
-        for i in np.random.default_rng(0).choice(w.n_inst, size=6, replace=False):
-            Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
-            ref, _ = O.crom_step(dec, w.q0[i], Y, w.dt, w.gn_iters, alpha=float(w.alpha[i]))
+        for i in acc_ids:
+            if i not in acc_ref:
+                Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
+                acc_ref[i] = O.crom_step(dec, w.q0[i], Y, w.dt, w.gn_iters, alpha=float(w.alpha[i]))[0]
+            ref = acc_ref[i]
             errs.append(np.linalg.norm(qg[i] - ref) / np.linalg.norm(ref))
             incs.append(np.linalg.norm((qg[i] - w.q0[i]) - (ref - w.q0[i])) / np.linalg.norm(ref - w.q0[i]))
-        acc = {"q_rel_l2_max": float(max(errs)), "increment_rel_l2_max": float(max(incs)), "instances": 6}
+        return {"q_rel_l2_max": float(max(errs)), "increment_rel_l2_max": float(max(incs)), "instances": 6}
+
+    acc = accuracy(crom.CROM_PREC_F16X2) if rank == 0 else None
+
+    # ---- the same step with single f16 activations (CROM_PREC_F16): time and accuracy
+    def time_step(prec, n):
+        for _ in range(3):
+            step(prec)
+        torch.cuda.synchronize()
+        evs_p = []
+        for _ in range(n):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(prec)
+            b.record(stream)
+            evs_p.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in evs_p]))
+
+    f16_ms = time_step(crom.CROM_PREC_F16, min(args.steps, 100))
+    f16_acc = accuracy(crom.CROM_PREC_F16) if rank == 0 else None
 
     # ---- end to end through the C ABI on host arrays (crom_step_host: the library
     # copies the pinned inputs in, steps, copies q and status out and synchronises)
@@ -695,7 +720,7 @@ def main():
     train_ms = time_train(crom.CROM_PREC_BF16_MIXED, 10)
     pts = Bt * St
     train_flops = pts * 6 * (2 * (2 + rt) * wt + 2 * (Lt - 1) * wt * wt + 2 * wt) / 2
-    train_bytes = (4.5 + 7 * (Lt - 1)) * pts * wt * 2
+    train_bytes = (7 * Lt - 4) * pts * wt * 2
     tr.close()
 
     next_rows = measure_next_rows(crom, gen, ctx, w, q0, alpha, s_off, samples, status, stream, flush, local)
@@ -726,6 +751,14 @@ def main():
                       "ms_per_step_large_small_s1": [round(tile_ms[0], 4), round(tile_ms[1], 4)]},
             "status_all_ok": bool(np.all(st == 0)),
             "accuracy_vs_fp64_oracle": acc,
+            "f16_single_step": {"ms_per_step": f16_ms, "value": world * w.n_inst / (f16_ms * 1e-3),
+                                "unit": "instance-steps/s",
+                                "tflops_algorithmic": flops / (f16_ms * 1e-3) / 1e12,
+                                "frac_of_measured_bf16": flops / (f16_ms * 1e-3) / 1e12 / peak_tf,
+                                "accuracy_vs_fp64_oracle": f16_acc,
+                                "note": "CROM_PREC_F16: activations as single f16 values (tiles of twice the "
+                                        "samples per UMMA); per-step errors up to ~10x F16X2's on "
+                                        "ill-conditioned decoders, so F16X2 is the headline"},
             "plain_fp32_single": {"value": plain_value, "unit": "instance-steps/s", "us_per_step": plain_ms * 1e3,
                                   "workload": "heat2d_single_M200_r8_w128_L5_gn2 (FP32 CUDA cores)"},
             "speedup_vs_plain_fp32": value / world / plain_value,
@@ -752,8 +785,8 @@ def main():
                          "frac_of_measured_bf16": train_flops / (train_ms * 1e-3) / 1e12 / peak_tf,
                          "hbm_gbs_algorithmic": train_bytes / (train_ms * 1e-3) / 1e9,
                          "frac_of_measured_hbm": train_bytes / (train_ms * 1e-3) / 1e9 / hbm,
-                         "bytes_note": "decoder pass: 4.5 + 7 (L - 1) reads or writes of a [B*S][w] bf16 "
-                                       "array per step (activations, deltas), the roofline that binds here",
+                         "bytes_note": "decoder pass: 7 L - 4 reads or writes of a [B*S][w] bf16 array "
+                                       "per step (activations, deltas), the roofline that binds here",
                          "precision": "library tcgen05 GEMMs with fused epilogues, bf16 operands, FP32 "
                                       "accumulation and master weights",
                          "fp32_ms_per_step": train_ms_fp32,

@@ -70,8 +70,11 @@ typedef enum {
  *           f16 rather than bf16 operands: both run at the same tensor rate, and
  *           bf16 weights (2^-9) move dense outputs by ~5e-3 and latent increments by
  *           several per cent against FP32 weights.
- *  F16    : as F16X2 with the high parts of the activations only and f16 weights.
- *           Dense reconstruction only.
+ *  F16    : as F16X2 with the high parts of the activations only (single f16
+ *           operands, 2^-12 relative) and f16 weights.  Dense reconstruction and
+ *           the step: the step's sample tiles hold twice the samples for the same
+ *           UMMA widths (about 1.5x the F16X2 step's speed); its per-step errors
+ *           are up to ~10x F16X2's on ill-conditioned decoders (kappa(J) ~ 1e5).
  *  BF16_MIXED : training step only: the decoder's dense products on the tcgen05
  *           tensor cores (the library's TMA-fed GEMM) with bf16 weights,
  *           activations and deltas and FP32 accumulation, the elementwise work
@@ -155,8 +158,8 @@ int crom_tangent_velocity(crom_ctx* ctx, int n_inst, const double* q, const doub
  *             (the paper's backtracking line search, §4.3); if none does, q is
  *             kept and the instance's remaining iterations are skipped.  Each
  *             trial costs one value-only pass over the instance's samples.
- *             Available with CROM_PREC_F16X2 (the FP32 path returns
- *             CROM_ERR_UNSUPPORTED). */
+ *             Available with CROM_PREC_F16X2 and CROM_PREC_F16 (the FP32
+ *             path returns CROM_ERR_UNSUPPORTED). */
 typedef struct {
   int pde;
   int gn_iters;
@@ -211,9 +214,9 @@ int crom_decode(crom_ctx* ctx, int n_inst, const double* q, const int* pt_off, c
  *   instance over several CTAs (the last CTA to finish reduces and solves); the
  *   context grows its scratch on first use, so the first call for a given size
  *   must not be made during stream capture.
- * precision CROM_PREC_F16X2: one persistent launch per step (plus a small
- *   ordering kernel); each of a CTA's four 128-thread groups takes whole
- *   instances, largest |M_i| first, from a queue. */
+ * precision CROM_PREC_F16X2 or CROM_PREC_F16: one persistent launch per step
+ *   (plus a small ordering kernel); each of a CTA's four 128-thread groups takes
+ *   whole instances, largest |M_i| first, from a queue. */
 int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_inst, double* q,
               const float* alpha, const float* vel, const int* s_off, const float* samples,
               int n_samples, int max_samples, int* status, crom_stream stream);
@@ -233,7 +236,8 @@ int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n
 /* Sample-tile shape of the tensor-core step (CROM_PREC_F16X2): s0 samples per
  * forward tile in the first Gauss-Newton iteration (4 channels: 8, fixed by the
  * 32 hi-part operand columns of a tile; two such tiles share one reverse pass),
- * s1 in later ones (2 channels: 16 or 8).  Larger tiles issue half as many UMMA
+ * s1 in later ones (2 channels: 16 or 8).  CROM_PREC_F16 (hi parts only) runs
+ * tiles of twice these sizes under the same setting.  Larger tiles issue half as many UMMA
  * stages; smaller ones waste less on the ragged last tile of each instance.
  * crom_set_step_tiles fixes the shape (default (8, 16)); crom_get_step_tiles reads
  * it and, into ms[2] (may be NULL), the per-step times that the last crom_autotune
@@ -390,7 +394,7 @@ int crom_reconstruct(crom_ctx* ctx, int precision, int n_codes, const double* q,
  *  init_idx  [n_init] distinct node indices, host
  *  idx_out   [max_samples] host: the selected node indices in order of addition
  *            (the initial ones first); count_out, metric_out host scalars.
- * step->pde must be CROM_PDE_HEAT; precision FP32 (no line search) or F16X2.
+ * step->pde must be CROM_PDE_HEAT; precision FP32 (no line search), F16X2 or F16.
  * Limits: 1 <= n_try <= 64, n_init <= max_samples <= min(n_nodes, 4096),
  * n_try * n_params <= 65535.  The call allocates its work buffers and returns
  * after the work on `stream` completed (not usable during stream capture). */

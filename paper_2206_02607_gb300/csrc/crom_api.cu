@@ -354,8 +354,8 @@ int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_in
     return fail(CROM_ERR_INVALID_ARG, "crom_step: coef_per_sample must be 0 or 1");
   if (step->line_search < 0 || step->line_search > 16)
     return fail(CROM_ERR_INVALID_ARG, "crom_step: line_search must be in 0..16");
-  if (step->line_search > 0 && precision != CROM_PREC_F16X2)
-    return fail(CROM_ERR_UNSUPPORTED, "crom_step: the line search is available with CROM_PREC_F16X2");
+  if (step->line_search > 0 && precision != CROM_PREC_F16X2 && precision != CROM_PREC_F16)
+    return fail(CROM_ERR_UNSUPPORTED, "crom_step: the line search is available with CROM_PREC_F16X2 and CROM_PREC_F16");
   if (n_inst == 0) return CROM_OK;
   if (!q || !alpha || !s_off || !status || (n_samples > 0 && !samples))
     return fail(CROM_ERR_INVALID_ARG, "crom_step: null array");
@@ -369,10 +369,11 @@ int crom_step(crom_ctx* ctx, const crom_step_desc* step, int precision, int n_in
       return fail(CROM_ERR_INVALID_ARG, "crom_step: max_samples too large for the FP32 step's grid (at most 65535 "
                                         "CTAs per instance); use CROM_PREC_F16X2 or split the instance");
     e = launch_step_fp32(ctx, step, n_inst, q, alpha, vel, s_off, samples, n_samples, max_samples, status, s);
-  } else if (precision == CROM_PREC_F16X2) {
+  } else if (precision == CROM_PREC_F16X2 || precision == CROM_PREC_F16) {
     if (!tc_shape_ok(ctx->desc) || !ctx->w.tc_img)
-      return fail(CROM_ERR_UNSUPPORTED, "crom_step: F16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15, ELU");
-    e = launch_step_tc(ctx, step, n_inst, q, alpha, vel, s_off, samples, n_samples, max_samples, status, s);
+      return fail(CROM_ERR_UNSUPPORTED, "crom_step: F16X2 and F16 need width 128, 2<=hidden<=5, m<=2, r<=15, ELU");
+    e = launch_step_tc(ctx, step, precision == CROM_PREC_F16X2, n_inst, q, alpha, vel, s_off, samples, n_samples,
+                       max_samples, status, s);
   } else {
     return fail(CROM_ERR_UNSUPPORTED, "crom_step: precision not available for the step");
   }
@@ -458,15 +459,15 @@ int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n
     return fail(CROM_ERR_INVALID_ARG, "crom_rollout: coef_per_sample must be 0 or 1");
   if (step->line_search < 0 || step->line_search > 16)
     return fail(CROM_ERR_INVALID_ARG, "crom_rollout: line_search must be in 0..16");
-  if (step->line_search > 0 && precision != CROM_PREC_F16X2)
-    return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: the line search is available with CROM_PREC_F16X2");
+  if (step->line_search > 0 && precision != CROM_PREC_F16X2 && precision != CROM_PREC_F16)
+    return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: the line search is available with CROM_PREC_F16X2 and CROM_PREC_F16");
   if (!q || !alpha || !s_off || !status || (n_samples > 0 && !samples))
     return fail(CROM_ERR_INVALID_ARG, "crom_rollout: null array");
   if (step->pde == CROM_PDE_ADVDIFF && !vel) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: advection needs vel");
   if (max_samples < 1) return fail(CROM_ERR_INVALID_ARG, "crom_rollout: max_samples must be >= 1");
-  if (precision == CROM_PREC_F16X2) {
+  if (precision == CROM_PREC_F16X2 || precision == CROM_PREC_F16) {
     if (!tc_shape_ok(ctx->desc) || !ctx->w.tc_img)
-      return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: F16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15, ELU");
+      return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: F16X2 and F16 need width 128, 2<=hidden<=5, m<=2, r<=15, ELU");
   } else if (precision != CROM_PREC_FP32) {
     return fail(CROM_ERR_UNSUPPORTED, "crom_rollout: precision not available for the step");
   } else if (step_fp32_max_tiles(ctx, n_inst, max_samples) > 65535) {
@@ -528,8 +529,8 @@ int crom_rollout(crom_ctx* ctx, const crom_step_desc* step, int precision, int n
       le = (precision == CROM_PREC_FP32)
                ? launch_step_fp32(ctx, step, n_inst, q, alpha, vel, s_off, samples, n_samples, max_samples, status,
                                   ctx->cap_stream)
-               : launch_step_tc(ctx, step, n_inst, q, alpha, vel, s_off, samples, n_samples, max_samples, status,
-                                ctx->cap_stream);
+               : launch_step_tc(ctx, step, precision == CROM_PREC_F16X2, n_inst, q, alpha, vel, s_off, samples,
+                                n_samples, max_samples, status, ctx->cap_stream);
     }
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(ctx->cap_stream, &graph);
@@ -857,11 +858,11 @@ int crom_robust_samples(crom_ctx* ctx, const crom_step_desc* step, int precision
       step->gn_iters > 16 || !(step->dt > 0.0) || !isfinite(step->dt) ||
       (step->coef_per_sample != 0 && step->coef_per_sample != 1))
     return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": needs a heat step with valid gn_iters, dt, coefficient mode");
-  if (precision == CROM_PREC_F16X2) {
+  if (precision == CROM_PREC_F16X2 || precision == CROM_PREC_F16) {
     if (!tc_shape_ok(ctx->desc) || !ctx->w.tc_img)
-      return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": F16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15");
+      return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": F16X2 and F16 need width 128, 2<=hidden<=5, m<=2, r<=15");
   } else if (precision != CROM_PREC_FP32 || step->line_search > 0) {
-    return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": precision FP32 (no line search) or F16X2");
+    return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": precision FP32 (no line search), F16X2 or F16");
   }
   std::vector<int> M(init_idx, init_idx + n_init);
   {
@@ -919,8 +920,9 @@ int crom_robust_samples(crom_ctx* ctx, const crom_step_desc* step, int precision
     const float* a = sd.coef_per_sample ? d_alpha_s : d_alpha;
     if (e == cudaSuccess && n_steps == 0) e = cudaMemsetAsync(d_status, 0, (size_t)n_inst * sizeof(int), s);
     for (int t = 0; t < n_steps && e == cudaSuccess; ++t)
-      e = precision == CROM_PREC_F16X2
-              ? launch_step_tc(ctx, &sd, n_inst, d_q, a, nullptr, d_off, d_samples, n_s, max_s, d_status, s)
+      e = precision != CROM_PREC_FP32
+              ? launch_step_tc(ctx, &sd, precision == CROM_PREC_F16X2, n_inst, d_q, a, nullptr, d_off, d_samples, n_s,
+                               max_s, d_status, s)
               : launch_step_fp32(ctx, &sd, n_inst, d_q, a, nullptr, d_off, d_samples, n_s, max_s, d_status, s);
     if (e == cudaSuccess) e = launch_recon_fp32(ctx, n_inst, d_q, n_nodes, nodes, d_out, s);
     if (e == cudaSuccess) e = launch_sampling_metric(d_out, fom_final, d_status, C, n_params, n_nodes, d_res, d_metric, s);

@@ -108,14 +108,15 @@ namespace crom {
 struct TrainerTc {
   bool ready = false;
   uint16_t* wh = nullptr;   // bf16 hidden matrices W_1..W_{L-1}, [w][w] each
-  uint16_t* w0p = nullptr;  // bf16 W_0 as [w][64] (row u: W_0[u][0..m+r), zeros)
   std::vector<uint16_t*> H; // bf16 activations of the hidden layers, [B*S][w] each
   uint16_t *d0 = nullptr, *d1 = nullptr;  // bf16 deltas [B*S][w]
   float *colpart = nullptr, *colpart2 = nullptr, *rowpart = nullptr;  // epilogue partial sums
   float* colmid = nullptr;  // first level of the column-sum reduction
   float* split = nullptr;   // split-K partials of the weight gradients
-  float* din = nullptr;     // [B*S][64]: delta_0 W_0 (input gradient), FP32
-  float* gw0part = nullptr; // row-chunk partials of dW_0
+  float* xin = nullptr;     // [B*S][m]: the sampled points' coordinates
+  float* c0 = nullptr;      // [B][w]: b_0 + W_0q q_b, the latent part of layer 0 per snapshot
+  float* part0 = nullptr;   // [B][chunks][w][1 + m]: row-chunk moments of delta_0
+  float* snap0 = nullptr;   // [B][w][1 + m]: per-snapshot moments of delta_0
   long* off_w = nullptr;    // device copy of the decoder weight offsets
   int* flag = nullptr;      // set by a GEMM whose bounded wait ran out
 };
@@ -159,12 +160,11 @@ int trainer_set_precision(crom_trainer* t, int precision);
 cudaError_t trainer_encode(crom_trainer* t, int nb, const float* snaps, float* q_out, cudaStream_t s);
 cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx, const float* coords, float lr,
                          double* loss_out, cudaStream_t s);
-// tensor-core decoder pass (train_tc.cu): loss, decoder gradients and the input
-// gradient din ([B*S][trainer_tc_din_ld()] FP32) from t->in0 and t->target
+// tensor-core decoder pass (train_tc.cu): loss, decoder gradients and the latent
+// codes' gradient t->dq ([B][r]) from t->tc.xin, t->q and t->target
 bool trainer_tc_supported(const crom_trainer* t);
 cudaError_t trainer_tc_alloc(crom_trainer* t);
 cudaError_t trainer_decoder_tc(crom_trainer* t, double* loss_out, int num_sms, cudaStream_t s);
-int trainer_tc_din_ld();
 
 // Channel configuration of the FP32 forward-mode evaluation.
 enum SecondOrder { kSecondNone = 0, kSecondPerK = 1, kSecondLap = 2 };
@@ -206,7 +206,8 @@ cudaError_t launch_fom(int kind, int n_batch, int nx, int ny, const float* coef,
                        double dt, int n_steps, float* u, float* tmp, cudaStream_t s);
 
 // Tensor-core launches (tc_step.cu, tc_recon.cu).
-cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, double* q,
+// lo_parts: 1 for F16X2 (activations as f16 hi + lo parts), 0 for F16 (hi parts only)
+cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int lo_parts, int n_inst, double* q,
                            const float* alpha, const float* vel, const int* s_off,
                            const float* samples, int n_samples, int max_samples, int* status,
                            cudaStream_t s);

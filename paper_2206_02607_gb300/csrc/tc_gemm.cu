@@ -2,16 +2,18 @@
 // App. D): D[m][n] = sum_k A(m, k) B(n, k) with FP32 accumulation in tensor memory
 // and the training pass's elementwise work fused into the epilogue.
 //
-// Persistent, one CTA per SM, 192 threads in warp roles:
+// Persistent, one CTA per SM, 320 threads in warp roles:
 //   warp 0   TMA producer: one elected lane loads the A and B boxes of each 64-wide
 //            K block (cp.async.bulk.tensor, 128-byte swizzle) into a 3-stage ring;
 //   warp 1   MMA issuer: four UMMAs (M = 128, N = BN, K = 16) per K block into one of
 //            two tensor-memory accumulators, commits free the ring stage and, after
 //            the tile's last block, hand the accumulator to the epilogue;
-//   warps 2-5 epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (one tile row per
-//            thread, all BN columns), applies the fused operation, frees the
-//            accumulator; bf16 rows go through a per-warp shared-memory staging
-//            area so that global loads and stores move whole rows (coalesced).
+//   warps 2-9 epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (one tile row per
+//            thread) and one half of the BN columns (warps 2-5 the first, 6-9 the
+//            second), applies the fused operation, frees the accumulator; bf16 rows
+//            go through a per-warp shared-memory staging area so that global loads
+//            and stores move whole half rows (coalesced).  Two warps per SM
+//            sub-partition hide each other's load, shuffle and exp latencies.
 // With two accumulators the epilogue of one tile overlaps the MMAs of the next.
 // Operands: A(m, k) K-major (A[m * lda + k]) or MN-major (A[k * lda + m]); B(n, k)
 // likewise; both are read through tensor maps whose boxes land in shared memory in
@@ -34,7 +36,8 @@ namespace {
 using namespace tc;
 
 constexpr int kBM = 128, kBK = 64, kStages = 3;
-constexpr int kGemmThreads = 192;
+constexpr int kEpiWarps = 8;
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kWait = 1u << 26;
 
 struct Args {
@@ -62,6 +65,7 @@ struct __align__(8) Bars {
   uint64_t full[kStages], empty[kStages], tfull[2], tempty[2];
   uint32_t tmem_base;
   int abort;
+  float gpart[2][2][4][32];  // output layer: [tile parity][column half][lane quadrant][row] partial sums
 };
 
 __device__ __forceinline__ bool g_aborted(Bars* b) { return *reinterpret_cast<volatile int*>(&b->abort) != 0; }
@@ -102,34 +106,12 @@ __device__ __forceinline__ float warp_colsum32(float (&v)[32], int lane) {
   return v[0];
 }
 
-__device__ __forceinline__ void store_bf16x32(uint16_t* dst, const float (&v)[32]) {
-  uint32_t w[16];
-#pragma unroll
-  for (int j = 0; j < 16; ++j) w[j] = (uint32_t)to_bf16(v[2 * j]) | ((uint32_t)to_bf16(v[2 * j + 1]) << 16);
-  uint4* d = reinterpret_cast<uint4*>(dst);
-#pragma unroll
-  for (int j = 0; j < 4; ++j) d[j] = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
-}
-__device__ __forceinline__ void load_bf16x32(const uint16_t* src, float (&v)[32]) {
-  const uint4* s = reinterpret_cast<const uint4*>(src);
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const uint4 q = __ldg(s + j);
-    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      v[8 * j + 2 * i] = __uint_as_float(w[i] << 16);
-      v[8 * j + 2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
-    }
-  }
-}
-
-// Per-warp staging of 32 bf16 rows of BN columns in shared memory, rows padded by
+// Per-warp staging of 32 bf16 rows of kW columns in shared memory, rows padded by
 // 16 bytes so that one lane per row writing 16 bytes is conflict-free.
-template <int kBN>
+template <int kW>
 struct Staging {
-  static constexpr int kSt = kBN + 8;  // row stride in elements
-  uint16_t* base;                      // this warp's 32 rows
+  static constexpr int kSt = kW + 8;  // row stride in elements
+  uint16_t* base;                     // this warp's 32 rows
   __device__ __forceinline__ void put32(int lane, int c0, const float (&v)[32]) const {
     uint32_t w[16];
 #pragma unroll
@@ -151,27 +133,28 @@ struct Staging {
       }
     }
   }
-  // rows row0 .. row0 + 31 (those < M) of the [M][ld] global array, whole rows per
-  // instruction (BN / 8 lanes per row)
-  __device__ __forceinline__ void store_rows(uint16_t* dst, long ld, int row0, int M, int lane) const {
+  // columns col0 .. col0 + kW - 1 of rows row0 .. row0 + 31 (those < M) of the [M][ld]
+  // global array, whole staged rows per instruction (kW / 8 lanes per row)
+  __device__ __forceinline__ void store_rows(uint16_t* dst, long ld, int row0, int col0, int M, int lane) const {
     __syncwarp();
-    constexpr int kLpr = kBN / 8, kRpi = 32 / kLpr;
-#pragma unroll 4
+    constexpr int kLpr = kW / 8, kRpi = 32 / kLpr;
+#pragma unroll
     for (int r0 = 0; r0 < 32; r0 += kRpi) {
       const int r = r0 + lane / kLpr, c = (lane % kLpr) * 8;
       if (row0 + r < M)
-        *reinterpret_cast<uint4*>(dst + (long)(row0 + r) * ld + c) = *reinterpret_cast<const uint4*>(base + r * kSt + c);
+        *reinterpret_cast<uint4*>(dst + (long)(row0 + r) * ld + col0 + c) =
+            *reinterpret_cast<const uint4*>(base + r * kSt + c);
     }
     __syncwarp();
   }
-  __device__ __forceinline__ void load_rows(const uint16_t* src, long ld, int row0, int M, int lane) const {
+  __device__ __forceinline__ void load_rows(const uint16_t* src, long ld, int row0, int col0, int M, int lane) const {
     __syncwarp();
-    constexpr int kLpr = kBN / 8, kRpi = 32 / kLpr;
-#pragma unroll 4
+    constexpr int kLpr = kW / 8, kRpi = 32 / kLpr;
+#pragma unroll
     for (int r0 = 0; r0 < 32; r0 += kRpi) {
       const int r = r0 + lane / kLpr, c = (lane % kLpr) * 8;
       uint4 q = make_uint4(0u, 0u, 0u, 0u);
-      if (row0 + r < M) q = __ldg(reinterpret_cast<const uint4*>(src + (long)(row0 + r) * ld + c));
+      if (row0 + r < M) q = __ldg(reinterpret_cast<const uint4*>(src + (long)(row0 + r) * ld + col0 + c));
       *reinterpret_cast<uint4*>(base + r * kSt + c) = q;
     }
     __syncwarp();
@@ -184,7 +167,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr uint32_t kABytes = kBM * kBK * 2, kBBytes = kBN * kBK * 2, kStageBytes = kABytes + kBBytes;
-  constexpr size_t kStgBytes = (size_t)4 * 32 * Staging<kBN>::kSt * 2;
+  constexpr int kHalf = kBN / 2;  // columns per epilogue warp
+  constexpr size_t kStgBytes = (size_t)kEpiWarps * 32 * Staging<kHalf>::kSt * 2;
   Bars* bars = reinterpret_cast<Bars*>(sm + kStages * kStageBytes + kStgBytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -194,7 +178,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&bars->tfull[a], 1);
-      mbar_init(&bars->tempty[a], 4);
+      mbar_init(&bars->tempty[a], kEpiWarps);
     }
     bars->abort = 0;
     fence_mbar_init();
@@ -280,8 +264,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
   } else {
     // ------------------------------------------------ epilogue
-    const int q = warp & 3;  // TMEM lane quadrant of this warp
-    const Staging<kBN> stg{reinterpret_cast<uint16_t*>(sm + kStages * kStageBytes) + (warp - 2) * 32 * Staging<kBN>::kSt};
+    const int ew = warp - 2;
+    const int q = warp & 3;                 // TMEM lane quadrant of this warp
+    const int half = ew >> 2, cb = half * kHalf;  // its column half
+    const Staging<kHalf> stg{reinterpret_cast<uint16_t*>(sm + kStages * kStageBytes) + ew * 32 * Staging<kHalf>::kSt};
     uint32_t tphase[2] = {0, 0};
     int local = 0;
     for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++local) {
@@ -291,46 +277,51 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       const int row = row0 + lane;
       const bool in = row < g.M;
       // h_{l-1} of the tile's rows does not depend on the accumulator: read it first
-      if (kEpi == kGemmEpiTimesEluD) stg.load_rows(g.hprev, g.ldo, row0, g.M, lane);
+      if (kEpi == kGemmEpiTimesEluD) stg.load_rows(g.hprev, g.ldo, row0, cb, g.M, lane);
       g_wait(bars, &bars->tfull[acc], tphase[acc]);
       tphase[acc] ^= 1;
       tc_fence_after();
-      const uint32_t ta = tb + (uint32_t)acc * kBN + ((uint32_t)(q * 32) << 16);
+      const uint32_t ta = tb + (uint32_t)acc * kBN + (uint32_t)cb + ((uint32_t)(q * 32) << 16);
       float gval = 0.f, dg = 0.f, rr = 0.f;
       if (kEpi == kGemmEpiOut) {
-        // output layer g = w_out . h_L + b_out on this row, then the loss terms
+        // output layer g = w_out . h_L + b_out on this row (the two column halves'
+        // partial sums meet in shared memory, added in a fixed order), then the loss terms
 #pragma unroll 1
-        for (int c0 = 0; c0 < kBN; c0 += 32) {
+        for (int c0 = 0; c0 < kHalf; c0 += 32) {
           float v[32];
           tmem_ld32(ta + c0, v);
           tmem_ld_wait();
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const float h = elu_g(v[j] + __ldg(g.bias + c0 + j));
+            const float h = elu_g(v[j] + __ldg(g.bias + cb + c0 + j));
             v[j] = h;
-            gval = fmaf(__ldg(g.wout + c0 + j), h, gval);
+            gval = fmaf(__ldg(g.wout + cb + c0 + j), h, gval);
           }
           stg.put32(lane, c0, v);
         }
-        stg.store_rows(g.out_bf16, g.ldo, row0, g.M, lane);
+        stg.store_rows(g.out_bf16, g.ldo, row0, cb, g.M, lane);
+        bars->gpart[local & 1][half][q][lane] = gval;
+        asm volatile("bar.sync %0, 64;" ::"r"(1 + q) : "memory");  // the two warps of quadrant q
+        gval = bars->gpart[local & 1][0][q][lane] + bars->gpart[local & 1][1][q][lane];
         const float r = in ? (gval + __ldg(g.bout) - __ldg(g.target + row)) : 0.f;
         rr = r * r;
         dg = 2.f * r * g.inv_count;
       }
 #pragma unroll 1
-      for (int c0 = 0; c0 < kBN; c0 += 32) {
+      for (int c0 = 0; c0 < kHalf; c0 += 32) {
         float v[32];
         tmem_ld32(ta + c0, v);
         tmem_ld_wait();
+        const int col = cb + c0;
         if (kEpi == kGemmEpiF32) {
           if (in) {
-            float4* o = reinterpret_cast<float4*>(g.out_f32 + (long)sp * g.M * g.ldo + (long)row * g.ldo + c0);
+            float4* o = reinterpret_cast<float4*>(g.out_f32 + (long)sp * g.M * g.ldo + (long)row * g.ldo + col);
 #pragma unroll
             for (int j = 0; j < 8; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
           }
         } else if (kEpi == kGemmEpiBiasElu) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = elu_g(v[j] + __ldg(g.bias + c0 + j));
+          for (int j = 0; j < 32; ++j) v[j] = elu_g(v[j] + __ldg(g.bias + col + j));
           stg.put32(lane, c0, v);
         } else if (kEpi == kGemmEpiTimesEluD) {
           float hp[32];
@@ -339,38 +330,40 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           for (int j = 0; j < 32; ++j) v[j] = in ? v[j] * elud_from_h(hp[j]) : 0.f;
           stg.put32(lane, c0, v);                    // in place of the h values just read
           const float cs = warp_colsum32(v, lane);  // column sums of delta over this warp's rows
-          g.colpart[(long)(mt * 4 + q) * g.N + c0 + lane] = cs;
+          g.colpart[(long)(mt * 4 + q) * g.N + col + lane] = cs;
         } else {  // kGemmEpiOut: delta_L = dg w_out s'(z_L) and the column sums of dg h_L, delta_L
           float dh[32];
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const float z = v[j] + __ldg(g.bias + c0 + j);
+            const float z = v[j] + __ldg(g.bias + col + j);
             const float h = elu_g(z);
             dh[j] = in ? dg * h : 0.f;
-            v[j] = in ? dg * __ldg(g.wout + c0 + j) * (z > 0.f ? 1.f : h + 1.f) : 0.f;
+            v[j] = in ? dg * __ldg(g.wout + col + j) * (z > 0.f ? 1.f : h + 1.f) : 0.f;
           }
           stg.put32(lane, c0, v);
           const float cs = warp_colsum32(v, lane);
-          g.colpart[(long)(mt * 4 + q) * g.N + c0 + lane] = cs;
+          g.colpart[(long)(mt * 4 + q) * g.N + col + lane] = cs;
           const float cs2 = warp_colsum32(dh, lane);
-          g.colpart2[(long)(mt * 4 + q) * g.N + c0 + lane] = cs2;
+          g.colpart2[(long)(mt * 4 + q) * g.N + col + lane] = cs2;
         }
       }
       // the accumulator is read: hand it back before the stores
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars->tempty[acc]);
-      if (kEpi == kGemmEpiBiasElu || kEpi == kGemmEpiTimesEluD) stg.store_rows(g.out_bf16, g.ldo, row0, g.M, lane);
+      if (kEpi == kGemmEpiBiasElu || kEpi == kGemmEpiTimesEluD) stg.store_rows(g.out_bf16, g.ldo, row0, cb, g.M, lane);
       if (kEpi == kGemmEpiOut) {
-        stg.store_rows(g.delta_out, g.ldo, row0, g.M, lane);
+        stg.store_rows(g.delta_out, g.ldo, row0, cb, g.M, lane);
+        if (half == 0) {  // the row terms once per row
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          rr += __shfl_xor_sync(0xffffffffu, rr, o);
-          dg += __shfl_xor_sync(0xffffffffu, dg, o);
-        }
-        if (lane == 0) {
-          g.rowpart[(mt * 4 + q) * 2] = rr;
-          g.rowpart[(mt * 4 + q) * 2 + 1] = dg;
+          for (int o = 16; o > 0; o >>= 1) {
+            rr += __shfl_xor_sync(0xffffffffu, rr, o);
+            dg += __shfl_xor_sync(0xffffffffu, dg, o);
+          }
+          if (lane == 0) {
+            g.rowpart[(mt * 4 + q) * 2] = rr;
+            g.rowpart[(mt * 4 + q) * 2 + 1] = dg;
+          }
         }
       }
     }
@@ -420,7 +413,7 @@ bool make_map(CUtensorMap* m, const void* base, long inner, long outer, long ld,
 template <int kBN, int kEpi>
 cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tbm, const Args& a, int grid, cudaStream_t s) {
   const size_t smem = 1024 + (size_t)kStages * (kBM * kBK * 2 + kBN * kBK * 2) +
-                      (size_t)4 * 32 * Staging<kBN>::kSt * 2 + sizeof(Bars);
+                      (size_t)kEpiWarps * 32 * Staging<kBN / 2>::kSt * 2 + sizeof(Bars);
   auto k = gemm_tc_kernel<kBN, kEpi>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

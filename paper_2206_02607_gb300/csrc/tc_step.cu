@@ -59,17 +59,25 @@ constexpr int kGroups = 4;
 constexpr int kTPU = 1;                  // threads per hidden unit
 constexpr int kGT = 128 * kTPU;          // threads per group
 constexpr int kThreads = kGroups * kGT;
-constexpr int kS0 = kTcTileS0;           // samples per forward tile at GN iteration 0 (4 channels)
+// Samples per forward tile at GN iteration 0 (4 channels): kTcTileS0 when the
+// operands carry hi and lo parts (2 x 4 x kTcTileS0 columns fill one N = 64 UMMA),
+// twice that with hi parts only (CROM_PREC_F16).
+template <bool kLoP>
+__host__ __device__ constexpr int tile_s0() {
+  return kLoP ? kTcTileS0 : 2 * kTcTileS0;
+}
 // Samples per tile at later iterations (2 channels): kTcTileS1Large or
-// kTcTileS1Small, a template parameter of the kernel chosen per context
-// (crom_autotune measures both).
-constexpr int kSMax = 2 * kTcTileS0;
-static_assert(kTcTileS1Large <= kSMax && 2 * kS0 <= kSMax, "sample slots");
+// kTcTileS1Small (doubled with hi parts only), a template parameter of the kernel
+// chosen per context (crom_autotune measures both).
+constexpr int kSMax = 4 * kTcTileS0;  // sample slots of a group
+static_assert(2 * kTcTileS1Large <= kSMax && 2 * tile_s0<false>() <= kSMax, "sample slots");
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kGroupCols = 128;     // TMEM columns per group
-// Accumulator in columns 0..63 (forward: W h_hi in 0..31, W h_lo in 32..63;
-// reverse: hi part in 0..kS-1, lo part in kS..2kS-1; projections: 16 columns);
-// s'(z_l) of hidden layers l = 2..L (<= 5), kS columns each, from column 64.
+// Accumulator in columns 0..63 (forward: W h_hi in 0..31, W h_lo in 32..63, or
+// W h_hi in 0..63 with hi parts only; reverse: hi part in 0..kS-1, lo part in
+// kS..2kS-1; projections: 16 columns); s'(z_l) of hidden layers l = 2..L (<= 5)
+// from column 64, kS FP32 columns each, or kS / 2 columns of f16 pairs with hi
+// parts only (whose tiles hold twice the samples).
 constexpr uint32_t kAcc = 0;
 constexpr uint32_t kSig = 64;
 // Forward operand block of a group: 64 columns, the bf16 hi parts of the (channel,
@@ -137,8 +145,12 @@ struct __align__(16) Group {
   float xs[2][kSMax];
   float rho[kSMax];
   float zero[kSMax];
-  float jt[2][kSMax][16];  // Jacobian rows from the hi and the lo parts of delta_1
+  // Jacobian rows from the hi (rows 0..15) and the lo (rows 16..31) parts of delta_1,
+  // or rows 0..31 of up to 32 samples with hi parts only (jrow)
+  float jt[2][16][16];
 };
+// Row s of the Jacobian rows from part `part` (0 = hi, 1 = lo) of delta_1.
+__device__ __forceinline__ float* jrow(Group* G, int part, int s) { return &G->jt[0][0][0] + (part * 16 + s) * 16; }
 
 __device__ __forceinline__ void group_sync(int g) {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGT) : "memory");
@@ -156,24 +168,64 @@ __device__ __forceinline__ bool group_sync_and(int g, bool pred) {
   return r != 0;
 }
 
-// kC (4 or 8) consecutive columns of row k as a bf16 hi/lo pair: the hi parts go
+// kC (4 or 8) consecutive columns of row k as an f16 hi/lo pair: the hi parts go
 // to columns n_hi.., the lo parts to n_lo.. of the MN-major operand H (columns
-// >= 64 lie in the next 64-column block); one 2 kC-byte chunk each.
-template <int kC>
+// >= 64 lie in the next 64-column block); one 2 kC-byte chunk each.  Without lo
+// parts (kLoP false) only the hi chunk is written.
+template <int kC, bool kLoP>
 __device__ __forceinline__ void split_store(uint8_t* H, int k, int n_hi, int n_lo, const float* v) {
   uint32_t hi[kC / 2], lo[kC / 2];
 #pragma unroll
   for (int j = 0; j < kC / 2; ++j) {
     hi[j] = pack_f16(v[2 * j], v[2 * j + 1]);
-    lo[j] = pack_f16_lo(hi[j], v[2 * j], v[2 * j + 1]);
+    if (kLoP) lo[j] = pack_f16_lo(hi[j], v[2 * j], v[2 * j + 1]);
   }
   if constexpr (kC == 8) {
     *reinterpret_cast<uint4*>(H + mn_offset(k, n_hi)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    *reinterpret_cast<uint4*>(H + mn_offset(k, n_lo)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    if (kLoP) *reinterpret_cast<uint4*>(H + mn_offset(k, n_lo)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
   } else {
     static_assert(kC == 4, "chunks of 4 or 8 columns");
     *reinterpret_cast<uint2*>(H + mn_offset(k, n_hi)) = make_uint2(hi[0], hi[1]);
-    *reinterpret_cast<uint2*>(H + mn_offset(k, n_lo)) = make_uint2(lo[0], lo[1]);
+    if (kLoP) *reinterpret_cast<uint2*>(H + mn_offset(k, n_lo)) = make_uint2(lo[0], lo[1]);
+  }
+}
+
+// s'(z) of kC = 8 samples of hidden layer l + 2 in tensor memory (region of kSS
+// samples per layer from column kSig): FP32 columns with hi/lo operands; with hi
+// parts only (tiles of twice the samples) f16 pairs, sample 2i in the low half of
+// column i, rounded like the f16 deltas they multiply.
+template <bool kLoP>
+__device__ __forceinline__ void store_sig(uint32_t tb, uint32_t lb, int kSS, int l, int slot, const float (&sg)[8]) {
+  if constexpr (kLoP) {
+    tmem_st8(taddr(tb, lb, kSig + l * kSS + slot), sg);
+  } else {
+    const float pk[4] = {__uint_as_float(pack_f16(sg[0], sg[1])), __uint_as_float(pack_f16(sg[2], sg[3])),
+                         __uint_as_float(pack_f16(sg[4], sg[5])), __uint_as_float(pack_f16(sg[6], sg[7]))};
+    tmem_st4(taddr(tb, lb, kSig + l * (kSS / 2) + slot / 2), pk);
+  }
+}
+// Issues the load of store_sig's columns; unpack_sig (after tmem_ld_wait) gives the values.
+template <bool kLoP>
+__device__ __forceinline__ void load_sig(uint32_t tb, uint32_t lb, int kSS, int l, int slot, float (&sg)[8]) {
+  if constexpr (kLoP) {
+    tmem_ld8(taddr(tb, lb, kSig + l * kSS + slot), sg);
+  } else {
+    float pk[4];
+    tmem_ld4(taddr(tb, lb, kSig + l * (kSS / 2) + slot / 2), pk);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) sg[i] = pk[i];
+  }
+}
+__device__ __forceinline__ void f16x2_to_f32(uint32_t v, float& a, float& b) {
+  asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\tcvt.f32.f16 %0, l;\n\tcvt.f32.f16 %1, h;\n\t}"
+      : "=f"(a), "=f"(b)
+      : "r"(v));
+}
+template <bool kLoP>
+__device__ __forceinline__ void unpack_sig(float (&sg)[8]) {
+  if constexpr (!kLoP) {
+#pragma unroll
+    for (int i = 3; i >= 0; --i) f16x2_to_f32(__float_as_uint(sg[i]), sg[2 * i], sg[2 * i + 1]);
   }
 }
 
@@ -327,10 +379,11 @@ __device__ __forceinline__ void two_sum_into(float& s, float& comp, float p) {
 
 // Exact product-sum of up to kSMax FP32 pairs: two-product (a*b = p + e exactly by
 // one FMA) and a compensated (two-sum) accumulation of the p, in FP32; returned in
-// FP64.  Relative error ~2^-46, well below the FP32 inputs' own rounding.  Each
-// factor is the FP32 sum of two parts (a0 + a1, b0 + b1).  Four interleaved
-// accumulators (element i goes to i mod 4) shorten the dependent chain; they are
-// merged by two-sums in a fixed order.
+// FP64.  Relative error ~2^-46, well below the FP32 inputs' own rounding.  A factor
+// is the FP32 sum of two parts (a0 + a1) where kTA (kTB) is set, else a0 (b0).
+// Four interleaved accumulators (element i goes to i mod 4) shorten the dependent
+// chain; they are merged by two-sums in a fixed order.
+template <bool kTA, bool kTB>
 __device__ __forceinline__ double dot_exact(const float* a0, const float* a1, int sa, const float* b0,
                                             const float* b1, int sb, int n) {
   float s[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
@@ -339,7 +392,8 @@ __device__ __forceinline__ double dot_exact(const float* a0, const float* a1, in
     for (int k = 0; k < 4; ++k) {
       const int i = i0 + k;
       if (i < n) {
-        const float x = __fadd_rn(a0[i * sa], a1[i * sa]), y = __fadd_rn(b0[i * sb], b1[i * sb]);
+        const float x = kTA ? __fadd_rn(a0[i * sa], a1[i * sa]) : a0[i * sa];
+        const float y = kTB ? __fadd_rn(b0[i * sb], b1[i * sb]) : b0[i * sb];
         const float p = __fmul_rn(x, y);  // rounded product (kept out of FMA contraction)
         const float e = fmaf(x, y, -p);   // its exact rounding error
         two_sum_into(s[k], comp[k], p);
@@ -395,7 +449,7 @@ __device__ __forceinline__ void sig1(const Lane& c, const Group* G, float cc, in
 // kSm..2kSm-1), the Jacobian projection and these samples' share of J^T J, J^T rho
 // (and rho^T rho for the line search).  s'(z_l) of hidden layer l + 2 is read from
 // TMEM column kSig + l * kSS + slot.
-template <int kM, int kSm, int kSS>
+template <int kM, int kSm, int kSS, bool kLoP>
 __device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int ns, Own& o) {
   constexpr int kPer = kSm / kTPU;
   constexpr int kC = kPer < 8 ? kPer : 8;
@@ -405,14 +459,16 @@ __device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int n
   // ---------------- reverse pass
 #pragma unroll 1
   for (int h8 = 0; h8 < kPer; h8 += kC) {
+    static_assert(kC == 8, "s'(z) is kept in chunks of 8 samples");
     float sg[kC];
-    tmem_ldc(taddr(tb, lb, kSig + (p.L - 2) * kSS + s0 + h8), sg);
+    load_sig<kLoP>(tb, lb, kSS, p.L - 2, s0 + h8, sg);
     tmem_ld_wait();
+    unpack_sig<kLoP>(sg);
 #pragma unroll
     for (int i = 0; i < kC; ++i) sg[i] *= c.wos;
-    split_store<kC>(c.H, u, s0 + h8, kSm + s0 + h8, sg);  // delta_L
+    split_store<kC, kLoP>(c.H, u, s0 + h8, kSm + s0 + h8, sg);  // delta_L
   }
-  constexpr uint32_t id_bwd = idesc_f16(128, 2 * kSm, true, true, false);
+  constexpr uint32_t id_bwd = idesc_f16(128, kLoP ? 2 * kSm : kSm, true, true, false);
   for (int l = p.L - 2; l >= 0; --l) {
     // accumulator = W_{l+2}^T delta_{l+2}; times s'(z_{l+1}) gives delta_{l+1}
     if (!stage<kStageBwd>(c, l, id_bwd)) return false;
@@ -421,26 +477,34 @@ __device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int n
     for (int h8 = 0; h8 < kPer; h8 += kC) {
       float v[kC], w[kC], sg[kC];
       tmem_ldc(taddr(tb, lb, kAcc + s0 + h8), v);
-      tmem_ldc(taddr(tb, lb, kAcc + kSm + s0 + h8), w);
-      if (l > 0) tmem_ldc(taddr(tb, lb, kSig + (l - 1) * kSS + s0 + h8), sg);
+      if (kLoP) tmem_ldc(taddr(tb, lb, kAcc + kSm + s0 + h8), w);
+      if (l > 0) load_sig<kLoP>(tb, lb, kSS, l - 1, s0 + h8, sg);
       else sig1<kM, kC>(c, G, cc, s0 + h8, sg);
       tmem_ld_wait();
+      if (l > 0) unpack_sig<kLoP>(sg);
+      if (kLoP) {
 #pragma unroll
-      for (int i = 0; i < kC; i += 2)
-        unpk2(mul2(add2(pk2(v[i], v[i + 1]), pk2(w[i], w[i + 1])), pk2(sg[i], sg[i + 1])), v[i], v[i + 1]);
-      split_store<kC>(c.H, u, s0 + h8, kSm + s0 + h8, v);
+        for (int i = 0; i < kC; i += 2)
+          unpk2(mul2(add2(pk2(v[i], v[i + 1]), pk2(w[i], w[i + 1])), pk2(sg[i], sg[i + 1])), v[i], v[i + 1]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < kC; i += 2) unpk2(mul2(pk2(v[i], v[i + 1]), pk2(sg[i], sg[i + 1])), v[i], v[i + 1]);
+      }
+      split_store<kC, kLoP>(c.H, u, s0 + h8, kSm + s0 + h8, v);
     }
   }
   // J[s][j] = sum_u W_1q[u][j] delta_1[u][s]: rows s (hi) and kSm + s (lo)
+  constexpr int kRows = kLoP ? 2 * kSm : kSm;
   if (!stage<kStageProj>(c, 0, 0)) return false;
-  if (c.gw < (2 * kSm + 31) / 32) {
+  if (c.gw < (kRows + 31) / 32) {
     float v[16];
     tmem_ld16(taddr(tb, lb, kAcc), v);
     tmem_ld_wait();
     const int part = u / kSm, s = u % kSm;
-    if (u < 2 * kSm) {
+    if (u < kRows) {
+      float* jr = jrow(G, part, s);
 #pragma unroll
-      for (int j = 0; j < 15; ++j) G->jt[part][s][j] = v[j + 1] * p.sri;
+      for (int j = 0; j < 15; ++j) jr[j] = v[j + 1] * p.sri;
     }
   }
   group_sync(c.g);
@@ -449,12 +513,12 @@ __device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int n
   for (int e = 0; e < 2; ++e) {
     const int ea = o.ea[e], eb = o.eb[e];
     if (ea >= 0) {
-      const float* a0 = &G->jt[0][0][ea];
-      const float* a1 = &G->jt[1][0][ea];
-      if (eb >= 0) o.acc[e] += dot_exact(a0, a1, 16, &G->jt[0][0][eb], &G->jt[1][0][eb], 16, ns);
-      else o.acc[e] += dot_exact(a0, a1, 16, G->rho, G->zero, 1, ns);
+      const float* a0 = jrow(G, 0, 0) + ea;
+      const float* a1 = jrow(G, 1, 0) + ea;
+      if (eb >= 0) o.acc[e] += dot_exact<kLoP, kLoP>(a0, a1, 16, jrow(G, 0, 0) + eb, jrow(G, 1, 0) + eb, 16, ns);
+      else o.acc[e] += dot_exact<kLoP, false>(a0, a1, 16, G->rho, G->zero, 1, ns);
     } else if (ea == -3) {
-      o.acc[e] += dot_exact(G->rho, G->zero, 1, G->rho, G->zero, 1, ns);  // rho^T rho for the line search
+      o.acc[e] += dot_exact<false, false>(G->rho, G->zero, 1, G->rho, G->zero, 1, ns);  // rho^T rho for the line search
     }
   }
   return true;
@@ -466,13 +530,14 @@ __device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int n
 // (coordinates xs, residual rho, and the TMEM columns kSig + l * kSS + slot that keep
 // s'(z) of hidden layer l + 2 for the reverse pass), so that two tiles of iteration
 // 0 can share one reverse pass.
-template <int kM, int kSm, bool kFirst, int kSS>
+template <int kM, int kSm, bool kFirst, int kSS, bool kLoP>
 __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j0, int so, int ns, float alpha) {
   constexpr int kCh = kFirst ? 2 + kM : 2;  // iteration 0: v, dx_1..dx_m, Lap; later: v(q^(k)), diff
   constexpr int kN = kCh * kSm;             // hi columns 0..kN-1, lo columns kLo..kLo+kN-1
   constexpr int kPer = kSm / kTPU;          // samples of this thread
   constexpr int kC = kPer < 8 ? kPer : 8;    // samples per chunk
-  static_assert(kN <= kLo && kPer % kC == 0 && kC % 4 == 0 && kSS >= kSm && kSig + 4 * kSS <= kGroupCols,
+  static_assert(kN <= (kLoP ? kLo : 64) && kPer % kC == 0 && kC == 8 && kSS >= kSm &&
+                    kSig + 4 * (kLoP ? kSS : kSS / 2) <= kGroupCols,
                 "tile shape");
   Group* G = c.G;
   const Shared* S = c.S;
@@ -514,14 +579,14 @@ __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) {
         const int n = ch * kSm + s0 + h8;
-        split_store<kC>(c.H, u, n, kLo + n, v[ch]);
+        split_store<kC, kLoP>(c.H, u, n, kLo + n, v[ch]);
       }
     }
   }
   // ---------------- hidden layers 2..L (tensor cores): one UMMA per K slice whose N
-  // spans the hi columns (0..kLo-1) and the used lo columns (kLo..kLo+kN-1), rounded
-  // up to a multiple of 16
-  constexpr uint32_t id_fwd = idesc_f16(128, kLo + ((kN + 15) & ~15), false, true, false);
+  // spans the hi columns (0..kLo-1) and the used lo columns (kLo..kLo+kN-1), or the
+  // kN hi columns alone, rounded up to a multiple of 16
+  constexpr uint32_t id_fwd = idesc_f16(128, (kLoP ? kLo : 0) + ((kN + 15) & ~15), false, true, false);
   for (int l = 0; l < p.L - 1; ++l) {
     if (!stage<kStageFwd>(c, l, id_fwd)) return false;
     const float bias = S->bh[l][u];
@@ -531,23 +596,25 @@ __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j
 #pragma unroll
       for (int ch = 0; ch < kCh; ++ch) {
         tmem_ldc(taddr(tb, lb, kAcc + ch * kSm + s0 + h8), v[ch]);
-        tmem_ldc(taddr(tb, lb, kAcc + kLo + ch * kSm + s0 + h8), w[ch]);
+        if (kLoP) tmem_ldc(taddr(tb, lb, kAcc + kLo + ch * kSm + s0 + h8), w[ch]);
       }
       tmem_ld_wait();
+      if (kLoP) {
 #pragma unroll
-      for (int ch = 0; ch < kCh; ++ch)
+        for (int ch = 0; ch < kCh; ++ch)
 #pragma unroll
-        for (int i = 0; i < kC; i += 2)
-          unpk2(add2(pk2(v[ch][i], v[ch][i + 1]), pk2(w[ch][i], w[ch][i + 1])), v[ch][i], v[ch][i + 1]);
+          for (int i = 0; i < kC; i += 2)
+            unpk2(add2(pk2(v[ch][i], v[ch][i + 1]), pk2(w[ch][i], w[ch][i + 1])), v[ch][i], v[ch][i + 1]);
+      }
 #pragma unroll
       for (int i = 0; i < kC; i += 2) unpk2(add2(pk2(v[0][i], v[0][i + 1]), pk2(bias, bias)), v[0][i], v[0][i + 1]);
       act<kM, kFirst, kCh, kC>(v, sg, c.dsc, c.dsci);
-      tmem_stc(taddr(tb, lb, kSig + l * kSS + so + s0 + h8), sg);
+      store_sig<kLoP>(tb, lb, kSS, l, so + s0 + h8, sg);
       if (l < p.L - 2) {
 #pragma unroll
         for (int ch = 0; ch < kCh; ++ch) {
           const int n = ch * kSm + s0 + h8;
-          split_store<kC>(c.H, u, n, kLo + n, v[ch]);
+          split_store<kC, kLoP>(c.H, u, n, kLo + n, v[ch]);
         }
       } else {
         // output layer on the CUDA cores, in FP32 from h_L itself: this warp's share
@@ -613,17 +680,17 @@ __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j
 // One tile of kSm samples of one GN iteration k >= 1: forward pass, PDE update /
 // residual, reverse pass, Jacobian projection and this tile's share of J^T J and
 // J^T rho; or, for a line-search trial (kValueOnly), the forward pass and rho^T rho.
-template <int kM, int kSm, bool kValueOnly = false>
+template <int kM, int kSm, bool kLoP, bool kValueOnly = false>
 __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, int t, int ns, float alpha, Own& o) {
-  if (!forward_tile<kM, kSm, false, kSm>(c, p, o0 + t * kSm, 0, ns, alpha)) return false;
+  if (!forward_tile<kM, kSm, false, kSm, kLoP>(c, p, o0 + t * kSm, 0, ns, alpha)) return false;
   if constexpr (kValueOnly) {  // line-search trial: only sum_j rho_j^2 is needed
     group_sync(c.g);
 #pragma unroll
     for (int e = 0; e < 2; ++e)
-      if (o.ea[e] == -3) o.acc[e] += dot_exact(c.G->rho, c.G->zero, 1, c.G->rho, c.G->zero, 1, ns);
+      if (o.ea[e] == -3) o.acc[e] += dot_exact<false, false>(c.G->rho, c.G->zero, 1, c.G->rho, c.G->zero, 1, ns);
     return true;
   } else {
-    return reverse_tile<kM, kSm, kSm>(c, p, ns, o);
+    return reverse_tile<kM, kSm, kSm, kLoP>(c, p, ns, o);
   }
 }
 
@@ -633,14 +700,15 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
 // the four-channel forward pass needs narrow tiles to fit the 32 hi columns of one
 // N = 64 UMMA, the
 // reverse pass does not.
-template <int kM>
+template <int kM, bool kLoP>
 __device__ __forceinline__ bool run_pair(Lane& c, const StepParams& p, int o0, int t, int ns, float alpha, Own& o) {
+  constexpr int kS0 = tile_s0<kLoP>();
   constexpr int kSS = 2 * kS0;
   const int j0 = o0 + t * kSS;
-  if (!forward_tile<kM, kS0, true, kSS>(c, p, j0, 0, min(ns, kS0), alpha)) return false;
-  if (ns <= kS0) return reverse_tile<kM, kS0, kSS>(c, p, ns, o);
-  if (!forward_tile<kM, kS0, true, kSS>(c, p, j0 + kS0, kS0, ns - kS0, alpha)) return false;
-  return reverse_tile<kM, kSS, kSS>(c, p, ns, o);
+  if (!forward_tile<kM, kS0, true, kSS, kLoP>(c, p, j0, 0, min(ns, kS0), alpha)) return false;
+  if (ns <= kS0) return reverse_tile<kM, kS0, kSS, kLoP>(c, p, ns, o);
+  if (!forward_tile<kM, kS0, true, kSS, kLoP>(c, p, j0 + kS0, kS0, ns - kS0, alpha)) return false;
+  return reverse_tile<kM, kSS, kSS, kLoP>(c, p, ns, o);
 }
 
 // Layer-1 constants of the tile passes at the point q: c1 = b_1 + W_1q q (value
@@ -671,8 +739,9 @@ __device__ __forceinline__ void set_layer1(Lane& c, const StepParams& p, Group* 
   G->dz1[c.u] = dzf * c.dsc;
 }
 
-template <int kM, int kS1>
+template <int kM, int kS1, bool kLoP>
 __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
+  constexpr int kS0 = tile_s0<kLoP>();
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x;
@@ -786,11 +855,11 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
       if (it == 0) {
         const int nt = (M + 2 * kS0 - 1) / (2 * kS0);
         for (int t = 0; t < nt && ok; ++t)
-          ok = run_pair<kM>(c, p, o0, t, min(2 * kS0, M - t * 2 * kS0), alpha, own);
+          ok = run_pair<kM, kLoP>(c, p, o0, t, min(2 * kS0, M - t * 2 * kS0), alpha, own);
       } else {
         const int nt = (M + kS1 - 1) / kS1;
         for (int t = 0; t < nt && ok; ++t)
-          ok = run_tile<kM, kS1>(c, p, o0, t, min(kS1, M - t * kS1), alpha, own);
+          ok = run_tile<kM, kS1, kLoP>(c, p, o0, t, min(kS1, M - t * kS1), alpha, own);
       }
       if (!ok) break;
       const int R = r + 1;
@@ -838,7 +907,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
           own.acc[0] = own.acc[1] = 0.0;
           const int nt = (M + kS1 - 1) / kS1;
           for (int t = 0; t < nt && ok; ++t)
-            ok = run_tile<kM, kS1, true>(c, p, o0, t, min(kS1, M - t * kS1), alpha, own);
+            ok = run_tile<kM, kS1, kLoP, true>(c, p, o0, t, min(kS1, M - t * kS1), alpha, own);
           if (!ok) break;
 #pragma unroll
           for (int e = 0; e < 2; ++e)
@@ -916,7 +985,7 @@ size_t tc_step_smem_bytes(int img_bytes) {
          kGroups * sizeof(Group);
 }
 
-cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst, double* q,
+cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int lo_parts, int n_inst, double* q,
                            const float* alpha, const float* vel, const int* s_off, const float* samples,
                            int n_samples, int max_samples, int* status, cudaStream_t s) {
   if ((size_t)n_inst > ctx->order_cap) {
@@ -982,8 +1051,15 @@ cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int n_inst
   };
   constexpr int kLarge = kTcTileS1Large, kSmall = kTcTileS1Small;
   const bool small_tiles = ctx->tc_tile_s1 == kSmall;
-  if (ctx->desc.m == 2) return small_tiles ? launch(step_tc_kernel<2, kSmall>) : launch(step_tc_kernel<2, kLarge>);
-  return small_tiles ? launch(step_tc_kernel<1, kSmall>) : launch(step_tc_kernel<1, kLarge>);
+  if (lo_parts) {
+    if (ctx->desc.m == 2)
+      return small_tiles ? launch(step_tc_kernel<2, kSmall, true>) : launch(step_tc_kernel<2, kLarge, true>);
+    return small_tiles ? launch(step_tc_kernel<1, kSmall, true>) : launch(step_tc_kernel<1, kLarge, true>);
+  }
+  // hi parts only: tiles of twice the samples for the same UMMA width
+  if (ctx->desc.m == 2)
+    return small_tiles ? launch(step_tc_kernel<2, 2 * kSmall, false>) : launch(step_tc_kernel<2, 2 * kLarge, false>);
+  return small_tiles ? launch(step_tc_kernel<1, 2 * kSmall, false>) : launch(step_tc_kernel<1, 2 * kLarge, false>);
 }
 
 }  // namespace crom

@@ -253,6 +253,17 @@ __global__ void gather_kernel(const float* snaps, const int* pt_idx, const float
   for (int j = 0; j < r; ++j) in[n * ld + m + j] = q[(long)b * r + j];
   target[n] = snaps[(long)b * P + node];
 }
+// The tensor-core pass's inputs: the points' coordinates x [B*S][m] (the latent part
+// of the input layer is formed per snapshot) and the targets.
+__global__ void gather_x_kernel(const float* snaps, const int* pt_idx, const float* coords, int B, int S, int P,
+                                int m, float* x, float* target) {
+  const long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (n >= (long)B * S) return;
+  const int b = (int)(n / S);
+  const int node = pt_idx[n];
+  for (int k = 0; k < m; ++k) x[n * m + k] = coords[(long)node * m + k];
+  target[n] = snaps[(long)b * P + node];
+}
 
 // Output layer g = w_out . h + b_out, residual and dL/dg = 2 (g - t) / N; per-block
 // partial sums of the squared residual (FP64).
@@ -489,14 +500,13 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
   // ---- encoder forward: q_b
   if ((e = trainer_encode(t, B, snaps, t->q, s)) != cudaSuccess) return e;
   // ---- decoder forward and reverse pass on the sampled points
-  gather_kernel<<<blocks(N, 256), 256, 0, s>>>(snaps, pt_idx, coords, t->q, B, S, P, m, r, t->in0, t->target);
-  const float* din = t->din;
-  int din_ld = m + r;
-  if (t->precision == CROM_PREC_BF16_MIXED) {
+  const bool tc = t->precision == CROM_PREC_BF16_MIXED;
+  if (tc) {
+    gather_x_kernel<<<blocks(N, 256), 256, 0, s>>>(snaps, pt_idx, coords, B, S, P, m, t->tc.xin, t->target);
+    // the decoder pass also leaves dL/dq_b in t->dq
     if ((e = trainer_decoder_tc(t, loss_out, t->num_sms, s)) != cudaSuccess) return e;
-    din = t->tc.din;
-    din_ld = trainer_tc_din_ld();
   } else {
+    gather_kernel<<<blocks(N, 256), 256, 0, s>>>(snaps, pt_idx, coords, t->q, B, S, P, m, r, t->in0, t->target);
     const float* hin = t->in0;
     int kin = m + r;
     for (int l = 0; l < L; ++l) {
@@ -548,7 +558,7 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
       dnext = tmp;
     }
   }
-  dq_kernel<<<dim3(B, r), 256, 0, s>>>(din, din_ld, B, S, m, r, t->dq);
+  if (!tc) dq_kernel<<<dim3(B, r), 256, 0, s>>>(t->din, m + r, B, S, m, r, t->dq);
   // ---- encoder reverse pass
   // dense 2: gW2 = dq^T h1, gb2 = sum dq, dz1 = (dq W2) * s'(z1)
   const int Ll = t->lens.back();

@@ -6,15 +6,18 @@
 // With hidden layers h = 0..L-1 (H[h] = ELU(z_h), z_0 = W_0 [x; q] + b_0,
 // z_h = W_h H[h-1] + b_h), output g = w_out . H[L-1] + b_out and
 // loss = mean (g - f)^2 over the B*S sampled points:
-//   forward:  H[0] on the CUDA cores (K = m + r is too short for the tensor cores);
+//   forward:  H[0] on the CUDA cores: the latent part W_0q q_b + b_0 is one vector per
+//             snapshot, so a point costs m FMAs per unit;
 //             H[h] = ELU(H[h-1] W_h^T + b_h) by the GEMM's bias + ELU epilogue;
 //             the last layer's epilogue also forms g, the residual, dL/dg and
 //             delta[L-1] = dL/dg w_out s'(z_{L-1}), with the column sums that give
 //             the gradients of w_out, b_out and b_{L-1};
 //   backward: for h = L-1 .. 1: dW_h = delta[h]^T H[h-1] (K = B*S, split over CTAs,
 //             the splits added in a fixed order) and delta[h-1] = (delta[h] W_h) s'(z_{h-1})
-//             with its column sums (db_{h-1}); then dW_0 = delta[0]^T [x; q] on the
-//             CUDA cores and din = delta[0] W_0 (GEMM, N padded to 64) for the encoder.
+//             with its column sums (db_{h-1}); then one pass over delta[0] forms, per
+//             snapshot, D_b = sum of its rows and their x-weighted sums, from which
+//             dW_0, db_0 and the encoder's dL/dq_b = W_0q^T D_b follow (the latent
+//             inputs are constant over a snapshot).
 // s'(z) is taken from h = ELU(z): 1 where h > 0, else h + 1 = e^z.  Every reduction
 // runs in a fixed order, so a step is deterministic.
 #include <cuda_bf16.h>
@@ -28,8 +31,6 @@ namespace crom {
 namespace {
 
 constexpr int kSplitsW = 64;      // K splits of the weight-gradient GEMMs
-constexpr int kGw0Chunks = 512;   // row chunks of the input-layer weight gradient
-constexpr int kDinCols = 64;      // din = delta[0] W_0 padded to 64 columns
 
 inline unsigned nblk(long n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -38,90 +39,202 @@ __device__ __forceinline__ uint16_t bf16_bits(float f) {
   return *reinterpret_cast<uint16_t*>(&h);
 }
 __device__ __forceinline__ float bf16_val(uint16_t u) { return __uint_as_float((uint32_t)u << 16); }
+// ELU with e^z - 1 from the hardware 2^x, as the GEMM epilogues form it (relative
+// error ~2^-22, far below the bf16 rounding of the stored activations).
+__device__ __forceinline__ float elu_fast(float z) {
+  if (z > 0.f) return z;
+  float e;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(z * 1.4426950408889634f));
+  return e - 1.f;
+}
 
-// bf16 copies of the hidden matrices W_1..W_{L-1} ([w][w] each) and of W_0 transposed
-// into a [w][64] block (row u holds W_0[u][0..m+r), zeros after).
-__global__ void weights_bf16_kernel(const float* params, const long* off_w, int L, int w, int kin, uint16_t* wh,
-                                    uint16_t* w0p) {
+// bf16 copies of the hidden matrices W_1..W_{L-1} ([w][w] each).
+__global__ void weights_bf16_kernel(const float* params, const long* off_w, int L, int w, uint16_t* wh) {
   const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
   const long per = (long)w * w;
   if (e < (long)(L - 1) * per) {
     const int h = 1 + (int)(e / per);
     wh[e] = bf16_bits(params[off_w[h] + e % per]);
   }
-  if (e < (long)w * kDinCols) {
-    const int u = (int)(e / kDinCols), j = (int)(e % kDinCols);
-    w0p[e] = bf16_bits(j < kin ? params[off_w[0] + (long)u * kin + j] : 0.f);
-  }
 }
 
-// H[0][n][u] = ELU(W_0[u] . in[n] + b_0[u]) in bf16: one thread per unit, 32 rows per
-// block (the rows' inputs staged in shared memory); the K = m + r <= 32 loops are
-// unrolled to their bound and predicated, so W_0's row stays in registers.
-constexpr int kRows0 = 32;
-__global__ void layer0_fwd_kernel(const float* in, long N, int kin, const float* W0, const float* b0, int w,
-                                  uint16_t* H) {
-  __shared__ float xs[kRows0][33];
-  const int u = threadIdx.x;
+// The latent part of the input layer is the same for every point of a snapshot:
+// c0[b][u] = b_0[u] + sum_j W_0[u][m + j] q_b[j] (FP32, in order of j).
+__global__ void layer0_const_kernel(const float* W0, const float* b0, const float* q, int m, int r, int w,
+                                    float* c0) {
+  const int b = blockIdx.x, u = threadIdx.x;
+  if (u >= w) return;
+  const float* wr = W0 + (long)u * (m + r) + m;
+  float z = b0[u];
+  for (int j = 0; j < r; ++j) z = fmaf(wr[j], q[(long)b * r + j], z);
+  c0[(long)b * w + u] = z;
+}
+
+// H[0][n][u] = ELU(c0[b(n)][u] + sum_k W_0[u][k] x_n[k]) in bf16, x [N][m] the
+// points' coordinates: a thread per pair of units, kRows0 rows per block (their
+// coordinates staged in shared memory).
+constexpr int kRows0 = 64;
+__global__ void layer0_fwd_kernel(const float* x_in, long N, int kin, int m, int S, const float* W0, const float* c0,
+                                  int w, uint16_t* H) {
+  __shared__ float xs[kRows0][3];
   const long n0 = (long)blockIdx.x * kRows0;
-  for (int i = threadIdx.x; i < kRows0 * 32; i += blockDim.x) {
-    const long n = n0 + i / 32;
-    const int j = i % 32;
-    xs[i / 32][j] = (n < N && j < kin) ? in[n * kin + j] : 0.f;   // zeros beyond kin
+  for (int i = threadIdx.x; i < kRows0 * 3; i += blockDim.x) {  // zeros beyond m and N
+    const long n = n0 + i / 3;
+    xs[i / 3][i % 3] = (n < N && i % 3 < m) ? x_in[n * m + i % 3] : 0.f;
   }
   __syncthreads();
+  const int u = 2 * threadIdx.x;
   if (u >= w) return;
-  float wr[32];
+  float wa[3], wb[3];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) wr[j] = j < kin ? W0[(long)u * kin + j] : 0.f;
-  const float b = b0[u];
-  for (int i = 0; i < kRows0; ++i) {
-    const long n = n0 + i;
-    if (n >= N) break;
-    float z = b;
+  for (int k = 0; k < 3; ++k) {
+    wa[k] = k < m ? W0[(long)u * kin + k] : 0.f;
+    wb[k] = k < m ? W0[(long)(u + 1) * kin + k] : 0.f;
+  }
+  const long n1 = n0 + kRows0 < N ? n0 + kRows0 : N;
+  long b = n0 / S, nb = (b + 1) * S;  // snapshot of row n and the first row of the next
+  float2 cb = *reinterpret_cast<const float2*>(c0 + b * w + u);
+#pragma unroll 4
+  for (long n = n0; n < n1; ++n) {
+    if (n == nb) {
+      ++b;
+      nb += S;
+      cb = *reinterpret_cast<const float2*>(c0 + b * w + u);
+    }
+    float za = cb.x, zb = cb.y;
+    const float* x = xs[n - n0];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) z = fmaf(wr[j], xs[i][j], z);
-    H[n * w + u] = bf16_bits(z > 0.f ? z : expm1f(z));
+    for (int k = 0; k < 3; ++k) {
+      za = fmaf(wa[k], x[k], za);
+      zb = fmaf(wb[k], x[k], zb);
+    }
+    *reinterpret_cast<uint32_t*>(H + n * w + u) =
+        (uint32_t)bf16_bits(elu_fast(za)) | ((uint32_t)bf16_bits(elu_fast(zb)) << 16);
   }
 }
 
-// dW_0 partials: part[c][u][j] = sum over the rows of chunk c of delta[n][u] in[n][j]
-// (loops over j unrolled to 32 and predicated: the accumulators stay in registers).
-__global__ void gw0_part_kernel(const uint16_t* delta, const float* in, long N, int kin, int w, float* part) {
-  __shared__ float xs[64][33];
-  const int u = threadIdx.x;
-  const long per = (N + gridDim.x - 1) / gridDim.x;
-  const long r0 = (long)blockIdx.x * per, r1 = (r0 + per < N ? r0 + per : N);
-  float acc[32];
+// Input-layer moments of delta_0 per chunk of a snapshot's rows: part[b][c][u][0] =
+// sum_n delta_0[n][u], part[b][c][u][1 + k] = sum_n delta_0[n][u] x_n[k] over rows
+// b S + c R .. (R = kRowsB), FP32 in row order.  A thread per pair of units, one block
+// per (chunk, snapshot).  With D[b][u] = sum over snapshot b of delta_0[n][u] the
+// input layer's gradients need nothing else: dW_0[u][k] (k < m) is the sum of the
+// x-moments, dW_0[u][m + j] = sum_b D[b][u] q_b[j], db_0[u] = sum_b D[b][u] and the
+// encoder's dL/dq_b[j] = sum_u W_0[u][m + j] D[b][u].
+constexpr int kRowsB = 256;
+__global__ void layer0_bwd_part_kernel(const uint16_t* delta, const float* x_in, int m, int S, int w,
+                                       float* part) {
+  __shared__ float xs[kRowsB][3];
+  const int b = blockIdx.y, cidx = blockIdx.x;
+  const long r0 = (long)b * S + (long)cidx * kRowsB;
+  const int nr = min(kRowsB, S - cidx * kRowsB);
+  for (int i = threadIdx.x; i < nr * 3; i += blockDim.x)  // zeros beyond m
+    xs[i / 3][i % 3] = i % 3 < m ? x_in[(r0 + i / 3) * m + i % 3] : 0.f;
+  __syncthreads();
+  const int u = 2 * threadIdx.x;
+  if (u >= w) return;
+  float sa = 0.f, sb = 0.f, xa[3] = {0.f, 0.f, 0.f}, xb[3] = {0.f, 0.f, 0.f};
+  const uint32_t* dp = reinterpret_cast<const uint32_t*>(delta + r0 * w + u);
+  const int ldw = w / 2;
+  int i = 0;
+  for (; i + 4 <= nr; i += 4) {
+    uint32_t d4[4];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) acc[j] = 0.f;
-  for (long b = r0; b < r1; b += 64) {
-    const int nr = (int)(r1 - b < 64 ? r1 - b : 64);
-    __syncthreads();
-    for (int i = threadIdx.x; i < 64 * 32; i += blockDim.x) {
-      const int row = i / 32, j = i % 32;
-      xs[row][j] = (row < nr && j < kin) ? in[(b + row) * kin + j] : 0.f;
-    }
-    __syncthreads();
-    if (u < w)
-      for (int i = 0; i < nr; ++i) {
-        const float d = bf16_val(delta[(b + i) * w + u]);
+    for (int k = 0; k < 4; ++k) d4[k] = __ldg(dp + (long)(i + k) * ldw);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] = fmaf(d, xs[i][j], acc[j]);
+    for (int k = 0; k < 4; ++k) {
+      const float da = bf16_val((uint16_t)(d4[k] & 0xffffu)), db = bf16_val((uint16_t)(d4[k] >> 16));
+      sa += da;
+      sb += db;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        xa[j] = fmaf(da, xs[i + k][j], xa[j]);
+        xb[j] = fmaf(db, xs[i + k][j], xb[j]);
       }
+    }
   }
-  if (u < w)
+  for (; i < nr; ++i) {
+    const uint32_t d = __ldg(dp + (long)i * ldw);
+    const float da = bf16_val((uint16_t)(d & 0xffffu)), db = bf16_val((uint16_t)(d >> 16));
+    sa += da;
+    sb += db;
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (j < kin) part[((long)blockIdx.x * w + u) * kin + j] = acc[j];
+    for (int j = 0; j < 3; ++j) {
+      xa[j] = fmaf(da, xs[i][j], xa[j]);
+      xb[j] = fmaf(db, xs[i][j], xb[j]);
+    }
+  }
+  float* o = part + (((long)b * gridDim.x + cidx) * w + u) * (1 + m);
+  o[0] = sa;
+  o[1 + m] = sb;
+  for (int k = 0; k < m; ++k) {
+    o[1 + k] = xa[k];
+    o[1 + m + 1 + k] = xb[k];
+  }
+}
+
+// snap[b][u][k] = sum over the chunks of snapshot b of part[b][c][u][k] (FP64, in order).
+__global__ void layer0_bwd_snap_kernel(const float* part, int chunks, int w, int m, float* snap) {
+  const int b = blockIdx.x;
+  const int e = threadIdx.x + blockIdx.y * blockDim.x;  // (u, k)
+  const int per = w * (1 + m);
+  if (e >= per) return;
+  double s = 0.0;
+  for (int c = 0; c < chunks; ++c) s += part[((long)b * chunks + c) * per + e];
+  snap[(long)b * per + e] = (float)s;
+}
+
+// The input layer's gradients from the per-snapshot moments, one warp per output
+// entry (lanes take every 32nd term, FP64, then a fixed butterfly): entries
+// e < w kin are dW_0[u][j] (u = e / kin), the next w are db_0, the last B r are the
+// encoder's dL/dq_b[j].
+__global__ void layer0_grad_kernel(const float* snap, const float* q, const float* W0, int B, int m, int r, int w,
+                                   float* gW0, float* gb0, float* dq) {
+  const int kin = m + r;
+  const long e = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const long nw = (long)w * kin;
+  const int per = w * (1 + m);
+  if (e >= nw + w + (long)B * r) return;  // whole warps leave together
+  double s = 0.0;
+  if (e < nw) {
+    const int u = (int)(e / kin), j = (int)(e % kin);
+    if (j < m) {
+      for (int b = lane; b < B; b += 32) s += snap[(long)b * per + u * (1 + m) + 1 + j];
+    } else {
+      for (int b = lane; b < B; b += 32) s += (double)snap[(long)b * per + u * (1 + m)] * q[(long)b * r + j - m];
+    }
+  } else if (e < nw + w) {
+    const int u = (int)(e - nw);
+    for (int b = lane; b < B; b += 32) s += snap[(long)b * per + u * (1 + m)];
+  } else {
+    const int b = (int)((e - nw - w) / r), j = (int)((e - nw - w) % r);
+    for (int u = lane; u < w; u += 32) s += (double)W0[(long)u * kin + m + j] * snap[(long)b * per + u * (1 + m)];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    if (e < nw) gW0[e] = (float)s;
+    else if (e < nw + w) gb0[e - nw] = (float)s;
+    else dq[e - nw - w] = (float)s;
+  }
 }
 
 // out[e] = sum_p part[p * stride + e], in order of p (FP64 accumulation).
+// Eight loads are issued before their (in-order) additions, so that their latencies
+// overlap.
 __global__ void sum_parts_kernel(const float* part, int nparts, long stride, long n, float* out) {
   const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (e >= n) return;
   double s = 0.0;
-  for (int p = 0; p < nparts; ++p) s += part[(long)p * stride + e];
+  int p = 0;
+  for (; p + 8 <= nparts; p += 8) {
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __ldg(part + (long)(p + k) * stride + e);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += v[k];
+  }
+  for (; p < nparts; ++p) s += part[(long)p * stride + e];
   out[e] = (float)s;
 }
 
@@ -135,8 +248,17 @@ __global__ void colsum_level1_kernel(const float* part, int nparts, int cols, fl
   const int col = blockIdx.x * 32 + threadIdx.x;
   const int p0 = blockIdx.y * kColPer, p1 = min(nparts, p0 + kColPer);
   double acc = 0.0;
-  if (col < cols)
-    for (int p = p0 + threadIdx.y; p < p1; p += 8) acc += part[(long)p * cols + col];
+  if (col < cols) {
+    constexpr int kPer = kColPer / 8;  // parts per thread, loaded before they are added in order
+    float v[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int p = p0 + threadIdx.y + 8 * k;
+      v[k] = p < p1 ? __ldg(part + (long)p * cols + col) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) acc += v[k];
+  }
   red[threadIdx.y][threadIdx.x] = acc;
   __syncthreads();
   if (threadIdx.y == 0 && col < cols) {
@@ -197,18 +319,19 @@ cudaError_t trainer_tc_alloc(crom_trainer* t) {
   };
   auto& c = t->tc;
   c.wh = (uint16_t*)A((size_t)(L - 1) * w * w * 2);
-  c.w0p = (uint16_t*)A((size_t)w * kDinCols * 2);
   for (int h = 0; h < L; ++h) c.H.push_back((uint16_t*)A((size_t)N * w * 2));
   c.d0 = (uint16_t*)A((size_t)N * w * 2);
   c.d1 = (uint16_t*)A((size_t)N * w * 2);
   c.colpart = (float*)A((size_t)tiles_m * 4 * w * 4);
   c.colpart2 = (float*)A((size_t)tiles_m * 4 * w * 4);
   c.rowpart = (float*)A((size_t)tiles_m * 4 * 2 * 4);
-  c.colmid = (float*)A((size_t)std::max<long>((tiles_m * 4 + kColPer - 1) / kColPer * w,
-                                              (long)(kGw0Chunks + kColPer - 1) / kColPer * w * kin) * 4);
+  c.colmid = (float*)A((size_t)(tiles_m * 4 + kColPer - 1) / kColPer * w * 4);
   c.split = (float*)A((size_t)kSplitsW * w * w * 4);
-  c.din = (float*)A((size_t)N * kDinCols * 4);
-  c.gw0part = (float*)A((size_t)kGw0Chunks * w * kin * 4);
+  const int m = t->dec.m;
+  c.xin = (float*)A((size_t)N * m * 4);
+  c.c0 = (float*)A((size_t)t->B * w * 4);
+  c.part0 = (float*)A((size_t)t->B * ((t->S + kRowsB - 1) / kRowsB) * w * (1 + m) * 4);
+  c.snap0 = (float*)A((size_t)t->B * w * (1 + m) * 4);
   c.off_w = (long*)A((size_t)(L + 1) * sizeof(long));
   c.flag = (int*)A(sizeof(int));
   for (void* p : t->owned)
@@ -229,11 +352,11 @@ cudaError_t trainer_decoder_tc(crom_trainer* t, double* loss_out, int num_sms, c
   const float* p = t->params;
   float* gr = t->grads;
   cudaError_t e;
-  weights_bf16_kernel<<<nblk(std::max<long>((long)(L - 1) * w * w, (long)w * kDinCols), 256), 256, 0, s>>>(
-      p, c.off_w, L, w, kin, c.wh, c.w0p);
+  const int m = t->dec.m, r = t->dec.r, B = t->B, S = t->S;
+  weights_bf16_kernel<<<nblk((long)(L - 1) * w * w, 256), 256, 0, s>>>(p, c.off_w, L, w, c.wh);
   // ---- forward
-  layer0_fwd_kernel<<<nblk(N, kRows0), std::max(w, 64), 0, s>>>(t->in0, N, kin, p + lay.dec_w[0], p + lay.dec_b[0], w,
-                                                          c.H[0]);
+  layer0_const_kernel<<<B, w, 0, s>>>(p + lay.dec_w[0], p + lay.dec_b[0], t->q, m, r, w, c.c0);
+  layer0_fwd_kernel<<<nblk(N, kRows0), w / 2, 0, s>>>(c.xin, N, kin, m, S, p + lay.dec_w[0], c.c0, w, c.H[0]);
   for (int h = 1; h < L; ++h) {
     TcGemm g;
     g.M = (int)N;
@@ -305,29 +428,17 @@ cudaError_t trainer_decoder_tc(crom_trainer* t, double* loss_out, int num_sms, c
       g.hprev = c.H[h - 1];
       g.colpart = c.colpart;
       if ((e = tc_gemm(g, num_sms, c.flag, s)) != cudaSuccess) return e;
-      colsum_parts(c.colpart, parts, w, c.colmid, gr + lay.dec_b[h - 1], s);
+      if (h > 1) colsum_parts(c.colpart, parts, w, c.colmid, gr + lay.dec_b[h - 1], s);  // db_0 below
     }
     std::swap(dcur, dnext);
   }
-  // ---- input layer: dW_0 on the CUDA cores, din = delta[0] W_0 on the tensor cores
-  gw0_part_kernel<<<kGw0Chunks, std::max(w, 64), 0, s>>>(dcur, t->in0, N, kin, w, c.gw0part);
-  colsum_parts(c.gw0part, kGw0Chunks, w * kin, c.colmid, gr + lay.dec_w[0], s);
-  TcGemm g;
-  g.M = (int)N;
-  g.N = kDinCols;
-  g.K = w;
-  g.A = dcur;
-  g.lda = w;
-  g.B = c.w0p;  // B(j, u) = W_0[u][j] stored [u][64]
-  g.ldb = kDinCols;
-  g.b_mn = 1;
-  g.epi = kGemmEpiF32;
-  g.out_f32 = c.din;
-  g.ldo = kDinCols;
-  if ((e = tc_gemm(g, num_sms, c.flag, s)) != cudaSuccess) return e;
+  // ---- input layer: per-snapshot moments of delta[0], then dW_0, db_0 and dL/dq
+  const int chunks = (S + kRowsB - 1) / kRowsB;
+  layer0_bwd_part_kernel<<<dim3(chunks, B), w / 2, 0, s>>>(dcur, c.xin, m, S, w, c.part0);
+  layer0_bwd_snap_kernel<<<dim3(B, nblk((long)w * (1 + m), 256)), 256, 0, s>>>(c.part0, chunks, w, m, c.snap0);
+  layer0_grad_kernel<<<nblk(32 * ((long)w * kin + w + (long)B * r), 256), 256, 0, s>>>(
+      c.snap0, t->q, p + lay.dec_w[0], B, m, r, w, gr + lay.dec_w[0], gr + lay.dec_b[0], t->dq);
   return cudaGetLastError();
 }
-
-int trainer_tc_din_ld() { return kDinCols; }
 
 }  // namespace crom

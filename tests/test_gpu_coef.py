@@ -54,7 +54,7 @@ def test_step_per_sample_coefficient_matches_oracle(c, prec_name, res_tol):
         assert res < (res_tol if margin > 1e-4 else max(res_tol, 5e-2)), (i, inc, res, kappa, margin)
 
 
-@pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_F16X2"])
+@pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_F16X2", "CROM_PREC_F16"])
 def test_per_sample_coefficient_equal_to_instance_value_is_the_same_step(c, prec_name):
     """nu(y_j) = alpha_i at every sample of instance i reproduces the per-instance
     step bit for bit (same arithmetic, coefficient read from another index)."""

@@ -19,7 +19,7 @@ out with the FP32 step: its hidden matrices, 512 KB in 16 bits, do not fit the
 shared memory that the tensor-core step keeps them in), and R^{2+15} -> R of width
 128 (the tensor-core step's shape), each trained on the same snapshots.
 
-Latent dynamics: Delta f_j = dt (-a(y_j) . grad g + nu Lap g) at 1024 cell centres,
+Latent dynamics: Delta f_j = dt (-a(y_j) . grad g + nu Lap g) at 4096 cell centres,
 in the decoder's standardised coordinates x' = (x - 1/2) / s (velocity a / s,
 diffusivity nu / s^2), the FOM's dt, 2 Gauss-Newton iterations; all 8 held-out
 trajectories advance together as 8 instances of one batched step.
@@ -35,9 +35,13 @@ from helpers import dev, rel_l2
 
 pytestmark = pytest.mark.gpu
 
-N_SAMPLES = 1024
-# training steps per decoder shape (the narrower decoder needs more to reach the bar)
-TRAIN_STEPS = {"w256_r16": 60000, "w128_r15": 120000}
+# 4096 integration samples: with 1024 the hyper-reduction error alone is ~4e-3 at the
+# final time (measured on the w = 256 decoder: 8.3e-3 vs 5.8e-3 with 4096)
+N_SAMPLES = 4096
+# training steps per decoder shape: the rollout error follows the decoder's fit of
+# the held-out fields (encoder fit at the final time 4.9e-3 after 120k steps on
+# w = 256, 8.9e-3 after 60k)
+TRAIN_STEPS = {"w256_r16": 120000, "w128_r15": 160000}
 ROLLOUT_BAR = 1e-2
 
 
@@ -145,7 +149,7 @@ def test_learned_advdiff_rollout_matches_full_order_solver(c, learned, prec_name
 
     q = dev(L["q0"], torch.float64)
     fit0 = max(rel_l2(f, h[0]) for f, h in zip(fields(q), held))
-    # the same 1024 cell centres for every held-out trajectory; velocity and
+    # the same 4096 cell centres for every held-out trajectory; velocity and
     # diffusivity in the decoder's coordinates
     cells = np.random.default_rng(9).choice(P, size=N_SAMPLES, replace=False)
     vel = gen.cell_velocity(w.ax, w.ay)[cells] / s

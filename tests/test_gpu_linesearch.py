@@ -26,21 +26,22 @@ def c():
     return crom
 
 
-def _run(c, w, dt, gn_iters, line_search):
+def _run(c, w, dt, gn_iters, line_search, prec_name="CROM_PREC_F16X2"):
     import torch
     d = StepInputs(w)
     c.crom_step(make_ctx(w.spec, w.params), d.q, d.alpha, d.s_off, d.samples, d.status, dt=dt, gn_iters=gn_iters,
-                max_samples=d.max_samples, precision=c.CROM_PREC_F16X2, line_search=line_search)
+                max_samples=d.max_samples, precision=getattr(c, prec_name), line_search=line_search)
     torch.cuda.synchronize()
     return d.q.cpu().numpy(), d.status.cpu().numpy()
 
 
-def test_full_steps_accepted_leave_the_step_unchanged(c):
+@pytest.mark.parametrize("prec_name", ["CROM_PREC_F16X2", "CROM_PREC_F16"])
+def test_full_steps_accepted_leave_the_step_unchanged(c, prec_name):
     """At the bench's time step the full GN step always satisfies the decrease
     condition: with one iteration the result is bit-identical to no line search."""
     w = gen.heat2d_batched(n_inst=16, m_lo=20, m_hi=400)
-    qa, sa = _run(c, w, w.dt, 1, 0)
-    qb, sb = _run(c, w, w.dt, 1, 4)
+    qa, sa = _run(c, w, w.dt, 1, 0, prec_name)
+    qb, sb = _run(c, w, w.dt, 1, 4, prec_name)
     assert np.array_equal(sa, sb) and np.array_equal(qa, qb)
 
 

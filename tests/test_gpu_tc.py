@@ -1,4 +1,4 @@
-"""GPU parity of the tcgen05 tensor-core paths (F16X2 step, F16X2 / F16 dense
+"""GPU parity of the tcgen05 tensor-core paths (F16X2 / F16 step, F16X2 / F16 dense
 reconstruction) against the FP64 oracle, through the C ABI.
 
 Every decoder here has general FP32 weights, the form a trained decoder has; the
@@ -9,7 +9,11 @@ parts (~2^-22).  Tolerances: dense values rel. L2 <= 1e-4 (F16X2) and <= 3e-3
 (F16: single f16 activations and weights).  Latent step:
 the increment q_{n+1} - q_n moves with the weight rounding (J and the network
 Laplacian change by up to ~1e-1 relative): <= 3e-2 or the least-squares
-perturbation bound; q_{n+1} <= 5e-5.  Rollouts: q_T rel. L2 <= 1e-3.
+perturbation bound; q_{n+1} <= 5e-5.  Rollouts: q_T rel. L2 <= 1e-3.  The F16
+step (activations as single f16 values, 2^-12 relative like the weights): twice
+the residual and increment tolerances and 20 times the q_{n+1} tolerance (measured
+up to 8.8 times the F16X2 bound on the ill-conditioned decoder shapes, kappa ~ 3e5);
+its rollouts keep the 1e-3 bar.
 """
 import numpy as np
 import pytest
@@ -96,7 +100,12 @@ RES_TOL = 0.15
 EPS_W = 2.0 ** -12 / np.sqrt(3.0)
 
 
-def _check_instance(w, i, q1_i, ref_i):
+# tolerance factors of the step per precision (q_{n+1}, residual and increment):
+# single f16 activations add a rounding of the weights' size to every layer input
+STEP_PRECS = [("CROM_PREC_F16X2", (1.0, 1.0)), ("CROM_PREC_F16", (20.0, 2.0))]
+
+
+def _check_instance(w, i, q1_i, ref_i, f=(1.0, 1.0)):
     """Least-squares perturbation theory (Golub & Van Loan, Thm. 5.3.1) bounds the
     J-space error of a projection solved with relative data errors eps by about
     eps (2 + 3 kappa) and the increment error by about eps kappa (2 + kappa tan theta),
@@ -107,44 +116,49 @@ def _check_instance(w, i, q1_i, ref_i):
     Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
     inc, res, kappa, margin = increment_errors(w.params, w.spec.m, w.q0[i], Y, q1_i, ref_i, w.dt, w.alpha[i])
     grow = max(1.0, kappa / 1e4)
-    assert rel_l2(q1_i, ref_i) < 5e-5 * grow, (i, rel_l2(q1_i, ref_i), kappa)
+    fq, fr = f
+    assert rel_l2(q1_i, ref_i) < 5e-5 * fq * grow, (i, rel_l2(q1_i, ref_i), kappa)
     # the fit's error grows linearly in kappa from a few thousand on (r = 15 decoders)
-    assert res < RES_TOL * max(1.0, kappa / 5e3), (i, res, kappa, margin)
+    assert res < fr * RES_TOL * max(1.0, kappa / 5e3), (i, res, kappa, margin)
     ev = O.MLPDecoder(w.params, w.spec.m)(Y, w.q0[i])
     jd = ev.gq @ (ref_i - w.q0[i])
     tan_theta = np.linalg.norm(w.dt * np.asarray(w.alpha[i], np.float64) * ev.lap - jd) / np.linalg.norm(jd)
-    assert inc < max(3e-2, EPS_W * kappa * (2 + kappa * tan_theta)), (i, inc, kappa, tan_theta)
+    assert inc < fr * max(3e-2, EPS_W * kappa * (2 + kappa * tan_theta)), (i, inc, kappa, tan_theta)
 
 
-def _check_step(w, q1, st):
+def _check_step(w, q1, st, f=(1.0, 1.0)):
     dec = O.MLPDecoder(w.params, w.spec.m)
     ref, rst = O.crom_step_batched(dec, w.q0, w.s_off, w.samples, w.alpha, w.dt, w.gn_iters)
     assert np.array_equal(st, rst), (st, rst)
     for i in range(w.n_inst):
         if rst[i] == 0:
-            _check_instance(w, i, q1[i], ref[i])
+            _check_instance(w, i, q1[i], ref[i], f)
 
 
-def test_step_tc_single_instance_heat2d():
+@pytest.mark.parametrize("prec_name,f", STEP_PRECS)
+def test_step_tc_single_instance_heat2d(prec_name, f):
     c = crom()
     w = gen.heat2d_single()
     ctx = make_ctx(w.spec, w.params)
-    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_F16X2)
-    _check_step(w, q1, st)
+    q1, st = run_steps(ctx, w, 1, getattr(c, prec_name))
+    _check_step(w, q1, st, f)
 
 
+@pytest.mark.parametrize("prec_name,f", STEP_PRECS)
 @pytest.mark.parametrize("gn_iters", [1, 2, 3])
-def test_step_tc_batched_ragged(gn_iters):
-    """Uneven |M_i| including sizes below, at and above one 32-sample tile."""
+def test_step_tc_batched_ragged(gn_iters, prec_name, f):
+    """Uneven |M_i| including sizes below, at and above one tile (16 .. 32 samples)
+    and several tiles with a ragged tail."""
     c = crom()
     w = gen.heat2d_batched(n_inst=20, m_lo=8, m_hi=300, bias_std=0.1)
     w.gn_iters = gn_iters
     ctx = make_ctx(w.spec, w.params)
-    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_F16X2)
-    _check_step(w, q1, st)
+    q1, st = run_steps(ctx, w, 1, getattr(c, prec_name))
+    _check_step(w, q1, st, f)
 
 
-def test_step_tc_one_dimensional_decoder():
+@pytest.mark.parametrize("prec_name,f", STEP_PRECS)
+def test_step_tc_one_dimensional_decoder(prec_name, f):
     c = crom()
     spec = gen.DecoderSpec(1, 4, 128, 4)
     params = gen.xavier_decoder(spec, seed=2, bias_std=0.1)
@@ -154,40 +168,45 @@ def test_step_tc_one_dimensional_decoder():
     w = gen.StepWorkload("1d", spec, params, rng.standard_normal((3, 4)), np.array([1.0, 0.5, 2.0], np.float32),
                          gen.ragged_offsets(sizes), samples, 1e-5, 2, 1)
     ctx = make_ctx(spec, params)
-    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_F16X2)
-    _check_step(w, q1, st)
+    q1, st = run_steps(ctx, w, 1, getattr(c, prec_name))
+    _check_step(w, q1, st, f)
 
 
-def test_step_tc_full_size_sampled_and_matches_fp32():
+@pytest.mark.parametrize("prec_name,f", STEP_PRECS)
+def test_step_tc_full_size_sampled_and_matches_fp32(prec_name, f):
     """All 1024 instances in one persistent launch (the launch the bench times); 10
     sampled instances recomputed by the oracle; the FP32 path agrees with it too."""
     c = crom()
     w = gen.heat2d_batched(n_inst=1024)
     ctx = make_ctx(w.spec, w.params)
-    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_F16X2)
+    q1, st = run_steps(ctx, w, 1, getattr(c, prec_name))
     assert np.all(st == 0)
     dec = O.MLPDecoder(w.params, 2)
     for i in np.random.default_rng(1).choice(w.n_inst, size=10, replace=False):
         Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
         ref, rst = O.crom_step(dec, w.q0[i], Y, w.dt, w.gn_iters, alpha=float(w.alpha[i]))
         assert rst == 0
-        _check_instance(w, i, q1[i], ref)
+        _check_instance(w, i, q1[i], ref, f)
     q32, st32 = run_steps(ctx, w, 1, c.CROM_PREC_FP32)
     assert np.all(st32 == 0)
-    assert rel_l2(q1, q32) < 1e-5
+    assert rel_l2(q1, q32) < 1e-5 * f[0]
     inc = np.linalg.norm((q1 - w.q0) - (q32 - w.q0), axis=1) / np.linalg.norm(q32 - w.q0, axis=1)
-    assert np.median(inc) < 3e-2
+    print(f"{prec_name}: q1 vs FP32 {rel_l2(q1, q32):.2e}, median increment {np.median(inc):.2e}")
+    assert np.median(inc) < 3e-2 * f[1]
 
 
-def test_step_tc_rollout_within_1e3():
+@pytest.mark.parametrize("prec_name", ["CROM_PREC_F16X2", "CROM_PREC_F16"])
+def test_step_tc_rollout_within_1e3(prec_name):
     """100-step rollouts of 6 instances: q_T within 1e-3 relative L2 of the oracle; the
-    increment q_T - q_0 within 3e-2 (the f16 weights perturb the latent dynamics)."""
+    increment q_T - q_0 within 3e-2 (the f16 weights perturb the latent dynamics;
+    6e-2 with single f16 activations)."""
     c = crom()
     full = gen.heat2d_batched(n_inst=64)
     w = subset(full, np.array([0, 5, 17, 33, 48, 63]))
     ctx = make_ctx(w.spec, w.params)
     steps = 100
-    qT, st = run_steps(ctx, w, steps, c.CROM_PREC_F16X2)
+    f = dict(STEP_PRECS)[prec_name][1]
+    qT, st = run_steps(ctx, w, steps, getattr(c, prec_name))
     assert np.all(st == 0)
     dec = O.MLPDecoder(w.params, 2)
     for i in range(w.n_inst):
@@ -195,10 +214,11 @@ def test_step_tc_rollout_within_1e3():
         traj = O.crom_rollout(dec, w.q0[i], Y, w.dt, w.gn_iters, steps, alpha=float(w.alpha[i]))
         e_q, e_inc = rel_l2(qT[i], traj[-1]), rel_l2(qT[i] - w.q0[i], traj[-1] - w.q0[i])
         print(f"instance {i}: q_T {e_q:.3e}, increment {e_inc:.3e}")
-        assert e_q < 1e-3 and e_inc < 3e-2, (i, e_q, e_inc)
+        assert e_q < 1e-3 and e_inc < 3e-2 * f, (i, e_q, e_inc)
 
 
-def test_rollout_1000_step_graph_full_batch():
+@pytest.mark.parametrize("prec_name", ["CROM_PREC_F16X2", "CROM_PREC_F16"])
+def test_rollout_1000_step_graph_full_batch(prec_name):
     """The batched workload end to end: all 1024 instances advanced 1000 steps by one
     cached CUDA graph, bit-identical to 1000 crom_step calls; the instance with the
     smallest |M_i| and one of about a hundred samples (several tiles and a ragged
@@ -212,13 +232,15 @@ def test_rollout_1000_step_graph_full_batch():
     steps = 1000
     q = dev(w.q0, torch.float64)
     st = torch.full((w.n_inst,), -1, dtype=torch.int32, device="cuda")
+    prec = getattr(c, prec_name)
+    f = dict(STEP_PRECS)[prec_name][1]
     c.crom_rollout(ctx, q, dev(w.alpha, torch.float32), dev(w.s_off, torch.int32), dev(w.samples, torch.float32),
                    st, n_steps=steps, dt=w.dt, gn_iters=w.gn_iters, max_samples=int(w.sizes.max()),
-                   precision=c.CROM_PREC_F16X2)
+                   precision=prec)
     torch.cuda.synchronize()
     qT, stT = q.cpu().numpy(), st.cpu().numpy()
     assert np.all(stT == 0) and np.all(np.isfinite(qT))
-    q_ref, st_ref = run_steps(ctx, w, steps, c.CROM_PREC_F16X2)
+    q_ref, st_ref = run_steps(ctx, w, steps, prec)
     assert np.array_equal(qT, q_ref) and np.array_equal(stT, st_ref)
     dec = O.MLPDecoder(w.params, 2)
     order = np.argsort(w.sizes, kind="stable")
@@ -227,11 +249,11 @@ def test_rollout_1000_step_graph_full_batch():
         Y = w.samples[w.s_off[i]:w.s_off[i + 1]]
         traj = O.crom_rollout(dec, w.q0[i], Y, w.dt, w.gn_iters, steps, alpha=float(w.alpha[i]))
         e_q, e_inc = rel_l2(qT[i], traj[-1]), rel_l2(qT[i] - w.q0[i], traj[-1] - w.q0[i])
-        print(f"instance {i} |M|={Y.shape[0]}: q_T {e_q:.3e}, increment {e_inc:.3e}")
-        assert e_q < 1e-3 and e_inc < 3e-2, (i, e_q, e_inc)
+        print(f"{prec_name} instance {i} |M|={Y.shape[0]}: q_T {e_q:.3e}, increment {e_inc:.3e}")
+        assert e_q < 1e-3 and e_inc < 3e-2 * f, (i, e_q, e_inc)
 
 
-@pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_F16X2"])
+@pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_F16X2", "CROM_PREC_F16"])
 def test_rollout_graph_equals_repeated_steps(prec_name):
     """crom_rollout (a cached CUDA graph of n steps) gives bit-identical results to n
     crom_step calls; a second call replays the cached graph and continues."""
@@ -252,7 +274,8 @@ def test_rollout_graph_equals_repeated_steps(prec_name):
     assert np.array_equal(st.cpu().numpy(), st_ref)
 
 
-def test_step_tc_edge_cases_status():
+@pytest.mark.parametrize("prec_name", ["CROM_PREC_F16X2", "CROM_PREC_F16"])
+def test_step_tc_edge_cases_status(prec_name):
     c = crom()
     spec = gen.DecoderSpec(2, 4, 128, 3)
     params = gen.xavier_decoder(spec, seed=9, bias_std=0.1)
@@ -267,7 +290,7 @@ def test_step_tc_edge_cases_status():
     q0 = rng.standard_normal((5, 4))
     alpha = np.array([1.0, 1.0, 1.0, np.nan, 1.0], np.float32)
     w = gen.StepWorkload("edge", spec, params, q0, alpha, off, samples, 1e-4, 2, 1)
-    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_F16X2)
+    q1, st = run_steps(ctx, w, 1, getattr(c, prec_name))
     assert list(st) == [c.CROM_OK, c.CROM_ERR_SINGULAR, c.CROM_ERR_INVALID_ARG, c.CROM_ERR_NONFINITE,
                         c.CROM_ERR_INVALID_ARG]
     assert np.array_equal(q1[1:], q0[1:])
@@ -293,8 +316,9 @@ def test_step_tc_rejects_unsupported():
     assert e.value.code == c.CROM_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("prec_name,f", STEP_PRECS)
 @pytest.mark.parametrize("n_samples", [2048, 5000])
-def test_step_tc_large_instance(n_samples):
+def test_step_tc_large_instance(n_samples, prec_name, f):
     """One instance with 2048 samples (the single-instance sample set of the precision
     workload) or 5000 (many tiles, far above the batched sizes)."""
     c = crom()
@@ -305,8 +329,8 @@ def test_step_tc_large_instance(n_samples):
     w = gen.StepWorkload("big", spec, params, rng.standard_normal((1, 8)), np.ones(1, np.float32),
                          gen.ragged_offsets([n_samples]), Y, 1e-5, 2, 1)
     ctx = make_ctx(spec, params)
-    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_F16X2)
-    _check_step(w, q1, st)
+    q1, st = run_steps(ctx, w, 1, getattr(c, prec_name))
+    _check_step(w, q1, st, f)
 
 
 # Sample tiles of the tensor-core step: TILE_S0 samples per forward tile at GN
@@ -314,10 +338,12 @@ def test_step_tc_large_instance(n_samples):
 TILE_S0, TILE_S1 = 8, (16, 8)
 
 
+@pytest.mark.parametrize("prec_name,f", STEP_PRECS)
 @pytest.mark.parametrize("gn_iters", [2, 3])
-def test_step_tc_small_tiles_matches_oracle(gn_iters):
+def test_step_tc_small_tiles_matches_oracle(gn_iters, prec_name, f):
     """The small sample-tile variant of the step (TILE_S1[1] samples per tile after
-    iteration 0) against the oracle on uneven |M_i|; other shapes are rejected."""
+    iteration 0, twice that with single f16 activations) against the oracle on uneven
+    |M_i|; other shapes are rejected."""
     c = crom()
     w = gen.heat2d_batched(n_inst=20, m_lo=8, m_hi=300, bias_std=0.1)
     w.gn_iters = gn_iters
@@ -325,8 +351,8 @@ def test_step_tc_small_tiles_matches_oracle(gn_iters):
     assert c.crom_get_step_tiles(ctx)[:2] == (TILE_S0, TILE_S1[0])
     c.crom_set_step_tiles(ctx, TILE_S0, TILE_S1[1])
     assert c.crom_get_step_tiles(ctx)[:2] == (TILE_S0, TILE_S1[1])
-    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_F16X2)
-    _check_step(w, q1, st)
+    q1, st = run_steps(ctx, w, 1, getattr(c, prec_name))
+    _check_step(w, q1, st, f)
     for bad in ((TILE_S0, 4), (TILE_S0, 32), (16, TILE_S1[0])):
         with pytest.raises(c.CromError):
             c.crom_set_step_tiles(ctx, *bad)
@@ -350,9 +376,10 @@ def test_autotune_measures_both_tile_shapes_and_leaves_q():
     _check_step(subset(w, np.arange(12)), q1, st)
 
 
+@pytest.mark.parametrize("prec_name,f", STEP_PRECS)
 @pytest.mark.parametrize("m,r,hidden", [(2, 1, 2), (2, 15, 5), (2, 15, 2), (1, 8, 3), (1, 4, 5), (2, 4, 3),
                                         (2, 12, 3), (2, 8, 4)])
-def test_step_tc_decoder_shapes(m, r, hidden):
+def test_step_tc_decoder_shapes(m, r, hidden, prec_name, f):
     """The tensor-core step over the shapes it accepts: r = 1 and the largest r = 15,
     2 to 5 hidden layers, 1D and 2D inputs; uneven |M_i| around the tile sizes, the
     smallest |M_i| = r for r = 15.  (A 1D decoder with r = 15 is left out: its
@@ -371,11 +398,12 @@ def test_step_tc_decoder_shapes(m, r, hidden):
                          rng.uniform(0.5, 2.0, len(sizes)).astype(np.float32), gen.ragged_offsets(sizes), samples,
                          1e-5, 2, 1)
     ctx = make_ctx(spec, params)
-    q1, st = run_steps(ctx, w, 1, c.CROM_PREC_F16X2)
-    _check_step(w, q1, st)
+    q1, st = run_steps(ctx, w, 1, getattr(c, prec_name))
+    _check_step(w, q1, st, f)
 
 
-def test_step_tc_advection_diffusion_matches_oracle():
+@pytest.mark.parametrize("prec_name,f", STEP_PRECS)
+def test_step_tc_advection_diffusion_matches_oracle(prec_name, f):
     """Delta f_j = dt (-a(y_j) . grad g + nu Lap g) on the tensor-core path (the
     gradient channels' outputs enter the residual), several instances."""
     import torch
@@ -395,7 +423,7 @@ def test_step_tc_advection_diffusion_matches_oracle():
     dt = 1e-4
     c.crom_step(ctx, q, dev(nu, torch.float32), dev(off, torch.int32), dev(Y, torch.float32), st,
                 dt=dt, gn_iters=2, max_samples=200, pde=c.CROM_PDE_ADVDIFF, vel=dev(vel, torch.float32),
-                precision=c.CROM_PREC_F16X2)
+                precision=getattr(c, prec_name))
     torch.cuda.synchronize()
     q1 = q.cpu().numpy()
     dec = O.MLPDecoder(params, 2)
@@ -407,4 +435,4 @@ def test_step_tc_advection_diffusion_matches_oracle():
         df = O.advdiff_delta_f(ev, vel[sl], float(nu[i]), dt)
         res = np.linalg.norm(ev.gq @ (q1[i] - ref)) / np.linalg.norm(df)
         # dt = 1e-4: ten times the heat tests' increment, so ten times their q tolerance
-        assert rel_l2(q1[i], ref) < 1e-4 and res < RES_TOL, (i, rel_l2(q1[i], ref), res)
+        assert rel_l2(q1[i], ref) < 1e-4 * f[0] and res < RES_TOL * f[1], (i, rel_l2(q1[i], ref), res)
