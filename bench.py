@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--tiles", default="auto",
                     help="sample tiles of the tensor-core step: auto (measured by crom_autotune) or s0,s1 "
                          "(fixed; profilers distort the autotuner's timings)")
+    ap.add_argument("--prec", default="f16x2", choices=["f16x2", "f16"],
+                    help="tensor-core precision of --only step / recon")
     ap.add_argument("--only", default=None, choices=["step", "recon", "plain", "fom", "heat", "train"],
                     help="run only one part (warmup + steps launches) for profiling; prints a short JSON line")
     return ap.parse_args()
@@ -72,7 +74,8 @@ def run_only(args):
     n = args.warmup + args.steps
     if args.only in ("step", "plain"):
         w = gen.heat2d_batched(n_inst=args.n_inst) if args.only == "step" else gen.heat2d_single()
-        prec = crom.CROM_PREC_F16X2 if args.only == "step" else crom.CROM_PREC_FP32
+        tc_prec = crom.CROM_PREC_F16X2 if args.prec == "f16x2" else crom.CROM_PREC_F16
+        prec = tc_prec if args.only == "step" else crom.CROM_PREC_FP32
         ctx = crom.crom_create(w.spec.m, w.spec.r, w.spec.width, w.spec.hidden, 0)
         crom.crom_set_weights(ctx, gen.pack_params(w.params))
         q = torch.tensor(w.q0, device="cuda")
@@ -130,7 +133,8 @@ def run_only(args):
         c, x = torch.tensor(codes, device="cuda"), torch.tensor(X, device="cuda")
         out = torch.empty((codes.shape[0], X.shape[0]), device="cuda")
         for _ in range(n):
-            crom.crom_reconstruct(ctx, c, x, out, precision=crom.CROM_PREC_F16X2)
+            crom.crom_reconstruct(ctx, c, x, out,
+                                  precision=crom.CROM_PREC_F16X2 if args.prec == "f16x2" else crom.CROM_PREC_F16)
         torch.cuda.synchronize()
         print(json.dumps({"only": "recon", "codes": codes.shape[0], "points": X.shape[0], "calls": n}))
     ctx.close()

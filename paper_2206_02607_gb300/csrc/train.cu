@@ -172,12 +172,25 @@ __global__ void colsum_part4_kernel(const float* X, long rows, int cols, double*
       part[(long)blockIdx.y * cols + 4 * q + e] =
           (red[0][threadIdx.x][e] + red[1][threadIdx.x][e]) + (red[2][threadIdx.x][e] + red[3][threadIdx.x][e]);
 }
+// Sum over the 32 lanes by a fixed butterfly (every lane ends with the same value).
+__device__ __forceinline__ double warp_sum_fixed(double t) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double u = __shfl_xor_sync(0xffffffffu, t, o);
+    t = (threadIdx.x & o) ? u + t : t + u;  // the lower lane's value first on both lanes
+  }
+  return t;
+}
+// out[c] = sum of the chunks' partials of column c: one warp per column, lanes take
+// every 32nd chunk, then a fixed butterfly.
 __global__ void colsum_final_kernel(const double* part, int chunks, int cols, float* out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
+  const int c = (int)((blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= cols) return;  // whole warps leave together
   double t = 0.0;
-  for (int k = 0; k < chunks; ++k) t += part[(long)k * cols + c];
-  out[c] = (float)t;
+  for (int k = lane; k < chunks; k += 32) t += part[(long)k * cols + c];
+  t = warp_sum_fixed(t);
+  if (lane == 0) out[c] = (float)t;
 }
 
 __global__ void conv_fwd_kernel(const float* x, int Lin, int Lout, int B, const float* w, float* z, float* h) {
@@ -234,12 +247,14 @@ __global__ void conv_grad_part_kernel(const float* dz, const float* x, int Lin, 
   }
   if (threadIdx.x == 0) part[(long)blockIdx.y * 7 + k] = red[0];
 }
+// gw[k] = sum over the chunks of part[chunk][k]: warp k, lanes take every 32nd chunk.
 __global__ void conv_grad_final_kernel(const double* part, int chunks, float* gw) {
-  const int k = threadIdx.x;
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (k >= 7) return;
   double t = 0.0;
-  for (int c = 0; c < chunks; ++c) t += part[(long)c * 7 + k];
-  gw[k] = (float)t;
+  for (int c = lane; c < chunks; c += 32) t += part[(long)c * 7 + k];
+  t = warp_sum_fixed(t);
+  if (lane == 0) gw[k] = (float)t;
 }
 
 __global__ void gather_kernel(const float* snaps, const int* pt_idx, const float* coords, const float* q, int B,
@@ -459,7 +474,7 @@ static void colsum(crom_trainer* t, cudaStream_t s, const float* X, long rows, i
     colsum_part4_kernel<<<dim3(blocks(cols / 4, 64), chunks), dim3(64, 4), 0, s>>>(X, rows, cols, t->red);
   else
     colsum_part_kernel<<<dim3(blocks(cols, 32), chunks), dim3(32, 8), 0, s>>>(X, rows, cols, t->red);
-  colsum_final_kernel<<<blocks(cols, 128), 128, 0, s>>>(t->red, chunks, cols, out);
+  colsum_final_kernel<<<blocks(32L * cols, 128), 128, 0, s>>>(t->red, chunks, cols, out);
 }
 
 int trainer_set_precision(crom_trainer* t, int precision) {
@@ -587,7 +602,7 @@ cudaError_t trainer_step(crom_trainer* t, const float* snaps, const int* pt_idx,
     {
       const int chunks = (int)std::min<long>(kColChunks, std::max<long>((long)B * Lout / 1024, 1));
       conv_grad_part_kernel<<<dim3(7, chunks), 256, 0, s>>>(t->edx, xin, Lin, Lout, B, t->red);
-      conv_grad_final_kernel<<<1, 32, 0, s>>>(t->red, chunks, gr + lay.conv[c - 1]);
+      conv_grad_final_kernel<<<1, 7 * 32, 0, s>>>(t->red, chunks, gr + lay.conv[c - 1]);
     }
     if (c > 1) conv_dx_kernel<<<blocks((long)B * Lin, 256), 256, 0, s>>>(t->edx, Lin, Lout, B,
                                                                          p + lay.conv[c - 1], t->edh);

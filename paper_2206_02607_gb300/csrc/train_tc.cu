@@ -172,21 +172,53 @@ __global__ void layer0_bwd_part_kernel(const uint16_t* delta, const float* x_in,
   }
 }
 
-// snap[b][u][k] = sum over the chunks of snapshot b of part[b][c][u][k] (FP64, in order).
+// Compensated FP32 sum (Knuth's two-sum per term): ~2^-48 relative for the term
+// counts here, deterministic in a fixed order, and without the FP64 pipe, which is
+// narrow on this GPU.
+struct CSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = __fadd_rn(s, x);
+    const float bp = __fsub_rn(t, s);
+    c += __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    s = t;
+  }
+  __device__ __forceinline__ void add(const CSum& o) {
+    add(o.s);
+    c += o.c;
+  }
+  __device__ __forceinline__ float value() const { return s + c; }
+};
+// The 32 lanes' sums combined by a fixed butterfly (every lane ends with the same value).
+__device__ __forceinline__ float warp_csum(CSum v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    CSum w;
+    w.s = __shfl_xor_sync(0xffffffffu, v.s, o);
+    w.c = __shfl_xor_sync(0xffffffffu, v.c, o);
+    // the lower lane's sum first, so that both lanes of a pair add in the same order
+    CSum lo = (threadIdx.x & o) ? w : v, hi = (threadIdx.x & o) ? v : w;
+    lo.add(hi);
+    v = lo;
+  }
+  return v.value();
+}
+
+// snap[b][u][k] = sum over the chunks of snapshot b of part[b][c][u][k] (in order).
 __global__ void layer0_bwd_snap_kernel(const float* part, int chunks, int w, int m, float* snap) {
   const int b = blockIdx.x;
   const int e = threadIdx.x + blockIdx.y * blockDim.x;  // (u, k)
   const int per = w * (1 + m);
   if (e >= per) return;
-  double s = 0.0;
-  for (int c = 0; c < chunks; ++c) s += part[((long)b * chunks + c) * per + e];
-  snap[(long)b * per + e] = (float)s;
+  CSum s;
+  for (int c = 0; c < chunks; ++c) s.add(part[((long)b * chunks + c) * per + e]);
+  snap[(long)b * per + e] = s.value();
 }
 
 // The input layer's gradients from the per-snapshot moments, one warp per output
-// entry (lanes take every 32nd term, FP64, then a fixed butterfly): entries
-// e < w kin are dW_0[u][j] (u = e / kin), the next w are db_0, the last B r are the
-// encoder's dL/dq_b[j].
+// entry (lanes take every 32nd term, then a fixed butterfly): entries e < w kin are
+// dW_0[u][j] (u = e / kin), the next w are db_0, the last B r are the encoder's
+// dL/dq_b[j].  Products are formed exactly (two-product) and added compensated.
 __global__ void layer0_grad_kernel(const float* snap, const float* q, const float* W0, int B, int m, int r, int w,
                                    float* gW0, float* gb0, float* dq) {
   const int kin = m + r;
@@ -195,47 +227,50 @@ __global__ void layer0_grad_kernel(const float* snap, const float* q, const floa
   const long nw = (long)w * kin;
   const int per = w * (1 + m);
   if (e >= nw + w + (long)B * r) return;  // whole warps leave together
-  double s = 0.0;
+  CSum s;
+  auto add_prod = [&](float a, float b) {
+    const float p = __fmul_rn(a, b);
+    s.add(p);
+    s.c += fmaf(a, b, -p);
+  };
   if (e < nw) {
     const int u = (int)(e / kin), j = (int)(e % kin);
     if (j < m) {
-      for (int b = lane; b < B; b += 32) s += snap[(long)b * per + u * (1 + m) + 1 + j];
+      for (int b = lane; b < B; b += 32) s.add(snap[(long)b * per + u * (1 + m) + 1 + j]);
     } else {
-      for (int b = lane; b < B; b += 32) s += (double)snap[(long)b * per + u * (1 + m)] * q[(long)b * r + j - m];
+      for (int b = lane; b < B; b += 32) add_prod(snap[(long)b * per + u * (1 + m)], q[(long)b * r + j - m]);
     }
   } else if (e < nw + w) {
     const int u = (int)(e - nw);
-    for (int b = lane; b < B; b += 32) s += snap[(long)b * per + u * (1 + m)];
+    for (int b = lane; b < B; b += 32) s.add(snap[(long)b * per + u * (1 + m)]);
   } else {
     const int b = (int)((e - nw - w) / r), j = (int)((e - nw - w) % r);
-    for (int u = lane; u < w; u += 32) s += (double)W0[(long)u * kin + m + j] * snap[(long)b * per + u * (1 + m)];
+    for (int u = lane; u < w; u += 32) add_prod(W0[(long)u * kin + m + j], snap[(long)b * per + u * (1 + m)]);
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const float t = warp_csum(s);
   if (lane == 0) {
-    if (e < nw) gW0[e] = (float)s;
-    else if (e < nw + w) gb0[e - nw] = (float)s;
-    else dq[e - nw - w] = (float)s;
+    if (e < nw) gW0[e] = t;
+    else if (e < nw + w) gb0[e - nw] = t;
+    else dq[e - nw - w] = t;
   }
 }
 
-// out[e] = sum_p part[p * stride + e], in order of p (FP64 accumulation).
-// Eight loads are issued before their (in-order) additions, so that their latencies
-// overlap.
+// out[e] = sum_p part[p * stride + e], in order of p (compensated).  Eight loads are
+// issued before their additions, so that their latencies overlap.
 __global__ void sum_parts_kernel(const float* part, int nparts, long stride, long n, float* out) {
   const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (e >= n) return;
-  double s = 0.0;
+  CSum s;
   int p = 0;
   for (; p + 8 <= nparts; p += 8) {
     float v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = __ldg(part + (long)(p + k) * stride + e);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) s += v[k];
+    for (int k = 0; k < 8; ++k) s.add(v[k]);
   }
-  for (; p < nparts; ++p) s += part[(long)p * stride + e];
-  out[e] = (float)s;
+  for (; p < nparts; ++p) s.add(part[(long)p * stride + e]);
+  out[e] = s.value();
 }
 
 // Column sums of part [nparts][cols] in a fixed order, first level: block (x, y)
@@ -244,10 +279,10 @@ __global__ void sum_parts_kernel(const float* part, int nparts, long stride, lon
 // (sum_parts_kernel).
 constexpr int kColPer = 128;
 __global__ void colsum_level1_kernel(const float* part, int nparts, int cols, float* mid) {
-  __shared__ double red[8][32];
+  __shared__ float red_s[8][32], red_c[8][32];
   const int col = blockIdx.x * 32 + threadIdx.x;
   const int p0 = blockIdx.y * kColPer, p1 = min(nparts, p0 + kColPer);
-  double acc = 0.0;
+  CSum acc;
   if (col < cols) {
     constexpr int kPer = kColPer / 8;  // parts per thread, loaded before they are added in order
     float v[kPer];
@@ -257,30 +292,38 @@ __global__ void colsum_level1_kernel(const float* part, int nparts, int cols, fl
       v[k] = p < p1 ? __ldg(part + (long)p * cols + col) : 0.f;
     }
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) acc += v[k];
+    for (int k = 0; k < kPer; ++k) acc.add(v[k]);
   }
-  red[threadIdx.y][threadIdx.x] = acc;
+  red_s[threadIdx.y][threadIdx.x] = acc.s;
+  red_c[threadIdx.y][threadIdx.x] = acc.c;
   __syncthreads();
   if (threadIdx.y == 0 && col < cols) {
-    double t = 0.0;
-    for (int k = 0; k < 8; ++k) t += red[k][threadIdx.x];
-    mid[(long)blockIdx.y * cols + col] = (float)t;
+    CSum t;
+    for (int k = 0; k < 8; ++k) {
+      CSum o;
+      o.s = red_s[k][threadIdx.x];
+      o.c = red_c[k][threadIdx.x];
+      t.add(o);
+    }
+    mid[(long)blockIdx.y * cols + col] = t.value();
   }
 }
 
-// loss = sum_p rowpart[p][0] * inv_count; gb_out = sum_p rowpart[p][1] (in order).
+// loss = sum_p rowpart[p][0] * inv_count; gb_out = sum_p rowpart[p][1]: each thread
+// a contiguous range of parts (compensated), then a fixed tree in FP64.
 __global__ void loss_parts_kernel(const float* rowpart, int nparts, double inv_count, double* loss, float* gbout) {
-  __shared__ double red[2][256];
-  double a = 0.0, b = 0.0;
-  const int per = (nparts + 255) / 256;
+  constexpr int kT = 1024;
+  __shared__ double red[2][kT];
+  CSum a, b;
+  const int per = (nparts + kT - 1) / kT;
   for (int p = threadIdx.x * per; p < min(nparts, (int)(threadIdx.x + 1) * per); ++p) {
-    a += rowpart[2 * p];
-    b += rowpart[2 * p + 1];
+    a.add(rowpart[2 * p]);
+    b.add(rowpart[2 * p + 1]);
   }
-  red[0][threadIdx.x] = a;
-  red[1][threadIdx.x] = b;
+  red[0][threadIdx.x] = (double)a.s + (double)a.c;
+  red[1][threadIdx.x] = (double)b.s + (double)b.c;
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
+  for (int o = kT / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) {
       red[0][threadIdx.x] += red[0][threadIdx.x + o];
       red[1][threadIdx.x] += red[1][threadIdx.x + o];
@@ -384,7 +427,7 @@ cudaError_t trainer_decoder_tc(crom_trainer* t, double* loss_out, int num_sms, c
     }
     if ((e = tc_gemm(g, num_sms, c.flag, s)) != cudaSuccess) return e;
   }
-  loss_parts_kernel<<<1, 256, 0, s>>>(c.rowpart, parts, 1.0 / (double)N, loss_out ? loss_out : t->loss_dev,
+  loss_parts_kernel<<<1, 1024, 0, s>>>(c.rowpart, parts, 1.0 / (double)N, loss_out ? loss_out : t->loss_dev,
                                       gr + lay.dec_b[L]);
   colsum_parts(c.colpart2, parts, w, c.colmid, gr + lay.dec_w[L], s);   // dL/dw_out
   colsum_parts(c.colpart, parts, w, c.colmid, gr + lay.dec_b[L - 1], s);

@@ -41,7 +41,7 @@ N_SAMPLES = 4096
 # training steps per decoder shape: the rollout error follows the decoder's fit of
 # the held-out fields (encoder fit at the final time 4.9e-3 after 120k steps on
 # w = 256, 8.9e-3 after 60k)
-TRAIN_STEPS = {"w256_r16": 120000, "w128_r15": 160000}
+TRAIN_STEPS = {"w256_r16": 120000, "w128_r15": 200000}
 ROLLOUT_BAR = 1e-2
 
 
