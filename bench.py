@@ -40,7 +40,7 @@ WORKLOAD = "heat2d_batched_1024inst_M32-512_r8_w128_L5_gn2"
 # dram__bytes_read.sum + dram__bytes_write.sum of one step_tc_kernel launch on the
 # 1024-instance workload, from an ncu capture of the current kernel; None until it has
 # been taken for the current kernel.
-STEP_KERNEL_DRAM_BYTES = None
+STEP_KERNEL_DRAM_BYTES = 2596096 + 0   # ncu dram__bytes_read.sum + write.sum of one launch (1024 instances)
 
 
 def parse():

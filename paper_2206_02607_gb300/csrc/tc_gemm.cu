@@ -66,7 +66,49 @@ struct __align__(8) Bars {
   uint32_t tmem_base;
   int abort;
   float gpart[2][2][4][32];  // output layer: [tile parity][column half][lane quadrant][row] partial sums
+  float bias[256];           // the epilogue's per-column vectors, staged once
+  float wout[256];
 };
+
+// tcgen05.wait::ld that names the destination registers of the loads it waits for,
+// so that their uses stay after it.
+__device__ __forceinline__ void tmem_wait32(float (&v)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),
+                 "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]),
+                 "+f"(v[15]), "+f"(v[16]), "+f"(v[17]), "+f"(v[18]), "+f"(v[19]), "+f"(v[20]), "+f"(v[21]),
+                 "+f"(v[22]), "+f"(v[23]), "+f"(v[24]), "+f"(v[25]), "+f"(v[26]), "+f"(v[27]), "+f"(v[28]),
+                 "+f"(v[29]), "+f"(v[30]), "+f"(v[31])
+               :
+               : "memory");
+}
+// f(c, v) on the kChunks consecutive 32-column chunks of a warp's accumulator rows
+// (TMEM address ta).  kPipe: the next chunk's load is in flight while f works on
+// this one (32 more registers); otherwise each chunk is loaded and waited for.
+template <int kChunks, bool kPipe, class F>
+__device__ __forceinline__ void acc_chunks(uint32_t ta, F&& f) {
+  if constexpr (kPipe) {
+    float va[32], vb[32];
+    tmem_ld32(ta, va);
+    tmem_wait32(va);
+#pragma unroll
+    for (int ci = 0; ci < kChunks; ++ci) {
+      float(&v)[32] = (ci & 1) ? vb : va;
+      float(&vn)[32] = (ci & 1) ? va : vb;
+      if (ci + 1 < kChunks) tmem_ld32(ta + 32 * (ci + 1), vn);
+      f(32 * ci, v);
+      if (ci + 1 < kChunks) tmem_wait32(vn);
+    }
+  } else {
+#pragma unroll 1
+    for (int ci = 0; ci < kChunks; ++ci) {
+      float v[32];
+      tmem_ld32(ta + 32 * ci, v);
+      tmem_wait32(v);
+      f(32 * ci, v);
+    }
+  }
+}
 
 __device__ __forceinline__ bool g_aborted(Bars* b) { return *reinterpret_cast<volatile int*>(&b->abort) != 0; }
 // the abort flag as lane 0 of the warp read it (a warp-uniform decision)
@@ -159,6 +201,30 @@ struct Staging {
     }
     __syncwarp();
   }
+  // load_rows in two halves: fetch_rows issues the global loads into registers (the
+  // loads stay in flight while the caller does other work), put_rows writes them to
+  // the staging rows
+  static constexpr int kFetch = 32 / (32 / (kW / 8));  // 16-byte loads per lane
+  __device__ __forceinline__ void fetch_rows(const uint16_t* src, long ld, int row0, int col0, int M, int lane,
+                                             uint4 (&R)[kFetch]) const {
+    constexpr int kLpr = kW / 8, kRpi = 32 / kLpr;
+#pragma unroll
+    for (int i = 0; i < kFetch; ++i) {
+      const int r = i * kRpi + lane / kLpr, c = (lane % kLpr) * 8;
+      R[i] = make_uint4(0u, 0u, 0u, 0u);
+      if (row0 + r < M) R[i] = __ldg(reinterpret_cast<const uint4*>(src + (long)(row0 + r) * ld + col0 + c));
+    }
+  }
+  __device__ __forceinline__ void put_rows(int lane, const uint4 (&R)[kFetch]) const {
+    constexpr int kLpr = kW / 8, kRpi = 32 / kLpr;
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < kFetch; ++i) {
+      const int r = i * kRpi + lane / kLpr, c = (lane % kLpr) * 8;
+      *reinterpret_cast<uint4*>(base + r * kSt + c) = R[i];
+    }
+    __syncwarp();
+  }
 };
 
 template <int kBN, int kEpi>
@@ -186,6 +252,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   if (warp == 1) {
     tmem_alloc(&bars->tmem_base, 2 * kBN);
     tmem_relinquish();
+  }
+  for (int i = tid; i < g.N; i += blockDim.x) {
+    bars->bias[i] = g.bias ? g.bias[i] : 0.f;
+    bars->wout[i] = g.wout ? g.wout[i] : 0.f;
   }
   tc_fence_before();
   __syncthreads();
@@ -276,29 +346,29 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       const int row0 = mt * kBM + q * 32;
       const int row = row0 + lane;
       const bool in = row < g.M;
-      // h_{l-1} of the tile's rows does not depend on the accumulator: read it first
-      if (kEpi == kGemmEpiTimesEluD) stg.load_rows(g.hprev, g.ldo, row0, cb, g.M, lane);
+      // h_{l-1} of the tile's rows does not depend on the accumulator: the first tile
+      // reads it here, later ones were fetched during the previous tile's stores
+      if (kEpi == kGemmEpiTimesEluD && local == 0) stg.load_rows(g.hprev, g.ldo, row0, cb, g.M, lane);
       g_wait(bars, &bars->tfull[acc], tphase[acc]);
       tphase[acc] ^= 1;
       tc_fence_after();
       const uint32_t ta = tb + (uint32_t)acc * kBN + (uint32_t)cb + ((uint32_t)(q * 32) << 16);
       float gval = 0.f, dg = 0.f, rr = 0.f;
+      constexpr int kCh = kHalf / 32;
+      const float* sbias = bars->bias + cb;
+      const float* swout = bars->wout + cb;
       if (kEpi == kGemmEpiOut) {
         // output layer g = w_out . h_L + b_out on this row (the two column halves'
         // partial sums meet in shared memory, added in a fixed order), then the loss terms
-#pragma unroll 1
-        for (int c0 = 0; c0 < kHalf; c0 += 32) {
-          float v[32];
-          tmem_ld32(ta + c0, v);
-          tmem_ld_wait();
+        acc_chunks<kCh, false>(ta, [&](int c0, float(&v)[32]) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const float h = elu_g(v[j] + __ldg(g.bias + cb + c0 + j));
+            const float h = elu_g(v[j] + sbias[c0 + j]);
             v[j] = h;
-            gval = fmaf(__ldg(g.wout + cb + c0 + j), h, gval);
+            gval = fmaf(swout[c0 + j], h, gval);
           }
           stg.put32(lane, c0, v);
-        }
+        });
         stg.store_rows(g.out_bf16, g.ldo, row0, cb, g.M, lane);
         bars->gpart[local & 1][half][q][lane] = gval;
         asm volatile("bar.sync %0, 64;" ::"r"(1 + q) : "memory");  // the two warps of quadrant q
@@ -307,11 +377,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         rr = r * r;
         dg = 2.f * r * g.inv_count;
       }
-#pragma unroll 1
-      for (int c0 = 0; c0 < kHalf; c0 += 32) {
-        float v[32];
-        tmem_ld32(ta + c0, v);
-        tmem_ld_wait();
+      // pipelined where the epilogue holds one 32-value row (bias + ELU, FP32 partials)
+      acc_chunks<kCh, kEpi == kGemmEpiBiasElu || kEpi == kGemmEpiF32>(ta, [&](int c0, float(&v)[32]) {
         const int col = cb + c0;
         if (kEpi == kGemmEpiF32) {
           if (in) {
@@ -321,7 +388,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           }
         } else if (kEpi == kGemmEpiBiasElu) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = elu_g(v[j] + __ldg(g.bias + col + j));
+          for (int j = 0; j < 32; ++j) v[j] = elu_g(v[j] + sbias[c0 + j]);
           stg.put32(lane, c0, v);
         } else if (kEpi == kGemmEpiTimesEluD) {
           float hp[32];
@@ -335,10 +402,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           float dh[32];
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const float z = v[j] + __ldg(g.bias + col + j);
+            const float z = v[j] + sbias[c0 + j];
             const float h = elu_g(z);
             dh[j] = in ? dg * h : 0.f;
-            v[j] = in ? dg * __ldg(g.wout + col + j) * (z > 0.f ? 1.f : h + 1.f) : 0.f;
+            v[j] = in ? dg * swout[c0 + j] * (z > 0.f ? 1.f : h + 1.f) : 0.f;
           }
           stg.put32(lane, c0, v);
           const float cs = warp_colsum32(v, lane);
@@ -346,12 +413,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           const float cs2 = warp_colsum32(dh, lane);
           g.colpart2[(long)(mt * 4 + q) * g.N + col + lane] = cs2;
         }
-      }
+      });
       // the accumulator is read: hand it back before the stores
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars->tempty[acc]);
-      if (kEpi == kGemmEpiBiasElu || kEpi == kGemmEpiTimesEluD) stg.store_rows(g.out_bf16, g.ldo, row0, cb, g.M, lane);
+      if (kEpi == kGemmEpiBiasElu) stg.store_rows(g.out_bf16, g.ldo, row0, cb, g.M, lane);
+      if (kEpi == kGemmEpiTimesEluD) {
+        // the next tile's h_{l-1} rows are loaded while this tile's delta rows are stored
+        const int tn = t + gridDim.x;
+        uint4 R[Staging<kHalf>::kFetch];
+        if (tn < tiles) stg.fetch_rows(g.hprev, g.ldo, (tn % g.tiles_m) * kBM + q * 32, cb, g.M, lane, R);
+        stg.store_rows(g.out_bf16, g.ldo, row0, cb, g.M, lane);
+        if (tn < tiles) stg.put_rows(lane, R);
+      }
       if (kEpi == kGemmEpiOut) {
         stg.store_rows(g.delta_out, g.ldo, row0, cb, g.M, lane);
         if (half == 0) {  // the row terms once per row

@@ -108,6 +108,28 @@ __device__ __forceinline__ float warp_sum16(const float (&v)[16], int lane) {
   return t;
 }
 
+// tcgen05.wait::ld that also names the registers of the loads it waits for, so that
+// the compiler keeps their uses after it (a load's destination registers are valid
+// only once the wait returns).
+__device__ __forceinline__ void tmem_wait_regs(float (&v)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),
+                 "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]),
+                 "+f"(v[15])
+               :
+               : "memory");
+}
+// Marks registers as written by a preceding wait (after tmem_wait_regs of other
+// registers has waited for all loads).
+__device__ __forceinline__ void tmem_bind_regs(float (&v)[16]) {
+  asm volatile(""
+               : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),
+                 "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]),
+                 "+f"(v[15])
+               :
+               : "memory");
+}
+
 __device__ __forceinline__ void slot_sync(int s) {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + s), "r"(kSlotThreads) : "memory");
 }
@@ -258,6 +280,16 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
     uint32_t pa = 0;
     int cur_code = -1;
     float c = 0.f;
+    // coordinates of this thread's point of a tile (thread et < kPts), loaded one
+    // tile ahead so that their latency hides behind the current tile
+    auto load_x = [&](int tt, float& x0, float& x1) {
+      const int n = (tt % p.tiles_per_code) * kPts + et;
+      const bool ok = tt >= 0 && tt < p.n_tiles && et < kPts && n >= 0 && n < p.n_pts;
+      x0 = ok ? __ldg(p.x + (size_t)n * m) : 0.f;
+      x1 = (ok && m > 1) ? __ldg(p.x + (size_t)n * m + 1) : 0.f;
+    };
+    float xn0, xn1;
+    load_x(blockIdx.x * kSlots + s, xn0, xn1);
     for (int t = blockIdx.x * kSlots + s; t < p.n_tiles; t += stride) {
       const int code = t / p.tiles_per_code;
       const int p0 = (t % p.tiles_per_code) * kPts;
@@ -269,9 +301,10 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
       }
       slot_sync(s);  // the previous tile's outputs are written
       if (et < kPts) {
-        const int n = p0 + et;
-        for (int k = 0; k < m; ++k) S->xs[s][k][et] = (n < p.n_pts) ? p.x[(size_t)n * m + k] : 0.f;
+        S->xs[s][0][et] = xn0;
+        S->xs[s][1][et] = xn1;
       }
+      load_x(t + stride, xn0, xn1);
       slot_sync(s);
       // ---- layer 1 on CUDA cores
 #pragma unroll 1
@@ -298,12 +331,29 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
         tc_fence_after();
         const float bias = S->bh[l][u];
         const f32x2 b2 = pk2(bias, bias);
-#pragma unroll 1
-        for (int n0 = hf * kPer; n0 < hf * kPer + kPer; n0 += 16) {
-          float v[16], w[16];
-          tmem_ld16(taddr(acc, lane_base, n0), v);
-          if (kSplit) tmem_ld16(taddr(acc, lane_base, 64 + n0), w);
-          tmem_ld_wait();
+        // The accumulator chunks (16 points each) of this thread's half: the next
+        // chunk's TMEM load is in flight while this one is computed.
+        constexpr int kChunks = kPer / 16;
+        float va[16], vb[16], wa[16], wb[16];
+        tmem_ld16(taddr(acc, lane_base, hf * kPer), va);
+        if (kSplit) tmem_ld16(taddr(acc, lane_base, 64 + hf * kPer), wa);
+        if (kSplit) {
+          tmem_wait_regs(va);
+          tmem_bind_regs(wa);
+        } else {
+          tmem_wait_regs(va);
+        }
+#pragma unroll
+        for (int ci = 0; ci < kChunks; ++ci) {
+          const int n0 = hf * kPer + 16 * ci;
+          float(&v)[16] = (ci & 1) ? vb : va;
+          float(&w)[16] = (ci & 1) ? wb : wa;
+          float(&vn)[16] = (ci & 1) ? va : vb;
+          float(&wn)[16] = (ci & 1) ? wa : wb;
+          if (ci + 1 < kChunks) {
+            tmem_ld16(taddr(acc, lane_base, n0 + 16), vn);
+            if (kSplit) tmem_ld16(taddr(acc, lane_base, 64 + n0 + 16), wn);
+          }
           f32x2 h[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
@@ -324,6 +374,10 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
             }
             const float tsum = warp_sum16(wv, lane);
             if ((lane & 1) == 0) S->outp[s][lq][n0 + ((lane >> 1) & 15)] = tsum;
+          }
+          if (ci + 1 < kChunks) {
+            tmem_wait_regs(vn);
+            if (kSplit) tmem_bind_regs(wn);
           }
         }
         tc_fence_before();
@@ -372,7 +426,7 @@ cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const d
   p.tiles_per_code = (n_pts + tile_pts - 1) / tile_pts;
   p.flag = ctx->queue + 2;
   const long long tiles = (long long)n_codes * p.tiles_per_code;
-  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (tiles > 0x7fffffffLL - 4096) return cudaErrorInvalidValue;  // t + stride stays an int
   p.n_tiles = (int)tiles;
   const size_t smem = 1024 + (size_t)p.hidden_bytes + (size_t)kSlots * kHBuf + sizeof(Shared);
   const int grid = (int)std::min<long long>((tiles + kSlots - 1) / kSlots, ctx->num_sms);
