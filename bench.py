@@ -557,6 +557,32 @@ def main():
     f16_ms = time_step(crom.CROM_PREC_F16, min(args.steps, 100))
     f16_acc = accuracy(crom.CROM_PREC_F16) if rank == 0 else None
 
+    # ---- Step 1 alone on the tensor cores (crom_decode_tc): value, dg/dx, Laplacian and
+    # dg/dq at the batch's 273,723 integration samples
+    want_all = crom.CROM_WANT_VAL | crom.CROM_WANT_DX | crom.CROM_WANT_LAP | crom.CROM_WANT_DQ
+    dec_out = torch.empty((1 + 2 + 1 + w.spec.r, samples.shape[0]), dtype=torch.float32, device="cuda")
+
+    def time_decode(prec, n=20):
+        for _ in range(3):
+            crom.crom_decode_tc(ctx, q0, s_off, samples, want_all, dec_out, precision=prec)
+        torch.cuda.synchronize()
+        evs_d = []
+        for _ in range(n):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            crom.crom_decode_tc(ctx, q0, s_off, samples, want_all, dec_out, precision=prec)
+            b.record(stream)
+            evs_d.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in evs_d]))
+
+    dec_ms = time_decode(crom.CROM_PREC_F16X2)
+    dec_ms_f16 = time_decode(crom.CROM_PREC_F16)
+    # forward channels (value, dg/dx_1, dg/dx_2, Laplacian) and one reverse pass over the
+    # 4 hidden matrices, 2 w^2 FLOP each
+    dec_flops = int(w.sizes.sum()) * 5 * 4 * 2 * 128 * 128
+
     # ---- end to end through the C ABI on host arrays (crom_step_host: the library
     # copies the pinned inputs in, steps, copies q and status out and synchronises)
     hq0 = torch.tensor(w.q0, dtype=torch.float64)
@@ -755,6 +781,12 @@ def main():
                       "ms_per_step_large_small_s1": [round(tile_ms[0], 4), round(tile_ms[1], 4)]},
             "status_all_ok": bool(np.all(st == 0)),
             "accuracy_vs_fp64_oracle": acc,
+            "decode_tc": {"points_per_s": int(w.sizes.sum()) / (dec_ms * 1e-3), "ms": dec_ms,
+                          "tflops_algorithmic": dec_flops / (dec_ms * 1e-3) / 1e12,
+                          "frac_of_measured_bf16": dec_flops / (dec_ms * 1e-3) / 1e12 / peak_tf,
+                          "f16_single_ms": dec_ms_f16,
+                          "workload": "crom_decode_tc F16X2: g, dg/dx, Laplacian, dg/dq (r = 8) at the batch's "
+                                      "273,723 samples of 1024 instances"},
             "f16_single_step": {"ms_per_step": f16_ms, "value": world * w.n_inst / (f16_ms * 1e-3),
                                 "unit": "instance-steps/s",
                                 "tflops_algorithmic": flops / (f16_ms * 1e-3) / 1e12,

@@ -199,6 +199,28 @@ int crom_set_weights(crom_ctx* ctx, const float* params, size_t n, int params_on
 int crom_decode(crom_ctx* ctx, int n_inst, const double* q, const int* pt_off, const float* x,
                 int n_pts, unsigned want, float* out, crom_stream stream);
 
+/* Step 1 alone on the tcgen05 tensor cores (paper §4.1, Algorithm 4: the batched
+ * network inference of the latent step, as the tensor-core step computes it):
+ * the same arguments, point layout and channel-major output as crom_decode, with
+ * precision CROM_PREC_F16X2 or CROM_PREC_F16 and want ⊆ VAL | DX | LAP | DQ
+ * (CROM_WANT_DXX returns CROM_ERR_UNSUPPORTED: the tensor-core path carries the
+ * m second-derivative channels summed into one Laplacian channel).  DQ comes from
+ * one reverse-mode pass.  The points are processed in chunks of 256 spread over
+ * the GPU whatever the instances' sizes; pt_off must be non-decreasing from 0 to
+ * n_pts (points outside [pt_off[0], pt_off[n_inst]) are not written).  Same shape
+ * limits as the F16X2 step; precision as the step's (f16 weights; F16X2 hi/lo
+ * activations, F16 single).  Asynchronous on `stream`; a device-side wait that ran
+ * out is reported by crom_device_flags. */
+int crom_decode_tc(crom_ctx* ctx, int precision, int n_inst, const double* q, const int* pt_off, const float* x,
+                   int n_pts, unsigned want, float* out, crom_stream stream);
+
+/* Device-side failure flags of the context's tensor-core kernels: synchronises
+ * `stream` and sets *flags to bit 0 = the last tensor-core step or decode launch
+ * gave up on a bounded wait (its unfinished instances carry CROM_ERR_TIMEOUT),
+ * bit 1 = a tensor-core reconstruction gave up since the last call (its output is
+ * incomplete); bit 1 is cleared by the call.  0 after every normal run. */
+int crom_device_flags(crom_ctx* ctx, int* flags, crom_stream stream);
+
 /* One latent step for n_inst independent instances sharing the decoder
  * (paper Algorithm 3).  Instance i has latent state q[i] (FP64 [n_inst][r],
  * updated in place), coefficient alpha[i] (FP32), and integration samples

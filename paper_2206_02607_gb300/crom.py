@@ -53,7 +53,7 @@ EXPORTED = ("crom_version", "crom_last_error", "crom_create", "crom_destroy", "c
             "crom_trainer_destroy", "crom_trainer_param_count", "crom_trainer_set_params",
             "crom_trainer_get_params", "crom_trainer_get_grads", "crom_train_step", "crom_encode",
             "crom_reconstruct", "crom_robust_samples", "crom_tangent_velocity", "crom_trainer_set_precision",
-            "crom_set_step_tiles", "crom_get_step_tiles", "crom_autotune")
+            "crom_set_step_tiles", "crom_get_step_tiles", "crom_autotune", "crom_decode_tc", "crom_device_flags")
 
 
 class CromError(RuntimeError):
@@ -84,6 +84,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.crom_destroy.argtypes = [vp]
     lib.crom_set_weights.argtypes = [vp, vp, sz, i, vp]
     lib.crom_decode.argtypes = [vp, i, vp, vp, vp, i, u, vp, vp]
+    lib.crom_decode_tc.argtypes = [vp, i, i, vp, vp, vp, i, u, vp, vp]
+    lib.crom_device_flags.argtypes = [vp, ctypes.POINTER(i), vp]
     lib.crom_step.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, i, vp, vp, vp, vp, vp, i, i, vp, vp]
     lib.crom_step_noalloc.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, vp, vp, vp, vp, vp, i, i, vp, vp]
     lib.crom_step_host.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, i, vp, vp, vp, vp, vp, i, i, vp, vp]
@@ -193,6 +195,23 @@ def crom_decode(ctx: CromContext, q, pt_off, x, want: int, out, stream=None):
     _need(x, torch.float32, "x"); _need(out, torch.float32, "out")
     _check(_LIB.crom_decode(ctx.handle, q.shape[0], _ptr(q), _ptr(pt_off), _ptr(x), x.shape[0], want,
                             _ptr(out), _stream(stream)))
+
+
+def crom_decode_tc(ctx: CromContext, q, pt_off, x, want: int, out, precision: int = CROM_PREC_F16X2, stream=None):
+    """Step 1 on the tensor cores (want: VAL, DX, LAP, DQ; no DXX)."""
+    import torch
+    _need(q, torch.float64, "q"); _need(pt_off, torch.int32, "pt_off")
+    _need(x, torch.float32, "x"); _need(out, torch.float32, "out")
+    _check(_LIB.crom_decode_tc(ctx.handle, precision, q.shape[0], _ptr(q), _ptr(pt_off), _ptr(x), x.shape[0], want,
+                               _ptr(out), _stream(stream)))
+
+
+def crom_device_flags(ctx: CromContext, stream=None) -> int:
+    """Bit 0: the last tensor-core step / decode launch gave up on a bounded wait;
+    bit 1: a tensor-core reconstruction did since the last call."""
+    f = ctypes.c_int(0)
+    _check(_LIB.crom_device_flags(ctx.handle, ctypes.byref(f), _stream(stream)))
+    return f.value
 
 
 def crom_step(ctx: CromContext, q, alpha, s_off, samples, status, *, dt: float, gn_iters: int,

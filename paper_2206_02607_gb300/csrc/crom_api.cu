@@ -315,6 +315,44 @@ int crom_decode(crom_ctx* ctx, int n_inst, const double* q, const int* pt_off, c
   return CROM_OK;
 }
 
+int crom_decode_tc(crom_ctx* ctx, int precision, int n_inst, const double* q, const int* pt_off, const float* x,
+                   int n_pts, unsigned want, float* out, crom_stream stream) {
+  const char* fn = "crom_decode_tc";
+  if (!ctx) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": null context");
+  if (!ctx->has_weights) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": weights not set");
+  if (n_inst < 0 || n_pts < 0) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": negative size");
+  if ((want & ~31u) != 0 || want == 0) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": bad channel mask");
+  if (want & CROM_WANT_DXX)
+    return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": the per-coordinate second derivatives (CROM_WANT_DXX) "
+                                                        "are FP32-only (crom_decode); the Laplacian is available");
+  if (precision != CROM_PREC_F16X2 && precision != CROM_PREC_F16)
+    return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": precision F16X2 or F16");
+  if (!tc_shape_ok(ctx->desc) || !ctx->w.tc_img)
+    return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": needs width 128, 2<=hidden<=5, m<=2, r<=15, ELU");
+  if (n_pts == 0) return CROM_OK;
+  if (n_inst == 0 || !q || !pt_off || !x || !out)
+    return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": null array or no instance for the points");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = launch_decode_tc(ctx, precision == CROM_PREC_F16X2, n_inst, q, pt_off, x, n_pts, want, out,
+                                   (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, fn);
+  return CROM_OK;
+}
+
+int crom_device_flags(crom_ctx* ctx, int* flags, crom_stream stream) {
+  if (!ctx || !flags) return fail(CROM_ERR_INVALID_ARG, "crom_device_flags: null argument");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int q[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaMemcpyAsync(q, ctx->queue, sizeof(q), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->queue + 2, 0, sizeof(int), s);  // the reconstruction's flag is sticky
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "crom_device_flags");
+  *flags = (q[1] ? 1 : 0) | (q[2] ? 2 : 0);
+  return CROM_OK;
+}
+
 int crom_tangent_velocity(crom_ctx* ctx, int n_inst, const double* q, const double* q_prev, double dt,
                           const int* pt_off, const float* x, int n_pts, float* out, crom_stream stream) {
   const char* fn = "crom_tangent_velocity";

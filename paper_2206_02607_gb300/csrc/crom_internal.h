@@ -211,6 +211,10 @@ cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int lo_par
                            const float* alpha, const float* vel, const int* s_off,
                            const float* samples, int n_samples, int max_samples, int* status,
                            cudaStream_t s);
+// Step 1 alone on the tensor cores (tc_step.cu, the step kernel's decode mode):
+// want ⊆ VAL | DX | LAP | DQ, out as crom_decode without the DXX rows.
+cudaError_t launch_decode_tc(crom_ctx* ctx, int lo_parts, int n_inst, const double* q, const int* pt_off,
+                             const float* x, int n_pts, unsigned want, float* out, cudaStream_t s);
 cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const double* q, int n_pts,
                             const float* x, float* out, cudaStream_t s);
 

@@ -117,7 +117,14 @@ struct StepParams {
   const int* order;
   int* queue;   // [0] work counter, [1] timeout flag
   double* df;   // [n_samples] Delta f_j
+  // decode mode (crom_decode_tc, the kernel's kDec instantiations): Step 1 alone at the points
+  // x[0 .. n_samples) of the instances off[], written channel-major to dec_out
+  // [rows][n_samples]; the output row of each channel, -1 where not wanted
+  float* dec_out;
+  int row_val, row_dx, row_lap, row_dq;
 };
+// Points per work item of the decode mode (a chunk may span several instances).
+constexpr int kDecChunk = 256;
 
 struct __align__(16) Shared {
   uint64_t bar_w;
@@ -449,8 +456,8 @@ __device__ __forceinline__ void sig1(const Lane& c, const Group* G, float cc, in
 // kSm..2kSm-1), the Jacobian projection and these samples' share of J^T J, J^T rho
 // (and rho^T rho for the line search).  s'(z_l) of hidden layer l + 2 is read from
 // TMEM column kSig + l * kSS + slot.
-template <int kM, int kSm, int kSS, bool kLoP>
-__device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int ns, Own& o) {
+template <int kM, int kSm, int kSS, bool kLoP, bool kDec = false>
+__device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int j0, int ns, Own& o) {
   constexpr int kPer = kSm / kTPU;
   constexpr int kC = kPer < 8 ? kPer : 8;
   Group* G = c.G;
@@ -508,6 +515,16 @@ __device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int n
     }
   }
   group_sync(c.g);
+  if constexpr (kDec) {  // decode mode: dg/dq rows of the tile's samples (hi + lo parts)
+    const int n = ns * p.r;
+    for (int e = c.gt; e < n; e += kGT) {
+      const int jq = e / ns, sq = e % ns;
+      float v = jrow(G, 0, sq)[jq];
+      if (kLoP) v = __fadd_rn(v, jrow(G, 1, sq)[jq]);
+      p.dec_out[(size_t)(p.row_dq + jq) * p.n_samples + j0 + sq] = v;
+    }
+    return true;
+  }
   // ---------------- this tile's normal-equation terms
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
@@ -530,7 +547,7 @@ __device__ __forceinline__ bool reverse_tile(Lane& c, const StepParams& p, int n
 // (coordinates xs, residual rho, and the TMEM columns kSig + l * kSS + slot that keep
 // s'(z) of hidden layer l + 2 for the reverse pass), so that two tiles of iteration
 // 0 can share one reverse pass.
-template <int kM, int kSm, bool kFirst, int kSS, bool kLoP>
+template <int kM, int kSm, bool kFirst, int kSS, bool kLoP, bool kDec = false>
 __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j0, int so, int ns, float alpha) {
   constexpr int kCh = kFirst ? 2 + kM : 2;  // iteration 0: v, dx_1..dx_m, Lap; later: v(q^(k)), diff
   constexpr int kN = kCh * kSm;             // hi columns 0..kN-1, lo columns kLo..kLo+kN-1
@@ -625,16 +642,17 @@ __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j
         const int lane = c.gt & 31, lq = c.gw & 3, sl = s0 + h8 + ((lane >> 2) & 7);
         float* pr = &G->jt[0][0][0];
 #pragma unroll
-        for (int ch = 1; ch < kCh; ++ch) {
-          // iteration 0: the gradient channels only for advection, the Laplacian always;
-          // later: the difference channel
-          const bool need = !kFirst || ch == kCh - 1 || p.pde != CROM_PDE_HEAT;
+        for (int ch = 0; ch < kCh; ++ch) {
+          // step, iteration 0: the gradient channels only for advection, the Laplacian
+          // always; later: the difference channel; decode: the requested channels
+          const bool need = kDec ? (ch == 0 ? p.row_val >= 0 : ch == kCh - 1 ? p.row_lap >= 0 : p.row_dx >= 0)
+                                 : ch >= 1 && (!kFirst || ch == kCh - 1 || p.pde != CROM_PDE_HEAT);
           if (need) {
             float wv[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) wv[i] = c.wo * v[ch][i];
             const float t = warp_sum8(wv, lane);
-            if ((lane & 3) == 0) pr[((ch - 1) * 4 + lq) * kSm + sl] = t;
+            if ((lane & 3) == 0) pr[(ch * 4 + lq) * kSm + sl] = t;
           }
         }
       }
@@ -643,12 +661,23 @@ __device__ __forceinline__ bool forward_tile(Lane& c, const StepParams& p, int j
     // before the reverse pass, which waits for them
   }
   group_sync(c.g);
-  // output channel ch (>= 1) of tile sample s: the four quadrants' partial sums
+  // output channel ch of tile sample s: the four quadrants' partial sums
   auto gout = [&](int ch, int s) {
     const float* pr = &G->jt[0][0][0];
-    const int b = (ch - 1) * 4 * kSm + s;
+    const int b = ch * 4 * kSm + s;
     return (pr[b] + pr[b + kSm]) + (pr[b + 2 * kSm] + pr[b + 3 * kSm]);
   };
+  if constexpr (kDec) {  // decode mode: the requested channels of the tile's samples
+    if (c.gt < ns) {
+      const size_t n = (size_t)p.n_samples, j = (size_t)(j0 + c.gt);
+      if (p.row_val >= 0) p.dec_out[(size_t)p.row_val * n + j] = gout(0, c.gt) + p.bout;
+      if (p.row_dx >= 0)
+        for (int k = 0; k < kM; ++k) p.dec_out[(size_t)(p.row_dx + k) * n + j] = gout(1 + k, c.gt) * p.sxi;
+      if (p.row_lap >= 0) p.dec_out[(size_t)p.row_lap * n + j] = gout(kCh - 1, c.gt) * p.sx2i;
+    }
+    tmem_st_wait();
+    return true;
+  }
   // ---------------- Step 2 and the residual rho_j
   if (c.gt < kSm) {
     float rho = 0.f;
@@ -690,7 +719,7 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
       if (o.ea[e] == -3) o.acc[e] += dot_exact<false, false>(c.G->rho, c.G->zero, 1, c.G->rho, c.G->zero, 1, ns);
     return true;
   } else {
-    return reverse_tile<kM, kSm, kSm, kLoP>(c, p, ns, o);
+    return reverse_tile<kM, kSm, kSm, kLoP>(c, p, o0 + t * kSm, ns, o);
   }
 }
 
@@ -700,16 +729,18 @@ __device__ __forceinline__ bool run_tile(Lane& c, const StepParams& p, int o0, i
 // the four-channel forward pass needs narrow tiles to fit the 32 hi columns of one
 // N = 64 UMMA, the
 // reverse pass does not.
-template <int kM, bool kLoP>
+template <int kM, bool kLoP, bool kDec = false>
 __device__ __forceinline__ bool run_pair(Lane& c, const StepParams& p, int o0, int t, int ns, float alpha, Own& o) {
   constexpr int kS0 = tile_s0<kLoP>();
   constexpr int kSS = 2 * kS0;
   const int j0 = o0 + t * kSS;
-  if (!forward_tile<kM, kS0, true, kSS, kLoP>(c, p, j0, 0, min(ns, kS0), alpha)) return false;
-  if (ns <= kS0) return reverse_tile<kM, kS0, kSS, kLoP>(c, p, ns, o);
-  if (!forward_tile<kM, kS0, true, kSS, kLoP>(c, p, j0 + kS0, kS0, ns - kS0, alpha)) return false;
-  return reverse_tile<kM, kSS, kSS, kLoP>(c, p, ns, o);
+  if (!forward_tile<kM, kS0, true, kSS, kLoP, kDec>(c, p, j0, 0, min(ns, kS0), alpha)) return false;
+  const bool rev = !kDec || p.row_dq >= 0;  // decode mode: the reverse pass only for dg/dq
+  if (ns <= kS0) return rev ? reverse_tile<kM, kS0, kSS, kLoP, kDec>(c, p, j0, ns, o) : true;
+  if (!forward_tile<kM, kS0, true, kSS, kLoP, kDec>(c, p, j0 + kS0, kS0, ns - kS0, alpha)) return false;
+  return rev ? reverse_tile<kM, kSS, kSS, kLoP, kDec>(c, p, j0, ns, o) : true;
 }
+
 
 // Layer-1 constants of the tile passes at the point q: c1 = b_1 + W_1q q (value
 // channel) and dz1 = W_1q (q - q_n) (difference channel), FP64 sums rounded once;
@@ -739,7 +770,40 @@ __device__ __forceinline__ void set_layer1(Lane& c, const StepParams& p, Group* 
   G->dz1[c.u] = dzf * c.dsc;
 }
 
-template <int kM, int kS1, bool kLoP>
+// Decode mode: the points a .. b-1 of one work item, instance by instance (the
+// instance of point a found by bisection of off; off non-decreasing from off[0] = 0).
+// Points beyond off[n_inst] are left untouched.
+template <int kM, bool kLoP>
+__device__ __forceinline__ bool decode_chunk(Lane& c, const StepParams& p, int a, int b, Own& o) {
+  constexpr int kS0 = tile_s0<kLoP>();
+  Group* G = c.G;
+  int lo = 0, hi = p.n_inst;  // largest inst with off[inst] <= a, in [0, n_inst)
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (p.off[mid] <= a) lo = mid;
+    else hi = mid;
+  }
+  bool ok = true;
+  for (int inst = lo; inst < p.n_inst && a < b && ok; ++inst) {
+    const int e = min(b, p.off[inst + 1]);
+    if (e <= a) continue;
+    group_sync(c.g);  // the previous range's layer-1 constants are no longer read
+    if (c.gt < p.r) {
+      const double v = p.q[(size_t)inst * p.r + c.gt];
+      G->qn[c.gt] = v;
+      G->qcur[c.gt] = v;
+    }
+    group_sync(c.g);
+    set_layer1<kM>(c, p, G, G->qcur);
+    const int M = e - a, nt = (M + 2 * kS0 - 1) / (2 * kS0);
+    for (int t = 0; t < nt && ok; ++t)
+      ok = run_pair<kM, kLoP, true>(c, p, a, t, min(2 * kS0, M - t * 2 * kS0), 0.f, o);
+    a = e;
+  }
+  return ok;
+}
+
+template <int kM, int kS1, bool kLoP, bool kDec = false>
 __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
   constexpr int kS0 = tile_s0<kLoP>();
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -832,6 +896,12 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(StepParams p) {
     if (c.gt == 0) G->s_idx = atomicAdd(&p.queue[0], 1);
     group_sync(c.g);
     const int idx = G->s_idx;
+    if constexpr (kDec) {  // decode mode: work item idx is a chunk of kDecChunk points
+      const long a0 = (long)idx * kDecChunk;
+      if (a0 >= p.n_samples) break;
+      ok = decode_chunk<kM, kLoP>(c, p, (int)a0, (int)min(a0 + kDecChunk, (long)p.n_samples), own);
+      continue;
+    }
     if (idx >= p.n_inst) break;
     const int inst = p.order[idx];
     const int o0 = p.off[inst];
@@ -1060,6 +1130,60 @@ cudaError_t launch_step_tc(crom_ctx* ctx, const crom_step_desc* step, int lo_par
   if (ctx->desc.m == 2)
     return small_tiles ? launch(step_tc_kernel<2, 2 * kSmall, false>) : launch(step_tc_kernel<2, 2 * kLarge, false>);
   return small_tiles ? launch(step_tc_kernel<1, 2 * kSmall, false>) : launch(step_tc_kernel<1, 2 * kLarge, false>);
+}
+
+cudaError_t launch_decode_tc(crom_ctx* ctx, int lo_parts, int n_inst, const double* q, const int* pt_off,
+                             const float* x, int n_pts, unsigned want, float* out, cudaStream_t s) {
+  StepParams p{};
+  p.img = ctx->w.tc_img;
+  p.img_bytes = (int)ctx->w.tc_img_bytes;
+  p.sx = ctx->w.tc_sx;
+  p.sxi = 1.f / ctx->w.tc_sx;
+  p.sx2i = p.sxi * p.sxi;
+  p.sr = ctx->w.tc_sr;
+  p.sri = 1.f / ctx->w.tc_sr;
+  p.L = ctx->desc.hidden;
+  p.r = ctx->desc.r;
+  p.w1 = ctx->w.w1;
+  p.b1 = ctx->w.b1;
+  p.bh = ctx->w.bh;
+  p.wout = ctx->w.wout;
+  p.bout = ctx->w.bout;
+  p.pde = CROM_PDE_HEAT;
+  p.gn_iters = 1;
+  p.dt = 1.0;
+  p.n_inst = n_inst;
+  p.q = const_cast<double*>(q);  // read only in decode mode
+  p.off = pt_off;
+  p.x = x;
+  p.max_samples = n_pts;
+  p.n_samples = n_pts;
+  p.queue = ctx->queue;
+  p.dec_out = out;
+  const int m = ctx->desc.m;
+  int row = 0;
+  p.row_val = (want & CROM_WANT_VAL) ? row++ : -1;
+  p.row_dx = (want & CROM_WANT_DX) ? row : -1;
+  if (want & CROM_WANT_DX) row += m;
+  p.row_lap = (want & CROM_WANT_LAP) ? row++ : -1;
+  p.row_dq = (want & CROM_WANT_DQ) ? row : -1;
+  cudaError_t e = cudaMemsetAsync(ctx->queue, 0, 2 * sizeof(int), s);  // work counter, timeout flag
+  if (e != cudaSuccess) return e;
+  const size_t smem = tc_step_smem_bytes(p.img_bytes);
+  const long chunks = ((long)n_pts + kDecChunk - 1) / kDecChunk;
+  const int grid = (int)std::min<long>((chunks + kGroups - 1) / kGroups, ctx->num_sms);
+  auto launch = [&](auto kernel) -> cudaError_t {
+    cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    kernel<<<grid, kThreads, smem, s>>>(p);
+    return cudaGetLastError();
+  };
+  // the later-iteration tile size is not used in decode mode: the default instantiations
+  constexpr int kLarge = kTcTileS1Large;
+  if (lo_parts)
+    return m == 2 ? launch(step_tc_kernel<2, kLarge, true, true>) : launch(step_tc_kernel<1, kLarge, true, true>);
+  return m == 2 ? launch(step_tc_kernel<2, 2 * kLarge, false, true>)
+                : launch(step_tc_kernel<1, 2 * kLarge, false, true>);
 }
 
 }  // namespace crom
