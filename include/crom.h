@@ -391,6 +391,28 @@ int crom_trainer_set_precision(crom_trainer* tr, int precision);
 /* Encoder only: q [n][r] FP32 for n <= B snapshots [n][P] (initial latent codes). */
 int crom_encode(crom_trainer* tr, int n, const float* snaps, float* q, crom_stream stream);
 
+/* Checkpoint / resume of a trainer (the paper trains in stages; this lets a run stop
+ * and continue).  crom_trainer_save writes, after synchronising the device, a
+ * binary file: a 64-byte header (magic "CROMCKPT", version 1, m, r, width, hidden,
+ * activation, P, the parameter count, the Adam step count, the CRC-32 of the
+ * payload) and the payload: FP32 parameters, first and second Adam moments, host
+ * byte order.  crom_trainer_load checks magic, version, shapes (the decoder's and
+ * P; B and S may differ) and the checksum (CROM_ERR_INVALID_ARG on any mismatch,
+ * the trainer then unchanged) and restores parameters, moments and step count, so
+ * that the following steps are bit-identical to an uninterrupted run. */
+int crom_trainer_save(crom_trainer* tr, const char* path);
+int crom_trainer_load(crom_trainer* tr, const char* path);
+
+/* CRC-32 (IEEE 802.3, reflected polynomial 0xEDB88320) of n bytes: the checksum
+ * of the checkpoint files. */
+unsigned crom_crc32(const void* data, size_t n);
+
+/* Host-side watchdog: polls the stream until its work has finished (CROM_OK) or
+ * timeout_ms have passed (CROM_ERR_TIMEOUT; the work keeps running and the call
+ * may be repeated); a CUDA error on the stream gives CROM_ERR_CUDA.  Never blocks
+ * in the driver. */
+int crom_stream_wait(crom_stream stream, double timeout_ms);
+
 /* Dense reconstruction g(x_p, q_c) for n_codes latent codes q [n_codes][r]
  * (FP64) at n_pts points x [n_pts][m] (FP32); out [n_codes][n_pts] FP32.
  * precision FP32 (any shape), F16X2 or F16 (tensor cores; width 128). */

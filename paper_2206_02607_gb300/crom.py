@@ -53,7 +53,8 @@ EXPORTED = ("crom_version", "crom_last_error", "crom_create", "crom_destroy", "c
             "crom_trainer_destroy", "crom_trainer_param_count", "crom_trainer_set_params",
             "crom_trainer_get_params", "crom_trainer_get_grads", "crom_train_step", "crom_encode",
             "crom_reconstruct", "crom_robust_samples", "crom_tangent_velocity", "crom_trainer_set_precision",
-            "crom_set_step_tiles", "crom_get_step_tiles", "crom_autotune", "crom_decode_tc", "crom_device_flags")
+            "crom_set_step_tiles", "crom_get_step_tiles", "crom_autotune", "crom_decode_tc", "crom_device_flags",
+            "crom_trainer_save", "crom_trainer_load", "crom_crc32", "crom_stream_wait")
 
 
 class CromError(RuntimeError):
@@ -86,6 +87,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.crom_decode.argtypes = [vp, i, vp, vp, vp, i, u, vp, vp]
     lib.crom_decode_tc.argtypes = [vp, i, i, vp, vp, vp, i, u, vp, vp]
     lib.crom_device_flags.argtypes = [vp, ctypes.POINTER(i), vp]
+    lib.crom_trainer_save.argtypes = [vp, ctypes.c_char_p]
+    lib.crom_trainer_load.argtypes = [vp, ctypes.c_char_p]
+    lib.crom_crc32.argtypes = [vp, ctypes.c_size_t]
+    lib.crom_crc32.restype = ctypes.c_uint
+    lib.crom_stream_wait.argtypes = [vp, d]
     lib.crom_step.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, i, vp, vp, vp, vp, vp, i, i, vp, vp]
     lib.crom_step_noalloc.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, vp, vp, vp, vp, vp, i, i, vp, vp]
     lib.crom_step_host.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, i, vp, vp, vp, vp, vp, i, i, vp, vp]
@@ -107,7 +113,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.crom_robust_samples.argtypes = [vp, ctypes.POINTER(crom_step_desc), i, i, vp, vp, i, i, vp, vp, i, vp, i,
                                         d, i, vp, vp, vp, vp]
     for name in EXPORTED:
-        if name not in ("crom_version", "crom_last_error"):
+        if name not in ("crom_version", "crom_last_error", "crom_crc32"):
             getattr(lib, name).restype = i
     return lib
 
@@ -204,6 +210,24 @@ def crom_decode_tc(ctx: CromContext, q, pt_off, x, want: int, out, precision: in
     _need(x, torch.float32, "x"); _need(out, torch.float32, "out")
     _check(_LIB.crom_decode_tc(ctx.handle, precision, q.shape[0], _ptr(q), _ptr(pt_off), _ptr(x), x.shape[0], want,
                                _ptr(out), _stream(stream)))
+
+
+def crom_trainer_save(tr, path: str):
+    _check(_LIB.crom_trainer_save(tr.handle, str(path).encode()))
+
+
+def crom_trainer_load(tr, path: str):
+    _check(_LIB.crom_trainer_load(tr.handle, str(path).encode()))
+
+
+def crom_crc32(data: bytes) -> int:
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    return int(_LIB.crom_crc32(buf, len(data)))
+
+
+def crom_stream_wait(timeout_ms: float, stream=None):
+    """Raises CromError(CROM_ERR_TIMEOUT) if the stream's work is not done in time."""
+    _check(_LIB.crom_stream_wait(_stream(stream), float(timeout_ms)))
 
 
 def crom_device_flags(ctx: CromContext, stream=None) -> int:

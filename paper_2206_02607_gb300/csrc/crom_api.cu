@@ -4,6 +4,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <thread>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -778,6 +780,121 @@ int crom_trainer_destroy(crom_trainer* tr) {
   }
   delete tr;
   return CROM_OK;
+}
+
+// ---- checkpoint / resume of a trainer, and a host-side deadline on a stream
+
+unsigned crom_crc32(const void* data, size_t n) {
+  // CRC-32 (IEEE 802.3): reflected polynomial 0xEDB88320, initial value and final
+  // xor 0xFFFFFFFF, one bit at a time
+  const unsigned char* b = static_cast<const unsigned char*>(data);
+  uint32_t c = 0xFFFFFFFFu;
+  for (size_t i = 0; i < n; ++i) {
+    c ^= b[i];
+    for (int k = 0; k < 8; ++k) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+  }
+  return c ^ 0xFFFFFFFFu;
+}
+
+namespace {
+struct CkptHeader {
+  char magic[8];  // "CROMCKPT"
+  uint32_t version;
+  int32_t m, r, width, hidden, activation, P;
+  uint64_t n_params;
+  int64_t step;
+  uint32_t crc;  // of params, first and second Adam moments, in that order
+  uint32_t pad;
+};
+constexpr uint32_t kCkptVersion = 1;
+
+// The trainer's parameters and Adam moments on the host, in file order.
+int trainer_state_to_host(crom_trainer* tr, std::vector<float>& buf, const char* fn) {
+  const size_t n = trainer_param_count(tr);
+  buf.resize(3 * n);
+  DeviceGuard g(tr->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(buf.data(), tr->params, n * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(buf.data() + n, tr->am, n * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(buf.data() + 2 * n, tr->av, n * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, fn);
+  return CROM_OK;
+}
+}  // namespace
+
+int crom_trainer_save(crom_trainer* tr, const char* path) {
+  const char* fn = "crom_trainer_save";
+  if (!tr || !path) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": null argument");
+  std::vector<float> buf;
+  int st = trainer_state_to_host(tr, buf, fn);
+  if (st != CROM_OK) return st;
+  CkptHeader h{};
+  memcpy(h.magic, "CROMCKPT", 8);
+  h.version = kCkptVersion;
+  h.m = tr->dec.m;
+  h.r = tr->dec.r;
+  h.width = tr->dec.width;
+  h.hidden = tr->dec.hidden;
+  h.activation = tr->dec.activation;
+  h.P = tr->P;
+  h.n_params = trainer_param_count(tr);
+  h.step = tr->step;
+  h.crc = crom_crc32(buf.data(), buf.size() * 4);
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": cannot open " + path);
+  const bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+  const bool closed = fclose(f) == 0;
+  if (!ok || !closed) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": write failed for " + path);
+  return CROM_OK;
+}
+
+int crom_trainer_load(crom_trainer* tr, const char* path) {
+  const char* fn = "crom_trainer_load";
+  if (!tr || !path) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": null argument");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": cannot open " + path);
+  CkptHeader h{};
+  const size_t n = trainer_param_count(tr);
+  std::vector<float> buf;
+  bool ok = fread(&h, sizeof(h), 1, f) == 1;
+  if (ok && (memcmp(h.magic, "CROMCKPT", 8) != 0 || h.version != kCkptVersion)) {
+    fclose(f);
+    return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": not a trainer checkpoint of this version");
+  }
+  if (ok && (h.m != tr->dec.m || h.r != tr->dec.r || h.width != tr->dec.width || h.hidden != tr->dec.hidden ||
+             h.activation != tr->dec.activation || h.P != tr->P || h.n_params != n)) {
+    fclose(f);
+    return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": the checkpoint's shapes differ from the trainer's");
+  }
+  if (ok) {
+    buf.resize(3 * n);
+    ok = fread(buf.data(), 4, buf.size(), f) == buf.size();
+  }
+  fclose(f);
+  if (!ok) return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": truncated file " + path);
+  if (crom_crc32(buf.data(), buf.size() * 4) != h.crc)
+    return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": checksum mismatch in " + path);
+  DeviceGuard g(tr->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(tr->params, buf.data(), n * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(tr->am, buf.data() + n, n * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(tr->av, buf.data() + 2 * n, n * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, fn);
+  tr->step = h.step;
+  return CROM_OK;
+}
+
+int crom_stream_wait(crom_stream stream, double timeout_ms) {
+  if (!(timeout_ms >= 0.0)) return fail(CROM_ERR_INVALID_ARG, "crom_stream_wait: timeout must be >= 0");
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery((cudaStream_t)stream);
+    if (e == cudaSuccess) return CROM_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(e, "crom_stream_wait");
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (ms >= timeout_ms) return fail(CROM_ERR_TIMEOUT, "crom_stream_wait: the stream's work did not finish in time");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
 }
 
 int crom_trainer_set_precision(crom_trainer* tr, int precision) {

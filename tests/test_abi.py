@@ -12,7 +12,7 @@ def declared_symbols():
     with open(os.path.join(ROOT, "include", "crom.h")) as f:
         text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(crom_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(crom_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
@@ -68,3 +68,17 @@ def test_missing_library_fails_loudly(tmp_path):
     from paper_2206_02607_gb300 import crom
     with pytest.raises(ImportError):
         crom.load_library(str(tmp_path / "libcrom.so"))
+
+
+def test_checkpoint_checksum_is_crc32(lib):
+    """The checkpoint checksum is CRC-32 (IEEE): the standard check value of the
+    ASCII digits 1..9 is 0xCBF43926, and random buffers agree with zlib's
+    independent implementation (host code only, no device)."""
+    import zlib
+    import numpy as np
+    assert lib.crom_crc32(b"123456789") == 0xCBF43926
+    assert lib.crom_crc32(b"") == 0
+    rng = np.random.default_rng(0)
+    for n in (1, 7, 64, 1000, 65537):
+        data = rng.integers(0, 256, size=n, dtype=np.uint8).tobytes()
+        assert lib.crom_crc32(data) == zlib.crc32(data)

@@ -13,7 +13,7 @@ import pytest
 
 from workloads import gen
 
-from helpers import dev, make_ctx, run_steps
+from helpers import StepInputs, dev, make_ctx, run_steps
 
 pytestmark = pytest.mark.gpu
 
@@ -114,4 +114,32 @@ def test_fp32_step_grid_limit_is_an_argument_error():
             fn()
         assert e.value.code == c.CROM_ERR_INVALID_ARG and "65535" in str(e.value)
     assert np.array_equal(q.cpu().numpy(), w.q0)
+    ctx.close()
+
+
+def test_stream_wait_deadline():
+    """The host watchdog: a 1000-step rollout of the 1024-instance batch (about a
+    second of GPU work) is not finished after 1 ms, so crom_stream_wait reports
+    TIMEOUT without blocking; waiting again with a long deadline returns OK, and the
+    kernels' own bounded-wait flags stayed clear."""
+    import time
+    import torch
+    c = crom()
+    w = gen.heat2d_batched(n_inst=1024)
+    ctx = make_ctx(w.spec, w.params)
+    d = StepInputs(w)
+    stream = torch.cuda.current_stream()
+    c.crom_rollout(ctx, d.q, d.alpha, d.s_off, d.samples, d.status, n_steps=1000, dt=w.dt, gn_iters=w.gn_iters,
+                   max_samples=d.max_samples, precision=c.CROM_PREC_F16X2)   # records the graph
+    torch.cuda.synchronize()
+    c.crom_rollout(ctx, d.q, d.alpha, d.s_off, d.samples, d.status, n_steps=1000, dt=w.dt, gn_iters=w.gn_iters,
+                   max_samples=d.max_samples, precision=c.CROM_PREC_F16X2)
+    t0 = time.perf_counter()
+    with pytest.raises(c.CromError) as e:
+        c.crom_stream_wait(1.0, stream)
+    assert e.value.code == c.CROM_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 0.5
+    c.crom_stream_wait(60000.0, stream)
+    assert np.all(d.status.cpu().numpy() == 0)
+    assert c.crom_device_flags(ctx) == 0
     ctx.close()

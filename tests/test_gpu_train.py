@@ -178,3 +178,56 @@ def test_train_step_learned_model_shapes(c, prec_name, loss_tol, grad_tol):
     errs = _step_and_check(c, dict(seed=4, n=256, r=16, width=256, hidden=5, B=64, S=4096),
                            getattr(c, prec_name), loss_tol, grad_tol, 1e-2, 1e-2)
     print(prec_name, "max gradient-group rel. L2", max(errs.values()))
+
+
+@pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_BF16_MIXED"])
+def test_checkpoint_resume_is_bit_identical(c, prec_name, tmp_path):
+    """Train 4 steps, save, train 3 more; a fresh trainer that loads the checkpoint
+    and takes the same 3 steps ends with bit-identical parameters and loss (Adam
+    moments and step count restored; every reduction has a fixed order).  A
+    checkpoint of other shapes and a corrupted one are refused and leave the
+    trainer unchanged."""
+    import torch
+    n, r, width, hidden, B, S = 64, 8, 64, 4, 4, 256
+    enc, dec, snaps, pt_idx, coords = make_problem(3, n, r, width, hidden, B, S)
+    p0 = T.flatten(enc, dec).astype(np.float32)
+    sn, pi, co = dev(snaps, torch.float32), dev(pt_idx, torch.int32), dev(coords, torch.float32)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def trainer():
+        tr = c.CromTrainer(2, r, width, hidden, n * n, B, S)
+        tr.set_precision(getattr(c, prec_name))
+        return tr
+
+    a = trainer()
+    a.set_params(p0)
+    for _ in range(4):
+        c.crom_train_step(a, sn, pi, co, 1e-3, loss)
+    path = tmp_path / "trainer.ckpt"
+    c.crom_trainer_save(a, path)
+    for _ in range(3):
+        c.crom_train_step(a, sn, pi, co, 1e-3, loss)
+    torch.cuda.synchronize()
+    pa, la = a.get_params(), loss.item()
+    b = trainer()
+    c.crom_trainer_load(b, path)
+    for _ in range(3):
+        c.crom_train_step(b, sn, pi, co, 1e-3, loss)
+    torch.cuda.synchronize()
+    assert np.array_equal(b.get_params(), pa) and loss.item() == la
+    # refused: other shapes, a flipped payload byte
+    other = c.CromTrainer(2, r, width, hidden + 1, n * n, B, S)
+    with pytest.raises(c.CromError) as e:
+        c.crom_trainer_load(other, path)
+    assert e.value.code == c.CROM_ERR_INVALID_ARG
+    raw = bytearray(path.read_bytes())
+    raw[100] ^= 0x01
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(bytes(raw))
+    before = b.get_params()
+    with pytest.raises(c.CromError) as e:
+        c.crom_trainer_load(b, bad)
+    assert e.value.code == c.CROM_ERR_INVALID_ARG and "checksum" in c.last_error()
+    assert np.array_equal(b.get_params(), before)
+    for t in (a, b, other):
+        t.close()
