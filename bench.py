@@ -750,7 +750,7 @@ def main():
     train_ms = time_train(crom.CROM_PREC_BF16_MIXED, 10)
     pts = Bt * St
     train_flops = pts * 6 * (2 * (2 + rt) * wt + 2 * (Lt - 1) * wt * wt + 2 * wt) / 2
-    train_bytes = (7 * Lt - 4) * pts * wt * 2
+    train_bytes = (7 * Lt - 3) * pts * wt * 2
     tr.close()
 
     next_rows = measure_next_rows(crom, gen, ctx, w, q0, alpha, s_off, samples, status, stream, flush, local)
@@ -821,7 +821,7 @@ def main():
                          "frac_of_measured_bf16": train_flops / (train_ms * 1e-3) / 1e12 / peak_tf,
                          "hbm_gbs_algorithmic": train_bytes / (train_ms * 1e-3) / 1e9,
                          "frac_of_measured_hbm": train_bytes / (train_ms * 1e-3) / 1e9 / hbm,
-                         "bytes_note": "decoder pass: 7 L - 4 reads or writes of a [B*S][w] bf16 array "
+                         "bytes_note": "decoder pass: 7 L - 3 reads or writes of a [B*S][w] bf16 array "
                                        "per step (activations, deltas), the roofline that binds here",
                          "precision": "library tcgen05 GEMMs with fused epilogues, bf16 operands, FP32 "
                                       "accumulation and master weights",

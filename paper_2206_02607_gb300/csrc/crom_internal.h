@@ -110,7 +110,8 @@ struct TrainerTc {
   uint16_t* wh = nullptr;   // bf16 hidden matrices W_1..W_{L-1}, [w][w] each
   std::vector<uint16_t*> H; // bf16 activations of the hidden layers, [B*S][w] each
   uint16_t *d0 = nullptr, *d1 = nullptr;  // bf16 deltas [B*S][w]
-  float *colpart = nullptr, *colpart2 = nullptr, *rowpart = nullptr;  // epilogue partial sums
+  float *colpart = nullptr, *colpart2 = nullptr, *rowpart = nullptr;  // per-32-row partial sums
+  float* resid = nullptr;   // [B*S]: g - f per point (FP32)
   float* colmid = nullptr;  // first level of the column-sum reduction
   float* split = nullptr;   // split-K partials of the weight gradients
   float* xin = nullptr;     // [B*S][m]: the sampled points' coordinates
@@ -227,9 +228,8 @@ enum GemmEpi {
   kGemmEpiF32 = 0,        // out_f32[split][m][n] = D (K split into `splits` ranges)
   kGemmEpiBiasElu = 1,    // out_bf16[m][n] = ELU(D + bias[n])
   kGemmEpiTimesEluD = 2,  // out_bf16[m][n] = D * s'(z), s' from hprev[m][n] = h = ELU(z); colpart = column sums
-  kGemmEpiOut = 3         // last hidden layer: out_bf16 = h_L = ELU(D + bias); per row g = wout . h_L + *bout,
-                          // r = g - target[m], dg = 2 r inv_count; delta_out[m][n] = dg wout[n] s'(z);
-                          // colpart = column sums of delta, colpart2 of dg h_L, rowpart = (sum r^2, sum dg)
+  kGemmEpiOut = 3         // last hidden layer: out_bf16 = h_L = ELU(D + bias); per row the residual
+                          // resid[m] = wout . h_L + *bout - target[m] (FP32 from the FP32 h_L)
 };
 struct TcGemm {
   int M = 0, N = 0, K = 0;
@@ -250,10 +250,7 @@ struct TcGemm {
   const float* wout = nullptr;
   const float* bout = nullptr;  // device scalar
   const float* target = nullptr;
-  uint16_t* delta_out = nullptr;
-  float* colpart2 = nullptr;
-  float* rowpart = nullptr;  // [ceil(M / 128) * 4][2]
-  float inv_count = 0.f;
+  float* resid = nullptr;  // [M]
 };
 bool tc_gemm_supported(int n);
 cudaError_t tc_gemm(const TcGemm& g, int num_sms, int* flag, cudaStream_t s);

@@ -54,10 +54,7 @@ struct Args {
   const float* wout;
   const float* bout;
   const float* target;
-  uint16_t* delta_out;
-  float* colpart2;  // [tiles_m * 4][N]
-  float* rowpart;   // [tiles_m * 4][2]: sum of r^2 and of dg per warp
-  float inv_count;  // 1 / (number of loss terms)
+  float* resid;     // [M]: g - target per row (output-layer epilogue)
   int* flag;
 };
 
@@ -353,14 +350,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       tphase[acc] ^= 1;
       tc_fence_after();
       const uint32_t ta = tb + (uint32_t)acc * kBN + (uint32_t)cb + ((uint32_t)(q * 32) << 16);
-      float gval = 0.f, dg = 0.f, rr = 0.f;
+      float gval = 0.f;
       constexpr int kCh = kHalf / 32;
       const float* sbias = bars->bias + cb;
       const float* swout = bars->wout + cb;
       if (kEpi == kGemmEpiOut) {
-        // output layer g = w_out . h_L + b_out on this row (the two column halves'
-        // partial sums meet in shared memory, added in a fixed order), then the loss terms
-        acc_chunks<kCh, false>(ta, [&](int c0, float(&v)[32]) {
+        // h_L = ELU(z + b) and this half's share of the output layer w_out . h_L (FP32)
+        acc_chunks<kCh, true>(ta, [&](int c0, float(&v)[32]) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const float h = elu_g(v[j] + sbias[c0 + j]);
@@ -369,14 +365,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           }
           stg.put32(lane, c0, v);
         });
-        stg.store_rows(g.out_bf16, g.ldo, row0, cb, g.M, lane);
-        bars->gpart[local & 1][half][q][lane] = gval;
-        asm volatile("bar.sync %0, 64;" ::"r"(1 + q) : "memory");  // the two warps of quadrant q
-        gval = bars->gpart[local & 1][0][q][lane] + bars->gpart[local & 1][1][q][lane];
-        const float r = in ? (gval + __ldg(g.bout) - __ldg(g.target + row)) : 0.f;
-        rr = r * r;
-        dg = 2.f * r * g.inv_count;
-      }
+      } else {
       // pipelined where the epilogue holds one 32-value row (bias + ELU, FP32 partials)
       acc_chunks<kCh, kEpi == kGemmEpiBiasElu || kEpi == kGemmEpiF32>(ta, [&](int c0, float(&v)[32]) {
         const int col = cb + c0;
@@ -398,22 +387,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           stg.put32(lane, c0, v);                    // in place of the h values just read
           const float cs = warp_colsum32(v, lane);  // column sums of delta over this warp's rows
           g.colpart[(long)(mt * 4 + q) * g.N + col + lane] = cs;
-        } else {  // kGemmEpiOut: delta_L = dg w_out s'(z_L) and the column sums of dg h_L, delta_L
-          float dh[32];
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float z = v[j] + sbias[c0 + j];
-            const float h = elu_g(z);
-            dh[j] = in ? dg * h : 0.f;
-            v[j] = in ? dg * swout[c0 + j] * (z > 0.f ? 1.f : h + 1.f) : 0.f;
-          }
-          stg.put32(lane, c0, v);
-          const float cs = warp_colsum32(v, lane);
-          g.colpart[(long)(mt * 4 + q) * g.N + col + lane] = cs;
-          const float cs2 = warp_colsum32(dh, lane);
-          g.colpart2[(long)(mt * 4 + q) * g.N + col + lane] = cs2;
         }
       });
+      }
       // the accumulator is read: hand it back before the stores
       tc_fence_before();
       __syncwarp();
@@ -428,18 +404,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         if (tn < tiles) stg.put_rows(lane, R);
       }
       if (kEpi == kGemmEpiOut) {
-        stg.store_rows(g.delta_out, g.ldo, row0, cb, g.M, lane);
-        if (half == 0) {  // the row terms once per row
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            rr += __shfl_xor_sync(0xffffffffu, rr, o);
-            dg += __shfl_xor_sync(0xffffffffu, dg, o);
-          }
-          if (lane == 0) {
-            g.rowpart[(mt * 4 + q) * 2] = rr;
-            g.rowpart[(mt * 4 + q) * 2 + 1] = dg;
-          }
-        }
+        stg.store_rows(g.out_bf16, g.ldo, row0, cb, g.M, lane);
+        // the two column halves' partial sums meet in shared memory, added in a fixed
+        // order; the residual g - target of each row
+        bars->gpart[local & 1][half][q][lane] = gval;
+        asm volatile("bar.sync %0, 64;" ::"r"(1 + q) : "memory");  // the two warps of quadrant q
+        gval = bars->gpart[local & 1][0][q][lane] + bars->gpart[local & 1][1][q][lane];
+        if (half == 0 && in) g.resid[row] = gval + __ldg(g.bout) - __ldg(g.target + row);
       }
     }
   }
@@ -538,10 +509,7 @@ cudaError_t tc_gemm(const TcGemm& p, int num_sms, int* flag, cudaStream_t s) {
   a.wout = p.wout;
   a.bout = p.bout;
   a.target = p.target;
-  a.delta_out = p.delta_out;
-  a.colpart2 = p.colpart2;
-  a.rowpart = p.rowpart;
-  a.inv_count = p.inv_count;
+  a.resid = p.resid;
   a.flag = flag;
   const long tiles = (long)a.tiles_m * a.splits;
   const int grid = (int)std::min<long>(tiles, num_sms);

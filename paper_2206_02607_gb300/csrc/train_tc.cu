@@ -9,9 +9,10 @@
 //   forward:  H[0] on the CUDA cores: the latent part W_0q q_b + b_0 is one vector per
 //             snapshot, so a point costs m FMAs per unit;
 //             H[h] = ELU(H[h-1] W_h^T + b_h) by the GEMM's bias + ELU epilogue;
-//             the last layer's epilogue also forms g, the residual, dL/dg and
-//             delta[L-1] = dL/dg w_out s'(z_{L-1}), with the column sums that give
-//             the gradients of w_out, b_out and b_{L-1};
+//             the last layer's epilogue also forms g (FP32, from the FP32 h) and the
+//             residual g - f; a row kernel then forms dL/dg, delta[L-1] =
+//             dL/dg w_out s'(z_{L-1}) and the column sums that give the gradients of
+//             w_out, b_out and b_{L-1};
 //   backward: for h = L-1 .. 1: dW_h = delta[h]^T H[h-1] (K = B*S, split over CTAs,
 //             the splits added in a fixed order) and delta[h-1] = (delta[h] W_h) s'(z_{h-1})
 //             with its column sums (db_{h-1}); then one pass over delta[0] forms, per
@@ -24,6 +25,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "crom_internal.h"
 
@@ -255,6 +257,75 @@ __global__ void layer0_grad_kernel(const float* snap, const float* q, const floa
   }
 }
 
+// The output layer's backward from h_L (bf16 rows of kW) and the residuals r = g - f
+// (FP32, from the GEMM epilogue that formed g from the FP32 h_L): per row
+// dL/dg = 2 r / N and delta_L[n][u] = dL/dg w_out[u] s'(z_u), s'(z) = 1 where h > 0,
+// else h + 1.  Warp p handles rows 32 p .. 32 p + 31 (one part), lane l columns
+// l kPer .. (kPer = kW / 32), four rows' loads in flight; per part the column sums of
+// delta (db_L) and of dL/dg h (dw_out) and the row sums of r^2 and dL/dg, each in
+// row order.
+constexpr int kOutWarps = 8;
+template <int kW>
+__global__ void out_delta_kernel(const uint16_t* H, const float* resid, const float* wout, long N, long nparts,
+                                 float inv_count, uint16_t* delta, float* colpart, float* colpart2, float* rowpart) {
+  constexpr int kPer = kW / 32;  // 2, 4 or 8 bf16 per lane
+  typedef typename std::conditional<kPer == 8, uint4, typename std::conditional<kPer == 4, uint2, uint32_t>::type>::type
+      Vec;
+  const long part = (long)blockIdx.x * kOutWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const long r0 = part * 32;
+  if (part >= nparts) return;  // whole warps; parts past N write zero sums
+  float wo[kPer], cs[kPer], cs2[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    wo[k] = wout[lane * kPer + k];
+    cs[k] = 0.f;
+    cs2[k] = 0.f;
+  }
+  float rr = 0.f, dgs = 0.f;
+  for (int i0 = 0; i0 < 32; i0 += 4) {
+    Vec hv[4];
+    float res[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long n = r0 + i0 + j;
+      const bool in = n < N;
+      hv[j] = in ? *reinterpret_cast<const Vec*>(H + n * kW + lane * kPer) : Vec{};
+      res[j] = in ? resid[n] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long n = r0 + i0 + j;
+      const uint32_t* hw = reinterpret_cast<const uint32_t*>(&hv[j]);
+      const float dg = 2.f * res[j] * inv_count;
+      uint32_t dw[kPer / 2];
+#pragma unroll
+      for (int k = 0; k < kPer / 2; ++k) {
+        const float h0 = bf16_val((uint16_t)(hw[k] & 0xffffu)), h1 = bf16_val((uint16_t)(hw[k] >> 16));
+        const float d0 = dg * wo[2 * k] * (h0 > 0.f ? 1.f : h0 + 1.f);
+        const float d1 = dg * wo[2 * k + 1] * (h1 > 0.f ? 1.f : h1 + 1.f);
+        cs[2 * k] += d0;
+        cs[2 * k + 1] += d1;
+        cs2[2 * k] = fmaf(dg, h0, cs2[2 * k]);
+        cs2[2 * k + 1] = fmaf(dg, h1, cs2[2 * k + 1]);
+        dw[k] = (uint32_t)bf16_bits(d0) | ((uint32_t)bf16_bits(d1) << 16);
+      }
+      if (n < N) *reinterpret_cast<Vec*>(delta + n * kW + lane * kPer) = *reinterpret_cast<const Vec*>(dw);
+      rr = fmaf(res[j], res[j], rr);
+      dgs += dg;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    colpart[part * kW + lane * kPer + k] = cs[k];
+    colpart2[part * kW + lane * kPer + k] = cs2[k];
+  }
+  if (lane == 0) {
+    rowpart[2 * part] = rr;
+    rowpart[2 * part + 1] = dgs;
+  }
+}
+
 // out[e] = sum_p part[p * stride + e], in order of p (compensated).  Eight loads are
 // issued before their additions, so that their latencies overlap.
 __global__ void sum_parts_kernel(const float* part, int nparts, long stride, long n, float* out) {
@@ -368,6 +439,7 @@ cudaError_t trainer_tc_alloc(crom_trainer* t) {
   c.colpart = (float*)A((size_t)tiles_m * 4 * w * 4);
   c.colpart2 = (float*)A((size_t)tiles_m * 4 * w * 4);
   c.rowpart = (float*)A((size_t)tiles_m * 4 * 2 * 4);
+  c.resid = (float*)A((size_t)N * 4);
   c.colmid = (float*)A((size_t)(tiles_m * 4 + kColPer - 1) / kColPer * w * 4);
   c.split = (float*)A((size_t)kSplitsW * w * w * 4);
   const int m = t->dec.m;
@@ -419,13 +491,23 @@ cudaError_t trainer_decoder_tc(crom_trainer* t, double* loss_out, int num_sms, c
       g.wout = p + lay.dec_w[L];
       g.bout = p + lay.dec_b[L];
       g.target = t->target;
-      g.delta_out = c.d0;
-      g.colpart = c.colpart;
-      g.colpart2 = c.colpart2;
-      g.rowpart = c.rowpart;
-      g.inv_count = (float)(1.0 / (double)N);
+      g.resid = c.resid;
     }
     if ((e = tc_gemm(g, num_sms, c.flag, s)) != cudaSuccess) return e;
+  }
+  // delta_L, the loss terms and the output layer's column sums from h_L and the residuals
+  {
+    const unsigned blocks = (unsigned)(((long)parts + kOutWarps - 1) / kOutWarps);
+    const float inv = (float)(1.0 / (double)N);
+    if (w == 256)
+      out_delta_kernel<256><<<blocks, 32 * kOutWarps, 0, s>>>(c.H[L - 1], c.resid, p + lay.dec_w[L], N, parts, inv, c.d0,
+                                                               c.colpart, c.colpart2, c.rowpart);
+    else if (w == 128)
+      out_delta_kernel<128><<<blocks, 32 * kOutWarps, 0, s>>>(c.H[L - 1], c.resid, p + lay.dec_w[L], N, parts, inv, c.d0,
+                                                               c.colpart, c.colpart2, c.rowpart);
+    else
+      out_delta_kernel<64><<<blocks, 32 * kOutWarps, 0, s>>>(c.H[L - 1], c.resid, p + lay.dec_w[L], N, parts, inv, c.d0,
+                                                              c.colpart, c.colpart2, c.rowpart);
   }
   loss_parts_kernel<<<1, 1024, 0, s>>>(c.rowpart, parts, 1.0 / (double)N, loss_out ? loss_out : t->loss_dev,
                                       gr + lay.dec_b[L]);
