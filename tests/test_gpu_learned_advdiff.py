@@ -25,7 +25,7 @@ diffusivity nu / s^2), the FOM's dt, 2 Gauss-Newton iterations; all 8 held-out
 trajectories advance together as 8 instances of one batched step.
 
 Bar: relative L2 of the reconstructed final field against the FOM's final field,
-for the FP32 and the F16X2 step."""
+for the FP32, the F16X2 and the F16 step."""
 import numpy as np
 import pytest
 
@@ -126,11 +126,11 @@ def learned(c, trajectories, request):
                 held=held.cpu().numpy().astype(np.float64), mu=mu, sigma=sigma, Xs=Xs, s=s, shape=request.param)
 
 
-@pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_F16X2"])
+@pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_F16X2", "CROM_PREC_F16"])
 def test_learned_advdiff_rollout_matches_full_order_solver(c, learned, prec_name):
     import torch
     L = learned
-    if prec_name == "CROM_PREC_F16X2" and L["shape"] != "w128_r15":
+    if prec_name != "CROM_PREC_FP32" and L["shape"] != "w128_r15":
         pytest.skip("the tensor-core step is built for width 128, r <= 15")
     w, spec, mu, sigma, s = L["w"], L["spec"], L["mu"], L["sigma"], L["s"]
     n, P = w.n, w.n * w.n
