@@ -177,7 +177,8 @@ def test_train_step_learned_model_shapes(c, prec_name, loss_tol, grad_tol):
     split-K weight gradients and fixed-order reductions at full depth."""
     errs = _step_and_check(c, dict(seed=4, n=256, r=16, width=256, hidden=5, B=64, S=4096),
                            getattr(c, prec_name), loss_tol, grad_tol, 1e-2, 1e-2)
-    print(prec_name, "max gradient-group rel. L2", max(errs.values()))
+    print(prec_name, "max gradient-group rel. L2", max(errs.values()),
+          "largest:", sorted(errs.items(), key=lambda kv: -kv[1])[:4])
 
 
 @pytest.mark.parametrize("prec_name", ["CROM_PREC_FP32", "CROM_PREC_BF16_MIXED"])
