@@ -58,7 +58,7 @@ def parse():
                          "(fixed; profilers distort the autotuner's timings)")
     ap.add_argument("--prec", default="f16x2", choices=["f16x2", "f16"],
                     help="tensor-core precision of --only step / recon")
-    ap.add_argument("--only", default=None, choices=["step", "recon", "plain", "fom", "heat", "train"],
+    ap.add_argument("--only", default=None, choices=["step", "recon", "plain", "fom", "heat", "train", "decode"],
                     help="run only one part (warmup + steps launches) for profiling; prints a short JSON line")
     return ap.parse_args()
 
@@ -87,6 +87,20 @@ def run_only(args):
         torch.cuda.synchronize()
         print(json.dumps({"only": args.only, "instances": w.n_inst, "calls": n,
                           "status_all_ok": bool((st.cpu().numpy() == 0).all())}))
+    elif args.only == "decode":
+        # crom_decode_tc (value, dg/dx, Laplacian, dg/dq) at the batch's integration samples
+        w = gen.heat2d_batched(n_inst=args.n_inst)
+        ctx = crom.crom_create(w.spec.m, w.spec.r, w.spec.width, w.spec.hidden, 0)
+        crom.crom_set_weights(ctx, gen.pack_params(w.params))
+        prec = crom.CROM_PREC_F16X2 if args.prec == "f16x2" else crom.CROM_PREC_F16
+        q, o = torch.tensor(w.q0, device="cuda"), torch.tensor(w.s_off, device="cuda")
+        x = torch.tensor(w.samples, device="cuda")
+        out = torch.empty((4 + w.spec.r, x.shape[0]), dtype=torch.float32, device="cuda")
+        want = crom.CROM_WANT_VAL | crom.CROM_WANT_DX | crom.CROM_WANT_LAP | crom.CROM_WANT_DQ
+        for _ in range(n):
+            crom.crom_decode_tc(ctx, q, o, x, want, out, precision=prec)
+        torch.cuda.synchronize()
+        print(json.dumps({"only": "decode", "instances": w.n_inst, "points": x.shape[0], "calls": n}))
     elif args.only == "train":
         # the learned-model training step (64 snapshots x 4096 points, width 256), bf16 tensor-core pass
         Bt, St, nt_side, rt, wt, Lt = 64, 4096, 256, 16, 256, 5
