@@ -438,7 +438,7 @@ int crom_reconstruct(crom_ctx* ctx, int precision, int n_codes, const double* q,
  *  init_idx  [n_init] distinct node indices, host
  *  idx_out   [max_samples] host: the selected node indices in order of addition
  *            (the initial ones first); count_out, metric_out host scalars.
- * step->pde must be CROM_PDE_HEAT; precision FP32 (no line search), F16X2 or F16.
+ * step->pde must be CROM_PDE_HEAT; precision FP32 (no line search) or F16X2.
  * Limits: 1 <= n_try <= 64, n_init <= max_samples <= min(n_nodes, 4096),
  * n_try * n_params <= 65535.  The call allocates its work buffers and returns
  * after the work on `stream` completed (not usable during stream capture). */

@@ -1013,11 +1013,11 @@ int crom_robust_samples(crom_ctx* ctx, const crom_step_desc* step, int precision
       step->gn_iters > 16 || !(step->dt > 0.0) || !isfinite(step->dt) ||
       (step->coef_per_sample != 0 && step->coef_per_sample != 1))
     return fail(CROM_ERR_INVALID_ARG, std::string(fn) + ": needs a heat step with valid gn_iters, dt, coefficient mode");
-  if (precision == CROM_PREC_F16X2 || precision == CROM_PREC_F16) {
+  if (precision == CROM_PREC_F16X2) {
     if (!tc_shape_ok(ctx->desc) || !ctx->w.tc_img)
-      return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": F16X2 and F16 need width 128, 2<=hidden<=5, m<=2, r<=15");
+      return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": F16X2 needs width 128, 2<=hidden<=5, m<=2, r<=15");
   } else if (precision != CROM_PREC_FP32 || step->line_search > 0) {
-    return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": precision FP32 (no line search), F16X2 or F16");
+    return fail(CROM_ERR_UNSUPPORTED, std::string(fn) + ": precision FP32 (no line search) or F16X2");
   }
   std::vector<int> M(init_idx, init_idx + n_init);
   {
