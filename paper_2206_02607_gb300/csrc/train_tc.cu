@@ -73,7 +73,7 @@ __global__ void layer0_const_kernel(const float* W0, const float* b0, const floa
 }
 
 // H[0][n][u] = ELU(c0[b(n)][u] + sum_k W_0[u][k] x_n[k]) in bf16, x [N][m] the
-// points' coordinates: a thread per pair of units, kRows0 rows per block (their
+// points' coordinates: a thread per four units, kRows0 rows per block (their
 // coordinates staged in shared memory).
 constexpr int kRows0 = 64;
 __global__ void layer0_fwd_kernel(const float* x_in, long N, int kin, int m, int S, const float* W0, const float* c0,
@@ -85,33 +85,32 @@ __global__ void layer0_fwd_kernel(const float* x_in, long N, int kin, int m, int
     xs[i / 3][i % 3] = (n < N && i % 3 < m) ? x_in[n * m + i % 3] : 0.f;
   }
   __syncthreads();
-  const int u = 2 * threadIdx.x;
+  const int u = 4 * threadIdx.x;  // four units per thread: 8-byte stores
   if (u >= w) return;
-  float wa[3], wb[3];
+  float wu[4][3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    wa[k] = k < m ? W0[(long)u * kin + k] : 0.f;
-    wb[k] = k < m ? W0[(long)(u + 1) * kin + k] : 0.f;
-  }
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) wu[j][k] = k < m ? W0[(long)(u + j) * kin + k] : 0.f;
   const long n1 = n0 + kRows0 < N ? n0 + kRows0 : N;
   long b = n0 / S, nb = (b + 1) * S;  // snapshot of row n and the first row of the next
-  float2 cb = *reinterpret_cast<const float2*>(c0 + b * w + u);
+  float4 cb = *reinterpret_cast<const float4*>(c0 + b * w + u);
 #pragma unroll 4
   for (long n = n0; n < n1; ++n) {
     if (n == nb) {
       ++b;
       nb += S;
-      cb = *reinterpret_cast<const float2*>(c0 + b * w + u);
+      cb = *reinterpret_cast<const float4*>(c0 + b * w + u);
     }
-    float za = cb.x, zb = cb.y;
+    float z[4] = {cb.x, cb.y, cb.z, cb.w};
     const float* x = xs[n - n0];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      za = fmaf(wa[k], x[k], za);
-      zb = fmaf(wb[k], x[k], zb);
-    }
-    *reinterpret_cast<uint32_t*>(H + n * w + u) =
-        (uint32_t)bf16_bits(elu_fast(za)) | ((uint32_t)bf16_bits(elu_fast(zb)) << 16);
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) z[j] = fmaf(wu[j][k], x[k], z[j]);
+    *reinterpret_cast<uint2*>(H + n * w + u) =
+        make_uint2((uint32_t)bf16_bits(elu_fast(z[0])) | ((uint32_t)bf16_bits(elu_fast(z[1])) << 16),
+                   (uint32_t)bf16_bits(elu_fast(z[2])) | ((uint32_t)bf16_bits(elu_fast(z[3])) << 16));
   }
 }
 
@@ -381,29 +380,31 @@ __global__ void colsum_level1_kernel(const float* part, int nparts, int cols, fl
 }
 
 // loss = sum_p rowpart[p][0] * inv_count; gb_out = sum_p rowpart[p][1]: each thread
-// a contiguous range of parts (compensated), then a fixed tree in FP64.
+// a contiguous range of parts (compensated), the warps' sums by fixed butterflies, the
+// 32 warp sums added in order by one thread in FP64.
 __global__ void loss_parts_kernel(const float* rowpart, int nparts, double inv_count, double* loss, float* gbout) {
   constexpr int kT = 1024;
-  __shared__ double red[2][kT];
+  __shared__ float red[2][kT / 32];
   CSum a, b;
   const int per = (nparts + kT - 1) / kT;
   for (int p = threadIdx.x * per; p < min(nparts, (int)(threadIdx.x + 1) * per); ++p) {
     a.add(rowpart[2 * p]);
     b.add(rowpart[2 * p + 1]);
   }
-  red[0][threadIdx.x] = (double)a.s + (double)a.c;
-  red[1][threadIdx.x] = (double)b.s + (double)b.c;
-  __syncthreads();
-  for (int o = kT / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) {
-      red[0][threadIdx.x] += red[0][threadIdx.x + o];
-      red[1][threadIdx.x] += red[1][threadIdx.x + o];
-    }
-    __syncthreads();
+  const float wa = warp_csum(a), wb = warp_csum(b);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = wa;
+    red[1][threadIdx.x >> 5] = wb;
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    *loss = red[0][0] * inv_count;
-    *gbout = (float)red[1][0];
+    double sa = 0.0, sb = 0.0;
+    for (int k = 0; k < kT / 32; ++k) {
+      sa += red[0][k];
+      sb += red[1][k];
+    }
+    *loss = sa * inv_count;
+    *gbout = (float)sb;
   }
 }
 
@@ -471,7 +472,7 @@ cudaError_t trainer_decoder_tc(crom_trainer* t, double* loss_out, int num_sms, c
   weights_bf16_kernel<<<nblk((long)(L - 1) * w * w, 256), 256, 0, s>>>(p, c.off_w, L, w, c.wh);
   // ---- forward
   layer0_const_kernel<<<B, w, 0, s>>>(p + lay.dec_w[0], p + lay.dec_b[0], t->q, m, r, w, c.c0);
-  layer0_fwd_kernel<<<nblk(N, kRows0), w / 2, 0, s>>>(c.xin, N, kin, m, S, p + lay.dec_w[0], c.c0, w, c.H[0]);
+  layer0_fwd_kernel<<<nblk(N, kRows0), w / 4, 0, s>>>(c.xin, N, kin, m, S, p + lay.dec_w[0], c.c0, w, c.H[0]);
   for (int h = 1; h < L; ++h) {
     TcGemm g;
     g.M = (int)N;
