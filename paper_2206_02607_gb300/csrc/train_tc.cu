@@ -380,31 +380,29 @@ __global__ void colsum_level1_kernel(const float* part, int nparts, int cols, fl
 }
 
 // loss = sum_p rowpart[p][0] * inv_count; gb_out = sum_p rowpart[p][1]: each thread
-// a contiguous range of parts (compensated), the warps' sums by fixed butterflies, the
-// 32 warp sums added in order by one thread in FP64.
+// a contiguous range of parts (compensated), then a fixed tree in FP64.
 __global__ void loss_parts_kernel(const float* rowpart, int nparts, double inv_count, double* loss, float* gbout) {
   constexpr int kT = 1024;
-  __shared__ float red[2][kT / 32];
+  __shared__ double red[2][kT];
   CSum a, b;
   const int per = (nparts + kT - 1) / kT;
   for (int p = threadIdx.x * per; p < min(nparts, (int)(threadIdx.x + 1) * per); ++p) {
     a.add(rowpart[2 * p]);
     b.add(rowpart[2 * p + 1]);
   }
-  const float wa = warp_csum(a), wb = warp_csum(b);
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = wa;
-    red[1][threadIdx.x >> 5] = wb;
-  }
+  red[0][threadIdx.x] = (double)a.s + (double)a.c;
+  red[1][threadIdx.x] = (double)b.s + (double)b.c;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double sa = 0.0, sb = 0.0;
-    for (int k = 0; k < kT / 32; ++k) {
-      sa += red[0][k];
-      sb += red[1][k];
+  for (int o = kT / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + o];
+      red[1][threadIdx.x] += red[1][threadIdx.x + o];
     }
-    *loss = sa * inv_count;
-    *gbout = (float)sb;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *loss = red[0][0] * inv_count;
+    *gbout = (float)red[1][0];
   }
 }
 

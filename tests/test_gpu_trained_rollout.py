@@ -9,9 +9,10 @@ Workload: 2D heat u_t = alpha Lap u on 48 x 48 nodes, zero Neumann, u0 = the sam
 8 Gaussian bumps (sigma in [0.06, 0.12], resolved by the 48-node grid) for every
 trajectory; training alpha in {0.5, 0.75, ..., 2.0},
 test alpha = 1.3; 96 FOM steps of dt = h^2 / 16, snapshots every 4 steps.
-Decoder R^{2+8} -> R, 5 ELU layers of width 128; 40000 Adam steps (the library's
+Decoder R^{2+8} -> R, 5 ELU layers of width 128; 80000 Adam steps (the library's
 bf16 tensor-core decoder pass) of 32 snapshots x 1024 nodes, learning rate 1e-3
-then decayed to 2e-5;
+for a quarter of them, then decayed to 2e-5 (with 40000 steps the final-field
+error sat at the 1e-2 bar, 7.6e-3 .. 1.2e-2 depending on rounding details);
 200 integration samples.
 
 Bar: relative L2 of the final reconstructed field against the FOM <= 1e-2 for
@@ -91,13 +92,13 @@ def trained(c):
     g = torch.Generator(device="cuda")
     g.manual_seed(5)
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
-    n_steps, losses = 40000, []
+    n_steps, losses = 80000, []
     for k in range(n_steps):
-        lr = 1e-3 if k < 10000 else 1e-3 * (2e-5 / 1e-3) ** ((k - 10000) / (n_steps - 10001))
+        lr = 1e-3 if k < 20000 else 1e-3 * (2e-5 / 1e-3) ** ((k - 20000) / (n_steps - 20001))
         pick = torch.randint(0, train.shape[0], (B,), device="cuda", generator=g)
         pts = torch.randint(0, P, (B, S), device="cuda", generator=g, dtype=torch.int32)
         c.crom_train_step(tr, train[pick].contiguous(), pts, coords, lr, loss)
-        if k % 8000 == 0 or k == n_steps - 1:
+        if k % 16000 == 0 or k == n_steps - 1:
             losses.append(loss.item())
     torch.cuda.synchronize()
     params = tr.get_params()
