@@ -255,9 +255,10 @@ int crom_set_weights(crom_ctx* ctx, const float* params, size_t n, int params_on
       if (fabsf(W1[(size_t)k * in + m + j]) > 65000.f) f16_range = false;
   }
   if (tc_shape_ok(d) && f16_range) {
-    // hidden matrices (K-major SW128), then the projection matrix P
+    // hidden matrices (K-major SW128), the projection matrix P, then the
+    // reconstruction's output operand (row 0 = f16(w_out), row 1 = its low part)
     const size_t layers_bytes = (size_t)(L - 1) * kTcLayerBytes;
-    std::vector<uint8_t> img(layers_bytes + kTcProjBytes, 0);
+    std::vector<uint8_t> img(layers_bytes + 2 * kTcProjBytes, 0);
     std::vector<uint16_t> lo((size_t)(L - 1) * w * w);
     for (int l = 0; l < L - 1; ++l)
       for (int o = 0; o < w; ++o)
@@ -275,6 +276,12 @@ int crom_set_weights(crom_ctx* ctx, const float* params, size_t n, int params_on
         const uint16_t v = f32_to_f16(val);
         memcpy(&img[layers_bytes + kmajor_sw128(row, k, kTcProjRows)], &v, 2);
       }
+    for (int k = 0; k < w; ++k) {
+      const uint16_t hi = f32_to_f16(Wout[k]);
+      const uint16_t lo = f32_to_f16(Wout[k] - f16_to_f32(hi));
+      memcpy(&img[layers_bytes + kTcProjBytes + kmajor_sw128(0, k, kTcProjRows)], &hi, 2);
+      memcpy(&img[layers_bytes + kTcProjBytes + kmajor_sw128(1, k, kTcProjRows)], &lo, 2);
+    }
     e = cudaMalloc(&dw.tc_img, img.size());
     if (e == cudaSuccess) e = cudaMemcpy(dw.tc_img, img.data(), img.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&dw.tc_lo, lo.size() * 2);
@@ -283,7 +290,7 @@ int crom_set_weights(crom_ctx* ctx, const float* params, size_t n, int params_on
       free_weights(ctx);
       return cuda_fail(e, "crom_set_weights (tensor-core image)");
     }
-    dw.tc_img_bytes = img.size();
+    dw.tc_img_bytes = layers_bytes + kTcProjBytes;  // what the step loads; the output operand follows
     dw.tc_lo_bytes = lo.size() * 2;
     float mx = 0.f, mo = 0.f;
     for (int u = 0; u < w; ++u) {

@@ -18,7 +18,9 @@ namespace crom {
 //                          K-major, 128B swizzle, two 64-column k-blocks
 //   [L*32768, +4096)       projection matrix P (16 x 128 f16, K-major, SW128):
 //                          row 0 = w_out, rows 1..r = W_1[:, m+j] (dg/dq projection)
-// and a second image of the hidden matrices' low parts W - f16(W), rounded to f16,
+//   [L*32768+4096, +4096)  output operand O of the reconstruction (same layout):
+//                          row 0 = f16(w_out), row 1 = f16(w_out - f16(w_out))
+// (tc_img_bytes counts the first two parts, which the step loads), and a second image of the hidden matrices' low parts W - f16(W), rounded to f16,
 // row-major [L][128][128] (loaded into tensor memory by the reconstruction kernel,
 // where it is the A operand of a third product per layer).
 constexpr int kTcWidth = 128;

@@ -335,6 +335,19 @@ __device__ __forceinline__ f32x2 elu2(f32x2 z, float& e0, float& e1) {
   e1 = ex2_approx(t1);
   return add2(pk2(fmaxf(z0, 0.f), fmaxf(z1, 0.f)), add2(pk2(e0, e1), pk2(-1.f, -1.f)));
 }
+// ELU of a pair when s'(z) is not wanted: e = 2^(-|z| log2 e) = e^{-|z|} needs no
+// clamp of the exponent (it is at most 1), and h = max(z, e - 1): for z > 0,
+// e - 1 < 0 < z; for z <= 0, e^z - 1 >= z (the exponential lies above its tangent
+// at 0), so the maximum is e^z - 1 (the same e as elu2 forms), or z itself near
+// z = 0 where the approximation of e^z - 1 falls below z.  No clamps and one
+// addition less than elu2.
+__device__ __forceinline__ f32x2 elu2_val(f32x2 z) {
+  float z0, z1, t0, t1, d0, d1;
+  unpk2(z, z0, z1);
+  unpk2(mul2(z, pk2(1.4426950408889634f, 1.4426950408889634f)), t0, t1);
+  unpk2(add2(pk2(ex2_approx(-fabsf(t0)), ex2_approx(-fabsf(t1))), pk2(-1.f, -1.f)), d0, d1);
+  return pk2(fmaxf(z0, d0), fmaxf(z1, d1));
+}
 
 // Pack two floats into bf16x2 (round to nearest even); low half = a.
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {

@@ -22,14 +22,23 @@
 //     W_lo = f16(W - f16(W)), read from tensor memory (the A operand of the
 //     TMEM form), into the first 64 columns.  The epilogue adds the two halves,
 //     the bias, applies ELU and writes the next operand;
-//   output layer: w_out . h_L on the CUDA cores in the last hidden layer's
-//     epilogue, in FP32 from h_L itself (a warp butterfly over the 32 units of
-//     each warp, then the four lane quadrants' partial sums), written coalesced.
+//   output layer, kSplit = 0: one more UMMA stage, O[n][j] = sum_k H[k][n] Wo[j][k]
+//     with the last hidden layer's operand block H (the tile's 128 points) as the
+//     MN-major A operand against the 16-row output operand Wo (row 0 = f16(w_out),
+//     row 1 = its low part); the epilogue adds a point's two products and the
+//     bias, one thread per point, written coalesced;
+//   output layer, kSplit = 1: w_out . h_L on the CUDA cores in the last hidden
+//     layer's epilogue, in FP32 from h_L itself (a warp butterfly over the 32
+//     units of each warp, then the four lane quadrants' partial sums).  The
+//     tensor-core stage measured slower here: the 64-point tiles make its fixed
+//     cost per point twice as large, on a tensor pipe that the third product
+//     already keeps busier.
 // Precision (kSplit = 1): activations carry ~2^-22 relative (hi + lo), weights
 // W + W_lo ~2^-22 (the W_lo lo product is below that and left out), FP32
-// accumulation.  kSplit = 0: f16 activations and weights (2^-11 relative each).
-// TMEM: slot s accumulator in columns 128 s .. 128 s + 127; W_lo of hidden matrix
-// l in columns 256 + 64 l .. + 63.
+// accumulation.  kSplit = 0: f16 activations and hidden weights (2^-11 relative
+// each), w_out ~2^-22.
+// TMEM: slot s accumulator in columns 128 s .. 128 s + 127 (the output stage's
+// 16 columns at its start); W_lo of hidden matrix l in columns 256 + 64 l .. + 63.
 #include <math.h>
 
 #include <algorithm>
@@ -57,6 +66,7 @@ constexpr int kMaxPts = 128;
 struct ReconParams {
   const uint8_t* img;  // hidden matrices, f16 K-major SW128
   int hidden_bytes;    // (hidden - 1) * 32 KB
+  const uint8_t* oimg;  // output operand Wo, 16 x 128 f16 K-major SW128 (4 KB)
   const uint16_t* lo;  // W_lo, f16 row-major [hidden - 1][128][128]
   int n_hidden_mats;   // hidden - 1
   int m, r;
@@ -85,7 +95,7 @@ struct __align__(16) Shared {
   float w1x[2][kTcWidth];
   float wout[kTcWidth];
   float xs[kSlots][2][kMaxPts];
-  float outp[kSlots][4][kMaxPts];  // output layer: partial sums of the four lane quadrants
+  float outp[kSlots][4][kMaxPts];  // CUDA-core output layer: the four lane quadrants' partial sums
 };
 
 // Sum over the 32 lanes of a warp (32 hidden units) of 16 per-lane values v[s]:
@@ -167,11 +177,13 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int kPts = kSplit ? 64 : 128;   // points per tile
+  constexpr bool kOutTc = !kSplit;          // output layer on the tensor cores
   constexpr int kPer = kPts / 2;            // points per epilogue thread
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m = p.m, r = p.r, L1 = p.n_hidden_mats;
   uint8_t* Wimg = sm;
-  uint8_t* Hbase = sm + p.hidden_bytes;
+  uint8_t* Oimg = sm + p.hidden_bytes;
+  uint8_t* Hbase = Oimg + kTcProjBytes;
   Shared* S = reinterpret_cast<Shared*>(Hbase + (size_t)kSlots * kHBuf);
 
   if (tid == 0) {
@@ -198,9 +210,10 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
   tc_fence_after();
   const uint32_t tb = S->tmem_base;
   if (tid == 0) {
-    mbar_arrive_expect_tx(&S->bar_w, (uint32_t)p.hidden_bytes);
+    mbar_arrive_expect_tx(&S->bar_w, (uint32_t)(p.hidden_bytes + (kOutTc ? kTcProjBytes : 0)));
     for (int off = 0; off < p.hidden_bytes; off += 16384)
       bulk_g2s(Wimg + off, p.img + off, (uint32_t)min(16384, p.hidden_bytes - off), &S->bar_w);
+    if (kOutTc) bulk_g2s(Oimg, p.oimg, (uint32_t)kTcProjBytes, &S->bar_w);
   }
   if (kSplit && warp < 4) {
     // W_lo into tensor memory: lane u = row u, column c = (k = 2c, 2c + 1)
@@ -235,19 +248,31 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
     const uint64_t dW = smem_desc_sw128(wbase, 16, 1024);
     constexpr uint32_t id_main = idesc_f16(128, 128, false, true, false);
     constexpr uint32_t id_lo = idesc_f16(128, 64, false, true, false);
+    constexpr uint32_t id_out = idesc_f16(128, 16, true, false, false);
+    const uint64_t dO = smem_desc_sw128(smem_u32(Oimg), 16, 1024);
     uint32_t pf[kSlots] = {0, 0};
     bool issued = false;
     for (int t0 = blockIdx.x * kSlots; t0 < p.n_tiles; t0 += stride) {
       const int nslot = min(kSlots, p.n_tiles - t0);
-      for (int l = 0; l < L1; ++l) {
+      for (int l = 0; l < L1 + (kOutTc ? 1 : 0); ++l) {
         for (int s = 0; s < nslot; ++s) {
           wait_or_abort(S, &S->full[s], pf[s]);
           pf[s] ^= 1;
           if (aborted(S)) continue;
           tc_fence_after();
           const uint32_t d = tb + (uint32_t)s * kSlotCols;
-          const uint64_t a0 = desc_add(dW, (uint32_t)l * kTcLayerBytes);
           const uint64_t b0 = smem_desc_sw128(smem_u32(Hbase + (size_t)s * kHBuf), 16384, 1024);
+          if (kOutTc && l == L1) {
+            // output stage: the operand block as the MN-major A operand
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk)
+              umma_f16_warp(d, desc_add(b0, mnmajor_kslice(kk)), desc_add(dO, kmajor_kslice(16, kk)), id_out,
+                            kk != 0);
+            umma_commit_warp(&S->acc[s]);
+            issued = true;
+            continue;
+          }
+          const uint64_t a0 = desc_add(dW, (uint32_t)l * kTcLayerBytes);
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk)
             umma_f16_warp(d, desc_add(a0, kmajor_kslice(128, kk)), desc_add(b0, mnmajor_kslice(kk)), id_main,
@@ -299,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
         c = (float)cc;
         cur_code = code;
       }
-      slot_sync(s);  // the previous tile's outputs are written
+      slot_sync(s);  // the previous tile's coordinates and outputs are used
       if (et < kPts) {
         S->xs[s][0][et] = xn0;
         S->xs[s][1][et] = xn1;
@@ -314,8 +339,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
         for (int i = 0; i < 8; ++i) {
           f32x2 z = fma2(pk2(wx0, wx0), pk2(S->xs[s][0][n0 + 2 * i], S->xs[s][0][n0 + 2 * i + 1]), pk2(c, c));
           if (m > 1) z = fma2(pk2(wx1, wx1), pk2(S->xs[s][1][n0 + 2 * i], S->xs[s][1][n0 + 2 * i + 1]), z);
-          float e0, e1;
-          h[i] = elu2(z, e0, e1);
+          h[i] = elu2_val(z);
         }
         store_split16<kSplit>(H, u, n0, h);
       }
@@ -325,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
       if (lane == 0) mbar_arrive(&S->full[s]);
       // ---- hidden layers: the accumulator, then the next operand (or the output)
       for (int l = 0; l < L1; ++l) {
-        const bool last = (l == L1 - 1);
+        const bool last_cc = !kOutTc && (l == L1 - 1);  // the output on the CUDA cores
         wait_or_abort(S, &S->acc[s], pa);
         pa ^= 1;
         tc_fence_after();
@@ -357,12 +381,11 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
           f32x2 h[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            float e0, e1;
             f32x2 z = add2(pk2(v[2 * i], v[2 * i + 1]), b2);
             if (kSplit) z = add2(z, pk2(w[2 * i], w[2 * i + 1]));
-            h[i] = elu2(z, e0, e1);
+            h[i] = elu2_val(z);
           }
-          if (!last) {
+          if (!last_cc) {
             store_split16<kSplit>(H, u, n0, h);
           } else {
             float wv[16];
@@ -381,17 +404,34 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
           }
         }
         tc_fence_before();
-        if (!last) {
+        if (!last_cc) {
           fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) mbar_arrive(&S->full[s]);
         }
       }
-      slot_sync(s);
-      if (et < kPts) {
-        const int n = p0 + et;
-        const float o = (S->outp[s][0][et] + S->outp[s][1][et]) + (S->outp[s][2][et] + S->outp[s][3][et]);
-        if (n < p.n_pts) p.out[(size_t)code * p.n_pts + n] = o + p.bout;
+      if constexpr (kOutTc) {
+        // ---- output stage: row u = 32 lq + lane of O (point u) in the first four warps
+        wait_or_abort(S, &S->acc[s], pa);
+        pa ^= 1;
+        tc_fence_after();
+        if (hf == 0) {
+          float ov[4];
+          tmem_ld4(taddr(acc, lane_base, 0), ov);
+          asm volatile("tcgen05.wait::ld.sync.aligned;"
+                       : "+f"(ov[0]), "+f"(ov[1]), "+f"(ov[2]), "+f"(ov[3])::"memory");
+          const int n = p0 + u;
+          // h . f16(w_out) + h . (its low part)
+          if (n < p.n_pts) p.out[(size_t)code * p.n_pts + n] = (ov[0] + ov[1]) + p.bout;
+        }
+        tc_fence_before();
+      } else {
+        slot_sync(s);
+        if (et < kPts) {
+          const int n = p0 + et;
+          const float o = (S->outp[s][0][et] + S->outp[s][1][et]) + (S->outp[s][2][et] + S->outp[s][3][et]);
+          if (n < p.n_pts) p.out[(size_t)code * p.n_pts + n] = o + p.bout;
+        }
       }
     }
   }
@@ -415,6 +455,7 @@ cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const d
   p.w1 = ctx->w.w1;
   p.b1 = ctx->w.b1;
   p.bh = ctx->w.bh;
+  p.oimg = ctx->w.tc_img + ctx->w.tc_img_bytes;
   p.wout = ctx->w.wout;
   p.bout = ctx->w.bout;
   p.q = q;
@@ -428,7 +469,7 @@ cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const d
   const long long tiles = (long long)n_codes * p.tiles_per_code;
   if (tiles > 0x7fffffffLL - 4096) return cudaErrorInvalidValue;  // t + stride stays an int
   p.n_tiles = (int)tiles;
-  const size_t smem = 1024 + (size_t)p.hidden_bytes + (size_t)kSlots * kHBuf + sizeof(Shared);
+  const size_t smem = 1024 + (size_t)p.hidden_bytes + kTcProjBytes + (size_t)kSlots * kHBuf + sizeof(Shared);
   const int grid = (int)std::min<long long>((tiles + kSlots - 1) / kSlots, ctx->num_sms);
   cudaError_t e;
   if (split) {
