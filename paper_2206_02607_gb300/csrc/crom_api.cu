@@ -249,6 +249,8 @@ int crom_set_weights(crom_ctx* ctx, const float* params, size_t n, int params_on
   for (int l = 0; l < L - 1 && f16_range; ++l)
     for (size_t i = 0; i < (size_t)w * w; ++i)
       if (fabsf(hidden_w[l][i]) > 65000.f) { f16_range = false; break; }
+  for (size_t i = 0; i < bh.size() && f16_range; ++i)
+    if (fabsf(bh[i]) > 45000.f) f16_range = false;  // log2 e * b in f16
   for (int k = 0; k < w && f16_range; ++k) {
     if (fabsf(Wout[k]) > 65000.f) f16_range = false;
     for (int j = 0; j < r; ++j)
@@ -258,7 +260,7 @@ int crom_set_weights(crom_ctx* ctx, const float* params, size_t n, int params_on
     // hidden matrices (K-major SW128), the projection matrix P, then the
     // reconstruction's output operand (row 0 = f16(w_out), row 1 = its low part)
     const size_t layers_bytes = (size_t)(L - 1) * kTcLayerBytes;
-    std::vector<uint8_t> img(layers_bytes + 2 * kTcProjBytes, 0);
+    std::vector<uint8_t> img(layers_bytes + 2 * kTcProjBytes + kTcBiasBytes, 0);
     std::vector<uint16_t> lo((size_t)(L - 1) * w * w);
     for (int l = 0; l < L - 1; ++l)
       for (int o = 0; o < w; ++o)
@@ -276,12 +278,26 @@ int crom_set_weights(crom_ctx* ctx, const float* params, size_t n, int params_on
         const uint16_t v = f32_to_f16(val);
         memcpy(&img[layers_bytes + kmajor_sw128(row, k, kTcProjRows)], &v, 2);
       }
+    // the f16 reconstruction's output and bias operands: high and low f16 parts of
+    // ln 2 * w_out and of log2 e * b_l (its activations are carried times log2 e)
+    auto split16 = [](double v, uint16_t& hi, uint16_t& lo) {
+      hi = f32_to_f16((float)v);
+      lo = f32_to_f16((float)(v - (double)f16_to_f32(hi)));
+    };
+    const double kLn2 = 0.6931471805599453, kLog2e = 1.4426950408889634;
     for (int k = 0; k < w; ++k) {
-      const uint16_t hi = f32_to_f16(Wout[k]);
-      const uint16_t lo = f32_to_f16(Wout[k] - f16_to_f32(hi));
+      uint16_t hi, lo;
+      split16(kLn2 * Wout[k], hi, lo);
       memcpy(&img[layers_bytes + kTcProjBytes + kmajor_sw128(0, k, kTcProjRows)], &hi, 2);
       memcpy(&img[layers_bytes + kTcProjBytes + kmajor_sw128(1, k, kTcProjRows)], &lo, 2);
     }
+    for (int l = 0; l < L - 1; ++l)
+      for (int u = 0; u < w; ++u) {
+        uint16_t hi, lo;
+        split16(kLog2e * bh[(size_t)l * w + u], hi, lo);
+        memcpy(&img[layers_bytes + 2 * kTcProjBytes + kmajor_sw128(u, 16 * l, w)], &hi, 2);
+        memcpy(&img[layers_bytes + 2 * kTcProjBytes + kmajor_sw128(u, 16 * l + 1, w)], &lo, 2);
+      }
     e = cudaMalloc(&dw.tc_img, img.size());
     if (e == cudaSuccess) e = cudaMemcpy(dw.tc_img, img.data(), img.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&dw.tc_lo, lo.size() * 2);

@@ -18,8 +18,12 @@ namespace crom {
 //                          K-major, 128B swizzle, two 64-column k-blocks
 //   [L*32768, +4096)       projection matrix P (16 x 128 f16, K-major, SW128):
 //                          row 0 = w_out, rows 1..r = W_1[:, m+j] (dg/dq projection)
-//   [L*32768+4096, +4096)  output operand O of the reconstruction (same layout):
-//                          row 0 = f16(w_out), row 1 = f16(w_out - f16(w_out))
+//   [L*32768+4096, +4096)  output operand O of the f16 reconstruction (same
+//                          layout): row 0 = f16(v), row 1 = f16(v - f16(v)) for
+//                          v = ln 2 * w_out (its activations carry a log2 e factor)
+//   [L*32768+8192, +16384) bias operand of the f16 reconstruction: 128 x 64 f16,
+//                          K-major, SW128; columns 16 l and 16 l + 1 hold the high
+//                          and low f16 parts of log2 e * b_l for hidden matrix l
 // (tc_img_bytes counts the first two parts, which the step loads), and a second image of the hidden matrices' low parts W - f16(W), rounded to f16,
 // row-major [L][128][128] (loaded into tensor memory by the reconstruction kernel,
 // where it is the A operand of a third product per layer).
@@ -33,6 +37,7 @@ constexpr int kTcTileS1Large = 16;
 constexpr int kTcTileS1Small = 8;
 constexpr int kTcProjRows = 16;
 constexpr int kTcProjBytes = kTcProjRows * kTcWidth * 2;
+constexpr int kTcBiasBytes = kTcWidth * 64 * 2;
 
 struct DeviceWeights {
   // FP32 copies for the CUDA-core path.

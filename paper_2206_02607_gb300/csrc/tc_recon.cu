@@ -21,12 +21,16 @@
 //     third product W_lo hi (N = 64) adds the weights' own low parts
 //     W_lo = f16(W - f16(W)), read from tensor memory (the A operand of the
 //     TMEM form), into the first 64 columns.  The epilogue adds the two halves,
-//     the bias, applies ELU and writes the next operand;
+//     the bias, applies ELU and writes the next operand.  With high parts only
+//     (kSplit = 0), where the epilogue's instruction issue is the limit, the
+//     activations are carried times log2 e (so that 2^x needs no scaling) and
+//     the bias enters the accumulator as one more UMMA, log2 e (b_hi + b_lo)
+//     times a ones operand (K = 16), leaving the epilogue ELU and the f16 store;
 //   output layer, kSplit = 0: one more UMMA stage, O[n][j] = sum_k H[k][n] Wo[j][k]
 //     with the last hidden layer's operand block H (the tile's 128 points) as the
-//     MN-major A operand against the 16-row output operand Wo (row 0 = f16(w_out),
-//     row 1 = its low part); the epilogue adds a point's two products and the
-//     bias, one thread per point, written coalesced;
+//     MN-major A operand against the 16-row output operand Wo (row 0 =
+//     f16(ln 2 w_out), row 1 = its low part); the epilogue adds a point's two
+//     products and the bias, one thread per point, written coalesced;
 //   output layer, kSplit = 1: w_out . h_L on the CUDA cores in the last hidden
 //     layer's epilogue, in FP32 from h_L itself (a warp butterfly over the 32
 //     units of each warp, then the four lane quadrants' partial sums).  The
@@ -36,7 +40,7 @@
 // Precision (kSplit = 1): activations carry ~2^-22 relative (hi + lo), weights
 // W + W_lo ~2^-22 (the W_lo lo product is below that and left out), FP32
 // accumulation.  kSplit = 0: f16 activations and hidden weights (2^-11 relative
-// each), w_out ~2^-22.
+// each), biases and w_out ~2^-22.
 // TMEM: slot s accumulator in columns 128 s .. 128 s + 127 (the output stage's
 // 16 columns at its start); W_lo of hidden matrix l in columns 256 + 64 l .. + 63.
 #include <math.h>
@@ -62,11 +66,13 @@ constexpr uint32_t kLoCol = 256;                   // W_lo of hidden matrix l at
 constexpr uint32_t kWaitLimit = 1u << 25;
 constexpr size_t kHBuf = (size_t)kTcWidth * 128 * 2;  // one slot's operand block: 128 columns, 32 KB
 constexpr int kMaxPts = 128;
+constexpr int kOnesBytes = 4096;  // ones operand of the bias product: 16 k-rows x 128 n, f16
 
 struct ReconParams {
   const uint8_t* img;  // hidden matrices, f16 K-major SW128
   int hidden_bytes;    // (hidden - 1) * 32 KB
-  const uint8_t* oimg;  // output operand Wo, 16 x 128 f16 K-major SW128 (4 KB)
+  const uint8_t* oimg;  // kSplit = 0: output operand Wo, 16 x 128 f16 K-major SW128 (4 KB),
+                        // then the bias operand, 128 x 64 f16 K-major SW128 (16 KB)
   const uint16_t* lo;  // W_lo, f16 row-major [hidden - 1][128][128]
   int n_hidden_mats;   // hidden - 1
   int m, r;
@@ -151,6 +157,23 @@ __device__ __forceinline__ void wait_or_abort(Shared* S, uint64_t* bar, uint32_t
   if (!mbar_wait(bar, parity, kWaitLimit)) *reinterpret_cast<volatile int*>(&S->abort) = 1;
 }
 
+// ELU in units of log2 e: for t = log2 e * z returns log2 e * ELU(z) =
+// max(t, log2 e (2^-|t| - 1)) (the maximum as in elu2_val); one multiply less a pair
+// than elu2_val on unscaled values.
+__device__ __forceinline__ f32x2 elu2_log2(f32x2 t) {
+  constexpr float kLog2e = 1.4426950408889634f;
+  float t0, t1, d0, d1;
+  unpk2(t, t0, t1);
+  unpk2(fma2(pk2(ex2_approx(-fabsf(t0)), ex2_approx(-fabsf(t1))), pk2(kLog2e, kLog2e), pk2(-kLog2e, -kLog2e)), d0,
+        d1);
+  return pk2(fmaxf(t0, d0), fmaxf(t1, d1));
+}
+
+// shared memory of the largest decoder (four hidden matrices) within the 227 KB per block
+static_assert(1024 + 4 * kTcLayerBytes + kTcProjBytes + kTcBiasBytes + kOnesBytes + kSlots * kHBuf + sizeof(Shared) <=
+                  232448,
+              "reconstruction shared memory");
+
 // Sixteen consecutive columns of row k, given as 8 packed pairs, stored as f16 hi
 // parts at columns n0..n0+15 (and lo = f16(h - hi) parts at 64 + n0.. when kSplit)
 // of the MN-major operand H.
@@ -182,8 +205,10 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m = p.m, r = p.r, L1 = p.n_hidden_mats;
   uint8_t* Wimg = sm;
-  uint8_t* Oimg = sm + p.hidden_bytes;
-  uint8_t* Hbase = Oimg + kTcProjBytes;
+  uint8_t* Oimg = sm + p.hidden_bytes;     // kSplit = 0: output operand,
+  uint8_t* Bimg = Oimg + kTcProjBytes;     // bias operand,
+  uint8_t* Ones = Bimg + kTcBiasBytes;     // and the ones operand of the bias product
+  uint8_t* Hbase = Ones + kOnesBytes;
   Shared* S = reinterpret_cast<Shared*>(Hbase + (size_t)kSlots * kHBuf);
 
   if (tid == 0) {
@@ -200,6 +225,14 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
     tmem_alloc(&S->tmem_base, kTmemCols);
     tmem_relinquish();
   }
+  if (!kSplit) {
+    // ones operand (MN-major, 16 k-rows x 128 n, two 64-column blocks of 2 KB):
+    // k-rows 0 and 1 are ones, the rest zero (a whole row is one value, so the
+    // swizzle leaves it in place)
+    for (int i = tid; i < kOnesBytes / 4; i += kThreads)
+      reinterpret_cast<uint32_t*>(Ones)[i] = ((i * 4) % 2048) / 128 < 2 ? 0x3C003C00u : 0u;
+    fence_proxy_async_smem();
+  }
   if (tid < kTcWidth) {
     for (int l = 0; l < L1; ++l) S->bh[l][tid] = p.bh[l * kTcWidth + tid];
     for (int k = 0; k < m; ++k) S->w1x[k][tid] = p.w1[tid * (m + r) + k];
@@ -210,10 +243,13 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
   tc_fence_after();
   const uint32_t tb = S->tmem_base;
   if (tid == 0) {
-    mbar_arrive_expect_tx(&S->bar_w, (uint32_t)(p.hidden_bytes + (kOutTc ? kTcProjBytes : 0)));
+    mbar_arrive_expect_tx(&S->bar_w, (uint32_t)(p.hidden_bytes + (kSplit ? 0 : kTcProjBytes + kTcBiasBytes)));
     for (int off = 0; off < p.hidden_bytes; off += 16384)
       bulk_g2s(Wimg + off, p.img + off, (uint32_t)min(16384, p.hidden_bytes - off), &S->bar_w);
-    if (kOutTc) bulk_g2s(Oimg, p.oimg, (uint32_t)kTcProjBytes, &S->bar_w);
+    if (!kSplit) {
+      bulk_g2s(Oimg, p.oimg, (uint32_t)kTcProjBytes, &S->bar_w);
+      bulk_g2s(Bimg, p.oimg + kTcProjBytes, (uint32_t)kTcBiasBytes, &S->bar_w);
+    }
   }
   if (kSplit && warp < 4) {
     // W_lo into tensor memory: lane u = row u, column c = (k = 2c, 2c + 1)
@@ -250,6 +286,8 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
     constexpr uint32_t id_lo = idesc_f16(128, 64, false, true, false);
     constexpr uint32_t id_out = idesc_f16(128, 16, true, false, false);
     const uint64_t dO = smem_desc_sw128(smem_u32(Oimg), 16, 1024);
+    const uint64_t dB = smem_desc_sw128(smem_u32(Bimg), 16, 1024);
+    const uint64_t dOnes = smem_desc_sw128(smem_u32(Ones), 2048, 1024);
     uint32_t pf[kSlots] = {0, 0};
     bool issued = false;
     for (int t0 = blockIdx.x * kSlots; t0 < p.n_tiles; t0 += stride) {
@@ -273,10 +311,12 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
             continue;
           }
           const uint64_t a0 = desc_add(dW, (uint32_t)l * kTcLayerBytes);
+          // kSplit = 0: the bias enters as a 17th product, (b_hi + b_lo) x ones
+          if (!kSplit) umma_f16_warp(d, desc_add(dB, kmajor_kslice(128, l)), dOnes, id_main, false);
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk)
             umma_f16_warp(d, desc_add(a0, kmajor_kslice(128, kk)), desc_add(b0, mnmajor_kslice(kk)), id_main,
-                          kk != 0);
+                          !kSplit || kk != 0);
           if (kSplit) {
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk)
@@ -300,7 +340,10 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
     const uint32_t lane_base = (uint32_t)lq * 32;
     const uint32_t acc = tb + (uint32_t)s * kSlotCols;
     uint8_t* H = Hbase + (size_t)s * kHBuf;
-    const float wx0 = S->w1x[0][u], wx1 = (m > 1) ? S->w1x[1][u] : 0.f;
+    // kSplit = 0 carries every activation times log2 e (layer 1 scaled here, the
+    // hidden biases and w_out in their operands)
+    constexpr float kAs = kSplit ? 1.f : 1.4426950408889634f;
+    const float wx0 = kAs * S->w1x[0][u], wx1 = (m > 1) ? kAs * S->w1x[1][u] : 0.f;
     const float wo = S->wout[u];
     uint32_t pa = 0;
     int cur_code = -1;
@@ -321,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
       if (code != cur_code) {
         double cc = (double)p.b1[u];
         for (int jj = 0; jj < r; ++jj) cc += (double)p.w1[u * (m + r) + m + jj] * p.q[(size_t)code * r + jj];
-        c = (float)cc;
+        c = (float)(kSplit ? cc : cc * 1.4426950408889634);
         cur_code = code;
       }
       slot_sync(s);  // the previous tile's coordinates and outputs are used
@@ -339,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
         for (int i = 0; i < 8; ++i) {
           f32x2 z = fma2(pk2(wx0, wx0), pk2(S->xs[s][0][n0 + 2 * i], S->xs[s][0][n0 + 2 * i + 1]), pk2(c, c));
           if (m > 1) z = fma2(pk2(wx1, wx1), pk2(S->xs[s][1][n0 + 2 * i], S->xs[s][1][n0 + 2 * i + 1]), z);
-          h[i] = elu2_val(z);
+          h[i] = kSplit ? elu2_val(z) : elu2_log2(z);
         }
         store_split16<kSplit>(H, u, n0, h);
       }
@@ -381,9 +424,12 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
           f32x2 h[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            f32x2 z = add2(pk2(v[2 * i], v[2 * i + 1]), b2);
-            if (kSplit) z = add2(z, pk2(w[2 * i], w[2 * i + 1]));
-            h[i] = elu2_val(z);
+            if (kSplit) {
+              const f32x2 z = add2(add2(pk2(v[2 * i], v[2 * i + 1]), b2), pk2(w[2 * i], w[2 * i + 1]));
+              h[i] = elu2_val(z);
+            } else {
+              h[i] = elu2_log2(pk2(v[2 * i], v[2 * i + 1]));  // the bias is in the accumulator
+            }
           }
           if (!last_cc) {
             store_split16<kSplit>(H, u, n0, h);
@@ -421,7 +467,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(ReconParams p) {
           asm volatile("tcgen05.wait::ld.sync.aligned;"
                        : "+f"(ov[0]), "+f"(ov[1]), "+f"(ov[2]), "+f"(ov[3])::"memory");
           const int n = p0 + u;
-          // h . f16(w_out) + h . (its low part)
+          // (log2 e h) . f16(ln 2 w_out) + (log2 e h) . (its low part)
           if (n < p.n_pts) p.out[(size_t)code * p.n_pts + n] = (ov[0] + ov[1]) + p.bout;
         }
         tc_fence_before();
@@ -455,7 +501,7 @@ cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const d
   p.w1 = ctx->w.w1;
   p.b1 = ctx->w.b1;
   p.bh = ctx->w.bh;
-  p.oimg = ctx->w.tc_img + ctx->w.tc_img_bytes;
+  p.oimg = ctx->w.tc_img + ctx->w.tc_img_bytes;  // output operand, then the bias operand
   p.wout = ctx->w.wout;
   p.bout = ctx->w.bout;
   p.q = q;
@@ -469,7 +515,8 @@ cudaError_t launch_recon_tc(const crom_ctx* ctx, int split, int n_codes, const d
   const long long tiles = (long long)n_codes * p.tiles_per_code;
   if (tiles > 0x7fffffffLL - 4096) return cudaErrorInvalidValue;  // t + stride stays an int
   p.n_tiles = (int)tiles;
-  const size_t smem = 1024 + (size_t)p.hidden_bytes + kTcProjBytes + (size_t)kSlots * kHBuf + sizeof(Shared);
+  const size_t smem =
+      1024 + (size_t)p.hidden_bytes + kTcProjBytes + kTcBiasBytes + kOnesBytes + (size_t)kSlots * kHBuf + sizeof(Shared);
   const int grid = (int)std::min<long long>((tiles + kSlots - 1) / kSlots, ctx->num_sms);
   cudaError_t e;
   if (split) {
