@@ -66,12 +66,16 @@ typedef enum {
  *           (and per Gauss-Newton iteration for the difference channel), so that
  *           their f16 operands stay in range.  FP32 activation/derivative chains,
  *           FP64 normal equations.  width == 128, 2 <= hidden <= 5, m <= 2, r <= 15,
- *           ELU, every hidden weight, w_out and W_1q entry of magnitude <= 65000.
+ *           ELU, every hidden weight, w_out and W_1q entry of magnitude <= 65000
+ *           and every hidden bias of magnitude <= 45000.
  *           f16 rather than bf16 operands: both run at the same tensor rate, and
  *           bf16 weights (2^-9) move dense outputs by ~5e-3 and latent increments by
  *           several per cent against FP32 weights.
  *  F16    : as F16X2 with the high parts of the activations only (single f16
- *           operands, 2^-12 relative) and f16 weights.  Dense reconstruction and
+ *           operands, 2^-12 relative) and f16 weights (the dense reconstruction
+ *           adds the hidden biases and w_out as f16 high and low parts, ~2^-22, on
+ *           the tensor cores, and scales its activations by log2 e inside; the
+ *           outputs are unscaled).  Dense reconstruction and
  *           the step: the step's sample tiles hold twice the samples for the same
  *           UMMA widths (about 1.5x the F16X2 step's speed); its per-step errors
  *           are up to ~10x F16X2's on ill-conditioned decoders (kappa(J) ~ 1e5).
