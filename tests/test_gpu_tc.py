@@ -76,7 +76,54 @@ def test_reconstruct_tc_full_grid_sampled():
         torch.cuda.synchronize()
         assert not torch.isnan(out).any().item()
         got = out[torch.as_tensor(ci, device="cuda"), torch.as_tensor(pi, device="cuda")].cpu().numpy()
+        print(f"dense 1024^2 x 64, precision {prec}: sampled rel. L2 {rel_l2(got, ref):.2e}")
         assert rel_l2(got, ref) < tol, (prec, rel_l2(got, ref))
+
+
+def test_reconstruct_tc_large_biases():
+    """Hidden biases of order one and more: at F16 the dense reconstruction adds them
+    on the tensor cores (f16 high and low parts of log2 e * b against a ones
+    operand) and carries its activations times log2 e; same tolerances as above."""
+    import torch
+    c = crom()
+    spec = gen.DecoderSpec(2, 8, 128, 4)
+    params = gen.xavier_decoder(spec, seed=11, bias_std=2.0)
+    ctx = make_ctx(spec, params)
+    X = np.random.default_rng(3).uniform(0, 1, size=(777, 2)).astype(np.float32)
+    codes = np.random.default_rng(4).standard_normal((2, 8))
+    ref = O.reconstruct(O.MLPDecoder(params, 2), codes, X)
+    for prec, tol in ((c.CROM_PREC_F16X2, 1e-4), (c.CROM_PREC_F16, 3e-3)):
+        out = torch.full((2, 777), float("nan"), dtype=torch.float32, device="cuda")
+        c.crom_reconstruct(ctx, dev(codes, torch.float64), dev(X, torch.float32), out, precision=prec)
+        err = rel_l2(out.cpu().numpy(), ref)
+        print(f"large biases, precision {prec}: {err:.2e}")
+        assert err < tol, (prec, err)
+    ctx.close()
+
+
+def test_tensor_core_precisions_refuse_biases_beyond_f16_range():
+    """A hidden bias beyond 45000 (log2 e * b would leave the f16 range) leaves the
+    tensor-core images out: F16X2 / F16 return UNSUPPORTED, FP32 still runs."""
+    import torch
+    c = crom()
+    spec = gen.DecoderSpec(2, 8, 128, 3)
+    params = gen.xavier_decoder(spec, seed=12, bias_std=0.1)
+    W, b = params[1]
+    b = b.copy()
+    b[5] = 5e4
+    params[1] = (W, b)
+    ctx = make_ctx(spec, params)
+    q = torch.zeros((1, 8), dtype=torch.float64, device="cuda")
+    x = torch.full((4, 2), 0.5, dtype=torch.float32, device="cuda")
+    out = torch.empty((1, 4), dtype=torch.float32, device="cuda")
+    for prec in (c.CROM_PREC_F16X2, c.CROM_PREC_F16):
+        with pytest.raises(c.CromError) as e:
+            c.crom_reconstruct(ctx, q, x, out, precision=prec)
+        assert e.value.code == c.CROM_ERR_UNSUPPORTED
+    c.crom_reconstruct(ctx, q, x, out, precision=c.CROM_PREC_FP32)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(out.cpu().numpy()))
+    ctx.close()
 
 
 def test_reconstruct_tc_rejects_unsupported_shape():
