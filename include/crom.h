@@ -75,7 +75,8 @@ typedef enum {
  *           operands, 2^-12 relative) and f16 weights (the dense reconstruction
  *           adds the hidden biases and w_out as f16 high and low parts, ~2^-22, on
  *           the tensor cores, and scales its activations by log2 e inside; the
- *           outputs are unscaled).  Dense reconstruction and
+ *           outputs are unscaled): dense error ~1e-3 against FP64 (F16X2 ~1e-6).
+ *           Dense reconstruction and
  *           the step: the step's sample tiles hold twice the samples for the same
  *           UMMA widths (about 1.5x the F16X2 step's speed); its per-step errors
  *           are up to ~10x F16X2's on ill-conditioned decoders (kappa(J) ~ 1e5).
