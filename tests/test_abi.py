@@ -82,3 +82,55 @@ def test_checkpoint_checksum_is_crc32(lib):
     for n in (1, 7, 64, 1000, 65537):
         data = rng.integers(0, 256, size=n, dtype=np.uint8).tobytes()
         assert lib.crom_crc32(data) == zlib.crc32(data)
+
+
+def test_every_entry_point_rejects_null_handles_on_the_host(lib):
+    """Each context / trainer entry point checks its handle (and the arguments it
+    validates before any device work) on the host: INVALID_ARG with a message that
+    names the call, no CUDA call made (this runs without a GPU)."""
+    sd = lib.crom_step_desc(0, 1, 1e-5)
+    sdp = ctypes.byref(sd)
+    calls = {
+        "crom_set_weights": (None, None, 0, 0, None),
+        "crom_decode_tc": (None, 1, 1, None, None, None, 1, 1, None, None),
+        "crom_device_flags": (None, None, None),
+        "crom_rollout": (None, sdp, 1, 1, 1, None, None, None, None, None, 1, 1, None, None),
+        "crom_step_host": (None, sdp, 1, 1, None, None, None, None, None, 1, 1, None, None),
+        "crom_step_noalloc": (None, sdp, 1, None, None, None, None, None, 1, 1, None, None),
+        "crom_set_step_tiles": (None, 8, 16),
+        "crom_get_step_tiles": (None, None, None, None),
+        "crom_autotune": (None, sdp, 1, None, None, None, None, None, 1, 1, None, None),
+        "crom_tangent_velocity": (None, 1, None, None, 1e-3, None, None, 1, None, None),
+        "crom_robust_samples": (None, sdp, 1, 1, None, None, 1, 1, None, None, 1, None, 1, 0.0, 8, None, None,
+                                None, None),
+        "crom_trainer_param_count": (None, None),
+        "crom_trainer_set_precision": (None, 0),
+        "crom_trainer_set_params": (None, None, 0, 0, None),
+        "crom_trainer_get_params": (None, None, 0, 0, None),
+        "crom_trainer_get_grads": (None, None, 0, 0, None),
+        "crom_train_step": (None, None, None, None, 1e-3, None, None),
+        "crom_encode": (None, 1, None, None, None),
+        "crom_trainer_save": (None, b"/nonexistent/ckpt"),
+        "crom_trainer_load": (None, b"/nonexistent/ckpt"),
+    }
+    for name, args in calls.items():
+        assert name in lib.EXPORTED, name
+        assert lib.raw_call(name, *args) == lib.CROM_ERR_INVALID_ARG, name
+        assert name in lib.last_error(), (name, lib.last_error())
+
+
+def test_full_order_and_watchdog_argument_checks_on_the_host(lib):
+    """crom_fom_step validates kind, sizes and dt, and crom_stream_wait its timeout,
+    before touching a device."""
+    bad = [(-1, 1, 8, 8, 1e-3), (99, 1, 8, 8, 1e-3), (lib.CROM_FOM_HEAT2D_NEUMANN, 1, 2, 2, 1e-3),
+           (lib.CROM_FOM_HEAT2D_NEUMANN, 1, 8, 7, 1e-3), (lib.CROM_FOM_HEAT2D_NEUMANN, 1, 8, 8, 0.0),
+           (lib.CROM_FOM_HEAT2D_NEUMANN, 1, 8, 8, float("nan")), (lib.CROM_FOM_HEAT2D_NEUMANN, -1, 8, 8, 1e-3),
+           (lib.CROM_FOM_HEAT2D_NEUMANN, 70000, 8, 8, 1e-3)]
+    for kind, nb, nx, ny, dt in bad:
+        assert lib.raw_call("crom_fom_step", kind, nb, nx, ny, None, None, None, dt, 1, None, None, None) == \
+            lib.CROM_ERR_INVALID_ARG, (kind, nb, nx, ny, dt)
+    # nothing to do is not an error, and needs no device
+    assert lib.raw_call("crom_fom_step", lib.CROM_FOM_HEAT2D_NEUMANN, 0, 8, 8, None, None, None, 1e-3, 1,
+                        None, None, None) == lib.CROM_OK
+    assert lib.raw_call("crom_stream_wait", None, -1.0) == lib.CROM_ERR_INVALID_ARG
+    assert lib.raw_call("crom_stream_wait", None, float("nan")) == lib.CROM_ERR_INVALID_ARG
